@@ -1,0 +1,220 @@
+"""Python harness for the FP64 brute-force oracle (``srp_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference legs.  The library under
+``paper_2608_07307_gb300/`` never imports this module, and this module never
+imports that library (it reads meshes produced by the shared input generators
+as plain numpy arrays).
+
+The C code is compiled with gcc on first use (or by ``build()``) into
+``oracle/_build/liboracle.so`` with floating-point contraction disabled, so
+x86 and Arm hosts round identically.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+BUILD = os.path.join(HERE, "_build")
+SOURCES = ["srp_oracle.c", "prop_oracle.c"]
+LIB = os.path.join(BUILD, "liboracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, no FP contraction, no fast-math)."""
+    srcs = [os.path.join(HERE, s) for s in SOURCES if os.path.exists(os.path.join(HERE, s))]
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in srcs):
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=BUILD)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class _Mesh(C.Structure):
+    _fields_ = [
+        ("n_verts", C.c_int32), ("xyz", C.POINTER(C.c_double)),
+        ("n_tris", C.c_int32), ("tri", C.POINTER(C.c_int32)),
+        ("tri_part", C.POINTER(C.c_int32)), ("tri_mat", C.POINTER(C.c_int32)),
+        ("n_mats", C.c_int32), ("mat", C.POINTER(C.c_double)),
+        ("n_parts", C.c_int32), ("parent", C.POINTER(C.c_int32)),
+        ("pivot", C.POINTER(C.c_double)), ("axis", C.POINTER(C.c_double)),
+        ("limits", C.POINTER(C.c_double)), ("normal0", C.POINTER(C.c_double)),
+        ("c_ref", C.c_double * 3),
+    ]
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("N", C.c_int32), ("bounces", C.c_int32), ("P0", C.c_double), ("dist_au", C.c_double),
+        ("eps_rel", C.c_double), ("track", C.c_int32), ("angles", C.POINTER(C.c_double)),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_eval_range.restype = C.c_int
+        _lib.orc_eval_rays.restype = C.c_int
+        _lib.orc_pose.restype = C.c_int
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class OMesh:
+    """A mesh held in the C layout (FP32 vertices promoted exactly to FP64)."""
+
+    def __init__(self, mesh):
+        self.keep = dict(
+            xyz=np.ascontiguousarray(np.asarray(mesh.xyz).astype(np.float64)),
+            tri=np.ascontiguousarray(mesh.tri.astype(np.int32)),
+            tri_part=np.ascontiguousarray(mesh.tri_part.astype(np.int32)),
+            tri_mat=np.ascontiguousarray(mesh.tri_mat.astype(np.int32)),
+            mat=np.ascontiguousarray(np.asarray(mesh.mat, np.float64)),
+            parent=np.ascontiguousarray(mesh.parent.astype(np.int32)),
+            pivot=np.ascontiguousarray(np.asarray(mesh.pivot, np.float64)),
+            axis=np.ascontiguousarray(np.asarray(mesh.axis, np.float64)),
+            limits=np.ascontiguousarray(np.asarray(mesh.limits, np.float64)),
+            normal0=np.ascontiguousarray(np.asarray(mesh.normal0, np.float64)),
+        )
+        k = self.keep
+        self.n_parts = len(k["parent"])
+        self.s = _Mesh(len(k["xyz"]), _dp(k["xyz"]), len(k["tri"]), _ip(k["tri"]), _ip(k["tri_part"]),
+                       _ip(k["tri_mat"]), len(k["mat"]), _dp(k["mat"]), self.n_parts, _ip(k["parent"]),
+                       _dp(k["pivot"]), _dp(k["axis"]), _dp(k["limits"]), _dp(k["normal0"]),
+                       (C.c_double * 3)(*np.asarray(mesh.c_ref, np.float64)))
+
+
+def _params(N, bounces, P0, dist_au, eps_rel, angles, n_parts):
+    if angles is None:
+        return _Params(N, bounces, P0, dist_au, eps_rel, 1, None), None
+    a = np.ascontiguousarray(np.asarray(angles, np.float64).reshape(n_parts))
+    return _Params(N, bounces, P0, dist_au, eps_rel, 0, _dp(a)), a
+
+
+def pose(mesh, s, angles=None):
+    """(joint angles [P], posed vertices [V,3]) for Sun direction s (Sec. 4.4.2)."""
+    om = OMesh(mesh)
+    s = np.ascontiguousarray(np.asarray(s, np.float64))
+    ang = np.zeros(om.n_parts)
+    xyz = np.zeros_like(om.keep["xyz"])
+    a_in = None if angles is None else np.ascontiguousarray(np.asarray(angles, np.float64))
+    rc = lib().orc_pose(C.byref(om.s), _dp(s), C.c_int32(0 if angles is not None else 1),
+                        _dp(a_in) if a_in is not None else None, _dp(ang), _dp(xyz))
+    if rc != 0:
+        raise ValueError(f"orc_pose failed: {rc}")
+    return ang, xyz
+
+
+def eval_range(mesh, s, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None, r0=0, r1=None,
+               want_hits=False, want_edge=False, _om=None):
+    """Trace rays [r0, r1) of one direction.  Returns a dict with the unscaled
+    sums `acc` (6), the `scale` P dA, the window `win` (8), joint `angles`,
+    per-segment hit counts `nhit`, and optionally `hits` / `edge` per ray."""
+    om = _om or OMesh(mesh)
+    r1 = N * N if r1 is None else r1
+    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts)
+    s = np.ascontiguousarray(np.asarray(s, np.float64))
+    acc = np.zeros(6)
+    scale = np.zeros(1)
+    win = np.zeros(8)
+    ang = np.zeros(om.n_parts)
+    nseg = bounces + 1
+    hits = np.empty((r1 - r0, nseg), np.int32) if want_hits else None
+    edge = np.empty((r1 - r0, nseg), np.float64) if want_edge else None
+    nhit = np.zeros(nseg, np.int64)
+    rc = lib().orc_eval_range(C.byref(om.s), C.byref(p), _dp(s), C.c_int64(r0), C.c_int64(r1), _dp(acc),
+                              _dp(scale), _dp(win), _dp(ang), _ip(hits) if hits is not None else None,
+                              _dp(edge) if edge is not None else None,
+                              nhit.ctypes.data_as(C.POINTER(C.c_int64)))
+    if rc != 0:
+        raise ValueError(f"orc_eval_range failed: {rc}")
+    return dict(acc=acc, scale=float(scale[0]), win=win, angles=ang, nhit=nhit, hits=hits, edge=edge)
+
+
+def _worker(args):
+    mesh, s, kw, r0, r1 = args
+    return eval_range(mesh, s, r0=r0, r1=r1, **kw)
+
+
+def evaluate(mesh, s, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None, want_hits=False,
+             want_edge=False, procs=1, chunks=None):
+    """Force F (N) and torque T (N m) about c_ref for one Sun direction.
+
+    With procs > 1 the ray range is split into contiguous chunks traced by
+    spawn-started worker processes (each single-threaded); the partial sums
+    are added in chunk order, so the result does not depend on scheduling."""
+    kw = dict(N=N, bounces=bounces, P0=P0, dist_au=dist_au, eps_rel=eps_rel, angles=angles,
+              want_hits=want_hits, want_edge=want_edge)
+    R = N * N
+    if procs <= 1:
+        parts = [eval_range(mesh, s, **kw)]
+    else:
+        import multiprocessing as mp
+        n = chunks or procs * 4
+        bounds = [R * k // n for k in range(n + 1)]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(procs) as pool:
+            parts = pool.map(_worker, [(mesh, s, kw, bounds[k], bounds[k + 1]) for k in range(n)])
+    acc = np.zeros(6)
+    for q in parts:
+        acc = acc + q["acc"]
+    out = dict(parts[0])
+    out["acc"] = acc
+    out["nhit"] = sum(q["nhit"] for q in parts)
+    if want_hits:
+        out["hits"] = np.concatenate([q["hits"] for q in parts])
+    if want_edge:
+        out["edge"] = np.concatenate([q["edge"] for q in parts])
+    out["F"] = acc[:3] * out["scale"]
+    out["T"] = acc[3:] * out["scale"]
+    return out
+
+
+def eval_rays(mesh, s, rays, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None):
+    """Per-ray unscaled contributions [n, 6], hits [n, nseg] and edge proximity
+    [n, nseg] for an explicit list of primary ray indices (sampled checks)."""
+    om = OMesh(mesh)
+    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts)
+    rays = np.ascontiguousarray(np.asarray(rays, np.int64))
+    n = len(rays)
+    nseg = bounces + 1
+    contrib = np.zeros((n, 6))
+    hits = np.empty((n, nseg), np.int32)
+    edge = np.empty((n, nseg))
+    s = np.ascontiguousarray(np.asarray(s, np.float64))
+    rc = lib().orc_eval_rays(C.byref(om.s), C.byref(p), _dp(s), C.c_int64(n),
+                             rays.ctypes.data_as(C.POINTER(C.c_int64)), _dp(contrib), _ip(hits), _dp(edge))
+    if rc != 0:
+        raise ValueError(f"orc_eval_rays failed: {rc}")
+    return dict(contrib=contrib, hits=hits, edge=edge)
+
+
+def timed_rays(mesh, s, N, bounces, n_rays, seed=0, **kw):
+    """Time the oracle on n_rays sampled primary rays (single thread).
+    Returns (seconds, rays traced)."""
+    rng = np.random.default_rng(seed)
+    rays = rng.choice(N * N, size=min(n_rays, N * N), replace=False)
+    t0 = time.perf_counter()
+    eval_rays(mesh, s, rays, N, bounces, **kw)
+    return time.perf_counter() - t0, len(rays)
