@@ -24,6 +24,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["srp_oracle.c", "prop_oracle.c"]
+HEADERS = ["srp_oracle.h"]
 LIB = os.path.join(BUILD, "liboracle.so")
 
 _lib = None
@@ -31,8 +32,9 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, -O2, no FP contraction, no fast-math)."""
-    srcs = [os.path.join(HERE, s) for s in SOURCES if os.path.exists(os.path.join(HERE, s))]
-    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in srcs):
+    srcs = [os.path.join(HERE, s) for s in SOURCES]
+    deps = srcs + [os.path.join(HERE, h) for h in HEADERS]
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in deps):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=BUILD)
@@ -218,3 +220,68 @@ def timed_rays(mesh, s, N, bounces, n_rays, seed=0, **kw):
     t0 = time.perf_counter()
     eval_rays(mesh, s, rays, N, bounces, **kw)
     return time.perf_counter() - t0, len(rays)
+
+
+# --------------------------------------------------------------- propagation
+class Prop(C.Structure):
+    """Propagation settings (layout of orc_prop in prop_oracle.c)."""
+    _fields_ = [
+        ("central", C.c_int32), ("j2", C.c_int32), ("sun3", C.c_int32), ("srp", C.c_int32),
+        ("attitude", C.c_int32), ("q", C.c_double * 4), ("epoch_mjd_tt", C.c_double), ("mass", C.c_double),
+        ("N", C.c_int32), ("bounces", C.c_int32), ("P0", C.c_double), ("eps_rel", C.c_double),
+        ("method", C.c_int32), ("rtol", C.c_double), ("atol_pos", C.c_double), ("atol_vel", C.c_double),
+        ("h0", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double), ("max_steps", C.c_int64),
+    ]
+
+
+def prop_params(central=0, j2=False, sun3=False, srp=False, attitude=0, q=(1.0, 0.0, 0.0, 0.0),
+                epoch_mjd_tt=61041.0, mass=1000.0, N=64, bounces=1, P0=4.56e-6, eps_rel=1e-9, method=0,
+                rtol=1e-12, atol_pos=1e-6, atol_vel=1e-9, h0=60.0, h_min=1e-6, h_max=0.0, max_steps=10_000_000):
+    return Prop(central, int(j2), int(sun3), int(srp), attitude, (C.c_double * 4)(*q), epoch_mjd_tt, mass, N,
+                bounces, P0, eps_rel, method, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps)
+
+
+def rkf78_tableau():
+    c, a, b7, b8 = np.zeros(13), np.zeros(169), np.zeros(13), np.zeros(13)
+    lib().orc_rkf78_tableau(_dp(c), _dp(a), _dp(b7), _dp(b8))
+    return c, a.reshape(13, 13), b7, b8
+
+
+def sun_position(mjd_tt):
+    r = np.zeros(3)
+    lib().orc_sun_position(C.c_double(mjd_tt), _dp(r))
+    return r
+
+
+def attitude(pp, y):
+    R = np.zeros(9)
+    y = np.ascontiguousarray(np.asarray(y, np.float64))
+    lib().orc_attitude(C.byref(pp), _dp(y), _dp(R))
+    return R.reshape(3, 3)
+
+
+def accel(mesh, pp, t, y):
+    """(a [3], aux [8]) with aux = Sun dir body, Sun distance AU, shadow flag, F_body."""
+    om = OMesh(mesh) if mesh is not None else None
+    y = np.ascontiguousarray(np.asarray(y, np.float64))
+    a, aux = np.zeros(3), np.zeros(8)
+    rc = lib().orc_accel(C.byref(om.s) if om else None, C.byref(pp), C.c_double(t), _dp(y), _dp(a), _dp(aux))
+    if rc != 0:
+        raise ValueError(f"orc_accel failed: {rc}")
+    return a, aux
+
+
+def propagate(mesh, pp, t0, t1, y0, h_cap=1_000_000, h_replay=None):
+    """Propagate y0 over [t0, t1].  Returns (y1, stats[acc, rej, evals], h_log)."""
+    om = OMesh(mesh) if mesh is not None else None
+    y0 = np.ascontiguousarray(np.asarray(y0, np.float64))
+    y1 = np.zeros(6)
+    stats = np.zeros(3, np.int64)
+    hlog = np.zeros(h_cap)
+    hr = None if h_replay is None else np.ascontiguousarray(np.asarray(h_replay, np.float64))
+    rc = lib().orc_propagate(C.byref(om.s) if om else None, C.byref(pp), C.c_double(t0), C.c_double(t1), _dp(y0),
+                             _dp(y1), stats.ctypes.data_as(C.POINTER(C.c_int64)), _dp(hlog), C.c_int64(h_cap),
+                             _dp(hr) if hr is not None else None, C.c_int64(0 if hr is None else len(hr)))
+    if rc != 0:
+        raise ValueError(f"orc_propagate failed: {rc}")
+    return y1, stats, hlog[: min(int(stats[0]), h_cap)]
