@@ -1,0 +1,188 @@
+/*
+ * srp.h -- C ABI of the GB300-native ray-traced solar radiation pressure
+ * library (libsrp.so).
+ *
+ * The library evaluates the solar radiation pressure (SRP) force and torque on
+ * a triangle-mesh spacecraft with articulated solar panels by casting one ray
+ * per pixel of a projection window along the Sun direction, following first
+ * hits (self-shadowing) and specular secondary rays, and propagates orbits
+ * whose acceleration includes that force.
+ *
+ * Paper sections that define the operations (arxiv 2608.07307):
+ *   Sec. 3, Eqs. 1-3   equations of motion y' = (v, a_g + a_SRP) integrated by an
+ *                      explicit embedded Runge-Kutta 7(8);
+ *   Sec. 4.3           per-pixel independent rays over a discretised image plane,
+ *                      iterated secondary rays, on-GPU reduction of all pixel
+ *                      contributions so only the final force is read back;
+ *   Sec. 4.4.1-4.4.2   kinematic tree of rigid parts; each movable joint rotates
+ *                      its subtree so the panel normal is as close as possible to
+ *                      the Sun, clamped to the joint's admissible interval;
+ *   Sec. 6.1           N x N projection window, levels of secondary reflections.
+ *
+ * Conventions shared by every entry point
+ *   - Units: SI (m, s, N, N m, kg) and radians.  Body frame for srp_eval_batch.
+ *   - Photons travel along d = -s, s the unit body-frame vector towards the Sun.
+ *   - Ray r of an evaluation is pixel (i, j) = (r / N, r % N) of the window;
+ *     i runs along the window's u axis, j along its v axis.
+ *   - Quaternions are scalar first and rotate body into inertial axes.
+ *   - Pointers to per-call data may be host or device memory (the library asks
+ *     the driver which); outputs are owned by the caller and written before the
+ *     call returns.  Mesh descriptions must be host memory; the library copies
+ *     them at load.
+ *   - Calls are ordered on the context's CUDA stream and synchronous on return.
+ *   - No C++ exception crosses the ABI.  Every call returns an srp_status; on
+ *     failure srp_last_error() describes it.  A context is used by one host
+ *     thread at a time.
+ */
+#ifndef SRP_H
+#define SRP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srp_ctx srp_ctx;
+typedef int32_t srp_status;
+
+#define SRP_OK 0
+#define SRP_ERR_ARG (-1)     /* invalid argument (null pointer, bad size, bad id)        */
+#define SRP_ERR_OOM (-2)     /* device or host allocation failed                         */
+#define SRP_ERR_CUDA (-3)    /* a CUDA runtime call failed                               */
+#define SRP_ERR_MESH (-4)    /* mesh rejected (indices, tree order, materials, degenerate) */
+#define SRP_ERR_STACK (-5)   /* a traversal stack bound was reached (device flag)       */
+#define SRP_ERR_TIMEOUT (-6) /* a bounded device-side wait gave up                       */
+#define SRP_ERR_STEP (-7)    /* integrator: step size underflow or step budget exhausted  */
+#define SRP_ERR_STATE (-8)   /* call out of order (e.g. no mesh loaded, context unusable) */
+
+#define SRP_F32 0
+#define SRP_F64 1
+
+/* Limits of this build. */
+#define SRP_MAX_PARTS 16
+#define SRP_MAX_MATS 256
+#define SRP_MAX_BOUNCES 4
+#define SRP_MAX_N 8192
+
+/*
+ * Mesh description (Sec. 4.4.1).  Part 0 is the root (body frame); part p > 0
+ * hangs from parent[p] < p.  A part with a non-zero axis is a movable joint:
+ * its transform is the parent's composed with a rotation by its angle about
+ * axis through pivot (rest body frame), so a joint moves its whole subtree.
+ * Triangles are counter-clockwise seen from their front side; every triangle
+ * has one part and a material per side.  A vertex may be used by one part only.
+ */
+typedef struct {
+    int32_t n_verts;
+    int32_t vertex_dtype;     /* SRP_F32 or SRP_F64                                    */
+    const void *xyz;          /* [n_verts][3] rest pose, metres                         */
+    int32_t n_tris;
+    const int32_t *tri;       /* [n_tris][3] vertex indices                             */
+    const int32_t *tri_part;  /* [n_tris]                                               */
+    const int32_t *tri_mat;   /* [n_tris][2] material of the front, back side          */
+    int32_t n_mats;
+    const double *mat;        /* [n_mats][2] rho_s, rho_d; rho_s, rho_d >= 0, sum <= 1  */
+    int32_t n_parts;
+    const int32_t *parent;    /* [n_parts]; parent[0] = -1                              */
+    const double *pivot;      /* [n_parts][3]                                           */
+    const double *axis;       /* [n_parts][3] unit, or all zero for a rigid link        */
+    const double *limits;     /* [n_parts][2] admissible angle interval lo <= hi (rad)  */
+    const double *normal0;    /* [n_parts][3] rest front normal of a movable panel part */
+    double c_ref[3];          /* torque reference point                                 */
+    double mass;              /* kg (used by srp_propagate)                             */
+} srp_mesh_desc;
+
+/* How joint angles are chosen for each evaluation (Sec. 4.4.2). */
+#define SRP_PANELS_TRACK 0        /* angle = argmax of n(theta) . s, clamped             */
+#define SRP_PANELS_SET 1          /* angle = value from srp_set_panel_angles, clamped    */
+#define SRP_PANELS_TRACK_OFFSET 2 /* angle = tracking angle + set value, clamped          */
+
+typedef struct {
+    int32_t N;           /* rays per side of the projection window, 1..SRP_MAX_N       */
+    int32_t bounces;     /* specular secondary levels, 0..SRP_MAX_BOUNCES                */
+    double P0;           /* radiation pressure at 1 AU, N/m^2 (e.g. 4.56e-6)             */
+    double eps_rel;      /* secondary-ray self-hit threshold / window diagonal (1e-9)    */
+    int32_t panel_mode;  /* SRP_PANELS_*                                                 */
+    int32_t flags;       /* 0, or SRP_EVAL_COUNT to gather srp_eval_stats counters       */
+} srp_eval_params;
+
+#define SRP_EVAL_COUNT 1
+
+/* Counters of the last srp_eval_batch call (summed over its evaluations). */
+typedef struct {
+    int64_t evals;
+    int64_t rays;             /* primary rays cast                                       */
+    int64_t segments;         /* ray segments traced (primary + secondary)               */
+    int64_t hits[SRP_MAX_BOUNCES + 1]; /* hits per segment level                         */
+    int64_t refined;          /* rays re-traced in FP64 because an FP32 decision was within its error bound */
+    int64_t nodes_visited;    /* BVH nodes fetched (SRP_EVAL_COUNT only)                  */
+    int64_t tris_tested;      /* ray/triangle tests (SRP_EVAL_COUNT only)                 */
+    int64_t box_tests;        /* ray/box slab tests (SRP_EVAL_COUNT only)                 */
+} srp_eval_stats;
+
+/*
+ * Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t to
+ * order work on, or NULL for a stream the context creates and owns.
+ * Errors: SRP_ERR_ARG (out NULL), SRP_ERR_CUDA (no such device), SRP_ERR_OOM.
+ */
+srp_status srp_create(srp_ctx **out, int32_t device, void *cuda_stream);
+
+/* Destroy a context and every mesh and buffer it holds.  NULL is a no-op. */
+void srp_destroy(srp_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" when none); valid until the next call. */
+const char *srp_last_error(const srp_ctx *ctx);
+
+/*
+ * Load a mesh: validate, copy to the device, build one LBVH per rigid part
+ * (Morton codes of triangle centroids, radix sort, binary radix tree) and fit
+ * its boxes to the rest pose.  mesh_id receives a handle >= 0.
+ * Errors: SRP_ERR_ARG (NULL pointers, counts <= 0, limits exceeded),
+ * SRP_ERR_MESH (index out of range, parent order, shared vertex, degenerate
+ * triangle, material coefficients outside [0, 1] or summing above 1).
+ */
+srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *desc, int32_t *mesh_id);
+
+/* Release a mesh and its device memory. */
+srp_status srp_mesh_free(srp_ctx *ctx, int32_t mesh_id);
+
+/*
+ * Joint angles (rad) used by SRP_PANELS_SET (as the angle) and
+ * SRP_PANELS_TRACK_OFFSET (as an offset added to the tracking angle); one per
+ * part, n == n_parts; entries of rigid parts are ignored.  Initially zero.
+ * Errors: SRP_ERR_ARG (bad id, n mismatch, NULL).
+ */
+srp_status srp_set_panel_angles(srp_ctx *ctx, int32_t mesh_id, int32_t n, const double *rad);
+
+/*
+ * SRP force and torque for n Sun directions (Sec. 4.3, 4.4.2, 6.1).
+ * For each direction k: joint angles per params->panel_mode; posed mesh; window
+ * = tight bounds of the posed vertices on the basis (u, v) of the plane normal
+ * to d; N x N rays from the pixel centres, 1 m in front of the nearest vertex;
+ * first hit of each ray (two-sided, ties to the lowest triangle id); per hit
+ * the absorbed + specular + Lambertian-diffuse momentum, with the specular beam
+ * traced for `bounces` more levels (weight times rho_s; a secondary ray never
+ * hits the triangle it leaves); sum of all pixels times P0 / dist^2 times the
+ * pixel area.
+ *   sun_dir_body [n][3]   unit vectors towards the Sun, body frame
+ *   sun_dist_au  [n]      Sun distance (AU); NULL means 1
+ *   force        [n][3]   out, N
+ *   torque       [n][3]   out, N m about c_ref
+ *   hit_tri      [n][N*N][bounces+1] out, original triangle id per ray segment,
+ *                         -1 when that segment missed or was not traced; NULL
+ *                         to skip (debug output, large)
+ * Errors: SRP_ERR_ARG, SRP_ERR_STATE (bad mesh id), SRP_ERR_STACK, SRP_ERR_CUDA.
+ */
+srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *params, int32_t n,
+                          const double *sun_dir_body, const double *sun_dist_au, double *force, double *torque,
+                          int32_t *hit_tri);
+
+/* Counters of the last srp_eval_batch on ctx. */
+srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRP_H */

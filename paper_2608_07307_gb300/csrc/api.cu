@@ -1,0 +1,618 @@
+// api.cu -- the C ABI of libsrp (include/srp.h): validation, device memory,
+// mesh build and the per-batch launch sequence.  No exception crosses the ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "srp_internal.cuh"
+
+using namespace srp;
+
+namespace {
+
+struct Mesh {
+    MeshDev h{};                 // host copy holding device pointers
+    MeshDev *d = nullptr;        // device copy
+    std::vector<void *> allocs;  // device allocations owned by the mesh
+    int4 *node_refs_dyn = nullptr;
+    double *angles_d = nullptr;  // commanded angles / offsets [n_parts]
+    double mass = 0.0;
+    int slots = 0;
+    SlotBufs sb{};
+    std::vector<void *> slot_allocs;
+};
+
+}  // namespace
+
+struct srp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<Mesh *> meshes;
+    // workspace, grown on demand
+    SlotPose *pose = nullptr;
+    size_t pose_cap = 0;
+    double *partials = nullptr;
+    size_t partials_cap = 0;
+    double *partials_ref = nullptr;
+    size_t partials_ref_cap = 0;
+    uint32_t *amb = nullptr;
+    size_t amb_cap = 0;
+    double *io = nullptr;
+    size_t io_cap = 0;
+    int32_t *hits = nullptr;
+    size_t hits_cap = 0;
+    int *err_flags = nullptr;
+    unsigned long long *stats = nullptr;
+    srp_eval_stats last{};
+};
+
+namespace {
+
+srp_status fail(srp_ctx *ctx, srp_status code, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+#define CK(ctx, x)                                                                                   \
+    do {                                                                                             \
+        cudaError_t e_ = (x);                                                                        \
+        if (e_ != cudaSuccess) {                                                                     \
+            srp_status c_ = (e_ == cudaErrorMemoryAllocation) ? SRP_ERR_OOM : SRP_ERR_CUDA;           \
+            return fail(ctx, c_, "%s failed: %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                            \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dmalloc(std::vector<void *> &owner, T **p, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    owner.push_back(q);
+    *p = static_cast<T *>(q);
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t grow(T **p, size_t *cap, size_t need, bool zero)
+{
+    if (need <= *cap) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t n = std::max<size_t>(need, 1);
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (zero) {
+        e = cudaMemset(*p, 0, n * sizeof(T));
+        if (e != cudaSuccess) return e;
+    }
+    *cap = n;
+    return cudaSuccess;
+}
+
+void free_mesh(Mesh *m)
+{
+    if (!m) return;
+    for (void *p : m->slot_allocs) cudaFree(p);
+    for (void *p : m->allocs) cudaFree(p);
+    delete m;
+}
+
+// Allocate per-slot dynamic storage for S concurrent evaluations.
+srp_status ensure_slots(srp_ctx *ctx, Mesh *m, int S)
+{
+    if (m->slots >= S) return SRP_OK;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (void *p : m->slot_allocs) cudaFree(p);
+    m->slot_allocs.clear();
+    m->slots = 0;
+    const MeshDev &h = m->h;
+    SlotBufs &b = m->sb;
+    CK(ctx, dmalloc(m->slot_allocs, &b.vert64, (size_t)S * h.n_dyn_verts * 3));
+    CK(ctx, dmalloc(m->slot_allocs, &b.tri, (size_t)S * h.n_dyn_tris * 3));
+    CK(ctx, dmalloc(m->slot_allocs, &b.node, (size_t)S * h.n_dyn_nodes * 4));
+    CK(ctx, dmalloc(m->slot_allocs, &b.counter, (size_t)S * h.n_dyn_nodes));
+    CK(ctx, dmalloc(m->slot_allocs, &b.root_box, (size_t)S * kMaxParts * 6));
+    CK(ctx, cudaMemset(b.counter, 0, sizeof(unsigned) * std::max<size_t>((size_t)S * h.n_dyn_nodes, 1)));
+    CK(ctx, cudaMemset(b.root_box, 0, sizeof(float) * (size_t)S * kMaxParts * 6));
+    for (int s = 0; s < S && h.n_dyn_nodes > 0; s++) {
+        // child refs of the dynamic nodes, the fourth float4 of every node
+        CK(ctx, cudaMemcpy2D(b.node + (size_t)s * h.n_dyn_nodes * 4 + 3, 4 * sizeof(float4), m->node_refs_dyn,
+                             sizeof(int4), sizeof(int4), h.n_dyn_nodes, cudaMemcpyDeviceToDevice));
+    }
+    m->slots = S;
+    return SRP_OK;
+}
+
+Mesh *get_mesh(srp_ctx *ctx, int32_t id)
+{
+    if (!ctx || id < 0 || id >= (int32_t)ctx->meshes.size()) return nullptr;
+    return ctx->meshes[id];
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+srp_status srp_create(srp_ctx **out, int32_t device, void *cuda_stream)
+{
+    if (!out) return SRP_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return SRP_ERR_CUDA;
+    }
+    srp_ctx *ctx = new (std::nothrow) srp_ctx();
+    if (!ctx) return SRP_ERR_OOM;
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return SRP_ERR_CUDA; }
+    if (cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return SRP_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc(&ctx->err_flags, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->stats, 16 * sizeof(unsigned long long)) != cudaSuccess) {
+        srp_destroy(ctx);
+        return SRP_ERR_OOM;
+    }
+    *out = ctx;
+    return SRP_OK;
+}
+
+void srp_destroy(srp_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (Mesh *m : ctx->meshes) free_mesh(m);
+    cudaFree(ctx->pose);
+    cudaFree(ctx->partials);
+    cudaFree(ctx->partials_ref);
+    cudaFree(ctx->amb);
+    cudaFree(ctx->io);
+    cudaFree(ctx->hits);
+    cudaFree(ctx->err_flags);
+    cudaFree(ctx->stats);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *srp_last_error(const srp_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    if (!D || !mesh_id) return fail(ctx, SRP_ERR_ARG, "null desc or mesh_id");
+    if (D->n_verts <= 0 || D->n_tris <= 0 || D->n_parts <= 0 || D->n_mats <= 0)
+        return fail(ctx, SRP_ERR_ARG, "counts must be positive");
+    if (D->n_parts > kMaxParts) return fail(ctx, SRP_ERR_ARG, "n_parts %d > %d", D->n_parts, kMaxParts);
+    if (D->n_mats > kMaxMats) return fail(ctx, SRP_ERR_ARG, "n_mats %d > %d", D->n_mats, kMaxMats);
+    if (!D->xyz || !D->tri || !D->tri_part || !D->tri_mat || !D->mat || !D->parent || !D->pivot || !D->axis ||
+        !D->limits || !D->normal0)
+        return fail(ctx, SRP_ERR_ARG, "null array in mesh description");
+    if (D->vertex_dtype != SRP_F32 && D->vertex_dtype != SRP_F64) return fail(ctx, SRP_ERR_ARG, "bad vertex dtype");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SRP_ERR_CUDA, "cudaSetDevice");
+    const int NV = D->n_verts, NT = D->n_tris, NP = D->n_parts, NM = D->n_mats;
+    // ---- validation
+    std::vector<double> xyz((size_t)NV * 3);
+    for (size_t k = 0; k < xyz.size(); k++) {
+        xyz[k] = D->vertex_dtype == SRP_F64 ? static_cast<const double *>(D->xyz)[k]
+                                            : (double)static_cast<const float *>(D->xyz)[k];
+        if (!std::isfinite(xyz[k])) return fail(ctx, SRP_ERR_MESH, "non-finite vertex coordinate %zu", k / 3);
+    }
+    if (D->parent[0] != -1) return fail(ctx, SRP_ERR_MESH, "parent[0] must be -1");
+    std::vector<int> movable(NP, 0), dynamic(NP, 0);
+    for (int p = 0; p < NP; p++) {
+        if (p > 0 && (D->parent[p] < 0 || D->parent[p] >= p))
+            return fail(ctx, SRP_ERR_MESH, "parent[%d] = %d must lie in [0, %d)", p, D->parent[p], p);
+        const double *a = D->axis + 3 * p;
+        double an = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        if (p > 0 && an != 0.0) {
+            if (std::fabs(an - 1.0) > 1e-9) return fail(ctx, SRP_ERR_MESH, "axis of part %d is not unit", p);
+            movable[p] = 1;
+        }
+        if (!(D->limits[2 * p] <= D->limits[2 * p + 1])) return fail(ctx, SRP_ERR_MESH, "limits of part %d", p);
+        dynamic[p] = movable[p] || (p > 0 && dynamic[D->parent[p]]);
+    }
+    for (int i = 0; i < NM; i++) {
+        double rs = D->mat[2 * i], rd = D->mat[2 * i + 1];
+        if (!(rs >= 0.0 && rd >= 0.0 && rs + rd <= 1.0 + 1e-12))
+            return fail(ctx, SRP_ERR_MESH, "material %d coefficients (%g, %g) outside [0,1] or sum > 1", i, rs, rd);
+    }
+    std::vector<int> vpart(NV, -1);
+    for (int t = 0; t < NT; t++) {
+        int p = D->tri_part[t];
+        if (p < 0 || p >= NP) return fail(ctx, SRP_ERR_MESH, "tri_part[%d] = %d out of range", t, p);
+        for (int s = 0; s < 2; s++)
+            if (D->tri_mat[2 * t + s] < 0 || D->tri_mat[2 * t + s] >= NM)
+                return fail(ctx, SRP_ERR_MESH, "tri_mat[%d] out of range", t);
+        for (int c = 0; c < 3; c++) {
+            int v = D->tri[3 * t + c];
+            if (v < 0 || v >= NV) return fail(ctx, SRP_ERR_MESH, "tri[%d] vertex %d out of range", t, v);
+            if (vpart[v] >= 0 && vpart[v] != p) return fail(ctx, SRP_ERR_MESH, "vertex %d shared by parts %d and %d", v, vpart[v], p);
+            vpart[v] = p;
+        }
+        const double *a = &xyz[3 * (size_t)D->tri[3 * t]], *b = &xyz[3 * (size_t)D->tri[3 * t + 1]],
+                     *c = &xyz[3 * (size_t)D->tri[3 * t + 2]];
+        double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        if (!(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] > 0.0)) return fail(ctx, SRP_ERR_MESH, "triangle %d is degenerate", t);
+    }
+    // ---- layout: static parts first, then dynamic; vertices and triangles grouped by part
+    std::vector<int> order;
+    for (int p = 0; p < NP; p++) if (!dynamic[p]) order.push_back(p);
+    for (int p = 0; p < NP; p++) if (dynamic[p]) order.push_back(p);
+    std::vector<int> rank(NP);
+    for (int r = 0; r < NP; r++) rank[order[r]] = r;
+    std::vector<std::vector<int>> pverts(NP), ptris(NP);
+    for (int v = 0; v < NV; v++) if (vpart[v] >= 0) pverts[vpart[v]].push_back(v);
+    for (int t = 0; t < NT; t++) ptris[D->tri_part[t]].push_back(t);
+    Mesh *m = new (std::nothrow) Mesh();
+    if (!m) return fail(ctx, SRP_ERR_OOM, "host allocation");
+    MeshDev &h = m->h;
+    h.n_parts = NP; h.n_tris = NT; h.n_mats = NM;
+    std::vector<int> newv(NV, -1);
+    std::vector<double> rest;
+    std::vector<int> vert_part;
+    int nv = 0, tb = 0, nb = 0;
+    double rmax = 0.0, piv = 0.0;
+    for (int r = 0; r < NP; r++) {
+        int p = order[r];
+        PartInfo &pi = h.part[p];
+        pi.parent = D->parent[p];
+        pi.movable = movable[p];
+        pi.dynamic = dynamic[p];
+        for (int k = 0; k < 3; k++) {
+            pi.pivot[k] = D->pivot[3 * p + k];
+            pi.axis[k] = D->axis[3 * p + k];
+            pi.n0[k] = D->normal0[3 * p + k];
+        }
+        pi.lim[0] = D->limits[2 * p];
+        pi.lim[1] = D->limits[2 * p + 1];
+        pi.vert_begin = nv;
+        pi.vert_count = (int)pverts[p].size();
+        for (int v : pverts[p]) {
+            newv[v] = nv++;
+            for (int k = 0; k < 3; k++) rest.push_back(xyz[3 * (size_t)v + k]);
+            vert_part.push_back(p);
+            rmax = std::max(rmax, std::sqrt(xyz[3 * (size_t)v] * xyz[3 * (size_t)v] +
+                                            xyz[3 * (size_t)v + 1] * xyz[3 * (size_t)v + 1] +
+                                            xyz[3 * (size_t)v + 2] * xyz[3 * (size_t)v + 2]));
+        }
+        pi.tri_begin = tb;
+        pi.tri_count = (int)ptris[p].size();
+        tb += pi.tri_count;
+        pi.node_begin = nb;
+        nb += std::max(pi.tri_count - 1, 0);
+        if (movable[p]) piv += std::sqrt(pi.pivot[0] * pi.pivot[0] + pi.pivot[1] * pi.pivot[1] + pi.pivot[2] * pi.pivot[2]);
+        if (!dynamic[p]) { h.n_static_tris = tb; h.n_static_nodes = nb; h.n_static_verts = nv; }
+    }
+    h.n_verts = nv;
+    h.n_dyn_tris = NT - h.n_static_tris;
+    h.n_dyn_nodes = nb - h.n_static_nodes;
+    h.n_dyn_verts = nv - h.n_static_verts;
+    for (int p = 0; p < NP; p++) {
+        PartInfo &pi = h.part[p];
+        pi.dyn_tri_off = pi.dynamic ? pi.tri_begin - h.n_static_tris : 0;
+        pi.dyn_node_off = pi.dynamic ? pi.node_begin - h.n_static_nodes : 0;
+        pi.dyn_vert_off = pi.dynamic ? pi.vert_begin - h.n_static_verts : 0;
+        h.part_order[rank[p]] = p;
+    }
+    h.R = rmax + 2.0 * piv;
+    h.pad = std::ldexp(h.R, -16) + 1e-9;
+    for (int k = 0; k < 3; k++) h.c_ref[k] = D->c_ref[k];
+    m->mass = D->mass;
+    // part boxes for Morton quantisation
+    std::vector<float> plo((size_t)NP * 3, 0.f), pext((size_t)NP * 3, 0.f);
+    for (int p = 0; p < NP; p++) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int v : pverts[p])
+            for (int k = 0; k < 3; k++) { lo[k] = std::min(lo[k], xyz[3 * (size_t)v + k]); hi[k] = std::max(hi[k], xyz[3 * (size_t)v + k]); }
+        for (int k = 0; k < 3; k++) {
+            plo[3 * p + k] = pverts[p].empty() ? 0.f : (float)lo[k];
+            pext[3 * p + k] = pverts[p].empty() ? 0.f : (float)(hi[k] - lo[k]);
+        }
+    }
+    std::vector<int> tvidx((size_t)NT * 3);
+    for (int t = 0; t < NT; t++)
+        for (int c = 0; c < 3; c++) tvidx[3 * (size_t)t + c] = newv[D->tri[3 * t + c]];
+    std::vector<int> rank_v(rank.begin(), rank.end());
+    std::vector<int> tpart(D->tri_part, D->tri_part + NT);
+
+    cudaStream_t st = ctx->stream;
+    std::vector<void *> tmp;  // build-only device buffers
+    auto free_tmp = [&]() { cudaStreamSynchronize(st); for (void *p : tmp) cudaFree(p); tmp.clear(); };
+    auto bail = [&](srp_status c, const char *what, cudaError_t e) {
+        free_tmp();
+        free_mesh(m);
+        return fail(ctx, c, "%s: %s", what, cudaGetErrorString(e));
+    };
+#define MK(x)                                                                                               \
+    do {                                                                                                    \
+        cudaError_t e_ = (x);                                                                               \
+        if (e_ != cudaSuccess) return bail(e_ == cudaErrorMemoryAllocation ? SRP_ERR_OOM : SRP_ERR_CUDA, #x, e_); \
+    } while (0)
+    int *d_tvidx0, *d_tpart, *d_rank, *vals, *vals2, *scratch, *d_ptb, *d_ptc, *d_pnb, *d_nodepart, *d_nodebase, *d_depth;
+    unsigned long long *keys, *keys2;
+    float *d_plo, *d_pext;
+    int4 *node_refs;
+    unsigned *cnt_static;
+    size_t sc_ints = radix_sort_scratch_ints(NT);
+    MK(dmalloc(m->allocs, &h.rest64, (size_t)nv * 3));
+    MK(dmalloc(m->allocs, &h.vert_part, (size_t)nv));
+    MK(dmalloc(m->allocs, &h.tri_vidx, (size_t)NT * 3));
+    MK(dmalloc(m->allocs, &h.tri_orig, (size_t)NT));
+    MK(dmalloc(m->allocs, &h.tri_mat, (size_t)NT));
+    MK(dmalloc(m->allocs, &h.leaf_parent, (size_t)NT));
+    MK(dmalloc(m->allocs, &h.tri_static, (size_t)std::max(h.n_static_tris, 1) * 3));
+    MK(dmalloc(m->allocs, &h.node_static, (size_t)std::max(h.n_static_nodes, 1) * 4));
+    MK(dmalloc(m->allocs, &h.mat32, (size_t)NM));
+    MK(dmalloc(m->allocs, &h.mat64, (size_t)NM * 2));
+    MK(dmalloc(m->allocs, &m->angles_d, (size_t)NP));
+    MK(dmalloc(m->allocs, &node_refs, (size_t)std::max(nb, 1)));
+    MK(dmalloc(tmp, &d_tvidx0, (size_t)NT * 3));
+    MK(dmalloc(tmp, &d_tpart, (size_t)NT));
+    MK(dmalloc(tmp, &d_rank, (size_t)NP));
+    MK(dmalloc(tmp, &keys, (size_t)NT));
+    MK(dmalloc(tmp, &keys2, (size_t)NT));
+    MK(dmalloc(tmp, &vals, (size_t)NT));
+    MK(dmalloc(tmp, &vals2, (size_t)NT));
+    MK(dmalloc(tmp, &scratch, sc_ints));
+    MK(dmalloc(tmp, &d_plo, (size_t)NP * 3));
+    MK(dmalloc(tmp, &d_pext, (size_t)NP * 3));
+    MK(dmalloc(tmp, &d_ptb, (size_t)NP));
+    MK(dmalloc(tmp, &d_ptc, (size_t)NP));
+    MK(dmalloc(tmp, &d_pnb, (size_t)NP));
+    MK(dmalloc(tmp, &d_nodepart, (size_t)std::max(nb, 1)));
+    MK(dmalloc(tmp, &d_nodebase, (size_t)std::max(nb, 1)));
+    MK(dmalloc(tmp, &d_depth, 1));
+    MK(dmalloc(tmp, &cnt_static, (size_t)std::max(h.n_static_nodes, 1)));
+    MK(cudaMemcpyAsync(h.rest64, rest.data(), sizeof(double) * rest.size(), cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(h.vert_part, vert_part.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_tvidx0, tvidx.data(), sizeof(int) * tvidx.size(), cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_tpart, tpart.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_rank, rank_v.data(), sizeof(int) * NP, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_plo, plo.data(), sizeof(float) * plo.size(), cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_pext, pext.data(), sizeof(float) * pext.size(), cudaMemcpyHostToDevice, st));
+    // 1-2: Morton codes and sort (bits 0..39 hold the code and the part rank)
+    MK(launch_morton(h.rest64, d_tvidx0, d_tpart, d_rank, d_plo, d_pext, NT, keys, vals, st));
+    MK(radix_sort_pairs(keys, vals, keys2, vals2, NT, 0, 40, scratch, sc_ints, st));
+    std::vector<int> sorted(NT);
+    MK(cudaMemcpyAsync(sorted.data(), vals, sizeof(int) * NT, cudaMemcpyDeviceToHost, st));
+    MK(cudaStreamSynchronize(st));
+    // sorted triangle arrays (a check that the sort kept parts contiguous comes for free)
+    std::vector<int> svidx((size_t)NT * 3), sorig(NT);
+    std::vector<unsigned> smat(NT);
+    for (int k = 0; k < NT; k++) {
+        int t = sorted[k];
+        if (t < 0 || t >= NT) return bail(SRP_ERR_CUDA, "sort produced an invalid index", cudaErrorUnknown);
+        sorig[k] = t;
+        for (int c = 0; c < 3; c++) svidx[3 * (size_t)k + c] = tvidx[3 * (size_t)t + c];
+        smat[k] = (unsigned)D->tri_mat[2 * t] | ((unsigned)D->tri_mat[2 * t + 1] << 16);
+    }
+    for (int r = 0; r < NP; r++) {
+        const PartInfo &pi = h.part[order[r]];
+        for (int k = pi.tri_begin; k < pi.tri_begin + pi.tri_count; k++)
+            if (D->tri_part[sorig[k]] != order[r]) return bail(SRP_ERR_CUDA, "sort mixed parts", cudaErrorUnknown);
+    }
+    MK(cudaMemcpyAsync(h.tri_vidx, svidx.data(), sizeof(int) * svidx.size(), cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(h.tri_orig, sorig.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(h.tri_mat, smat.data(), sizeof(unsigned) * NT, cudaMemcpyHostToDevice, st));
+    // 3: binary radix tree per part
+    std::vector<int> ptb(NP), ptc(NP), pnb(NP), nodepart(std::max(nb, 1)), nodebase(std::max(nb, 1));
+    for (int p = 0; p < NP; p++) {
+        ptb[p] = h.part[p].tri_begin;
+        ptc[p] = h.part[p].tri_count;
+        pnb[p] = h.part[p].node_begin;
+        for (int g = pnb[p]; g < pnb[p] + std::max(ptc[p] - 1, 0); g++) { nodepart[g] = p; nodebase[g] = pnb[p]; }
+    }
+    std::vector<int4> refs0(std::max(nb, 1), make_int4(0, 0, -1, 0));
+    std::vector<int> lp0(NT, -1);
+    MK(cudaMemcpyAsync(d_ptb, ptb.data(), sizeof(int) * NP, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_ptc, ptc.data(), sizeof(int) * NP, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_pnb, pnb.data(), sizeof(int) * NP, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_nodepart, nodepart.data(), sizeof(int) * nodepart.size(), cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_nodebase, nodebase.data(), sizeof(int) * nodebase.size(), cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(node_refs, refs0.data(), sizeof(int4) * refs0.size(), cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(h.leaf_parent, lp0.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
+    MK(launch_karras(keys, d_ptb, d_ptc, d_pnb, NP, nb, d_nodepart, node_refs, h.leaf_parent, st));
+    int zero = 0, depth = 0;
+    MK(cudaMemcpyAsync(d_depth, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    MK(launch_depth(node_refs, d_nodebase, nb, d_depth, st));
+    MK(cudaMemcpyAsync(&depth, d_depth, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MK(cudaStreamSynchronize(st));
+    h.max_depth = depth;
+    if (depth + 2 > kStack) {
+        free_tmp();
+        free_mesh(m);
+        return fail(ctx, SRP_ERR_MESH, "BVH depth %d exceeds the traversal stack (%d)", depth, kStack);
+    }
+    // static nodes: child refs into the fourth float4; dynamic refs kept for the slots
+    if (h.n_static_nodes > 0)
+        MK(cudaMemcpy2DAsync(h.node_static + 3, 4 * sizeof(float4), node_refs, sizeof(int4), sizeof(int4),
+                             h.n_static_nodes, cudaMemcpyDeviceToDevice, st));
+    m->node_refs_dyn = node_refs + h.n_static_nodes;
+    // materials and angles
+    std::vector<float2> m32(NM);
+    for (int i = 0; i < NM; i++) m32[i] = make_float2((float)D->mat[2 * i], (float)D->mat[2 * i + 1]);
+    MK(cudaMemcpyAsync(h.mat32, m32.data(), sizeof(float2) * NM, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(h.mat64, D->mat, sizeof(double) * 2 * NM, cudaMemcpyHostToDevice, st));
+    MK(cudaMemsetAsync(m->angles_d, 0, sizeof(double) * NP, st));
+    MK(cudaMemsetAsync(cnt_static, 0, sizeof(unsigned) * std::max(h.n_static_nodes, 1), st));
+    // device copy of the mesh, then the static refit (writes root boxes into it)
+    MK(dmalloc(m->allocs, &m->d, 1));
+    MK(cudaMemcpyAsync(m->d, &h, sizeof(MeshDev), cudaMemcpyHostToDevice, st));
+    MK(launch_refit(m->d, h, SlotBufs{}, 1, true, h.node_static, h.tri_static, cnt_static,
+                    &m->d->root_box_static[0][0], st));
+    MK(cudaMemcpyAsync(&h.root_box_static[0][0], &m->d->root_box_static[0][0], sizeof(h.root_box_static),
+                       cudaMemcpyDeviceToHost, st));
+    MK(cudaStreamSynchronize(st));
+    free_tmp();
+#undef MK
+    ctx->meshes.push_back(m);
+    *mesh_id = (int32_t)ctx->meshes.size() - 1;
+    return SRP_OK;
+}
+
+srp_status srp_mesh_free(srp_ctx *ctx, int32_t mesh_id)
+{
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_ARG, "bad mesh id %d", mesh_id);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_mesh(m);
+    ctx->meshes[mesh_id] = nullptr;
+    return SRP_OK;
+}
+
+srp_status srp_set_panel_angles(srp_ctx *ctx, int32_t mesh_id, int32_t n, const double *rad)
+{
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_ARG, "bad mesh id %d", mesh_id);
+    if (!rad || n != m->h.n_parts) return fail(ctx, SRP_ERR_ARG, "need %d angles", m->h.n_parts);
+    CK(ctx, cudaSetDevice(ctx->device));
+    CK(ctx, cudaMemcpyAsync(m->angles_d, rad, sizeof(double) * n,
+                            is_device_ptr(rad) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return SRP_OK;
+}
+
+srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, int32_t n,
+                          const double *sun_dir_body, const double *sun_dist_au, double *force, double *torque,
+                          int32_t *hit_tri)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
+    if (!prm) return fail(ctx, SRP_ERR_ARG, "null params");
+    if (prm->N < 1 || prm->N > SRP_MAX_N) return fail(ctx, SRP_ERR_ARG, "N = %d outside [1, %d]", prm->N, SRP_MAX_N);
+    if (prm->bounces < 0 || prm->bounces > kMaxBounces) return fail(ctx, SRP_ERR_ARG, "bounces = %d", prm->bounces);
+    if (!(prm->P0 >= 0.0) || !(prm->eps_rel >= 0.0)) return fail(ctx, SRP_ERR_ARG, "P0 and eps_rel must be >= 0");
+    if (prm->panel_mode < 0 || prm->panel_mode > 2) return fail(ctx, SRP_ERR_ARG, "bad panel_mode");
+    if (n < 0) return fail(ctx, SRP_ERR_ARG, "n < 0");
+    memset(&ctx->last, 0, sizeof ctx->last);
+    if (n == 0) return SRP_OK;
+    if (!sun_dir_body || !force || !torque) return fail(ctx, SRP_ERR_ARG, "null input or output");
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int N = prm->N, nseg = prm->bounces + 1;
+    const size_t R = (size_t)N * N;
+    // concurrent evaluations: enough rays in flight to fill the GPU several times
+    int S = (int)std::min<size_t>(std::max<size_t>((size_t)(1u << 21) / R, 1), 64);
+    S = std::min(S, n);
+    srp_status rc = ensure_slots(ctx, m, S);
+    if (rc) return rc;
+    int tiles = (N + kTile - 1) / kTile;
+    int nbx = tiles * tiles;
+    int nbr = (int)((R + kTraceThreads - 1) / kTraceThreads);
+    size_t words = (R + 31) / 32;
+    CK(ctx, grow(&ctx->pose, &ctx->pose_cap, (size_t)S, false));
+    CK(ctx, grow(&ctx->partials, &ctx->partials_cap, (size_t)S * nbx * 16, false));
+    CK(ctx, grow(&ctx->partials_ref, &ctx->partials_ref_cap, (size_t)S * nbr * 16, false));
+    CK(ctx, grow(&ctx->amb, &ctx->amb_cap, (size_t)S * words, true));
+    bool in_dev = is_device_ptr(sun_dir_body);
+    bool dist_dev = sun_dist_au && is_device_ptr(sun_dist_au);
+    bool f_dev = is_device_ptr(force), t_dev = is_device_ptr(torque);
+    bool h_dev = hit_tri && is_device_ptr(hit_tri);
+    size_t io_need = (size_t)n * 3 * 3 + (size_t)n;
+    CK(ctx, grow(&ctx->io, &ctx->io_cap, io_need, false));
+    double *d_sun = in_dev ? const_cast<double *>(sun_dir_body) : ctx->io;
+    double *d_dist = sun_dist_au ? (dist_dev ? const_cast<double *>(sun_dist_au) : ctx->io + (size_t)n * 3) : nullptr;
+    double *d_f = f_dev ? force : ctx->io + (size_t)n * 4;
+    double *d_t = t_dev ? torque : ctx->io + (size_t)n * 7;
+    if (!in_dev) CK(ctx, cudaMemcpyAsync(d_sun, sun_dir_body, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (sun_dist_au && !dist_dev)
+        CK(ctx, cudaMemcpyAsync(d_dist, sun_dist_au, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    if (hit_tri && !h_dev) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, (size_t)S * R * nseg, false));
+    CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
+    CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
+    TraceArgs a{};
+    a.mesh_d = m->d;
+    a.pose = ctx->pose;
+    a.slot = m->sb;
+    a.N = N;
+    a.bounces = prm->bounces;
+    a.nseg = nseg;
+    a.eps_rel = prm->eps_rel;
+    a.n_blocks_x = nbx;
+    a.n_blocks_ref = nbr;
+    a.partials = ctx->partials;
+    a.partials_ref = ctx->partials_ref;
+    a.amb = ctx->amb;
+    a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
+    for (int e0 = 0; e0 < n; e0 += S) {
+        int Sc = std::min(S, n - e0);
+        CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, ctx->pose, st));
+        CK(ctx, launch_vertices(m->d, m->h, ctx->pose, m->sb, Sc, st));
+        if (m->h.n_dyn_tris > 0) CK(ctx, launch_refit(m->d, m->h, m->sb, Sc, false, nullptr, nullptr, nullptr, nullptr, st));
+        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : ctx->hits) : nullptr;
+        CK(ctx, launch_trace(a, Sc, st));
+        CK(ctx, launch_refine(a, Sc, st));
+        CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, st));
+        if (hit_tri && !h_dev)
+            CK(ctx, cudaMemcpyAsync(hit_tri + (size_t)e0 * R * nseg, ctx->hits, sizeof(int32_t) * Sc * R * nseg,
+                                    cudaMemcpyDeviceToHost, st));
+    }
+    if (!f_dev) CK(ctx, cudaMemcpyAsync(force, d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (!t_dev) CK(ctx, cudaMemcpyAsync(torque, d_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    int flags = 0;
+    unsigned long long stats[16];
+    CK(ctx, cudaMemcpyAsync(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(stats, ctx->stats, sizeof stats, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    srp_eval_stats &L = ctx->last;
+    L.evals = (int64_t)stats[0];
+    L.rays = (int64_t)stats[1];
+    L.refined = (int64_t)stats[2];
+    L.segments = (int64_t)stats[3];
+    for (int k = 0; k <= kMaxBounces; k++) L.hits[k] = (int64_t)stats[4 + k];
+    L.nodes_visited = (int64_t)stats[9];
+    L.tris_tested = (int64_t)stats[10];
+    L.box_tests = (int64_t)stats[11];
+    if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
+    return SRP_OK;
+}
+
+srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out)
+{
+    if (!ctx || !out) return SRP_ERR_ARG;
+    *out = ctx->last;
+    return SRP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+// pose.cu -- per-evaluation geometry update (Sec. 4.4.2) and window bounds.
+//
+//   k_pose      one thread per evaluation slot: joint angles (Sun tracking,
+//               commanded, or tracking + offset; clamped), part transforms
+//               composed down the kinematic tree (Sec. 4.4.1), image-plane
+//               basis, window accumulators reset.
+//   k_vertices  one thread per vertex and slot: posed FP64 position of dynamic
+//               vertices; FP64 projections on (u, v, d) reduced to the window
+//               min / max (exact, order independent).
+//   k_refit     one thread per triangle of the refitted parts: FP32 triangle
+//               record from the posed FP64 vertices, leaf box, then bottom-up
+//               box refit: the second child to arrive at a node (counted with
+//               an atomic whose parity flips twice per pass) fits the parent.
+#include <math.h>
+
+#include "srp_internal.cuh"
+
+namespace srp {
+
+__device__ inline void rot_axis(const double *a, double th, double *R)
+{
+    double c = cos(th), s = sin(th), k = 1.0 - c;
+    R[0] = c + k * a[0] * a[0];        R[1] = k * a[0] * a[1] - s * a[2]; R[2] = k * a[0] * a[2] + s * a[1];
+    R[3] = k * a[1] * a[0] + s * a[2]; R[4] = c + k * a[1] * a[1];        R[5] = k * a[1] * a[2] - s * a[0];
+    R[6] = k * a[2] * a[0] - s * a[1]; R[7] = k * a[2] * a[1] + s * a[0]; R[8] = c + k * a[2] * a[2];
+}
+
+__global__ void k_pose(const MeshDev *mesh, const double *sun_dirs, const double *sun_dist, const double *angles,
+                       int panel_mode, double P0, int eval0, int S, SlotPose *pose)
+{
+    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= S) return;
+    SlotPose &P = pose[slot];
+    int e = eval0 + slot;
+    double s[3] = {sun_dirs[3 * e], sun_dirs[3 * e + 1], sun_dirs[3 * e + 2]};
+    double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    for (int k = 0; k < 3; k++) s[k] /= sn;
+    double dist = sun_dist ? sun_dist[e] : 1.0;
+    int np = mesh->n_parts;
+    for (int p = 0; p < np; p++) {
+        const PartInfo &pi = mesh->part[p];
+        double th = 0.0;
+        double *M = P.M[p], *T = P.T[p];
+        if (p == 0) {
+            for (int k = 0; k < 9; k++) M[k] = (k % 4 == 0) ? 1.0 : 0.0;
+            T[0] = T[1] = T[2] = 0.0;
+            P.angle[0] = 0.0;
+            continue;
+        }
+        int q = pi.parent;
+        const double *Mq = P.M[q], *Tq = P.T[q];
+        if (pi.movable) {
+            if (panel_mode != SRP_PANELS_SET) {
+                // Sun in the parent's current frame: Mq^T s
+                double sl[3];
+                for (int k = 0; k < 3; k++) sl[k] = Mq[k] * s[0] + Mq[3 + k] * s[1] + Mq[6 + k] * s[2];
+                const double *a = pi.axis, *n0 = pi.n0;
+                double na = n0[0] * a[0] + n0[1] * a[1] + n0[2] * a[2];
+                double n[3] = {n0[0] - na * a[0], n0[1] - na * a[1], n0[2] - na * a[2]};
+                double b[3] = {a[1] * n[2] - a[2] * n[1], a[2] * n[0] - a[0] * n[2], a[0] * n[1] - a[1] * n[0]};
+                double x = n[0] * sl[0] + n[1] * sl[1] + n[2] * sl[2];
+                double y = b[0] * sl[0] + b[1] * sl[1] + b[2] * sl[2];
+                th = (x == 0.0 && y == 0.0) ? 0.0 : atan2(y, x);
+                if (panel_mode == SRP_PANELS_TRACK_OFFSET && angles) th += angles[p];
+            } else {
+                th = angles ? angles[p] : 0.0;
+            }
+            th = fmin(fmax(th, pi.lim[0]), pi.lim[1]);
+        }
+        P.angle[p] = th;
+        double R[9];
+        if (pi.movable) rot_axis(pi.axis, th, R);
+        else for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) M[3 * i + j] = Mq[3 * i] * R[j] + Mq[3 * i + 1] * R[3 + j] + Mq[3 * i + 2] * R[6 + j];
+        const double *pv = pi.pivot;
+        double w[3];
+        for (int i = 0; i < 3; i++) w[i] = pv[i] - (R[3 * i] * pv[0] + R[3 * i + 1] * pv[1] + R[3 * i + 2] * pv[2]);
+        for (int i = 0; i < 3; i++) T[i] = Mq[3 * i] * w[0] + Mq[3 * i + 1] * w[1] + Mq[3 * i + 2] * w[2] + Tq[i];
+    }
+    // basis of the image plane around d = -s (Duff et al., JCGT 2017)
+    double d[3] = {-s[0], -s[1], -s[2]};
+    double sg = copysign(1.0, d[2]);
+    double a = -1.0 / (sg + d[2]);
+    double b = d[0] * d[1] * a;
+    P.u[0] = 1.0 + sg * d[0] * d[0] * a; P.u[1] = sg * b; P.u[2] = -sg * d[0];
+    P.v[0] = b; P.v[1] = sg + d[1] * d[1] * a; P.v[2] = -d[1];
+    for (int k = 0; k < 3; k++) { P.d[k] = d[k]; P.s[k] = s[k]; }
+    for (int k = 0; k < 3; k++) {
+        P.wmin_bits[k] = dbl_to_ord(INFINITY);
+        P.wmax_bits[k] = dbl_to_ord(-INFINITY);
+    }
+    P.scale = P0 / (dist * dist);
+    P.eval = e;
+    P.flags = 0;
+}
+
+cudaError_t launch_pose(const MeshDev *mesh_d, const double *sun_dirs, const double *sun_dist, const double *angles,
+                        int panel_mode, double P0, int eval0, int S, SlotPose *pose, cudaStream_t st)
+{
+    k_pose<<<(S + 31) / 32, 32, 0, st>>>(mesh_d, sun_dirs, sun_dist, angles, panel_mode, P0, eval0, S, pose);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- vertices
+__device__ inline double warp_min(double x)
+{
+    for (int o = 16; o; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ inline double warp_max(double x)
+{
+    for (int o = 16; o; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+__global__ void __launch_bounds__(256) k_vertices(const MeshDev *mesh, SlotPose *pose, SlotBufs slot, int n_verts,
+                                                  int n_dyn_verts)
+{
+    int s = blockIdx.y;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    SlotPose &P = pose[s];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (k < n_verts) {
+        int p = mesh->vert_part[k];
+        const PartInfo &pi = mesh->part[p];
+        double x[3] = {mesh->rest64[3 * k], mesh->rest64[3 * k + 1], mesh->rest64[3 * k + 2]};
+        if (pi.dynamic) {
+            const double *M = P.M[p], *T = P.T[p];
+            double y[3];
+            for (int i = 0; i < 3; i++) y[i] = M[3 * i] * x[0] + M[3 * i + 1] * x[1] + M[3 * i + 2] * x[2] + T[i];
+            size_t o = ((size_t)s * n_dyn_verts + (k - pi.vert_begin + pi.dyn_vert_off)) * 3;
+            slot.vert64[o] = y[0]; slot.vert64[o + 1] = y[1]; slot.vert64[o + 2] = y[2];
+            x[0] = y[0]; x[1] = y[1]; x[2] = y[2];
+        }
+        const double *ax[3] = {P.u, P.v, P.d};
+        for (int c = 0; c < 3; c++) {
+            double pr = ax[c][0] * x[0] + ax[c][1] * x[1] + ax[c][2] * x[2];
+            mn[c] = pr; mx[c] = pr;
+        }
+    }
+    __shared__ double smn[3][8], smx[3][8];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = 0; c < 3; c++) {
+        double a = warp_min(mn[c]), b = warp_max(mx[c]);
+        if (lane == 0) { smn[c][w] = a; smx[c][w] = b; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int c = threadIdx.x;
+        double a = smn[c][0], b = smx[c][0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) { a = fmin(a, smn[c][i]); b = fmax(b, smx[c][i]); }
+        if (a <= b) {
+            atomicMin(&P.wmin_bits[c], dbl_to_ord(a));
+            atomicMax(&P.wmax_bits[c], dbl_to_ord(b));
+        }
+    }
+}
+
+cudaError_t launch_vertices(const MeshDev *mesh_d, const MeshDev &mh, SlotPose *pose, SlotBufs slot, int S,
+                            cudaStream_t st)
+{
+    dim3 grid((mh.n_verts + 255) / 256, S);
+    k_vertices<<<grid, 256, 0, st>>>(mesh_d, pose, slot, mh.n_verts, mh.n_dyn_verts);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- refit
+__device__ inline void store_child_box(float4 *node, int which, const float *b)
+{
+    // child 0: a = (lo.x hi.x lo.y hi.y), b.xy = (lo.z hi.z); child 1: b.zw = (lo.x hi.x), c = (lo.y hi.y lo.z hi.z)
+    float *f = reinterpret_cast<float *>(node);
+    if (which == 0) {
+        *reinterpret_cast<float4 *>(f) = make_float4(b[0], b[3], b[1], b[4]);
+        *reinterpret_cast<float2 *>(f + 4) = make_float2(b[2], b[5]);
+    } else {
+        *reinterpret_cast<float2 *>(f + 6) = make_float2(b[0], b[3]);
+        *reinterpret_cast<float4 *>(f + 8) = make_float4(b[1], b[4], b[2], b[5]);
+    }
+}
+
+__device__ inline void load_child_box_cg(const float4 *node, int which, float *b)
+{
+    const float *f = reinterpret_cast<const float *>(node);
+    if (which == 0) {
+        float4 x = __ldcg(reinterpret_cast<const float4 *>(f));
+        float2 y = __ldcg(reinterpret_cast<const float2 *>(f + 4));
+        b[0] = x.x; b[3] = x.y; b[1] = x.z; b[4] = x.w; b[2] = y.x; b[5] = y.y;
+    } else {
+        float2 x = __ldcg(reinterpret_cast<const float2 *>(f + 6));
+        float4 y = __ldcg(reinterpret_cast<const float4 *>(f + 8));
+        b[0] = x.x; b[3] = x.y; b[1] = y.x; b[4] = y.y; b[2] = y.z; b[5] = y.w;
+    }
+}
+
+// Thread per sorted triangle in [t0, t0 + n) (all static, or all dynamic).
+__global__ void __launch_bounds__(256) k_refit(const MeshDev *mesh, SlotBufs slot, int t0, int n, int dyn,
+                                               float4 *node_static, float4 *tri_static, unsigned *counter_static,
+                                               float *root_static)
+{
+    int s = blockIdx.y;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    int t = t0 + idx;
+    // part of this sorted triangle: parts are contiguous in sorted order
+    int p = -1;
+    for (int q = 0; q < mesh->n_parts; q++) {
+        const PartInfo &pi = mesh->part[q];
+        if (t >= pi.tri_begin && t < pi.tri_begin + pi.tri_count) p = q;
+    }
+    if (p < 0) return;
+    const PartInfo &pi = mesh->part[p];
+    float4 *nodes;
+    float4 *tris;
+    unsigned *cnt;
+    float *root;
+    int tl = t - pi.tri_begin;
+    if (dyn) {
+        nodes = slot.node + ((size_t)s * mesh->n_dyn_nodes + pi.dyn_node_off) * 4;
+        tris = slot.tri + ((size_t)s * mesh->n_dyn_tris + pi.dyn_tri_off) * 3;
+        cnt = slot.counter + (size_t)s * mesh->n_dyn_nodes + pi.dyn_node_off;
+        root = slot.root_box + ((size_t)s * kMaxParts + p) * 6;
+    } else {
+        nodes = node_static + (size_t)pi.node_begin * 4;
+        tris = tri_static + (size_t)pi.tri_begin * 3;
+        cnt = counter_static + pi.node_begin;
+        root = root_static + p * 6;
+    }
+    // triangle record from FP64 vertices (posed for dynamic parts)
+    float v[3][3];
+    for (int c = 0; c < 3; c++) {
+        int vi = mesh->tri_vidx[3 * t + c];
+        const double *x;
+        if (dyn) x = slot.vert64 + ((size_t)s * mesh->n_dyn_verts + (vi - pi.vert_begin + pi.dyn_vert_off)) * 3;
+        else x = mesh->rest64 + (size_t)vi * 3;
+        v[c][0] = (float)x[0]; v[c][1] = (float)x[1]; v[c][2] = (float)x[2];
+    }
+    int orig = mesh->tri_orig[t];
+    unsigned mt = mesh->tri_mat[t];
+    float4 *rec = tris + (size_t)tl * 3;
+    rec[0] = make_float4(v[0][0], v[0][1], v[0][2], __int_as_float(orig));
+    rec[1] = make_float4(v[1][0], v[1][1], v[1][2], __uint_as_float(mt));
+    rec[2] = make_float4(v[2][0], v[2][1], v[2][2], 0.f);
+    float pad = (float)mesh->pad;
+    float box[6];
+    for (int k = 0; k < 3; k++) {
+        box[k] = fminf(fminf(v[0][k], v[1][k]), v[2][k]) - pad;
+        box[3 + k] = fmaxf(fmaxf(v[0][k], v[1][k]), v[2][k]) + pad;
+    }
+    int child = ~tl;
+    int node = mesh->leaf_parent[t];
+    for (int guard = 0; node >= 0; guard++) {
+        if (guard > kStack + 4) return;  // cannot happen for a tree that passed the depth check
+        float4 *nd = nodes + (size_t)node * 4;
+        int4 refs = *reinterpret_cast<const int4 *>(nd + 3);
+        int which = (refs.x == child) ? 0 : 1;
+        store_child_box(nd, which, box);
+        __threadfence();
+        unsigned old = atomicAdd(cnt + node, 1u);
+        if ((old & 1u) == 0u) return;  // first arrival: the sibling finishes this node
+        __threadfence();
+        float sib[6];
+        load_child_box_cg(nd, 1 - which, sib);
+        for (int k = 0; k < 3; k++) {
+            box[k] = fminf(box[k], sib[k]);
+            box[3 + k] = fmaxf(box[3 + k], sib[3 + k]);
+        }
+        child = node;
+        node = refs.z;
+    }
+    for (int k = 0; k < 6; k++) root[k] = box[k];
+}
+
+cudaError_t launch_refit(const MeshDev *mesh_d, const MeshDev &mh, SlotBufs slot, int S, bool static_pass,
+                         float4 *node_static, float4 *tri_static, unsigned *counter_static, float *root_static,
+                         cudaStream_t st)
+{
+    int t0 = static_pass ? 0 : mh.n_static_tris;
+    int n = static_pass ? mh.n_static_tris : mh.n_dyn_tris;
+    if (n <= 0) return cudaSuccess;
+    dim3 grid((n + 255) / 256, static_pass ? 1 : S);
+    k_refit<<<grid, 256, 0, st>>>(mesh_d, slot, t0, n, static_pass ? 0 : 1, node_static, tri_static, counter_static,
+                                  root_static);
+    return cudaGetLastError();
+}
+
+}  // namespace srp

@@ -1,0 +1,162 @@
+// srp_internal.cuh -- device data layout and kernel launchers of libsrp.
+//
+// Layout in HBM (one mesh):
+//   * triangles are sorted part-major (static parts first, then parts whose
+//     pose depends on a joint angle), Morton order within a part;
+//   * each part has its own binary LBVH over its triangles: n-1 internal
+//     nodes of 64 B (two child boxes + child refs), leaves are triangles;
+//   * a triangle record is 48 B: three FP32 vertices + original id +
+//     packed front/back material;
+//   * FP64 copies of the vertices (rest pose for static parts, posed per slot
+//     for dynamic parts) are read only by the FP64 refinement path;
+//   * dynamic parts have one copy of their vertices / triangle records /
+//     nodes per evaluation "slot", so S evaluations of a batch run at once.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/srp.h"
+
+namespace srp {
+
+constexpr int kMaxParts = SRP_MAX_PARTS;
+constexpr int kMaxMats = SRP_MAX_MATS;
+constexpr int kMaxBounces = SRP_MAX_BOUNCES;
+constexpr int kStack = 64;          // traversal stack entries (>= tree depth, checked at load)
+constexpr int kTraceThreads = 256;  // 16 x 16 pixel tile per block
+constexpr int kTile = 16;
+constexpr double kStandoff = 1.0;   // ray origins start 1 m in front of the nearest vertex
+
+// Device error flags (bits of SlotPose::flags / the context error word).
+constexpr int kFlagStack = 1;
+
+// Static per-part description (host and device copies).
+struct PartInfo {
+    int parent;         // -1 for the root
+    int movable;        // has its own joint
+    int dynamic;        // pose depends on some joint angle (itself or an ancestor)
+    int tri_begin;      // first sorted triangle of the part (global sorted index)
+    int tri_count;
+    int node_begin;     // first internal node of the part within its node array
+    int vert_begin;     // first vertex of the part (global, part-major re-indexed)
+    int vert_count;
+    int dyn_tri_off;    // offset of the part in the per-slot dynamic arrays (dynamic only)
+    int dyn_node_off;
+    int dyn_vert_off;
+    int pad_;
+    double pivot[3], axis[3], lim[2], n0[3];
+};
+
+// Per-slot pose + window, written by the pose / vertex kernels.
+struct SlotPose {
+    double M[kMaxParts][9];   // part rotation (row-major), body = M x_rest + T
+    double T[kMaxParts][3];
+    double angle[kMaxParts];
+    double s[3];              // unit Sun direction, body frame
+    double u[3], v[3], d[3];  // image-plane basis, d = -s
+    unsigned long long wmin_bits[3];  // ordered-int encodings of min(u.x), min(v.x), min(d.x)
+    unsigned long long wmax_bits[3];
+    double scale;             // P0 / dist^2 (multiplied by the pixel area at the end)
+    int eval;                 // evaluation index in the batch
+    int flags;                // device error flags
+};
+
+// Per-slot traversal view built from SlotPose by each trace block.
+struct Frame {
+    float org[3], du[3], dv[3], dir[3];  // FP32 ray generation: o = org + (i+.5) du + (j+.5) dv
+    double umin, vmin, wmin, Du, Dv, L, eps;
+};
+
+struct MeshDev {
+    int n_parts, n_tris, n_verts, n_mats;
+    int n_static_tris, n_static_nodes, n_static_verts;
+    int n_dyn_tris, n_dyn_nodes, n_dyn_verts;
+    int max_depth;
+    double pad;                 // absolute AABB padding (m)
+    double R;                   // bound on |x| over all poses (m)
+    double c_ref[3];
+    PartInfo part[kMaxParts];
+    int part_order[kMaxParts];  // layout position -> part id (static parts first)
+    // device arrays
+    double *rest64;        // [n_verts][3] rest pose FP64 (part-major)
+    int *vert_part;        // [n_verts]
+    int *tri_vidx;         // [n_tris][3] sorted triangles -> global vertex index
+    int *tri_orig;         // [n_tris] sorted -> original triangle id
+    unsigned *tri_mat;     // [n_tris] sorted -> (front | back << 16)
+    int *leaf_parent;      // [n_tris] sorted -> parent internal node (part-local), -1 for a single-leaf part
+    float4 *tri_static;    // [n_static_tris][3]
+    float4 *node_static;   // [n_static_nodes][4]
+    float2 *mat32;         // [n_mats] (rho_s, rho_d) FP32
+    double *mat64;         // [n_mats][2]
+    float root_box_static[kMaxParts][6];
+};
+
+// Per-slot dynamic storage (one block of arrays per concurrent evaluation).
+struct SlotBufs {
+    double *vert64;     // [S][n_dyn_verts][3] posed FP64
+    float4 *tri;        // [S][n_dyn_tris][3]
+    float4 *node;       // [S][n_dyn_nodes][4]
+    unsigned *counter;  // [S][n_dyn_nodes] refit arrival counters (never reset; parity of the count)
+    float *root_box;    // [S][kMaxParts][6]
+};
+
+// Arguments of the trace / refine kernels.
+struct TraceArgs {
+    const MeshDev *mesh_d;       // device copy of MeshDev
+    SlotPose *pose;              // [S] (trace / refine OR their error flags into it)
+    SlotBufs slot;
+    int N, bounces, nseg;
+    double eps_rel;
+    int n_blocks_x;              // trace blocks per evaluation
+    double *partials;            // [S][n_blocks_x][16]
+    double *partials_ref;        // [S][n_blocks_ref][16]
+    int n_blocks_ref;
+    uint32_t *amb;               // [S][ceil(N*N/32)] rays needing FP64 refinement (self-clearing)
+    int32_t *hits;               // [S][N*N][nseg] or null
+    int count;                   // gather traversal counters
+};
+
+// ordered-int encoding of doubles for atomicMin/Max
+__host__ __device__ inline unsigned long long dbl_to_ord(double x)
+{
+    unsigned long long b;
+    memcpy(&b, &x, 8);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double ord_to_dbl(unsigned long long o)
+{
+    unsigned long long b = (o & 0x8000000000000000ull) ? (o & 0x7fffffffffffffffull) : ~o;
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+}
+
+// ---------------------------------------------------------------- launchers
+// build.cu
+cudaError_t launch_morton(const double *rest64, const int *tri_vidx, const int *tri_part, const int *rank_of_part,
+                          const float *part_lo, const float *part_ext, int n_tris, unsigned long long *keys,
+                          int *vals, cudaStream_t st);
+cudaError_t radix_sort_pairs(unsigned long long *keys, int *vals, unsigned long long *keys_tmp, int *vals_tmp,
+                             int n, int lo_bit, int hi_bit, int *scratch, size_t scratch_ints, cudaStream_t st);
+size_t radix_sort_scratch_ints(int n);
+cudaError_t launch_karras(const unsigned long long *keys, const int *part_tri_begin, const int *part_tri_count,
+                          const int *part_node_begin, int n_parts_layout, int n_internal_total,
+                          const int *node_part, int4 *node_refs, int *leaf_parent, cudaStream_t st);
+cudaError_t launch_depth(const int4 *node_refs, const int *node_part_base, int n_nodes, int *depth, cudaStream_t st);
+
+// pose.cu
+cudaError_t launch_pose(const MeshDev *mesh_d, const double *sun_dirs, const double *sun_dist, const double *angles,
+                        int panel_mode, double P0, int eval0, int S, SlotPose *pose, cudaStream_t st);
+cudaError_t launch_vertices(const MeshDev *mesh_d, const MeshDev &mh, SlotPose *pose, SlotBufs slot, int S,
+                            cudaStream_t st);
+cudaError_t launch_refit(const MeshDev *mesh_d, const MeshDev &mh, SlotBufs slot, int S, bool static_pass,
+                         float4 *node_static, float4 *tri_static, unsigned *counter_static, float *root_static,
+                         cudaStream_t st);
+
+// trace.cu
+cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st);
+cudaError_t launch_refine(const TraceArgs &a, int S, cudaStream_t st);
+cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
+                          unsigned long long *stats_accum, cudaStream_t st);
+
+}  // namespace srp

@@ -1,0 +1,223 @@
+"""Python binding of libsrp (include/srp.h): argument marshalling only.
+
+Every computation happens in the CUDA kernels behind the C ABI.  Arrays may be
+numpy arrays (host memory) or torch tensors (CUDA tensors are passed as device
+pointers, on the context's stream).  There is no fallback: if libsrp.so cannot
+be loaded, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SRP_OK = 0
+ERRORS = {-1: "SRP_ERR_ARG", -2: "SRP_ERR_OOM", -3: "SRP_ERR_CUDA", -4: "SRP_ERR_MESH", -5: "SRP_ERR_STACK",
+          -6: "SRP_ERR_TIMEOUT", -7: "SRP_ERR_STEP", -8: "SRP_ERR_STATE"}
+SRP_F32, SRP_F64 = 0, 1
+PANELS_TRACK, PANELS_SET, PANELS_TRACK_OFFSET = 0, 1, 2
+EVAL_COUNT = 1
+MAX_BOUNCES = 4
+
+# Symbols declared in include/srp.h (checked by the tests against the library).
+EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",
+           "srp_eval_batch", "srp_eval_stats_get"]
+
+
+class SrpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [
+        ("n_verts", C.c_int32), ("vertex_dtype", C.c_int32), ("xyz", C.c_void_p),
+        ("n_tris", C.c_int32), ("tri", C.c_void_p), ("tri_part", C.c_void_p), ("tri_mat", C.c_void_p),
+        ("n_mats", C.c_int32), ("mat", C.c_void_p),
+        ("n_parts", C.c_int32), ("parent", C.c_void_p), ("pivot", C.c_void_p), ("axis", C.c_void_p),
+        ("limits", C.c_void_p), ("normal0", C.c_void_p),
+        ("c_ref", C.c_double * 3), ("mass", C.c_double),
+    ]
+
+
+class EvalParams(C.Structure):
+    _fields_ = [("N", C.c_int32), ("bounces", C.c_int32), ("P0", C.c_double), ("eps_rel", C.c_double),
+                ("panel_mode", C.c_int32), ("flags", C.c_int32)]
+
+
+class EvalStats(C.Structure):
+    _fields_ = [("evals", C.c_int64), ("rays", C.c_int64), ("segments", C.c_int64),
+                ("hits", C.c_int64 * (MAX_BOUNCES + 1)), ("refined", C.c_int64), ("nodes_visited", C.c_int64),
+                ("tris_tested", C.c_int64), ("box_tests", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libsrp.so (building it first when sources changed)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsrp.so not found at {path}")
+        lib = C.CDLL(path)
+        lib.srp_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p]
+        lib.srp_destroy.argtypes = [C.c_void_p]
+        lib.srp_destroy.restype = None
+        lib.srp_last_error.argtypes = [C.c_void_p]
+        lib.srp_last_error.restype = C.c_char_p
+        lib.srp_mesh_load.argtypes = [C.c_void_p, C.POINTER(MeshDesc), C.POINTER(C.c_int32)]
+        lib.srp_mesh_free.argtypes = [C.c_void_p, C.c_int32]
+        lib.srp_set_panel_angles.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
+        lib.srp_eval_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.srp_eval_stats_get.argtypes = [C.c_void_p, C.POINTER(EvalStats)]
+        _lib = lib
+    return _lib
+
+
+def _ptr(x):
+    """(pointer, keepalive) of a numpy array or torch tensor (C-contiguous)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, x
+    import torch
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), x
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _is_cuda(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor) and x.is_cuda
+    except ImportError:
+        return False
+
+
+class Context:
+    """One srp_ctx: a CUDA device, a stream, the loaded meshes."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        h = C.c_void_p()
+        st = None
+        if stream is not None:
+            st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = self.lib.srp_create(C.byref(h), device, st)
+        if rc != SRP_OK:
+            raise SrpError(rc, f"srp_create(device={device}) failed")
+        self.h = h
+        self.meshes = {}
+
+    def _check(self, rc):
+        if rc != SRP_OK:
+            raise SrpError(rc, self.lib.srp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.srp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load_mesh(self, mesh) -> int:
+        """Load a mesh given as paper_2608_07307_gb300.inputs.Mesh (or any object
+        with the same array attributes)."""
+        xyz = np.ascontiguousarray(mesh.xyz)
+        dt = SRP_F64 if xyz.dtype == np.float64 else SRP_F32
+        if xyz.dtype not in (np.float32, np.float64):
+            xyz = np.ascontiguousarray(xyz, np.float64)
+            dt = SRP_F64
+        keep = dict(
+            xyz=xyz, tri=np.ascontiguousarray(mesh.tri, np.int32), tri_part=np.ascontiguousarray(mesh.tri_part, np.int32),
+            tri_mat=np.ascontiguousarray(mesh.tri_mat, np.int32), mat=np.ascontiguousarray(mesh.mat, np.float64),
+            parent=np.ascontiguousarray(mesh.parent, np.int32), pivot=np.ascontiguousarray(mesh.pivot, np.float64),
+            axis=np.ascontiguousarray(mesh.axis, np.float64), limits=np.ascontiguousarray(mesh.limits, np.float64),
+            normal0=np.ascontiguousarray(mesh.normal0, np.float64))
+        d = MeshDesc(len(xyz), dt, keep["xyz"].ctypes.data, len(keep["tri"]), keep["tri"].ctypes.data,
+                     keep["tri_part"].ctypes.data, keep["tri_mat"].ctypes.data, len(keep["mat"]),
+                     keep["mat"].ctypes.data, len(keep["parent"]), keep["parent"].ctypes.data,
+                     keep["pivot"].ctypes.data, keep["axis"].ctypes.data, keep["limits"].ctypes.data,
+                     keep["normal0"].ctypes.data, (C.c_double * 3)(*np.asarray(mesh.c_ref, np.float64)),
+                     float(getattr(mesh, "mass", 1.0)))
+        mid = C.c_int32(-1)
+        self._check(self.lib.srp_mesh_load(self.h, C.byref(d), C.byref(mid)))
+        self.meshes[mid.value] = len(keep["parent"])
+        return mid.value
+
+    def free_mesh(self, mesh_id: int):
+        self._check(self.lib.srp_mesh_free(self.h, mesh_id))
+        self.meshes.pop(mesh_id, None)
+
+    def set_panel_angles(self, mesh_id: int, angles):
+        a = np.ascontiguousarray(np.asarray(angles, np.float64))
+        self._check(self.lib.srp_set_panel_angles(self.h, mesh_id, len(a), a.ctypes.data))
+
+    def eval_batch(self, mesh_id: int, sun_dirs, sun_dist=None, N: int = 256, bounces: int = 1, P0: float = 4.56e-6,
+                   eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, hits: bool = False, count: bool = False,
+                   out=None):
+        """Force [n,3] (N) and torque [n,3] (N m); with hits=True also the per-ray
+        hit triangle ids [n, N*N, bounces+1].  Outputs live where the input lives
+        (CUDA tensor in, CUDA tensors out; numpy in, numpy out) unless `out`
+        = (force, torque[, hits]) is given."""
+        n = int(sun_dirs.shape[0])
+        cuda = _is_cuda(sun_dirs)
+        if isinstance(sun_dirs, np.ndarray):
+            sun_dirs = np.ascontiguousarray(sun_dirs, np.float64)
+        else:
+            sun_dirs = sun_dirs.contiguous()
+        if isinstance(sun_dist, np.ndarray):
+            sun_dist = np.ascontiguousarray(sun_dist, np.float64)
+        elif sun_dist is not None:
+            sun_dist = sun_dist.contiguous()
+        nseg = bounces + 1
+        if out is not None:
+            force, torque = out[0], out[1]
+            hit = out[2] if len(out) > 2 else None
+        elif cuda:
+            import torch
+            force = torch.empty((n, 3), dtype=torch.float64, device=sun_dirs.device)
+            torque = torch.empty_like(force)
+            hit = torch.empty((n, N * N, nseg), dtype=torch.int32, device=sun_dirs.device) if hits else None
+        else:
+            force, torque = np.empty((n, 3)), np.empty((n, 3))
+            hit = np.empty((n, N * N, nseg), np.int32) if hits else None
+        p = EvalParams(N, bounces, P0, eps_rel, panel_mode, EVAL_COUNT if count else 0)
+        ps, k1 = _ptr(sun_dirs)
+        pd, k2 = _ptr(sun_dist)
+        pf, k3 = _ptr(force)
+        pt, k4 = _ptr(torque)
+        ph, k5 = _ptr(hit)
+        self._check(self.lib.srp_eval_batch(self.h, mesh_id, C.byref(p), n, ps, pd, pf, pt, ph))
+        return (force, torque, hit) if hits else (force, torque)
+
+    def eval_stats(self) -> dict:
+        s = EvalStats()
+        self._check(self.lib.srp_eval_stats_get(self.h, C.byref(s)))
+        return dict(evals=s.evals, rays=s.rays, segments=s.segments, hits=list(s.hits), refined=s.refined,
+                    nodes_visited=s.nodes_visited, tris_tested=s.tris_tested, box_tests=s.box_tests)

@@ -1,0 +1,194 @@
+"""GPU parity: libsrp (CUDA, through the C ABI) against the FP64 oracle.
+
+Bars (from the method's stated tolerances):
+  * hit-triangle ids identical per ray and segment, except rays whose first
+    differing segment lies within 1e-6 of the window diagonal from a triangle
+    edge (oracle edge proximity), and those may be at most 1e-5 of the rays;
+  * force and torque within 1e-4 relative (torque relative to
+    max(|tau|, |F| * 1 m), since torque can vanish by symmetry).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2608_07307_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+P0 = 4.56e-6
+FTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2608_07307_gb300 import srp
+    c = srp.Context(0)
+    yield c
+    c.close()
+
+
+def check_force(Fg, Tg, Fo, To, tol=FTOL):
+    Fg, Tg, Fo, To = map(np.asarray, (Fg, Tg, Fo, To))
+    for k in range(len(Fo)):
+        fn = np.linalg.norm(Fo[k])
+        assert np.linalg.norm(Fg[k] - Fo[k]) <= tol * fn, (k, Fg[k], Fo[k])
+        tn = max(np.linalg.norm(To[k]), fn * 1.0)
+        assert np.linalg.norm(Tg[k] - To[k]) <= tol * tn, (k, Tg[k], To[k])
+
+
+def check_hits(gh, oh, oe, L, label=""):
+    """gh, oh: [rays, nseg] ids; oe: oracle edge proximity [rays, nseg] (m)."""
+    gh = np.asarray(gh).reshape(oh.shape)
+    diff = gh != oh
+    bad = np.nonzero(diff.any(axis=1))[0]
+    for r in bad:
+        k = int(np.argmax(diff[r]))
+        assert oe[r, k] < 1e-6 * L, f"{label} ray {r} seg {k}: gpu {gh[r]} oracle {oh[r]} edge {oe[r, k]:.3g} L {L:.3g}"
+    assert len(bad) <= 1e-5 * len(oh), f"{label}: {len(bad)} mismatching rays of {len(oh)}"
+    return len(bad)
+
+
+def oracle_batch(mesh, dirs, N, bounces, hits=False, dist=None, angles=None, procs=1):
+    F, T, H, E, L = [], [], [], [], []
+    for k, s in enumerate(dirs):
+        r = O.evaluate(mesh, s, N, bounces, P0=P0, dist_au=1.0 if dist is None else dist[k], angles=angles,
+                       want_hits=hits, want_edge=hits, procs=procs)
+        F.append(r["F"]); T.append(r["T"]); L.append(r["win"][6])
+        if hits:
+            H.append(r["hits"]); E.append(r["edge"])
+    return np.array(F), np.array(T), H, E, L
+
+
+def test_box_wing_small_hits_and_force(ctx):
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_uniform(16, seed=0)
+    N, B = 64, 1
+    Fg, Tg, Hg = ctx.eval_batch(mid, dirs, N=N, bounces=B, hits=True)
+    Fo, To, Ho, Eo, L = oracle_batch(m, dirs, N, B, hits=True)
+    check_force(Fg, Tg, Fo, To)
+    for k in range(len(dirs)):
+        check_hits(Hg[k], Ho[k], Eo[k], L[k], f"dir {k}")
+
+
+def test_box_wing_full_config(ctx):
+    """Box-wing, 256 uniform directions (SplitMix64 seed 0), 256 x 256 rays, 1 bounce, tracking panels."""
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_uniform(256, seed=0)
+    N, B = 256, 1
+    Fg, Tg, Hg = ctx.eval_batch(mid, dirs, N=N, bounces=B, hits=True)
+    Fo, To, _, _, _ = oracle_batch(m, dirs, N, B)
+    check_force(Fg, Tg, Fo, To)
+    for k in (0, 37, 101, 255):
+        r = O.evaluate(m, dirs[k], N, B, want_hits=True, want_edge=True)
+        check_hits(Hg[k], r["hits"], r["edge"], r["win"][6], f"dir {k}")
+
+
+@pytest.mark.parametrize("N", [1, 17, 100])
+def test_ragged_grids(ctx, N):
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_uniform(5, seed=3)
+    Fg, Tg, Hg = ctx.eval_batch(mid, dirs, N=N, bounces=2, hits=True)
+    Fo, To, Ho, Eo, L = oracle_batch(m, dirs, N, 2, hits=True)
+    check_force(Fg, Tg, Fo, To)
+    for k in range(len(dirs)):
+        check_hits(Hg[k], Ho[k], Eo[k], L[k])
+
+
+def test_spacecraft_small_two_bounces(ctx):
+    m = I.spacecraft(0.25)
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_fibonacci(24)[::3]
+    N, B = 128, 2
+    Fg, Tg, Hg = ctx.eval_batch(mid, dirs, N=N, bounces=B, hits=True)
+    Fo, To, Ho, Eo, L = oracle_batch(m, dirs, N, B, hits=True, procs=4)
+    check_force(Fg, Tg, Fo, To)
+    for k in range(len(dirs)):
+        check_hits(Hg[k], Ho[k], Eo[k], L[k], f"dir {k}")
+    st = ctx.eval_stats()
+    assert st["evals"] == len(dirs) and st["rays"] == len(dirs) * N * N
+
+
+def test_panel_modes_set_and_offset(ctx):
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_uniform(6, seed=8)
+    ang = np.array([0.0, 0.4, -1.1])
+    from paper_2608_07307_gb300 import srp
+    ctx.set_panel_angles(mid, ang)
+    Fg, Tg = ctx.eval_batch(mid, dirs, N=96, bounces=1, panel_mode=srp.PANELS_SET)
+    Fo, To, _, _, _ = oracle_batch(m, dirs, 96, 1, angles=ang)
+    check_force(Fg, Tg, Fo, To)
+    # offset mode: tracking angle + offset, equals SET with the oracle's tracking angles + offset
+    off = np.array([0.0, 0.05, -0.02])
+    ctx.set_panel_angles(mid, off)
+    Fg2, Tg2 = ctx.eval_batch(mid, dirs, N=96, bounces=1, panel_mode=srp.PANELS_TRACK_OFFSET)
+    for k, s in enumerate(dirs):
+        a0, _ = O.pose(m, s)
+        r = O.evaluate(m, s, 96, 1, angles=a0 + off)
+        check_force(Fg2[k:k + 1], Tg2[k:k + 1], r["F"][None], r["T"][None])
+
+
+def test_distance_scaling_and_device_pointers(ctx):
+    import torch
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_uniform(8, seed=4)
+    dist = np.linspace(0.4, 1.3, 8)
+    Fh, Th = ctx.eval_batch(mid, dirs, dist, N=64, bounces=1)
+    Fo, To, _, _, _ = oracle_batch(m, dirs, 64, 1, dist=dist)
+    check_force(Fh, Th, Fo, To)
+    Fd, Td = ctx.eval_batch(mid, torch.tensor(dirs, device="cuda"), torch.tensor(dist, device="cuda"), N=64, bounces=1)
+    assert np.array_equal(Fd.cpu().numpy(), Fh) and np.array_equal(Td.cpu().numpy(), Th)
+
+
+def test_deterministic(ctx):
+    m = I.spacecraft(0.25)
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_fibonacci(10)
+    a = ctx.eval_batch(mid, dirs, N=200, bounces=2)
+    b = ctx.eval_batch(mid, dirs, N=200, bounces=2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_empty_batch_and_errors(ctx):
+    from paper_2608_07307_gb300 import srp
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    F, T = ctx.eval_batch(mid, np.zeros((0, 3)), N=16, bounces=1)
+    assert F.shape == (0, 3)
+    with pytest.raises(srp.SrpError) as e:
+        ctx.eval_batch(mid, np.array([[0, 0, 1.0]]), N=0)
+    assert e.value.code == -1
+    with pytest.raises(srp.SrpError) as e:
+        ctx.eval_batch(mid, np.array([[0, 0, 1.0]]), N=16, bounces=9)
+    assert e.value.code == -1
+    with pytest.raises(srp.SrpError) as e:
+        ctx.eval_batch(12345, np.array([[0, 0, 1.0]]), N=16)
+    assert e.value.code == -8
+    bad = I.box_wing()
+    bad.tri = bad.tri.copy()
+    bad.tri[0, 0] = 10 ** 6
+    with pytest.raises(srp.SrpError) as e:
+        ctx.load_mesh(bad)
+    assert e.value.code == -4
+
+
+def test_closed_form_plate_and_retroreflector(ctx):
+    mat = ((0.3, 0.2), (0.1, 0.4))
+    m = I.flat_plate(2.0, 1.0, mat=mat)
+    mid = ctx.load_mesh(m)
+    th = 0.7
+    s = np.array([[math.sin(th), 0, math.cos(th)]])
+    F, T = ctx.eval_batch(mid, s, N=48, bounces=0)
+    c = math.cos(th)
+    Fcf = -P0 * 2.0 * c * ((1 - 0.3) * s[0] + 2 * (0.3 * c + 0.2 / 3) * np.array([0, 0, 1.0]))
+    assert np.linalg.norm(F[0] - Fcf) < 1e-6 * np.linalg.norm(Fcf)
+    v = I.v_trough(1.0, 1.5, mat=((1.0, 0.0),))
+    vid = ctx.load_mesh(v)
+    F, T = ctx.eval_batch(vid, np.array([[0, 0, 1.0]]), N=64, bounces=1)
+    assert np.linalg.norm(F[0] - 2 * P0 * 3.0 * np.array([0, 0, -1.0])) < 1e-6 * 2 * P0 * 3.0
