@@ -1,0 +1,294 @@
+#!/usr/bin/env python
+"""Benchmark: ray-traced SRP evaluations per second on one GB300.
+
+Workload (synthetic stand-in for the paper's complex spacecraft, Sec. 5.1):
+the procedural spacecraft at 0.025 m facets (199 800 triangles: bus, dish,
+two Sun-tracking wings), a 1024 x 1024 ray window, 2 specular bounces, Sun
+directions from a 4096-point Fibonacci sphere (an SPAD-style table, Sec. 6.1).
+A step is one srp_eval_batch call over `--batch` directions: the whole path
+(tracking angles, panel rotation, refit, window, traversal, shading, bounces,
+reduction).  The BVH and triangles (~36 MB) fit in L2, so L2 is flushed by a
+256 MiB write between timed steps (outside the timed events).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 oracle on
+the host cores instead (bounded ray samples of the same workload).
+Under torchrun every rank takes its own share of the direction table
+(independent evaluations, no data exchange); the value is the sum of all
+ranks' evaluations over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SRP evals/s (200k-triangle spacecraft, 1024^2 rays, 2 specular bounces, tracking panels)"
+# Algorithmic FP32 work per test (FMA = 2 FLOP; add, mul, min, max, compare = 1):
+#   ray/box slab test: 3 x (2 FMA + min + max) + 2 max + 2 min + 1 compare = 23
+#   watertight ray/triangle test (published form): 9 sub + 6 FMA (shear) + 6 mul
+#   + 3 sub (edge functions) + 6 compare + 2 add (det) + 3 mul + 3 FMA (depth)
+#   + 1 div + 2 compare = 50
+FLOP_BOX, FLOP_TRI = 23, 50
+# FP32 peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--batch", type=int, default=32, help="directions per step")
+    p.add_argument("--facet", type=float, default=0.025)
+    p.add_argument("--N", type=int, default=1024)
+    p.add_argument("--bounces", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(a):
+    return f"spacecraft facet {a.facet} m, N={a.N}, bounces={a.bounces}, fibonacci-4096 directions, batch {a.batch}"
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+           "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+           "clocks_event_reasons.sw_power_cap")
+
+
+def start_clocks(index):
+    path = tempfile.mktemp(suffix=".csv")
+    try:
+        proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None, path
+    return proc, path
+
+
+def stop_clocks(proc, path):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    sm, mx, reasons, power = [], 0.0, set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1])); mx = max(mx, float(f[2])); power.append(float(f[3]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    os.unlink(path)
+    if not sm:
+        return None
+    busy = [x for x in sm if x > 0.5 * mx] or sm
+    return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "power_w_max": max(power) if power else None, "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def cpu_baseline(mesh, dirs, a, seconds):
+    """The oracle as it stands on a bounded ray sample; evals/s extrapolated."""
+    from oracle import oracle as O
+    t_tot, n_tot, k = 0.0, 0, 0
+    while t_tot < seconds and k < 64:
+        dt, n = O.timed_rays(mesh, dirs[k % len(dirs)], a.N, a.bounces, 64, seed=k)
+        t_tot += dt
+        n_tot += n
+        k += 1
+    per_ray = t_tot / n_tot
+    evals = 1.0 / (per_ray * a.N * a.N)
+    return {"value": evals, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_tot} random primary rays (+bounces) over {k} directions, single thread, "
+                      f"{t_tot:.1f} s; extrapolated to N^2 = {a.N * a.N} rays per evaluation"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2608_07307_gb300 import inputs as I
+    mesh = I.spacecraft(a.facet)
+    dirs = I.sun_dirs_fibonacci(4096)
+    per_step = max(2.0, min(20.0, 120.0 / max(a.steps + a.warmup, 1)))
+    vals = []
+    for k in range(a.warmup + a.steps):
+        r = cpu_baseline(mesh, dirs[k * 97 % 4096:][:8], a, per_step)
+        if k >= a.warmup:
+            vals.append(r["value"])
+    v = statistics.mean(vals)
+    ms = 1000.0 * a.batch / v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "tris": mesh.n_tris},
+            "cpu_baseline": dict(r, value=v),
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ native
+def run_native(a):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2608_07307_gb300 import inputs as I
+    from paper_2608_07307_gb300 import srp
+
+    mesh = I.spacecraft(a.facet)
+    table = I.sun_dirs_fibonacci(4096)
+    mine = np.ascontiguousarray(table[rank::world])
+    stream = torch.cuda.Stream(device=dev)
+    ctx = srp.Context(local, stream=stream)
+    mid = ctx.load_mesh(mesh)
+    d_dirs = torch.tensor(mine, device=dev)
+    B = a.batch
+    F = torch.empty((B, 3), dtype=torch.float64, device=dev)
+    T = torch.empty_like(F)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def batch(k):
+        o = (k * B) % (len(mine) - B + 1)
+        return d_dirs[o:o + B]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for k in range(a.warmup):
+            ctx.eval_batch(mid, batch(k), N=a.N, bounces=a.bounces, out=(F, T))
+        # traversal counters of one step (separate counting kernel, not timed)
+        ctx.eval_batch(mid, batch(0), N=a.N, bounces=a.bounces, out=(F, T), count=True)
+        cnt = ctx.eval_stats()
+        stream.synchronize()
+        barrier()
+        clk_proc, clk_path = start_clocks(local)
+        time.sleep(0.3)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        ms_trace = ms_refine = ms_geom = ms_reduce = 0.0
+        launches = trace_launches = refined = rays = segments = 0
+        for k in range(a.steps):
+            flush.zero_()
+            stream.synchronize()
+            ev[k][0].record(stream)
+            ctx.eval_batch(mid, batch(a.warmup + k), N=a.N, bounces=a.bounces, out=(F, T), timing=True)
+            ev[k][1].record(stream)
+            st = ctx.eval_stats()
+            ms_trace += st["ms_trace"]; ms_refine += st["ms_refine"]; ms_geom += st["ms_geometry"]
+            ms_reduce += st["ms_reduce"]
+            launches += st["launches"]; trace_launches += st["trace_launches"]
+            refined += st["refined"]; rays += st["rays"]; segments += st["segments"]
+        stream.synchronize()
+        clocks = stop_clocks(clk_proc, clk_path)
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        total_ms = sum(step_ms)
+        # end to end through the public API with host (pinned) buffers
+        hd = torch.empty((B, 3), dtype=torch.float64).pin_memory()
+        hF = torch.empty((B, 3), dtype=torch.float64).pin_memory()
+        hT = torch.empty((B, 3), dtype=torch.float64).pin_memory()
+        e2e_s = 0.0
+        for k in range(a.steps):
+            hd.copy_(torch.from_numpy(mine[(k * B) % (len(mine) - B + 1):][:B]))
+            flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            ctx.eval_batch(mid, hd, N=a.N, bounces=a.bounces, out=(hF, hT))
+            e2e_s += time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+    evals = B * a.steps * world
+    value = evals / (total_ms / 1000.0)
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    # roofline of the dominant kernel (FP32 trace)
+    n_ev = cnt["evals"]
+    flop_per_eval = (FLOP_BOX * cnt["box_tests"] + FLOP_TRI * cnt["tris_tested"]) / n_ev
+    evals_per_launch = B * a.steps / trace_launches
+    ms_per_launch = ms_trace / trace_launches
+    achieved = flop_per_eval * evals_per_launch / (ms_per_launch / 1000.0) / 1e12
+    bytes_per_eval = (64 * cnt["nodes_visited"] + 48 * cnt["tris_tested"]) / n_ev
+    l2_gbs = bytes_per_eval * evals_per_launch / (ms_per_launch / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "tris": mesh.n_tris, "N": a.N, "bounces": a.bounces,
+                   "batch": B, "accumulation": "f64", "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas{world}"},
+        "rays_per_s": value * a.N * a.N,
+        "segments_per_s": segments / (total_ms / 1000.0) * world,
+        "refined_fraction": refined / max(rays, 1),
+        "phases_ms_per_step": {"geometry": ms_geom / a.steps, "trace": ms_trace / a.steps,
+                               "refine": ms_refine / a.steps, "reduce": ms_reduce / a.steps},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
+                     "kernel": "k_trace", "ms_per_launch": ms_per_launch, "evals_per_launch": evals_per_launch,
+                     "flop_per_eval": flop_per_eval,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "roofline_l2": {"algorithmic_bytes_per_eval": bytes_per_eval, "achieved_gbs": l2_gbs,
+                        "note": "node (64 B) and triangle (48 B) fetches per eval; served mostly by L1/L2"},
+        "gpu_launches": launches,
+        "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": B * 3 * 8,
+                "d2h_bytes_per_step": B * 6 * 8},
+        "clocks": clocks,
+    }
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mesh, table[:8], a, a.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_native(a)
+
+
+if __name__ == "__main__":
+    main()

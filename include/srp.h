@@ -107,7 +107,8 @@ typedef struct {
     int32_t flags;       /* 0, or SRP_EVAL_COUNT to gather srp_eval_stats counters       */
 } srp_eval_params;
 
-#define SRP_EVAL_COUNT 1
+#define SRP_EVAL_COUNT 1  /* gather traversal counters (slower kernel variant)        */
+#define SRP_EVAL_TIMING 2 /* time each phase with CUDA events on the context stream   */
 
 /* Counters of the last srp_eval_batch call (summed over its evaluations). */
 typedef struct {
@@ -119,6 +120,16 @@ typedef struct {
     int64_t nodes_visited;    /* BVH nodes fetched (SRP_EVAL_COUNT only)                  */
     int64_t tris_tested;      /* ray/triangle tests (SRP_EVAL_COUNT only)                 */
     int64_t box_tests;        /* ray/box slab tests (SRP_EVAL_COUNT only)                 */
+    int64_t launches;         /* kernels launched by the call                            */
+    int64_t trace_launches;   /* of which FP32 trace kernels                             */
+    /* GPU time per phase, milliseconds (SRP_EVAL_TIMING only), after the
+     * paper's split of an evaluation into compute, transfer and reduction
+     * (Sec. 8.2, Eq. 4): */
+    double ms_geometry;       /* joint angles, posing, window, refit                     */
+    double ms_trace;          /* FP32 first-hit traversal, shading, bounces              */
+    double ms_refine;         /* FP64 re-trace of rays near an FP32 decision bound       */
+    double ms_reduce;         /* fixed-order FP64 reduction to force / torque            */
+    double ms_transfer;       /* host <-> device copies made by the call                 */
 } srp_eval_stats;
 
 /*

@@ -212,14 +212,22 @@ def eval_rays(mesh, s, rays, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9
     return dict(contrib=contrib, hits=hits, edge=edge)
 
 
-def timed_rays(mesh, s, N, bounces, n_rays, seed=0, **kw):
-    """Time the oracle on n_rays sampled primary rays (single thread).
-    Returns (seconds, rays traced)."""
+def timed_rays(mesh, s, N, bounces, n_rays, seed=0, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None):
+    """Time the oracle, as it stands, on n_rays sampled primary rays of one
+    direction (single thread, force sums only).  Returns (seconds, rays)."""
+    om = OMesh(mesh)
+    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts)
     rng = np.random.default_rng(seed)
-    rays = rng.choice(N * N, size=min(n_rays, N * N), replace=False)
+    rays = np.ascontiguousarray(rng.choice(N * N, size=min(n_rays, N * N), replace=False).astype(np.int64))
+    contrib = np.zeros((len(rays), 6))
+    s = np.ascontiguousarray(np.asarray(s, np.float64))
     t0 = time.perf_counter()
-    eval_rays(mesh, s, rays, N, bounces, **kw)
-    return time.perf_counter() - t0, len(rays)
+    rc = lib().orc_eval_rays(C.byref(om.s), C.byref(p), _dp(s), C.c_int64(len(rays)),
+                             rays.ctypes.data_as(C.POINTER(C.c_int64)), _dp(contrib), None, None)
+    dt = time.perf_counter() - t0
+    if rc != 0:
+        raise ValueError(f"orc_eval_rays failed: {rc}")
+    return dt, len(rays)
 
 
 # --------------------------------------------------------------- propagation

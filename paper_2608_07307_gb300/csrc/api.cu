@@ -50,6 +50,7 @@ struct srp_ctx {
     int *err_flags = nullptr;
     unsigned long long *stats = nullptr;
     srp_eval_stats last{};
+    std::vector<cudaEvent_t> events;  // pool for SRP_EVAL_TIMING
 };
 
 namespace {
@@ -206,6 +207,7 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->hits);
     cudaFree(ctx->err_flags);
     cudaFree(ctx->stats);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -545,6 +547,21 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     CK(ctx, grow(&ctx->partials, &ctx->partials_cap, (size_t)S * nbx * 16, false));
     CK(ctx, grow(&ctx->partials_ref, &ctx->partials_ref_cap, (size_t)S * nbr * 16, false));
     CK(ctx, grow(&ctx->amb, &ctx->amb_cap, (size_t)S * words, true));
+    // phase timing: events recorded on the context stream, summed per phase
+    const bool timing = (prm->flags & SRP_EVAL_TIMING) != 0;
+    std::vector<std::pair<int, int>> spans[5];  // geometry, trace, refine, reduce, transfer
+    int n_ev = 0;
+    auto mark = [&]() -> int {
+        if (!timing) return -1;
+        if (n_ev >= (int)ctx->events.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            ctx->events.push_back(e);
+        }
+        cudaEventRecord(ctx->events[n_ev], st);
+        return n_ev++;
+    };
+    int64_t launches = 0, trace_launches = 0;
     bool in_dev = is_device_ptr(sun_dir_body);
     bool dist_dev = sun_dist_au && is_device_ptr(sun_dist_au);
     bool f_dev = is_device_ptr(force), t_dev = is_device_ptr(torque);
@@ -555,9 +572,11 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     double *d_dist = sun_dist_au ? (dist_dev ? const_cast<double *>(sun_dist_au) : ctx->io + (size_t)n * 3) : nullptr;
     double *d_f = f_dev ? force : ctx->io + (size_t)n * 4;
     double *d_t = t_dev ? torque : ctx->io + (size_t)n * 7;
+    int t_in0 = mark();
     if (!in_dev) CK(ctx, cudaMemcpyAsync(d_sun, sun_dir_body, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     if (sun_dist_au && !dist_dev)
         CK(ctx, cudaMemcpyAsync(d_dist, sun_dist_au, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    spans[4].push_back({t_in0, mark()});
     if (hit_tri && !h_dev) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, (size_t)S * R * nseg, false));
     CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
     CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
@@ -577,19 +596,38 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
     for (int e0 = 0; e0 < n; e0 += S) {
         int Sc = std::min(S, n - e0);
+        int g0 = mark();
         CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, ctx->pose, st));
         CK(ctx, launch_vertices(m->d, m->h, ctx->pose, m->sb, Sc, st));
-        if (m->h.n_dyn_tris > 0) CK(ctx, launch_refit(m->d, m->h, m->sb, Sc, false, nullptr, nullptr, nullptr, nullptr, st));
+        launches += 2;
+        if (m->h.n_dyn_tris > 0) {
+            CK(ctx, launch_refit(m->d, m->h, m->sb, Sc, false, nullptr, nullptr, nullptr, nullptr, st));
+            launches++;
+        }
+        int g1 = mark();
         a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : ctx->hits) : nullptr;
         CK(ctx, launch_trace(a, Sc, st));
+        int g2 = mark();
         CK(ctx, launch_refine(a, Sc, st));
+        int g3 = mark();
         CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, st));
-        if (hit_tri && !h_dev)
+        int g4 = mark();
+        launches += 3;
+        trace_launches++;
+        spans[0].push_back({g0, g1});
+        spans[1].push_back({g1, g2});
+        spans[2].push_back({g2, g3});
+        spans[3].push_back({g3, g4});
+        if (hit_tri && !h_dev) {
             CK(ctx, cudaMemcpyAsync(hit_tri + (size_t)e0 * R * nseg, ctx->hits, sizeof(int32_t) * Sc * R * nseg,
                                     cudaMemcpyDeviceToHost, st));
+            spans[4].push_back({g4, mark()});
+        }
     }
+    int t_out0 = mark();
     if (!f_dev) CK(ctx, cudaMemcpyAsync(force, d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     if (!t_dev) CK(ctx, cudaMemcpyAsync(torque, d_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    spans[4].push_back({t_out0, mark()});
     int flags = 0;
     unsigned long long stats[16];
     CK(ctx, cudaMemcpyAsync(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -604,6 +642,18 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     L.nodes_visited = (int64_t)stats[9];
     L.tris_tested = (int64_t)stats[10];
     L.box_tests = (int64_t)stats[11];
+    L.launches = launches;
+    L.trace_launches = trace_launches;
+    if (timing) {
+        double *ms[5] = {&L.ms_geometry, &L.ms_trace, &L.ms_refine, &L.ms_reduce, &L.ms_transfer};
+        for (int p = 0; p < 5; p++)
+            for (auto &sp : spans[p]) {
+                float t = 0.f;
+                if (sp.first >= 0 && sp.second >= 0 &&
+                    cudaEventElapsedTime(&t, ctx->events[sp.first], ctx->events[sp.second]) == cudaSuccess)
+                    *ms[p] += t;
+            }
+    }
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
     return SRP_OK;
 }

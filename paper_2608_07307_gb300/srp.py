@@ -20,6 +20,7 @@ ERRORS = {-1: "SRP_ERR_ARG", -2: "SRP_ERR_OOM", -3: "SRP_ERR_CUDA", -4: "SRP_ERR
 SRP_F32, SRP_F64 = 0, 1
 PANELS_TRACK, PANELS_SET, PANELS_TRACK_OFFSET = 0, 1, 2
 EVAL_COUNT = 1
+EVAL_TIMING = 2
 MAX_BOUNCES = 4
 
 # Symbols declared in include/srp.h (checked by the tests against the library).
@@ -52,7 +53,9 @@ class EvalParams(C.Structure):
 class EvalStats(C.Structure):
     _fields_ = [("evals", C.c_int64), ("rays", C.c_int64), ("segments", C.c_int64),
                 ("hits", C.c_int64 * (MAX_BOUNCES + 1)), ("refined", C.c_int64), ("nodes_visited", C.c_int64),
-                ("tris_tested", C.c_int64), ("box_tests", C.c_int64)]
+                ("tris_tested", C.c_int64), ("box_tests", C.c_int64), ("launches", C.c_int64),
+                ("trace_launches", C.c_int64), ("ms_geometry", C.c_double), ("ms_trace", C.c_double),
+                ("ms_refine", C.c_double), ("ms_reduce", C.c_double), ("ms_transfer", C.c_double)]
 
 
 _lib = None
@@ -180,7 +183,7 @@ class Context:
 
     def eval_batch(self, mesh_id: int, sun_dirs, sun_dist=None, N: int = 256, bounces: int = 1, P0: float = 4.56e-6,
                    eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, hits: bool = False, count: bool = False,
-                   out=None):
+                   timing: bool = False, out=None):
         """Force [n,3] (N) and torque [n,3] (N m); with hits=True also the per-ray
         hit triangle ids [n, N*N, bounces+1].  Outputs live where the input lives
         (CUDA tensor in, CUDA tensors out; numpy in, numpy out) unless `out`
@@ -207,7 +210,7 @@ class Context:
         else:
             force, torque = np.empty((n, 3)), np.empty((n, 3))
             hit = np.empty((n, N * N, nseg), np.int32) if hits else None
-        p = EvalParams(N, bounces, P0, eps_rel, panel_mode, EVAL_COUNT if count else 0)
+        p = EvalParams(N, bounces, P0, eps_rel, panel_mode, (EVAL_COUNT if count else 0) | (EVAL_TIMING if timing else 0))
         ps, k1 = _ptr(sun_dirs)
         pd, k2 = _ptr(sun_dist)
         pf, k3 = _ptr(force)
@@ -220,4 +223,6 @@ class Context:
         s = EvalStats()
         self._check(self.lib.srp_eval_stats_get(self.h, C.byref(s)))
         return dict(evals=s.evals, rays=s.rays, segments=s.segments, hits=list(s.hits), refined=s.refined,
-                    nodes_visited=s.nodes_visited, tris_tested=s.tris_tested, box_tests=s.box_tests)
+                    nodes_visited=s.nodes_visited, tris_tested=s.tris_tested, box_tests=s.box_tests,
+                    launches=s.launches, trace_launches=s.trace_launches, ms_geometry=s.ms_geometry,
+                    ms_trace=s.ms_trace, ms_refine=s.ms_refine, ms_reduce=s.ms_reduce, ms_transfer=s.ms_transfer)
