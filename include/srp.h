@@ -192,6 +192,48 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
 /* Counters of the last srp_eval_batch on ctx. */
 srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out);
 
+/* Limits of srp_eval_noalloc. */
+#define SRP_NOALLOC_MAX_N 1024    /* rays per window side                     */
+#define SRP_NOALLOC_MAX_TRIS 4096 /* triangles (every ray tests every one)     */
+
+/*
+ * srp_eval_noalloc -- one SRP evaluation that allocates no memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run, e.g. flight or real-time code
+ * whose memory budget is fixed at start-up, work issued inside a CUDA stream
+ * capture (an allocation there would break the capture), or hosts whose memory
+ * only comes from their own pool.  It needs no srp_ctx (creating one allocates)
+ * and calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * It computes the same force and torque as srp_eval_batch for one Sun
+ * direction, for a mesh already posed by the caller (no joints), by testing
+ * every ray against every triangle in FP64 (no BVH), so it is meant for small
+ * meshes.  Its only scratch is a fixed array of 8 + 8 * SRP_NOALLOC_MAX_N^2 / 256
+ * doubles (about 256 KiB) in the library's device globals, which every GPU that
+ * loads the library holds until the process exits.
+ *   tri_xyz  [n_tris][3][3] device, posed vertices (m), counter-clockwise front
+ *   tri_mat  [n_tris][2]    device, material of the front, back side
+ *   mat      [n_mats][2]    device, rho_s, rho_d
+ *   sun_dir  [3] host, towards the Sun, body frame (normalised here)
+ *   c_ref    [3] host, torque reference point
+ *   force, torque  [3] device outputs (N, N m)
+ *   cuda_stream    stream to launch on (NULL = legacy default stream)
+ * Work runs on the current CUDA device and is asynchronous: synchronise the
+ * stream before reading the outputs.  The first call on a device looks up the
+ * scratch array's device address (once per device); make that first call
+ * before any stream capture.  All calls share the scratch array, which keeps
+ * the last call's contents (each call rewrites all it reads), so calls whose
+ * work overlaps on the GPU (other streams, other host threads) race.
+ * Errors: SRP_ERR_ARG (null pointer, n_tris outside [1, SRP_NOALLOC_MAX_TRIS],
+ * N outside [1, SRP_NOALLOC_MAX_N], bounces outside [0, SRP_MAX_BOUNCES], bad
+ * distance / pressure / direction), SRP_ERR_CUDA (device lookup or launch).
+ */
+srp_status srp_eval_noalloc(const double *tri_xyz, const int32_t *tri_mat, int32_t n_tris, const double *mat,
+                            int32_t n_mats, const double sun_dir[3], double sun_dist_au, const double c_ref[3],
+                            int32_t N, int32_t bounces, double P0, double eps_rel, double *force, double *torque,
+                            void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ MAX_BOUNCES = 4
 
 # Symbols declared in include/srp.h (checked by the tests against the library).
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",
-           "srp_eval_batch", "srp_eval_stats_get"]
+           "srp_eval_batch", "srp_eval_stats_get", "srp_eval_noalloc"]
 
 
 class SrpError(RuntimeError):
@@ -84,8 +84,30 @@ def load(build_if_needed: bool = True):
         lib.srp_eval_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.srp_eval_stats_get.argtypes = [C.c_void_p, C.POINTER(EvalStats)]
+        lib.srp_eval_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                         C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double), C.c_int32,
+                                         C.c_int32, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = lib
     return _lib
+
+
+def eval_noalloc(tri_xyz, tri_mat, mat, sun_dir, sun_dist_au, c_ref, N, bounces, P0, eps_rel, force, torque,
+                 stream=None):
+    """srp_eval_noalloc: one evaluation that allocates nothing.  tri_xyz
+    [n_tris, 9] float64, tri_mat [n_tris, 2] int32, mat [n_mats, 2] float64,
+    force / torque [3] float64 are CUDA tensors the caller owns; sun_dir and
+    c_ref are 3-sequences.  Asynchronous on `stream` (default: torch's current
+    stream); raises SrpError on a non-zero status."""
+    import torch
+    lib = load()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    s = (C.c_double * 3)(*[float(x) for x in sun_dir])
+    c = (C.c_double * 3)(*[float(x) for x in c_ref])
+    rc = lib.srp_eval_noalloc(tri_xyz.data_ptr(), tri_mat.data_ptr(), int(tri_xyz.shape[0]), mat.data_ptr(),
+                              int(mat.shape[0]), s, float(sun_dist_au), c, int(N), int(bounces), float(P0),
+                              float(eps_rel), force.data_ptr(), torque.data_ptr(), st.cuda_stream)
+    if rc != SRP_OK:
+        raise SrpError(rc, "srp_eval_noalloc failed")
 
 
 def _ptr(x):
