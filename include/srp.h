@@ -120,6 +120,8 @@ typedef struct {
     int64_t nodes_visited;    /* BVH nodes fetched (SRP_EVAL_COUNT only)                  */
     int64_t tris_tested;      /* ray/triangle tests (SRP_EVAL_COUNT only)                 */
     int64_t box_tests;        /* ray/box slab tests (SRP_EVAL_COUNT only)                 */
+    int64_t handoff_cause[4]; /* FP64 hand-offs by cause: primary edge, secondary edge,
+                                 near tie in t, self-hit band (SRP_EVAL_COUNT only)       */
     int64_t launches;         /* kernels launched by the call                            */
     int64_t trace_launches;   /* of which FP32 trace kernels                             */
     /* GPU time per phase, milliseconds (SRP_EVAL_TIMING only), after the

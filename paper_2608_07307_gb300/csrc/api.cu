@@ -41,8 +41,16 @@ struct srp_ctx {
     size_t partials_cap = 0;
     double *partials_ref = nullptr;
     size_t partials_ref_cap = 0;
-    uint32_t *amb = nullptr;
-    size_t amb_cap = 0;
+    int *amb_list = nullptr;
+    size_t amb_list_cap = 0;
+    double *partials1 = nullptr;
+    size_t partials1_cap = 0;
+    unsigned char *tctx = nullptr;
+    size_t tctx_cap = 0;
+    int *amb_count = nullptr;
+    size_t amb_count_cap = 0;
+    int *amb_off = nullptr;
+    size_t amb_off_cap = 0;
     double *io = nullptr;
     size_t io_cap = 0;
     int32_t *hits = nullptr;
@@ -51,6 +59,8 @@ struct srp_ctx {
     unsigned long long *stats = nullptr;
     srp_eval_stats last{};
     std::vector<cudaEvent_t> events;  // pool for SRP_EVAL_TIMING
+    cudaStream_t lane[2] = {nullptr, nullptr};  // pipeline lanes (forked from / joined to `stream`)
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -136,6 +146,7 @@ srp_status ensure_slots(srp_ctx *ctx, Mesh *m, int S)
     const MeshDev &h = m->h;
     SlotBufs &b = m->sb;
     CK(ctx, dmalloc(m->slot_allocs, &b.vert64, (size_t)S * h.n_dyn_verts * 3));
+    CK(ctx, dmalloc(m->slot_allocs, &b.vview, (size_t)S * h.n_verts));
     CK(ctx, dmalloc(m->slot_allocs, &b.tri, (size_t)S * h.n_dyn_tris * 3));
     CK(ctx, dmalloc(m->slot_allocs, &b.node, (size_t)S * h.n_dyn_nodes * 4));
     CK(ctx, dmalloc(m->slot_allocs, &b.counter, (size_t)S * h.n_dyn_nodes));
@@ -189,6 +200,16 @@ srp_status srp_create(srp_ctx **out, int32_t device, void *cuda_stream)
         srp_destroy(ctx);
         return SRP_ERR_OOM;
     }
+    for (int b = 0; b < 2; b++)
+        if (cudaStreamCreateWithFlags(&ctx->lane[b], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming) != cudaSuccess) {
+            srp_destroy(ctx);
+            return SRP_ERR_CUDA;
+        }
+    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+        srp_destroy(ctx);
+        return SRP_ERR_CUDA;
+    }
     *out = ctx;
     return SRP_OK;
 }
@@ -202,12 +223,21 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->pose);
     cudaFree(ctx->partials);
     cudaFree(ctx->partials_ref);
-    cudaFree(ctx->amb);
+    cudaFree(ctx->amb_list);
+    cudaFree(ctx->partials1);
+    cudaFree(ctx->tctx);
+    cudaFree(ctx->amb_count);
+    cudaFree(ctx->amb_off);
     cudaFree(ctx->io);
     cudaFree(ctx->hits);
     cudaFree(ctx->err_flags);
     cudaFree(ctx->stats);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    for (int b = 0; b < 2; b++) {
+        if (ctx->lane[b]) cudaStreamSynchronize(ctx->lane[b]), cudaStreamDestroy(ctx->lane[b]);
+        if (ctx->ev_join[b]) cudaEventDestroy(ctx->ev_join[b]);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -377,6 +407,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     MK(dmalloc(m->allocs, &h.rest64, (size_t)nv * 3));
     MK(dmalloc(m->allocs, &h.vert_part, (size_t)nv));
     MK(dmalloc(m->allocs, &h.tri_vidx, (size_t)NT * 3));
+    MK(dmalloc(m->allocs, &h.tri_v4, (size_t)NT));
     MK(dmalloc(m->allocs, &h.tri_orig, (size_t)NT));
     MK(dmalloc(m->allocs, &h.tri_mat, (size_t)NT));
     MK(dmalloc(m->allocs, &h.leaf_parent, (size_t)NT));
@@ -432,6 +463,9 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
             if (D->tri_part[sorig[k]] != order[r]) return bail(SRP_ERR_CUDA, "sort mixed parts", cudaErrorUnknown);
     }
     MK(cudaMemcpyAsync(h.tri_vidx, svidx.data(), sizeof(int) * svidx.size(), cudaMemcpyHostToDevice, st));
+    std::vector<int4> sv4(NT);
+    for (int k = 0; k < NT; k++) sv4[k] = make_int4(svidx[3 * (size_t)k], svidx[3 * (size_t)k + 1], svidx[3 * (size_t)k + 2], 0);
+    MK(cudaMemcpyAsync(h.tri_v4, sv4.data(), sizeof(int4) * NT, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(h.tri_orig, sorig.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(h.tri_mat, smat.data(), sizeof(unsigned) * NT, cudaMemcpyHostToDevice, st));
     // 3: binary radix tree per part
@@ -537,30 +571,41 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     // concurrent evaluations: enough rays in flight to fill the GPU several times
     int S = (int)std::min<size_t>(std::max<size_t>((size_t)(1u << 21) / R, 1), 64);
     S = std::min(S, n);
-    srp_status rc = ensure_slots(ctx, m, S);
+    // chunks of S evaluations alternate between two lane streams with their own
+    // slots and buffers, so the short, latency-bound tail of one chunk (FP64
+    // re-trace, reduction) overlaps the traversal of the next
+    const int nchunks = (n + S - 1) / S;
+    const int lanes = std::min(nchunks, 2);
+    srp_status rc = ensure_slots(ctx, m, S * lanes);
     if (rc) return rc;
-    int tiles = (N + kTile - 1) / kTile;
-    int nbx = tiles * tiles;
-    int nbr = (int)((R + kTraceThreads - 1) / kTraceThreads);
-    size_t words = (R + 31) / 32;
-    CK(ctx, grow(&ctx->pose, &ctx->pose_cap, (size_t)S, false));
-    CK(ctx, grow(&ctx->partials, &ctx->partials_cap, (size_t)S * nbx * 16, false));
-    CK(ctx, grow(&ctx->partials_ref, &ctx->partials_ref_cap, (size_t)S * nbr * 16, false));
-    CK(ctx, grow(&ctx->amb, &ctx->amb_cap, (size_t)S * words, true));
-    // phase timing: events recorded on the context stream, summed per phase
+    // trace tiles of 8 x 4 pixels, one warp each
+    int nbx = ((N + 7) / 8) * ((N + 3) / 4);
+    // FP64 re-trace grid: a few blocks per SM, walking the compacted hand-off list
+    int nbr = std::max(1, std::min(nbx, 1216 / S));
+    const size_t SL = (size_t)S * lanes;
+    CK(ctx, grow(&ctx->pose, &ctx->pose_cap, SL, false));
+    CK(ctx, grow(&ctx->partials, &ctx->partials_cap, SL * nbx * kPart, false));
+    CK(ctx, grow(&ctx->partials_ref, &ctx->partials_ref_cap, SL * nbr * kPart, false));
+    CK(ctx, grow(&ctx->amb_list, &ctx->amb_list_cap, SL * nbx * kTileRays, false));
+    CK(ctx, grow(&ctx->partials1, &ctx->partials1_cap, SL * kRed1 * kPart, false));
+    CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
+    CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * nbx, false));
+    CK(ctx, grow(&ctx->amb_off, &ctx->amb_off_cap, SL * (nbx + 1), false));
+    // phase timing: events recorded on the stream each phase runs on, summed per phase
     const bool timing = (prm->flags & SRP_EVAL_TIMING) != 0;
     std::vector<std::pair<int, int>> spans[5];  // geometry, trace, refine, reduce, transfer
     int n_ev = 0;
-    auto mark = [&]() -> int {
+    auto mark_on = [&](cudaStream_t s_) -> int {
         if (!timing) return -1;
         if (n_ev >= (int)ctx->events.size()) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return -1;
             ctx->events.push_back(e);
         }
-        cudaEventRecord(ctx->events[n_ev], st);
+        cudaEventRecord(ctx->events[n_ev], s_);
         return n_ev++;
     };
+    auto mark = [&]() -> int { return mark_on(st); };
     int64_t launches = 0, trace_launches = 0;
     bool in_dev = is_device_ptr(sun_dir_body);
     bool dist_dev = sun_dist_au && is_device_ptr(sun_dist_au);
@@ -577,52 +622,78 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     if (sun_dist_au && !dist_dev)
         CK(ctx, cudaMemcpyAsync(d_dist, sun_dist_au, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     spans[4].push_back({t_in0, mark()});
-    if (hit_tri && !h_dev) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, (size_t)S * R * nseg, false));
+    if (hit_tri && !h_dev) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * R * nseg, false));
     CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
     CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
-    TraceArgs a{};
-    a.mesh_d = m->d;
-    a.pose = ctx->pose;
-    a.slot = m->sb;
-    a.N = N;
-    a.bounces = prm->bounces;
-    a.nseg = nseg;
-    a.eps_rel = prm->eps_rel;
-    a.n_blocks_x = nbx;
-    a.n_blocks_ref = nbr;
-    a.partials = ctx->partials;
-    a.partials_ref = ctx->partials_ref;
-    a.amb = ctx->amb;
-    a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
-    for (int e0 = 0; e0 < n; e0 += S) {
-        int Sc = std::min(S, n - e0);
-        int g0 = mark();
-        CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, ctx->pose, st));
-        CK(ctx, launch_vertices(m->d, m->h, ctx->pose, m->sb, Sc, st));
+    // fork: both lanes start after everything already queued on the context stream
+    CK(ctx, cudaEventRecord(ctx->ev_fork, st));
+    for (int b = 0; b < lanes; b++) CK(ctx, cudaStreamWaitEvent(ctx->lane[b], ctx->ev_fork, 0));
+    for (int c = 0; c < nchunks; c++) {
+        const int e0 = c * S, b = c % lanes;
+        const int Sc = std::min(S, n - e0);
+        cudaStream_t ls = ctx->lane[b];
+        // lane b's slots and buffers
+        const MeshDev &h = m->h;
+        SlotBufs sb = m->sb;
+        size_t s0 = (size_t)b * S;
+        sb.vert64 += s0 * h.n_dyn_verts * 3;
+        sb.vview += s0 * h.n_verts;
+        sb.tri += s0 * h.n_dyn_tris * 3;
+        sb.node += s0 * h.n_dyn_nodes * 4;
+        sb.counter += s0 * h.n_dyn_nodes;
+        sb.root_box += s0 * kMaxParts * 6;
+        SlotPose *pose = ctx->pose + s0;
+        TraceArgs a{};
+        a.mesh_d = m->d;
+        a.pose = pose;
+        a.slot = sb;
+        a.N = N;
+        a.bounces = prm->bounces;
+        a.nseg = nseg;
+        a.eps_rel = prm->eps_rel;
+        a.n_blocks_x = nbx;
+        a.n_blocks_ref = nbr;
+        a.partials = ctx->partials + s0 * nbx * kPart;
+        a.partials1 = ctx->partials1 + s0 * kRed1 * kPart;
+        a.tctx = ctx->tctx + s0 * trace_ctx_bytes();
+        a.partials_ref = ctx->partials_ref + s0 * nbr * kPart;
+        a.amb_list = ctx->amb_list + s0 * nbx * kTileRays;
+        a.amb_count = ctx->amb_count + s0 * nbx;
+        a.amb_off = ctx->amb_off + s0 * (nbx + 1);
+        a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
+        int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
+        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : nullptr;
+        int g0 = mark_on(ls);
+        CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, pose, ls));
+        CK(ctx, launch_vertices(m->d, h, pose, sb, Sc, ls));
         launches += 2;
-        if (m->h.n_dyn_tris > 0) {
-            CK(ctx, launch_refit(m->d, m->h, m->sb, Sc, false, nullptr, nullptr, nullptr, nullptr, st));
+        if (h.n_dyn_tris > 0) {
+            CK(ctx, launch_refit(m->d, h, sb, Sc, false, nullptr, nullptr, nullptr, nullptr, ls));
             launches++;
         }
-        int g1 = mark();
-        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : ctx->hits) : nullptr;
-        CK(ctx, launch_trace(a, Sc, st));
-        int g2 = mark();
-        CK(ctx, launch_refine(a, Sc, st));
-        int g3 = mark();
-        CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, st));
-        int g4 = mark();
-        launches += 3;
+        int g1 = mark_on(ls);
+        CK(ctx, launch_trace(a, Sc, ls));
+        int g2 = mark_on(ls);
+        CK(ctx, launch_refine(a, Sc, ls));
+        int g3 = mark_on(ls);
+        CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
+        int g4 = mark_on(ls);
+        launches += 6;  // frame, trace, hand-off scan, refine, two reduction levels
         trace_launches++;
         spans[0].push_back({g0, g1});
         spans[1].push_back({g1, g2});
         spans[2].push_back({g2, g3});
         spans[3].push_back({g3, g4});
         if (hit_tri && !h_dev) {
-            CK(ctx, cudaMemcpyAsync(hit_tri + (size_t)e0 * R * nseg, ctx->hits, sizeof(int32_t) * Sc * R * nseg,
-                                    cudaMemcpyDeviceToHost, st));
-            spans[4].push_back({g4, mark()});
+            CK(ctx, cudaMemcpyAsync(hit_tri + (size_t)e0 * R * nseg, stage, sizeof(int32_t) * Sc * R * nseg,
+                                    cudaMemcpyDeviceToHost, ls));
+            spans[4].push_back({g4, mark_on(ls)});
         }
+    }
+    // join: the context stream continues after both lanes
+    for (int b = 0; b < lanes; b++) {
+        CK(ctx, cudaEventRecord(ctx->ev_join[b], ctx->lane[b]));
+        CK(ctx, cudaStreamWaitEvent(st, ctx->ev_join[b], 0));
     }
     int t_out0 = mark();
     if (!f_dev) CK(ctx, cudaMemcpyAsync(force, d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
@@ -642,6 +713,7 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     L.nodes_visited = (int64_t)stats[9];
     L.tris_tested = (int64_t)stats[10];
     L.box_tests = (int64_t)stats[11];
+    for (int k = 0; k < 4; k++) L.handoff_cause[k] = (int64_t)stats[12 + k];
     L.launches = launches;
     L.trace_launches = trace_launches;
     if (timing) {

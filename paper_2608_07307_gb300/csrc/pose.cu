@@ -134,10 +134,13 @@ __global__ void __launch_bounds__(256) k_vertices(const MeshDev *mesh, SlotPose 
             x[0] = y[0]; x[1] = y[1]; x[2] = y[2];
         }
         const double *ax[3] = {P.u, P.v, P.d};
+        double pr[3];
         for (int c = 0; c < 3; c++) {
-            double pr = ax[c][0] * x[0] + ax[c][1] * x[1] + ax[c][2] * x[2];
-            mn[c] = pr; mx[c] = pr;
+            pr[c] = ax[c][0] * x[0] + ax[c][1] * x[1] + ax[c][2] * x[2];
+            mn[c] = pr[c]; mx[c] = pr[c];
         }
+        // view-frame position of the vertex for the primary-ray test, rounded once
+        slot.vview[(size_t)s * n_verts + k] = make_float4((float)pr[0], (float)pr[1], (float)pr[2], 0.f);
     }
     __shared__ double smn[3][8], smx[3][8];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -81,6 +81,7 @@ struct MeshDev {
     double *rest64;        // [n_verts][3] rest pose FP64 (part-major)
     int *vert_part;        // [n_verts]
     int *tri_vidx;         // [n_tris][3] sorted triangles -> global vertex index
+    int4 *tri_v4;          // [n_tris] the same, padded to one 16-byte load
     int *tri_orig;         // [n_tris] sorted -> original triangle id
     unsigned *tri_mat;     // [n_tris] sorted -> (front | back << 16)
     int *leaf_parent;      // [n_tris] sorted -> parent internal node (part-local), -1 for a single-leaf part
@@ -94,27 +95,44 @@ struct MeshDev {
 // Per-slot dynamic storage (one block of arrays per concurrent evaluation).
 struct SlotBufs {
     double *vert64;     // [S][n_dyn_verts][3] posed FP64
+    float4 *vview;      // [S][n_verts] (u.x, v.x, d.x, 0) of every posed vertex, FP32 rounded from FP64
     float4 *tri;        // [S][n_dyn_tris][3]
     float4 *node;       // [S][n_dyn_nodes][4]
     unsigned *counter;  // [S][n_dyn_nodes] refit arrival counters (never reset; parity of the count)
     float *root_box;    // [S][kMaxParts][6]
 };
 
-// Arguments of the trace / refine kernels.
+// Partial sums per block (FP64; integer counts are exact below 2^53):
+//   0..2 force, 3..5 torque (unscaled), 6 rays sent to / done by the FP64 path,
+//   7 segments traced, 8..12 hits per segment level, 13 nodes, 14 triangles,
+//   15 box tests, 16..19 FP64 hand-offs by cause (primary edge, secondary
+//   edge, near tie, self-hit band).
+constexpr int kPart = 20;
+
+// Arguments of the trace / refine kernels.  A trace block is one warp over an
+// 8 x 4 pixel tile (kTileRays rays).
+constexpr int kTileRays = 32;
+constexpr int kRed1 = 64;  // first-level reduction blocks per slot
+
 struct TraceArgs {
     const MeshDev *mesh_d;       // device copy of MeshDev
     SlotPose *pose;              // [S] (trace / refine OR their error flags into it)
     SlotBufs slot;
+    unsigned char *tctx;         // [S] per-slot traversal context (k_frame output)
     int N, bounces, nseg;
     double eps_rel;
-    int n_blocks_x;              // trace blocks per evaluation
-    double *partials;            // [S][n_blocks_x][16]
-    double *partials_ref;        // [S][n_blocks_ref][16]
+    int n_blocks_x;              // trace tiles (blocks) per evaluation
+    double *partials;            // [S][n_blocks_x][kPart] one partial per tile
+    double *partials1;           // [S][kRed1][kPart] first-level sums of the tile partials
+    double *partials_ref;        // [S][n_blocks_ref][kPart]
     int n_blocks_ref;
-    uint32_t *amb;               // [S][ceil(N*N/32)] rays needing FP64 refinement (self-clearing)
+    int *amb_list;               // [S][n_blocks_x][kTileRays] rays handed to the FP64 path, per tile
+    int *amb_count;              // [S][n_blocks_x]
+    int *amb_off;                // [S][n_blocks_x + 1] exclusive scan of amb_count
     int32_t *hits;               // [S][N*N][nseg] or null
     int count;                   // gather traversal counters
 };
+size_t trace_ctx_bytes();
 
 // ordered-int encoding of doubles for atomicMin/Max
 __host__ __device__ inline unsigned long long dbl_to_ord(double x)

@@ -1,115 +1,176 @@
 // trace.cu -- ray generation, first-hit traversal, SRP shading, specular
 // bounces and the force / torque reduction (Sec. 4.3, 6.1).
 //
-// k_trace (FP32 fast path).  One thread per pixel ray, 16 x 16 pixel tiles
-// per block (a warp covers 8 x 4 pixels, so neighbouring rays walk the same
-// nodes).  Per segment: stack traversal of each part's binary LBVH (64 B
-// nodes fetched as four float4; child boxes slab-tested with the segment's
-// current best t), watertight ray/triangle test in FP32 (Woop, Benthin and
-// Wald, "Watertight ray/triangle intersection", JCGT 2(1), 2013).  Every FP32
-// decision carries an error bound: when an edge function, the self-hit test
-// or the nearest-hit comparison is within its bound, the ray is marked for the
-// FP64 path and contributes nothing here.  Per hit: absorbed + specular +
-// Lambertian momentum, torque about c_ref, specular ray of weight w rho_s.
-// Per-ray sums in FP32 (at most 1 + bounces terms), per-thread and block sums
-// in FP64 (warp shuffles, then shared memory), one FP64 partial per block.
+// k_frame.  Once per slot: the window (u, v bounds from the vertex pass), the
+// FP32 ray generation, the error bounds of the FP32 decisions and the
+// per-part traversal views, into a small context every trace block copies.
 //
-// k_refine (FP64 path).  Re-traces the marked rays from the pixel definition
-// with FP64 rays and vertices, the same BVH (boxes are padded well beyond the
-// FP32 rounding of the ray) and the same watertight test in FP64.
+// k_trace (FP32 fast path).  A block is one warp over an 8 x 4 pixel tile, so
+// no warp ever waits for another: the hardware block scheduler balances the
+// load at 32-ray granularity.  Per segment: stack traversal of each part's
+// binary LBVH (64 B nodes fetched as four float4; child boxes slab-tested
+// against the segment's current best t) with the watertight ray/triangle test
+// (Woop, Benthin and Wald, "Watertight ray/triangle intersection", JCGT 2(1),
+// 2013):
+//   * primary rays share the direction d, so their test runs in the view frame
+//     (u, v, d): per-vertex projections computed in FP64 and rounded once to
+//     FP32, the ray is the line through the pixel centre (uc, vc) along the
+//     third axis, and the watertight shear vanishes;
+//   * secondary (specular) rays use the world-frame test with the shear; their
+//     origin is rebuilt from the hit's barycentric weights.
+// Every FP32 decision carries an error bound: when an edge function, the
+// nearest-hit comparison or the self-hit threshold is within its bound, the
+// ray is handed to the FP64 path and contributes nothing here.  Per hit:
+// absorbed + specular + Lambertian momentum, torque about c_ref, specular ray
+// of weight w rho_s.  Per-ray sums in FP32 (at most 1 + bounces terms), tile
+// sums in FP64 by warp shuffles, one FP64 partial per tile; the tile's
+// handed-off rays go to its own list slot.
 //
-// k_reduce.  Fixed-order FP64 sum of the block partials of one evaluation,
-// scaled by P0 / dist^2 times the pixel area.  No atomics on data: results are
-// bit-reproducible for a given launch shape.
+// k_amb_scan + k_refine (FP64 path).  The per-tile hand-off counts are
+// scanned; refine threads walk the dense list in a fixed order and re-trace
+// each ray from its pixel definition with FP64 rays and vertices, the same BVH
+// (boxes padded well beyond the FP32 rounding of the ray; leaves pre-tested in
+// FP32 with a bound, so only triangles not certainly missed are tested in
+// FP64) and the same watertight test in FP64.
+//
+// k_reduce1 + k_reduce.  Fixed-order FP64 sums: contiguous ranges of tile
+// partials per first-level block, then those and the refine partials per
+// evaluation, scaled by P0 / dist^2 times the pixel area.  No atomics on data:
+// results are bit-reproducible for a given launch shape.
 #include <math.h>
+#include <stddef.h>
 
 #include "srp_internal.cuh"
 
 namespace srp {
 
+constexpr float kU = 5.9604645e-8f;  // unit roundoff of FP32, 2^-24
+
 struct PartView {
     const float4 *node;
-    const float4 *tri;
+    const float4 *tri;   // world-frame triangle records
+    const int4 *v4;      // vertex ids of the part's sorted triangles
     const double *v64;   // v64[3 * (vi - vert_begin) + c]
     int root;            // 0, or ~0 for a one-triangle part
     int limit;           // bound on loop iterations of one part walk (2 n - 1 items)
-    int tri_begin, vert_begin, pad_;
+    int tri_begin, vert_begin;
     float box[6];
+    int pad_[2];
 };
 
-struct BlockCtx {
-    Frame fr;
-    PartView part[kMaxParts];
-    int n_parts, n_mats;
-    double u[3], v[3], d[3];
-    double c_ref[3];
+struct TraceCtx {
+    // FP32 ray generation: o = org + (i+.5) du + (j+.5) dv; view-frame pixel centres
+    float org[3], du[3], dv[3], dir[3];
+    float umin32, vmin32, du32, dv32, w0_32;
+    float delta_p, tau_p;  // primary: bound on view-frame coordinate error, band on t
+    float delta_s;         // secondary: origin-error term added per segment
+    float R, L, pad, eps32;
     float cref32[3];
-    float delta0;   // bound on the FP32 error of projected coordinates (m), primary segment
-    float tau;      // band on t for near ties and the self-hit threshold (m)
-    float pad;
+    int n_parts, n_mats;
+    const float4 *vview;   // slot's view-frame vertices
+    const float2 *mat32;
+    const double *mat64;
+    const unsigned *tri_mat;
+    const int *tri_vidx;
+    // FP64 window and basis for the FP64 path
+    double umin, vmin, wmin, Du, Dv, Lw, eps;
+    double u[3], v[3], d[3], c_ref[3];
+    PartView part[kMaxParts];
 };
+
+size_t trace_ctx_bytes() { return sizeof(TraceCtx); }
 
 __device__ __forceinline__ float pick(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
 __device__ __forceinline__ double pickd(double x, double y, double z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
 
-// Fill the block context of slot s (thread 0), materials (all threads).
-__device__ void setup_block(BlockCtx &B, float2 *mat, const TraceArgs &a, int s)
+// ------------------------------------------------------------- k_frame
+__global__ void k_frame(TraceArgs a)
 {
+    int s = blockIdx.x;
+    if (threadIdx.x != 0) return;
     const MeshDev *m = a.mesh_d;
-    if (threadIdx.x == 0) {
-        const SlotPose &P = a.pose[s];
-        double umin = ord_to_dbl(P.wmin_bits[0]), umax = ord_to_dbl(P.wmax_bits[0]);
-        double vmin = ord_to_dbl(P.wmin_bits[1]), vmax = ord_to_dbl(P.wmax_bits[1]);
-        double wmin = ord_to_dbl(P.wmin_bits[2]), wmax = ord_to_dbl(P.wmax_bits[2]);
-        Frame &f = B.fr;
-        f.umin = umin; f.vmin = vmin; f.wmin = wmin;
-        f.Du = umax - umin; f.Dv = vmax - vmin;
-        double Dw = wmax - wmin;
-        f.L = sqrt(f.Du * f.Du + f.Dv * f.Dv + Dw * Dw);
-        f.eps = a.eps_rel * f.L;
-        double w0 = wmin - kStandoff;
-        double omax = 0.0;
-        for (int k = 0; k < 3; k++) {
-            double o = umin * P.u[k] + vmin * P.v[k] + w0 * P.d[k];
-            f.org[k] = (float)o;
-            f.du[k] = (float)(f.Du / a.N * P.u[k]);
-            f.dv[k] = (float)(f.Dv / a.N * P.v[k]);
-            f.dir[k] = (float)P.d[k];
-            B.u[k] = P.u[k]; B.v[k] = P.v[k]; B.d[k] = P.d[k];
-            B.c_ref[k] = m->c_ref[k];
-            B.cref32[k] = (float)m->c_ref[k];
-            omax = fmax(omax, fabs(o));
-        }
-        // Magnitude bound of every coordinate and difference the FP32 path forms.
-        double R = fmax(m->R, omax + f.Du + f.Dv) + f.L + 2.0 * kStandoff;
-        B.delta0 = (float)(16.0 * 5.9604644775390625e-8 * R);
-        B.tau = (float)(64.0 * 16.0 * 5.9604644775390625e-8 * R + 1e-6 * f.L);
-        B.pad = (float)m->pad;
-        B.n_parts = m->n_parts;
-        B.n_mats = m->n_mats;
-        for (int p = 0; p < m->n_parts; p++) {
-            const PartInfo &pi = m->part[p];
-            PartView &pv = B.part[p];
-            pv.root = pi.tri_count > 1 ? 0 : ~0;
-            pv.limit = 2 * pi.tri_count + 8;
-            pv.tri_begin = pi.tri_begin;
-            pv.vert_begin = pi.vert_begin;
-            if (pi.dynamic) {
-                pv.node = a.slot.node + ((size_t)s * m->n_dyn_nodes + pi.dyn_node_off) * 4;
-                pv.tri = a.slot.tri + ((size_t)s * m->n_dyn_tris + pi.dyn_tri_off) * 3;
-                pv.v64 = a.slot.vert64 + ((size_t)s * m->n_dyn_verts + pi.dyn_vert_off) * 3;
-                const float *rb = a.slot.root_box + ((size_t)s * kMaxParts + p) * 6;
-                for (int k = 0; k < 6; k++) pv.box[k] = rb[k];
-            } else {
-                pv.node = m->node_static + (size_t)pi.node_begin * 4;
-                pv.tri = m->tri_static + (size_t)pi.tri_begin * 3;
-                pv.v64 = m->rest64 + (size_t)pi.vert_begin * 3;
-                for (int k = 0; k < 6; k++) pv.box[k] = m->root_box_static[p][k];
-            }
+    const SlotPose &P = a.pose[s];
+    TraceCtx &B = reinterpret_cast<TraceCtx *>(a.tctx)[s];
+    double umin = ord_to_dbl(P.wmin_bits[0]), umax = ord_to_dbl(P.wmax_bits[0]);
+    double vmin = ord_to_dbl(P.wmin_bits[1]), vmax = ord_to_dbl(P.wmax_bits[1]);
+    double wmin = ord_to_dbl(P.wmin_bits[2]), wmax = ord_to_dbl(P.wmax_bits[2]);
+    B.umin = umin; B.vmin = vmin; B.wmin = wmin;
+    B.Du = umax - umin; B.Dv = vmax - vmin;
+    double Dw = wmax - wmin;
+    B.Lw = sqrt(B.Du * B.Du + B.Dv * B.Dv + Dw * Dw);
+    B.eps = a.eps_rel * B.Lw;
+    B.eps32 = (float)B.eps;
+    double w0 = wmin - kStandoff;
+    for (int k = 0; k < 3; k++) {
+        double o = umin * P.u[k] + vmin * P.v[k] + w0 * P.d[k];
+        B.org[k] = (float)o;
+        B.du[k] = (float)(B.Du / a.N * P.u[k]);
+        B.dv[k] = (float)(B.Dv / a.N * P.v[k]);
+        B.dir[k] = (float)P.d[k];
+        B.u[k] = P.u[k]; B.v[k] = P.v[k]; B.d[k] = P.d[k];
+        B.c_ref[k] = m->c_ref[k];
+        B.cref32[k] = (float)m->c_ref[k];
+    }
+    B.umin32 = (float)umin; B.vmin32 = (float)vmin;
+    B.du32 = (float)(B.Du / a.N); B.dv32 = (float)(B.Dv / a.N);
+    B.w0_32 = (float)w0;
+    const double u = 5.9604644775390625e-8;
+    // Primary (view frame): vertex projections rounded once (|p| u/2), pixel
+    // centres from rounded umin, du and one FMA, differences rounded; the bound
+    // doubles that sum.
+    double Mw = fmax(fmax(fabs(umin), fabs(umax)), fmax(fabs(vmin), fabs(vmax)));
+    double Dm = fmax(B.Du, B.Dv);
+    B.delta_p = (float)(2.0 * u * (3.0 * Mw + 2.0 * Dm));
+    double Wm = fmax(fabs(wmin), fabs(wmax)) + kStandoff;
+    B.tau_p = (float)(16.0 * u * Wm + 32.0 * B.delta_p);
+    // Secondary (world frame): the origin is rebuilt from the hit's barycentric
+    // weights (error ~2 x the previous bound + rounding at |x| <= R, plus the
+    // rounding of posed vertices); the per-triangle terms (subtraction, shear,
+    // reflected direction) are added in the test from that triangle's distance.
+    double R = m->R;
+    B.delta_s = (float)(6.0 * u * R);
+    B.R = (float)R;
+    B.L = (float)B.Lw;
+    B.pad = (float)m->pad;
+    B.n_parts = m->n_parts;
+    B.n_mats = m->n_mats;
+    B.vview = a.slot.vview + (size_t)s * m->n_verts;
+    B.mat32 = m->mat32;
+    B.mat64 = m->mat64;
+    B.tri_mat = m->tri_mat;
+    B.tri_vidx = m->tri_vidx;
+    for (int p = 0; p < m->n_parts; p++) {
+        const PartInfo &pi = m->part[p];
+        PartView &pv = B.part[p];
+        pv.root = pi.tri_count > 1 ? 0 : ~0;
+        pv.limit = 2 * pi.tri_count + 8;
+        pv.tri_begin = pi.tri_begin;
+        pv.vert_begin = pi.vert_begin;
+        pv.v4 = m->tri_v4 + pi.tri_begin;
+        if (pi.dynamic) {
+            pv.node = a.slot.node + ((size_t)s * m->n_dyn_nodes + pi.dyn_node_off) * 4;
+            pv.tri = a.slot.tri + ((size_t)s * m->n_dyn_tris + pi.dyn_tri_off) * 3;
+            pv.v64 = a.slot.vert64 + ((size_t)s * m->n_dyn_verts + pi.dyn_vert_off) * 3;
+            const float *rb = a.slot.root_box + ((size_t)s * kMaxParts + p) * 6;
+            for (int k = 0; k < 6; k++) pv.box[k] = rb[k];
+        } else {
+            pv.node = m->node_static + (size_t)pi.node_begin * 4;
+            pv.tri = m->tri_static + (size_t)pi.tri_begin * 3;
+            pv.v64 = m->rest64 + (size_t)pi.vert_begin * 3;
+            for (int k = 0; k < 6; k++) pv.box[k] = m->root_box_static[p][k];
         }
     }
-    for (int i = threadIdx.x; i < m->n_mats; i += blockDim.x) mat[i] = m->mat32[i];
-    __syncthreads();
+}
+
+// Copy the slot context (header + the parts in use) into shared memory.
+__device__ __forceinline__ void load_ctx(TraceCtx &B, const TraceArgs &a, int s)
+{
+    const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
+    int np = a.mesh_d->n_parts;
+    int words = (int)((offsetof(TraceCtx, part) + np * sizeof(PartView)) / 4);
+    const int *src = reinterpret_cast<const int *>(g);
+    int *dst = reinterpret_cast<int *>(&B);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = __ldg(src + k);
 }
 
 // Slab test of one box; returns entry t or +inf.
@@ -153,31 +214,60 @@ __device__ __forceinline__ void ray_setup(Ray32 &r)
 struct Best32 {
     float t;
     int part, tl;
+    float b1, b2;  // barycentric weights of the hit's second and third vertex
 };
 
-// Nearest hit of one segment in FP32.  Returns false when some decision was
-// within its error bound (the ray then goes to the FP64 path).
 struct Counts {
     float nodes, tris, boxes;
+    float why[4];  // hand-offs: primary edge, secondary edge, near tie, self-hit band
     int flags;
 };
 
+// Classify one candidate from its edge functions and depth.  Returns true when
+// the FP32 decision is not certain.  Updates best on a certain nearer hit.
 template <bool COUNT>
-__device__ bool nearest32(const BlockCtx &B, const Ray32 &r, float tlo, int skip, float delta, Best32 &best,
-                          Counts &cn)
+__device__ __forceinline__ bool classify(float U, float V, float W, float eU, float eV, float eW, float T, float det,
+                                         float tlo, float tau, int p, int tl, Best32 &best, bool primary, Counts &cn)
+{
+    bool neg = (U < -eU) || (V < -eV) || (W < -eW);
+    bool pos = (U > eU) || (V > eV) || (W > eW);
+    if (neg && pos) return false;  // certainly outside
+    bool unsure = fabsf(U) <= eU || fabsf(V) <= eV || fabsf(W) <= eW;
+    float t = T / det;
+    if (unsure) {
+        // near an edge: matters unless the plane is certainly behind the origin or beyond the best hit
+        bool far = (fabsf(det) > 1e-30f) && (t > best.t + tau || t < tlo - tau);
+        if (!far && COUNT) cn.why[primary ? 0 : 1] += 1.f;
+        return !far;
+    }
+    bool amb = false;
+    if (fabsf(t - tlo) <= tau) { amb = true; if (COUNT) cn.why[3] += 1.f; }
+    else if (fabsf(t - best.t) <= tau) { amb = true; if (COUNT) cn.why[2] += 1.f; }
+    if (t > tlo && t < best.t) {
+        float id = 1.0f / det;
+        best.t = t; best.part = p; best.tl = tl; best.b1 = V * id; best.b2 = W * id;
+    }
+    return amb;
+}
+
+// Nearest hit of one segment in FP32.  `primary`: the view-frame test at pixel
+// centre (uc, vc); otherwise the world-frame test.  Returns false when some
+// decision was within its error bound (the ray then goes to the FP64 path).
+template <bool COUNT>
+__device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float uc, float vc, float tlo, int skip,
+                          float delta, float tau, Best32 &best, Counts &cn)
 {
     best.t = INFINITY;
     best.part = -1;
     best.tl = -1;
-    const float tau = B.tau;
     int stack[kStack];
     unsigned n_nodes = 0, n_tris = 0, n_boxes = 0;
     bool clean = true;
+    const float u4 = 4.0f * kU;
     for (int p = 0; p < B.n_parts; p++) {
         const PartView &pv = B.part[p];
-        float thi = best.t + tau;
         if (box_enter(pv.box[0], pv.box[3], pv.box[1], pv.box[4], pv.box[2], pv.box[5], r.inv, r.oi, tlo - tau,
-                      thi) == INFINITY)
+                      best.t + tau) == INFINITY)
             continue;
         int sp = 0, iters = 0;
         int ref = pv.root;
@@ -202,43 +292,50 @@ __device__ bool nearest32(const BlockCtx &B, const Ray32 &r, float tlo, int skip
                 else if (h1) { ref = c.y; continue; }
             } else {
                 int tl = ~ref;
-                const float4 *tr = pv.tri + (size_t)tl * 3;
-                float4 a = __ldg(tr), b = __ldg(tr + 1), c = __ldg(tr + 2);
                 if (COUNT) n_tris++;
-                if (__float_as_int(a.w) != skip) {
-                    // watertight test, FP32, with error bounds
-                    float A0 = a.x - r.o[0], A1 = a.y - r.o[1], A2 = a.z - r.o[2];
-                    float B0 = b.x - r.o[0], B1 = b.y - r.o[1], B2 = b.z - r.o[2];
-                    float C0 = c.x - r.o[0], C1 = c.y - r.o[1], C2 = c.z - r.o[2];
-                    float Akz = pick(A0, A1, A2, r.kz), Bkz = pick(B0, B1, B2, r.kz), Ckz = pick(C0, C1, C2, r.kz);
-                    float Ax = fmaf(-r.Sx, Akz, pick(A0, A1, A2, r.kx)), Ay = fmaf(-r.Sy, Akz, pick(A0, A1, A2, r.ky));
-                    float Bx = fmaf(-r.Sx, Bkz, pick(B0, B1, B2, r.kx)), By = fmaf(-r.Sy, Bkz, pick(B0, B1, B2, r.ky));
-                    float Cx = fmaf(-r.Sx, Ckz, pick(C0, C1, C2, r.kx)), Cy = fmaf(-r.Sy, Ckz, pick(C0, C1, C2, r.ky));
+                if (primary) {
+                    int4 vi = __ldg(pv.v4 + tl);
+                    float4 a = __ldg(B.vview + vi.x), b = __ldg(B.vview + vi.y), c = __ldg(B.vview + vi.z);
+                    // view frame: the ray is the third axis through (uc, vc)
+                    float Ax = a.x - uc, Ay = a.y - vc, Bx = b.x - uc, By = b.y - vc, Cx = c.x - uc, Cy = c.y - vc;
                     float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
                     float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
                     float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-                    const float u4 = 4.0f * 5.9604645e-8f;
                     float eU = delta * (fabsf(Bx) + fabsf(By) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Cx * By) + fabsf(Cy * Bx));
                     float eV = delta * (fabsf(Ax) + fabsf(Ay) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Ax * Cy) + fabsf(Ay * Cx));
                     float eW = delta * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + u4 * (fabsf(Bx * Ay) + fabsf(By * Ax));
-                    bool neg = (U < -eU) || (V < -eV) || (W < -eW);
-                    bool pos = (U > eU) || (V > eV) || (W > eW);
-                    if (!(neg && pos)) {
-                        bool unsure = fabsf(U) <= eU || fabsf(V) <= eV || fabsf(W) <= eW;
+                    float det = U + V + W;
+                    float T = fmaf(U, a.z - B.w0_32, fmaf(V, b.z - B.w0_32, W * (c.z - B.w0_32)));
+                    if (classify<COUNT>(U, V, W, eU, eV, eW, T, det, tlo, tau, p, tl, best, true, cn)) { clean = false; sp = 0; }
+                } else {
+                    const float4 *tr = pv.tri + (size_t)tl * 3;
+                    float4 a = __ldg(tr), b = __ldg(tr + 1), c = __ldg(tr + 2);
+                    if (__float_as_int(a.w) != skip) {
+                        float A0 = a.x - r.o[0], A1 = a.y - r.o[1], A2 = a.z - r.o[2];
+                        float B0 = b.x - r.o[0], B1 = b.y - r.o[1], B2 = b.z - r.o[2];
+                        float C0 = c.x - r.o[0], C1 = c.y - r.o[1], C2 = c.z - r.o[2];
+                        float Akz = pick(A0, A1, A2, r.kz), Bkz = pick(B0, B1, B2, r.kz), Ckz = pick(C0, C1, C2, r.kz);
+                        float Ax = fmaf(-r.Sx, Akz, pick(A0, A1, A2, r.kx)), Ay = fmaf(-r.Sy, Akz, pick(A0, A1, A2, r.ky));
+                        float Bx = fmaf(-r.Sx, Bkz, pick(B0, B1, B2, r.kx)), By = fmaf(-r.Sy, Bkz, pick(B0, B1, B2, r.ky));
+                        float Cx = fmaf(-r.Sx, Ckz, pick(C0, C1, C2, r.kx)), Cy = fmaf(-r.Sy, Ckz, pick(C0, C1, C2, r.ky));
+                        float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+                        float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+                        float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+                        // coordinate error: origin error (delta) + subtraction, shear and
+                        // reflected-direction rounding, growing with this triangle's distance
+                        float dz = fmaxf(fmaxf(fabsf(Akz), fabsf(Bkz)), fabsf(Ckz)) + fmaxf(fmaxf(fabsf(Ax), fabsf(Bx)), fabsf(Cx)) +
+                                   fmaxf(fmaxf(fabsf(Ay), fabsf(By)), fabsf(Cy));
+                        float dc = fmaf(16.0f * kU, dz, delta);
+                        float eU = dc * (fabsf(Bx) + fabsf(By) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Cx * By) + fabsf(Cy * Bx));
+                        float eV = dc * (fabsf(Ax) + fabsf(Ay) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Ax * Cy) + fabsf(Ay * Cx));
+                        float eW = dc * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + u4 * (fabsf(Bx * Ay) + fabsf(By * Ax));
                         float det = U + V + W;
                         float T = fmaf(U, r.Sz * Akz, fmaf(V, r.Sz * Bkz, W * (r.Sz * Ckz)));
-                        float t = T / det;
-                        if (unsure) {
-                            // near an edge: matters unless the plane is clearly behind or beyond the best hit
-                            bool far = (fabsf(det) > 1e-30f) && (t > best.t + tau || t < tlo - tau);
-                            if (!far) clean = false;
-                        } else {
-                            if (fabsf(t - tlo) <= tau || fabsf(t - best.t) <= tau) clean = false;
-                            if (t > tlo && t < best.t) { best.t = t; best.part = p; best.tl = tl; }
-                        }
+                        if (classify<COUNT>(U, V, W, eU, eV, eW, T, det, tlo, tau, p, tl, best, false, cn)) { clean = false; sp = 0; }
                     }
                 }
             }
+            // a handed-off ray is re-traced from scratch: its stack was emptied
             if (sp == 0) break;
             ref = stack[--sp];
         }
@@ -253,16 +350,10 @@ __device__ inline double warp_sum(double x)
     return x;
 }
 
-// Partial sums per block (FP64; integer counts are exact below 2^53):
-//   0..2 force, 3..5 torque (unscaled), 6 rays sent to / done by the FP64 path,
-//   7 segments traced, 8..12 hits per segment level, 13 nodes, 14 triangles,
-//   15 box tests.
-constexpr int kPart = 16;
-
-// Block-wide FP64 sum of v[0..15] into out[0..15] (fixed order).
-__device__ void block_sum16(const double *v, double *out)
+// Block-wide FP64 sum of v[0..kPart) into out[0..kPart) (fixed order).
+__device__ void block_sum(const double *v, double *out)
 {
-    __shared__ double red[kPart][kTraceThreads / 32];
+    __shared__ double red[kPart][32];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = 0; k < kPart; k++) {
         double x = warp_sum(v[k]);
@@ -277,30 +368,33 @@ __device__ void block_sum16(const double *v, double *out)
     __syncthreads();
 }
 
+// One warp per block, one 8 x 4 pixel tile per block.  Latency bound: 32 warps
+// per SM at the kernel's 64 registers (no spills).
 template <bool COUNT>
-__global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a)
+__global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
 {
-    __shared__ BlockCtx B;
-    __shared__ float2 mat[kMaxMats];
-    __shared__ int blk_flags;
-    int s = blockIdx.y;
-    if (threadIdx.x == 0) blk_flags = 0;
-    setup_block(B, mat, a, s);
+    __shared__ TraceCtx B;
+    const int s = blockIdx.y;
+    load_ctx(B, a, s);
+    __syncwarp();
     const int N = a.N;
-    int tiles_x = (N + kTile - 1) / kTile;
-    int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int i = tx * kTile + (w & 1) * 8 + (lane & 7);
-    int j = ty * kTile + (w >> 1) * 4 + (lane >> 3);
+    const int lane = threadIdx.x;
+    const int tiles_x = (N + 7) / 8;
+    const int i = (blockIdx.x % tiles_x) * 8 + (lane & 7);
+    const int j = (blockIdx.x / tiles_x) * 4 + (lane >> 3);
     double acc64[kPart];
     for (int k = 0; k < kPart; k++) acc64[k] = 0.0;
+    bool handoff = false;
+    int flags = 0;
+    const int ray = i * N + j;
     if (i < N && j < N) {
-        int ray = i * N + j;
         Ray32 r;
         for (int k = 0; k < 3; k++) {
-            r.o[k] = fmaf((float)i + 0.5f, B.fr.du[k], fmaf((float)j + 0.5f, B.fr.dv[k], B.fr.org[k]));
-            r.d[k] = B.fr.dir[k];
+            r.o[k] = fmaf((float)i + 0.5f, B.du[k], fmaf((float)j + 0.5f, B.dv[k], B.org[k]));
+            r.d[k] = B.dir[k];
         }
+        const float uc = fmaf((float)i + 0.5f, B.du32, B.umin32);
+        const float vc = fmaf((float)j + 0.5f, B.dv32, B.vmin32);
         float wgt = 1.0f;
         int skip = -1;
         float acc[6] = {0, 0, 0, 0, 0, 0};
@@ -308,14 +402,14 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a)
         for (int k = 0; k <= kMaxBounces; k++) hits[k] = -1;
         bool clean = true;
         int nseg_done = 0;
-        Counts cn = {0.f, 0.f, 0.f, 0};
-        float delta = B.delta0;
+        Counts cn = {0.f, 0.f, 0.f, {0.f, 0.f, 0.f, 0.f}, 0};
+        float delta = B.delta_p, tau = B.tau_p;
         for (int seg = 0; seg < a.nseg; seg++) {
             ray_setup(r);
             Best32 h;
-            float tlo = seg == 0 ? 0.0f : (float)B.fr.eps;
+            float tlo = seg == 0 ? 0.0f : B.eps32;
             nseg_done++;
-            if (!nearest32<COUNT>(B, r, tlo, skip, delta, h, cn)) { clean = false; break; }
+            if (!nearest32<COUNT>(B, r, seg == 0, uc, vc, tlo, skip, delta, tau, h, cn)) { clean = false; break; }
             if (h.part < 0) break;
             const float4 *tr = B.part[h.part].tri + (size_t)h.tl * 3;
             float4 a0 = __ldg(tr), a1 = __ldg(tr + 1), a2 = __ldg(tr + 2);
@@ -330,14 +424,17 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a)
             float dn = r.d[0] * n[0] + r.d[1] * n[1] + r.d[2] * n[2];
             int side = dn < 0.f ? 0 : 1;
             float sg = side ? -1.f : 1.f;
-            float2 m = mat[side ? (mt >> 16) : (mt & 0xffffu)];
+            float2 m = __ldg(B.mat32 + (side ? (mt >> 16) : (mt & 0xffffu)));
             float c = -sg * dn;
             // f = w [(1 - rho_s) d - 2 (rho_s c + rho_d / 3) n_f],  n_f = sg n
             float ka = wgt * (1.0f - m.x), kn = -2.0f * wgt * (m.x * c + m.y * (1.0f / 3.0f)) * sg;
             float F[3], hp[3], arm[3];
+            const float a0v[3] = {a0.x, a0.y, a0.z};
             for (int k = 0; k < 3; k++) {
                 F[k] = ka * r.d[k] + kn * n[k];
-                hp[k] = fmaf(h.t, r.d[k], r.o[k]);
+                // hit point from the barycentric weights on the hit triangle: its error
+                // is that of the test, not that of a long FP32 ray
+                hp[k] = fmaf(h.b1, e1[k], fmaf(h.b2, e2[k], a0v[k]));
                 arm[k] = hp[k] - B.cref32[k];
             }
             acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
@@ -351,27 +448,71 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a)
                 r.d[k] = r.d[k] - 2.0f * dn * n[k];
             }
             skip = orig;
-            delta = delta * 4.0f;
+            // next segment: world-frame test; the origin error grows with the previous bound
+            delta = B.delta_s + 2.0f * delta;
+            tau = 64.0f * delta + 32.0f * kU * (B.R + B.L);
         }
-        if (cn.flags) atomicOr(&blk_flags, cn.flags);
+        flags = cn.flags;
         if (clean) {
             for (int k = 0; k < 6; k++) acc64[k] = (double)acc[k];
             acc64[7] = (double)nseg_done;
             for (int k = 0; k < a.nseg; k++) acc64[8 + k] = hits[k] >= 0 ? 1.0 : 0.0;
             if (a.hits) {
-                int32_t *hp = a.hits + ((size_t)s * N * N + ray) * a.nseg;
-                for (int k = 0; k < a.nseg; k++) hp[k] = hits[k];
+                int32_t *hq = a.hits + ((size_t)s * N * N + ray) * a.nseg;
+                for (int k = 0; k < a.nseg; k++) hq[k] = hits[k];
             }
         } else {
-            atomicOr(a.amb + (size_t)s * ((N * N + 31) / 32) + (ray >> 5), 1u << (ray & 31));
+            handoff = true;
             acc64[6] = 1.0;
         }
-        if (COUNT) { acc64[13] = cn.nodes; acc64[14] = cn.tris; acc64[15] = cn.boxes; }
+        if (COUNT) {
+            acc64[13] = cn.nodes; acc64[14] = cn.tris; acc64[15] = cn.boxes;
+            for (int k = 0; k < 4; k++) acc64[16 + k] = cn.why[k];
+        }
     }
-    __shared__ double out[kPart];
-    block_sum16(acc64, out);
-    if (threadIdx.x < kPart) a.partials[((size_t)s * a.n_blocks_x + blockIdx.x) * kPart + threadIdx.x] = out[threadIdx.x];
-    if (threadIdx.x == 0 && blk_flags) atomicOr(&a.pose[s].flags, blk_flags);
+    // tile-ordered list of the rays handed to the FP64 path
+    const size_t tile = (size_t)s * a.n_blocks_x + blockIdx.x;
+    unsigned bal = __ballot_sync(0xffffffffu, handoff);
+    if (handoff) a.amb_list[tile * kTileRays + __popc(bal & ((1u << lane) - 1u))] = ray;
+    // tile sum (fixed shuffle order), one partial per tile
+    for (int k = 0; k < kPart; k++) {
+        double x = warp_sum(acc64[k]);
+        if (lane == 0) a.partials[tile * kPart + k] = x;
+    }
+    int fl = __reduce_or_sync(0xffffffffu, flags);
+    if (lane == 0) {
+        a.amb_count[tile] = __popc(bal);
+        if (fl) atomicOr(&a.pose[s].flags, fl);
+    }
+}
+
+// Exclusive scan of the per-tile hand-off counts of one slot (one block per
+// slot): each thread scans a contiguous chunk, the chunk totals are scanned
+// across the block, then added back.
+__global__ void __launch_bounds__(1024) k_amb_scan(TraceArgs a)
+{
+    __shared__ int tot[1024];
+    const int s = blockIdx.x, n = a.n_blocks_x, t = threadIdx.x;
+    const int *cnt = a.amb_count + (size_t)s * n;
+    int *off = a.amb_off + (size_t)s * (n + 1);
+    const int chunk = (n + 1023) / 1024;
+    const int b0 = min(t * chunk, n), b1 = min(b0 + chunk, n);
+    int sum = 0;
+    for (int b = b0; b < b1; b++) sum += cnt[b];
+    tot[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int x = t >= o ? tot[t - o] : 0;
+        __syncthreads();
+        tot[t] += x;
+        __syncthreads();
+    }
+    int run = tot[t] - sum;
+    for (int b = b0; b < b1; b++) {
+        off[b] = run;
+        run += cnt[b];
+    }
+    if (t == 1023) off[n] = tot[1023];
 }
 
 // ------------------------------------------------------------- FP64 path
@@ -395,20 +536,47 @@ __device__ void ray64_setup(Ray64 &r)
     r.Sz = 1.0 / dz;
 }
 
-__device__ void tri_v64(const BlockCtx &B, const MeshDev *m, int p, int tl, double *v)
+__device__ void tri_v64(const TraceCtx &B, int p, int tl, double *v)
 {
     const PartView &pv = B.part[p];
     int t = pv.tri_begin + tl;
     for (int c = 0; c < 3; c++) {
-        int vi = m->tri_vidx[3 * t + c] - pv.vert_begin;
+        int vi = B.tri_vidx[3 * t + c] - pv.vert_begin;
         for (int k = 0; k < 3; k++) v[3 * c + k] = pv.v64[3 * vi + k];
     }
 }
 
+// True when the FP32 world-frame test shows the triangle certainly misses the
+// ray: some edge function certainly negative and another certainly positive,
+// with the per-triangle error bound of the secondary-ray test.
+__device__ __forceinline__ bool outside32(const Ray32 &r, float4 a, float4 b, float4 c, float delta)
+{
+    const float u4 = 4.0f * kU;
+    float A0 = a.x - r.o[0], A1 = a.y - r.o[1], A2 = a.z - r.o[2];
+    float B0 = b.x - r.o[0], B1 = b.y - r.o[1], B2 = b.z - r.o[2];
+    float C0 = c.x - r.o[0], C1 = c.y - r.o[1], C2 = c.z - r.o[2];
+    float Akz = pick(A0, A1, A2, r.kz), Bkz = pick(B0, B1, B2, r.kz), Ckz = pick(C0, C1, C2, r.kz);
+    float Ax = fmaf(-r.Sx, Akz, pick(A0, A1, A2, r.kx)), Ay = fmaf(-r.Sy, Akz, pick(A0, A1, A2, r.ky));
+    float Bx = fmaf(-r.Sx, Bkz, pick(B0, B1, B2, r.kx)), By = fmaf(-r.Sy, Bkz, pick(B0, B1, B2, r.ky));
+    float Cx = fmaf(-r.Sx, Ckz, pick(C0, C1, C2, r.kx)), Cy = fmaf(-r.Sy, Ckz, pick(C0, C1, C2, r.ky));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    float dz = fmaxf(fmaxf(fabsf(Akz), fabsf(Bkz)), fabsf(Ckz)) + fmaxf(fmaxf(fabsf(Ax), fabsf(Bx)), fabsf(Cx)) +
+               fmaxf(fmaxf(fabsf(Ay), fabsf(By)), fabsf(Cy));
+    float dc = fmaf(16.0f * kU, dz, delta);
+    float eU = dc * (fabsf(Bx) + fabsf(By) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Cx * By) + fabsf(Cy * Bx));
+    float eV = dc * (fabsf(Ax) + fabsf(Ay) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Ax * Cy) + fabsf(Ay * Cx));
+    float eW = dc * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + u4 * (fabsf(Bx * Ay) + fabsf(By * Ax));
+    bool neg = (U < -eU) || (V < -eV) || (W < -eW);
+    bool pos = (U > eU) || (V > eV) || (W > eW);
+    return neg && pos;
+}
+
 // Nearest hit in FP64 (same BVH; boxes tested with the rounded ray, whose
 // deviation from the FP64 ray is far below the box padding).
-__device__ void nearest64(const BlockCtx &B, const MeshDev *m, const Ray64 &r, double tlo, int skip, double &bt,
-                          int &bpart, int &btl, int &borig, int &flags)
+__device__ void nearest64(const TraceCtx &B, const Ray64 &r, double tlo, int skip, double &bt, int &bpart, int &btl,
+                          int &borig, int &flags)
 {
     bt = INFINITY;
     bpart = -1; btl = -1; borig = 0x7fffffff;
@@ -416,6 +584,10 @@ __device__ void nearest64(const BlockCtx &B, const MeshDev *m, const Ray64 &r, d
     for (int k = 0; k < 3; k++) { q.o[k] = (float)r.o[k]; q.d[k] = (float)r.d[k]; }
     ray_setup(q);
     const float slack = 4.0f * B.pad;
+    // bound on the coordinate error of the rounded ray and FP32 vertices, for the
+    // FP32 pre-test that skips triangles the ray certainly misses
+    float omax = fmaxf(fmaxf(fabsf(q.o[0]), fabsf(q.o[1])), fabsf(q.o[2]));
+    const float dq = 2.0f * kU * (omax + B.R);
     int stack[kStack];
     for (int p = 0; p < B.n_parts; p++) {
         const PartView &pv = B.part[p];
@@ -443,10 +615,12 @@ __device__ void nearest64(const BlockCtx &B, const MeshDev *m, const Ray64 &r, d
                 else if (h1) { ref = c.y; continue; }
             } else {
                 int tl = ~ref;
-                int orig = __float_as_int(__ldg(pv.tri + (size_t)tl * 3).w);
-                if (orig != skip) {
+                const float4 *tr = pv.tri + (size_t)tl * 3;
+                float4 fa = __ldg(tr), fb = __ldg(tr + 1), fc = __ldg(tr + 2);
+                int orig = __float_as_int(fa.w);
+                if (orig != skip && !outside32(q, fa, fb, fc, dq)) {
                     double v[9];
-                    tri_v64(B, m, p, tl, v);
+                    tri_v64(B, p, tl, v);
                     double A[3], Bv[3], C[3];
                     for (int k = 0; k < 3; k++) { A[k] = v[k] - r.o[k]; Bv[k] = v[3 + k] - r.o[k]; C[k] = v[6 + k] - r.o[k]; }
                     double Akz = pickd(A[0], A[1], A[2], r.kz), Bkz = pickd(Bv[0], Bv[1], Bv[2], r.kz),
@@ -474,120 +648,130 @@ __device__ void nearest64(const BlockCtx &B, const MeshDev *m, const Ray64 &r, d
     }
 }
 
-__global__ void __launch_bounds__(kTraceThreads) k_refine(TraceArgs a)
+// Re-trace of one handed-off ray, FP64 from the pixel definition; adds to acc.
+__device__ void refine_ray(const TraceCtx &B, const TraceArgs &a, int s, int ray, double *acc, int &flags)
 {
-    __shared__ BlockCtx B;
-    __shared__ float2 mat[kMaxMats];
-    __shared__ int any, blk_flags;
-    int s = blockIdx.y;
     const int N = a.N;
-    size_t R = (size_t)N * N;
-    size_t words = (R + 31) / 32;
-    uint32_t *amb = a.amb + (size_t)s * words;
-    size_t ray0 = (size_t)blockIdx.x * blockDim.x;
-    if (threadIdx.x == 0) { any = 0; blk_flags = 0; }
-    __syncthreads();
-    size_t ray = ray0 + threadIdx.x;
-    bool mine = false;
-    if (ray < R) mine = (amb[ray >> 5] >> (ray & 31)) & 1u;
-    if (mine) any = 1;
-    __syncthreads();
+    int i = ray / N, j = ray % N;
+    Ray64 r;
+    double uc = B.umin + ((double)i + 0.5) * B.Du / N;
+    double vc = B.vmin + ((double)j + 0.5) * B.Dv / N;
+    double w0 = B.wmin - kStandoff;
+    for (int k = 0; k < 3; k++) { r.o[k] = uc * B.u[k] + vc * B.v[k] + w0 * B.d[k]; r.d[k] = B.d[k]; }
+    double wgt = 1.0;
+    int skip = -1, nseg_done = 0;
+    int32_t *hp = a.hits ? a.hits + ((size_t)s * N * N + ray) * a.nseg : nullptr;
+    if (hp) for (int k = 0; k < a.nseg; k++) hp[k] = -1;
+    for (int seg = 0; seg < a.nseg; seg++) {
+        ray64_setup(r);
+        double t;
+        int hpart, htl, horig;
+        nseg_done++;
+        nearest64(B, r, seg == 0 ? 0.0 : B.eps, skip, t, hpart, htl, horig, flags);
+        if (hpart < 0) break;
+        if (hp) hp[seg] = horig;
+        acc[8 + seg] += 1.0;
+        double v[9];
+        tri_v64(B, hpart, htl, v);
+        double e1[3], e2[3], n[3];
+        for (int k = 0; k < 3; k++) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int k = 0; k < 3; k++) n[k] /= nl;
+        double dn = r.d[0] * n[0] + r.d[1] * n[1] + r.d[2] * n[2];
+        int side = dn < 0.0 ? 0 : 1;
+        double sg = side ? -1.0 : 1.0;
+        unsigned mt = B.tri_mat[B.part[hpart].tri_begin + htl];
+        int mi = side ? (int)(mt >> 16) : (int)(mt & 0xffffu);
+        double rs = B.mat64[2 * mi], rd = B.mat64[2 * mi + 1];
+        double c = -sg * dn;
+        double F[3], x[3];
+        for (int k = 0; k < 3; k++) F[k] = wgt * ((1.0 - rs) * r.d[k] - 2.0 * (rs * c + rd / 3.0) * sg * n[k]);
+        for (int k = 0; k < 3; k++) x[k] = r.o[k] + t * r.d[k];
+        double arm[3] = {x[0] - B.c_ref[0], x[1] - B.c_ref[1], x[2] - B.c_ref[2]};
+        acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
+        acc[3] += arm[1] * F[2] - arm[2] * F[1];
+        acc[4] += arm[2] * F[0] - arm[0] * F[2];
+        acc[5] += arm[0] * F[1] - arm[1] * F[0];
+        wgt *= rs;
+        if (seg + 1 >= a.nseg || wgt == 0.0) break;
+        for (int k = 0; k < 3; k++) { r.d[k] = r.d[k] - 2.0 * dn * n[k]; r.o[k] = x[k]; }
+        skip = horig;
+    }
+    acc[6] += 1.0;
+    acc[7] += (double)nseg_done;
+}
+
+// Threads walk the dense hand-off list of their slot in a fixed order.
+__global__ void __launch_bounds__(256) k_refine(TraceArgs a)
+{
+    __shared__ TraceCtx B;
+    __shared__ int blk_flags;
+    const int s = blockIdx.y;
+    const int *off = a.amb_off + (size_t)s * (a.n_blocks_x + 1);
+    const int total = off[a.n_blocks_x];
     double acc[kPart];
     for (int k = 0; k < kPart; k++) acc[k] = 0.0;
-    if (any) {
-        setup_block(B, mat, a, s);
-        const MeshDev *m = a.mesh_d;
-        if (mine) {
-            int i = (int)(ray / N), j = (int)(ray % N);
-            Ray64 r;
-            double uc = B.fr.umin + ((double)i + 0.5) * B.fr.Du / N;
-            double vc = B.fr.vmin + ((double)j + 0.5) * B.fr.Dv / N;
-            double w0 = B.fr.wmin - kStandoff;
-            for (int k = 0; k < 3; k++) { r.o[k] = uc * B.u[k] + vc * B.v[k] + w0 * B.d[k]; r.d[k] = B.d[k]; }
-            double wgt = 1.0;
-            int skip = -1, nseg_done = 0, flags = 0;
-            int32_t *hp = a.hits ? a.hits + ((size_t)s * R + ray) * a.nseg : nullptr;
-            if (hp) for (int k = 0; k < a.nseg; k++) hp[k] = -1;
-            for (int seg = 0; seg < a.nseg; seg++) {
-                ray64_setup(r);
-                double t;
-                int hpart, htl, horig;
-                nseg_done++;
-                nearest64(B, m, r, seg == 0 ? 0.0 : B.fr.eps, skip, t, hpart, htl, horig, flags);
-                if (hpart < 0) break;
-                if (hp) hp[seg] = horig;
-                acc[8 + seg] += 1.0;
-                double v[9];
-                tri_v64(B, m, hpart, htl, v);
-                double e1[3], e2[3], n[3];
-                for (int k = 0; k < 3; k++) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
-                n[0] = e1[1] * e2[2] - e1[2] * e2[1];
-                n[1] = e1[2] * e2[0] - e1[0] * e2[2];
-                n[2] = e1[0] * e2[1] - e1[1] * e2[0];
-                double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-                for (int k = 0; k < 3; k++) n[k] /= nl;
-                double dn = r.d[0] * n[0] + r.d[1] * n[1] + r.d[2] * n[2];
-                int side = dn < 0.0 ? 0 : 1;
-                double sg = side ? -1.0 : 1.0;
-                unsigned mt = m->tri_mat[B.part[hpart].tri_begin + htl];
-                int mi = side ? (int)(mt >> 16) : (int)(mt & 0xffffu);
-                double rs = m->mat64[2 * mi], rd = m->mat64[2 * mi + 1];
-                double c = -sg * dn;
-                double F[3], x[3];
-                for (int k = 0; k < 3; k++) F[k] = wgt * ((1.0 - rs) * r.d[k] - 2.0 * (rs * c + rd / 3.0) * sg * n[k]);
-                for (int k = 0; k < 3; k++) x[k] = r.o[k] + t * r.d[k];
-                double arm[3] = {x[0] - B.c_ref[0], x[1] - B.c_ref[1], x[2] - B.c_ref[2]};
-                acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
-                acc[3] += arm[1] * F[2] - arm[2] * F[1];
-                acc[4] += arm[2] * F[0] - arm[0] * F[2];
-                acc[5] += arm[0] * F[1] - arm[1] * F[0];
-                wgt *= rs;
-                if (seg + 1 >= a.nseg || wgt == 0.0) break;
-                for (int k = 0; k < 3; k++) { r.d[k] = r.d[k] - 2.0 * dn * n[k]; r.o[k] = x[k]; }
-                skip = horig;
+    if ((int)(blockIdx.x * blockDim.x) < total) {
+        if (threadIdx.x == 0) blk_flags = 0;
+        load_ctx(B, a, s);
+        __syncthreads();
+        int flags = 0;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+            // tile holding item g: largest b with off[b] <= g
+            int lo = 0, hi = a.n_blocks_x - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (off[mid] <= g) lo = mid; else hi = mid - 1;
             }
-            acc[6] = 1.0;
-            acc[7] = (double)nseg_done;
-            if (flags) atomicOr(&blk_flags, flags);
+            int ray = a.amb_list[((size_t)s * a.n_blocks_x + lo) * kTileRays + (g - off[lo])];
+            refine_ray(B, a, s, ray, acc, flags);
         }
-    }
-    __syncthreads();
-    // clear this block's mask words for the next use of the slot
-    if (threadIdx.x < blockDim.x / 32) {
-        size_t wi = (ray0 >> 5) + threadIdx.x;
-        if (wi < words) amb[wi] = 0u;
+        if (flags) atomicOr(&blk_flags, flags);
+        __syncthreads();
+        if (threadIdx.x == 0 && blk_flags) atomicOr(&a.pose[s].flags, blk_flags);
     }
     __shared__ double out[kPart];
-    block_sum16(acc, out);
+    block_sum(acc, out);
     if (threadIdx.x < kPart)
         a.partials_ref[((size_t)s * a.n_blocks_ref + blockIdx.x) * kPart + threadIdx.x] = out[threadIdx.x];
-    if (threadIdx.x == 0 && blk_flags) atomicOr(&a.pose[s].flags, blk_flags);
 }
 
 // ------------------------------------------------------------- reduce
-// One block per slot: fixed-order sums of the trace and refine partials.
-// stats_accum[16]: 0 evals, 1 rays, 2 refined rays, 3 segments,
-// 4..8 hits per segment, 9 nodes, 10 triangles, 11 box tests.
+// First level: block b of slot s sums tiles [b * chunk, (b + 1) * chunk).
+__global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
+{
+    const int s = blockIdx.y, b = blockIdx.x;
+    const int chunk = (a.n_blocks_x + kRed1 - 1) / kRed1;
+    const int t0 = b * chunk, t1 = min(t0 + chunk, a.n_blocks_x);
+    double acc[kPart];
+    for (int k = 0; k < kPart; k++) acc[k] = 0.0;
+    for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x)
+        for (int k = 0; k < kPart; k++) acc[k] += a.partials[((size_t)s * a.n_blocks_x + t) * kPart + k];
+    __shared__ double out[kPart];
+    block_sum(acc, out);
+    if (threadIdx.x < kPart) a.partials1[((size_t)s * kRed1 + b) * kPart + threadIdx.x] = out[threadIdx.x];
+}
+
+// One block per slot: the first-level sums and the refine partials.
+// stats_accum[16]: 0 evals, 1 rays, 2 refined rays, 3 segments, 4..8 hits per
+// segment, 9 nodes, 10 triangles, 11 box tests, 12..15 hand-offs by cause.
 __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *force, double *torque, int *err_flags,
                                                 unsigned long long *stats_accum)
 {
-    int s = blockIdx.x;
-    __shared__ double red[kPart][256];
-    double acc[kPart], accr[kPart];
-    for (int k = 0; k < kPart; k++) { acc[k] = 0.0; accr[k] = 0.0; }
-    for (int b = threadIdx.x; b < a.n_blocks_x; b += blockDim.x)
-        for (int k = 0; k < kPart; k++) acc[k] += a.partials[((size_t)s * a.n_blocks_x + b) * kPart + k];
+    const int s = blockIdx.x;
+    double acc[kPart];
+    for (int k = 0; k < kPart; k++) acc[k] = 0.0;
+    // slot 6: the trace side counts hand-offs, the refine side the rays it did
+    for (int b = threadIdx.x; b < kRed1; b += blockDim.x)
+        for (int k = 0; k < kPart; k++)
+            if (k != 6) acc[k] += a.partials1[((size_t)s * kRed1 + b) * kPart + k];
     for (int b = threadIdx.x; b < a.n_blocks_ref; b += blockDim.x)
-        for (int k = 0; k < kPart; k++) accr[k] += a.partials_ref[((size_t)s * a.n_blocks_ref + b) * kPart + k];
-    // refined rays: their count is in the refine partials; the trace partial
-    // counted the same rays as sent, so take the refine side for slot 6
-    for (int k = 0; k < kPart; k++) red[k][threadIdx.x] = (k == 6) ? accr[k] : acc[k] + accr[k];
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h)
-            for (int k = 0; k < kPart; k++) red[k][threadIdx.x] += red[k][threadIdx.x + h];
-        __syncthreads();
-    }
+        for (int k = 0; k < kPart; k++) acc[k] += a.partials_ref[((size_t)s * a.n_blocks_ref + b) * kPart + k];
+    __shared__ double red[kPart];
+    block_sum(acc, red);
     if (threadIdx.x == 0) {
         const SlotPose &P = a.pose[s];
         double Du = ord_to_dbl(P.wmax_bits[0]) - ord_to_dbl(P.wmin_bits[0]);
@@ -595,17 +779,18 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
         double sc = P.scale * (Du * Dv) / ((double)a.N * (double)a.N);
         int e = eval0 + s;
         for (int k = 0; k < 3; k++) {
-            force[3 * e + k] = red[k][0] * sc;
-            torque[3 * e + k] = red[3 + k][0] * sc;
+            force[3 * e + k] = red[k] * sc;
+            torque[3 * e + k] = red[3 + k] * sc;
         }
         if (P.flags) atomicOr(err_flags, P.flags);
         if (stats_accum) {
             atomicAdd(&stats_accum[0], 1ull);
             atomicAdd(&stats_accum[1], (unsigned long long)a.N * (unsigned long long)a.N);
-            atomicAdd(&stats_accum[2], (unsigned long long)red[6][0]);
-            atomicAdd(&stats_accum[3], (unsigned long long)red[7][0]);
-            for (int k = 0; k < 5; k++) atomicAdd(&stats_accum[4 + k], (unsigned long long)red[8 + k][0]);
-            for (int k = 0; k < 3; k++) atomicAdd(&stats_accum[9 + k], (unsigned long long)red[13 + k][0]);
+            atomicAdd(&stats_accum[2], (unsigned long long)red[6]);
+            atomicAdd(&stats_accum[3], (unsigned long long)red[7]);
+            for (int k = 0; k < 5; k++) atomicAdd(&stats_accum[4 + k], (unsigned long long)red[8 + k]);
+            for (int k = 0; k < 3; k++) atomicAdd(&stats_accum[9 + k], (unsigned long long)red[13 + k]);
+            for (int k = 0; k < 4; k++) atomicAdd(&stats_accum[12 + k], (unsigned long long)red[16 + k]);
         }
     }
 }
@@ -613,22 +798,25 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
 // ------------------------------------------------------------ launchers
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
 {
+    k_frame<<<S, 32, 0, st>>>(a);
     dim3 grid(a.n_blocks_x, S);
-    if (a.count) k_trace<true><<<grid, kTraceThreads, 0, st>>>(a);
-    else k_trace<false><<<grid, kTraceThreads, 0, st>>>(a);
+    if (a.count) k_trace<true><<<grid, kTileRays, 0, st>>>(a);
+    else k_trace<false><<<grid, kTileRays, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine(const TraceArgs &a, int S, cudaStream_t st)
 {
+    k_amb_scan<<<S, 1024, 0, st>>>(a);
     dim3 grid(a.n_blocks_ref, S);
-    k_refine<<<grid, kTraceThreads, 0, st>>>(a);
+    k_refine<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
                           unsigned long long *stats_accum, cudaStream_t st)
 {
+    k_reduce1<<<dim3(kRed1, S), 256, 0, st>>>(a);
     k_reduce<<<S, 256, 0, st>>>(a, eval0, force, torque, err_flags, stats_accum);
     return cudaGetLastError();
 }

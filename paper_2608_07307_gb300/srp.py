@@ -53,7 +53,8 @@ class EvalParams(C.Structure):
 class EvalStats(C.Structure):
     _fields_ = [("evals", C.c_int64), ("rays", C.c_int64), ("segments", C.c_int64),
                 ("hits", C.c_int64 * (MAX_BOUNCES + 1)), ("refined", C.c_int64), ("nodes_visited", C.c_int64),
-                ("tris_tested", C.c_int64), ("box_tests", C.c_int64), ("launches", C.c_int64),
+                ("tris_tested", C.c_int64), ("box_tests", C.c_int64), ("handoff_cause", C.c_int64 * 4),
+                ("launches", C.c_int64),
                 ("trace_launches", C.c_int64), ("ms_geometry", C.c_double), ("ms_trace", C.c_double),
                 ("ms_refine", C.c_double), ("ms_reduce", C.c_double), ("ms_transfer", C.c_double)]
 
@@ -246,5 +247,5 @@ class Context:
         self._check(self.lib.srp_eval_stats_get(self.h, C.byref(s)))
         return dict(evals=s.evals, rays=s.rays, segments=s.segments, hits=list(s.hits), refined=s.refined,
                     nodes_visited=s.nodes_visited, tris_tested=s.tris_tested, box_tests=s.box_tests,
-                    launches=s.launches, trace_launches=s.trace_launches, ms_geometry=s.ms_geometry,
+                    handoff_cause=list(s.handoff_cause), launches=s.launches, trace_launches=s.trace_launches, ms_geometry=s.ms_geometry,
                     ms_trace=s.ms_trace, ms_refine=s.ms_refine, ms_reduce=s.ms_reduce, ms_transfer=s.ms_transfer)
