@@ -194,6 +194,71 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
 /* Counters of the last srp_eval_batch on ctx. */
 srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out);
 
+/* ------------------------------------------------------------ propagation */
+#define SRP_RKF78 0           /* Fehlberg 7(8) embedded pair, adaptive step      */
+#define SRP_RK4 1             /* classical RK4, fixed step h0                    */
+#define SRP_CENTRAL_EARTH 0
+#define SRP_CENTRAL_SUN 1
+#define SRP_ATT_LVLH 0        /* body z to nadir, body y along minus the orbit normal */
+#define SRP_ATT_INERTIAL 1    /* fixed quaternion q                               */
+
+typedef struct {
+    int32_t method;        /* SRP_RKF78 or SRP_RK4                                        */
+    int32_t central;       /* SRP_CENTRAL_EARTH or SRP_CENTRAL_SUN                         */
+    int32_t j2;            /* Earth J2, pole along inertial z (Earth-centred only)         */
+    int32_t sun3;          /* Sun as a third body (Earth-centred only)                     */
+    int32_t srp;           /* ray-traced SRP acceleration on (1) or off (0)                */
+    int32_t attitude;      /* SRP_ATT_LVLH or SRP_ATT_INERTIAL                             */
+    double q[4];           /* body -> inertial quaternion (scalar first), SRP_ATT_INERTIAL */
+    double epoch_mjd_tt;   /* epoch of t = 0, MJD in TT (Sun ephemeris)                     */
+    double rtol;           /* RKF7(8) relative tolerance                                   */
+    double atol_pos;       /* absolute tolerance on position components (m)                 */
+    double atol_vel;       /* absolute tolerance on velocity components (m/s)               */
+    double h0;             /* first step (RKF7(8)) or fixed step (RK4), s                   */
+    double h_min;          /* step-size floor (RKF7(8)); below it: SRP_ERR_STEP              */
+    double h_max;          /* step-size ceiling (RKF7(8)); 0 = none                          */
+    int64_t max_steps;     /* accepted + rejected step budget per trajectory                */
+    int32_t poll;          /* steps launched between completion checks (0 = 16)             */
+    int32_t reserved;
+    srp_eval_params eval;  /* ray grid, bounces, P0, panel mode of every SRP evaluation     */
+    const double *h_replay; /* NULL, or [n_traj][n_replay] step sizes (host or device): RKF7(8)
+                               then takes exactly these steps, all accepted, no error control,
+                               and ends after n_replay steps (t1 is ignored); this reproduces
+                               another integrator's accepted steps                            */
+    int64_t n_replay;
+} srp_prop_params;
+
+typedef struct {
+    int64_t steps, rejects, evals; /* accepted steps, rejected steps, SRP evaluations          */
+    double t;                      /* time reached (s)                                          */
+    int32_t status;                /* SRP_OK or SRP_ERR_STEP                                    */
+    int32_t reserved;
+} srp_prop_stats;
+
+/*
+ * Propagate n_traj trajectories of one mesh's spacecraft (Sec. 3, Eqs. 1-3):
+ * y' = (v, a_g + a_SRP), a_SRP = R(q) F_body / mass with F_body the ray-traced
+ * force of srp_eval_batch for the Sun direction in the body frame (zero inside
+ * a cylindrical Earth shadow), integrated with RKF7(8) (adaptive: error norm
+ * max_i |e_i| / (atol_i + rtol max(|y_i|, |y_new_i|)), accepted when <= 1,
+ * next h = h clamp(0.9 err^(-1/8), 0.2, 5), the 7th-order solution kept) or RK4
+ * (fixed step).  Every trajectory evaluates the SRP force in every stage; the
+ * whole step (stage states, Sun directions, the SRP pipeline for all
+ * trajectories, accelerations, step control) is captured once in a CUDA graph
+ * and relaunched until every trajectory reached its end time.
+ *   y0     [n_traj][6]  initial position (m) and velocity (m/s), inertial
+ *   t0_t1  [n_traj][2]  start and end time (s after the epoch)
+ *   y1     [n_traj][6]  out: state at t1 (or where the trajectory stopped)
+ *   stats  [n_traj]     out (may be NULL)
+ *   h_log  [n_traj][h_cap] out (may be NULL): accepted step sizes, in order
+ * Errors: SRP_ERR_ARG, SRP_ERR_STATE (bad mesh id), SRP_ERR_STEP (some
+ * trajectory hit h_min or max_steps; its stats say which), SRP_ERR_STACK,
+ * SRP_ERR_CUDA.
+ */
+srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *params, int32_t n_traj,
+                         const double *y0, const double *t0_t1, double *y1, srp_prop_stats *stats, double *h_log,
+                         int64_t h_cap);
+
 /* Limits of srp_eval_noalloc. */
 #define SRP_NOALLOC_MAX_N 1024    /* rays per window side                     */
 #define SRP_NOALLOC_MAX_TRIS 4096 /* triangles (every ray tests every one)     */

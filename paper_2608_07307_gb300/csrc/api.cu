@@ -14,6 +14,9 @@ using namespace srp;
 
 namespace {
 
+// Evaluation chunks rotate over this many lane streams.
+constexpr int kLanes = 3;
+
 struct Mesh {
     MeshDev h{};                 // host copy holding device pointers
     MeshDev *d = nullptr;        // device copy
@@ -59,8 +62,18 @@ struct srp_ctx {
     unsigned long long *stats = nullptr;
     srp_eval_stats last{};
     std::vector<cudaEvent_t> events;  // pool for SRP_EVAL_TIMING
-    cudaStream_t lane[2] = {nullptr, nullptr};  // pipeline lanes (forked from / joined to `stream`)
-    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    // propagation
+    double *prop_io = nullptr;
+    size_t prop_io_cap = 0;
+    PropState *prop_state = nullptr;
+    size_t prop_state_cap = 0;
+    double *prop_hlog = nullptr;
+    size_t prop_hlog_cap = 0;
+    double *prop_replay = nullptr;
+    size_t prop_replay_cap = 0;
+    int *prop_done = nullptr;
+    cudaStream_t lane[kLanes] = {};  // pipeline lanes (forked from / joined to `stream`)
+    cudaEvent_t ev_fork = nullptr, ev_join[kLanes] = {};
 };
 
 namespace {
@@ -168,6 +181,186 @@ Mesh *get_mesh(srp_ctx *ctx, int32_t id)
     return ctx->meshes[id];
 }
 
+
+// ------------------------------------------------------------ evaluation
+srp_status check_eval_params(srp_ctx *ctx, const srp_eval_params *prm)
+{
+    if (!prm) return fail(ctx, SRP_ERR_ARG, "null params");
+    if (prm->N < 1 || prm->N > SRP_MAX_N) return fail(ctx, SRP_ERR_ARG, "N = %d outside [1, %d]", prm->N, SRP_MAX_N);
+    if (prm->bounces < 0 || prm->bounces > kMaxBounces) return fail(ctx, SRP_ERR_ARG, "bounces = %d", prm->bounces);
+    if (!(prm->P0 >= 0.0) || !(prm->eps_rel >= 0.0)) return fail(ctx, SRP_ERR_ARG, "P0 and eps_rel must be >= 0");
+    if (prm->panel_mode < 0 || prm->panel_mode > 2) return fail(ctx, SRP_ERR_ARG, "bad panel_mode");
+    return SRP_OK;
+}
+
+// Launch shape of a batch of n evaluations.
+struct EvalPlan {
+    int N, nseg, S, nchunks, lanes, nbx, nbr;
+    size_t R, SL;
+};
+
+// Phase timing with CUDA events recorded on the stream each phase runs on.
+struct Timing {
+    srp_ctx *ctx;
+    bool on;
+    int n = 0;
+    std::vector<std::pair<int, int>> spans[5];  // geometry, trace, refine, reduce, transfer
+    Timing(srp_ctx *c, bool o) : ctx(c), on(o) {}
+    int mark(cudaStream_t s)
+    {
+        if (!on) return -1;
+        if (n >= (int)ctx->events.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            ctx->events.push_back(e);
+        }
+        cudaEventRecord(ctx->events[n], s);
+        return n++;
+    }
+    void span(int phase, int a, int b) { if (on) spans[phase].push_back({a, b}); }
+    void collect(srp_eval_stats &L)
+    {
+        if (!on) return;
+        double *ms[5] = {&L.ms_geometry, &L.ms_trace, &L.ms_refine, &L.ms_reduce, &L.ms_transfer};
+        for (int p = 0; p < 5; p++)
+            for (auto &sp : spans[p]) {
+                float t = 0.f;
+                if (sp.first >= 0 && sp.second >= 0 &&
+                    cudaEventElapsedTime(&t, ctx->events[sp.first], ctx->events[sp.second]) == cudaSuccess)
+                    *ms[p] += t;
+            }
+    }
+};
+
+void fill_stats(srp_eval_stats &L, const unsigned long long *stats)
+{
+    L.evals = (int64_t)stats[0];
+    L.rays = (int64_t)stats[1];
+    L.refined = (int64_t)stats[2];
+    L.segments = (int64_t)stats[3];
+    for (int k = 0; k <= kMaxBounces; k++) L.hits[k] = (int64_t)stats[4 + k];
+    L.nodes_visited = (int64_t)stats[9];
+    L.tris_tested = (int64_t)stats[10];
+    L.box_tests = (int64_t)stats[11];
+    for (int k = 0; k < 4; k++) L.handoff_cause[k] = (int64_t)stats[12 + k];
+}
+
+// Size the batch and grow every buffer it needs (may allocate; never inside a capture).
+srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, bool want_hits, EvalPlan &pl)
+{
+    pl.N = prm->N;
+    pl.nseg = prm->bounces + 1;
+    pl.R = (size_t)pl.N * pl.N;
+    // concurrent evaluations: enough rays in flight to fill the GPU several times
+    pl.S = (int)std::min<size_t>(std::max<size_t>((size_t)(1u << 21) / pl.R, 1), 64);
+    pl.S = std::min(pl.S, std::max(n, 1));
+    // chunks of S evaluations alternate between lane streams with their own
+    // slots and buffers, so the short, latency-bound tail of one chunk (FP64
+    // re-trace, reduction) overlaps the traversal of the next
+    pl.nchunks = (n + pl.S - 1) / pl.S;
+    pl.lanes = std::max(1, std::min(pl.nchunks, kLanes));
+    srp_status rc = ensure_slots(ctx, m, pl.S * pl.lanes);
+    if (rc) return rc;
+    // trace tiles of 8 x 4 pixels, one warp each
+    pl.nbx = ((pl.N + 7) / 8) * ((pl.N + 3) / 4);
+    // FP64 re-trace grid: a few blocks per SM, walking the compacted hand-off list
+    pl.nbr = std::max(1, std::min(pl.nbx, 1216 / pl.S));
+    pl.SL = (size_t)pl.S * pl.lanes;
+    const size_t SL = pl.SL;
+    CK(ctx, grow(&ctx->pose, &ctx->pose_cap, SL, false));
+    CK(ctx, grow(&ctx->partials, &ctx->partials_cap, SL * pl.nbx * kPart, false));
+    CK(ctx, grow(&ctx->partials_ref, &ctx->partials_ref_cap, SL * pl.nbr * kPart, false));
+    CK(ctx, grow(&ctx->amb_list, &ctx->amb_list_cap, SL * pl.nbx * kTileRays, false));
+    CK(ctx, grow(&ctx->partials1, &ctx->partials1_cap, SL * kRed1 * kPart, false));
+    CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
+    CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * pl.nbx, false));
+    CK(ctx, grow(&ctx->amb_off, &ctx->amb_off_cap, SL * (pl.nbx + 1), false));
+    if (want_hits) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
+    return SRP_OK;
+}
+
+// Queue the evaluations on the lane streams, forked from and joined back into
+// the context stream.  Launches and event records only: no allocation, no
+// synchronisation, so a stream capture can record it.
+srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const EvalPlan &pl, int n,
+                        const double *d_sun, const double *d_dist, double *d_f, double *d_t, int32_t *hit_tri,
+                        bool h_dev, Timing &tm, int64_t &launches, int64_t &trace_launches)
+{
+    cudaStream_t st = ctx->stream;
+    const int S = pl.S, nbx = pl.nbx, nbr = pl.nbr, nseg = pl.nseg;
+    const size_t R = pl.R;
+    CK(ctx, cudaEventRecord(ctx->ev_fork, st));
+    for (int b = 0; b < pl.lanes; b++) CK(ctx, cudaStreamWaitEvent(ctx->lane[b], ctx->ev_fork, 0));
+    for (int c = 0; c < pl.nchunks; c++) {
+        const int e0 = c * S, b = c % pl.lanes;
+        const int Sc = std::min(S, n - e0);
+        cudaStream_t ls = ctx->lane[b];
+        // lane b's slots and buffers
+        const MeshDev &h = m->h;
+        SlotBufs sb = m->sb;
+        size_t s0 = (size_t)b * S;
+        sb.vert64 += s0 * h.n_dyn_verts * 3;
+        sb.vview += s0 * h.n_verts;
+        sb.tri += s0 * h.n_dyn_tris * 3;
+        sb.node += s0 * h.n_dyn_nodes * 4;
+        sb.counter += s0 * h.n_dyn_nodes;
+        sb.root_box += s0 * kMaxParts * 6;
+        SlotPose *pose = ctx->pose + s0;
+        TraceArgs a{};
+        a.mesh_d = m->d;
+        a.pose = pose;
+        a.slot = sb;
+        a.N = pl.N;
+        a.bounces = prm->bounces;
+        a.nseg = nseg;
+        a.eps_rel = prm->eps_rel;
+        a.n_blocks_x = nbx;
+        a.n_blocks_ref = nbr;
+        a.partials = ctx->partials + s0 * nbx * kPart;
+        a.partials1 = ctx->partials1 + s0 * kRed1 * kPart;
+        a.tctx = ctx->tctx + s0 * trace_ctx_bytes();
+        a.partials_ref = ctx->partials_ref + s0 * nbr * kPart;
+        a.amb_list = ctx->amb_list + s0 * nbx * kTileRays;
+        a.amb_count = ctx->amb_count + s0 * nbx;
+        a.amb_off = ctx->amb_off + s0 * (nbx + 1);
+        a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
+        int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
+        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : nullptr;
+        int g0 = tm.mark(ls);
+        CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, pose, ls));
+        CK(ctx, launch_vertices(m->d, h, pose, sb, Sc, ls));
+        launches += 2;
+        if (h.n_dyn_tris > 0) {
+            CK(ctx, launch_refit(m->d, h, sb, Sc, false, nullptr, nullptr, nullptr, nullptr, ls));
+            launches++;
+        }
+        int g1 = tm.mark(ls);
+        CK(ctx, launch_trace(a, Sc, ls));
+        int g2 = tm.mark(ls);
+        CK(ctx, launch_refine(a, Sc, ls));
+        int g3 = tm.mark(ls);
+        CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
+        int g4 = tm.mark(ls);
+        launches += 6;  // frame, trace, hand-off scan, refine, two reduction levels
+        trace_launches++;
+        tm.span(0, g0, g1);
+        tm.span(1, g1, g2);
+        tm.span(2, g2, g3);
+        tm.span(3, g3, g4);
+        if (hit_tri && !h_dev) {
+            CK(ctx, cudaMemcpyAsync(hit_tri + (size_t)e0 * R * nseg, stage, sizeof(int32_t) * Sc * R * nseg,
+                                    cudaMemcpyDeviceToHost, ls));
+            tm.span(4, g4, tm.mark(ls));
+        }
+    }
+    // join: the context stream continues after every lane
+    for (int b = 0; b < pl.lanes; b++) {
+        CK(ctx, cudaEventRecord(ctx->ev_join[b], ctx->lane[b]));
+        CK(ctx, cudaStreamWaitEvent(st, ctx->ev_join[b], 0));
+    }
+    return SRP_OK;
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -196,11 +389,12 @@ srp_status srp_create(srp_ctx **out, int32_t device, void *cuda_stream)
         ctx->own_stream = true;
     }
     if (cudaMalloc(&ctx->err_flags, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&ctx->stats, 16 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&ctx->stats, 16 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&ctx->prop_done, sizeof(int)) != cudaSuccess) {
         srp_destroy(ctx);
         return SRP_ERR_OOM;
     }
-    for (int b = 0; b < 2; b++)
+    for (int b = 0; b < kLanes; b++)
         if (cudaStreamCreateWithFlags(&ctx->lane[b], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming) != cudaSuccess) {
             srp_destroy(ctx);
@@ -226,6 +420,11 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->amb_list);
     cudaFree(ctx->partials1);
     cudaFree(ctx->tctx);
+    cudaFree(ctx->prop_io);
+    cudaFree(ctx->prop_state);
+    cudaFree(ctx->prop_hlog);
+    cudaFree(ctx->prop_replay);
+    cudaFree(ctx->prop_done);
     cudaFree(ctx->amb_count);
     cudaFree(ctx->amb_off);
     cudaFree(ctx->io);
@@ -233,7 +432,7 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->err_flags);
     cudaFree(ctx->stats);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
-    for (int b = 0; b < 2; b++) {
+    for (int b = 0; b < kLanes; b++) {
         if (ctx->lane[b]) cudaStreamSynchronize(ctx->lane[b]), cudaStreamDestroy(ctx->lane[b]);
         if (ctx->ev_join[b]) cudaEventDestroy(ctx->ev_join[b]);
     }
@@ -555,58 +754,18 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     ctx->err.clear();
     Mesh *m = get_mesh(ctx, mesh_id);
     if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
-    if (!prm) return fail(ctx, SRP_ERR_ARG, "null params");
-    if (prm->N < 1 || prm->N > SRP_MAX_N) return fail(ctx, SRP_ERR_ARG, "N = %d outside [1, %d]", prm->N, SRP_MAX_N);
-    if (prm->bounces < 0 || prm->bounces > kMaxBounces) return fail(ctx, SRP_ERR_ARG, "bounces = %d", prm->bounces);
-    if (!(prm->P0 >= 0.0) || !(prm->eps_rel >= 0.0)) return fail(ctx, SRP_ERR_ARG, "P0 and eps_rel must be >= 0");
-    if (prm->panel_mode < 0 || prm->panel_mode > 2) return fail(ctx, SRP_ERR_ARG, "bad panel_mode");
+    srp_status rc = check_eval_params(ctx, prm);
+    if (rc) return rc;
     if (n < 0) return fail(ctx, SRP_ERR_ARG, "n < 0");
     memset(&ctx->last, 0, sizeof ctx->last);
     if (n == 0) return SRP_OK;
     if (!sun_dir_body || !force || !torque) return fail(ctx, SRP_ERR_ARG, "null input or output");
     CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    const int N = prm->N, nseg = prm->bounces + 1;
-    const size_t R = (size_t)N * N;
-    // concurrent evaluations: enough rays in flight to fill the GPU several times
-    int S = (int)std::min<size_t>(std::max<size_t>((size_t)(1u << 21) / R, 1), 64);
-    S = std::min(S, n);
-    // chunks of S evaluations alternate between two lane streams with their own
-    // slots and buffers, so the short, latency-bound tail of one chunk (FP64
-    // re-trace, reduction) overlaps the traversal of the next
-    const int nchunks = (n + S - 1) / S;
-    const int lanes = std::min(nchunks, 2);
-    srp_status rc = ensure_slots(ctx, m, S * lanes);
+    EvalPlan pl;
+    rc = eval_plan(ctx, m, prm, n, hit_tri != nullptr, pl);
     if (rc) return rc;
-    // trace tiles of 8 x 4 pixels, one warp each
-    int nbx = ((N + 7) / 8) * ((N + 3) / 4);
-    // FP64 re-trace grid: a few blocks per SM, walking the compacted hand-off list
-    int nbr = std::max(1, std::min(nbx, 1216 / S));
-    const size_t SL = (size_t)S * lanes;
-    CK(ctx, grow(&ctx->pose, &ctx->pose_cap, SL, false));
-    CK(ctx, grow(&ctx->partials, &ctx->partials_cap, SL * nbx * kPart, false));
-    CK(ctx, grow(&ctx->partials_ref, &ctx->partials_ref_cap, SL * nbr * kPart, false));
-    CK(ctx, grow(&ctx->amb_list, &ctx->amb_list_cap, SL * nbx * kTileRays, false));
-    CK(ctx, grow(&ctx->partials1, &ctx->partials1_cap, SL * kRed1 * kPart, false));
-    CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
-    CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * nbx, false));
-    CK(ctx, grow(&ctx->amb_off, &ctx->amb_off_cap, SL * (nbx + 1), false));
-    // phase timing: events recorded on the stream each phase runs on, summed per phase
-    const bool timing = (prm->flags & SRP_EVAL_TIMING) != 0;
-    std::vector<std::pair<int, int>> spans[5];  // geometry, trace, refine, reduce, transfer
-    int n_ev = 0;
-    auto mark_on = [&](cudaStream_t s_) -> int {
-        if (!timing) return -1;
-        if (n_ev >= (int)ctx->events.size()) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return -1;
-            ctx->events.push_back(e);
-        }
-        cudaEventRecord(ctx->events[n_ev], s_);
-        return n_ev++;
-    };
-    auto mark = [&]() -> int { return mark_on(st); };
-    int64_t launches = 0, trace_launches = 0;
+    Timing tm(ctx, (prm->flags & SRP_EVAL_TIMING) != 0);
     bool in_dev = is_device_ptr(sun_dir_body);
     bool dist_dev = sun_dist_au && is_device_ptr(sun_dist_au);
     bool f_dev = is_device_ptr(force), t_dev = is_device_ptr(torque);
@@ -617,117 +776,155 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     double *d_dist = sun_dist_au ? (dist_dev ? const_cast<double *>(sun_dist_au) : ctx->io + (size_t)n * 3) : nullptr;
     double *d_f = f_dev ? force : ctx->io + (size_t)n * 4;
     double *d_t = t_dev ? torque : ctx->io + (size_t)n * 7;
-    int t_in0 = mark();
+    int t_in0 = tm.mark(st);
     if (!in_dev) CK(ctx, cudaMemcpyAsync(d_sun, sun_dir_body, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     if (sun_dist_au && !dist_dev)
         CK(ctx, cudaMemcpyAsync(d_dist, sun_dist_au, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-    spans[4].push_back({t_in0, mark()});
-    if (hit_tri && !h_dev) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * R * nseg, false));
+    tm.span(4, t_in0, tm.mark(st));
     CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
     CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
-    // fork: both lanes start after everything already queued on the context stream
-    CK(ctx, cudaEventRecord(ctx->ev_fork, st));
-    for (int b = 0; b < lanes; b++) CK(ctx, cudaStreamWaitEvent(ctx->lane[b], ctx->ev_fork, 0));
-    for (int c = 0; c < nchunks; c++) {
-        const int e0 = c * S, b = c % lanes;
-        const int Sc = std::min(S, n - e0);
-        cudaStream_t ls = ctx->lane[b];
-        // lane b's slots and buffers
-        const MeshDev &h = m->h;
-        SlotBufs sb = m->sb;
-        size_t s0 = (size_t)b * S;
-        sb.vert64 += s0 * h.n_dyn_verts * 3;
-        sb.vview += s0 * h.n_verts;
-        sb.tri += s0 * h.n_dyn_tris * 3;
-        sb.node += s0 * h.n_dyn_nodes * 4;
-        sb.counter += s0 * h.n_dyn_nodes;
-        sb.root_box += s0 * kMaxParts * 6;
-        SlotPose *pose = ctx->pose + s0;
-        TraceArgs a{};
-        a.mesh_d = m->d;
-        a.pose = pose;
-        a.slot = sb;
-        a.N = N;
-        a.bounces = prm->bounces;
-        a.nseg = nseg;
-        a.eps_rel = prm->eps_rel;
-        a.n_blocks_x = nbx;
-        a.n_blocks_ref = nbr;
-        a.partials = ctx->partials + s0 * nbx * kPart;
-        a.partials1 = ctx->partials1 + s0 * kRed1 * kPart;
-        a.tctx = ctx->tctx + s0 * trace_ctx_bytes();
-        a.partials_ref = ctx->partials_ref + s0 * nbr * kPart;
-        a.amb_list = ctx->amb_list + s0 * nbx * kTileRays;
-        a.amb_count = ctx->amb_count + s0 * nbx;
-        a.amb_off = ctx->amb_off + s0 * (nbx + 1);
-        a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
-        int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
-        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : nullptr;
-        int g0 = mark_on(ls);
-        CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, pose, ls));
-        CK(ctx, launch_vertices(m->d, h, pose, sb, Sc, ls));
-        launches += 2;
-        if (h.n_dyn_tris > 0) {
-            CK(ctx, launch_refit(m->d, h, sb, Sc, false, nullptr, nullptr, nullptr, nullptr, ls));
-            launches++;
-        }
-        int g1 = mark_on(ls);
-        CK(ctx, launch_trace(a, Sc, ls));
-        int g2 = mark_on(ls);
-        CK(ctx, launch_refine(a, Sc, ls));
-        int g3 = mark_on(ls);
-        CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
-        int g4 = mark_on(ls);
-        launches += 6;  // frame, trace, hand-off scan, refine, two reduction levels
-        trace_launches++;
-        spans[0].push_back({g0, g1});
-        spans[1].push_back({g1, g2});
-        spans[2].push_back({g2, g3});
-        spans[3].push_back({g3, g4});
-        if (hit_tri && !h_dev) {
-            CK(ctx, cudaMemcpyAsync(hit_tri + (size_t)e0 * R * nseg, stage, sizeof(int32_t) * Sc * R * nseg,
-                                    cudaMemcpyDeviceToHost, ls));
-            spans[4].push_back({g4, mark_on(ls)});
-        }
-    }
-    // join: the context stream continues after both lanes
-    for (int b = 0; b < lanes; b++) {
-        CK(ctx, cudaEventRecord(ctx->ev_join[b], ctx->lane[b]));
-        CK(ctx, cudaStreamWaitEvent(st, ctx->ev_join[b], 0));
-    }
-    int t_out0 = mark();
+    int64_t launches = 0, trace_launches = 0;
+    rc = eval_enqueue(ctx, m, prm, pl, n, d_sun, d_dist, d_f, d_t, hit_tri, h_dev, tm, launches, trace_launches);
+    if (rc) return rc;
+    int t_out0 = tm.mark(st);
     if (!f_dev) CK(ctx, cudaMemcpyAsync(force, d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     if (!t_dev) CK(ctx, cudaMemcpyAsync(torque, d_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
-    spans[4].push_back({t_out0, mark()});
+    tm.span(4, t_out0, tm.mark(st));
     int flags = 0;
     unsigned long long stats[16];
     CK(ctx, cudaMemcpyAsync(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(ctx, cudaMemcpyAsync(stats, ctx->stats, sizeof stats, cudaMemcpyDeviceToHost, st));
     CK(ctx, cudaStreamSynchronize(st));
-    srp_eval_stats &L = ctx->last;
-    L.evals = (int64_t)stats[0];
-    L.rays = (int64_t)stats[1];
-    L.refined = (int64_t)stats[2];
-    L.segments = (int64_t)stats[3];
-    for (int k = 0; k <= kMaxBounces; k++) L.hits[k] = (int64_t)stats[4 + k];
-    L.nodes_visited = (int64_t)stats[9];
-    L.tris_tested = (int64_t)stats[10];
-    L.box_tests = (int64_t)stats[11];
-    for (int k = 0; k < 4; k++) L.handoff_cause[k] = (int64_t)stats[12 + k];
-    L.launches = launches;
-    L.trace_launches = trace_launches;
-    if (timing) {
-        double *ms[5] = {&L.ms_geometry, &L.ms_trace, &L.ms_refine, &L.ms_reduce, &L.ms_transfer};
-        for (int p = 0; p < 5; p++)
-            for (auto &sp : spans[p]) {
-                float t = 0.f;
-                if (sp.first >= 0 && sp.second >= 0 &&
-                    cudaEventElapsedTime(&t, ctx->events[sp.first], ctx->events[sp.second]) == cudaSuccess)
-                    *ms[p] += t;
-            }
-    }
+    fill_stats(ctx->last, stats);
+    ctx->last.launches = launches;
+    ctx->last.trace_launches = trace_launches;
+    tm.collect(ctx->last);
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
     return SRP_OK;
+}
+
+srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p, int32_t n, const double *y0,
+                         const double *t0_t1, double *y1, srp_prop_stats *stats, double *h_log, int64_t h_cap)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
+    if (!p) return fail(ctx, SRP_ERR_ARG, "null params");
+    srp_status rc = check_eval_params(ctx, &p->eval);
+    if (rc) return rc;
+    if (n <= 0 || !y0 || !t0_t1 || !y1) return fail(ctx, SRP_ERR_ARG, "need n > 0, y0, t0_t1 and y1");
+    if (p->method != SRP_RKF78 && p->method != SRP_RK4) return fail(ctx, SRP_ERR_ARG, "bad method");
+    if (p->central != SRP_CENTRAL_EARTH && p->central != SRP_CENTRAL_SUN) return fail(ctx, SRP_ERR_ARG, "bad central body");
+    if (p->attitude != SRP_ATT_LVLH && p->attitude != SRP_ATT_INERTIAL) return fail(ctx, SRP_ERR_ARG, "bad attitude");
+    if (!(p->h0 > 0.0) || !(p->h_min >= 0.0) || p->max_steps <= 0) return fail(ctx, SRP_ERR_ARG, "bad step settings");
+    if (p->method == SRP_RKF78 && (!(p->rtol > 0.0) || !(p->atol_pos > 0.0) || !(p->atol_vel > 0.0)))
+        return fail(ctx, SRP_ERR_ARG, "tolerances must be > 0");
+    if (p->srp && !(m->mass > 0.0)) return fail(ctx, SRP_ERR_ARG, "mesh mass must be > 0 for SRP");
+    if (h_log && h_cap <= 0) return fail(ctx, SRP_ERR_ARG, "h_cap must be > 0 with h_log");
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    memset(&ctx->last, 0, sizeof ctx->last);
+    EvalPlan pl;
+    rc = eval_plan(ctx, m, &p->eval, n, false, pl);
+    if (rc) return rc;
+    // device buffers (grown, kept by the context)
+    size_t need = (size_t)n * (3 + 1 + 3 + 3 + 6 + 2);
+    CK(ctx, grow(&ctx->prop_io, &ctx->prop_io_cap, need, false));
+    CK(ctx, grow(&ctx->prop_state, &ctx->prop_state_cap, (size_t)n, false));
+    if (h_log) CK(ctx, grow(&ctx->prop_hlog, &ctx->prop_hlog_cap, (size_t)n * h_cap, false));
+    double *d_sun = ctx->prop_io, *d_dist = d_sun + 3 * (size_t)n, *d_f = d_dist + n, *d_t = d_f + 3 * (size_t)n;
+    double *d_y0 = d_t + 3 * (size_t)n, *d_t01 = d_y0 + 6 * (size_t)n;
+    CK(ctx, cudaMemcpyAsync(d_y0, y0, sizeof(double) * 6 * n, cudaMemcpyDefault, st));
+    CK(ctx, cudaMemcpyAsync(d_t01, t0_t1, sizeof(double) * 2 * n, cudaMemcpyDefault, st));
+    CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
+    CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
+    CK(ctx, cudaMemsetAsync(ctx->prop_done, 0, sizeof(int), st));
+    PropState *S = ctx->prop_state;
+    CK(ctx, launch_prop_init(S, n, d_y0, d_t01, p->h0, ctx->prop_done, st));
+    PropDev P{};
+    P.method = p->method; P.central = p->central; P.j2 = p->j2; P.sun3 = p->sun3; P.srp = p->srp;
+    P.attitude = p->attitude;
+    for (int k = 0; k < 4; k++) P.q[k] = p->q[k];
+    P.epoch_mjd_tt = p->epoch_mjd_tt; P.mass = m->mass;
+    P.rtol = p->rtol; P.atol_pos = p->atol_pos; P.atol_vel = p->atol_vel;
+    P.h0 = p->h0; P.h_min = p->h_min; P.h_max = p->h_max; P.max_steps = p->max_steps;
+    if (p->h_replay && p->n_replay > 0) {
+        if (p->method != SRP_RKF78) return fail(ctx, SRP_ERR_ARG, "step replay needs SRP_RKF78");
+        CK(ctx, grow(&ctx->prop_replay, &ctx->prop_replay_cap, (size_t)n * p->n_replay, false));
+        CK(ctx, cudaMemcpyAsync(ctx->prop_replay, p->h_replay, sizeof(double) * n * p->n_replay, cudaMemcpyDefault, st));
+        P.h_replay = ctx->prop_replay;
+        P.n_replay = p->n_replay;
+    }
+    const int nstage = p->method == SRP_RK4 ? 4 : 13;
+    // capture one step into a graph
+    Timing off(ctx, false);
+    int64_t launches = 0, trace_launches = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    srp_status crc = SRP_OK;
+    for (int sg = 0; sg < nstage && crc == SRP_OK; sg++) {
+        if (launch_prop_stage(S, n, P, sg, d_sun, d_dist, st) != cudaSuccess) { crc = SRP_ERR_CUDA; break; }
+        if (p->srp) crc = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, nullptr, false, off, launches,
+                                       trace_launches);
+        if (crc == SRP_OK && launch_prop_accel(S, n, P, sg, d_f, st) != cudaSuccess) crc = SRP_ERR_CUDA;
+    }
+    if (crc == SRP_OK && launch_prop_control(S, n, P, ctx->prop_done, h_log ? ctx->prop_hlog : nullptr, h_cap, st) !=
+                             cudaSuccess)
+        crc = SRP_ERR_CUDA;
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (crc != SRP_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return crc != SRP_OK ? crc : fail(ctx, SRP_ERR_CUDA, "step capture failed: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(ctx, SRP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    // relaunch until every trajectory is done; the device counts them
+    const int poll = p->poll > 0 ? p->poll : 16;
+    const int64_t max_rounds = (p->max_steps + 2) / poll + 2;
+    int done = 0;
+    for (int64_t round = 0; round < max_rounds; round++) {
+        CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        cudaError_t se = cudaStreamSynchronize(st);
+        if (se != cudaSuccess) { cudaGraphExecDestroy(exec); return fail(ctx, SRP_ERR_CUDA, "%s", cudaGetErrorString(se)); }
+        if (done >= n) break;
+        for (int k = 0; k < poll; k++) {
+            se = cudaGraphLaunch(exec, st);
+            if (se != cudaSuccess) { cudaGraphExecDestroy(exec); return fail(ctx, SRP_ERR_CUDA, "%s", cudaGetErrorString(se)); }
+        }
+    }
+    cudaGraphExecDestroy(exec);
+    std::vector<PropState> hs(n);
+    int flags = 0;
+    unsigned long long st16[16];
+    CK(ctx, cudaMemcpyAsync(hs.data(), S, sizeof(PropState) * n, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(st16, ctx->stats, sizeof st16, cudaMemcpyDeviceToHost, st));
+    if (h_log) CK(ctx, cudaMemcpyAsync(h_log, ctx->prop_hlog, sizeof(double) * n * h_cap, cudaMemcpyDefault, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    std::vector<double> yo((size_t)n * 6);
+    srp_status out = SRP_OK;
+    for (int i = 0; i < n; i++) {
+        for (int k = 0; k < 6; k++) yo[6 * (size_t)i + k] = hs[i].y[k];
+        if (stats) {
+            stats[i].steps = hs[i].steps;
+            stats[i].rejects = hs[i].rejects;
+            stats[i].evals = hs[i].evals;
+            stats[i].t = hs[i].t;
+            stats[i].status = hs[i].status;
+            stats[i].reserved = 0;
+        }
+        if (hs[i].status) out = SRP_ERR_STEP;
+        if (!hs[i].done) out = fail(ctx, SRP_ERR_STEP, "trajectory %d did not finish within the step budget", i);
+    }
+    CK(ctx, cudaMemcpy(y1, yo.data(), sizeof(double) * 6 * n, cudaMemcpyDefault));
+    fill_stats(ctx->last, st16);
+    if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
+    if (out == SRP_ERR_STEP && ctx->err.empty()) fail(ctx, SRP_ERR_STEP, "a trajectory hit h_min or max_steps");
+    return out;
 }
 
 srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out)

@@ -134,6 +134,29 @@ struct TraceArgs {
 };
 size_t trace_ctx_bytes();
 
+// Propagation settings as seen by the device (from srp_prop_params).
+struct PropDev {
+    int method, central, j2, sun3, srp, attitude;
+    double q[4];
+    double epoch_mjd_tt, mass;
+    double rtol, atol_pos, atol_vel, h0, h_min, h_max;
+    long long max_steps;
+    const double *h_replay;  // [n][n_replay] device, or null
+    long long n_replay;
+};
+
+// Per-trajectory integrator state (device).
+struct PropState {
+    double t, t1, h, hs;       // time, end time, proposed step, step of the current attempt
+    double y[6];               // state (m, m/s), inertial
+    double ys[6], ts;          // current stage state and time
+    double k[13][6];           // stage derivatives
+    double rsun[3];            // Sun position at the stage time
+    double R[9];               // body -> inertial at the stage
+    long long steps, rejects, evals, nlog;
+    int done, status, shadow, pad_;
+};
+
 // ordered-int encoding of doubles for atomicMin/Max
 __host__ __device__ inline unsigned long long dbl_to_ord(double x)
 {
@@ -176,5 +199,14 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st);
 cudaError_t launch_refine(const TraceArgs &a, int S, cudaStream_t st);
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
                           unsigned long long *stats_accum, cudaStream_t st);
+
+// prop.cu
+cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double *t01, double h0, int *n_done,
+                             cudaStream_t st);
+cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, double *sun_dir, double *sun_dist,
+                              cudaStream_t st);
+cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st);
+cudaError_t launch_prop_control(PropState *S, int n, const PropDev &P, int *n_done, double *h_log, int64_t h_cap,
+                                cudaStream_t st);
 
 }  // namespace srp

@@ -25,7 +25,7 @@ MAX_BOUNCES = 4
 
 # Symbols declared in include/srp.h (checked by the tests against the library).
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",
-           "srp_eval_batch", "srp_eval_stats_get", "srp_eval_noalloc"]
+           "srp_eval_batch", "srp_eval_stats_get", "srp_propagate", "srp_eval_noalloc"]
 
 
 class SrpError(RuntimeError):
@@ -59,6 +59,24 @@ class EvalStats(C.Structure):
                 ("ms_refine", C.c_double), ("ms_reduce", C.c_double), ("ms_transfer", C.c_double)]
 
 
+RKF78, RK4 = 0, 1
+CENTRAL_EARTH, CENTRAL_SUN = 0, 1
+ATT_LVLH, ATT_INERTIAL = 0, 1
+
+
+class PropParams(C.Structure):
+    _fields_ = [("method", C.c_int32), ("central", C.c_int32), ("j2", C.c_int32), ("sun3", C.c_int32),
+                ("srp", C.c_int32), ("attitude", C.c_int32), ("q", C.c_double * 4), ("epoch_mjd_tt", C.c_double),
+                ("rtol", C.c_double), ("atol_pos", C.c_double), ("atol_vel", C.c_double), ("h0", C.c_double),
+                ("h_min", C.c_double), ("h_max", C.c_double), ("max_steps", C.c_int64), ("poll", C.c_int32),
+                ("reserved", C.c_int32), ("eval", EvalParams), ("h_replay", C.c_void_p), ("n_replay", C.c_int64)]
+
+
+class PropStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("rejects", C.c_int64), ("evals", C.c_int64), ("t", C.c_double),
+                ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
 _lib = None
 
 
@@ -85,6 +103,8 @@ def load(build_if_needed: bool = True):
         lib.srp_eval_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.srp_eval_stats_get.argtypes = [C.c_void_p, C.POINTER(EvalStats)]
+        lib.srp_propagate.argtypes = [C.c_void_p, C.c_int32, C.POINTER(PropParams), C.c_int32, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(PropStats), C.c_void_p, C.c_int64]
         lib.srp_eval_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                          C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double), C.c_int32,
                                          C.c_int32, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -241,6 +261,35 @@ class Context:
         ph, k5 = _ptr(hit)
         self._check(self.lib.srp_eval_batch(self.h, mesh_id, C.byref(p), n, ps, pd, pf, pt, ph))
         return (force, torque, hit) if hits else (force, torque)
+
+    def propagate(self, mesh_id: int, y0, t0_t1, method: int = RKF78, central: int = CENTRAL_EARTH, j2=False,
+                  sun3=False, srp_on=True, attitude: int = ATT_LVLH, q=(1.0, 0.0, 0.0, 0.0),
+                  epoch_mjd_tt: float = 61041.0, rtol: float = 1e-12, atol_pos: float = 1e-6,
+                  atol_vel: float = 1e-9, h0: float = 60.0, h_min: float = 1e-6, h_max: float = 0.0,
+                  max_steps: int = 10_000_000, poll: int = 16, N: int = 64, bounces: int = 1, P0: float = 4.56e-6,
+                  eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, h_cap: int = 0, h_replay=None):
+        """srp_propagate: y1 [n, 6], per-trajectory stats (list of dicts) and,
+        with h_cap > 0, the accepted step sizes [n, h_cap] (NaN padded).
+        h_replay [n, k]: take exactly these RKF7(8) steps (replay)."""
+        y0 = np.ascontiguousarray(np.asarray(y0, np.float64).reshape(-1, 6))
+        n = len(y0)
+        t01 = np.ascontiguousarray(np.asarray(t0_t1, np.float64).reshape(n, 2))
+        hr = None if h_replay is None else np.ascontiguousarray(np.asarray(h_replay, np.float64).reshape(n, -1))
+        p = PropParams(method, central, int(j2), int(sun3), int(srp_on), attitude, (C.c_double * 4)(*q),
+                       epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, 0,
+                       EvalParams(N, bounces, P0, eps_rel, panel_mode, 0),
+                       hr.ctypes.data if hr is not None else None, 0 if hr is None else hr.shape[1])
+        y1 = np.empty((n, 6))
+        st = (PropStats * n)()
+        hl = np.full((n, h_cap), np.nan) if h_cap > 0 else None
+        self._check(self.lib.srp_propagate(self.h, mesh_id, C.byref(p), n, y0.ctypes.data, t01.ctypes.data,
+                                           y1.ctypes.data, st, hl.ctypes.data if hl is not None else None,
+                                           h_cap))
+        stats = [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status) for s in st]
+        if hl is not None:
+            for i, s in enumerate(stats):
+                hl[i, min(s["steps"], h_cap):] = np.nan
+        return y1, stats, hl
 
     def eval_stats(self) -> dict:
         s = EvalStats()
