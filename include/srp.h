@@ -179,7 +179,8 @@ srp_status srp_set_panel_angles(srp_ctx *ctx, int32_t mesh_id, int32_t n, const 
  * hits the triangle it leaves); sum of all pixels times P0 / dist^2 times the
  * pixel area.
  *   sun_dir_body [n][3]   unit vectors towards the Sun, body frame
- *   sun_dist_au  [n]      Sun distance (AU); NULL means 1
+ *   sun_dist_au  [n]      Sun distance (AU); NULL means 1; a negative entry skips
+ *                         that evaluation (force and torque 0, hit ids untouched)
  *   force        [n][3]   out, N
  *   torque       [n][3]   out, N m about c_ref
  *   hit_tri      [n][N*N][bounces+1] out, original triangle id per ray segment,
@@ -219,7 +220,9 @@ typedef struct {
     double h_max;          /* step-size ceiling (RKF7(8)); 0 = none                          */
     int64_t max_steps;     /* accepted + rejected step budget per trajectory                */
     int32_t poll;          /* steps launched between completion checks (0 = 16)             */
-    int32_t reserved;
+    int32_t host_loop;     /* 0: graph-captured steps; 1: the same kernels issued stage by
+                              stage with the host waiting for every stage's SRP result (the
+                              pattern of a host integrator calling a GPU force model)       */
     srp_eval_params eval;  /* ray grid, bounces, P0, panel mode of every SRP evaluation     */
     const double *h_replay; /* NULL, or [n_traj][n_replay] step sizes (host or device): RKF7(8)
                                then takes exactly these steps, all accepted, no error control,

@@ -331,7 +331,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         CK(ctx, launch_vertices(m->d, h, pose, sb, Sc, ls));
         launches += 2;
         if (h.n_dyn_tris > 0) {
-            CK(ctx, launch_refit(m->d, h, sb, Sc, false, nullptr, nullptr, nullptr, nullptr, ls));
+            CK(ctx, launch_refit(m->d, h, sb, pose, Sc, false, nullptr, nullptr, nullptr, nullptr, ls));
             launches++;
         }
         int g1 = tm.mark(ls);
@@ -359,6 +359,41 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         CK(ctx, cudaStreamWaitEvent(st, ctx->ev_join[b], 0));
     }
     return SRP_OK;
+}
+
+// Read back the trajectories: final states, per-trajectory stats, step log.
+srp_status finish_propagate(srp_ctx *ctx, int n, const PropState *S, double *y1, srp_prop_stats *stats, double *h_log,
+                            int64_t h_cap)
+{
+    cudaStream_t st = ctx->stream;
+    std::vector<PropState> hs(n);
+    int flags = 0;
+    unsigned long long st16[16];
+    CK(ctx, cudaMemcpyAsync(hs.data(), S, sizeof(PropState) * n, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(st16, ctx->stats, sizeof st16, cudaMemcpyDeviceToHost, st));
+    if (h_log) CK(ctx, cudaMemcpyAsync(h_log, ctx->prop_hlog, sizeof(double) * n * h_cap, cudaMemcpyDefault, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    std::vector<double> yo((size_t)n * 6);
+    srp_status out = SRP_OK;
+    for (int i = 0; i < n; i++) {
+        for (int k = 0; k < 6; k++) yo[6 * (size_t)i + k] = hs[i].y[k];
+        if (stats) {
+            stats[i].steps = hs[i].steps;
+            stats[i].rejects = hs[i].rejects;
+            stats[i].evals = hs[i].evals;
+            stats[i].t = hs[i].t;
+            stats[i].status = hs[i].status;
+            stats[i].reserved = 0;
+        }
+        if (hs[i].status) out = SRP_ERR_STEP;
+        if (!hs[i].done) out = fail(ctx, SRP_ERR_STEP, "trajectory %d did not finish within the step budget", i);
+    }
+    CK(ctx, cudaMemcpy(y1, yo.data(), sizeof(double) * 6 * n, cudaMemcpyDefault));
+    fill_stats(ctx->last, st16);
+    if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
+    if (out == SRP_ERR_STEP && ctx->err.empty()) fail(ctx, SRP_ERR_STEP, "a trajectory hit h_min or max_steps");
+    return out;
 }
 
 }  // namespace
@@ -711,7 +746,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     // device copy of the mesh, then the static refit (writes root boxes into it)
     MK(dmalloc(m->allocs, &m->d, 1));
     MK(cudaMemcpyAsync(m->d, &h, sizeof(MeshDev), cudaMemcpyHostToDevice, st));
-    MK(launch_refit(m->d, h, SlotBufs{}, 1, true, h.node_static, h.tri_static, cnt_static,
+    MK(launch_refit(m->d, h, SlotBufs{}, nullptr, 1, true, h.node_static, h.tri_static, cnt_static,
                     &m->d->root_box_static[0][0], st));
     MK(cudaMemcpyAsync(&h.root_box_static[0][0], &m->d->root_box_static[0][0], sizeof(h.root_box_static),
                        cudaMemcpyDeviceToHost, st));
@@ -857,9 +892,31 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
         P.n_replay = p->n_replay;
     }
     const int nstage = p->method == SRP_RK4 ? 4 : 13;
-    // capture one step into a graph
     Timing off(ctx, false);
     int64_t launches = 0, trace_launches = 0;
+    if (p->host_loop) {
+        // the same kernels, issued stage by stage with the host waiting for each
+        // stage's SRP result, as a host-side integrator calling a GPU force model would
+        int done = 0;
+        for (int64_t step = 0; step <= p->max_steps + 1; step++) {
+            CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(ctx, cudaStreamSynchronize(st));
+            if (done >= n) break;
+            for (int sg = 0; sg < nstage; sg++) {
+                CK(ctx, launch_prop_stage(S, n, P, sg, d_sun, d_dist, st));
+                if (p->srp) {
+                    srp_status erc = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, nullptr, false,
+                                                  off, launches, trace_launches);
+                    if (erc) return erc;
+                }
+                CK(ctx, cudaStreamSynchronize(st));
+                CK(ctx, launch_prop_accel(S, n, P, sg, d_f, st));
+            }
+            CK(ctx, launch_prop_control(S, n, P, ctx->prop_done, h_log ? ctx->prop_hlog : nullptr, h_cap, st));
+        }
+        return finish_propagate(ctx, n, S, y1, stats, h_log, h_cap);
+    }
+    // capture one step into a graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -882,49 +939,36 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return fail(ctx, SRP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
-    // relaunch until every trajectory is done; the device counts them
-    const int poll = p->poll > 0 ? p->poll : 16;
-    const int64_t max_rounds = (p->max_steps + 2) / poll + 2;
+    // relaunch until every trajectory is done.  Each round launches about as many
+    // steps as the furthest trajectory still needs at its current step size
+    // (at most `poll`), so finished work is rarely repeated; finished and
+    // shadowed trajectories skip their SRP evaluations anyway.
+    const int poll_max = p->poll > 0 ? p->poll : 16;
+    const int64_t max_rounds = p->max_steps + 2;
     int done = 0;
+    std::vector<PropState> peek(n);
+    int launch = 1;
     for (int64_t round = 0; round < max_rounds; round++) {
         CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaMemcpyAsync(peek.data(), S, sizeof(PropState) * n, cudaMemcpyDeviceToHost, st));
         cudaError_t se = cudaStreamSynchronize(st);
         if (se != cudaSuccess) { cudaGraphExecDestroy(exec); return fail(ctx, SRP_ERR_CUDA, "%s", cudaGetErrorString(se)); }
         if (done >= n) break;
-        for (int k = 0; k < poll; k++) {
+        double need = 1.0;
+        for (int i = 0; i < n; i++) {
+            const PropState &X = peek[i];
+            if (X.done) continue;
+            double r = P.n_replay > 0 ? (double)(P.n_replay - X.steps) : (X.t1 - X.t) / fmax(X.h, 1e-300);
+            need = fmax(need, r);
+        }
+        launch = (int)std::min<double>(poll_max, std::max(1.0, std::ceil(need)));
+        for (int k = 0; k < launch; k++) {
             se = cudaGraphLaunch(exec, st);
             if (se != cudaSuccess) { cudaGraphExecDestroy(exec); return fail(ctx, SRP_ERR_CUDA, "%s", cudaGetErrorString(se)); }
         }
     }
     cudaGraphExecDestroy(exec);
-    std::vector<PropState> hs(n);
-    int flags = 0;
-    unsigned long long st16[16];
-    CK(ctx, cudaMemcpyAsync(hs.data(), S, sizeof(PropState) * n, cudaMemcpyDeviceToHost, st));
-    CK(ctx, cudaMemcpyAsync(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(ctx, cudaMemcpyAsync(st16, ctx->stats, sizeof st16, cudaMemcpyDeviceToHost, st));
-    if (h_log) CK(ctx, cudaMemcpyAsync(h_log, ctx->prop_hlog, sizeof(double) * n * h_cap, cudaMemcpyDefault, st));
-    CK(ctx, cudaStreamSynchronize(st));
-    std::vector<double> yo((size_t)n * 6);
-    srp_status out = SRP_OK;
-    for (int i = 0; i < n; i++) {
-        for (int k = 0; k < 6; k++) yo[6 * (size_t)i + k] = hs[i].y[k];
-        if (stats) {
-            stats[i].steps = hs[i].steps;
-            stats[i].rejects = hs[i].rejects;
-            stats[i].evals = hs[i].evals;
-            stats[i].t = hs[i].t;
-            stats[i].status = hs[i].status;
-            stats[i].reserved = 0;
-        }
-        if (hs[i].status) out = SRP_ERR_STEP;
-        if (!hs[i].done) out = fail(ctx, SRP_ERR_STEP, "trajectory %d did not finish within the step budget", i);
-    }
-    CK(ctx, cudaMemcpy(y1, yo.data(), sizeof(double) * 6 * n, cudaMemcpyDefault));
-    fill_stats(ctx->last, st16);
-    if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
-    if (out == SRP_ERR_STEP && ctx->err.empty()) fail(ctx, SRP_ERR_STEP, "a trajectory hit h_min or max_steps");
-    return out;
+    return finish_propagate(ctx, n, S, y1, stats, h_log, h_cap);
 }
 
 srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out)

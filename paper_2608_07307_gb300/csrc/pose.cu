@@ -36,6 +36,10 @@ __global__ void k_pose(const MeshDev *mesh, const double *sun_dirs, const double
     double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
     for (int k = 0; k < 3; k++) s[k] /= sn;
     double dist = sun_dist ? sun_dist[e] : 1.0;
+    P.eval = e;
+    P.flags = 0;
+    P.skip = dist < 0.0 ? 1 : 0;  // a negative distance asks to skip this evaluation
+    if (P.skip) return;
     int np = mesh->n_parts;
     for (int p = 0; p < np; p++) {
         const PartInfo &pi = mesh->part[p];
@@ -120,6 +124,7 @@ __global__ void __launch_bounds__(256) k_vertices(const MeshDev *mesh, SlotPose 
     int s = blockIdx.y;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     SlotPose &P = pose[s];
+    if (P.skip) return;  // uniform over the block
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     if (k < n_verts) {
         int p = mesh->vert_part[k];
@@ -197,13 +202,14 @@ __device__ inline void load_child_box_cg(const float4 *node, int which, float *b
 }
 
 // Thread per sorted triangle in [t0, t0 + n) (all static, or all dynamic).
-__global__ void __launch_bounds__(256) k_refit(const MeshDev *mesh, SlotBufs slot, int t0, int n, int dyn,
-                                               float4 *node_static, float4 *tri_static, unsigned *counter_static,
-                                               float *root_static)
+__global__ void __launch_bounds__(256) k_refit(const MeshDev *mesh, SlotBufs slot, const SlotPose *pose, int t0, int n,
+                                               int dyn, float4 *node_static, float4 *tri_static,
+                                               unsigned *counter_static, float *root_static)
 {
     int s = blockIdx.y;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
+    if (pose && pose[s].skip) return;  // no arrivals in a skipped slot: counter parities stay consistent
     int t = t0 + idx;
     // part of this sorted triangle: parts are contiguous in sorted order
     int p = -1;
@@ -274,16 +280,16 @@ __global__ void __launch_bounds__(256) k_refit(const MeshDev *mesh, SlotBufs slo
     for (int k = 0; k < 6; k++) root[k] = box[k];
 }
 
-cudaError_t launch_refit(const MeshDev *mesh_d, const MeshDev &mh, SlotBufs slot, int S, bool static_pass,
-                         float4 *node_static, float4 *tri_static, unsigned *counter_static, float *root_static,
-                         cudaStream_t st)
+cudaError_t launch_refit(const MeshDev *mesh_d, const MeshDev &mh, SlotBufs slot, const SlotPose *pose, int S,
+                         bool static_pass, float4 *node_static, float4 *tri_static, unsigned *counter_static,
+                         float *root_static, cudaStream_t st)
 {
     int t0 = static_pass ? 0 : mh.n_static_tris;
     int n = static_pass ? mh.n_static_tris : mh.n_dyn_tris;
     if (n <= 0) return cudaSuccess;
     dim3 grid((n + 255) / 256, static_pass ? 1 : S);
-    k_refit<<<grid, 256, 0, st>>>(mesh_d, slot, t0, n, static_pass ? 0 : 1, node_static, tri_static, counter_static,
-                                  root_static);
+    k_refit<<<grid, 256, 0, st>>>(mesh_d, slot, static_pass ? nullptr : pose, t0, n, static_pass ? 0 : 1, node_static,
+                                  tri_static, counter_static, root_static);
     return cudaGetLastError();
 }
 

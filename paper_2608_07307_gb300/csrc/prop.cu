@@ -183,7 +183,8 @@ __global__ void k_prop_stage(PropState *S, int n, PropDev P, int stage, double *
     body_to_inertial(P, X.ys, R);
     for (int k = 0; k < 9; k++) X.R[k] = R[k];
     for (int k = 0; k < 3; k++) sun_dir[3 * i + k] = R[k] * sv[0] + R[3 + k] * sv[1] + R[6 + k] * sv[2];
-    sun_dist[i] = sd / kAU;
+    // finished and shadowed trajectories skip their SRP evaluation (negative distance)
+    sun_dist[i] = (X.done || X.shadow || !P.srp) ? -1.0 : sd / kAU;
 }
 
 __global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const double *force)

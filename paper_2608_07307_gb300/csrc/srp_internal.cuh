@@ -59,6 +59,7 @@ struct SlotPose {
     double scale;             // P0 / dist^2 (multiplied by the pixel area at the end)
     int eval;                 // evaluation index in the batch
     int flags;                // device error flags
+    int skip;                 // evaluation skipped (negative Sun distance): every later kernel returns early
 };
 
 // Per-slot traversal view built from SlotPose by each trace block.
@@ -190,7 +191,8 @@ cudaError_t launch_pose(const MeshDev *mesh_d, const double *sun_dirs, const dou
                         int panel_mode, double P0, int eval0, int S, SlotPose *pose, cudaStream_t st);
 cudaError_t launch_vertices(const MeshDev *mesh_d, const MeshDev &mh, SlotPose *pose, SlotBufs slot, int S,
                             cudaStream_t st);
-cudaError_t launch_refit(const MeshDev *mesh_d, const MeshDev &mh, SlotBufs slot, int S, bool static_pass,
+cudaError_t launch_refit(const MeshDev *mesh_d, const MeshDev &mh, SlotBufs slot, const SlotPose *pose, int S,
+                         bool static_pass,
                          float4 *node_static, float4 *tri_static, unsigned *counter_static, float *root_static,
                          cudaStream_t st);
 

@@ -67,6 +67,7 @@ struct TraceCtx {
     float R, L, pad, eps32;
     float cref32[3];
     int n_parts, n_mats;
+    int skip;              // evaluation skipped: trace blocks only clear their hand-off count
     const float4 *vview;   // slot's view-frame vertices
     const float2 *mat32;
     const double *mat64;
@@ -91,6 +92,9 @@ __global__ void k_frame(TraceArgs a)
     const MeshDev *m = a.mesh_d;
     const SlotPose &P = a.pose[s];
     TraceCtx &B = reinterpret_cast<TraceCtx *>(a.tctx)[s];
+    B.skip = P.skip;
+    B.n_parts = m->n_parts;
+    if (P.skip) return;
     double umin = ord_to_dbl(P.wmin_bits[0]), umax = ord_to_dbl(P.wmax_bits[0]);
     double vmin = ord_to_dbl(P.wmin_bits[1]), vmax = ord_to_dbl(P.wmax_bits[1]);
     double wmin = ord_to_dbl(P.wmin_bits[2]), wmax = ord_to_dbl(P.wmax_bits[2]);
@@ -379,6 +383,10 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
     __syncwarp();
     const int N = a.N;
     const int lane = threadIdx.x;
+    if (B.skip) {
+        if (lane == 0) a.amb_count[(size_t)s * a.n_blocks_x + blockIdx.x] = 0;
+        return;
+    }
     const int tiles_x = (N + 7) / 8;
     const int i = (blockIdx.x % tiles_x) * 8 + (lane & 7);
     const int j = (blockIdx.x / tiles_x) * 4 + (lane >> 3);
@@ -744,6 +752,7 @@ __global__ void __launch_bounds__(256) k_refine(TraceArgs a)
 __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
 {
     const int s = blockIdx.y, b = blockIdx.x;
+    if (a.pose[s].skip) return;  // uniform over the block
     const int chunk = (a.n_blocks_x + kRed1 - 1) / kRed1;
     const int t0 = b * chunk, t1 = min(t0 + chunk, a.n_blocks_x);
     double acc[kPart];
@@ -762,6 +771,11 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
                                                 unsigned long long *stats_accum)
 {
     const int s = blockIdx.x;
+    if (a.pose[s].skip) {
+        // a skipped evaluation outputs zero force and torque
+        if (threadIdx.x < 6) (threadIdx.x < 3 ? force : torque)[3 * (eval0 + s) + threadIdx.x % 3] = 0.0;
+        return;
+    }
     double acc[kPart];
     for (int k = 0; k < kPart; k++) acc[k] = 0.0;
     // slot 6: the trace side counts hand-offs, the refine side the rays it did

@@ -69,7 +69,7 @@ class PropParams(C.Structure):
                 ("srp", C.c_int32), ("attitude", C.c_int32), ("q", C.c_double * 4), ("epoch_mjd_tt", C.c_double),
                 ("rtol", C.c_double), ("atol_pos", C.c_double), ("atol_vel", C.c_double), ("h0", C.c_double),
                 ("h_min", C.c_double), ("h_max", C.c_double), ("max_steps", C.c_int64), ("poll", C.c_int32),
-                ("reserved", C.c_int32), ("eval", EvalParams), ("h_replay", C.c_void_p), ("n_replay", C.c_int64)]
+                ("host_loop", C.c_int32), ("eval", EvalParams), ("h_replay", C.c_void_p), ("n_replay", C.c_int64)]
 
 
 class PropStats(C.Structure):
@@ -267,7 +267,8 @@ class Context:
                   epoch_mjd_tt: float = 61041.0, rtol: float = 1e-12, atol_pos: float = 1e-6,
                   atol_vel: float = 1e-9, h0: float = 60.0, h_min: float = 1e-6, h_max: float = 0.0,
                   max_steps: int = 10_000_000, poll: int = 16, N: int = 64, bounces: int = 1, P0: float = 4.56e-6,
-                  eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, h_cap: int = 0, h_replay=None):
+                  eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, h_cap: int = 0, h_replay=None,
+                  host_loop: bool = False):
         """srp_propagate: y1 [n, 6], per-trajectory stats (list of dicts) and,
         with h_cap > 0, the accepted step sizes [n, h_cap] (NaN padded).
         h_replay [n, k]: take exactly these RKF7(8) steps (replay)."""
@@ -276,7 +277,7 @@ class Context:
         t01 = np.ascontiguousarray(np.asarray(t0_t1, np.float64).reshape(n, 2))
         hr = None if h_replay is None else np.ascontiguousarray(np.asarray(h_replay, np.float64).reshape(n, -1))
         p = PropParams(method, central, int(j2), int(sun3), int(srp_on), attitude, (C.c_double * 4)(*q),
-                       epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, 0,
+                       epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, int(host_loop),
                        EvalParams(N, bounces, P0, eps_rel, panel_mode, 0),
                        hr.ctypes.data if hr is not None else None, 0 if hr is None else hr.shape[1])
         y1 = np.empty((n, 6))

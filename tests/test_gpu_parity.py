@@ -146,6 +146,19 @@ def test_distance_scaling_and_device_pointers(ctx):
     assert np.array_equal(Fd.cpu().numpy(), Fh) and np.array_equal(Td.cpu().numpy(), Th)
 
 
+def test_negative_distance_skips_an_evaluation(ctx):
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_uniform(6, seed=12)
+    dist = np.ones(6)
+    F0, T0 = ctx.eval_batch(mid, dirs, dist, N=64, bounces=1)
+    dist[[1, 4]] = -1.0
+    F1, T1 = ctx.eval_batch(mid, dirs, dist, N=64, bounces=1)
+    assert np.all(F1[[1, 4]] == 0.0) and np.all(T1[[1, 4]] == 0.0)
+    keep = [0, 2, 3, 5]
+    assert np.array_equal(F1[keep], F0[keep]) and np.array_equal(T1[keep], T0[keep])
+
+
 def test_deterministic(ctx):
     m = I.spacecraft(0.25)
     mid = ctx.load_mesh(m)

@@ -136,6 +136,15 @@ def test_thirty_day_geo_within_ten_metres(ctx):
     assert abs(st[0]["steps"] - so[0]) <= 0.05 * so[0]
 
 
+def test_host_loop_matches_graph_bitwise(ctx):
+    """The host-driven mode issues the same kernels in the same order."""
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    a, sa, _ = ctx.propagate(mid, GEO, [0.0, 20000.0], j2=True, sun3=True, N=32, bounces=1)
+    b, sb, _ = ctx.propagate(mid, GEO, [0.0, 20000.0], j2=True, sun3=True, N=32, bounces=1, host_loop=True)
+    assert np.array_equal(a, b) and sa[0]["steps"] == sb[0]["steps"]
+
+
 def test_propagate_argument_errors(ctx):
     from paper_2608_07307_gb300 import srp
     m = I.box_wing()
