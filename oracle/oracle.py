@@ -23,7 +23,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["srp_oracle.c", "prop_oracle.c"]
+SOURCES = ["srp_oracle.c", "frozen_oracle.c", "prop_oracle.c"]
 HEADERS = ["srp_oracle.h"]
 LIB = os.path.join(BUILD, "liboracle.so")
 
@@ -72,6 +72,8 @@ def lib():
         _lib.orc_eval_range.restype = C.c_int
         _lib.orc_eval_rays.restype = C.c_int
         _lib.orc_pose.restype = C.c_int
+        _lib.orc_window_ids.restype = C.c_int
+        _lib.orc_eval_frozen.restype = C.c_int
     return _lib
 
 
@@ -107,35 +109,39 @@ class OMesh:
                        (C.c_double * 3)(*np.asarray(mesh.c_ref, np.float64)))
 
 
-def _params(N, bounces, P0, dist_au, eps_rel, angles, n_parts):
-    if angles is None:
+def _params(N, bounces, P0, dist_au, eps_rel, angles, n_parts, offsets=None):
+    """Sun tracking (no angles), commanded angles, or tracking + offsets."""
+    if angles is not None and offsets is not None:
+        raise ValueError("give commanded angles or tracking offsets, not both")
+    if angles is None and offsets is None:
         return _Params(N, bounces, P0, dist_au, eps_rel, 1, None), None
-    a = np.ascontiguousarray(np.asarray(angles, np.float64).reshape(n_parts))
-    return _Params(N, bounces, P0, dist_au, eps_rel, 0, _dp(a)), a
+    a = np.ascontiguousarray(np.asarray(angles if offsets is None else offsets, np.float64).reshape(n_parts))
+    return _Params(N, bounces, P0, dist_au, eps_rel, 0 if offsets is None else 2, _dp(a)), a
 
 
-def pose(mesh, s, angles=None):
-    """(joint angles [P], posed vertices [V,3]) for Sun direction s (Sec. 4.4.2)."""
+def pose(mesh, s, angles=None, offsets=None):
+    """(joint angles [P], posed vertices [V,3]) for Sun direction s (Sec. 4.4.2):
+    tracking, commanded `angles`, or tracking plus `offsets`."""
     om = OMesh(mesh)
     s = np.ascontiguousarray(np.asarray(s, np.float64))
     ang = np.zeros(om.n_parts)
     xyz = np.zeros_like(om.keep["xyz"])
-    a_in = None if angles is None else np.ascontiguousarray(np.asarray(angles, np.float64))
-    rc = lib().orc_pose(C.byref(om.s), _dp(s), C.c_int32(0 if angles is not None else 1),
-                        _dp(a_in) if a_in is not None else None, _dp(ang), _dp(xyz))
+    p, a_in = _params(1, 0, 0.0, 1.0, 0.0, angles, om.n_parts, offsets)
+    rc = lib().orc_pose(C.byref(om.s), _dp(s), C.c_int32(p.track), _dp(a_in) if a_in is not None else None,
+                        _dp(ang), _dp(xyz))
     if rc != 0:
         raise ValueError(f"orc_pose failed: {rc}")
     return ang, xyz
 
 
 def eval_range(mesh, s, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None, r0=0, r1=None,
-               want_hits=False, want_edge=False, _om=None):
+               want_hits=False, want_edge=False, _om=None, offsets=None):
     """Trace rays [r0, r1) of one direction.  Returns a dict with the unscaled
     sums `acc` (6), the `scale` P dA, the window `win` (8), joint `angles`,
     per-segment hit counts `nhit`, and optionally `hits` / `edge` per ray."""
     om = _om or OMesh(mesh)
     r1 = N * N if r1 is None else r1
-    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts)
+    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts, offsets)
     s = np.ascontiguousarray(np.asarray(s, np.float64))
     acc = np.zeros(6)
     scale = np.zeros(1)
@@ -160,14 +166,14 @@ def _worker(args):
 
 
 def evaluate(mesh, s, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None, want_hits=False,
-             want_edge=False, procs=1, chunks=None):
+             want_edge=False, procs=1, chunks=None, offsets=None):
     """Force F (N) and torque T (N m) about c_ref for one Sun direction.
 
     With procs > 1 the ray range is split into contiguous chunks traced by
     spawn-started worker processes (each single-threaded); the partial sums
     are added in chunk order, so the result does not depend on scheduling."""
     kw = dict(N=N, bounces=bounces, P0=P0, dist_au=dist_au, eps_rel=eps_rel, angles=angles,
-              want_hits=want_hits, want_edge=want_edge)
+              want_hits=want_hits, want_edge=want_edge, offsets=offsets)
     R = N * N
     if procs <= 1:
         parts = [eval_range(mesh, s, **kw)]
@@ -228,6 +234,97 @@ def timed_rays(mesh, s, N, bounces, n_rays, seed=0, P0=4.56e-6, dist_au=1.0, eps
     if rc != 0:
         raise ValueError(f"orc_eval_rays failed: {rc}")
     return dt, len(rays)
+
+
+# ------------------------------------------------------- frozen-hit gradients
+def window_ids(mesh, s, angles=None, offsets=None):
+    """The four posed vertices extreme along u and v for unit Sun direction s
+    (argmin u, argmax u, argmin v, argmax v; lowest index among equals)."""
+    om = OMesh(mesh)
+    p, keep = _params(1, 0, 0.0, 1.0, 0.0, angles, om.n_parts, offsets)
+    ids = np.zeros(4, np.int32)
+    s = np.ascontiguousarray(np.asarray(s, np.float64))
+    rc = lib().orc_window_ids(C.byref(om.s), C.byref(p), _dp(s), _ip(ids))
+    if rc != 0:
+        raise ValueError(f"orc_window_ids failed: {rc}")
+    return ids
+
+
+def eval_frozen(mesh, s, hits, ids, N, bounces=1, P0=4.56e-6, dist_au=1.0, angles=None, offsets=None, mat=None,
+                _om=None):
+    """Force and torque of the frozen-hit function F_H (frozen_oracle.c) at Sun
+    direction s (any length), with optical coefficients `mat` [M, 2] in place
+    of the mesh's when given.  hits: [N*N, bounces+1] recorded ids."""
+    om = _om or OMesh(mesh)
+    ms = om.s
+    keepm = None
+    if mat is not None:
+        keepm = np.ascontiguousarray(np.asarray(mat, np.float64).reshape(-1, 2))
+        ms = _Mesh.from_buffer_copy(om.s)
+        ms.mat = _dp(keepm)
+    p, keep = _params(N, bounces, P0, dist_au, 0.0, angles, om.n_parts, offsets)
+    hits = np.ascontiguousarray(np.asarray(hits, np.int32).reshape(N * N, bounces + 1))
+    ids = np.ascontiguousarray(np.asarray(ids, np.int32))
+    s = np.ascontiguousarray(np.asarray(s, np.float64))
+    acc, scale = np.zeros(6), np.zeros(1)
+    rc = lib().orc_eval_frozen(C.byref(ms), C.byref(p), _dp(s), C.c_int64(0), C.c_int64(N * N), _ip(hits), _ip(ids),
+                               _dp(acc), _dp(scale))
+    if rc != 0:
+        raise ValueError(f"orc_eval_frozen failed: {rc}")
+    return acc[:3] * scale[0], acc[3:] * scale[0]
+
+
+def frozen_grad(mesh, s, N, bounces, gF, gT, dist_au=1.0, P0=4.56e-6, eps_rel=1e-9, angles=None, offsets=None,
+                h=1e-6, procs=1):
+    """Reference gradient: central differences, step h, of the scalar
+    L = gF . F_H + gT . T_H with respect to every optical coefficient, every
+    joint angle parameter (commanded angle, or offset from the tracking angle;
+    tracking alone is read as offsets of zero), the three components of the
+    Sun direction s and the Sun distance.  The hit set and window vertices are
+    recorded by the traced oracle at the base point.
+    Returns dict(mat [M, 2], angle [P], sun [3], dist, F, T, hits, ids)."""
+    om = OMesh(mesh)
+    P = om.n_parts
+    if angles is None and offsets is None:
+        offsets = np.zeros(P)
+    s = np.asarray(s, np.float64)
+    base = evaluate(mesh, s, N, bounces, P0=P0, dist_au=dist_au, eps_rel=eps_rel, angles=angles, offsets=offsets,
+                    want_hits=True, procs=procs)
+    hits = base["hits"]
+    ids = window_ids(mesh, s, angles=angles, offsets=offsets)
+    gF, gT = np.asarray(gF, np.float64), np.asarray(gT, np.float64)
+    mat0 = np.asarray(mesh.mat, np.float64).reshape(-1, 2)
+
+    def L(s_=s, dist=dist_au, ang=angles, off=offsets, mat=None):
+        F, T = eval_frozen(mesh, s_, hits, ids, N, bounces, P0, dist, angles=ang, offsets=off, mat=mat, _om=om)
+        return float(gF @ F + gT @ T)
+
+    g_mat = np.zeros_like(mat0)
+    for i in range(mat0.shape[0]):
+        for c in range(2):
+            mp, mm = mat0.copy(), mat0.copy()
+            mp[i, c] += h
+            mm[i, c] -= h
+            g_mat[i, c] = (L(mat=mp) - L(mat=mm)) / (2 * h)
+    g_ang = np.zeros(P)
+    for q in range(P):
+        if angles is not None:
+            ap, am = np.array(angles, np.float64), np.array(angles, np.float64)
+            ap[q] += h
+            am[q] -= h
+            g_ang[q] = (L(ang=ap) - L(ang=am)) / (2 * h)
+        else:
+            op, omn = np.array(offsets, np.float64), np.array(offsets, np.float64)
+            op[q] += h
+            omn[q] -= h
+            g_ang[q] = (L(off=op) - L(off=omn)) / (2 * h)
+    g_sun = np.zeros(3)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        g_sun[k] = (L(s_=s + e) - L(s_=s - e)) / (2 * h)
+    g_dist = (L(dist=dist_au + h) - L(dist=dist_au - h)) / (2 * h)
+    return dict(mat=g_mat, angle=g_ang, sun=g_sun, dist=g_dist, F=base["F"], T=base["T"], hits=hits, ids=ids)
 
 
 # --------------------------------------------------------------- propagation

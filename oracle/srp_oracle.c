@@ -112,7 +112,8 @@ void orc_onb(const double n[3], double b1[3], double b2[3])
  * a joint moves its whole subtree.  Sec. 4.4.2: for a movable joint the angle
  * brings the panel normal as close as possible to s (step 3), then is clamped
  * to the joint's interval (step 4); the transform is applied to every vertex of
- * the subtree (step 5).  A commanded angle (track == 0) is clamped the same way.
+ * the subtree (step 5).  A commanded angle (track == 0) is clamped the same way;
+ * track == 2 adds angles_in[p] to the tracking angle before the clamp.
  * Returns ORC_ERR_MESH when a vertex is shared by two parts or the part order
  * is not topological.
  */
@@ -141,6 +142,7 @@ int orc_pose(const orc_mesh *m, const double s[3], int32_t track, const double *
                 cross3(a, n, b);
                 double x = dot3(n, sl), y = dot3(b, sl);
                 th = (x == 0.0 && y == 0.0) ? 0.0 : atan2(y, x);
+                if (track == 2 && angles_in) th += angles_in[p]; /* offset from the tracking angle */
             } else {
                 th = angles_in ? angles_in[p] : 0.0;
             }

@@ -37,8 +37,8 @@ typedef struct {
     double P0;               /* radiation pressure at 1 AU, N/m^2               */
     double dist_au;          /* Sun distance, AU (pressure scales as 1/r^2)     */
     double eps_rel;          /* self-hit threshold, relative to window diagonal */
-    int32_t track;           /* 1: Sun-tracking joint angles; 0: angles[]       */
-    const double *angles;    /* [n_parts] commanded angles when track == 0      */
+    int32_t track;           /* 1: Sun tracking; 0: angles[]; 2: tracking + angles[] */
+    const double *angles;    /* [n_parts] commanded angles (0) or offsets (2)   */
 } orc_params;
 
 
