@@ -288,10 +288,11 @@ def frozen_grad(mesh, s, N, bounces, gF, gT, dist_au=1.0, P0=4.56e-6, eps_rel=1e
     if angles is None and offsets is None:
         offsets = np.zeros(P)
     s = np.asarray(s, np.float64)
-    base = evaluate(mesh, s, N, bounces, P0=P0, dist_au=dist_au, eps_rel=eps_rel, angles=angles, offsets=offsets,
-                    want_hits=True, procs=procs)
+    s_unit = s / np.linalg.norm(s)  # the traced oracle takes a unit vector; F_H normalises itself
+    base = evaluate(mesh, s_unit, N, bounces, P0=P0, dist_au=dist_au, eps_rel=eps_rel, angles=angles,
+                    offsets=offsets, want_hits=True, procs=procs)
     hits = base["hits"]
-    ids = window_ids(mesh, s, angles=angles, offsets=offsets)
+    ids = window_ids(mesh, s_unit, angles=angles, offsets=offsets)
     gF, gT = np.asarray(gF, np.float64), np.asarray(gT, np.float64)
     mat0 = np.asarray(mesh.mat, np.float64).reshape(-1, 2)
 

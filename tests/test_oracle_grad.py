@@ -153,3 +153,20 @@ def test_clamped_joint_has_no_offset_gradient():
     s = np.array([math.sin(0.9), 0.0, math.cos(0.9)])  # tracking wants 0.9 rad: clamped at 0.2
     g = O.frozen_grad(m, s, 16, 1, np.array([1.0, 0.5, -0.3]), np.array([0.2, -0.1, 0.4]))
     assert g["angle"][1] == 0.0
+
+
+def test_sun_direction_length_is_irrelevant():
+    """F_H(lambda s) = F_H(s): the gradient in s at lambda s is the gradient at
+    s divided by lambda, and every other gradient is unchanged."""
+    m = I.box_wing()
+    s = I.sun_dirs_uniform(4, seed=6)[2]
+    gF, gT = np.array([0.3, -1.0, 0.4]), np.array([0.5, 0.2, -0.7])
+    off = np.array([0.0, 0.1, -0.05])
+    g1 = O.frozen_grad(m, s, 24, 1, gF, gT, offsets=off)
+    g2 = O.frozen_grad(m, 2.5 * s, 24, 1, gF, gT, offsets=off)
+    sc = np.max(np.abs(g1["sun"]))
+    assert rel(g2["sun"] * 2.5, g1["sun"], sc) < 1e-8
+    assert rel(g2["angle"], g1["angle"], np.max(np.abs(g1["angle"]))) < 1e-8
+    assert rel(g2["mat"], g1["mat"], np.max(np.abs(g1["mat"]))) < 1e-8
+    # the radial component of the direction gradient vanishes
+    assert abs(g1["sun"] @ s) < 1e-6 * sc
