@@ -195,6 +195,54 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
 /* Counters of the last srp_eval_batch on ctx. */
 srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out);
 
+/*
+ * Replace the optical coefficients of a loaded mesh (the rho_s, rho_d per
+ * material of Sec. 4.3's per-hit momentum law); the geometry and its
+ * acceleration structure are kept.
+ *   mat [n_mats][2] host or device, n_mats == the mesh's material count.
+ * Errors: SRP_ERR_ARG (bad id, count mismatch, NULL), SRP_ERR_MESH (a
+ * coefficient outside [0, 1] or rho_s + rho_d above 1).
+ */
+srp_status srp_set_materials(srp_ctx *ctx, int32_t mesh_id, int32_t n_mats, const double *mat);
+
+/* ------------------------------------------------------------- gradients */
+/*
+ * Gradient of the SRP evaluation with its hit set frozen (reverse mode).
+ *
+ * For each direction k this runs srp_eval_batch's evaluation, recording every
+ * ray segment's hit triangle and the four posed vertices that bound the window
+ * (extreme along u and v).  Holding those fixed -- each segment meets the
+ * plane of its recorded triangle, the window spans the recorded vertices --
+ * force and torque are smooth in the optical coefficients, the joint angles,
+ * the Sun direction and the Sun distance (Sec. 4.3 momentum law, Sec. 4.4.2
+ * tracking and clamping, Sec. 6.1 window).  With the caller's cotangents the
+ * call returns the derivatives of
+ *     L = sum_k g_force[k] . F_k + g_torque[k] . T_k
+ * with respect to
+ *   g_sun    [n][3]  out: each sun_dir_body entry as given (before the
+ *                    normalisation; so g_sun[k] . sun_dir_body[k] = 0);
+ *   g_dist   [n]     out: each sun_dist_au entry (needs sun_dist_au; NULL skips);
+ *   g_mat    [n_mats][2] out: each material's (rho_s, rho_d), summed over k;
+ *   g_angle  [n_parts]   out: the joint parameter of each part, summed over k:
+ *                    the commanded angle (SRP_PANELS_SET) or the offset added
+ *                    to the tracking angle (SRP_PANELS_TRACK_OFFSET; for
+ *                    SRP_PANELS_TRACK the offset at 0).  Zero for rigid parts
+ *                    and for joints held at a limit of their interval.
+ * Sun tracking is differentiated: a tracking joint's angle moves with the Sun
+ * direction, and with the angles of the joints above it.
+ *   g_force, g_torque [n][3]  in: cotangents (host or device).
+ *   force, torque     [n][3]  out (may be NULL): the evaluation itself, equal
+ *                    to srp_eval_batch's.
+ * Any of g_sun, g_dist, g_mat, g_angle may be NULL.  An entry skipped with a
+ * negative distance contributes nothing and gets zero gradients.  The result
+ * is deterministic (every sum has a fixed order).
+ * Errors: as srp_eval_batch; SRP_ERR_ARG when g_force or g_torque is NULL.
+ */
+srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *params, int32_t n,
+                    const double *sun_dir_body, const double *sun_dist_au, const double *g_force,
+                    const double *g_torque, double *force, double *torque, double *g_sun, double *g_dist,
+                    double *g_mat, double *g_angle);
+
 /* ------------------------------------------------------------ propagation */
 #define SRP_RKF78 0           /* Fehlberg 7(8) embedded pair, adaptive step      */
 #define SRP_RK4 1             /* classical RK4, fixed step h0                    */

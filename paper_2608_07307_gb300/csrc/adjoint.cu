@@ -1,0 +1,482 @@
+// adjoint.cu -- reverse-mode derivative of one SRP evaluation with the hit set
+// frozen: each ray segment meets the plane of the triangle the trace recorded
+// for it, and the window spans the four vertices that were extreme, so the
+// force and torque are smooth functions of the optical coefficients, the joint
+// angles (hence the joint offsets and, through Sun tracking, the Sun
+// direction), the Sun direction and the Sun distance (Sec. 4.3, 4.4.2, 6.1).
+//
+//   k_adj_window  one block per slot: the posed vertices extreme along u and v
+//                 (lowest vertex index among equal projections).
+//   k_adj_rays    grid-stride over the rays of every slot: per ray, the
+//                 segments are replayed forward in FP64 from the recorded hits,
+//                 then swept backward; cotangents of the ray direction, the
+//                 basis, the window bounds and the local loss stay in
+//                 registers; per-coefficient and per-part terms are summed
+//                 over the warp for each distinct key (fixed butterfly) and
+//                 added by one lane into the warp's own shared-memory row.
+//                 Every sum has a fixed order: the result is deterministic.
+//   k_adj_finish  one block per slot: the block partials are added in block
+//                 order, then one thread chains window -> vertices, basis ->
+//                 direction, joint rotations -> angles, Sun tracking ->
+//                 direction, normalisation -> the direction as given.
+//   k_adj_sum     coefficient and angle gradients summed over the batch in
+//                 evaluation order.
+//
+// Scalar loss per evaluation: L = g_F . F + g_T . T, F = scale * A_pix * sum f,
+// per segment f = w [(1 - rho_s) d - 2 (rho_s c + rho_d / 3) n_f],
+// T = scale * A_pix * sum (x - c_ref) x f.
+#include <math.h>
+
+#include <algorithm>
+
+#include "srp_internal.cuh"
+
+namespace srp {
+
+namespace {
+
+constexpr int kAdjThreads = 256;
+constexpr int kAdjWarps = kAdjThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct V3 {
+    double x, y, z;
+};
+__device__ inline V3 v3(double x, double y, double z) { return {x, y, z}; }
+__device__ inline V3 ld3(const double *p) { return {p[0], p[1], p[2]}; }
+__device__ inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ inline V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ inline V3 &operator+=(V3 &a, V3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
+__device__ inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ inline V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+__device__ inline V3 mat_mul(const double *M, V3 x)
+{
+    return {M[0] * x.x + M[1] * x.y + M[2] * x.z, M[3] * x.x + M[4] * x.y + M[5] * x.z,
+            M[6] * x.x + M[7] * x.y + M[8] * x.z};
+}
+__device__ inline V3 mat_tmul(const double *M, V3 x)
+{
+    return {M[0] * x.x + M[3] * x.y + M[6] * x.z, M[1] * x.x + M[4] * x.y + M[7] * x.z,
+            M[2] * x.x + M[5] * x.y + M[8] * x.z};
+}
+
+__device__ inline double wsum(double x)
+{
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+// posed FP64 position of (re-indexed) vertex v in slot s
+__device__ inline V3 vertex(const MeshDev &m, const SlotBufs &sb, int s, int v)
+{
+    const PartInfo &pi = m.part[m.vert_part[v]];
+    if (!pi.dynamic) return ld3(m.rest64 + 3 * (size_t)v);
+    return ld3(sb.vert64 + ((size_t)s * m.n_dyn_verts + (v - pi.vert_begin + pi.dyn_vert_off)) * 3);
+}
+
+// Add val[0..n) of the lanes holding `key` (>= 0) into row[key * n ..], for
+// every distinct key in the warp: masked butterfly sums, one writer (lane 0).
+template <int n>
+__device__ inline void warp_scatter(int key, const double *val, double *row)
+{
+    unsigned todo = __ballot_sync(kFull, key >= 0);
+    while (todo) {
+        int k = __shfl_sync(kFull, key, __ffs(todo) - 1);
+        bool mine = key == k;
+        double sum[n];
+#pragma unroll
+        for (int c = 0; c < n; c++) sum[c] = wsum(mine ? val[c] : 0.0);
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int c = 0; c < n; c++) row[k * n + c] += sum[c];
+        }
+        todo &= ~__ballot_sync(kFull, mine);
+    }
+}
+
+// ------------------------------------------------------------- window
+__global__ void __launch_bounds__(kAdjThreads) k_adj_window(AdjArgs a)
+{
+    const int s = blockIdx.x;
+    const SlotPose &P = a.pose[s];
+    if (P.skip) return;
+    const MeshDev &m = *a.mesh_d;
+    V3 u = ld3(P.u), v = ld3(P.v);
+    double best[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
+    int id[4] = {-1, -1, -1, -1};
+    for (int k = threadIdx.x; k < m.n_verts; k += blockDim.x) {  // ascending k per thread
+        V3 x = vertex(m, a.slot, s, k);
+        double pu = dot(u, x), pv = dot(v, x);
+        if (pu < best[0]) { best[0] = pu; id[0] = k; }
+        if (pu > best[1]) { best[1] = pu; id[1] = k; }
+        if (pv < best[2]) { best[2] = pv; id[2] = k; }
+        if (pv > best[3]) { best[3] = pv; id[3] = k; }
+    }
+    __shared__ double sb[4][kAdjThreads];
+    __shared__ int si[4][kAdjThreads];
+    for (int c = 0; c < 4; c++) { sb[c][threadIdx.x] = best[c]; si[c][threadIdx.x] = id[c]; }
+    __syncthreads();
+    for (int h = kAdjThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            for (int c = 0; c < 4; c++) {
+                double b0 = sb[c][threadIdx.x], b1 = sb[c][threadIdx.x + h];
+                int i0 = si[c][threadIdx.x], i1 = si[c][threadIdx.x + h];
+                bool take = (c & 1) ? (b1 > b0) : (b1 < b0);
+                if (i1 >= 0 && (i0 < 0 || take || (b1 == b0 && i1 < i0))) {
+                    sb[c][threadIdx.x] = b1;
+                    si[c][threadIdx.x] = i1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) a.win_ids[4 * s + threadIdx.x] = si[threadIdx.x][0];
+}
+
+// --------------------------------------------------------------- rays
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
+{
+    const int s = blockIdx.y;
+    const SlotPose &P = a.pose[s];
+    if (P.skip) return;
+    const MeshDev &m = *a.mesh_d;
+    const int e = a.eval0 + s, N = a.N, nseg = a.nseg;
+    const int W = a.width, nm2 = 2 * a.n_mats;
+    extern __shared__ double sh[];  // [kAdjWarps][W]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *row = sh + (size_t)warp * W;
+    for (int k = lane; k < W; k += 32) row[k] = 0.0;
+    __syncwarp();
+    __shared__ double win[4];
+    if (threadIdx.x < 4) {
+        int vi = a.win_ids[4 * s + threadIdx.x];
+        V3 x = vertex(m, a.slot, s, vi);
+        win[threadIdx.x] = dot(threadIdx.x < 2 ? ld3(P.u) : ld3(P.v), x);
+    }
+    __syncthreads();
+    const V3 u = ld3(P.u), v = ld3(P.v), d0 = ld3(P.d), cref = ld3(m.c_ref);
+    const V3 gF = ld3(a.g_force + 3 * (size_t)e), gT = ld3(a.g_torque + 3 * (size_t)e);
+    const double umin = win[0], umax = win[1], vmin = win[2], vmax = win[3];
+    const double Du = (umax - umin) / N, Dv = (vmax - vmin) / N;
+    const size_t R = (size_t)N * N;
+    V3 acc_d = v3(0, 0, 0), acc_u = v3(0, 0, 0), acc_v = v3(0, 0, 0);
+    double acc_w[4] = {0, 0, 0, 0}, acc_l = 0.0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of iterations (warp_scatter needs the whole warp)
+    const size_t iters = (R + stride - 1) / stride;
+    for (size_t it = 0; it < iters; it++) {
+        const size_t ray = it * stride + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const bool live = ray < R;
+        int tri[kMaxBounces + 1];
+        int nh = 0;
+        if (live) {
+            const int32_t *hq = a.hits + ((size_t)s * R + ray) * nseg;
+            for (int k = 0; k < nseg; k++) {
+                int h = hq[k];
+                if (h < 0) break;
+                tri[nh++] = m.tri_pos[h];
+            }
+        }
+        const int i = live ? (int)(ray / N) : 0, j = live ? (int)(ray % N) : 0;
+        const double al = (i + 0.5) / N, be = (j + 0.5) / N;
+        const double uc = umin + (i + 0.5) * Du, vc = vmin + (j + 0.5) * Dv;
+        // forward replay: origin, direction and weight entering each segment
+        V3 so[kMaxBounces + 1], sd[kMaxBounces + 1];
+        double sw[kMaxBounces + 1];
+        {
+            V3 o = uc * u + vc * v, d = d0;
+            double w = 1.0;
+            for (int k = 0; k < nh; k++) {
+                so[k] = o; sd[k] = d; sw[k] = w;
+                int4 tv = m.tri_v4[tri[k]];
+                V3 A = vertex(m, a.slot, s, tv.x), B = vertex(m, a.slot, s, tv.y), C = vertex(m, a.slot, s, tv.z);
+                V3 n = cross(B - A, C - A);
+                n = (1.0 / sqrt(dot(n, n))) * n;
+                double dn = dot(d, n);
+                double t = dot(n, A - o) / dn;
+                V3 x = o + t * d;
+                unsigned mp = m.tri_mat[tri[k]];
+                int mi = dn < 0.0 ? (int)(mp & 0xffffu) : (int)(mp >> 16);
+                w *= m.mat64[2 * mi];
+                d = d - (2.0 * dn) * n;
+                o = x;
+            }
+        }
+        // backward sweep, uniform over the warp
+        V3 ob = v3(0, 0, 0), db = v3(0, 0, 0);
+        double wb = 0.0;
+        for (int k = nseg - 1; k >= 0; k--) {
+            const bool act = k < nh;
+            int mkey = -1, pkey = -1;
+            double mval[2] = {0.0, 0.0}, pval[6] = {0, 0, 0, 0, 0, 0};
+            if (act) {
+                const V3 o = so[k], d = sd[k];
+                const double w = sw[k];
+                const int4 tv = m.tri_v4[tri[k]];
+                const V3 A = vertex(m, a.slot, s, tv.x), B = vertex(m, a.slot, s, tv.y), C = vertex(m, a.slot, s, tv.z);
+                const V3 e1 = B - A, e2 = C - A, mr = cross(e1, e2);
+                const double ml = sqrt(dot(mr, mr));
+                const V3 n = (1.0 / ml) * mr;
+                const double dn = dot(d, n);
+                const V3 ao = A - o;
+                const double t = dot(n, ao) / dn;
+                const V3 x = o + t * d;
+                const unsigned mp = m.tri_mat[tri[k]];
+                const bool front = dn < 0.0;
+                const int mi = front ? (int)(mp & 0xffffu) : (int)(mp >> 16);
+                const double rs = m.mat64[2 * mi], rd = m.mat64[2 * mi + 1];
+                const double sg = front ? 1.0 : -1.0;
+                const V3 nf = sg * n;
+                const double c = -dot(nf, d);
+                const double kq = rs * c + rd / 3.0;
+                const V3 q = (1.0 - rs) * d - (2.0 * kq) * nf;
+                const V3 f = w * q;
+                const V3 r = x - cref;
+                acc_l += dot(gF, f) + dot(gT, cross(r, f));
+                // cotangents
+                const V3 fb = gF + cross(gT, r);
+                V3 xb = cross(f, gT) + ob;           // ob: cotangent of the next segment's origin (= x)
+                double wl = dot(fb, q);               // cotangent of w
+                const V3 qb = w * fb;
+                double rsb = dot(qb, -1.0 * d - (2.0 * c) * nf);
+                double rdb = -(2.0 / 3.0) * dot(qb, nf);
+                V3 dbl = (1.0 - rs) * qb;             // cotangent of d (this segment)
+                double cb = -2.0 * rs * dot(qb, nf);
+                V3 nfb = (-2.0 * kq) * qb;
+                double dnb = 0.0;
+                V3 nb = v3(0, 0, 0);
+                if (k + 1 < nh) {                     // the next segment's d' = d - 2 dn n and w' = w rho_s
+                    rsb += wb * w;
+                    wl += wb * rs;
+                    dbl += db;
+                    dnb += -2.0 * dot(db, n);
+                    nb += (-2.0 * dn) * db;
+                }
+                nfb += (-cb) * d;                     // c = -nf . d
+                dbl += (-cb) * nf;
+                nb += sg * nfb;
+                V3 obl = xb;                          // x = o + t d
+                const double tb = dot(xb, d);
+                dbl += t * xb;
+                const double naob = tb / dn;          // t = (n . ao) / dn
+                dnb += -tb * t / dn;
+                nb += naob * ao;
+                V3 Ab = naob * n;
+                obl += (-naob) * n;
+                dbl += dnb * n;                       // dn = d . n
+                nb += dnb * d;
+                const V3 mb = (1.0 / ml) * (nb - dot(nb, n) * n);
+                const V3 e1b = cross(e2, mb), e2b = cross(mb, e1);
+                const V3 Bb = e1b, Cb = e2b;
+                Ab += -1.0 * (e1b + e2b);
+                mkey = mi;
+                mval[0] = rsb;
+                mval[1] = rdb;
+                const int pp = m.vert_part[tv.x];
+                if (m.part[pp].dynamic) {
+                    pkey = pp;
+                    V3 G = Ab + Bb + Cb, Mm = cross(A, Ab) + cross(B, Bb) + cross(C, Cb);
+                    pval[0] = G.x; pval[1] = G.y; pval[2] = G.z;
+                    pval[3] = Mm.x; pval[4] = Mm.y; pval[5] = Mm.z;
+                }
+                ob = obl;
+                db = dbl;
+                wb = wl;
+            }
+            warp_scatter<2>(mkey, mval, row + kAdjFixed);
+            warp_scatter<6>(pkey, pval, row + kAdjFixed + nm2);
+        }
+        if (nh > 0) {
+            // primary origin o = uc u + vc v (its component along d does not move the hit point)
+            acc_d += db;
+            acc_u += uc * ob;
+            acc_v += vc * ob;
+            const double ucb = dot(u, ob), vcb = dot(v, ob);
+            acc_w[0] += (1.0 - al) * ucb;
+            acc_w[1] += al * ucb;
+            acc_w[2] += (1.0 - be) * vcb;
+            acc_w[3] += be * vcb;
+        }
+    }
+    double fix[kAdjFixed] = {acc_d.x, acc_d.y, acc_d.z, acc_u.x, acc_u.y, acc_u.z, acc_v.x, acc_v.y, acc_v.z,
+                             acc_w[0], acc_w[1], acc_w[2], acc_w[3], acc_l};
+#pragma unroll
+    for (int c = 0; c < kAdjFixed; c++) {
+        double x = wsum(fix[c]);
+        if (lane == 0) row[c] += x;
+    }
+    __syncthreads();
+    double *out = a.partials + ((size_t)s * a.nb + blockIdx.x) * W;
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+        double x = 0.0;
+        for (int w = 0; w < kAdjWarps; w++) x += sh[(size_t)w * W + k];
+        out[k] = x;
+    }
+}
+
+// -------------------------------------------------------------- finish
+__global__ void __launch_bounds__(128) k_adj_finish(AdjArgs a)
+{
+    const int s = blockIdx.x;
+    const SlotPose &P = a.pose[s];
+    const MeshDev &m = *a.mesh_d;
+    const int e = a.eval0 + s, W = a.width, nm2 = 2 * a.n_mats, np = a.n_parts;
+    double *ge = a.g_eval + (size_t)e * (nm2 + np);
+    if (P.skip) {
+        for (int k = threadIdx.x; k < nm2 + np; k += blockDim.x) ge[k] = 0.0;
+        if (threadIdx.x < 3) a.g_sun[3 * (size_t)e + threadIdx.x] = 0.0;
+        if (threadIdx.x == 0 && a.g_dist) a.g_dist[e] = 0.0;
+        return;
+    }
+    extern __shared__ double tot[];  // [W]
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+        double x = 0.0;
+        for (int b = 0; b < a.nb; b++) x += a.partials[((size_t)s * a.nb + b) * W + k];
+        tot[k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int N = a.N;
+    const int *ids = a.win_ids + 4 * s;
+    V3 X[4];
+    for (int c = 0; c < 4; c++) X[c] = vertex(m, a.slot, s, ids[c]);
+    V3 u = ld3(P.u), v = ld3(P.v), d = ld3(P.d), sh = ld3(P.s);
+    const double umin = dot(u, X[0]), umax = dot(u, X[1]), vmin = dot(v, X[2]), vmax = dot(v, X[3]);
+    const double area = (umax - umin) * (vmax - vmin) / ((double)N * N);
+    const double sc = P.scale * area;
+    const double Lsum = tot[13], L = sc * Lsum;
+    V3 db = sc * v3(tot[0], tot[1], tot[2]);
+    V3 ub = sc * v3(tot[3], tot[4], tot[5]);
+    V3 vb = sc * v3(tot[6], tot[7], tot[8]);
+    double wb[4] = {sc * tot[9], sc * tot[10], sc * tot[11], sc * tot[12]};
+    // pixel area: A_pix = (umax - umin)(vmax - vmin) / N^2
+    const double kA = P.scale * Lsum / ((double)N * N);
+    wb[0] -= kA * (vmax - vmin);
+    wb[1] += kA * (vmax - vmin);
+    wb[2] -= kA * (umax - umin);
+    wb[3] += kA * (umax - umin);
+    // part accumulators: G = sum of vertex cotangents, M = sum of x cross cotangent
+    double G[kMaxParts][3], Mx[kMaxParts][3];
+    for (int p = 0; p < np; p++)
+        for (int c = 0; c < 3; c++) {
+            G[p][c] = sc * tot[kAdjFixed + nm2 + 6 * p + c];
+            Mx[p][c] = sc * tot[kAdjFixed + nm2 + 6 * p + 3 + c];
+        }
+    // window bounds: umin = u . X0, umax = u . X1, vmin = v . X2, vmax = v . X3
+    for (int c = 0; c < 4; c++) {
+        const V3 ax = c < 2 ? u : v;
+        if (c < 2) ub += wb[c] * X[c]; else vb += wb[c] * X[c];
+        const int p = m.vert_part[ids[c]];
+        if (m.part[p].dynamic) {
+            const V3 g = wb[c] * ax, mm = cross(X[c], g);
+            G[p][0] += g.x; G[p][1] += g.y; G[p][2] += g.z;
+            Mx[p][0] += mm.x; Mx[p][1] += mm.y; Mx[p][2] += mm.z;
+        }
+    }
+    // joint angles: a rotation d theta of joint q moves every vertex of its
+    // subtree by (a_q x (x - p_q)) d theta, a_q and p_q the axis and pivot in
+    // the body frame, so dL/dtheta_q = a_q . sum over the subtree (M - p_q x G)
+    double thb[kMaxParts];
+    for (int q = 0; q < np; q++) {
+        thb[q] = 0.0;
+        const PartInfo &pq = m.part[q];
+        if (!pq.movable) continue;
+        const int par = pq.parent;
+        const V3 aw = mat_mul(P.M[par], ld3(pq.axis));
+        const V3 pw = mat_mul(P.M[par], ld3(pq.pivot)) + ld3(P.T[par]);
+        V3 Gs = v3(0, 0, 0), Ms = v3(0, 0, 0);
+        for (int p = 0; p < np; p++) {
+            int x = p;
+            while (x > q) x = m.part[x].parent;
+            if (x != q) continue;
+            Gs += v3(G[p][0], G[p][1], G[p][2]);
+            Ms += v3(Mx[p][0], Mx[p][1], Mx[p][2]);
+        }
+        thb[q] = dot(aw, Ms - cross(pw, Gs));
+    }
+    // Sun tracking, children first: theta_q = atan2(b . s', n . s') (+ offset),
+    // s' = M_parent^T s; s' also turns with every movable ancestor of q
+    V3 shb = v3(0, 0, 0);
+    for (int q = np - 1; q >= 1; q--) {
+        const PartInfo &pq = m.part[q];
+        const bool free = (P.free_mask >> q) & 1u;
+        ge[nm2 + q] = free ? thb[q] : 0.0;
+        if (!free || !((P.track_mask >> q) & 1u) || a.panel_mode == SRP_PANELS_SET) continue;
+        const int par = pq.parent;
+        const V3 ax = ld3(pq.axis), n0 = ld3(pq.n0);
+        const V3 nn = n0 - dot(n0, ax) * ax;
+        const V3 bb = cross(ax, nn);
+        const V3 sl = mat_tmul(P.M[par], sh);
+        const double x = dot(nn, sl), y = dot(bb, sl), den = x * x + y * y;
+        const V3 slb = (thb[q] / den) * (x * bb - y * nn);
+        const V3 g = mat_mul(P.M[par], slb);  // cotangent of s through s'
+        shb += g;
+        for (int an = par; an > 0; an = m.part[an].parent) {
+            const PartInfo &pa = m.part[an];
+            if (!pa.movable || !((P.free_mask >> an) & 1u)) continue;
+            const V3 aw = mat_mul(P.M[pa.parent], ld3(pa.axis));
+            thb[an] += -dot(g, cross(aw, sh));
+        }
+    }
+    ge[nm2 + 0] = 0.0;
+    for (int k = 0; k < nm2; k++) ge[k] = sc * tot[kAdjFixed + k];
+    // basis (u, v) of the plane normal to d (Duff et al., JCGT 2017), differentiated
+    {
+        const double sg = copysign(1.0, d.z);
+        const double aa = -1.0 / (sg + d.z);
+        const double bbv = sg * ub.y + vb.x;              // cotangent of b = dx dy a
+        const double ab = sg * d.x * d.x * ub.x + d.y * d.y * vb.y + bbv * d.x * d.y;
+        db.x += 2.0 * sg * d.x * aa * ub.x - sg * ub.z + bbv * d.y * aa;
+        db.y += 2.0 * d.y * aa * vb.y - vb.z + bbv * d.x * aa;
+        db.z += ab * aa * aa;
+    }
+    // d = -s_hat, s_hat = s / |s|
+    shb += -1.0 * db;
+    const V3 gs = (1.0 / P.s_norm) * (shb - dot(shb, sh) * sh);
+    a.g_sun[3 * (size_t)e] = gs.x;
+    a.g_sun[3 * (size_t)e + 1] = gs.y;
+    a.g_sun[3 * (size_t)e + 2] = gs.z;
+    if (a.g_dist) a.g_dist[e] = -2.0 * L / a.sun_dist[e];  // pressure P0 / dist^2
+}
+
+__global__ void k_adj_sum(const double *g_eval, int n, int width, double *g_mat, int nm2, double *g_angle)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= width) return;
+    double x = 0.0;
+    for (int e = 0; e < n; e++) x += g_eval[(size_t)e * width + k];
+    if (k < nm2) {
+        if (g_mat) g_mat[k] = x;
+    } else if (g_angle) {
+        g_angle[k - nm2] = x;
+    }
+}
+
+}  // namespace
+
+int adj_blocks(int S, size_t rays)
+{
+    size_t need = (rays + kAdjThreads - 1) / kAdjThreads;
+    size_t cap = (size_t)std::max(1, 4 * 152 / std::max(S, 1));
+    return (int)std::max<size_t>(1, std::min(need, cap));
+}
+
+cudaError_t launch_adjoint(const AdjArgs &a, int S, cudaStream_t st)
+{
+    k_adj_window<<<S, kAdjThreads, 0, st>>>(a);
+    size_t smem = sizeof(double) * (size_t)kAdjWarps * a.width;
+    k_adj_rays<<<dim3(a.nb, S), kAdjThreads, smem, st>>>(a);
+    k_adj_finish<<<S, 128, sizeof(double) * a.width, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_sum(const double *g_eval, int n, int n_mats, int n_parts, double *g_mat, double *g_angle,
+                           cudaStream_t st)
+{
+    int width = 2 * n_mats + n_parts;
+    k_adj_sum<<<(width + 127) / 128, 128, 0, st>>>(g_eval, n, width, g_mat, 2 * n_mats, g_angle);
+    return cudaGetLastError();
+}
+
+}  // namespace srp

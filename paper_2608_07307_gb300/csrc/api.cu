@@ -72,6 +72,13 @@ struct srp_ctx {
     double *prop_replay = nullptr;
     size_t prop_replay_cap = 0;
     int *prop_done = nullptr;
+    // adjoint
+    double *adj_partials = nullptr;
+    size_t adj_partials_cap = 0;
+    int *win_ids = nullptr;
+    size_t win_ids_cap = 0;
+    double *gio = nullptr;
+    size_t gio_cap = 0;
     cudaStream_t lane[kLanes] = {};  // pipeline lanes (forked from / joined to `stream`)
     cudaEvent_t ev_fork = nullptr, ev_join[kLanes] = {};
 };
@@ -197,6 +204,14 @@ srp_status check_eval_params(srp_ctx *ctx, const srp_eval_params *prm)
 struct EvalPlan {
     int N, nseg, S, nchunks, lanes, nbx, nbr;
     size_t R, SL;
+    int nba = 0, wa = 0;  // adjoint: ray blocks per slot, doubles per block partial
+};
+
+// Adjoint inputs of one batch (device pointers); null for a plain evaluation.
+struct AdjBatch {
+    const double *sun, *dist, *gF, *gT;
+    double *g_sun, *g_dist, *g_eval;
+    int panel_mode;
 };
 
 // Phase timing with CUDA events recorded on the stream each phase runs on.
@@ -246,7 +261,8 @@ void fill_stats(srp_eval_stats &L, const unsigned long long *stats)
 }
 
 // Size the batch and grow every buffer it needs (may allocate; never inside a capture).
-srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, bool want_hits, EvalPlan &pl)
+srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, bool want_hits, EvalPlan &pl,
+                     bool adjoint = false)
 {
     pl.N = prm->N;
     pl.nseg = prm->bounces + 1;
@@ -275,7 +291,13 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
     CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * pl.nbx, false));
     CK(ctx, grow(&ctx->amb_off, &ctx->amb_off_cap, SL * (pl.nbx + 1), false));
-    if (want_hits) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
+    if (want_hits || adjoint) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
+    if (adjoint) {
+        pl.nba = adj_blocks(pl.S, pl.R);
+        pl.wa = kAdjFixed + 2 * m->h.n_mats + 6 * m->h.n_parts;
+        CK(ctx, grow(&ctx->adj_partials, &ctx->adj_partials_cap, SL * pl.nba * pl.wa, false));
+        CK(ctx, grow(&ctx->win_ids, &ctx->win_ids_cap, SL * 4, false));
+    }
     return SRP_OK;
 }
 
@@ -284,7 +306,8 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
 // synchronisation, so a stream capture can record it.
 srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const EvalPlan &pl, int n,
                         const double *d_sun, const double *d_dist, double *d_f, double *d_t, int32_t *hit_tri,
-                        bool h_dev, Timing &tm, int64_t &launches, int64_t &trace_launches)
+                        bool h_dev, Timing &tm, int64_t &launches, int64_t &trace_launches,
+                        const AdjBatch *adj = nullptr)
 {
     cudaStream_t st = ctx->stream;
     const int S = pl.S, nbx = pl.nbx, nbr = pl.nbr, nseg = pl.nseg;
@@ -325,7 +348,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         a.amb_off = ctx->amb_off + s0 * (nbx + 1);
         a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
-        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : nullptr;
+        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : (adj ? stage : nullptr);
         int g0 = tm.mark(ls);
         CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, pose, ls));
         CK(ctx, launch_vertices(m->d, h, pose, sb, Sc, ls));
@@ -343,6 +366,32 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         int g4 = tm.mark(ls);
         launches += 6;  // frame, trace, hand-off scan, refine, two reduction levels
         trace_launches++;
+        if (adj) {
+            AdjArgs g{};
+            g.mesh_d = m->d;
+            g.pose = pose;
+            g.slot = sb;
+            g.hits = a.hits;
+            g.sun_dirs = adj->sun;
+            g.sun_dist = adj->dist;
+            g.g_force = adj->gF;
+            g.g_torque = adj->gT;
+            g.N = pl.N;
+            g.nseg = nseg;
+            g.panel_mode = adj->panel_mode;
+            g.n_mats = h.n_mats;
+            g.n_parts = h.n_parts;
+            g.eval0 = e0;
+            g.nb = pl.nba;
+            g.width = pl.wa;
+            g.win_ids = ctx->win_ids + s0 * 4;
+            g.partials = ctx->adj_partials + s0 * pl.nba * pl.wa;
+            g.g_sun = adj->g_sun;
+            g.g_dist = adj->g_dist;
+            g.g_eval = adj->g_eval;
+            CK(ctx, launch_adjoint(g, Sc, ls));
+            launches += 3;  // window vertices, rays, finish
+        }
         tm.span(0, g0, g1);
         tm.span(1, g1, g2);
         tm.span(2, g2, g3);
@@ -464,6 +513,9 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->amb_off);
     cudaFree(ctx->io);
     cudaFree(ctx->hits);
+    cudaFree(ctx->adj_partials);
+    cudaFree(ctx->win_ids);
+    cudaFree(ctx->gio);
     cudaFree(ctx->err_flags);
     cudaFree(ctx->stats);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
@@ -643,6 +695,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     MK(dmalloc(m->allocs, &h.tri_vidx, (size_t)NT * 3));
     MK(dmalloc(m->allocs, &h.tri_v4, (size_t)NT));
     MK(dmalloc(m->allocs, &h.tri_orig, (size_t)NT));
+    MK(dmalloc(m->allocs, &h.tri_pos, (size_t)NT));
     MK(dmalloc(m->allocs, &h.tri_mat, (size_t)NT));
     MK(dmalloc(m->allocs, &h.leaf_parent, (size_t)NT));
     MK(dmalloc(m->allocs, &h.tri_static, (size_t)std::max(h.n_static_tris, 1) * 3));
@@ -701,6 +754,9 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     for (int k = 0; k < NT; k++) sv4[k] = make_int4(svidx[3 * (size_t)k], svidx[3 * (size_t)k + 1], svidx[3 * (size_t)k + 2], 0);
     MK(cudaMemcpyAsync(h.tri_v4, sv4.data(), sizeof(int4) * NT, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(h.tri_orig, sorig.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
+    std::vector<int> spos(NT);
+    for (int k = 0; k < NT; k++) spos[sorig[k]] = k;
+    MK(cudaMemcpyAsync(h.tri_pos, spos.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(h.tri_mat, smat.data(), sizeof(unsigned) * NT, cudaMemcpyHostToDevice, st));
     // 3: binary radix tree per part
     std::vector<int> ptb(NP), ptc(NP), pnb(NP), nodepart(std::max(nb, 1)), nodebase(std::max(nb, 1));
@@ -975,6 +1031,105 @@ srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out)
 {
     if (!ctx || !out) return SRP_ERR_ARG;
     *out = ctx->last;
+    return SRP_OK;
+}
+
+srp_status srp_set_materials(srp_ctx *ctx, int32_t mesh_id, int32_t n_mats, const double *mat)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_ARG, "bad mesh id %d", mesh_id);
+    if (!mat || n_mats != m->h.n_mats) return fail(ctx, SRP_ERR_ARG, "need %d materials", m->h.n_mats);
+    CK(ctx, cudaSetDevice(ctx->device));
+    std::vector<double> hm((size_t)2 * n_mats);
+    CK(ctx, cudaMemcpy(hm.data(), mat, sizeof(double) * hm.size(), cudaMemcpyDefault));
+    std::vector<float2> m32(n_mats);
+    for (int i = 0; i < n_mats; i++) {
+        double rs = hm[2 * i], rd = hm[2 * i + 1];
+        if (!(rs >= 0.0 && rd >= 0.0 && rs + rd <= 1.0 + 1e-12))
+            return fail(ctx, SRP_ERR_MESH, "material %d coefficients (%g, %g) outside [0,1] or sum > 1", i, rs, rd);
+        m32[i] = make_float2((float)rs, (float)rd);
+    }
+    cudaStream_t st = ctx->stream;
+    CK(ctx, cudaMemcpyAsync(m->h.mat32, m32.data(), sizeof(float2) * n_mats, cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaMemcpyAsync(m->h.mat64, hm.data(), sizeof(double) * hm.size(), cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    return SRP_OK;
+}
+
+srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, int32_t n, const double *sun_dir_body,
+                    const double *sun_dist_au, const double *g_force, const double *g_torque, double *force,
+                    double *torque, double *g_sun, double *g_dist, double *g_mat, double *g_angle)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
+    srp_status rc = check_eval_params(ctx, prm);
+    if (rc) return rc;
+    if (n < 0) return fail(ctx, SRP_ERR_ARG, "n < 0");
+    if (g_dist && !sun_dist_au) return fail(ctx, SRP_ERR_ARG, "g_dist needs sun_dist_au");
+    memset(&ctx->last, 0, sizeof ctx->last);
+    const int NM2 = 2 * m->h.n_mats, NP = m->h.n_parts, GE = NM2 + NP;
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    if (n == 0) {
+        // empty batch: the summed gradients are zero
+        std::vector<double> z((size_t)GE, 0.0);
+        if (g_mat) CK(ctx, cudaMemcpy(g_mat, z.data(), sizeof(double) * NM2, cudaMemcpyDefault));
+        if (g_angle) CK(ctx, cudaMemcpy(g_angle, z.data(), sizeof(double) * NP, cudaMemcpyDefault));
+        return SRP_OK;
+    }
+    if (!sun_dir_body || !g_force || !g_torque) return fail(ctx, SRP_ERR_ARG, "null input or cotangent");
+    EvalPlan pl;
+    rc = eval_plan(ctx, m, prm, n, false, pl, true);
+    if (rc) return rc;
+    // device staging: inputs, cotangents, outputs, per-evaluation terms, batch sums
+    const size_t n3 = (size_t)n * 3;
+    size_t off_sun = 0, off_dist = n3, off_gf = off_dist + n, off_gt = off_gf + n3, off_f = off_gt + n3,
+           off_t = off_f + n3, off_gs = off_t + n3, off_gd = off_gs + n3, off_ge = off_gd + n,
+           off_sum = off_ge + (size_t)n * GE, need = off_sum + GE;
+    CK(ctx, grow(&ctx->gio, &ctx->gio_cap, need, false));
+    double *G = ctx->gio;
+    struct In {
+        const double *src;
+        size_t off, count;
+    } ins[4] = {{sun_dir_body, off_sun, n3}, {sun_dist_au, off_dist, (size_t)n}, {g_force, off_gf, n3},
+                {g_torque, off_gt, n3}};
+    const double *dev[4];
+    for (int k = 0; k < 4; k++) {
+        if (!ins[k].src) { dev[k] = nullptr; continue; }
+        if (is_device_ptr(ins[k].src)) { dev[k] = ins[k].src; continue; }
+        CK(ctx, cudaMemcpyAsync(G + ins[k].off, ins[k].src, sizeof(double) * ins[k].count, cudaMemcpyHostToDevice, st));
+        dev[k] = G + ins[k].off;
+    }
+    CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
+    CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
+    AdjBatch ab{dev[0], dev[1], dev[2], dev[3], G + off_gs, g_dist ? G + off_gd : nullptr, G + off_ge, prm->panel_mode};
+    Timing tm(ctx, false);
+    int64_t launches = 0, trace_launches = 0;
+    rc = eval_enqueue(ctx, m, prm, pl, n, dev[0], dev[1], G + off_f, G + off_t, nullptr, false, tm, launches,
+                      trace_launches, &ab);
+    if (rc) return rc;
+    CK(ctx, launch_adj_sum(G + off_ge, n, m->h.n_mats, NP, G + off_sum, G + off_sum + NM2, st));
+    launches++;
+    struct Out {
+        double *dst;
+        size_t off, count;
+    } outs[6] = {{force, off_f, n3}, {torque, off_t, n3}, {g_sun, off_gs, n3}, {g_dist, off_gd, (size_t)n},
+                 {g_mat, off_sum, (size_t)NM2}, {g_angle, off_sum + NM2, (size_t)NP}};
+    for (auto &o : outs)
+        if (o.dst) CK(ctx, cudaMemcpyAsync(o.dst, G + o.off, sizeof(double) * o.count, cudaMemcpyDefault, st));
+    int flags = 0;
+    unsigned long long stats[16];
+    CK(ctx, cudaMemcpyAsync(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(stats, ctx->stats, sizeof stats, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    fill_stats(ctx->last, stats);
+    ctx->last.launches = launches;
+    ctx->last.trace_launches = trace_launches;
+    if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
     return SRP_OK;
 }
 

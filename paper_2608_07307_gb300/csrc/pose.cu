@@ -38,6 +38,9 @@ __global__ void k_pose(const MeshDev *mesh, const double *sun_dirs, const double
     double dist = sun_dist ? sun_dist[e] : 1.0;
     P.eval = e;
     P.flags = 0;
+    P.s_norm = sn;
+    P.free_mask = 0;
+    P.track_mask = 0;
     P.skip = dist < 0.0 ? 1 : 0;  // a negative distance asks to skip this evaluation
     if (P.skip) return;
     int np = mesh->n_parts;
@@ -65,10 +68,12 @@ __global__ void k_pose(const MeshDev *mesh, const double *sun_dirs, const double
                 double x = n[0] * sl[0] + n[1] * sl[1] + n[2] * sl[2];
                 double y = b[0] * sl[0] + b[1] * sl[1] + b[2] * sl[2];
                 th = (x == 0.0 && y == 0.0) ? 0.0 : atan2(y, x);
+                if (!(x == 0.0 && y == 0.0)) P.track_mask |= 1u << p;
                 if (panel_mode == SRP_PANELS_TRACK_OFFSET && angles) th += angles[p];
             } else {
                 th = angles ? angles[p] : 0.0;
             }
+            if (th > pi.lim[0] && th < pi.lim[1]) P.free_mask |= 1u << p;
             th = fmin(fmax(th, pi.lim[0]), pi.lim[1]);
         }
         P.angle[p] = th;

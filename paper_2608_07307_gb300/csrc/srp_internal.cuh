@@ -60,6 +60,9 @@ struct SlotPose {
     int eval;                 // evaluation index in the batch
     int flags;                // device error flags
     int skip;                 // evaluation skipped (negative Sun distance): every later kernel returns early
+    unsigned free_mask;       // bit p: joint p is movable and its angle lies strictly inside its limits
+    unsigned track_mask;      // bit p: joint p's angle follows the Sun (tracking, non-degenerate)
+    double s_norm;            // length of the Sun direction as given
 };
 
 // Per-slot traversal view built from SlotPose by each trace block.
@@ -84,6 +87,7 @@ struct MeshDev {
     int *tri_vidx;         // [n_tris][3] sorted triangles -> global vertex index
     int4 *tri_v4;          // [n_tris] the same, padded to one 16-byte load
     int *tri_orig;         // [n_tris] sorted -> original triangle id
+    int *tri_pos;          // [n_tris] original triangle id -> sorted position
     unsigned *tri_mat;     // [n_tris] sorted -> (front | back << 16)
     int *leaf_parent;      // [n_tris] sorted -> parent internal node (part-local), -1 for a single-leaf part
     float4 *tri_static;    // [n_static_tris][3]
@@ -201,6 +205,31 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st);
 cudaError_t launch_refine(const TraceArgs &a, int S, cudaStream_t st);
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
                           unsigned long long *stats_accum, cudaStream_t st);
+
+// adjoint.cu: reverse sweep of one evaluation with the hit set frozen
+struct AdjArgs {
+    const MeshDev *mesh_d;
+    const SlotPose *pose;        // [S]
+    SlotBufs slot;
+    const int32_t *hits;         // [S][N*N][nseg] original triangle ids recorded by the trace
+    const double *sun_dirs;      // [n][3] as given (device)
+    const double *sun_dist;      // [n] Sun distance (AU, device) when g_dist is wanted
+    const double *g_force;       // [n][3] cotangent of the force (device)
+    const double *g_torque;      // [n][3] cotangent of the torque (device)
+    int N, nseg, panel_mode, n_mats, n_parts, eval0;
+    int nb;                      // ray blocks per slot
+    int width;                   // doubles per block partial (kAdjFixed + 2 n_mats + 6 n_parts)
+    int *win_ids;                // [S][4] extreme vertices: argmin u, argmax u, argmin v, argmax v
+    double *partials;            // [S][nb][width]
+    double *g_sun;               // [n][3] out
+    double *g_dist;              // [n] out, or null
+    double *g_eval;              // [n][2 n_mats + n_parts] out: per-evaluation coefficient and angle terms
+};
+constexpr int kAdjFixed = 14;    // dbar(3) ubar(3) vbar(3) umin umax vmin vmax, sum of the local loss
+int adj_blocks(int S, size_t rays);
+cudaError_t launch_adjoint(const AdjArgs &a, int S, cudaStream_t st);
+cudaError_t launch_adj_sum(const double *g_eval, int n, int n_mats, int n_parts, double *g_mat, double *g_angle,
+                           cudaStream_t st);
 
 // prop.cu
 cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double *t01, double h0, int *n_done,

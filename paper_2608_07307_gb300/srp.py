@@ -25,7 +25,8 @@ MAX_BOUNCES = 4
 
 # Symbols declared in include/srp.h (checked by the tests against the library).
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",
-           "srp_eval_batch", "srp_eval_stats_get", "srp_propagate", "srp_eval_noalloc"]
+           "srp_eval_batch", "srp_eval_stats_get", "srp_propagate", "srp_eval_noalloc", "srp_set_materials",
+           "srp_grad"]
 
 
 class SrpError(RuntimeError):
@@ -103,6 +104,8 @@ def load(build_if_needed: bool = True):
         lib.srp_eval_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.srp_eval_stats_get.argtypes = [C.c_void_p, C.POINTER(EvalStats)]
+        lib.srp_set_materials.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
+        lib.srp_grad.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32] + [C.c_void_p] * 10
         lib.srp_propagate.argtypes = [C.c_void_p, C.c_int32, C.POINTER(PropParams), C.c_int32, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(PropStats), C.c_void_p, C.c_int64]
         lib.srp_eval_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
@@ -147,6 +150,14 @@ def _ptr(x):
     raise TypeError(f"unsupported array type {type(x)}")
 
 
+def _maker(like):
+    """Allocator of float64 outputs placed like `like` (CUDA tensor or numpy)."""
+    if _is_cuda(like):
+        import torch
+        return lambda shape: torch.empty(shape, dtype=torch.float64, device=like.device)
+    return lambda shape: np.empty(shape)
+
+
 def _is_cuda(x):
     try:
         import torch
@@ -169,6 +180,7 @@ class Context:
             raise SrpError(rc, f"srp_create(device={device}) failed")
         self.h = h
         self.meshes = {}
+        self.mesh_info = {}
 
     def _check(self, rc):
         if rc != SRP_OK:
@@ -214,6 +226,7 @@ class Context:
         mid = C.c_int32(-1)
         self._check(self.lib.srp_mesh_load(self.h, C.byref(d), C.byref(mid)))
         self.meshes[mid.value] = len(keep["parent"])
+        self.mesh_info[mid.value] = dict(n_parts=len(keep["parent"]), n_mats=len(keep["mat"]))
         return mid.value
 
     def free_mesh(self, mesh_id: int):
@@ -221,8 +234,15 @@ class Context:
         self.meshes.pop(mesh_id, None)
 
     def set_panel_angles(self, mesh_id: int, angles):
-        a = np.ascontiguousarray(np.asarray(angles, np.float64))
-        self._check(self.lib.srp_set_panel_angles(self.h, mesh_id, len(a), a.ctypes.data))
+        """srp_set_panel_angles: commanded angles / tracking offsets [n_parts]
+        (numpy, sequence, or torch tensor on the host or the device)."""
+        if _is_cuda(angles):
+            a = angles.detach().to(dtype=__import__("torch").float64).contiguous()
+        else:
+            a = angles.detach().cpu().numpy() if hasattr(angles, "detach") else angles
+            a = np.ascontiguousarray(np.asarray(a, np.float64))
+        pa, k = _ptr(a)
+        self._check(self.lib.srp_set_panel_angles(self.h, mesh_id, int(a.shape[0]), pa))
 
     def eval_batch(self, mesh_id: int, sun_dirs, sun_dist=None, N: int = 256, bounces: int = 1, P0: float = 4.56e-6,
                    eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, hits: bool = False, count: bool = False,
@@ -291,6 +311,41 @@ class Context:
             for i, s in enumerate(stats):
                 hl[i, min(s["steps"], h_cap):] = np.nan
         return y1, stats, hl
+
+    def set_materials(self, mesh_id: int, mat):
+        """srp_set_materials: new (rho_s, rho_d) per material, [n_mats, 2]."""
+        if _is_cuda(mat):
+            mat = mat.detach().to(dtype=__import__("torch").float64).contiguous()
+        else:
+            mat = mat.detach().cpu().numpy() if hasattr(mat, "detach") else mat
+            mat = np.ascontiguousarray(np.asarray(mat, np.float64))
+        pm, k = _ptr(mat)
+        self._check(self.lib.srp_set_materials(self.h, mesh_id, int(mat.shape[0]), pm))
+
+    def grad(self, mesh_id: int, sun_dirs, g_force, g_torque, sun_dist=None, N: int = 256, bounces: int = 1,
+             P0: float = 4.56e-6, eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, n_mats=None,
+             n_parts=None):
+        """srp_grad: force, torque and the frozen-hit gradients of
+        L = sum g_force . F + g_torque . T.  Returns a dict with F, T [n,3],
+        sun [n,3], dist [n] (when sun_dist is given), mat [n_mats,2] and
+        angle [n_parts].  CUDA tensors in, CUDA tensors out; numpy otherwise."""
+        n = int(sun_dirs.shape[0])
+        cuda = _is_cuda(sun_dirs)
+        mk = _maker(sun_dirs)
+        conv = lambda x: None if x is None else (np.ascontiguousarray(x, np.float64) if isinstance(x, np.ndarray)  # noqa: E731
+                                                 else x.contiguous())
+        sun_dirs, g_force, g_torque, sun_dist = map(conv, (sun_dirs, g_force, g_torque, sun_dist))
+        M = self.mesh_info[mesh_id]["n_mats"] if n_mats is None else n_mats
+        P = self.mesh_info[mesh_id]["n_parts"] if n_parts is None else n_parts
+        out = dict(F=mk((n, 3)), T=mk((n, 3)), sun=mk((n, 3)), mat=mk((M, 2)), angle=mk((P,)))
+        if sun_dist is not None:
+            out["dist"] = mk((n,))
+        p = EvalParams(N, bounces, P0, eps_rel, panel_mode, 0)
+        args = [sun_dirs, sun_dist, g_force, g_torque, out["F"], out["T"], out["sun"], out.get("dist"), out["mat"],
+                out["angle"]]
+        ptrs = [_ptr(x) for x in args]
+        self._check(self.lib.srp_grad(self.h, mesh_id, C.byref(p), n, *[q[0] for q in ptrs]))
+        return out
 
     def eval_stats(self) -> dict:
         s = EvalStats()
