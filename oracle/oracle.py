@@ -74,6 +74,7 @@ def lib():
         _lib.orc_pose.restype = C.c_int
         _lib.orc_window_ids.restype = C.c_int
         _lib.orc_eval_frozen.restype = C.c_int
+        _lib.orc_rk4_arc.restype = C.c_int
     return _lib
 
 
@@ -391,3 +392,108 @@ def propagate(mesh, pp, t0, t1, y0, h_cap=1_000_000, h_replay=None):
     if rc != 0:
         raise ValueError(f"orc_propagate failed: {rc}")
     return y1, stats, hlog[: min(int(stats[0]), h_cap)]
+
+
+# ------------------------------------------------ frozen-hit RK4 arc gradients
+def _arc(mesh, pp, t0, t1, y0, record, rec, track, angles, om=None):
+    om = om or (OMesh(mesh) if mesh is not None else None)
+    y0 = np.ascontiguousarray(np.asarray(y0, np.float64))
+    y1 = np.zeros(6)
+    nst = np.zeros(1, np.int64)
+    a = None if angles is None else np.ascontiguousarray(np.asarray(angles, np.float64))
+    hits, ids, lit = rec["hits"], rec["ids"], rec["lit"]
+    rc = lib().orc_rk4_arc(C.byref(om.s) if om else None, C.byref(pp), C.c_int32(track), _dp(a) if a is not None else None,
+                           C.c_double(t0), C.c_double(t1), _dp(y0), C.c_int32(record), _ip(hits), _ip(ids), _ip(lit),
+                           C.c_int64(len(lit)), _dp(y1), nst.ctypes.data_as(C.POINTER(C.c_int64)))
+    if rc != 0:
+        raise ValueError(f"orc_rk4_arc failed: {rc}")
+    return y1, int(nst[0])
+
+
+def _arc_mode(offsets, angles):
+    if offsets is not None and angles is not None:
+        raise ValueError("give commanded angles or tracking offsets, not both")
+    if angles is not None:
+        return 0, angles
+    if offsets is not None:
+        return 2, offsets
+    return 1, None
+
+
+def rk4_arc_record(mesh, pp, t0, t1, y0, offsets=None, angles=None):
+    """Fixed-step RK4 arc (pp.method must be 1) with the traced SRP in every
+    stage, recording each stage's hit set, window vertices and lit flag.
+    Returns (y1, record)."""
+    n_steps = int(math.ceil((t1 - t0) / pp.h0 - 1e-9))
+    cap = 4 * max(n_steps, 1) + 4
+    rays = pp.N * pp.N
+    rec = dict(hits=np.full((cap, rays, pp.bounces + 1), -1, np.int32), ids=np.zeros((cap, 4), np.int32),
+               lit=np.zeros(cap, np.int32))
+    track, a = _arc_mode(offsets, angles)
+    y1, _ = _arc(mesh, pp, t0, t1, y0, 1, rec, track, a)
+    return y1, rec
+
+
+def rk4_arc_frozen(mesh, pp, t0, t1, y0, rec, offsets=None, angles=None, mat=None, _om=None):
+    """The same arc with every SRP evaluation replaced by F_H on the record;
+    `mat` [M, 2] replaces the optical coefficients when given."""
+    om = _om or OMesh(mesh)
+    if mat is not None:
+        keepm = np.ascontiguousarray(np.asarray(mat, np.float64).reshape(-1, 2))
+        om2 = OMesh.__new__(OMesh)
+        om2.keep = dict(om.keep, mat=keepm)
+        om2.n_parts = om.n_parts
+        om2.s = _Mesh.from_buffer_copy(om.s)
+        om2.s.mat = _dp(keepm)
+        om = om2
+    track, a = _arc_mode(offsets, angles)
+    return _arc(mesh, pp, t0, t1, y0, 0, rec, track, a, om=om)[0]
+
+
+def arc_frozen_grad(mesh, pp, t0, t1, y0, lam, offsets=None, angles=None, h=1e-6, h_pos=1.0, h_vel=1e-3):
+    """Reference gradient of L = lam . y1 for an RK4 arc with every SRP
+    evaluation frozen at the hit sets of the base arc: central differences
+    with step h in each optical coefficient, joint parameter and quaternion
+    component (pp.q), and steps h_pos (m) / h_vel (m/s) in the initial state.
+    Returns dict(y0 [6], mat [M, 2], angle [P], q [4], y1 [6], record)."""
+    om = OMesh(mesh)
+    P = om.n_parts
+    if offsets is None and angles is None:
+        offsets = np.zeros(P)
+    lam = np.asarray(lam, np.float64)
+    y0 = np.asarray(y0, np.float64)
+    y1, rec = rk4_arc_record(mesh, pp, t0, t1, y0, offsets=offsets, angles=angles)
+
+    def L(y0_=y0, pp_=pp, off=offsets, ang=angles, mat=None):
+        return float(lam @ rk4_arc_frozen(mesh, pp_, t0, t1, y0_, rec, offsets=off, angles=ang, mat=mat, _om=om))
+
+    g_y0 = np.zeros(6)
+    for i in range(6):
+        e = np.zeros(6)
+        e[i] = h_pos if i < 3 else h_vel
+        g_y0[i] = (L(y0_=y0 + e) - L(y0_=y0 - e)) / (2 * e[i])
+    mat0 = np.asarray(mesh.mat, np.float64).reshape(-1, 2)
+    g_mat = np.zeros_like(mat0)
+    for i in range(mat0.shape[0]):
+        for c in range(2):
+            mp, mm = mat0.copy(), mat0.copy()
+            mp[i, c] += h
+            mm[i, c] -= h
+            g_mat[i, c] = (L(mat=mp) - L(mat=mm)) / (2 * h)
+    g_ang = np.zeros(P)
+    for q in range(P):
+        base = np.array(angles if angles is not None else offsets, np.float64)
+        bp, bm = base.copy(), base.copy()
+        bp[q] += h
+        bm[q] -= h
+        if angles is not None:
+            g_ang[q] = (L(ang=bp) - L(ang=bm)) / (2 * h)
+        else:
+            g_ang[q] = (L(off=bp) - L(off=bm)) / (2 * h)
+    g_q = np.zeros(4)
+    for c in range(4):
+        qp, qm = Prop.from_buffer_copy(pp), Prop.from_buffer_copy(pp)
+        qp.q[c] += h
+        qm.q[c] -= h
+        g_q[c] = (L(pp_=qp) - L(pp_=qm)) / (2 * h)
+    return dict(y0=g_y0, mat=g_mat, angle=g_ang, q=g_q, y1=y1, record=rec)

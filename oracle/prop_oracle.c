@@ -18,8 +18,9 @@
  *   - SRP: the force of srp_oracle.c for the Sun direction in the body frame,
  *     rotated to inertial and divided by the mass; zero inside a cylindrical
  *     Earth shadow;
- *   - attitude: LVLH (body z to nadir, body y along minus the orbit normal)
- *     or a fixed inertial quaternion (scalar first, body -> inertial).
+ *   - attitude: the LVLH frame (z to nadir, y along minus the orbit normal)
+ *     turned by a constant quaternion q (body -> LVLH; identity by default),
+ *     or a fixed inertial quaternion q (body -> inertial); q scalar first.
  */
 #include <math.h>
 #include <stdint.h>
@@ -101,13 +102,17 @@ void orc_sun_position(double mjd_tt, double r[3])
 /* Body -> inertial rotation (row-major) for state y at time t. */
 void orc_attitude(const orc_prop *pp, const double y[6], double R[9])
 {
-    if (pp->attitude == 1) {
+    double Q[9];
+    {
         double w = pp->q[0], x = pp->q[1], yy = pp->q[2], z = pp->q[3];
         double n = sqrt(w * w + x * x + yy * yy + z * z);
         w /= n; x /= n; yy /= n; z /= n;
-        R[0] = 1 - 2 * (yy * yy + z * z); R[1] = 2 * (x * yy - w * z);     R[2] = 2 * (x * z + w * yy);
-        R[3] = 2 * (x * yy + w * z);     R[4] = 1 - 2 * (x * x + z * z);  R[5] = 2 * (yy * z - w * x);
-        R[6] = 2 * (x * z - w * yy);     R[7] = 2 * (yy * z + w * x);     R[8] = 1 - 2 * (x * x + yy * yy);
+        Q[0] = 1 - 2 * (yy * yy + z * z); Q[1] = 2 * (x * yy - w * z);     Q[2] = 2 * (x * z + w * yy);
+        Q[3] = 2 * (x * yy + w * z);     Q[4] = 1 - 2 * (x * x + z * z);  Q[5] = 2 * (yy * z - w * x);
+        Q[6] = 2 * (x * z - w * yy);     Q[7] = 2 * (yy * z + w * x);     Q[8] = 1 - 2 * (x * x + yy * yy);
+    }
+    if (pp->attitude == 1) {
+        memcpy(R, Q, sizeof Q);
         return;
     }
     const double *r = y, *v = y + 3;
@@ -119,7 +124,11 @@ void orc_attitude(const orc_prop *pp, const double y[6], double R[9])
     xb[0] = yb[1] * zb[2] - yb[2] * zb[1];
     xb[1] = yb[2] * zb[0] - yb[0] * zb[2];
     xb[2] = yb[0] * zb[1] - yb[1] * zb[0];
-    for (int k = 0; k < 3; k++) { R[3 * k] = xb[k]; R[3 * k + 1] = yb[k]; R[3 * k + 2] = zb[k]; }
+    double L[9];
+    for (int k = 0; k < 3; k++) { L[3 * k] = xb[k]; L[3 * k + 1] = yb[k]; L[3 * k + 2] = zb[k]; }
+    /* body -> LVLH -> inertial */
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) R[3 * i + j] = L[3 * i] * Q[j] + L[3 * i + 1] * Q[3 + j] + L[3 * i + 2] * Q[6 + j];
 }
 
 /*
@@ -127,13 +136,13 @@ void orc_attitude(const orc_prop *pp, const double y[6], double R[9])
  * [0..2] Sun direction in the body frame, [3] Sun distance (AU), [4] shadow
  * flag, [5..7] SRP force in the body frame (N).
  */
-int orc_accel(const orc_mesh *mesh, const orc_prop *pp, double t, const double y[6], double a[3], double *aux)
+/* Gravity of the configured bodies; rs receives the Sun position (Earth-centred). */
+static void gravity(const orc_prop *pp, double t, const double *r, double a[3], double rs[3])
 {
-    const double *r = y;
     double rn2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], rn = sqrt(rn2);
     double mu = pp->central == 1 ? MU_SUN : MU_EARTH;
     for (int k = 0; k < 3; k++) a[k] = -mu * r[k] / (rn2 * rn);
-    double rs[3] = {0, 0, 0};
+    rs[0] = rs[1] = rs[2] = 0.0;
     if (pp->central == 0 && (pp->sun3 || pp->srp)) orc_sun_position(pp->epoch_mjd_tt + t / 86400.0, rs);
     if (pp->central == 0 && pp->j2) {
         double z2 = r[2] * r[2] / rn2;
@@ -148,35 +157,50 @@ int orc_accel(const orc_mesh *mesh, const orc_prop *pp, double t, const double y
         double s3 = pow(rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2], 1.5);
         for (int k = 0; k < 3; k++) a[k] += MU_SUN * (dr[k] / d3 - rs[k] / s3);
     }
-    if (aux) memset(aux, 0, 8 * sizeof(double));
-    if (!pp->srp) return 0;
-    /* unit vector spacecraft -> Sun and distance */
-    double sv[3];
+}
+
+/* Sun direction (inertial, unit), distance (AU) and the shadow test. */
+static int sun_geometry(const orc_prop *pp, const double *r, const double rs[3], double sv[3], double *dist_au)
+{
     if (pp->central == 1) { for (int k = 0; k < 3; k++) sv[k] = -r[k]; }
     else { for (int k = 0; k < 3; k++) sv[k] = rs[k] - r[k]; }
     double sd = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
     for (int k = 0; k < 3; k++) sv[k] /= sd;
+    *dist_au = sd / AU;
     if (pp->central == 0) {
         /* cylindrical Earth shadow (Montenbruck & Gill, Sec. 3.4.2) */
         double rsn = sqrt(rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2]);
         double e[3] = {rs[0] / rsn, rs[1] / rsn, rs[2] / rsn};
         double pr = r[0] * e[0] + r[1] * e[1] + r[2] * e[2];
         double perp[3] = {r[0] - pr * e[0], r[1] - pr * e[1], r[2] - pr * e[2]};
-        if (pr < 0.0 && sqrt(perp[0] * perp[0] + perp[1] * perp[1] + perp[2] * perp[2]) < R_EARTH) {
-            if (aux) aux[4] = 1.0;
-            return 0;
-        }
+        if (pr < 0.0 && sqrt(perp[0] * perp[0] + perp[1] * perp[1] + perp[2] * perp[2]) < R_EARTH) return 1;
+    }
+    return 0;
+}
+
+int orc_accel(const orc_mesh *mesh, const orc_prop *pp, double t, const double y[6], double a[3], double *aux)
+{
+    const double *r = y;
+    double rs[3];
+    gravity(pp, t, r, a, rs);
+    if (aux) memset(aux, 0, 8 * sizeof(double));
+    if (!pp->srp) return 0;
+    /* unit vector spacecraft -> Sun and distance */
+    double sv[3], dist;
+    if (sun_geometry(pp, r, rs, sv, &dist)) {
+        if (aux) aux[4] = 1.0;
+        return 0;
     }
     double R[9], sb[3];
     orc_attitude(pp, y, R);
     for (int k = 0; k < 3; k++) sb[k] = R[k] * sv[0] + R[3 + k] * sv[1] + R[6 + k] * sv[2];
-    orc_params ep = {pp->N, pp->bounces, pp->P0, sd / AU, pp->eps_rel, 1, NULL};
+    orc_params ep = {pp->N, pp->bounces, pp->P0, dist, pp->eps_rel, 1, NULL};
     double acc[6] = {0, 0, 0, 0, 0, 0}, scale = 0.0;
     int rc = orc_eval_range(mesh, &ep, sb, 0, (int64_t)pp->N * pp->N, acc, &scale, NULL, NULL, NULL, NULL, NULL);
     if (rc) return rc;
     double Fb[3] = {acc[0] * scale, acc[1] * scale, acc[2] * scale};
     for (int k = 0; k < 3; k++) a[k] += (R[3 * k] * Fb[0] + R[3 * k + 1] * Fb[1] + R[3 * k + 2] * Fb[2]) / pp->mass;
-    if (aux) { aux[0] = sb[0]; aux[1] = sb[1]; aux[2] = sb[2]; aux[3] = sd / AU; aux[5] = Fb[0]; aux[6] = Fb[1]; aux[7] = Fb[2]; }
+    if (aux) { aux[0] = sb[0]; aux[1] = sb[1]; aux[2] = sb[2]; aux[3] = dist; aux[5] = Fb[0]; aux[6] = Fb[1]; aux[7] = Fb[2]; }
     return 0;
 }
 
@@ -298,4 +322,77 @@ int orc_propagate(const orc_mesh *mesh, const orc_prop *pp, double t0, double t1
     memcpy(y1, y, sizeof y);
     if (stats) { stats[0] = acc_steps; stats[1] = rej; stats[2] = evals; }
     return rc;
+}
+
+/* ------------------------------------------------- frozen-hit RK4 arcs */
+int orc_window_ids(const orc_mesh *m, const orc_params *p, const double s[3], int32_t ids[4]);
+int orc_eval_frozen(const orc_mesh *m, const orc_params *p, const double s_raw[3], int64_t r0, int64_t r1,
+                    const int32_t *hits, const int32_t ids[4], double *acc, double *scale);
+
+/*
+ * A fixed-step RK4 arc (the step loop of orc_propagate with method 1) whose
+ * SRP evaluations are either traced and recorded (record = 1) or replaced by
+ * the frozen-hit function F_H of frozen_oracle.c using those records
+ * (record = 0).  Stage k = 4 * step + stage keeps:
+ *   hits [k][N*N][bounces+1]  triangle ids, ids [k][4] window vertices,
+ *   lit  [k]                  1 when SRP was evaluated (not shadowed, SRP on).
+ * The frozen arc takes the lit flags from the record (the shadow boundary is
+ * part of the frozen combinatorial state).  track / angles: joint mode of
+ * every evaluation (1 tracking, 2 tracking + offsets, 0 commanded).
+ * Returns 0, or -1 for bad arguments / a record too small (cap stages).
+ */
+int orc_rk4_arc(const orc_mesh *mesh, const orc_prop *pp, int32_t track, const double *angles, double t0, double t1,
+                const double y0[6], int32_t record, int32_t *hits, int32_t *ids, int32_t *lit, int64_t cap,
+                double y1[6], int64_t *n_steps)
+{
+    if (!pp || !y0 || !y1 || t1 < t0 || pp->method != 1 || !(pp->h0 > 0.0)) return -1;
+    if (pp->srp && (!mesh || !hits || !ids || !lit)) return -1;
+    const int64_t rays = (int64_t)pp->N * pp->N, nseg = pp->bounces + 1;
+    double y[6], k[4][6], ys[6];
+    memcpy(y, y0, sizeof y);
+    double t = t0;
+    int64_t step = 0;
+    static const double C4[4] = {0.0, 0.5, 0.5, 1.0}, A4[4] = {0.0, 0.5, 0.5, 1.0};
+    while (t < t1) {
+        double h = pp->h0;
+        if (t + h > t1) h = t1 - t;
+        for (int sg = 0; sg < 4; sg++) {
+            for (int i = 0; i < 6; i++) ys[i] = sg == 0 ? y[i] : y[i] + A4[sg] * h * k[sg - 1][i];
+            double ts = t + C4[sg] * h, a[3], rs[3];
+            gravity(pp, ts, ys, a, rs);
+            if (pp->srp) {
+                int64_t kk = 4 * step + sg;
+                if (kk >= cap) return -1;
+                double sv[3], dist;
+                int shadow = sun_geometry(pp, ys, rs, sv, &dist);
+                if (record) lit[kk] = !shadow;
+                if (lit[kk]) {
+                    double R[9], sb[3];
+                    orc_attitude(pp, ys, R);
+                    for (int c = 0; c < 3; c++) sb[c] = R[c] * sv[0] + R[3 + c] * sv[1] + R[6 + c] * sv[2];
+                    orc_params ep = {pp->N, pp->bounces, pp->P0, dist, pp->eps_rel, track, angles};
+                    double acc[6] = {0, 0, 0, 0, 0, 0}, scale = 0.0;
+                    int32_t *hk = hits + kk * rays * nseg, *ik = ids + 4 * kk;
+                    int rc;
+                    if (record) {
+                        rc = orc_eval_range(mesh, &ep, sb, 0, rays, acc, &scale, NULL, NULL, hk, NULL, NULL);
+                        if (!rc) rc = orc_window_ids(mesh, &ep, sb, ik);
+                    } else {
+                        rc = orc_eval_frozen(mesh, &ep, sb, 0, rays, hk, ik, acc, &scale);
+                    }
+                    if (rc) return -1;
+                    double Fb[3] = {acc[0] * scale, acc[1] * scale, acc[2] * scale};
+                    for (int c = 0; c < 3; c++)
+                        a[c] += (R[3 * c] * Fb[0] + R[3 * c + 1] * Fb[1] + R[3 * c + 2] * Fb[2]) / pp->mass;
+                }
+            }
+            for (int i = 0; i < 3; i++) { k[sg][i] = ys[3 + i]; k[sg][3 + i] = a[i]; }
+        }
+        for (int i = 0; i < 6; i++) y[i] = y[i] + h / 6.0 * (k[0][i] + 2.0 * k[1][i] + 2.0 * k[2][i] + k[3][i]);
+        t = (t + h > t1 || t1 - (t + h) < 1e-9 * pp->h0) ? t1 : t + h;
+        step++;
+    }
+    memcpy(y1, y, sizeof y);
+    if (n_steps) *n_steps = step;
+    return 0;
 }
