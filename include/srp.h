@@ -24,7 +24,8 @@
  *   - Photons travel along d = -s, s the unit body-frame vector towards the Sun.
  *   - Ray r of an evaluation is pixel (i, j) = (r / N, r % N) of the window;
  *     i runs along the window's u axis, j along its v axis.
- *   - Quaternions are scalar first and rotate body into inertial axes.
+ *   - Quaternions are scalar first and rotate body axes into inertial axes
+ *     (into LVLH axes for SRP_ATT_LVLH).
  *   - Pointers to per-call data may be host or device memory (the library asks
  *     the driver which); outputs are owned by the caller and written before the
  *     call returns.  Mesh descriptions must be host memory; the library copies
@@ -248,8 +249,9 @@ srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *params
 #define SRP_RK4 1             /* classical RK4, fixed step h0                    */
 #define SRP_CENTRAL_EARTH 0
 #define SRP_CENTRAL_SUN 1
-#define SRP_ATT_LVLH 0        /* body z to nadir, body y along minus the orbit normal */
-#define SRP_ATT_INERTIAL 1    /* fixed quaternion q                               */
+#define SRP_ATT_LVLH 0        /* LVLH frame (z to nadir, y along minus the orbit normal)
+                                 turned by the constant quaternion q (body -> LVLH)    */
+#define SRP_ATT_INERTIAL 1    /* fixed quaternion q (body -> inertial)             */
 
 typedef struct {
     int32_t method;        /* SRP_RKF78 or SRP_RK4                                        */
@@ -258,7 +260,9 @@ typedef struct {
     int32_t sun3;          /* Sun as a third body (Earth-centred only)                     */
     int32_t srp;           /* ray-traced SRP acceleration on (1) or off (0)                */
     int32_t attitude;      /* SRP_ATT_LVLH or SRP_ATT_INERTIAL                             */
-    double q[4];           /* body -> inertial quaternion (scalar first), SRP_ATT_INERTIAL */
+    double q[4];           /* attitude quaternion, scalar first (normalised by the library):
+                              body -> inertial (SRP_ATT_INERTIAL) or body -> LVLH (SRP_ATT_LVLH;
+                              (1, 0, 0, 0) keeps the body on the LVLH axes)                   */
     double epoch_mjd_tt;   /* epoch of t = 0, MJD in TT (Sun ephemeris)                     */
     double rtol;           /* RKF7(8) relative tolerance                                   */
     double atol_pos;       /* absolute tolerance on position components (m)                 */
@@ -309,6 +313,39 @@ typedef struct {
 srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *params, int32_t n_traj,
                          const double *y0, const double *t0_t1, double *y1, srp_prop_stats *stats, double *h_log,
                          int64_t h_cap);
+
+/*
+ * Discrete adjoint of an RK4 arc (Sec. 3, Eqs. 1-3, with the frozen-hit SRP
+ * gradient of srp_grad in every stage).  Propagates like srp_propagate with
+ * params->method == SRP_RK4 (fixed step h0, the last step shortened to land on
+ * t1; every trajectory must take the same number of steps), then returns the
+ * derivatives of
+ *     L = sum_i g_y1[i] . y1[i]
+ * with respect to the initial states, the optical coefficients, the joint
+ * parameters (as srp_grad: commanded angle or offset from the tracking angle)
+ * and the attitude quaternion params->q.  Each SRP evaluation keeps the hit set
+ * and window vertices it had on the propagated arc, and each stage keeps its
+ * lit / shadowed state; gravity (central body, J2, Sun), the Sun direction and
+ * distance, the attitude (LVLH turned by q, or q) and the RK4 stage
+ * combination are differentiated exactly.
+ * Memory: the forward pass keeps the state every ckpt_every steps; the reverse
+ * pass recomputes one segment at a time, recording its stage states and hit
+ * ids (ckpt_every * 4 * n_traj * N^2 * (bounces + 1) int32 on the device),
+ * then sweeps it backward, so each SRP evaluation is traced twice and
+ * differentiated once.
+ *   g_y1     [n_traj][6]  in: cotangent of the final state
+ *   y1       [n_traj][6]  out (may be NULL): final state
+ *   g_y0     [n_traj][6]  out (may be NULL)
+ *   g_mat    [n_mats][2], g_angle [n_parts], g_q [4]: out (may be NULL), summed
+ *                         over the trajectories; g_q is orthogonal to q
+ *   stats    [n_traj]     out (may be NULL)
+ * Errors: SRP_ERR_ARG (not RK4, step replay, unequal step counts,
+ * ckpt_every < 1), SRP_ERR_STEP (more than max_steps steps), SRP_ERR_OOM,
+ * and those of srp_propagate.
+ */
+srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *params, int32_t n_traj,
+                         const double *y0, const double *t0_t1, const double *g_y1, int32_t ckpt_every, double *y1,
+                         double *g_y0, double *g_mat, double *g_angle, double *g_q, srp_prop_stats *stats);
 
 /* Limits of srp_eval_noalloc. */
 #define SRP_NOALLOC_MAX_N 1024    /* rays per window side                     */

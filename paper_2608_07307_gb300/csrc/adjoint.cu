@@ -440,17 +440,14 @@ __global__ void __launch_bounds__(128) k_adj_finish(AdjArgs a)
     if (a.g_dist) a.g_dist[e] = -2.0 * L / a.sun_dist[e];  // pressure P0 / dist^2
 }
 
-__global__ void k_adj_sum(const double *g_eval, int n, int width, double *g_mat, int nm2, double *g_angle)
+__global__ void k_adj_sum(const double *g_eval, int n, int width, double *g_mat, int nm2, double *g_angle, int accumulate)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= width) return;
     double x = 0.0;
     for (int e = 0; e < n; e++) x += g_eval[(size_t)e * width + k];
-    if (k < nm2) {
-        if (g_mat) g_mat[k] = x;
-    } else if (g_angle) {
-        g_angle[k - nm2] = x;
-    }
+    double *dst = k < nm2 ? (g_mat ? g_mat + k : nullptr) : (g_angle ? g_angle + (k - nm2) : nullptr);
+    if (dst) *dst = accumulate ? *dst + x : x;
 }
 
 }  // namespace
@@ -472,10 +469,10 @@ cudaError_t launch_adjoint(const AdjArgs &a, int S, cudaStream_t st)
 }
 
 cudaError_t launch_adj_sum(const double *g_eval, int n, int n_mats, int n_parts, double *g_mat, double *g_angle,
-                           cudaStream_t st)
+                           cudaStream_t st, bool accumulate)
 {
     int width = 2 * n_mats + n_parts;
-    k_adj_sum<<<(width + 127) / 128, 128, 0, st>>>(g_eval, n, width, g_mat, 2 * n_mats, g_angle);
+    k_adj_sum<<<(width + 127) / 128, 128, 0, st>>>(g_eval, n, width, g_mat, 2 * n_mats, g_angle, accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -79,6 +79,11 @@ struct srp_ctx {
     size_t win_ids_cap = 0;
     double *gio = nullptr;
     size_t gio_cap = 0;
+    // propagation adjoint
+    int32_t *arc_hits = nullptr;
+    size_t arc_hits_cap = 0;
+    unsigned char *arc_buf = nullptr;
+    size_t arc_buf_cap = 0;
     cudaStream_t lane[kLanes] = {};  // pipeline lanes (forked from / joined to `stream`)
     cudaEvent_t ev_fork = nullptr, ev_join[kLanes] = {};
 };
@@ -410,6 +415,75 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
     return SRP_OK;
 }
 
+// Adjoint of evaluations whose hits were recorded earlier: posing and window
+// vertices again (no trace), then the frozen-hit reverse sweep, on `st` with
+// the first lane's slots.  hits: [n][N*N][nseg] original triangle ids.
+srp_status adj_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const EvalPlan &pl, int n,
+                       const double *d_sun, const double *d_dist, const int32_t *hits, const AdjBatch &ab,
+                       cudaStream_t st, int64_t &launches)
+{
+    const MeshDev &h = m->h;
+    for (int e0 = 0; e0 < n; e0 += pl.S) {
+        const int Sc = std::min(pl.S, n - e0);
+        SlotPose *pose = ctx->pose;
+        CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, pose, st));
+        CK(ctx, launch_vertices(m->d, h, pose, m->sb, Sc, st));
+        AdjArgs g{};
+        g.mesh_d = m->d;
+        g.pose = pose;
+        g.slot = m->sb;
+        g.hits = hits + (size_t)e0 * pl.R * pl.nseg;
+        g.sun_dirs = d_sun;
+        g.sun_dist = ab.dist;
+        g.g_force = ab.gF;
+        g.g_torque = ab.gT;
+        g.N = pl.N;
+        g.nseg = pl.nseg;
+        g.panel_mode = ab.panel_mode;
+        g.n_mats = h.n_mats;
+        g.n_parts = h.n_parts;
+        g.eval0 = e0;
+        g.nb = pl.nba;
+        g.width = pl.wa;
+        g.win_ids = ctx->win_ids;
+        g.partials = ctx->adj_partials;
+        g.g_sun = ab.g_sun;
+        g.g_dist = ab.g_dist;
+        g.g_eval = ab.g_eval;
+        CK(ctx, launch_adjoint(g, Sc, st));
+        launches += 5;
+    }
+    return SRP_OK;
+}
+
+PropDev prop_dev(const srp_prop_params *p, const Mesh *m)
+{
+    PropDev P{};
+    P.method = p->method; P.central = p->central; P.j2 = p->j2; P.sun3 = p->sun3; P.srp = p->srp;
+    P.attitude = p->attitude;
+    for (int k = 0; k < 4; k++) P.q[k] = p->q[k];
+    P.epoch_mjd_tt = p->epoch_mjd_tt; P.mass = m->mass;
+    P.rtol = p->rtol; P.atol_pos = p->atol_pos; P.atol_vel = p->atol_vel;
+    P.h0 = p->h0; P.h_min = p->h_min; P.h_max = p->h_max; P.max_steps = p->max_steps;
+    return P;
+}
+
+// Number of fixed RK4 steps from t0 to t1 (the last one shortened to land on
+// t1, a step ending within 1e-9 h0 of t1 snapped onto it), as k_prop_control
+// takes them; -1 beyond max_steps.
+int64_t rk4_steps(double t0, double t1, double h0, int64_t max_steps)
+{
+    int64_t k = 0;
+    double t = t0;
+    while (t < t1) {
+        const bool last = t + h0 >= t1;
+        const double h = last ? t1 - t : h0;
+        t = (last || t1 - (t + h) < 1e-9 * h0) ? t1 : t + h;
+        if (++k > max_steps) return -1;
+    }
+    return k;
+}
+
 // Read back the trajectories: final states, per-trajectory stats, step log.
 srp_status finish_propagate(srp_ctx *ctx, int n, const PropState *S, double *y1, srp_prop_stats *stats, double *h_log,
                             int64_t h_cap)
@@ -516,6 +590,8 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->adj_partials);
     cudaFree(ctx->win_ids);
     cudaFree(ctx->gio);
+    cudaFree(ctx->arc_hits);
+    cudaFree(ctx->arc_buf);
     cudaFree(ctx->err_flags);
     cudaFree(ctx->stats);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
@@ -933,13 +1009,7 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     CK(ctx, cudaMemsetAsync(ctx->prop_done, 0, sizeof(int), st));
     PropState *S = ctx->prop_state;
     CK(ctx, launch_prop_init(S, n, d_y0, d_t01, p->h0, ctx->prop_done, st));
-    PropDev P{};
-    P.method = p->method; P.central = p->central; P.j2 = p->j2; P.sun3 = p->sun3; P.srp = p->srp;
-    P.attitude = p->attitude;
-    for (int k = 0; k < 4; k++) P.q[k] = p->q[k];
-    P.epoch_mjd_tt = p->epoch_mjd_tt; P.mass = m->mass;
-    P.rtol = p->rtol; P.atol_pos = p->atol_pos; P.atol_vel = p->atol_vel;
-    P.h0 = p->h0; P.h_min = p->h_min; P.h_max = p->h_max; P.max_steps = p->max_steps;
+    PropDev P = prop_dev(p, m);
     if (p->h_replay && p->n_replay > 0) {
         if (p->method != SRP_RKF78) return fail(ctx, SRP_ERR_ARG, "step replay needs SRP_RKF78");
         CK(ctx, grow(&ctx->prop_replay, &ctx->prop_replay_cap, (size_t)n * p->n_replay, false));
@@ -1127,6 +1197,180 @@ srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, i
     CK(ctx, cudaMemcpyAsync(stats, ctx->stats, sizeof stats, cudaMemcpyDeviceToHost, st));
     CK(ctx, cudaStreamSynchronize(st));
     fill_stats(ctx->last, stats);
+    ctx->last.launches = launches;
+    ctx->last.trace_launches = trace_launches;
+    if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
+    return SRP_OK;
+}
+
+srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p, int32_t n, const double *y0,
+                         const double *t0_t1, const double *g_y1, int32_t ckpt_every, double *y1, double *g_y0,
+                         double *g_mat, double *g_angle, double *g_q, srp_prop_stats *stats)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
+    if (!p) return fail(ctx, SRP_ERR_ARG, "null params");
+    srp_status rc = check_eval_params(ctx, &p->eval);
+    if (rc) return rc;
+    if (n <= 0 || !y0 || !t0_t1 || !g_y1) return fail(ctx, SRP_ERR_ARG, "need n > 0, y0, t0_t1 and g_y1");
+    if (p->method != SRP_RK4) return fail(ctx, SRP_ERR_ARG, "the propagation adjoint needs SRP_RK4 (fixed steps)");
+    if (p->h_replay && p->n_replay > 0) return fail(ctx, SRP_ERR_ARG, "step replay is not differentiated");
+    if (p->central != SRP_CENTRAL_EARTH && p->central != SRP_CENTRAL_SUN) return fail(ctx, SRP_ERR_ARG, "bad central body");
+    if (p->attitude != SRP_ATT_LVLH && p->attitude != SRP_ATT_INERTIAL) return fail(ctx, SRP_ERR_ARG, "bad attitude");
+    if (!(p->h0 > 0.0) || p->max_steps <= 0) return fail(ctx, SRP_ERR_ARG, "bad step settings");
+    if (ckpt_every < 1) return fail(ctx, SRP_ERR_ARG, "ckpt_every must be >= 1");
+    if (p->srp && !(m->mass > 0.0)) return fail(ctx, SRP_ERR_ARG, "mesh mass must be > 0 for SRP");
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    memset(&ctx->last, 0, sizeof ctx->last);
+    // every trajectory takes the same number of steps
+    std::vector<double> t01h((size_t)2 * n);
+    CK(ctx, cudaMemcpy(t01h.data(), t0_t1, sizeof(double) * 2 * n, cudaMemcpyDefault));
+    const int64_t K = rk4_steps(t01h[0], t01h[1], p->h0, p->max_steps);
+    if (K < 0) return fail(ctx, SRP_ERR_STEP, "the arc needs more than max_steps steps");
+    for (int i = 1; i < n; i++)
+        if (rk4_steps(t01h[2 * i], t01h[2 * i + 1], p->h0, p->max_steps) != K)
+            return fail(ctx, SRP_ERR_ARG, "trajectory %d takes a different number of steps", i);
+    const int C = (int)std::min<int64_t>(ckpt_every, std::max<int64_t>(K, 1));
+    const int64_t nck = K > 0 ? (K + C - 1) / C : 0;
+    EvalPlan pl;
+    rc = eval_plan(ctx, m, &p->eval, n, false, pl, true);
+    if (rc) return rc;
+    const int NM2 = 2 * m->h.n_mats, NP = m->h.n_parts, GE = NM2 + NP;
+    const size_t R = pl.R, nseg = pl.nseg, n3 = (size_t)n * 3;
+    // device buffers
+    const size_t rec_count = (size_t)C * 4 * n;
+    CK(ctx, grow(&ctx->arc_hits, &ctx->arc_hits_cap, p->srp ? rec_count * R * nseg : 1, false));
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+    const size_t o_state = take(sizeof(PropState) * n), o_adj = take(sizeof(PropAdj) * n),
+                 o_ckpt = take(sizeof(double) * 7 * n * std::max<int64_t>(nck, 1)),
+                 o_rec = take(sizeof(StageRec) * rec_count), o_rsun = take(sizeof(double) * 3 * rec_count),
+                 o_rdist = take(sizeof(double) * rec_count), o_io = take(sizeof(double) * (8 * n3 + 2 * n + 8)),
+                 o_ge = take(sizeof(double) * ((size_t)n * GE + GE + 4)), o_t01 = take(sizeof(double) * 2 * n);
+    CK(ctx, grow(&ctx->arc_buf, &ctx->arc_buf_cap, off, false));
+    unsigned char *B = ctx->arc_buf;
+    PropState *S = reinterpret_cast<PropState *>(B + o_state);
+    PropAdj *A = reinterpret_cast<PropAdj *>(B + o_adj);
+    double *ck = reinterpret_cast<double *>(B + o_ckpt);
+    StageRec *rec = reinterpret_cast<StageRec *>(B + o_rec);
+    double *rsun = reinterpret_cast<double *>(B + o_rsun), *rdist = reinterpret_cast<double *>(B + o_rdist);
+    double *io = reinterpret_cast<double *>(B + o_io);
+    double *d_sun = io, *d_f = io + n3, *d_t = io + 2 * n3, *gF = io + 3 * n3, *gT = io + 4 * n3,
+           *gS = io + 5 * n3, *d_y0 = io + 6 * n3, *d_dist = io + 8 * n3, *gD = d_dist + n;
+    double *ge = reinterpret_cast<double *>(B + o_ge), *acc = ge + (size_t)n * GE, *qsum = acc + GE;
+    double *d_t01 = reinterpret_cast<double *>(B + o_t01);
+    CK(ctx, cudaMemcpyAsync(d_y0, y0, sizeof(double) * 6 * n, cudaMemcpyDefault, st));
+    CK(ctx, cudaMemcpyAsync(d_t01, t0_t1, sizeof(double) * 2 * n, cudaMemcpyDefault, st));
+    CK(ctx, cudaMemsetAsync(gT, 0, sizeof(double) * n3, st));
+    CK(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * (GE + 4), st));
+    CK(ctx, cudaMemsetAsync(A, 0, sizeof(PropAdj) * n, st));
+    CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
+    CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
+    CK(ctx, cudaMemsetAsync(ctx->prop_done, 0, sizeof(int), st));
+    CK(ctx, launch_prop_init(S, n, d_y0, d_t01, p->h0, ctx->prop_done, st));
+    const PropDev P = prop_dev(p, m);
+    Timing off_t(ctx, false);
+    int64_t launches = 1, trace_launches = 0;
+    // one RK4 step; with hrec != null every stage's hits and state are recorded at step j of the segment
+    auto step = [&](int64_t j, bool record) -> srp_status {
+        for (int sg = 0; sg < 4; sg++) {
+            CK(ctx, launch_prop_stage(S, n, P, sg, d_sun, d_dist, st));
+            const size_t k = (size_t)j * 4 + sg;
+            if (p->srp) {
+                int32_t *hrec = record ? ctx->arc_hits + k * n * R * nseg : nullptr;
+                srp_status e = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, hrec, record, off_t,
+                                            launches, trace_launches);
+                if (e) return e;
+            }
+            CK(ctx, launch_prop_accel(S, n, P, sg, d_f, st));
+            launches += 2;
+            if (record) {
+                CK(ctx, launch_prop_record(S, n, d_sun, d_dist, d_f, rec + k * n, rsun + k * 3 * n, rdist + k * n, st));
+                launches++;
+            }
+        }
+        CK(ctx, launch_prop_control(S, n, P, ctx->prop_done, nullptr, 0, st));
+        launches++;
+        return SRP_OK;
+    };
+    // forward, saving a checkpoint at the start of every segment
+    for (int64_t c = 0; c < nck; c++) {
+        CK(ctx, launch_prop_ckpt(S, n, ck + (size_t)c * 7 * n, true, p->h0, st));
+        const int64_t Ks = std::min<int64_t>(C, K - c * C);
+        for (int64_t j = 0; j < Ks; j++)
+            if ((rc = step(j, false))) return rc;
+    }
+    std::vector<PropState> fin(n);
+    CK(ctx, cudaMemcpyAsync(fin.data(), S, sizeof(PropState) * n, cudaMemcpyDeviceToHost, st));
+    // reverse: lam = g_y1, then segment by segment from the end
+    std::vector<PropAdj> a0(n);
+    {
+        std::vector<double> g1((size_t)6 * n);
+        CK(ctx, cudaMemcpy(g1.data(), g_y1, sizeof(double) * 6 * n, cudaMemcpyDefault));
+        for (int i = 0; i < n; i++) {
+            memset(&a0[i], 0, sizeof(PropAdj));
+            for (int k = 0; k < 6; k++) a0[i].lam[k] = g1[6 * (size_t)i + k];
+        }
+        CK(ctx, cudaMemcpyAsync(A, a0.data(), sizeof(PropAdj) * n, cudaMemcpyHostToDevice, st));
+        CK(ctx, cudaStreamSynchronize(st));  // a0 leaves scope
+    }
+    AdjBatch ab{d_sun, nullptr, gF, gT, gS, gD, ge, p->eval.panel_mode};
+    for (int64_t c = nck - 1; c >= 0; c--) {
+        CK(ctx, launch_prop_ckpt(S, n, ck + (size_t)c * 7 * n, false, p->h0, st));
+        const int64_t Ks = std::min<int64_t>(C, K - c * C);
+        for (int64_t j = 0; j < Ks; j++)
+            if ((rc = step(j, true))) return rc;
+        for (int64_t j = Ks - 1; j >= 0; j--) {
+            for (int sg = 3; sg >= 0; sg--) {
+                const size_t k = (size_t)j * 4 + sg;
+                CK(ctx, launch_adj_prop_in(n, P, sg, rec + k * n, A, gF, st));
+                if (p->srp) {
+                    ab.sun = rsun + k * 3 * n;
+                    ab.dist = rdist + k * n;
+                    rc = adj_enqueue(ctx, m, &p->eval, pl, n, ab.sun, ab.dist, ctx->arc_hits + k * n * R * nseg, ab,
+                                     st, launches);
+                    if (rc) return rc;
+                    CK(ctx, launch_adj_sum(ge, n, m->h.n_mats, NP, acc, acc + NM2, st, true));
+                    launches++;
+                }
+                CK(ctx, launch_adj_prop_out(n, P, sg, rec + k * n, A, gS, gD, st));
+                launches += 2;
+            }
+            CK(ctx, launch_adj_prop_step(n, A, st));
+            launches++;
+        }
+    }
+    CK(ctx, launch_adj_prop_qsum(n, A, qsum, st));
+    std::vector<PropAdj> ah(n);
+    std::vector<double> accs((size_t)GE + 4);
+    int flags = 0;
+    CK(ctx, cudaMemcpyAsync(ah.data(), A, sizeof(PropAdj) * n, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(accs.data(), acc, sizeof(double) * (GE + 4), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    std::vector<double> yo((size_t)6 * n), gy((size_t)6 * n);
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < 6; k++) {
+            yo[6 * (size_t)i + k] = fin[i].y[k];
+            gy[6 * (size_t)i + k] = ah[i].lam[k];
+        }
+    if (y1) CK(ctx, cudaMemcpy(y1, yo.data(), sizeof(double) * 6 * n, cudaMemcpyDefault));
+    if (g_y0) CK(ctx, cudaMemcpy(g_y0, gy.data(), sizeof(double) * 6 * n, cudaMemcpyDefault));
+    if (g_mat) CK(ctx, cudaMemcpy(g_mat, accs.data(), sizeof(double) * NM2, cudaMemcpyDefault));
+    if (g_angle) CK(ctx, cudaMemcpy(g_angle, accs.data() + NM2, sizeof(double) * NP, cudaMemcpyDefault));
+    if (g_q) CK(ctx, cudaMemcpy(g_q, accs.data() + GE, sizeof(double) * 4, cudaMemcpyDefault));
+    if (stats)
+        for (int i = 0; i < n; i++) {
+            stats[i].steps = fin[i].steps;
+            stats[i].rejects = fin[i].rejects;
+            stats[i].evals = fin[i].evals;
+            stats[i].t = fin[i].t;
+            stats[i].status = fin[i].status;
+            stats[i].reserved = 0;
+        }
     ctx->last.launches = launches;
     ctx->last.trace_launches = trace_launches;
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");

@@ -16,8 +16,9 @@
 // err^(-1/8), 0.2, 5); or classical RK4 with a fixed step.  Forces: central
 // point mass, optional Earth J2 (z = pole) and the Sun as a third body from the
 // low-precision solar coordinates of Montenbruck & Gill (Satellite Orbits,
-// Sec. 3.3.2), SRP zero inside a cylindrical Earth shadow; attitude LVLH (body
-// z to nadir, body y along minus the orbit normal) or a fixed quaternion.
+// Sec. 3.3.2), SRP zero inside a cylindrical Earth shadow; attitude: the LVLH
+// frame (z to nadir, y along minus the orbit normal) turned by a constant
+// quaternion, or a fixed inertial quaternion.
 #include <math.h>
 
 #include "srp_internal.cuh"
@@ -74,25 +75,43 @@ __device__ void sun_pos(double mjd_tt, double *r)
     r[2] = rr * sin(lam) * se;
 }
 
-// body -> inertial rotation, row-major
-__device__ void body_to_inertial(const PropDev &P, const double *y, double *R)
+// rotation of the normalised scalar-first quaternion q, row-major
+__device__ void quat_matrix(const double *q, double *Q)
 {
-    if (P.attitude == 1) {
-        double w = P.q[0], x = P.q[1], yy = P.q[2], z = P.q[3];
-        double qn = sqrt(w * w + x * x + yy * yy + z * z);
-        w /= qn; x /= qn; yy /= qn; z /= qn;
-        R[0] = 1.0 - 2.0 * (yy * yy + z * z); R[1] = 2.0 * (x * yy - w * z);       R[2] = 2.0 * (x * z + w * yy);
-        R[3] = 2.0 * (x * yy + w * z);       R[4] = 1.0 - 2.0 * (x * x + z * z);   R[5] = 2.0 * (yy * z - w * x);
-        R[6] = 2.0 * (x * z - w * yy);       R[7] = 2.0 * (yy * z + w * x);       R[8] = 1.0 - 2.0 * (x * x + yy * yy);
-        return;
-    }
+    double w = q[0], x = q[1], yy = q[2], z = q[3];
+    double qn = sqrt(w * w + x * x + yy * yy + z * z);
+    w /= qn; x /= qn; yy /= qn; z /= qn;
+    Q[0] = 1.0 - 2.0 * (yy * yy + z * z); Q[1] = 2.0 * (x * yy - w * z);       Q[2] = 2.0 * (x * z + w * yy);
+    Q[3] = 2.0 * (x * yy + w * z);       Q[4] = 1.0 - 2.0 * (x * x + z * z);   Q[5] = 2.0 * (yy * z - w * x);
+    Q[6] = 2.0 * (x * z - w * yy);       Q[7] = 2.0 * (yy * z + w * x);       Q[8] = 1.0 - 2.0 * (x * x + yy * yy);
+}
+
+// LVLH frame at y: columns x_b = y_b x z_b, y_b = -orbit normal, z_b = nadir
+__device__ void lvlh_matrix(const double *y, double *L)
+{
     double rn = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
     double h[3] = {y[1] * y[5] - y[2] * y[4], y[2] * y[3] - y[0] * y[5], y[0] * y[4] - y[1] * y[3]};
     double hn = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
     double zb[3] = {-y[0] / rn, -y[1] / rn, -y[2] / rn};
     double yb[3] = {-h[0] / hn, -h[1] / hn, -h[2] / hn};
     double xb[3] = {yb[1] * zb[2] - yb[2] * zb[1], yb[2] * zb[0] - yb[0] * zb[2], yb[0] * zb[1] - yb[1] * zb[0]};
-    for (int k = 0; k < 3; k++) { R[3 * k] = xb[k]; R[3 * k + 1] = yb[k]; R[3 * k + 2] = zb[k]; }
+    for (int k = 0; k < 3; k++) { L[3 * k] = xb[k]; L[3 * k + 1] = yb[k]; L[3 * k + 2] = zb[k]; }
+}
+
+// body -> inertial rotation, row-major: Q(q) (inertial attitude) or
+// LVLH(y) Q(q) (the LVLH frame turned by the constant quaternion q)
+__device__ void body_to_inertial(const PropDev &P, const double *y, double *R)
+{
+    double Q[9];
+    quat_matrix(P.q, Q);
+    if (P.attitude == 1) {
+        for (int k = 0; k < 9; k++) R[k] = Q[k];
+        return;
+    }
+    double L[9];
+    lvlh_matrix(y, L);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) R[3 * i + j] = L[3 * i] * Q[j] + L[3 * i + 1] * Q[3 + j] + L[3 * i + 2] * Q[6 + j];
 }
 
 // Gravity of the configured bodies at (t, y).
@@ -266,6 +285,211 @@ __global__ void k_prop_control(PropState *S, int n, PropDev P, int *n_done, doub
     if (X.done) atomicAdd(n_done, 1);
 }
 
+
+// ------------------------------------------------------------------ adjoint
+// Discrete adjoint of the RK4 step y' = y + h sum_i b_i k_i, k_i = f(t_i, y_i),
+// y_i = y + h a_{i,i-1} k_{i-1}: with lam the cotangent of y',
+//   kbar_i = h b_i lam + h a_{i+1,i} ybar_{i+1},   ybar_i = (df/dy_i)^T kbar_i,
+//   lam_before = lam + sum_i ybar_i,
+// and the SRP part of df/dy_i, d f / d(parameters) through the frozen-hit
+// adjoint of the evaluation (adjoint.cu).  Stages run 3, 2, 1, 0.
+
+__device__ inline void save_ckpt(const PropState &X, double *b)
+{
+    b[0] = X.t;
+    for (int k = 0; k < 6; k++) b[1 + k] = X.y[k];
+}
+
+__global__ void k_prop_ckpt(PropState *S, int n, double *buf, int save, double h0)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PropState &X = S[i];
+    double *b = buf + 7 * (size_t)i;
+    if (save) {
+        save_ckpt(X, b);
+        return;
+    }
+    X.t = b[0];
+    for (int k = 0; k < 6; k++) X.y[k] = b[1 + k];
+    X.h = X.hs = h0;  // a fixed-step arc always proposes h0
+    X.done = X.t >= X.t1 ? 1 : 0;
+    X.status = 0;
+}
+
+__global__ void k_prop_record(const PropState *S, int n, const double *sun, const double *dist, const double *force,
+                              StageRec *rec, double *rec_sun, double *rec_dist)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const PropState &X = S[i];
+    StageRec &r = rec[i];
+    for (int k = 0; k < 6; k++) r.ys[k] = X.ys[k];
+    r.ts = X.ts;
+    r.hs = X.hs;
+    for (int k = 0; k < 9; k++) r.R[k] = X.R[k];
+    for (int k = 0; k < 3; k++) r.rsun[k] = X.rsun[k];
+    r.lit = dist[i] >= 0.0 ? 1 : 0;
+    for (int k = 0; k < 3; k++) {
+        r.F[k] = r.lit ? force[3 * i + k] : 0.0;
+        rec_sun[3 * i + k] = sun[3 * i + k];
+    }
+    rec_dist[i] = dist[i];
+}
+
+// kbar of this stage, and the cotangent of the body-frame SRP force
+__global__ void k_adj_prop_in(int n, PropDev P, int stage, const StageRec *rec, PropAdj *A, double *g_force)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const StageRec &r = rec[i];
+    PropAdj &X = A[i];
+    const double h = r.hs;
+    const double anext = stage == 2 ? 1.0 : 0.5;  // a_{stage+1, stage}
+    for (int k = 0; k < 6; k++)
+        X.kbar[k] = h * cB4[stage] * X.lam[k] + (stage < 3 ? h * anext * X.ybar[stage + 1][k] : 0.0);
+    const double *ab = X.kbar + 3;
+    for (int k = 0; k < 3; k++)
+        g_force[3 * i + k] = r.lit ? (r.R[k] * ab[0] + r.R[3 + k] * ab[1] + r.R[6 + k] * ab[2]) / P.mass : 0.0;
+}
+
+// (df/dy)^T kbar at this stage: gravity, SRP through the Sun direction,
+// distance and attitude; attitude quaternion cotangent
+__global__ void k_adj_prop_out(int n, PropDev P, int stage, const StageRec *rec, PropAdj *A, const double *g_sun,
+                               const double *g_dist)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const StageRec &r = rec[i];
+    PropAdj &X = A[i];
+    const double *y = r.ys, *ab = X.kbar + 3;
+    double rb[3] = {0, 0, 0}, vb[3] = {X.kbar[0], X.kbar[1], X.kbar[2]};  // x' = v
+    // central body: J = -mu (I / r^3 - 3 r r^T / r^5), symmetric
+    {
+        double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2], rn = sqrt(r2);
+        double mu = P.central == 1 ? kMuSun : kMuEarth;
+        double ra = y[0] * ab[0] + y[1] * ab[1] + y[2] * ab[2];
+        for (int k = 0; k < 3; k++) rb[k] += -mu * (ab[k] / (r2 * rn) - 3.0 * y[k] * ra / (r2 * r2 * rn));
+    }
+    if (P.central == 0 && P.j2) {
+        double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+        double z2 = y[2] * y[2] / r2;
+        double f = -1.5 * kJ2 * kMuEarth * kREarth * kREarth / (r2 * r2 * sqrt(r2));
+        double g[3] = {y[0] * (1.0 - 5.0 * z2), y[1] * (1.0 - 5.0 * z2), y[2] * (3.0 - 5.0 * z2)};
+        double fb = ab[0] * g[0] + ab[1] * g[1] + ab[2] * g[2];
+        rb[0] += f * ab[0] * (1.0 - 5.0 * z2);
+        rb[1] += f * ab[1] * (1.0 - 5.0 * z2);
+        rb[2] += f * ab[2] * (3.0 - 5.0 * z2);
+        double z2b = -5.0 * f * (ab[0] * y[0] + ab[1] * y[1] + ab[2] * y[2]);
+        rb[2] += z2b * 2.0 * y[2] / r2;
+        double r2b = -z2b * y[2] * y[2] / (r2 * r2) + fb * (-2.5) * f / r2;
+        for (int k = 0; k < 3; k++) rb[k] += 2.0 * r2b * y[k];
+    }
+    if (P.central == 0 && P.sun3) {
+        double d[3] = {r.rsun[0] - y[0], r.rsun[1] - y[1], r.rsun[2] - y[2]};
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dn = sqrt(d2);
+        double da = d[0] * ab[0] + d[1] * ab[1] + d[2] * ab[2];
+        for (int k = 0; k < 3; k++) rb[k] += -kMuSun * (ab[k] / (d2 * dn) - 3.0 * d[k] * da / (d2 * d2 * dn));
+    }
+    if (r.lit) {
+        // a_SRP = R F / m, s_body = R^T s_hat, s_hat = w / |w|, w = r_sun - r, dist = |w| / AU
+        const double *R = r.R, *gs = g_sun + 3 * i;
+        double Rb[9];
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) Rb[3 * a + b] = ab[a] * r.F[b] / P.mass;
+        double w[3] = {r.rsun[0] - y[0], r.rsun[1] - y[1], r.rsun[2] - y[2]};
+        double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        double sh[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+        double shb[3];
+        for (int a = 0; a < 3; a++) {
+            shb[a] = R[3 * a] * gs[0] + R[3 * a + 1] * gs[1] + R[3 * a + 2] * gs[2];
+            for (int b = 0; b < 3; b++) Rb[3 * a + b] += sh[a] * gs[b];
+        }
+        double sd = shb[0] * sh[0] + shb[1] * sh[1] + shb[2] * sh[2];
+        for (int k = 0; k < 3; k++) {
+            double wb = (shb[k] - sd * sh[k]) / wn + g_dist[i] * sh[k] / kAU;
+            rb[k] -= wb;
+        }
+        // attitude: R = Q(q) or R = L(y) Q(q)
+        double Q[9], L[9], Qb[9];
+        quat_matrix(P.q, Q);
+        if (P.attitude == 1) {
+            for (int k = 0; k < 9; k++) Qb[k] = Rb[k];
+        } else {
+            lvlh_matrix(y, L);
+            double Lb[9];
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    double x = 0.0, z = 0.0;
+                    for (int c = 0; c < 3; c++) {
+                        x += L[3 * c + a] * Rb[3 * c + b];  // Qb = L^T Rb
+                        z += Rb[3 * a + c] * Q[3 * b + c];  // Lb = Rb Q^T
+                    }
+                    Qb[3 * a + b] = x;
+                    Lb[3 * a + b] = z;
+                }
+            // L = [x_b y_b z_b]: x_b = y_b x z_b, y_b = -h / |h|, h = r x v, z_b = -r / |r|
+            double yb[3] = {L[1], L[4], L[7]}, zb[3] = {L[2], L[5], L[8]};
+            double xbb[3] = {Lb[0], Lb[3], Lb[6]}, ybb[3] = {Lb[1], Lb[4], Lb[7]}, zbb[3] = {Lb[2], Lb[5], Lb[8]};
+            ybb[0] += zb[1] * xbb[2] - zb[2] * xbb[1];
+            ybb[1] += zb[2] * xbb[0] - zb[0] * xbb[2];
+            ybb[2] += zb[0] * xbb[1] - zb[1] * xbb[0];
+            zbb[0] += xbb[1] * yb[2] - xbb[2] * yb[1];
+            zbb[1] += xbb[2] * yb[0] - xbb[0] * yb[2];
+            zbb[2] += xbb[0] * yb[1] - xbb[1] * yb[0];
+            const double *v = y + 3;
+            double hv[3] = {y[1] * v[2] - y[2] * v[1], y[2] * v[0] - y[0] * v[2], y[0] * v[1] - y[1] * v[0]};
+            double hn = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+            double hh[3] = {hv[0] / hn, hv[1] / hn, hv[2] / hn};
+            double yd = ybb[0] * hh[0] + ybb[1] * hh[1] + ybb[2] * hh[2];
+            double hb[3];
+            for (int k = 0; k < 3; k++) hb[k] = -(ybb[k] - yd * hh[k]) / hn;
+            rb[0] += v[1] * hb[2] - v[2] * hb[1];
+            rb[1] += v[2] * hb[0] - v[0] * hb[2];
+            rb[2] += v[0] * hb[1] - v[1] * hb[0];
+            vb[0] += hb[1] * y[2] - hb[2] * y[1];
+            vb[1] += hb[2] * y[0] - hb[0] * y[2];
+            vb[2] += hb[0] * y[1] - hb[1] * y[0];
+            double rn = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+            double rh[3] = {y[0] / rn, y[1] / rn, y[2] / rn};
+            double zd = zbb[0] * rh[0] + zbb[1] * rh[1] + zbb[2] * rh[2];
+            for (int k = 0; k < 3; k++) rb[k] += -(zbb[k] - zd * rh[k]) / rn;
+        }
+        // Q of the normalised quaternion, differentiated
+        double qn = sqrt(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
+        double w0 = P.q[0] / qn, x = P.q[1] / qn, yy = P.q[2] / qn, z = P.q[3] / qn;
+        double g[4];
+        g[0] = -2 * z * Qb[1] + 2 * yy * Qb[2] + 2 * z * Qb[3] - 2 * x * Qb[5] - 2 * yy * Qb[6] + 2 * x * Qb[7];
+        g[1] = 2 * yy * Qb[1] + 2 * z * Qb[2] + 2 * yy * Qb[3] - 4 * x * Qb[4] - 2 * w0 * Qb[5] + 2 * z * Qb[6] +
+               2 * w0 * Qb[7] - 4 * x * Qb[8];
+        g[2] = -4 * yy * Qb[0] + 2 * x * Qb[1] + 2 * w0 * Qb[2] + 2 * x * Qb[3] + 2 * z * Qb[5] - 2 * w0 * Qb[6] +
+               2 * z * Qb[7] - 4 * yy * Qb[8];
+        g[3] = -4 * z * Qb[0] - 2 * w0 * Qb[1] + 2 * x * Qb[2] + 2 * w0 * Qb[3] - 4 * z * Qb[4] + 2 * yy * Qb[5] +
+               2 * x * Qb[6] + 2 * yy * Qb[7];
+        double qh[4] = {w0, x, yy, z};
+        double gd = g[0] * qh[0] + g[1] * qh[1] + g[2] * qh[2] + g[3] * qh[3];
+        for (int k = 0; k < 4; k++) X.qbar[k] += (g[k] - gd * qh[k]) / qn;
+    }
+    for (int k = 0; k < 3; k++) { X.ybar[stage][k] = rb[k]; X.ybar[stage][3 + k] = vb[k]; }
+}
+
+// attitude quaternion cotangent summed over the trajectories, in order
+__global__ void k_adj_prop_qsum(int n, const PropAdj *A, double *out)
+{
+    if (threadIdx.x >= 4) return;
+    double x = 0.0;
+    for (int i = 0; i < n; i++) x += A[i].qbar[threadIdx.x];
+    out[threadIdx.x] = x;
+}
+
+__global__ void k_adj_prop_step(int n, PropAdj *A)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PropAdj &X = A[i];
+    for (int k = 0; k < 6; k++) X.lam[k] += X.ybar[0][k] + X.ybar[1][k] + X.ybar[2][k] + X.ybar[3][k];
+}
+
 }  // namespace
 
 cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double *t01, double h0, int *n_done,
@@ -289,6 +513,40 @@ cudaError_t launch_prop_control(PropState *S, int n, const PropDev &P, int *n_do
                                 cudaStream_t st)
 {
     k_prop_control<<<(n + 63) / 64, 64, 0, st>>>(S, n, P, n_done, h_log, h_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prop_ckpt(PropState *S, int n, double *buf, bool save, double h0, cudaStream_t st)
+{
+    k_prop_ckpt<<<(n + 63) / 64, 64, 0, st>>>(S, n, buf, save ? 1 : 0, h0);
+    return cudaGetLastError();
+}
+cudaError_t launch_prop_record(const PropState *S, int n, const double *sun, const double *dist, const double *force,
+                               StageRec *rec, double *rec_sun, double *rec_dist, cudaStream_t st)
+{
+    k_prop_record<<<(n + 63) / 64, 64, 0, st>>>(S, n, sun, dist, force, rec, rec_sun, rec_dist);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_prop_in(int n, const PropDev &P, int stage, const StageRec *rec, PropAdj *A, double *g_force,
+                               cudaStream_t st)
+{
+    k_adj_prop_in<<<(n + 63) / 64, 64, 0, st>>>(n, P, stage, rec, A, g_force);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_prop_out(int n, const PropDev &P, int stage, const StageRec *rec, PropAdj *A,
+                                const double *g_sun, const double *g_dist, cudaStream_t st)
+{
+    k_adj_prop_out<<<(n + 63) / 64, 64, 0, st>>>(n, P, stage, rec, A, g_sun, g_dist);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_prop_qsum(int n, const PropAdj *A, double *out, cudaStream_t st)
+{
+    k_adj_prop_qsum<<<1, 32, 0, st>>>(n, A, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_prop_step(int n, PropAdj *A, cudaStream_t st)
+{
+    k_adj_prop_step<<<(n + 63) / 64, 64, 0, st>>>(n, A);
     return cudaGetLastError();
 }
 

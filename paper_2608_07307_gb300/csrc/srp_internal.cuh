@@ -162,6 +162,24 @@ struct PropState {
     int done, status, shadow, pad_;
 };
 
+// One stage of an RK4 step, recorded for the reverse pass of the propagation adjoint.
+struct StageRec {
+    double ys[6], ts, hs;  // stage state and time, step size
+    double R[9];           // body -> inertial at the stage
+    double rsun[3];        // Sun position at the stage time
+    double F[3];           // SRP force, body frame (N); zero when not lit
+    int lit;               // the SRP evaluation ran (SRP on, not shadowed)
+    int pad_;
+};
+
+// Reverse-pass state of one trajectory.
+struct PropAdj {
+    double lam[6];      // cotangent of the state at the current step boundary
+    double ybar[4][6];  // cotangents of the current step's stage states
+    double kbar[6];     // cotangent of the current stage derivative
+    double qbar[4];     // attitude quaternion cotangent, summed over the arc
+};
+
 // ordered-int encoding of doubles for atomicMin/Max
 __host__ __device__ inline unsigned long long dbl_to_ord(double x)
 {
@@ -229,7 +247,7 @@ constexpr int kAdjFixed = 14;    // dbar(3) ubar(3) vbar(3) umin umax vmin vmax,
 int adj_blocks(int S, size_t rays);
 cudaError_t launch_adjoint(const AdjArgs &a, int S, cudaStream_t st);
 cudaError_t launch_adj_sum(const double *g_eval, int n, int n_mats, int n_parts, double *g_mat, double *g_angle,
-                           cudaStream_t st);
+                           cudaStream_t st, bool accumulate = false);
 
 // prop.cu
 cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double *t01, double h0, int *n_done,
@@ -239,5 +257,15 @@ cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, 
 cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st);
 cudaError_t launch_prop_control(PropState *S, int n, const PropDev &P, int *n_done, double *h_log, int64_t h_cap,
                                 cudaStream_t st);
+// propagation adjoint (RK4): checkpoints, stage records, reverse stage sweep
+cudaError_t launch_prop_ckpt(PropState *S, int n, double *buf, bool save, double h0, cudaStream_t st);
+cudaError_t launch_prop_record(const PropState *S, int n, const double *sun, const double *dist, const double *force,
+                               StageRec *rec, double *rec_sun, double *rec_dist, cudaStream_t st);
+cudaError_t launch_adj_prop_in(int n, const PropDev &P, int stage, const StageRec *rec, PropAdj *A, double *g_force,
+                               cudaStream_t st);
+cudaError_t launch_adj_prop_out(int n, const PropDev &P, int stage, const StageRec *rec, PropAdj *A,
+                                const double *g_sun, const double *g_dist, cudaStream_t st);
+cudaError_t launch_adj_prop_step(int n, PropAdj *A, cudaStream_t st);
+cudaError_t launch_adj_prop_qsum(int n, const PropAdj *A, double *out, cudaStream_t st);
 
 }  // namespace srp

@@ -26,7 +26,7 @@ MAX_BOUNCES = 4
 # Symbols declared in include/srp.h (checked by the tests against the library).
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",
            "srp_eval_batch", "srp_eval_stats_get", "srp_propagate", "srp_eval_noalloc", "srp_set_materials",
-           "srp_grad"]
+           "srp_grad", "srp_prop_grad"]
 
 
 class SrpError(RuntimeError):
@@ -106,6 +106,9 @@ def load(build_if_needed: bool = True):
         lib.srp_eval_stats_get.argtypes = [C.c_void_p, C.POINTER(EvalStats)]
         lib.srp_set_materials.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
         lib.srp_grad.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32] + [C.c_void_p] * 10
+        lib.srp_prop_grad.argtypes = [C.c_void_p, C.c_int32, C.POINTER(PropParams), C.c_int32, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.POINTER(PropStats)]
         lib.srp_propagate.argtypes = [C.c_void_p, C.c_int32, C.POINTER(PropParams), C.c_int32, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(PropStats), C.c_void_p, C.c_int64]
         lib.srp_eval_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
@@ -345,6 +348,31 @@ class Context:
                 out["angle"]]
         ptrs = [_ptr(x) for x in args]
         self._check(self.lib.srp_grad(self.h, mesh_id, C.byref(p), n, *[q[0] for q in ptrs]))
+        return out
+
+    def prop_grad(self, mesh_id: int, y0, t0_t1, g_y1, ckpt_every: int = 100, central: int = CENTRAL_EARTH,
+                  j2=False, sun3=False, srp_on=True, attitude: int = ATT_LVLH, q=(1.0, 0.0, 0.0, 0.0),
+                  epoch_mjd_tt: float = 61041.0, h0: float = 60.0, max_steps: int = 10_000_000, N: int = 64,
+                  bounces: int = 1, P0: float = 4.56e-6, eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK):
+        """srp_prop_grad: RK4 arc and the gradients of sum g_y1 . y1.  Returns
+        a dict with y1 [n,6], y0 [n,6] (gradient), mat [M,2], angle [P], q [4]
+        and the per-trajectory stats."""
+        y0 = np.ascontiguousarray(np.asarray(y0, np.float64).reshape(-1, 6))
+        n = len(y0)
+        t01 = np.ascontiguousarray(np.asarray(t0_t1, np.float64).reshape(n, 2))
+        g1 = np.ascontiguousarray(np.asarray(g_y1, np.float64).reshape(n, 6))
+        p = PropParams(RK4, central, int(j2), int(sun3), int(srp_on), attitude, (C.c_double * 4)(*q), epoch_mjd_tt,
+                       0.0, 0.0, 0.0, h0, 0.0, 0.0, max_steps, 0, 0, EvalParams(N, bounces, P0, eps_rel, panel_mode, 0),
+                       None, 0)
+        info = self.mesh_info[mesh_id]
+        out = dict(y1=np.empty((n, 6)), y0=np.empty((n, 6)), mat=np.empty((info["n_mats"], 2)),
+                   angle=np.empty(info["n_parts"]), q=np.empty(4))
+        st = (PropStats * n)()
+        self._check(self.lib.srp_prop_grad(self.h, mesh_id, C.byref(p), n, y0.ctypes.data, t01.ctypes.data,
+                                           g1.ctypes.data, int(ckpt_every), out["y1"].ctypes.data,
+                                           out["y0"].ctypes.data, out["mat"].ctypes.data, out["angle"].ctypes.data,
+                                           out["q"].ctypes.data, st))
+        out["stats"] = [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status) for s in st]
         return out
 
     def eval_stats(self) -> dict:
