@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--bounces", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-prop", action="store_true", help="skip the propagation measurement")
+    p.add_argument("--no-grad", action="store_true", help="skip the differentiated-form measurement")
+    p.add_argument("--grad-arc-steps", type=int, default=1000,
+                   help="RK4 steps of the timed adjoint arc (the full differentiated arc is 10000)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     return p.parse_args()
 
@@ -183,6 +186,70 @@ def bench_propagation(ctx, mid, mesh, arc_s=6 * 3600.0, N=512, bounces=1):
             "speedup_vs_host_loop": out["graph"]["steps_per_s"] / out["host_loop"]["steps_per_s"], "runs": out}
 
 
+# --------------------------------------------------------- differentiated
+def bench_differentiated(ctx, stream, arc_steps, facet=0.05, N=512, bounces=1, batch=32, reps=5):
+    """The differentiated form: the 50k-triangle spacecraft, 512^2 rays, 1
+    bounce.  (1) srp_grad (evaluation + frozen-hit adjoint) against
+    srp_eval_batch on the same batch of directions, CUDA events on the
+    context's stream; (2) srp_prop_grad over a GEO RK4 arc at 60 s with
+    checkpoints every 100 steps against srp_propagate's RK4 arc (wall clock,
+    both synchronous)."""
+    import math
+
+    import numpy as np
+    import torch
+    from paper_2608_07307_gb300 import inputs as I
+    from paper_2608_07307_gb300 import srp
+
+    mesh = I.spacecraft(facet)
+    mid = ctx.load_mesh(mesh)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = torch.tensor(I.sun_dirs_fibonacci(4096)[:batch], device=dev)
+    dist = torch.ones(batch, dtype=torch.float64, device=dev)
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    gF = torch.randn((batch, 3), dtype=torch.float64, generator=gen).to(dev)
+    gT = torch.randn((batch, 3), dtype=torch.float64, generator=gen).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        calls = {"eval": lambda: ctx.eval_batch(mid, d, dist, N=N, bounces=bounces),
+                 "grad": lambda: ctx.grad(mid, d, gF, gT, sun_dist=dist, N=N, bounces=bounces)}
+        for name, fn in calls.items():
+            for _ in range(2):
+                fn()
+            ms = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                stream.synchronize()
+                ms += e0.elapsed_time(e1)
+            out[name] = batch * reps / (ms / 1000.0)
+    a_geo, inc = 42164e3, math.radians(0.1)
+    v = math.sqrt(3.986004418e14 / a_geo)
+    y0 = np.array([a_geo, 0.0, 0.0, 0.0, v * math.cos(inc), v * math.sin(inc)])
+    kw = dict(j2=True, sun3=True, N=N, bounces=bounces, h0=60.0)
+    T = arc_steps * 60.0
+    ctx.propagate(mid, y0, [0.0, 600.0], method=srp.RK4, **kw)
+    ctx.prop_grad(mid, y0[None], [[0.0, 600.0]], np.array([[1.0, 0, 0, 0, 0, 0]]), ckpt_every=100, **kw)
+    t0 = time.perf_counter()
+    ctx.propagate(mid, y0, [0.0, T], method=srp.RK4, **kw)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = ctx.prop_grad(mid, y0[None], [[0.0, T]], np.array([[1.0, 0, 0, 0, 0, 0]]), ckpt_every=100, **kw)
+    t_adj = time.perf_counter() - t0
+    ctx.free_mesh(mid)
+    return {"workload": f"spacecraft facet {facet} m ({mesh.n_tris} triangles), N={N}, bounces={bounces}, "
+                        f"batch {batch}; GEO RK4 arc of {arc_steps} steps at 60 s, checkpoints every 100",
+            "grad_evals_per_s": out["grad"], "eval_evals_per_s": out["eval"],
+            "grad_cost_vs_eval": out["eval"] / out["grad"],
+            "arc_steps": arc_steps, "arc_forward_steps_per_s": arc_steps / t_fwd,
+            "arc_adjoint_steps_per_s": arc_steps / t_adj, "arc_adjoint_cost_vs_forward": t_adj / t_fwd,
+            "arc_gradient_of_x": {"mat": g["mat"].tolist(), "angle": g["angle"].tolist(), "q": g["q"].tolist()}}
+
+
 # ------------------------------------------------------------------ native
 def run_native(a):
     import numpy as np
@@ -304,6 +371,8 @@ def run_native(a):
     }
     if not a.no_prop:
         line["propagation"] = bench_propagation(ctx, mid, mesh)
+    if not a.no_grad:
+        line["differentiated"] = bench_differentiated(ctx, stream, a.grad_arc_steps)
     if not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mesh, table[:8], a, a.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -8,7 +8,7 @@
 //   k_adj_window  one block per slot: the posed vertices extreme along u and v
 //                 (lowest vertex index among equal projections).
 //   k_adj_rays    grid-stride over the rays of every slot: per ray, the
-//                 segments are replayed forward in FP64 from the recorded hits,
+//                 segments are replayed forward in FP32 from the recorded hits,
 //                 then swept backward; cotangents of the ray direction, the
 //                 basis, the window bounds and the local loss stay in
 //                 registers; per-coefficient and per-part terms are summed
@@ -135,6 +135,49 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_window(AdjArgs a)
 }
 
 // --------------------------------------------------------------- rays
+// Per-ray arithmetic is FP32 (GB300's FP64 rate is a small fraction of its
+// FP32 rate; a ray's terms are O(1) with relative rounding ~1e-7), sums over
+// rays are FP64 from the warp level up.
+struct F3 {
+    float x, y, z;
+};
+__device__ inline F3 f3(float x, float y, float z) { return {x, y, z}; }
+__device__ inline F3 f3(V3 a) { return {(float)a.x, (float)a.y, (float)a.z}; }
+__device__ inline F3 operator+(F3 a, F3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ inline F3 operator-(F3 a, F3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ inline F3 operator*(float s, F3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ inline F3 &operator+=(F3 &a, F3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
+__device__ inline float dot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ inline F3 cross(F3 a, F3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+
+__device__ inline float wsumf(float x)
+{
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+// FP32 copy of a posed vertex
+__device__ inline F3 vertex32(const MeshDev &m, const SlotBufs &sb, int s, int v) { return f3(vertex(m, sb, s, v)); }
+
+// warp_scatter with FP32 lane values and FP64 accumulation
+template <int n>
+__device__ inline void warp_scatter32(int key, const float *val, double *row)
+{
+    unsigned todo = __ballot_sync(kFull, key >= 0);
+    while (todo) {
+        int k = __shfl_sync(kFull, key, __ffs(todo) - 1);
+        bool mine = key == k;
+        float sum[n];
+#pragma unroll
+        for (int c = 0; c < n; c++) sum[c] = wsumf(mine ? val[c] : 0.0f);
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int c = 0; c < n; c++) row[k * n + c] += (double)sum[c];
+        }
+        todo &= ~__ballot_sync(kFull, mine);
+    }
+}
+
 __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
 {
     const int s = blockIdx.y;
@@ -155,13 +198,13 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
         win[threadIdx.x] = dot(threadIdx.x < 2 ? ld3(P.u) : ld3(P.v), x);
     }
     __syncthreads();
-    const V3 u = ld3(P.u), v = ld3(P.v), d0 = ld3(P.d), cref = ld3(m.c_ref);
-    const V3 gF = ld3(a.g_force + 3 * (size_t)e), gT = ld3(a.g_torque + 3 * (size_t)e);
-    const double umin = win[0], umax = win[1], vmin = win[2], vmax = win[3];
-    const double Du = (umax - umin) / N, Dv = (vmax - vmin) / N;
+    const F3 u = f3(ld3(P.u)), v = f3(ld3(P.v)), d0 = f3(ld3(P.d)), cref = f3(ld3(m.c_ref));
+    const F3 gF = f3(ld3(a.g_force + 3 * (size_t)e)), gT = f3(ld3(a.g_torque + 3 * (size_t)e));
+    const float umin = (float)win[0], vmin = (float)win[2];
+    const float Du = (float)((win[1] - win[0]) / N), Dv = (float)((win[3] - win[2]) / N);
     const size_t R = (size_t)N * N;
-    V3 acc_d = v3(0, 0, 0), acc_u = v3(0, 0, 0), acc_v = v3(0, 0, 0);
-    double acc_w[4] = {0, 0, 0, 0}, acc_l = 0.0;
+    F3 acc_d = f3(0, 0, 0), acc_u = f3(0, 0, 0), acc_v = f3(0, 0, 0);
+    float acc_w[4] = {0, 0, 0, 0}, acc_l = 0.0f;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     // every lane of a warp runs the same number of iterations (warp_scatter needs the whole warp)
     const size_t iters = (R + stride - 1) / stride;
@@ -179,104 +222,105 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
             }
         }
         const int i = live ? (int)(ray / N) : 0, j = live ? (int)(ray % N) : 0;
-        const double al = (i + 0.5) / N, be = (j + 0.5) / N;
-        const double uc = umin + (i + 0.5) * Du, vc = vmin + (j + 0.5) * Dv;
+        const float al = (i + 0.5f) / N, be = (j + 0.5f) / N;
+        const float uc = fmaf(i + 0.5f, Du, umin), vc = fmaf(j + 0.5f, Dv, vmin);
         // forward replay: origin, direction and weight entering each segment
-        V3 so[kMaxBounces + 1], sd[kMaxBounces + 1];
-        double sw[kMaxBounces + 1];
+        F3 so[kMaxBounces + 1], sd[kMaxBounces + 1];
+        float sw[kMaxBounces + 1];
         {
-            V3 o = uc * u + vc * v, d = d0;
-            double w = 1.0;
+            F3 o = uc * u + vc * v, d = d0;
+            float w = 1.0f;
             for (int k = 0; k < nh; k++) {
                 so[k] = o; sd[k] = d; sw[k] = w;
                 int4 tv = m.tri_v4[tri[k]];
-                V3 A = vertex(m, a.slot, s, tv.x), B = vertex(m, a.slot, s, tv.y), C = vertex(m, a.slot, s, tv.z);
-                V3 n = cross(B - A, C - A);
-                n = (1.0 / sqrt(dot(n, n))) * n;
-                double dn = dot(d, n);
-                double t = dot(n, A - o) / dn;
-                V3 x = o + t * d;
+                F3 A = vertex32(m, a.slot, s, tv.x), B = vertex32(m, a.slot, s, tv.y), C = vertex32(m, a.slot, s, tv.z);
+                F3 n = cross(B - A, C - A);
+                n = rsqrtf(dot(n, n)) * n;
+                float dn = dot(d, n);
+                float t = dot(n, A - o) / dn;
+                F3 x = o + t * d;
                 unsigned mp = m.tri_mat[tri[k]];
-                int mi = dn < 0.0 ? (int)(mp & 0xffffu) : (int)(mp >> 16);
-                w *= m.mat64[2 * mi];
-                d = d - (2.0 * dn) * n;
+                int mi = dn < 0.0f ? (int)(mp & 0xffffu) : (int)(mp >> 16);
+                w *= m.mat32[mi].x;
+                d = d - (2.0f * dn) * n;
                 o = x;
             }
         }
         // backward sweep, uniform over the warp
-        V3 ob = v3(0, 0, 0), db = v3(0, 0, 0);
-        double wb = 0.0;
+        F3 ob = f3(0, 0, 0), db = f3(0, 0, 0);
+        float wb = 0.0f;
         for (int k = nseg - 1; k >= 0; k--) {
             const bool act = k < nh;
             int mkey = -1, pkey = -1;
-            double mval[2] = {0.0, 0.0}, pval[6] = {0, 0, 0, 0, 0, 0};
+            float mval[2] = {0.0f, 0.0f}, pval[6] = {0, 0, 0, 0, 0, 0};
             if (act) {
-                const V3 o = so[k], d = sd[k];
-                const double w = sw[k];
+                const F3 o = so[k], d = sd[k];
+                const float w = sw[k];
                 const int4 tv = m.tri_v4[tri[k]];
-                const V3 A = vertex(m, a.slot, s, tv.x), B = vertex(m, a.slot, s, tv.y), C = vertex(m, a.slot, s, tv.z);
-                const V3 e1 = B - A, e2 = C - A, mr = cross(e1, e2);
-                const double ml = sqrt(dot(mr, mr));
-                const V3 n = (1.0 / ml) * mr;
-                const double dn = dot(d, n);
-                const V3 ao = A - o;
-                const double t = dot(n, ao) / dn;
-                const V3 x = o + t * d;
+                const F3 A = vertex32(m, a.slot, s, tv.x), B = vertex32(m, a.slot, s, tv.y),
+                         C = vertex32(m, a.slot, s, tv.z);
+                const F3 e1 = B - A, e2 = C - A, mr = cross(e1, e2);
+                const float il = rsqrtf(dot(mr, mr));
+                const F3 n = il * mr;
+                const float dn = dot(d, n);
+                const F3 ao = A - o;
+                const float t = dot(n, ao) / dn;
+                const F3 x = o + t * d;
                 const unsigned mp = m.tri_mat[tri[k]];
-                const bool front = dn < 0.0;
+                const bool front = dn < 0.0f;
                 const int mi = front ? (int)(mp & 0xffffu) : (int)(mp >> 16);
-                const double rs = m.mat64[2 * mi], rd = m.mat64[2 * mi + 1];
-                const double sg = front ? 1.0 : -1.0;
-                const V3 nf = sg * n;
-                const double c = -dot(nf, d);
-                const double kq = rs * c + rd / 3.0;
-                const V3 q = (1.0 - rs) * d - (2.0 * kq) * nf;
-                const V3 f = w * q;
-                const V3 r = x - cref;
+                const float2 rho = m.mat32[mi];
+                const float rs = rho.x, rd = rho.y;
+                const float sg = front ? 1.0f : -1.0f;
+                const F3 nf = sg * n;
+                const float c = -dot(nf, d);
+                const float kq = rs * c + rd * (1.0f / 3.0f);
+                const F3 q = (1.0f - rs) * d - (2.0f * kq) * nf;
+                const F3 f = w * q;
+                const F3 r = x - cref;
                 acc_l += dot(gF, f) + dot(gT, cross(r, f));
                 // cotangents
-                const V3 fb = gF + cross(gT, r);
-                V3 xb = cross(f, gT) + ob;           // ob: cotangent of the next segment's origin (= x)
-                double wl = dot(fb, q);               // cotangent of w
-                const V3 qb = w * fb;
-                double rsb = dot(qb, -1.0 * d - (2.0 * c) * nf);
-                double rdb = -(2.0 / 3.0) * dot(qb, nf);
-                V3 dbl = (1.0 - rs) * qb;             // cotangent of d (this segment)
-                double cb = -2.0 * rs * dot(qb, nf);
-                V3 nfb = (-2.0 * kq) * qb;
-                double dnb = 0.0;
-                V3 nb = v3(0, 0, 0);
+                const F3 fb = gF + cross(gT, r);
+                const F3 xb = cross(f, gT) + ob;      // ob: cotangent of the next segment's origin (= x)
+                float wl = dot(fb, q);                // cotangent of w
+                const F3 qb = w * fb;
+                float rsb = dot(qb, -1.0f * d - (2.0f * c) * nf);
+                float rdb = -(2.0f / 3.0f) * dot(qb, nf);
+                F3 dbl = (1.0f - rs) * qb;            // cotangent of d (this segment)
+                const float cb = -2.0f * rs * dot(qb, nf);
+                F3 nfb = (-2.0f * kq) * qb;
+                float dnb = 0.0f;
+                F3 nb = f3(0, 0, 0);
                 if (k + 1 < nh) {                     // the next segment's d' = d - 2 dn n and w' = w rho_s
                     rsb += wb * w;
                     wl += wb * rs;
                     dbl += db;
-                    dnb += -2.0 * dot(db, n);
-                    nb += (-2.0 * dn) * db;
+                    dnb += -2.0f * dot(db, n);
+                    nb += (-2.0f * dn) * db;
                 }
                 nfb += (-cb) * d;                     // c = -nf . d
                 dbl += (-cb) * nf;
                 nb += sg * nfb;
-                V3 obl = xb;                          // x = o + t d
-                const double tb = dot(xb, d);
+                F3 obl = xb;                          // x = o + t d
+                const float tb = dot(xb, d);
                 dbl += t * xb;
-                const double naob = tb / dn;          // t = (n . ao) / dn
+                const float naob = tb / dn;           // t = (n . ao) / dn
                 dnb += -tb * t / dn;
                 nb += naob * ao;
-                V3 Ab = naob * n;
+                F3 Ab = naob * n;
                 obl += (-naob) * n;
                 dbl += dnb * n;                       // dn = d . n
                 nb += dnb * d;
-                const V3 mb = (1.0 / ml) * (nb - dot(nb, n) * n);
-                const V3 e1b = cross(e2, mb), e2b = cross(mb, e1);
-                const V3 Bb = e1b, Cb = e2b;
-                Ab += -1.0 * (e1b + e2b);
+                const F3 mb = il * (nb - dot(nb, n) * n);
+                const F3 e1b = cross(e2, mb), e2b = cross(mb, e1);
+                Ab += -1.0f * (e1b + e2b);
                 mkey = mi;
                 mval[0] = rsb;
                 mval[1] = rdb;
                 const int pp = m.vert_part[tv.x];
                 if (m.part[pp].dynamic) {
                     pkey = pp;
-                    V3 G = Ab + Bb + Cb, Mm = cross(A, Ab) + cross(B, Bb) + cross(C, Cb);
+                    const F3 G = Ab + e1b + e2b, Mm = cross(A, Ab) + cross(B, e1b) + cross(C, e2b);
                     pval[0] = G.x; pval[1] = G.y; pval[2] = G.z;
                     pval[3] = Mm.x; pval[4] = Mm.y; pval[5] = Mm.z;
                 }
@@ -284,26 +328,26 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
                 db = dbl;
                 wb = wl;
             }
-            warp_scatter<2>(mkey, mval, row + kAdjFixed);
-            warp_scatter<6>(pkey, pval, row + kAdjFixed + nm2);
+            warp_scatter32<2>(mkey, mval, row + kAdjFixed);
+            warp_scatter32<6>(pkey, pval, row + kAdjFixed + nm2);
         }
         if (nh > 0) {
             // primary origin o = uc u + vc v (its component along d does not move the hit point)
             acc_d += db;
             acc_u += uc * ob;
             acc_v += vc * ob;
-            const double ucb = dot(u, ob), vcb = dot(v, ob);
-            acc_w[0] += (1.0 - al) * ucb;
+            const float ucb = dot(u, ob), vcb = dot(v, ob);
+            acc_w[0] += (1.0f - al) * ucb;
             acc_w[1] += al * ucb;
-            acc_w[2] += (1.0 - be) * vcb;
+            acc_w[2] += (1.0f - be) * vcb;
             acc_w[3] += be * vcb;
         }
     }
-    double fix[kAdjFixed] = {acc_d.x, acc_d.y, acc_d.z, acc_u.x, acc_u.y, acc_u.z, acc_v.x, acc_v.y, acc_v.z,
-                             acc_w[0], acc_w[1], acc_w[2], acc_w[3], acc_l};
+    float fix[kAdjFixed] = {acc_d.x, acc_d.y, acc_d.z, acc_u.x, acc_u.y, acc_u.z, acc_v.x, acc_v.y, acc_v.z,
+                            acc_w[0], acc_w[1], acc_w[2], acc_w[3], acc_l};
 #pragma unroll
     for (int c = 0; c < kAdjFixed; c++) {
-        double x = wsum(fix[c]);
+        double x = wsum((double)fix[c]);
         if (lane == 0) row[c] += x;
     }
     __syncthreads();
