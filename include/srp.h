@@ -314,6 +314,71 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
                          const double *y0, const double *t0_t1, double *y1, srp_prop_stats *stats, double *h_log,
                          int64_t h_cap);
 
+/* ---------------------------------------------------- batched propagation */
+/* One trajectory of a heterogeneous batch (srp_propagate_batch). */
+typedef struct {
+    int32_t mesh_id;        /* a loaded mesh                                                   */
+    int32_t N;              /* rays per side of this trajectory's SRP evaluations               */
+    int32_t bounces;        /* specular levels                                                  */
+    int32_t panel_mode;     /* SRP_PANELS_*                                                     */
+    const double *angles;   /* [n_parts] host: commanded angles / tracking offsets, or NULL for
+                               the mesh's values (srp_set_panel_angles)                          */
+    int32_t central;        /* SRP_CENTRAL_*                                                    */
+    int32_t attitude;       /* SRP_ATT_*                                                        */
+    double q[4];            /* attitude quaternion, scalar first (see srp_prop_params)          */
+    double y0[6];           /* initial position (m) and velocity (m/s), inertial                */
+    double t0, t1;          /* start and end time (s after the epoch)                           */
+} srp_traj;
+
+/*
+ * Propagate a batch of trajectories that may differ in mesh, ray grid, bounce
+ * count, joint law, central body and attitude (Sec. 3 Eqs. 1-3 with the
+ * evaluation of srp_eval_batch in every stage), in persistent graph-captured
+ * rounds.  Every integrator stage evaluates the SRP force of all running
+ * trajectories in one pipeline: one launch per kernel covers the work items
+ * (trajectory, tile) of every mesh and grid at once (each slot carries its own
+ * mesh, grid, bounces, joint values and tile shape).  A round relaunches the
+ * captured step until the furthest trajectory is likely done; when half of the
+ * running trajectories have finished, the rest are compacted into fewer slots
+ * and the step is captured again.  Results equal srp_propagate's for each
+ * trajectory alone (same kernels; the per-slot sums do not depend on the batch).
+ *   params  shared settings: method, j2, sun3, srp, epoch, tolerances, h0,
+ *           h_min, h_max, max_steps, poll, eval.P0, eval.eps_rel; eval.flags may
+ *           hold SRP_EVAL_AUTOTUNE (tune the tile shape of every new (mesh, N,
+ *           bounces) key first, see srp_autotune).  Its central, attitude, q,
+ *           eval.N, eval.bounces, eval.panel_mode, h_replay and host_loop are
+ *           ignored: each srp_traj supplies its own.
+ *   traj    [n] host
+ *   y1      [n][6] out; stats [n] out (may be NULL)
+ * Errors: SRP_ERR_ARG (a bad field; its index in srp_last_error), SRP_ERR_STATE
+ * (bad mesh id), SRP_ERR_STEP, SRP_ERR_STACK, SRP_ERR_OOM, SRP_ERR_CUDA.
+ */
+srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *params, int32_t n, const srp_traj *traj,
+                               double *y1, srp_prop_stats *stats);
+
+#define SRP_EVAL_AUTOTUNE 4 /* srp_propagate_batch: autotune every new (mesh, N, bounces) key */
+
+/*
+ * Autotuner of the trace launch shape: times srp_eval_batch's pipeline on 8
+ * fixed Sun directions (a Fibonacci sphere) with each trace tile shape
+ * (4 x 8, 8 x 4, 16 x 2 and 32 x 1 pixels per warp), and keeps the fastest for
+ * (mesh, params->N, params->bounces) in the context; later evaluations,
+ * propagations and batches with that key use it.  Forces and hit decisions do
+ * not depend on the tile shape (sums of tile partials change order: results
+ * agree to rounding).
+ *   tile_w  out (may be NULL): the chosen tile width in pixels
+ *   ms      out (may be NULL): [4] milliseconds per evaluation of each shape
+ * Errors: as srp_eval_batch.
+ */
+srp_status srp_autotune(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *params, int32_t *tile_w, double *ms);
+
+/*
+ * Set the trace tile width (4, 8, 16 or 32 pixels; the tile is 32 pixels) for
+ * (mesh, N, bounces) in the context, as srp_autotune would.  The default is 8.
+ * Errors: SRP_ERR_ARG (bad id or width).
+ */
+srp_status srp_set_tile_shape(srp_ctx *ctx, int32_t mesh_id, int32_t N, int32_t bounces, int32_t tile_w);
+
 /*
  * Discrete adjoint of an RK4 arc (Sec. 3, Eqs. 1-3, with the frozen-hit SRP
  * gradient of srp_grad in every stage).  Propagates like srp_propagate with

@@ -67,12 +67,12 @@ __device__ inline double wsum(double x)
     return x;
 }
 
-// posed FP64 position of (re-indexed) vertex v in slot s
-__device__ inline V3 vertex(const MeshDev &m, const SlotBufs &sb, int s, int v)
+// posed FP64 position of (re-indexed) vertex v of a slot
+__device__ inline V3 vertex(const MeshDev &m, const SlotBufs &sb, int v)
 {
     const PartInfo &pi = m.part[m.vert_part[v]];
     if (!pi.dynamic) return ld3(m.rest64 + 3 * (size_t)v);
-    return ld3(sb.vert64 + ((size_t)s * m.n_dyn_verts + (v - pi.vert_begin + pi.dyn_vert_off)) * 3);
+    return ld3(sb.vert64 + (size_t)(v - pi.vert_begin + pi.dyn_vert_off) * 3);
 }
 
 // Add val[0..n) of the lanes holding `key` (>= 0) into row[key * n ..], for
@@ -101,30 +101,31 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_window(AdjArgs a)
     const int s = blockIdx.x;
     const SlotPose &P = a.pose[s];
     if (P.skip) return;
-    const MeshDev &m = *a.mesh_d;
+    const MeshDev &m = *a.sd[s].mesh;
+    const SlotBufs &sb = a.sd[s].sb;
     V3 u = ld3(P.u), v = ld3(P.v);
     double best[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
     int id[4] = {-1, -1, -1, -1};
     for (int k = threadIdx.x; k < m.n_verts; k += blockDim.x) {  // ascending k per thread
-        V3 x = vertex(m, a.slot, s, k);
+        V3 x = vertex(m, sb, k);
         double pu = dot(u, x), pv = dot(v, x);
         if (pu < best[0]) { best[0] = pu; id[0] = k; }
         if (pu > best[1]) { best[1] = pu; id[1] = k; }
         if (pv < best[2]) { best[2] = pv; id[2] = k; }
         if (pv > best[3]) { best[3] = pv; id[3] = k; }
     }
-    __shared__ double sb[4][kAdjThreads];
+    __shared__ double sv[4][kAdjThreads];
     __shared__ int si[4][kAdjThreads];
-    for (int c = 0; c < 4; c++) { sb[c][threadIdx.x] = best[c]; si[c][threadIdx.x] = id[c]; }
+    for (int c = 0; c < 4; c++) { sv[c][threadIdx.x] = best[c]; si[c][threadIdx.x] = id[c]; }
     __syncthreads();
     for (int h = kAdjThreads / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) {
             for (int c = 0; c < 4; c++) {
-                double b0 = sb[c][threadIdx.x], b1 = sb[c][threadIdx.x + h];
+                double b0 = sv[c][threadIdx.x], b1 = sv[c][threadIdx.x + h];
                 int i0 = si[c][threadIdx.x], i1 = si[c][threadIdx.x + h];
                 bool take = (c & 1) ? (b1 > b0) : (b1 < b0);
                 if (i1 >= 0 && (i0 < 0 || take || (b1 == b0 && i1 < i0))) {
-                    sb[c][threadIdx.x] = b1;
+                    sv[c][threadIdx.x] = b1;
                     si[c][threadIdx.x] = i1;
                 }
             }
@@ -157,7 +158,7 @@ __device__ inline float wsumf(float x)
 }
 
 // FP32 copy of a posed vertex
-__device__ inline F3 vertex32(const MeshDev &m, const SlotBufs &sb, int s, int v) { return f3(vertex(m, sb, s, v)); }
+__device__ inline F3 vertex32(const MeshDev &m, const SlotBufs &sb, int v) { return f3(vertex(m, sb, v)); }
 
 // warp_scatter with FP32 lane values and FP64 accumulation
 template <int n>
@@ -183,8 +184,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
     const int s = blockIdx.y;
     const SlotPose &P = a.pose[s];
     if (P.skip) return;
-    const MeshDev &m = *a.mesh_d;
-    const int e = a.eval0 + s, N = a.N, nseg = a.nseg;
+    const MeshDev &m = *a.sd[s].mesh;
+    const SlotBufs &sb = a.sd[s].sb;
+    const int e = a.eval0 + s, N = a.sd[s].N, nseg = a.sd[s].nseg;
     const int W = a.width, nm2 = 2 * a.n_mats;
     extern __shared__ double sh[];  // [kAdjWarps][W]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
     __shared__ double win[4];
     if (threadIdx.x < 4) {
         int vi = a.win_ids[4 * s + threadIdx.x];
-        V3 x = vertex(m, a.slot, s, vi);
+        V3 x = vertex(m, sb, vi);
         win[threadIdx.x] = dot(threadIdx.x < 2 ? ld3(P.u) : ld3(P.v), x);
     }
     __syncthreads();
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
         int tri[kMaxBounces + 1];
         int nh = 0;
         if (live) {
-            const int32_t *hq = a.hits + ((size_t)s * R + ray) * nseg;
+            const int32_t *hq = a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride;
             for (int k = 0; k < nseg; k++) {
                 int h = hq[k];
                 if (h < 0) break;
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
             for (int k = 0; k < nh; k++) {
                 so[k] = o; sd[k] = d; sw[k] = w;
                 int4 tv = m.tri_v4[tri[k]];
-                F3 A = vertex32(m, a.slot, s, tv.x), B = vertex32(m, a.slot, s, tv.y), C = vertex32(m, a.slot, s, tv.z);
+                F3 A = vertex32(m, sb, tv.x), B = vertex32(m, sb, tv.y), C = vertex32(m, sb, tv.z);
                 F3 n = cross(B - A, C - A);
                 n = rsqrtf(dot(n, n)) * n;
                 float dn = dot(d, n);
@@ -257,8 +259,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
                 const F3 o = so[k], d = sd[k];
                 const float w = sw[k];
                 const int4 tv = m.tri_v4[tri[k]];
-                const F3 A = vertex32(m, a.slot, s, tv.x), B = vertex32(m, a.slot, s, tv.y),
-                         C = vertex32(m, a.slot, s, tv.z);
+                const F3 A = vertex32(m, sb, tv.x), B = vertex32(m, sb, tv.y),
+                         C = vertex32(m, sb, tv.z);
                 const F3 e1 = B - A, e2 = C - A, mr = cross(e1, e2);
                 const float il = rsqrtf(dot(mr, mr));
                 const F3 n = il * mr;
@@ -364,7 +366,8 @@ __global__ void __launch_bounds__(128) k_adj_finish(AdjArgs a)
 {
     const int s = blockIdx.x;
     const SlotPose &P = a.pose[s];
-    const MeshDev &m = *a.mesh_d;
+    const MeshDev &m = *a.sd[s].mesh;
+    const SlotBufs &sb = a.sd[s].sb;
     const int e = a.eval0 + s, W = a.width, nm2 = 2 * a.n_mats, np = a.n_parts;
     double *ge = a.g_eval + (size_t)e * (nm2 + np);
     if (P.skip) {
@@ -381,10 +384,10 @@ __global__ void __launch_bounds__(128) k_adj_finish(AdjArgs a)
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    const int N = a.N;
+    const int N = a.sd[s].N;
     const int *ids = a.win_ids + 4 * s;
     V3 X[4];
-    for (int c = 0; c < 4; c++) X[c] = vertex(m, a.slot, s, ids[c]);
+    for (int c = 0; c < 4; c++) X[c] = vertex(m, sb, ids[c]);
     V3 u = ld3(P.u), v = ld3(P.v), d = ld3(P.d), sh = ld3(P.s);
     const double umin = dot(u, X[0]), umax = dot(u, X[1]), vmin = dot(v, X[2]), vmax = dot(v, X[3]);
     const double area = (umax - umin) * (vmax - vmin) / ((double)N * N);

@@ -5,7 +5,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "srp_internal.cuh"
@@ -84,6 +86,12 @@ struct srp_ctx {
     size_t arc_hits_cap = 0;
     unsigned char *arc_buf = nullptr;
     size_t arc_buf_cap = 0;
+    // per-slot descriptors of the current plan (device copy and the host copy it was made from)
+    SlotDesc *sdesc = nullptr;
+    size_t sdesc_cap = 0;
+    std::vector<SlotDesc> sdesc_host;
+    // autotuned trace tile width per (mesh, N, segments)
+    std::map<std::tuple<const void *, int, int>, int> tile_w;
     cudaStream_t lane[kLanes] = {};  // pipeline lanes (forked from / joined to `stream`)
     cudaEvent_t ev_fork = nullptr, ev_join[kLanes] = {};
 };
@@ -207,7 +215,7 @@ srp_status check_eval_params(srp_ctx *ctx, const srp_eval_params *prm)
 
 // Launch shape of a batch of n evaluations.
 struct EvalPlan {
-    int N, nseg, S, nchunks, lanes, nbx, nbr;
+    int N, nseg, S, nchunks, lanes, nbx, nbr, tw;
     size_t R, SL;
     int nba = 0, wa = 0;  // adjoint: ray blocks per slot, doubles per block partial
 };
@@ -265,6 +273,45 @@ void fill_stats(srp_eval_stats &L, const unsigned long long *stats)
     for (int k = 0; k < 4; k++) L.handoff_cause[k] = (int64_t)stats[12 + k];
 }
 
+// Trace tiles of a grid of N x N rays with tiles tw pixels wide (32 / tw high).
+void tile_grid(int N, int tw, int &tiles_x, int &tiles)
+{
+    const int th = kTileRays / tw;
+    tiles_x = (N + tw - 1) / tw;
+    tiles = tiles_x * ((N + th - 1) / th);
+}
+
+// Slot k of the strided per-mesh slot buffers allocated by ensure_slots.
+SlotBufs slot_bufs(const MeshDev &h, const SlotBufs &base, size_t k)
+{
+    SlotBufs b = base;
+    b.vert64 += k * h.n_dyn_verts * 3;
+    b.vview += k * h.n_verts;
+    b.tri += k * h.n_dyn_tris * 3;
+    b.node += k * h.n_dyn_nodes * 4;
+    b.counter += k * h.n_dyn_nodes;
+    b.root_box += k * kMaxParts * 6;
+    return b;
+}
+
+// Upload the slot descriptors unless the device already holds exactly these.
+srp_status upload_slots(srp_ctx *ctx, const std::vector<SlotDesc> &sd)
+{
+    if (ctx->sdesc && ctx->sdesc_host.size() == sd.size() &&
+        memcmp(ctx->sdesc_host.data(), sd.data(), sizeof(SlotDesc) * sd.size()) == 0)
+        return SRP_OK;
+    CK(ctx, grow(&ctx->sdesc, &ctx->sdesc_cap, sd.size(), false));
+    CK(ctx, cudaMemcpy(ctx->sdesc, sd.data(), sizeof(SlotDesc) * sd.size(), cudaMemcpyHostToDevice));
+    ctx->sdesc_host = sd;
+    return SRP_OK;
+}
+
+int tuned_tile_w(const srp_ctx *ctx, const Mesh *m, int N, int nseg)
+{
+    auto it = ctx->tile_w.find(std::make_tuple((const void *)m, N, nseg));
+    return it == ctx->tile_w.end() ? 8 : it->second;
+}
+
 // Size the batch and grow every buffer it needs (may allocate; never inside a capture).
 srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, bool want_hits, EvalPlan &pl,
                      bool adjoint = false)
@@ -282,8 +329,10 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     pl.lanes = std::max(1, std::min(pl.nchunks, kLanes));
     srp_status rc = ensure_slots(ctx, m, pl.S * pl.lanes);
     if (rc) return rc;
-    // trace tiles of 8 x 4 pixels, one warp each
-    pl.nbx = ((pl.N + 7) / 8) * ((pl.N + 3) / 4);
+    // trace tiles of 32 pixels, one warp each (shape from the autotuner, else 8 x 4)
+    pl.tw = tuned_tile_w(ctx, m, pl.N, pl.nseg);
+    int tiles_x = 0;
+    tile_grid(pl.N, pl.tw, tiles_x, pl.nbx);
     // FP64 re-trace grid: a few blocks per SM, walking the compacted hand-off list
     pl.nbr = std::max(1, std::min(pl.nbx, 1216 / pl.S));
     pl.SL = (size_t)pl.S * pl.lanes;
@@ -297,6 +346,23 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * pl.nbx, false));
     CK(ctx, grow(&ctx->amb_off, &ctx->amb_off_cap, SL * (pl.nbx + 1), false));
     if (want_hits || adjoint) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
+    // every slot evaluates this mesh on this grid; lane b owns slots [b S, (b + 1) S)
+    std::vector<SlotDesc> sd(SL);
+    for (size_t k = 0; k < SL; k++) {
+        SlotDesc &d = sd[k];
+        d.mesh = m->d;
+        d.sb = slot_bufs(m->h, m->sb, k);
+        d.angles = m->angles_d;
+        d.N = pl.N;
+        d.nseg = pl.nseg;
+        d.panel_mode = prm->panel_mode;
+        d.tile_w = pl.tw;
+        d.tiles_x = tiles_x;
+        d.tiles = pl.nbx;
+        d.tile0 = (int)(k % pl.S) * pl.nbx;
+    }
+    rc = upload_slots(ctx, sd);
+    if (rc) return rc;
     if (adjoint) {
         pl.nba = adj_blocks(pl.S, pl.R);
         pl.wa = kAdjFixed + 2 * m->h.n_mats + 6 * m->h.n_parts;
@@ -325,22 +391,16 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         cudaStream_t ls = ctx->lane[b];
         // lane b's slots and buffers
         const MeshDev &h = m->h;
-        SlotBufs sb = m->sb;
         size_t s0 = (size_t)b * S;
-        sb.vert64 += s0 * h.n_dyn_verts * 3;
-        sb.vview += s0 * h.n_verts;
-        sb.tri += s0 * h.n_dyn_tris * 3;
-        sb.node += s0 * h.n_dyn_nodes * 4;
-        sb.counter += s0 * h.n_dyn_nodes;
-        sb.root_box += s0 * kMaxParts * 6;
+        const SlotDesc *sd = ctx->sdesc + s0;
         SlotPose *pose = ctx->pose + s0;
         TraceArgs a{};
-        a.mesh_d = m->d;
+        a.sd = sd;
+        a.n_slots = Sc;
+        a.n_tiles = Sc * nbx;
         a.pose = pose;
-        a.slot = sb;
-        a.N = pl.N;
-        a.bounces = prm->bounces;
-        a.nseg = nseg;
+        a.ray_stride = R;
+        a.seg_stride = nseg;
         a.eps_rel = prm->eps_rel;
         a.n_blocks_x = nbx;
         a.n_blocks_ref = nbr;
@@ -355,11 +415,11 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
         a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : (adj ? stage : nullptr);
         int g0 = tm.mark(ls);
-        CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, pose, ls));
-        CK(ctx, launch_vertices(m->d, h, pose, sb, Sc, ls));
+        CK(ctx, launch_pose(sd, d_sun, d_dist, prm->P0, e0, Sc, pose, ls));
+        CK(ctx, launch_vertices(sd, pose, Sc, h.n_verts, ls));
         launches += 2;
         if (h.n_dyn_tris > 0) {
-            CK(ctx, launch_refit(m->d, h, sb, pose, Sc, false, nullptr, nullptr, nullptr, nullptr, ls));
+            CK(ctx, launch_refit(sd, pose, Sc, h.n_dyn_tris, ls));
             launches++;
         }
         int g1 = tm.mark(ls);
@@ -373,16 +433,15 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         trace_launches++;
         if (adj) {
             AdjArgs g{};
-            g.mesh_d = m->d;
+            g.sd = sd;
             g.pose = pose;
-            g.slot = sb;
             g.hits = a.hits;
+            g.ray_stride = R;
+            g.seg_stride = nseg;
             g.sun_dirs = adj->sun;
             g.sun_dist = adj->dist;
             g.g_force = adj->gF;
             g.g_torque = adj->gT;
-            g.N = pl.N;
-            g.nseg = nseg;
             g.panel_mode = adj->panel_mode;
             g.n_mats = h.n_mats;
             g.n_parts = h.n_parts;
@@ -426,19 +485,19 @@ srp_status adj_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const 
     for (int e0 = 0; e0 < n; e0 += pl.S) {
         const int Sc = std::min(pl.S, n - e0);
         SlotPose *pose = ctx->pose;
-        CK(ctx, launch_pose(m->d, d_sun, d_dist, m->angles_d, prm->panel_mode, prm->P0, e0, Sc, pose, st));
-        CK(ctx, launch_vertices(m->d, h, pose, m->sb, Sc, st));
+        const SlotDesc *sd = ctx->sdesc;
+        CK(ctx, launch_pose(sd, d_sun, d_dist, prm->P0, e0, Sc, pose, st));
+        CK(ctx, launch_vertices(sd, pose, Sc, h.n_verts, st));
         AdjArgs g{};
-        g.mesh_d = m->d;
+        g.sd = sd;
         g.pose = pose;
-        g.slot = m->sb;
         g.hits = hits + (size_t)e0 * pl.R * pl.nseg;
+        g.ray_stride = pl.R;
+        g.seg_stride = pl.nseg;
         g.sun_dirs = d_sun;
         g.sun_dist = ab.dist;
         g.g_force = ab.gF;
         g.g_torque = ab.gT;
-        g.N = pl.N;
-        g.nseg = pl.nseg;
         g.panel_mode = ab.panel_mode;
         g.n_mats = h.n_mats;
         g.n_parts = h.n_parts;
@@ -590,6 +649,7 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->adj_partials);
     cudaFree(ctx->win_ids);
     cudaFree(ctx->gio);
+    cudaFree(ctx->sdesc);
     cudaFree(ctx->arc_hits);
     cudaFree(ctx->arc_buf);
     cudaFree(ctx->err_flags);
@@ -878,8 +938,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     // device copy of the mesh, then the static refit (writes root boxes into it)
     MK(dmalloc(m->allocs, &m->d, 1));
     MK(cudaMemcpyAsync(m->d, &h, sizeof(MeshDev), cudaMemcpyHostToDevice, st));
-    MK(launch_refit(m->d, h, SlotBufs{}, nullptr, 1, true, h.node_static, h.tri_static, cnt_static,
-                    &m->d->root_box_static[0][0], st));
+    MK(launch_refit_static(m->d, h, h.node_static, h.tri_static, cnt_static, &m->d->root_box_static[0][0], st));
     MK(cudaMemcpyAsync(&h.root_box_static[0][0], &m->d->root_box_static[0][0], sizeof(h.root_box_static),
                        cudaMemcpyDeviceToHost, st));
     MK(cudaStreamSynchronize(st));
@@ -1008,8 +1067,8 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
     CK(ctx, cudaMemsetAsync(ctx->prop_done, 0, sizeof(int), st));
     PropState *S = ctx->prop_state;
-    CK(ctx, launch_prop_init(S, n, d_y0, d_t01, p->h0, ctx->prop_done, st));
     PropDev P = prop_dev(p, m);
+    CK(ctx, launch_prop_init(S, n, d_y0, d_t01, P, nullptr, ctx->prop_done, st));
     if (p->h_replay && p->n_replay > 0) {
         if (p->method != SRP_RKF78) return fail(ctx, SRP_ERR_ARG, "step replay needs SRP_RKF78");
         CK(ctx, grow(&ctx->prop_replay, &ctx->prop_replay_cap, (size_t)n * p->n_replay, false));
@@ -1270,8 +1329,8 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
     CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
     CK(ctx, cudaMemsetAsync(ctx->prop_done, 0, sizeof(int), st));
-    CK(ctx, launch_prop_init(S, n, d_y0, d_t01, p->h0, ctx->prop_done, st));
     const PropDev P = prop_dev(p, m);
+    CK(ctx, launch_prop_init(S, n, d_y0, d_t01, P, nullptr, ctx->prop_done, st));
     Timing off_t(ctx, false);
     int64_t launches = 1, trace_launches = 0;
     // one RK4 step; with hrec != null every stage's hits and state are recorded at step j of the segment
@@ -1374,6 +1433,354 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     ctx->last.launches = launches;
     ctx->last.trace_launches = trace_launches;
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
+    return SRP_OK;
+}
+
+srp_status srp_autotune(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, int32_t *tile_w, double *ms)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
+    srp_status rc = check_eval_params(ctx, prm);
+    if (rc) return rc;
+    CK(ctx, cudaSetDevice(ctx->device));
+    // 8 directions of a Fibonacci sphere, resident on the device
+    const int nd = 8;
+    std::vector<double> dirs(3 * nd);
+    for (int i = 0; i < nd; i++) {
+        double z = 1.0 - (2.0 * i + 1.0) / nd, r = std::sqrt(std::max(0.0, 1.0 - z * z));
+        double ph = i * 3.14159265358979323846 * (3.0 - std::sqrt(5.0));
+        dirs[3 * i] = r * std::cos(ph); dirs[3 * i + 1] = r * std::sin(ph); dirs[3 * i + 2] = z;
+    }
+    double *d = nullptr;
+    CK(ctx, cudaMalloc(&d, sizeof(double) * 9 * nd));
+    struct Free { double *p; ~Free() { cudaFree(p); } } fr{d};
+    CK(ctx, cudaMemcpy(d, dirs.data(), sizeof(double) * 3 * nd, cudaMemcpyHostToDevice));
+    srp_eval_params q = *prm;
+    q.flags = 0;
+    const auto key = std::make_tuple((const void *)m, prm->N, prm->bounces + 1);
+    const int cand[4] = {4, 8, 16, 32};
+    double best = INFINITY;
+    int best_w = 8;
+    cudaEvent_t e0, e1;
+    CK(ctx, cudaEventCreate(&e0));
+    CK(ctx, cudaEventCreate(&e1));
+    for (int c = 0; c < 4; c++) {
+        ctx->tile_w[key] = cand[c];
+        double tmin = INFINITY;
+        for (int rep = 0; rep < 3; rep++) {
+            CK(ctx, cudaEventRecord(e0, ctx->stream));
+            rc = srp_eval_batch(ctx, mesh_id, &q, nd, d, nullptr, d + 3 * nd, d + 6 * nd, nullptr);
+            if (rc) break;
+            CK(ctx, cudaEventRecord(e1, ctx->stream));
+            CK(ctx, cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(ctx, cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) tmin = std::min(tmin, (double)t);  // the first run is a warm-up
+        }
+        if (rc) break;
+        if (ms) ms[c] = tmin / nd;
+        if (tmin < best) { best = tmin; best_w = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tile_w[key] = best_w;
+    if (rc) return rc;
+    if (tile_w) *tile_w = best_w;
+    return SRP_OK;
+}
+
+srp_status srp_set_tile_shape(srp_ctx *ctx, int32_t mesh_id, int32_t N, int32_t bounces, int32_t tile_w)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_ARG, "bad mesh id %d", mesh_id);
+    if (tile_w != 4 && tile_w != 8 && tile_w != 16 && tile_w != 32) return fail(ctx, SRP_ERR_ARG, "tile width %d", tile_w);
+    ctx->tile_w[std::make_tuple((const void *)m, N, bounces + 1)] = tile_w;
+    return SRP_OK;
+}
+
+srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n, const srp_traj *tr, double *y1,
+                               srp_prop_stats *stats)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    if (!p || !tr || !y1 || n <= 0) return fail(ctx, SRP_ERR_ARG, "need params, n > 0 trajectories and y1");
+    if (p->method != SRP_RKF78 && p->method != SRP_RK4) return fail(ctx, SRP_ERR_ARG, "bad method");
+    if (!(p->h0 > 0.0) || !(p->h_min >= 0.0) || p->max_steps <= 0) return fail(ctx, SRP_ERR_ARG, "bad step settings");
+    if (p->method == SRP_RKF78 && (!(p->rtol > 0.0) || !(p->atol_pos > 0.0) || !(p->atol_vel > 0.0)))
+        return fail(ctx, SRP_ERR_ARG, "tolerances must be > 0");
+    if (!(p->eval.P0 >= 0.0) || !(p->eval.eps_rel >= 0.0)) return fail(ctx, SRP_ERR_ARG, "P0 and eps_rel must be >= 0");
+    std::vector<Mesh *> mk(n);
+    for (int i = 0; i < n; i++) {
+        const srp_traj &t = tr[i];
+        if (!(mk[i] = get_mesh(ctx, t.mesh_id))) return fail(ctx, SRP_ERR_STATE, "trajectory %d: bad mesh id", i);
+        if (t.N < 1 || t.N > SRP_MAX_N || t.bounces < 0 || t.bounces > kMaxBounces || t.panel_mode < 0 ||
+            t.panel_mode > 2 || (t.central != SRP_CENTRAL_EARTH && t.central != SRP_CENTRAL_SUN) ||
+            (t.attitude != SRP_ATT_LVLH && t.attitude != SRP_ATT_INERTIAL))
+            return fail(ctx, SRP_ERR_ARG, "trajectory %d: bad N, bounces, panel mode, central body or attitude", i);
+        if (p->srp && !(mk[i]->mass > 0.0)) return fail(ctx, SRP_ERR_ARG, "trajectory %d: mesh mass must be > 0", i);
+    }
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    memset(&ctx->last, 0, sizeof ctx->last);
+    // trace tile shape per (mesh, N, bounces): tuned on request, else the context's choice
+    std::vector<int> tw(n), tx(n), tiles(n);
+    for (int i = 0; i < n; i++) {
+        const auto key = std::make_tuple((const void *)mk[i], tr[i].N, tr[i].bounces + 1);
+        if ((p->eval.flags & SRP_EVAL_AUTOTUNE) && !ctx->tile_w.count(key)) {
+            srp_eval_params q{tr[i].N, tr[i].bounces, p->eval.P0, p->eval.eps_rel, tr[i].panel_mode, 0};
+            srp_status rc = srp_autotune(ctx, tr[i].mesh_id, &q, nullptr, nullptr);
+            if (rc) return rc;
+        }
+        tw[i] = tuned_tile_w(ctx, mk[i], tr[i].N, tr[i].bounces + 1);
+        tile_grid(tr[i].N, tw[i], tx[i], tiles[i]);
+    }
+    // ---- device memory, owned by this call
+    std::vector<void *> owned;
+    struct Owner {
+        std::vector<void *> &v;
+        ~Owner() { for (void *q : v) cudaFree(q); }
+    } owner{owned};
+    int nbx = 0, max_verts = 0, max_dyn = 0;
+    size_t n64 = 0, nview = 0, ntri = 0, nnode = 0;
+    for (int i = 0; i < n; i++) {
+        const MeshDev &h = mk[i]->h;
+        nbx = std::max(nbx, tiles[i]);
+        max_verts = std::max(max_verts, h.n_verts);
+        max_dyn = std::max(max_dyn, h.n_dyn_tris);
+        n64 += (size_t)h.n_dyn_verts * 3;
+        nview += h.n_verts;
+        ntri += (size_t)h.n_dyn_tris * 3;
+        nnode += (size_t)h.n_dyn_nodes;
+    }
+    const int nbr = std::max(1, std::min(nbx, 1216 / n));
+    double *v64, *io, *ang, *cfg;
+    float4 *vview, *trec, *nodes;
+    unsigned *cnt;
+    float *rbox;
+    SlotPose *pose;
+    unsigned char *tctx;
+    double *part, *part1, *partr;
+    int *alist, *acount, *aoff;
+    SlotDesc *sd;
+    PropState *S;
+    CK(ctx, dmalloc(owned, &v64, std::max<size_t>(n64, 1)));
+    CK(ctx, dmalloc(owned, &vview, nview));
+    CK(ctx, dmalloc(owned, &trec, std::max<size_t>(ntri, 1)));
+    CK(ctx, dmalloc(owned, &nodes, std::max<size_t>(nnode * 4, 1)));
+    CK(ctx, dmalloc(owned, &cnt, std::max<size_t>(nnode, 1)));
+    CK(ctx, dmalloc(owned, &rbox, (size_t)n * kMaxParts * 6));
+    CK(ctx, dmalloc(owned, &io, (size_t)n * 18));
+    CK(ctx, dmalloc(owned, &ang, (size_t)n * kMaxParts));
+    CK(ctx, dmalloc(owned, &cfg, (size_t)n * 8));
+    CK(ctx, dmalloc(owned, &pose, (size_t)n));
+    CK(ctx, dmalloc(owned, &tctx, (size_t)n * trace_ctx_bytes()));
+    CK(ctx, dmalloc(owned, &part, (size_t)n * nbx * kPart));
+    CK(ctx, dmalloc(owned, &part1, (size_t)n * kRed1 * kPart));
+    CK(ctx, dmalloc(owned, &partr, (size_t)n * nbr * kPart));
+    CK(ctx, dmalloc(owned, &alist, (size_t)n * nbx * kTileRays));
+    CK(ctx, dmalloc(owned, &acount, (size_t)n * nbx));
+    CK(ctx, dmalloc(owned, &aoff, (size_t)n * (nbx + 1)));
+    CK(ctx, dmalloc(owned, &sd, (size_t)n));
+    CK(ctx, dmalloc(owned, &S, (size_t)n));
+    double *d_sun = io, *d_dist = io + 3 * (size_t)n, *d_f = d_dist + n, *d_t = d_f + 3 * (size_t)n,
+           *d_y0 = d_t + 3 * (size_t)n, *d_t01 = d_y0 + 6 * (size_t)n;
+    CK(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned) * std::max<size_t>(nnode, 1), st));
+    CK(ctx, cudaMemsetAsync(rbox, 0, sizeof(float) * n * kMaxParts * 6, st));
+    // per-trajectory slot storage, joint values and settings
+    std::vector<SlotDesc> desc(n);
+    std::vector<double> hang((size_t)n * kMaxParts, 0.0), hcfg((size_t)n * 8, 0.0), hy((size_t)n * 6), ht((size_t)n * 2);
+    size_t o64 = 0, oview = 0, otri = 0, onode = 0;
+    for (int i = 0; i < n; i++) {
+        const Mesh *m = mk[i];
+        const MeshDev &h = m->h;
+        SlotDesc &d = desc[i];
+        d.mesh = m->d;
+        d.sb.vert64 = v64 + o64;
+        d.sb.vview = vview + oview;
+        d.sb.tri = trec + otri;
+        d.sb.node = nodes + onode * 4;
+        d.sb.counter = cnt + onode;
+        d.sb.root_box = rbox + (size_t)i * kMaxParts * 6;
+        if (h.n_dyn_nodes > 0)
+            CK(ctx, cudaMemcpy2DAsync(d.sb.node + 3, 4 * sizeof(float4), m->node_refs_dyn, sizeof(int4), sizeof(int4),
+                                      h.n_dyn_nodes, cudaMemcpyDeviceToDevice, st));
+        o64 += (size_t)h.n_dyn_verts * 3;
+        oview += h.n_verts;
+        otri += (size_t)h.n_dyn_tris * 3;
+        onode += h.n_dyn_nodes;
+        if (tr[i].angles) {
+            for (int k = 0; k < h.n_parts; k++) hang[(size_t)i * kMaxParts + k] = tr[i].angles[k];
+            d.angles = ang + (size_t)i * kMaxParts;
+        } else {
+            d.angles = m->angles_d;
+        }
+        d.N = tr[i].N;
+        d.nseg = tr[i].bounces + 1;
+        d.panel_mode = tr[i].panel_mode;
+        d.tile_w = tw[i];
+        d.tiles_x = tx[i];
+        d.tiles = tiles[i];
+        double *c = &hcfg[8 * (size_t)i];
+        c[0] = tr[i].central;
+        c[1] = tr[i].attitude;
+        for (int k = 0; k < 4; k++) c[2 + k] = tr[i].q[k];
+        c[6] = m->mass;
+        for (int k = 0; k < 6; k++) hy[6 * (size_t)i + k] = tr[i].y0[k];
+        ht[2 * (size_t)i] = tr[i].t0;
+        ht[2 * (size_t)i + 1] = tr[i].t1;
+    }
+    CK(ctx, cudaMemcpyAsync(ang, hang.data(), sizeof(double) * hang.size(), cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaMemcpyAsync(cfg, hcfg.data(), sizeof(double) * hcfg.size(), cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaMemcpyAsync(d_y0, hy.data(), sizeof(double) * hy.size(), cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaMemcpyAsync(d_t01, ht.data(), sizeof(double) * ht.size(), cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
+    CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
+    CK(ctx, cudaMemsetAsync(ctx->prop_done, 0, sizeof(int), st));
+    PropDev P{};
+    P.method = p->method; P.j2 = p->j2; P.sun3 = p->sun3; P.srp = p->srp;
+    P.epoch_mjd_tt = p->epoch_mjd_tt;
+    P.rtol = p->rtol; P.atol_pos = p->atol_pos; P.atol_vel = p->atol_vel;
+    P.h0 = p->h0; P.h_min = p->h_min; P.h_max = p->h_max; P.max_steps = p->max_steps;
+    CK(ctx, launch_prop_init(S, n, d_y0, d_t01, P, cfg, ctx->prop_done, st));
+    const int nstage = p->method == SRP_RK4 ? 4 : 13;
+    // slot k runs trajectory act[k]; finished ones leave through compaction
+    std::vector<int> act(n);
+    for (int i = 0; i < n; i++) act[i] = i;
+    std::vector<PropState> fin(n), peek(n);
+    std::vector<char> have(n, 0);
+    cudaGraphExec_t exec = nullptr;
+    struct GraphGuard {
+        cudaGraphExec_t &e;
+        ~GraphGuard() { if (e) cudaGraphExecDestroy(e); }
+    } gg{exec};
+    int64_t launches = 0, trace_launches = 0, graphs = 0;
+    auto capture = [&](int na) -> srp_status {
+        // descriptors of the running trajectories, their tiles laid end to end
+        std::vector<SlotDesc> dd(na);
+        int t0 = 0, mv = 0, md = 0;
+        for (int k = 0; k < na; k++) {
+            dd[k] = desc[act[k]];
+            dd[k].tile0 = t0;
+            t0 += dd[k].tiles;
+            mv = std::max(mv, mk[act[k]]->h.n_verts);
+            md = std::max(md, mk[act[k]]->h.n_dyn_tris);
+        }
+        CK(ctx, cudaMemcpyAsync(sd, dd.data(), sizeof(SlotDesc) * na, cudaMemcpyHostToDevice, st));
+        CK(ctx, cudaStreamSynchronize(st));
+        TraceArgs a{};
+        a.sd = sd;
+        a.n_slots = na;
+        a.n_tiles = t0;
+        a.pose = pose;
+        a.tctx = tctx;
+        a.eps_rel = p->eval.eps_rel;
+        a.n_blocks_x = nbx;
+        a.partials = part;
+        a.partials1 = part1;
+        a.partials_ref = partr;
+        a.n_blocks_ref = nbr;
+        a.amb_list = alist;
+        a.amb_count = acount;
+        a.amb_off = aoff;
+        cudaGraph_t graph = nullptr;
+        CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int sg = 0; sg < nstage && e == cudaSuccess; sg++) {
+            e = launch_prop_stage(S, na, P, sg, d_sun, d_dist, st);
+            if (p->srp) {
+                if (e == cudaSuccess) e = launch_pose(sd, d_sun, d_dist, p->eval.P0, 0, na, pose, st);
+                if (e == cudaSuccess) e = launch_vertices(sd, pose, na, mv, st);
+                if (e == cudaSuccess) e = launch_refit(sd, pose, na, md, st);
+                if (e == cudaSuccess) e = launch_trace(a, na, st);
+                if (e == cudaSuccess) e = launch_refine(a, na, st);
+                if (e == cudaSuccess) e = launch_reduce(a, na, 0, d_f, d_t, ctx->err_flags, nullptr, st);
+            }
+            if (e == cudaSuccess) e = launch_prop_accel(S, na, P, sg, d_f, st);
+        }
+        if (e == cudaSuccess) e = launch_prop_control(S, na, P, ctx->prop_done, nullptr, 0, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (e != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(ctx, SRP_ERR_CUDA, "batch step capture failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : ce));
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(ctx, SRP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        graphs++;
+        return SRP_OK;
+    };
+    int na = n;
+    srp_status rc = capture(na);
+    if (rc) return rc;
+    const int poll_max = p->poll > 0 ? p->poll : 16;
+    const int per_step = nstage * (p->srp ? 12 : 2) + 1;
+    for (int64_t round = 0; round < p->max_steps + 2 && na > 0; round++) {
+        int done = 0;
+        CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaMemcpyAsync(peek.data(), S, sizeof(PropState) * na, cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaStreamSynchronize(st));
+        if (done >= na) break;
+        if (na >= 4 && 2 * done >= na) {
+            // compaction: keep the running trajectories in the first slots
+            std::vector<int> keep;
+            std::vector<PropState> ks;
+            for (int k = 0; k < na; k++) {
+                if (peek[k].done) { fin[act[k]] = peek[k]; have[act[k]] = 1; }
+                else { keep.push_back(act[k]); ks.push_back(peek[k]); }
+            }
+            act = keep;
+            na = (int)act.size();
+            CK(ctx, cudaMemcpyAsync(S, ks.data(), sizeof(PropState) * na, cudaMemcpyHostToDevice, st));
+            CK(ctx, cudaMemsetAsync(ctx->prop_done, 0, sizeof(int), st));
+            if ((rc = capture(na))) return rc;
+            continue;
+        }
+        double need = 1.0;
+        for (int k = 0; k < na; k++) {
+            const PropState &X = peek[k];
+            if (X.done) continue;
+            need = std::max(need, (X.t1 - X.t) / std::max(X.h, 1e-300));
+        }
+        const int launch = (int)std::min<double>(poll_max, std::max(1.0, std::ceil(need)));
+        for (int k = 0; k < launch; k++) CK(ctx, cudaGraphLaunch(exec, st));
+        launches += (int64_t)launch * per_step;
+        trace_launches += (int64_t)launch * nstage;
+    }
+    if (na > 0) {
+        CK(ctx, cudaMemcpyAsync(peek.data(), S, sizeof(PropState) * na, cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaStreamSynchronize(st));
+        for (int k = 0; k < na; k++) { fin[act[k]] = peek[k]; have[act[k]] = 1; }
+    }
+    int flags = 0;
+    CK(ctx, cudaMemcpy(&flags, ctx->err_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<double> yo((size_t)6 * n);
+    srp_status out = SRP_OK;
+    for (int i = 0; i < n; i++) {
+        for (int k = 0; k < 6; k++) yo[6 * (size_t)i + k] = fin[i].y[k];
+        if (stats) {
+            stats[i].steps = fin[i].steps;
+            stats[i].rejects = fin[i].rejects;
+            stats[i].evals = fin[i].evals;
+            stats[i].t = fin[i].t;
+            stats[i].status = fin[i].status;
+            stats[i].reserved = 0;
+        }
+        if (!have[i] || fin[i].status || !fin[i].done) out = SRP_ERR_STEP;
+    }
+    CK(ctx, cudaMemcpy(y1, yo.data(), sizeof(double) * 6 * n, cudaMemcpyDefault));
+    ctx->last.launches = launches;
+    ctx->last.trace_launches = trace_launches;
+    if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
+    if (out) return fail(ctx, SRP_ERR_STEP, "a trajectory hit h_min or max_steps");
+    (void)graphs;
     return SRP_OK;
 }
 

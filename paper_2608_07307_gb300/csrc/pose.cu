@@ -25,12 +25,15 @@ __device__ inline void rot_axis(const double *a, double th, double *R)
     R[6] = k * a[2] * a[0] - s * a[1]; R[7] = k * a[2] * a[1] + s * a[0]; R[8] = c + k * a[2] * a[2];
 }
 
-__global__ void k_pose(const MeshDev *mesh, const double *sun_dirs, const double *sun_dist, const double *angles,
-                       int panel_mode, double P0, int eval0, int S, SlotPose *pose)
+__global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist, double P0, int eval0, int S,
+                       SlotPose *pose)
 {
     int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= S) return;
     SlotPose &P = pose[slot];
+    const MeshDev *mesh = sd[slot].mesh;
+    const double *angles = sd[slot].angles;
+    const int panel_mode = sd[slot].panel_mode;
     int e = eval0 + slot;
     double s[3] = {sun_dirs[3 * e], sun_dirs[3 * e + 1], sun_dirs[3 * e + 2]};
     double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
@@ -104,10 +107,10 @@ __global__ void k_pose(const MeshDev *mesh, const double *sun_dirs, const double
     P.flags = 0;
 }
 
-cudaError_t launch_pose(const MeshDev *mesh_d, const double *sun_dirs, const double *sun_dist, const double *angles,
-                        int panel_mode, double P0, int eval0, int S, SlotPose *pose, cudaStream_t st)
+cudaError_t launch_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist, double P0, int eval0,
+                        int S, SlotPose *pose, cudaStream_t st)
 {
-    k_pose<<<(S + 31) / 32, 32, 0, st>>>(mesh_d, sun_dirs, sun_dist, angles, panel_mode, P0, eval0, S, pose);
+    k_pose<<<(S + 31) / 32, 32, 0, st>>>(sd, sun_dirs, sun_dist, P0, eval0, S, pose);
     return cudaGetLastError();
 }
 
@@ -123,13 +126,15 @@ __device__ inline double warp_max(double x)
     return x;
 }
 
-__global__ void __launch_bounds__(256) k_vertices(const MeshDev *mesh, SlotPose *pose, SlotBufs slot, int n_verts,
-                                                  int n_dyn_verts)
+__global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *pose)
 {
     int s = blockIdx.y;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     SlotPose &P = pose[s];
-    if (P.skip) return;  // uniform over the block
+    const MeshDev *mesh = sd[s].mesh;
+    const SlotBufs &slot = sd[s].sb;
+    const int n_verts = mesh->n_verts;
+    if (P.skip || (int)(blockIdx.x * blockDim.x) >= n_verts) return;  // uniform over the block
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     if (k < n_verts) {
         int p = mesh->vert_part[k];
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(256) k_vertices(const MeshDev *mesh, SlotPose 
             const double *M = P.M[p], *T = P.T[p];
             double y[3];
             for (int i = 0; i < 3; i++) y[i] = M[3 * i] * x[0] + M[3 * i + 1] * x[1] + M[3 * i + 2] * x[2] + T[i];
-            size_t o = ((size_t)s * n_dyn_verts + (k - pi.vert_begin + pi.dyn_vert_off)) * 3;
+            size_t o = (size_t)(k - pi.vert_begin + pi.dyn_vert_off) * 3;
             slot.vert64[o] = y[0]; slot.vert64[o + 1] = y[1]; slot.vert64[o + 2] = y[2];
             x[0] = y[0]; x[1] = y[1]; x[2] = y[2];
         }
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(256) k_vertices(const MeshDev *mesh, SlotPose 
             mn[c] = pr[c]; mx[c] = pr[c];
         }
         // view-frame position of the vertex for the primary-ray test, rounded once
-        slot.vview[(size_t)s * n_verts + k] = make_float4((float)pr[0], (float)pr[1], (float)pr[2], 0.f);
+        slot.vview[k] = make_float4((float)pr[0], (float)pr[1], (float)pr[2], 0.f);
     }
     __shared__ double smn[3][8], smx[3][8];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -170,11 +175,10 @@ __global__ void __launch_bounds__(256) k_vertices(const MeshDev *mesh, SlotPose 
     }
 }
 
-cudaError_t launch_vertices(const MeshDev *mesh_d, const MeshDev &mh, SlotPose *pose, SlotBufs slot, int S,
-                            cudaStream_t st)
+cudaError_t launch_vertices(const SlotDesc *sd, SlotPose *pose, int S, int max_verts, cudaStream_t st)
 {
-    dim3 grid((mh.n_verts + 255) / 256, S);
-    k_vertices<<<grid, 256, 0, st>>>(mesh_d, pose, slot, mh.n_verts, mh.n_dyn_verts);
+    dim3 grid((max_verts + 255) / 256, S);
+    k_vertices<<<grid, 256, 0, st>>>(sd, pose);
     return cudaGetLastError();
 }
 
@@ -206,15 +210,21 @@ __device__ inline void load_child_box_cg(const float4 *node, int which, float *b
     }
 }
 
-// Thread per sorted triangle in [t0, t0 + n) (all static, or all dynamic).
-__global__ void __launch_bounds__(256) k_refit(const MeshDev *mesh, SlotBufs slot, const SlotPose *pose, int t0, int n,
-                                               int dyn, float4 *node_static, float4 *tri_static,
-                                               unsigned *counter_static, float *root_static)
+// Thread per sorted triangle: the static parts of one mesh (sd == null, at
+// load) or the dynamic parts of every slot's mesh.
+__global__ void __launch_bounds__(256) k_refit(const SlotDesc *sd, const SlotPose *pose, const MeshDev *static_mesh,
+                                               float4 *node_static, float4 *tri_static, unsigned *counter_static,
+                                               float *root_static)
 {
     int s = blockIdx.y;
+    const int dyn = sd != nullptr;
+    const MeshDev *mesh = dyn ? sd[s].mesh : static_mesh;
+    const int t0 = dyn ? mesh->n_static_tris : 0, n = dyn ? mesh->n_dyn_tris : mesh->n_static_tris;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
-    if (pose && pose[s].skip) return;  // no arrivals in a skipped slot: counter parities stay consistent
+    if (dyn && pose[s].skip) return;  // no arrivals in a skipped slot: counter parities stay consistent
+    SlotBufs slot{};
+    if (dyn) slot = sd[s].sb;
     int t = t0 + idx;
     // part of this sorted triangle: parts are contiguous in sorted order
     int p = -1;
@@ -230,10 +240,10 @@ __global__ void __launch_bounds__(256) k_refit(const MeshDev *mesh, SlotBufs slo
     float *root;
     int tl = t - pi.tri_begin;
     if (dyn) {
-        nodes = slot.node + ((size_t)s * mesh->n_dyn_nodes + pi.dyn_node_off) * 4;
-        tris = slot.tri + ((size_t)s * mesh->n_dyn_tris + pi.dyn_tri_off) * 3;
-        cnt = slot.counter + (size_t)s * mesh->n_dyn_nodes + pi.dyn_node_off;
-        root = slot.root_box + ((size_t)s * kMaxParts + p) * 6;
+        nodes = slot.node + (size_t)pi.dyn_node_off * 4;
+        tris = slot.tri + (size_t)pi.dyn_tri_off * 3;
+        cnt = slot.counter + pi.dyn_node_off;
+        root = slot.root_box + (size_t)p * 6;
     } else {
         nodes = node_static + (size_t)pi.node_begin * 4;
         tris = tri_static + (size_t)pi.tri_begin * 3;
@@ -245,7 +255,7 @@ __global__ void __launch_bounds__(256) k_refit(const MeshDev *mesh, SlotBufs slo
     for (int c = 0; c < 3; c++) {
         int vi = mesh->tri_vidx[3 * t + c];
         const double *x;
-        if (dyn) x = slot.vert64 + ((size_t)s * mesh->n_dyn_verts + (vi - pi.vert_begin + pi.dyn_vert_off)) * 3;
+        if (dyn) x = slot.vert64 + (size_t)(vi - pi.vert_begin + pi.dyn_vert_off) * 3;
         else x = mesh->rest64 + (size_t)vi * 3;
         v[c][0] = (float)x[0]; v[c][1] = (float)x[1]; v[c][2] = (float)x[2];
     }
@@ -285,16 +295,20 @@ __global__ void __launch_bounds__(256) k_refit(const MeshDev *mesh, SlotBufs slo
     for (int k = 0; k < 6; k++) root[k] = box[k];
 }
 
-cudaError_t launch_refit(const MeshDev *mesh_d, const MeshDev &mh, SlotBufs slot, const SlotPose *pose, int S,
-                         bool static_pass, float4 *node_static, float4 *tri_static, unsigned *counter_static,
-                         float *root_static, cudaStream_t st)
+cudaError_t launch_refit(const SlotDesc *sd, const SlotPose *pose, int S, int max_dyn_tris, cudaStream_t st)
 {
-    int t0 = static_pass ? 0 : mh.n_static_tris;
-    int n = static_pass ? mh.n_static_tris : mh.n_dyn_tris;
-    if (n <= 0) return cudaSuccess;
-    dim3 grid((n + 255) / 256, static_pass ? 1 : S);
-    k_refit<<<grid, 256, 0, st>>>(mesh_d, slot, static_pass ? nullptr : pose, t0, n, static_pass ? 0 : 1, node_static,
-                                  tri_static, counter_static, root_static);
+    if (max_dyn_tris <= 0) return cudaSuccess;
+    dim3 grid((max_dyn_tris + 255) / 256, S);
+    k_refit<<<grid, 256, 0, st>>>(sd, pose, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refit_static(const MeshDev *mesh_d, const MeshDev &mh, float4 *node_static, float4 *tri_static,
+                                unsigned *counter_static, float *root_static, cudaStream_t st)
+{
+    if (mh.n_static_tris <= 0) return cudaSuccess;
+    dim3 grid((mh.n_static_tris + 255) / 256, 1);
+    k_refit<<<grid, 256, 0, st>>>(nullptr, nullptr, mesh_d, node_static, tri_static, counter_static, root_static);
     return cudaGetLastError();
 }
 

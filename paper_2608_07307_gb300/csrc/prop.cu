@@ -100,11 +100,11 @@ __device__ void lvlh_matrix(const double *y, double *L)
 
 // body -> inertial rotation, row-major: Q(q) (inertial attitude) or
 // LVLH(y) Q(q) (the LVLH frame turned by the constant quaternion q)
-__device__ void body_to_inertial(const PropDev &P, const double *y, double *R)
+__device__ void body_to_inertial(int attitude, const double *q, const double *y, double *R)
 {
     double Q[9];
-    quat_matrix(P.q, Q);
-    if (P.attitude == 1) {
+    quat_matrix(q, Q);
+    if (attitude == 1) {
         for (int k = 0; k < 9; k++) R[k] = Q[k];
         return;
     }
@@ -115,19 +115,19 @@ __device__ void body_to_inertial(const PropDev &P, const double *y, double *R)
 }
 
 // Gravity of the configured bodies at (t, y).
-__device__ void gravity(const PropDev &P, double t, const double *y, const double *rs, double *a)
+__device__ void gravity(const PropDev &P, int central, const double *y, const double *rs, double *a)
 {
     double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2], r = sqrt(r2);
-    double mu = P.central == 1 ? kMuSun : kMuEarth;
+    double mu = central == 1 ? kMuSun : kMuEarth;
     for (int k = 0; k < 3; k++) a[k] = -mu * y[k] / (r2 * r);
-    if (P.central == 0 && P.j2) {
+    if (central == 0 && P.j2) {
         double z2 = y[2] * y[2] / r2;
         double f = -1.5 * kJ2 * kMuEarth * kREarth * kREarth / (r2 * r2 * r);
         a[0] += f * y[0] * (1.0 - 5.0 * z2);
         a[1] += f * y[1] * (1.0 - 5.0 * z2);
         a[2] += f * y[2] * (3.0 - 5.0 * z2);
     }
-    if (P.central == 0 && P.sun3) {
+    if (central == 0 && P.sun3) {
         double d[3] = {rs[0] - y[0], rs[1] - y[1], rs[2] - y[2]};
         double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         double sn = sqrt(rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2]);
@@ -136,11 +136,26 @@ __device__ void gravity(const PropDev &P, double t, const double *y, const doubl
     }
 }
 
-__global__ void k_prop_init(PropState *S, int n, const double *y0, const double *t01, double h0, int *n_done)
+// cfg (null: P's values for every trajectory): [n][8] central, attitude, q[4], mass, unused
+__global__ void k_prop_init(PropState *S, int n, const double *y0, const double *t01, PropDev P, const double *cfg,
+                            int *n_done)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     PropState &X = S[i];
+    const double h0 = P.h0;
+    if (cfg) {
+        const double *c = cfg + 8 * (size_t)i;
+        X.central = (int)c[0];
+        X.attitude = (int)c[1];
+        for (int k = 0; k < 4; k++) X.q[k] = c[2 + k];
+        X.mass = c[6];
+    } else {
+        X.central = P.central;
+        X.attitude = P.attitude;
+        for (int k = 0; k < 4; k++) X.q[k] = P.q[k];
+        X.mass = P.mass;
+    }
     for (int k = 0; k < 6; k++) X.y[k] = y0[6 * i + k];
     X.t = t01[2 * i];
     X.t1 = t01[2 * i + 1];
@@ -185,13 +200,13 @@ __global__ void k_prop_stage(PropState *S, int n, PropDev P, int stage, double *
     X.ts = X.t + c * X.hs;
     // Sun direction and distance
     double rs[3] = {0.0, 0.0, 0.0}, sv[3];
-    if (P.central == 0) sun_pos(P.epoch_mjd_tt + X.ts / 86400.0, rs);
+    if (X.central == 0) sun_pos(P.epoch_mjd_tt + X.ts / 86400.0, rs);
     for (int k = 0; k < 3; k++) { X.rsun[k] = rs[k]; sv[k] = rs[k] - X.ys[k]; }
     double sd = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
     for (int k = 0; k < 3; k++) sv[k] /= sd;
     // cylindrical Earth shadow
     X.shadow = 0;
-    if (P.central == 0) {
+    if (X.central == 0) {
         double rsn = sqrt(rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2]);
         double e[3] = {rs[0] / rsn, rs[1] / rsn, rs[2] / rsn};
         double pr = X.ys[0] * e[0] + X.ys[1] * e[1] + X.ys[2] * e[2];
@@ -199,7 +214,7 @@ __global__ void k_prop_stage(PropState *S, int n, PropDev P, int stage, double *
         if (pr < 0.0 && sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) < kREarth) X.shadow = 1;
     }
     double R[9];
-    body_to_inertial(P, X.ys, R);
+    body_to_inertial(X.attitude, X.q, X.ys, R);
     for (int k = 0; k < 9; k++) X.R[k] = R[k];
     for (int k = 0; k < 3; k++) sun_dir[3 * i + k] = R[k] * sv[0] + R[3 + k] * sv[1] + R[6 + k] * sv[2];
     // finished and shadowed trajectories skip their SRP evaluation (negative distance)
@@ -212,10 +227,10 @@ __global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const do
     if (i >= n) return;
     PropState &X = S[i];
     double a[3];
-    gravity(P, X.ts, X.ys, X.rsun, a);
+    gravity(P, X.central, X.ys, X.rsun, a);
     if (P.srp && !X.shadow) {
         const double *F = force + 3 * i;
-        for (int k = 0; k < 3; k++) a[k] += (X.R[3 * k] * F[0] + X.R[3 * k + 1] * F[1] + X.R[3 * k + 2] * F[2]) / P.mass;
+        for (int k = 0; k < 3; k++) a[k] += (X.R[3 * k] * F[0] + X.R[3 * k + 1] * F[1] + X.R[3 * k + 2] * F[2]) / X.mass;
     }
     for (int k = 0; k < 3; k++) { X.k[stage][k] = X.ys[3 + k]; X.k[stage][3 + k] = a[k]; }
     if (!X.done) X.evals++;
@@ -492,10 +507,10 @@ __global__ void k_adj_prop_step(int n, PropAdj *A)
 
 }  // namespace
 
-cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double *t01, double h0, int *n_done,
-                             cudaStream_t st)
+cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double *t01, const PropDev &P,
+                             const double *cfg, int *n_done, cudaStream_t st)
 {
-    k_prop_init<<<(n + 63) / 64, 64, 0, st>>>(S, n, y0, t01, h0, n_done);
+    k_prop_init<<<(n + 63) / 64, 64, 0, st>>>(S, n, y0, t01, P, cfg, n_done);
     return cudaGetLastError();
 }
 cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, double *sun_dir, double *sun_dist,

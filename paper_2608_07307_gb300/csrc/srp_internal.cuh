@@ -107,6 +107,21 @@ struct SlotBufs {
     float *root_box;    // [S][kMaxParts][6]
 };
 
+// One evaluation slot of a launch: what is evaluated there.  A launch may mix
+// meshes, grid sizes, bounce counts, joint laws and tile shapes (batched
+// propagation); a single-mesh call fills every slot alike.
+struct SlotDesc {
+    const MeshDev *mesh;   // device copy of the slot's mesh
+    SlotBufs sb;           // the slot's own dynamic storage (already offset to the slot)
+    const double *angles;  // [n_parts] commanded angles / tracking offsets of the slot
+    int N, nseg;           // rays per side; segments per ray (1 + bounces)
+    int panel_mode;        // SRP_PANELS_*
+    int tile_w;            // trace tile width in pixels (4, 8, 16 or 32); height 32 / tile_w
+    int tiles_x, tiles;    // trace tiles across the window, in total
+    int tile0;             // first flattened trace block of the slot
+    int pad_;
+};
+
 // Partial sums per block (FP64; integer counts are exact below 2^53):
 //   0..2 force, 3..5 torque (unscaled), 6 rays sent to / done by the FP64 path,
 //   7 segments traced, 8..12 hits per segment level, 13 nodes, 14 triangles,
@@ -120,13 +135,15 @@ constexpr int kTileRays = 32;
 constexpr int kRed1 = 64;  // first-level reduction blocks per slot
 
 struct TraceArgs {
-    const MeshDev *mesh_d;       // device copy of MeshDev
+    const SlotDesc *sd;          // [S] what each slot evaluates
+    int n_slots;                 // S
+    int n_tiles;                 // trace blocks of the launch (sum of the slots' tiles)
     SlotPose *pose;              // [S] (trace / refine OR their error flags into it)
-    SlotBufs slot;
     unsigned char *tctx;         // [S] per-slot traversal context (k_frame output)
-    int N, bounces, nseg;
     double eps_rel;
-    int n_blocks_x;              // trace tiles (blocks) per evaluation
+    size_t ray_stride;           // hits: [S][ray_stride][seg_stride]
+    int seg_stride;
+    int n_blocks_x;              // stride of the per-tile arrays: the largest tile count of a slot
     double *partials;            // [S][n_blocks_x][kPart] one partial per tile
     double *partials1;           // [S][kRed1][kPart] first-level sums of the tile partials
     double *partials_ref;        // [S][n_blocks_ref][kPart]
@@ -134,7 +151,7 @@ struct TraceArgs {
     int *amb_list;               // [S][n_blocks_x][kTileRays] rays handed to the FP64 path, per tile
     int *amb_count;              // [S][n_blocks_x]
     int *amb_off;                // [S][n_blocks_x + 1] exclusive scan of amb_count
-    int32_t *hits;               // [S][N*N][nseg] or null
+    int32_t *hits;               // [S][ray_stride][seg_stride] or null
     int count;                   // gather traversal counters
 };
 size_t trace_ctx_bytes();
@@ -160,6 +177,8 @@ struct PropState {
     double R[9];               // body -> inertial at the stage
     long long steps, rejects, evals, nlog;
     int done, status, shadow, pad_;
+    int central, attitude;     // per-trajectory force model and attitude law
+    double q[4], mass;         // attitude quaternion, spacecraft mass (kg)
 };
 
 // One stage of an RK4 step, recorded for the reverse pass of the propagation adjoint.
@@ -209,14 +228,14 @@ cudaError_t launch_karras(const unsigned long long *keys, const int *part_tri_be
 cudaError_t launch_depth(const int4 *node_refs, const int *node_part_base, int n_nodes, int *depth, cudaStream_t st);
 
 // pose.cu
-cudaError_t launch_pose(const MeshDev *mesh_d, const double *sun_dirs, const double *sun_dist, const double *angles,
-                        int panel_mode, double P0, int eval0, int S, SlotPose *pose, cudaStream_t st);
-cudaError_t launch_vertices(const MeshDev *mesh_d, const MeshDev &mh, SlotPose *pose, SlotBufs slot, int S,
-                            cudaStream_t st);
-cudaError_t launch_refit(const MeshDev *mesh_d, const MeshDev &mh, SlotBufs slot, const SlotPose *pose, int S,
-                         bool static_pass,
-                         float4 *node_static, float4 *tri_static, unsigned *counter_static, float *root_static,
-                         cudaStream_t st);
+cudaError_t launch_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist, double P0, int eval0,
+                        int S, SlotPose *pose, cudaStream_t st);
+cudaError_t launch_vertices(const SlotDesc *sd, SlotPose *pose, int S, int max_verts, cudaStream_t st);
+// dynamic parts of every slot (max_dyn_tris: the largest count of a slot's mesh)
+cudaError_t launch_refit(const SlotDesc *sd, const SlotPose *pose, int S, int max_dyn_tris, cudaStream_t st);
+// static parts of one mesh at load
+cudaError_t launch_refit_static(const MeshDev *mesh_d, const MeshDev &mh, float4 *node_static, float4 *tri_static,
+                                unsigned *counter_static, float *root_static, cudaStream_t st);
 
 // trace.cu
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st);
@@ -226,15 +245,16 @@ cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, d
 
 // adjoint.cu: reverse sweep of one evaluation with the hit set frozen
 struct AdjArgs {
-    const MeshDev *mesh_d;
+    const SlotDesc *sd;          // [S]
     const SlotPose *pose;        // [S]
-    SlotBufs slot;
-    const int32_t *hits;         // [S][N*N][nseg] original triangle ids recorded by the trace
+    const int32_t *hits;         // [S][ray_stride][seg_stride] original triangle ids recorded by the trace
+    size_t ray_stride;
+    int seg_stride;
     const double *sun_dirs;      // [n][3] as given (device)
     const double *sun_dist;      // [n] Sun distance (AU, device) when g_dist is wanted
     const double *g_force;       // [n][3] cotangent of the force (device)
     const double *g_torque;      // [n][3] cotangent of the torque (device)
-    int N, nseg, panel_mode, n_mats, n_parts, eval0;
+    int panel_mode, n_mats, n_parts, eval0;
     int nb;                      // ray blocks per slot
     int width;                   // doubles per block partial (kAdjFixed + 2 n_mats + 6 n_parts)
     int *win_ids;                // [S][4] extreme vertices: argmin u, argmax u, argmin v, argmax v
@@ -250,8 +270,9 @@ cudaError_t launch_adj_sum(const double *g_eval, int n, int n_mats, int n_parts,
                            cudaStream_t st, bool accumulate = false);
 
 // prop.cu
-cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double *t01, double h0, int *n_done,
-                             cudaStream_t st);
+// cfg: null, or [n][8] per trajectory: central, attitude, q[4], mass, unused
+cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double *t01, const PropDev &P,
+                             const double *cfg, int *n_done, cudaStream_t st);
 cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, double *sun_dir, double *sun_dist,
                               cudaStream_t st);
 cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st);

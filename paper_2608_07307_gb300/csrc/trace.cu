@@ -5,9 +5,12 @@
 // FP32 ray generation, the error bounds of the FP32 decisions and the
 // per-part traversal views, into a small context every trace block copies.
 //
-// k_trace (FP32 fast path).  A block is one warp over an 8 x 4 pixel tile, so
-// no warp ever waits for another: the hardware block scheduler balances the
-// load at 32-ray granularity.  Per segment: stack traversal of each part's
+// k_trace (FP32 fast path).  A block is one warp over a 32-pixel tile (8 x 4
+// by default; the shape is chosen per mesh, grid and bounce count by the
+// autotuner), so no warp ever waits for another: the hardware block scheduler
+// balances the load at 32-ray granularity.  The tiles of every slot of a
+// launch form one flat grid, so one launch can trace different meshes, grid
+// sizes and bounce counts.  Per segment: stack traversal of each part's
 // binary LBVH (64 B nodes fetched as four float4; child boxes slab-tested
 // against the segment's current best t) with the watertight ray/triangle test
 // (Woop, Benthin and Wald, "Watertight ray/triangle intersection", JCGT 2(1),
@@ -89,7 +92,10 @@ __global__ void k_frame(TraceArgs a)
 {
     int s = blockIdx.x;
     if (threadIdx.x != 0) return;
-    const MeshDev *m = a.mesh_d;
+    const SlotDesc &D = a.sd[s];
+    const MeshDev *m = D.mesh;
+    const SlotBufs &sb = D.sb;
+    const int N = D.N;
     const SlotPose &P = a.pose[s];
     TraceCtx &B = reinterpret_cast<TraceCtx *>(a.tctx)[s];
     B.skip = P.skip;
@@ -108,15 +114,15 @@ __global__ void k_frame(TraceArgs a)
     for (int k = 0; k < 3; k++) {
         double o = umin * P.u[k] + vmin * P.v[k] + w0 * P.d[k];
         B.org[k] = (float)o;
-        B.du[k] = (float)(B.Du / a.N * P.u[k]);
-        B.dv[k] = (float)(B.Dv / a.N * P.v[k]);
+        B.du[k] = (float)(B.Du / N * P.u[k]);
+        B.dv[k] = (float)(B.Dv / N * P.v[k]);
         B.dir[k] = (float)P.d[k];
         B.u[k] = P.u[k]; B.v[k] = P.v[k]; B.d[k] = P.d[k];
         B.c_ref[k] = m->c_ref[k];
         B.cref32[k] = (float)m->c_ref[k];
     }
     B.umin32 = (float)umin; B.vmin32 = (float)vmin;
-    B.du32 = (float)(B.Du / a.N); B.dv32 = (float)(B.Dv / a.N);
+    B.du32 = (float)(B.Du / N); B.dv32 = (float)(B.Dv / N);
     B.w0_32 = (float)w0;
     const double u = 5.9604644775390625e-8;
     // Primary (view frame): vertex projections rounded once (|p| u/2), pixel
@@ -138,7 +144,7 @@ __global__ void k_frame(TraceArgs a)
     B.pad = (float)m->pad;
     B.n_parts = m->n_parts;
     B.n_mats = m->n_mats;
-    B.vview = a.slot.vview + (size_t)s * m->n_verts;
+    B.vview = sb.vview;
     B.mat32 = m->mat32;
     B.mat64 = m->mat64;
     B.tri_mat = m->tri_mat;
@@ -152,10 +158,10 @@ __global__ void k_frame(TraceArgs a)
         pv.vert_begin = pi.vert_begin;
         pv.v4 = m->tri_v4 + pi.tri_begin;
         if (pi.dynamic) {
-            pv.node = a.slot.node + ((size_t)s * m->n_dyn_nodes + pi.dyn_node_off) * 4;
-            pv.tri = a.slot.tri + ((size_t)s * m->n_dyn_tris + pi.dyn_tri_off) * 3;
-            pv.v64 = a.slot.vert64 + ((size_t)s * m->n_dyn_verts + pi.dyn_vert_off) * 3;
-            const float *rb = a.slot.root_box + ((size_t)s * kMaxParts + p) * 6;
+            pv.node = sb.node + (size_t)pi.dyn_node_off * 4;
+            pv.tri = sb.tri + (size_t)pi.dyn_tri_off * 3;
+            pv.v64 = sb.vert64 + (size_t)pi.dyn_vert_off * 3;
+            const float *rb = sb.root_box + (size_t)p * 6;
             for (int k = 0; k < 6; k++) pv.box[k] = rb[k];
         } else {
             pv.node = m->node_static + (size_t)pi.node_begin * 4;
@@ -170,7 +176,7 @@ __global__ void k_frame(TraceArgs a)
 __device__ __forceinline__ void load_ctx(TraceCtx &B, const TraceArgs &a, int s)
 {
     const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
-    int np = a.mesh_d->n_parts;
+    int np = a.sd[s].mesh->n_parts;
     int words = (int)((offsetof(TraceCtx, part) + np * sizeof(PartView)) / 4);
     const int *src = reinterpret_cast<const int *>(g);
     int *dst = reinterpret_cast<int *>(&B);
@@ -372,24 +378,38 @@ __device__ void block_sum(const double *v, double *out)
     __syncthreads();
 }
 
-// One warp per block, one 8 x 4 pixel tile per block.  Latency bound: 32 warps
-// per SM at the kernel's 64 registers (no spills).
+// Slot of flattened trace block g: the last slot whose first block is <= g.
+__device__ __forceinline__ int slot_of_block(const SlotDesc *sd, int S, int g)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&sd[mid].tile0) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One warp per block, one 32-pixel tile (tile_w x 32 / tile_w) per block; the
+// blocks of all slots form one flat grid.  Latency bound: 32 warps per SM at
+// the kernel's 64 registers (no spills).
 template <bool COUNT>
 __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
 {
     __shared__ TraceCtx B;
-    const int s = blockIdx.y;
+    const int s = slot_of_block(a.sd, a.n_slots, blockIdx.x);
+    const SlotDesc &D = a.sd[s];
+    const int tile_id = blockIdx.x - D.tile0;
     load_ctx(B, a, s);
     __syncwarp();
-    const int N = a.N;
+    const int N = D.N, nseg = D.nseg;
     const int lane = threadIdx.x;
     if (B.skip) {
-        if (lane == 0) a.amb_count[(size_t)s * a.n_blocks_x + blockIdx.x] = 0;
+        if (lane == 0) a.amb_count[(size_t)s * a.n_blocks_x + tile_id] = 0;
         return;
     }
-    const int tiles_x = (N + 7) / 8;
-    const int i = (blockIdx.x % tiles_x) * 8 + (lane & 7);
-    const int j = (blockIdx.x / tiles_x) * 4 + (lane >> 3);
+    const int tw = D.tile_w, lw = __ffs(tw) - 1;
+    const int i = (tile_id % D.tiles_x) * tw + (lane & (tw - 1));
+    const int j = (tile_id / D.tiles_x) * (kTileRays >> lw) + (lane >> lw);
     double acc64[kPart];
     for (int k = 0; k < kPart; k++) acc64[k] = 0.0;
     bool handoff = false;
@@ -412,7 +432,7 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
         int nseg_done = 0;
         Counts cn = {0.f, 0.f, 0.f, {0.f, 0.f, 0.f, 0.f}, 0};
         float delta = B.delta_p, tau = B.tau_p;
-        for (int seg = 0; seg < a.nseg; seg++) {
+        for (int seg = 0; seg < nseg; seg++) {
             ray_setup(r);
             Best32 h;
             float tlo = seg == 0 ? 0.0f : B.eps32;
@@ -450,7 +470,7 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
             acc[4] += arm[2] * F[0] - arm[0] * F[2];
             acc[5] += arm[0] * F[1] - arm[1] * F[0];
             wgt *= m.x;
-            if (seg + 1 >= a.nseg || wgt == 0.0f) break;
+            if (seg + 1 >= nseg || wgt == 0.0f) break;
             for (int k = 0; k < 3; k++) {
                 r.o[k] = hp[k];
                 r.d[k] = r.d[k] - 2.0f * dn * n[k];
@@ -464,10 +484,10 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
         if (clean) {
             for (int k = 0; k < 6; k++) acc64[k] = (double)acc[k];
             acc64[7] = (double)nseg_done;
-            for (int k = 0; k < a.nseg; k++) acc64[8 + k] = hits[k] >= 0 ? 1.0 : 0.0;
+            for (int k = 0; k < nseg; k++) acc64[8 + k] = hits[k] >= 0 ? 1.0 : 0.0;
             if (a.hits) {
-                int32_t *hq = a.hits + ((size_t)s * N * N + ray) * a.nseg;
-                for (int k = 0; k < a.nseg; k++) hq[k] = hits[k];
+                int32_t *hq = a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride;
+                for (int k = 0; k < nseg; k++) hq[k] = hits[k];
             }
         } else {
             handoff = true;
@@ -479,7 +499,7 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
         }
     }
     // tile-ordered list of the rays handed to the FP64 path
-    const size_t tile = (size_t)s * a.n_blocks_x + blockIdx.x;
+    const size_t tile = (size_t)s * a.n_blocks_x + tile_id;
     unsigned bal = __ballot_sync(0xffffffffu, handoff);
     if (handoff) a.amb_list[tile * kTileRays + __popc(bal & ((1u << lane) - 1u))] = ray;
     // tile sum (fixed shuffle order), one partial per tile
@@ -500,9 +520,9 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
 __global__ void __launch_bounds__(1024) k_amb_scan(TraceArgs a)
 {
     __shared__ int tot[1024];
-    const int s = blockIdx.x, n = a.n_blocks_x, t = threadIdx.x;
-    const int *cnt = a.amb_count + (size_t)s * n;
-    int *off = a.amb_off + (size_t)s * (n + 1);
+    const int s = blockIdx.x, n = a.sd[s].tiles, t = threadIdx.x;
+    const int *cnt = a.amb_count + (size_t)s * a.n_blocks_x;
+    int *off = a.amb_off + (size_t)s * (a.n_blocks_x + 1);
     const int chunk = (n + 1023) / 1024;
     const int b0 = min(t * chunk, n), b1 = min(b0 + chunk, n);
     int sum = 0;
@@ -659,7 +679,7 @@ __device__ void nearest64(const TraceCtx &B, const Ray64 &r, double tlo, int ski
 // Re-trace of one handed-off ray, FP64 from the pixel definition; adds to acc.
 __device__ void refine_ray(const TraceCtx &B, const TraceArgs &a, int s, int ray, double *acc, int &flags)
 {
-    const int N = a.N;
+    const int N = a.sd[s].N, nseg = a.sd[s].nseg;
     int i = ray / N, j = ray % N;
     Ray64 r;
     double uc = B.umin + ((double)i + 0.5) * B.Du / N;
@@ -668,9 +688,9 @@ __device__ void refine_ray(const TraceCtx &B, const TraceArgs &a, int s, int ray
     for (int k = 0; k < 3; k++) { r.o[k] = uc * B.u[k] + vc * B.v[k] + w0 * B.d[k]; r.d[k] = B.d[k]; }
     double wgt = 1.0;
     int skip = -1, nseg_done = 0;
-    int32_t *hp = a.hits ? a.hits + ((size_t)s * N * N + ray) * a.nseg : nullptr;
-    if (hp) for (int k = 0; k < a.nseg; k++) hp[k] = -1;
-    for (int seg = 0; seg < a.nseg; seg++) {
+    int32_t *hp = a.hits ? a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride : nullptr;
+    if (hp) for (int k = 0; k < nseg; k++) hp[k] = -1;
+    for (int seg = 0; seg < nseg; seg++) {
         ray64_setup(r);
         double t;
         int hpart, htl, horig;
@@ -704,7 +724,7 @@ __device__ void refine_ray(const TraceCtx &B, const TraceArgs &a, int s, int ray
         acc[4] += arm[2] * F[0] - arm[0] * F[2];
         acc[5] += arm[0] * F[1] - arm[1] * F[0];
         wgt *= rs;
-        if (seg + 1 >= a.nseg || wgt == 0.0) break;
+        if (seg + 1 >= nseg || wgt == 0.0) break;
         for (int k = 0; k < 3; k++) { r.d[k] = r.d[k] - 2.0 * dn * n[k]; r.o[k] = x[k]; }
         skip = horig;
     }
@@ -718,8 +738,9 @@ __global__ void __launch_bounds__(256) k_refine(TraceArgs a)
     __shared__ TraceCtx B;
     __shared__ int blk_flags;
     const int s = blockIdx.y;
+    const int nt = a.sd[s].tiles;
     const int *off = a.amb_off + (size_t)s * (a.n_blocks_x + 1);
-    const int total = off[a.n_blocks_x];
+    const int total = a.pose[s].skip ? 0 : off[nt];
     double acc[kPart];
     for (int k = 0; k < kPart; k++) acc[k] = 0.0;
     if ((int)(blockIdx.x * blockDim.x) < total) {
@@ -729,7 +750,7 @@ __global__ void __launch_bounds__(256) k_refine(TraceArgs a)
         int flags = 0;
         for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
             // tile holding item g: largest b with off[b] <= g
-            int lo = 0, hi = a.n_blocks_x - 1;
+            int lo = 0, hi = nt - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
                 if (off[mid] <= g) lo = mid; else hi = mid - 1;
@@ -753,8 +774,9 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
 {
     const int s = blockIdx.y, b = blockIdx.x;
     if (a.pose[s].skip) return;  // uniform over the block
-    const int chunk = (a.n_blocks_x + kRed1 - 1) / kRed1;
-    const int t0 = b * chunk, t1 = min(t0 + chunk, a.n_blocks_x);
+    const int nt = a.sd[s].tiles;
+    const int chunk = (nt + kRed1 - 1) / kRed1;
+    const int t0 = b * chunk, t1 = min(t0 + chunk, nt);
     double acc[kPart];
     for (int k = 0; k < kPart; k++) acc[k] = 0.0;
     for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x)
@@ -790,7 +812,8 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
         const SlotPose &P = a.pose[s];
         double Du = ord_to_dbl(P.wmax_bits[0]) - ord_to_dbl(P.wmin_bits[0]);
         double Dv = ord_to_dbl(P.wmax_bits[1]) - ord_to_dbl(P.wmin_bits[1]);
-        double sc = P.scale * (Du * Dv) / ((double)a.N * (double)a.N);
+        const int N = a.sd[s].N;
+        double sc = P.scale * (Du * Dv) / ((double)N * (double)N);
         int e = eval0 + s;
         for (int k = 0; k < 3; k++) {
             force[3 * e + k] = red[k] * sc;
@@ -799,7 +822,7 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
         if (P.flags) atomicOr(err_flags, P.flags);
         if (stats_accum) {
             atomicAdd(&stats_accum[0], 1ull);
-            atomicAdd(&stats_accum[1], (unsigned long long)a.N * (unsigned long long)a.N);
+            atomicAdd(&stats_accum[1], (unsigned long long)N * (unsigned long long)N);
             atomicAdd(&stats_accum[2], (unsigned long long)red[6]);
             atomicAdd(&stats_accum[3], (unsigned long long)red[7]);
             for (int k = 0; k < 5; k++) atomicAdd(&stats_accum[4 + k], (unsigned long long)red[8 + k]);
@@ -813,9 +836,9 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
 {
     k_frame<<<S, 32, 0, st>>>(a);
-    dim3 grid(a.n_blocks_x, S);
-    if (a.count) k_trace<true><<<grid, kTileRays, 0, st>>>(a);
-    else k_trace<false><<<grid, kTileRays, 0, st>>>(a);
+    if (a.n_tiles <= 0) return cudaGetLastError();
+    if (a.count) k_trace<true><<<a.n_tiles, kTileRays, 0, st>>>(a);
+    else k_trace<false><<<a.n_tiles, kTileRays, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -21,12 +21,20 @@ SRP_F32, SRP_F64 = 0, 1
 PANELS_TRACK, PANELS_SET, PANELS_TRACK_OFFSET = 0, 1, 2
 EVAL_COUNT = 1
 EVAL_TIMING = 2
+EVAL_AUTOTUNE = 4
 MAX_BOUNCES = 4
 
 # Symbols declared in include/srp.h (checked by the tests against the library).
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",
            "srp_eval_batch", "srp_eval_stats_get", "srp_propagate", "srp_eval_noalloc", "srp_set_materials",
-           "srp_grad", "srp_prop_grad"]
+           "srp_grad", "srp_prop_grad", "srp_propagate_batch", "srp_autotune", "srp_set_tile_shape"]
+
+
+class Traj(C.Structure):
+    """One trajectory of srp_propagate_batch (layout of srp_traj)."""
+    _fields_ = [("mesh_id", C.c_int32), ("N", C.c_int32), ("bounces", C.c_int32), ("panel_mode", C.c_int32),
+                ("angles", C.c_void_p), ("central", C.c_int32), ("attitude", C.c_int32), ("q", C.c_double * 4),
+                ("y0", C.c_double * 6), ("t0", C.c_double), ("t1", C.c_double)]
 
 
 class SrpError(RuntimeError):
@@ -106,6 +114,11 @@ def load(build_if_needed: bool = True):
         lib.srp_eval_stats_get.argtypes = [C.c_void_p, C.POINTER(EvalStats)]
         lib.srp_set_materials.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
         lib.srp_grad.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32] + [C.c_void_p] * 10
+        lib.srp_propagate_batch.argtypes = [C.c_void_p, C.POINTER(PropParams), C.c_int32, C.POINTER(Traj),
+                                            C.c_void_p, C.POINTER(PropStats)]
+        lib.srp_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double)]
+        lib.srp_set_tile_shape.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
         lib.srp_prop_grad.argtypes = [C.c_void_p, C.c_int32, C.POINTER(PropParams), C.c_int32, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.POINTER(PropStats)]
@@ -374,6 +387,46 @@ class Context:
                                            out["q"].ctypes.data, st))
         out["stats"] = [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status) for s in st]
         return out
+
+    def propagate_batch(self, trajs, method: int = RKF78, j2=False, sun3=False, srp_on=True,
+                        epoch_mjd_tt: float = 61041.0, rtol: float = 1e-12, atol_pos: float = 1e-6,
+                        atol_vel: float = 1e-9, h0: float = 60.0, h_min: float = 1e-6, h_max: float = 0.0,
+                        max_steps: int = 10_000_000, poll: int = 16, P0: float = 4.56e-6, eps_rel: float = 1e-9,
+                        autotune: bool = False):
+        """srp_propagate_batch over a list of trajectory dicts with keys mesh_id,
+        N, bounces, panel_mode, angles (or None), central, attitude, q, y0, t0,
+        t1.  Returns (y1 [n, 6], stats list)."""
+        n = len(trajs)
+        arr = (Traj * n)()
+        keep = []
+        for i, t in enumerate(trajs):
+            ang = t.get("angles")
+            a = None if ang is None else np.ascontiguousarray(np.asarray(ang, np.float64))
+            keep.append(a)
+            arr[i] = Traj(int(t["mesh_id"]), int(t["N"]), int(t["bounces"]), int(t.get("panel_mode", PANELS_TRACK)),
+                          a.ctypes.data if a is not None else None, int(t.get("central", CENTRAL_EARTH)),
+                          int(t.get("attitude", ATT_LVLH)), (C.c_double * 4)(*t.get("q", (1.0, 0.0, 0.0, 0.0))),
+                          (C.c_double * 6)(*[float(x) for x in t["y0"]]), float(t["t0"]), float(t["t1"]))
+        p = PropParams(method, 0, int(j2), int(sun3), int(srp_on), 0, (C.c_double * 4)(1.0, 0.0, 0.0, 0.0),
+                       epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, 0,
+                       EvalParams(1, 0, P0, eps_rel, 0, EVAL_AUTOTUNE if autotune else 0), None, 0)
+        y1 = np.empty((n, 6))
+        st = (PropStats * n)()
+        self._check(self.lib.srp_propagate_batch(self.h, C.byref(p), n, arr, y1.ctypes.data, st))
+        return y1, [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status) for s in st]
+
+    def autotune(self, mesh_id: int, N: int, bounces: int, P0: float = 4.56e-6, eps_rel: float = 1e-9,
+                 panel_mode: int = PANELS_TRACK):
+        """srp_autotune: (chosen tile width, ms per evaluation of widths 4, 8, 16, 32)."""
+        p = EvalParams(N, bounces, P0, eps_rel, panel_mode, 0)
+        w = C.c_int32(0)
+        ms = (C.c_double * 4)()
+        self._check(self.lib.srp_autotune(self.h, mesh_id, C.byref(p), C.byref(w), ms))
+        return int(w.value), list(ms)
+
+    def set_tile_shape(self, mesh_id: int, N: int, bounces: int, tile_w: int):
+        """srp_set_tile_shape: trace tiles tile_w pixels wide for (mesh, N, bounces)."""
+        self._check(self.lib.srp_set_tile_shape(self.h, mesh_id, N, bounces, tile_w))
 
     def eval_stats(self) -> dict:
         s = EvalStats()
