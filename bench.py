@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-prop", action="store_true", help="skip the propagation measurement")
     p.add_argument("--no-grad", action="store_true", help="skip the differentiated-form measurement")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    p.add_argument("--batch-traj", type=int, default=256, help="trajectories of the batched form")
     p.add_argument("--grad-arc-steps", type=int, default=1000,
                    help="RK4 steps of the timed adjoint arc (the full differentiated arc is 10000)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
@@ -250,6 +252,104 @@ def bench_differentiated(ctx, stream, arc_steps, facet=0.05, N=512, bounces=1, b
             "arc_gradient_of_x": {"mat": g["mat"].tolist(), "angle": g["angle"].tolist(), "q": g["q"].tolist()}}
 
 
+# ---------------------------------------------------------------- batched
+def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7):
+    """The batched form: n_traj trajectories drawn from a seed, each with its
+    own mesh (a pool of 8 spacecraft meshes of ~0.9k-200k triangles), ray grid
+    (256-1024 per side), bounces (0-2), joint law (tracking, tracking + offsets,
+    commanded), orbit (GEO with an LVLH attitude turned by a random quaternion,
+    or heliocentric at 0.7-1.2 AU with a random inertial quaternion; +-1 km /
+    1 m/s Gaussian perturbations) and arc (GEO 1-4 h, heliocentric 1-10 days),
+    RKF7(8) rtol 1e-12 with J2 + Sun.  Aggregate accepted steps/s and SRP
+    evaluations/s of one srp_propagate_batch call (tile shapes autotuned per
+    (mesh, N, bounces) first, timed separately), against the plain GPU method
+    (srp_propagate on one trajectory at a time) timed on a seeded sample of
+    the same trajectories and extrapolated to all of them."""
+    import math
+
+    import numpy as np
+    from paper_2608_07307_gb300 import inputs as I
+    from paper_2608_07307_gb300 import srp
+
+    rng = np.random.default_rng(seed)
+    facets = [0.4, 0.3, 0.2, 0.15, 0.1, 0.07, 0.035, 0.025]
+    meshes = [I.spacecraft(h) for h in facets]
+    mids = [ctx.load_mesh(m) for m in meshes]
+    mu_e, mu_s, au = 3.986004418e14, 1.32712440018e20, 1.495978707e11
+    trajs = []
+    for k in range(n_traj):
+        mi = int(rng.integers(len(meshes)))
+        mode = int(rng.integers(3))
+        npart = len(meshes[mi].parent)
+        ang = None
+        if mode == srp.PANELS_TRACK_OFFSET:
+            ang = np.concatenate([[0.0, 0.0], rng.uniform(-0.1, 0.1, npart - 2)])
+        elif mode == srp.PANELS_SET:
+            ang = np.concatenate([[0.0, 0.0], rng.uniform(-0.5, 0.5, npart - 2)])
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        if rng.uniform() < 0.5:
+            a = 42164e3
+            v = math.sqrt(mu_e / a)
+            ph, inc = rng.uniform(0, 2 * math.pi), math.radians(0.1)
+            y0 = np.array([a * math.cos(ph), a * math.sin(ph), 0.0, -v * math.sin(ph) * math.cos(inc),
+                           v * math.cos(ph) * math.cos(inc), v * math.sin(inc)])
+            central, att, t1 = 0, 0, rng.uniform(1, 4) * 3600.0
+        else:
+            r = rng.uniform(0.7, 1.2) * au
+            v = math.sqrt(mu_s / r)
+            ph = rng.uniform(0, 2 * math.pi)
+            y0 = np.array([r * math.cos(ph), r * math.sin(ph), 0.0, -v * math.sin(ph), v * math.cos(ph), 0.0])
+            central, att, t1 = 1, 1, rng.uniform(1, 10) * 86400.0
+        y0[:3] += rng.normal(scale=1e3, size=3)
+        y0[3:] += rng.normal(scale=1.0, size=3)
+        trajs.append(dict(mesh_id=mids[mi], N=int(rng.choice([256, 512, 768, 1024])), bounces=int(rng.integers(3)),
+                          panel_mode=mode, angles=ang, central=central, attitude=att, q=tuple(q), y0=y0, t0=0.0,
+                          t1=t1))
+    kw = dict(j2=True, sun3=True, rtol=1e-12, h0=60.0)
+    keys = sorted({(t["mesh_id"], t["N"], t["bounces"]) for t in trajs})
+    t0 = time.perf_counter()
+    shapes = {}
+    for mid, N, b in keys:
+        w, _ = ctx.autotune(mid, N, b)
+        shapes[w] = shapes.get(w, 0) + 1
+    t_tune = time.perf_counter() - t0
+    ctx.propagate_batch(trajs[:8], **kw)  # warm-up (workspace, graph path)
+    t0 = time.perf_counter()
+    y1, st = ctx.propagate_batch(trajs, **kw)
+    t_batch = time.perf_counter() - t0
+    steps = sum(s["steps"] for s in st)
+    evals = sum(s["evals"] for s in st)
+    # plain GPU method on a sample: each trajectory alone
+    idx = rng.choice(n_traj, size=min(plain_sample, n_traj), replace=False)
+    t_plain, steps_plain = 0.0, 0
+    for k in idx:
+        t = trajs[k]
+        if t["angles"] is not None:
+            ctx.set_panel_angles(t["mesh_id"], t["angles"])
+        t0 = time.perf_counter()
+        _, sp, _ = ctx.propagate(t["mesh_id"], t["y0"], [t["t0"], t["t1"]], central=t["central"],
+                                 attitude=t["attitude"], q=t["q"], N=t["N"], bounces=t["bounces"],
+                                 panel_mode=t["panel_mode"], **kw)
+        t_plain += time.perf_counter() - t0
+        steps_plain += sp[0]["steps"]
+        if t["angles"] is not None:
+            ctx.set_panel_angles(t["mesh_id"], np.zeros(len(t["angles"])))
+    plain_steps_per_s = steps_plain / t_plain
+    for mid in mids:
+        ctx.free_mesh(mid)
+    return {"workload": f"{n_traj} trajectories, meshes of {min(m.n_tris for m in meshes)}-"
+                        f"{max(m.n_tris for m in meshes)} triangles, N 256-1024, bounces 0-2, GEO 1-4 h / "
+                        f"heliocentric 1-10 d arcs, RKF7(8) rtol 1e-12, J2 + Sun + SRP",
+            "steps_per_s": steps / t_batch, "evals_per_s": evals / t_batch, "accepted_steps": steps,
+            "srp_evals": evals, "seconds": t_batch,
+            "plain_steps_per_s": plain_steps_per_s,
+            "plain_sample": f"{len(idx)} trajectories one at a time (srp_propagate), {steps_plain} steps in "
+                            f"{t_plain:.2f} s, extrapolated as a rate",
+            "speedup_vs_plain": (steps / t_batch) / plain_steps_per_s,
+            "autotune": {"keys": len(keys), "seconds": t_tune, "chosen_tile_widths": shapes}}
+
+
 # ------------------------------------------------------------------ native
 def run_native(a):
     import numpy as np
@@ -285,6 +385,8 @@ def run_native(a):
             import torch.distributed as dist
             dist.barrier()
 
+    # the library's autotuner picks the trace tile shape for this (mesh, N, bounces)
+    tile_w, tile_ms = ctx.autotune(mid, a.N, a.bounces)
     with torch.cuda.stream(stream):
         for k in range(a.warmup):
             ctx.eval_batch(mid, batch(k), N=a.N, bounces=a.bounces, out=(F, T))
@@ -351,6 +453,8 @@ def run_native(a):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(a), "tris": mesh.n_tris, "N": a.N, "bounces": a.bounces,
                    "batch": B, "accumulation": "f64", "l2": "flushed between timed steps (256 MiB write)",
+                   "tile": f"{tile_w}x{32 // tile_w} (autotuned; ms/eval for widths 4, 8, 16, 32: "
+                           f"{', '.join(f'{x:.3f}' for x in tile_ms)})",
                    "parallelism": f"replicas{world}"},
         "rays_per_s": value * a.N * a.N,
         "segments_per_s": segments / (total_ms / 1000.0) * world,
@@ -373,6 +477,8 @@ def run_native(a):
         line["propagation"] = bench_propagation(ctx, mid, mesh)
     if not a.no_grad:
         line["differentiated"] = bench_differentiated(ctx, stream, a.grad_arc_steps)
+    if not a.no_batch:
+        line["batched"] = bench_batched(ctx, a.batch_traj)
     if not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mesh, table[:8], a, a.cpu_seconds)
     print(json.dumps(line), flush=True)
