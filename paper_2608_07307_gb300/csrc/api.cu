@@ -54,8 +54,6 @@ struct srp_ctx {
     size_t tctx_cap = 0;
     int *amb_count = nullptr;
     size_t amb_count_cap = 0;
-    int *amb_off = nullptr;
-    size_t amb_off_cap = 0;
     double *io = nullptr;
     size_t io_cap = 0;
     int32_t *hits = nullptr;
@@ -333,8 +331,8 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     pl.tw = tuned_tile_w(ctx, m, pl.N, pl.nseg);
     int tiles_x = 0;
     tile_grid(pl.N, pl.tw, tiles_x, pl.nbx);
-    // FP64 re-trace grid: a few blocks per SM, walking the compacted hand-off list
-    pl.nbr = std::max(1, std::min(pl.nbx, 1216 / pl.S));
+    // FP64 re-trace grid: a few blocks per slot (the hand-offs are rare)
+    pl.nbr = std::max(1, std::min(8, 152 / pl.S));
     pl.SL = (size_t)pl.S * pl.lanes;
     const size_t SL = pl.SL;
     CK(ctx, grow(&ctx->pose, &ctx->pose_cap, SL, false));
@@ -344,7 +342,6 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     CK(ctx, grow(&ctx->partials1, &ctx->partials1_cap, SL * kRed1 * kPart, false));
     CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
     CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * pl.nbx, false));
-    CK(ctx, grow(&ctx->amb_off, &ctx->amb_off_cap, SL * (pl.nbx + 1), false));
     if (want_hits || adjoint) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
     // every slot evaluates this mesh on this grid; lane b owns slots [b S, (b + 1) S)
     std::vector<SlotDesc> sd(SL);
@@ -410,7 +407,6 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         a.partials_ref = ctx->partials_ref + s0 * nbr * kPart;
         a.amb_list = ctx->amb_list + s0 * nbx * kTileRays;
         a.amb_count = ctx->amb_count + s0 * nbx;
-        a.amb_off = ctx->amb_off + s0 * (nbx + 1);
         a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
         a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : (adj ? stage : nullptr);
@@ -643,7 +639,6 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->prop_replay);
     cudaFree(ctx->prop_done);
     cudaFree(ctx->amb_count);
-    cudaFree(ctx->amb_off);
     cudaFree(ctx->io);
     cudaFree(ctx->hits);
     cudaFree(ctx->adj_partials);
@@ -1556,7 +1551,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         ntri += (size_t)h.n_dyn_tris * 3;
         nnode += (size_t)h.n_dyn_nodes;
     }
-    const int nbr = std::max(1, std::min(nbx, 1216 / n));
+    const int nbr = std::max(1, std::min(8, 152 / n));
     double *v64, *io, *ang, *cfg;
     float4 *vview, *trec, *nodes;
     unsigned *cnt;
@@ -1564,7 +1559,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     SlotPose *pose;
     unsigned char *tctx;
     double *part, *part1, *partr;
-    int *alist, *acount, *aoff;
+    int *alist, *acount;
     SlotDesc *sd;
     PropState *S;
     CK(ctx, dmalloc(owned, &v64, std::max<size_t>(n64, 1)));
@@ -1583,7 +1578,6 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &partr, (size_t)n * nbr * kPart));
     CK(ctx, dmalloc(owned, &alist, (size_t)n * nbx * kTileRays));
     CK(ctx, dmalloc(owned, &acount, (size_t)n * nbx));
-    CK(ctx, dmalloc(owned, &aoff, (size_t)n * (nbx + 1)));
     CK(ctx, dmalloc(owned, &sd, (size_t)n));
     CK(ctx, dmalloc(owned, &S, (size_t)n));
     double *d_sun = io, *d_dist = io + 3 * (size_t)n, *d_f = d_dist + n, *d_t = d_f + 3 * (size_t)n,
@@ -1685,7 +1679,6 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         a.n_blocks_ref = nbr;
         a.amb_list = alist;
         a.amb_count = acount;
-        a.amb_off = aoff;
         cudaGraph_t graph = nullptr;
         CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;

@@ -150,7 +150,6 @@ struct TraceArgs {
     int n_blocks_ref;
     int *amb_list;               // [S][n_blocks_x][kTileRays] rays handed to the FP64 path, per tile
     int *amb_count;              // [S][n_blocks_x]
-    int *amb_off;                // [S][n_blocks_x + 1] exclusive scan of amb_count
     int32_t *hits;               // [S][ray_stride][seg_stride] or null
     int count;                   // gather traversal counters
 };

@@ -23,18 +23,24 @@
 //     origin is rebuilt from the hit's barycentric weights.
 // Every FP32 decision carries an error bound: when an edge function, the
 // nearest-hit comparison or the self-hit threshold is within its bound, the
-// ray is handed to the FP64 path and contributes nothing here.  Per hit:
+// triangle is settled in FP64 at the end of the segment (resolve64); only a ray
+// with too many such triangles is handed to the FP64 re-trace and contributes
+// nothing here.  Per hit:
 // absorbed + specular + Lambertian momentum, torque about c_ref, specular ray
 // of weight w rho_s.  Per-ray sums in FP32 (at most 1 + bounces terms), tile
 // sums in FP64 by warp shuffles, one FP64 partial per tile; the tile's
 // handed-off rays go to its own list slot.
 //
-// k_amb_scan + k_refine (FP64 path).  The per-tile hand-off counts are
-// scanned; refine threads walk the dense list in a fixed order and re-trace
-// each ray from its pixel definition with FP64 rays and vertices, the same BVH
-// (boxes padded well beyond the FP32 rounding of the ray; leaves pre-tested in
-// FP32 with a bound, so only triangles not certainly missed are tested in
-// FP64) and the same watertight test in FP64.
+// resolve64 (FP64, inside k_trace).  When a segment had FP32 decisions within
+// their bounds, its uncertain triangles and its nearest certain hit are tested
+// again in FP64 against the exact ray of the segment (rare: ~0.5% of the rays
+// of a 200k-triangle mesh at 1024^2).
+//
+// k_refine (FP64 path).  A ray whose uncertain triangles overflow the
+// candidate list is re-traced from its pixel definition with FP64 rays and
+// vertices, the same BVH (boxes padded well beyond the FP32 rounding of the
+// ray; leaves pre-tested in FP32 with a bound, so only triangles not certainly
+// missed are tested in FP64) and the same watertight test in FP64.
 //
 // k_reduce1 + k_reduce.  Fixed-order FP64 sums: contiguous ranges of tile
 // partials per first-level block, then those and the refine partials per
@@ -233,43 +239,68 @@ struct Counts {
     int flags;
 };
 
-// Classify one candidate from its edge functions and depth.  Returns true when
-// the FP32 decision is not certain.  Updates best on a certain nearer hit.
+// Triangles whose FP32 decision was not certain, for the FP64 resolution at the
+// end of the segment (part << 24 | part-local triangle).
+constexpr int kCand = 8;
+struct Cands {
+    int n;
+    int id[kCand];
+};
+
+__device__ __forceinline__ bool push_cand(Cands &c, int p, int tl)
+{
+    if (c.n >= kCand) return false;
+    c.id[c.n++] = (p << 24) | tl;
+    return true;
+}
+
+// Classify one candidate from its edge functions and depth.  Certain misses and
+// certain hits are settled here (best keeps the nearest certain hit); a triangle
+// whose decision is within its bound becomes a candidate of the FP64 resolution,
+// and so does the best hit it displaces within the tie band.  Returns false when
+// the candidate list overflows (the ray then goes to the FP64 re-trace).
 template <bool COUNT>
 __device__ __forceinline__ bool classify(float U, float V, float W, float eU, float eV, float eW, float T, float det,
-                                         float tlo, float tau, int p, int tl, Best32 &best, bool primary, Counts &cn)
+                                         float tlo, float tau, int p, int tl, Best32 &best, bool primary, Counts &cn,
+                                         Cands &cd)
 {
     bool neg = (U < -eU) || (V < -eV) || (W < -eW);
     bool pos = (U > eU) || (V > eV) || (W > eW);
-    if (neg && pos) return false;  // certainly outside
+    if (neg && pos) return true;  // certainly outside
     bool unsure = fabsf(U) <= eU || fabsf(V) <= eV || fabsf(W) <= eW;
     float t = T / det;
     if (unsure) {
         // near an edge: matters unless the plane is certainly behind the origin or beyond the best hit
         bool far = (fabsf(det) > 1e-30f) && (t > best.t + tau || t < tlo - tau);
-        if (!far && COUNT) cn.why[primary ? 0 : 1] += 1.f;
-        return !far;
+        if (far) return true;
+        if (COUNT) cn.why[primary ? 0 : 1] += 1.f;
+        return push_cand(cd, p, tl);
     }
     bool amb = false;
     if (fabsf(t - tlo) <= tau) { amb = true; if (COUNT) cn.why[3] += 1.f; }
     else if (fabsf(t - best.t) <= tau) { amb = true; if (COUNT) cn.why[2] += 1.f; }
+    if (amb && !push_cand(cd, p, tl)) return false;
     if (t > tlo && t < best.t) {
+        if (amb && best.part >= 0 && !push_cand(cd, best.part, best.tl)) return false;
         float id = 1.0f / det;
         best.t = t; best.part = p; best.tl = tl; best.b1 = V * id; best.b2 = W * id;
     }
-    return amb;
+    return true;
 }
 
 // Nearest hit of one segment in FP32.  `primary`: the view-frame test at pixel
-// centre (uc, vc); otherwise the world-frame test.  Returns false when some
-// decision was within its error bound (the ray then goes to the FP64 path).
+// centre (uc, vc); otherwise the world-frame test.  Triangles whose decision
+// was within its error bound are collected in cd (settled in FP64 afterwards);
+// returns false when they overflow the list or a walk bound is reached (the ray
+// then goes to the FP64 re-trace).
 template <bool COUNT>
 __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float uc, float vc, float tlo, int skip,
-                          float delta, float tau, Best32 &best, Counts &cn)
+                          float delta, float tau, Best32 &best, Counts &cn, Cands &cd)
 {
     best.t = INFINITY;
     best.part = -1;
     best.tl = -1;
+    cd.n = 0;
     int stack[kStack];
     unsigned n_nodes = 0, n_tris = 0, n_boxes = 0;
     bool clean = true;
@@ -316,7 +347,7 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
                     float eW = delta * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + u4 * (fabsf(Bx * Ay) + fabsf(By * Ax));
                     float det = U + V + W;
                     float T = fmaf(U, a.z - B.w0_32, fmaf(V, b.z - B.w0_32, W * (c.z - B.w0_32)));
-                    if (classify<COUNT>(U, V, W, eU, eV, eW, T, det, tlo, tau, p, tl, best, true, cn)) { clean = false; sp = 0; }
+                    if (!classify<COUNT>(U, V, W, eU, eV, eW, T, det, tlo, tau, p, tl, best, true, cn, cd)) { clean = false; sp = 0; }
                 } else {
                     const float4 *tr = pv.tri + (size_t)tl * 3;
                     float4 a = __ldg(tr), b = __ldg(tr + 1), c = __ldg(tr + 2);
@@ -341,11 +372,11 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
                         float eW = dc * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + u4 * (fabsf(Bx * Ay) + fabsf(By * Ax));
                         float det = U + V + W;
                         float T = fmaf(U, r.Sz * Akz, fmaf(V, r.Sz * Bkz, W * (r.Sz * Ckz)));
-                        if (classify<COUNT>(U, V, W, eU, eV, eW, T, det, tlo, tau, p, tl, best, false, cn)) { clean = false; sp = 0; }
+                        if (!classify<COUNT>(U, V, W, eU, eV, eW, T, det, tlo, tau, p, tl, best, false, cn, cd)) { clean = false; sp = 0; }
                     }
                 }
             }
-            // a handed-off ray is re-traced from scratch: its stack was emptied
+            // a handed-off ray (overflow) is re-traced from scratch: its stack was emptied
             if (sp == 0) break;
             ref = stack[--sp];
         }
@@ -389,6 +420,9 @@ __device__ __forceinline__ int slot_of_block(const SlotDesc *sd, int S, int g)
     return lo;
 }
 
+__device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, int seg, const int *hpt, int skip,
+                                       const Cands &cd, Best32 &best);
+
 // One warp per block, one 32-pixel tile (tile_w x 32 / tile_w) per block; the
 // blocks of all slots form one flat grid.  Latency bound: 32 warps per SM at
 // the kernel's 64 registers (no spills).
@@ -426,10 +460,11 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
         float wgt = 1.0f;
         int skip = -1;
         float acc[6] = {0, 0, 0, 0, 0, 0};
-        int hits[kMaxBounces + 1];
+        int hits[kMaxBounces + 1], hpt[kMaxBounces + 1];
         for (int k = 0; k <= kMaxBounces; k++) hits[k] = -1;
         bool clean = true;
         int nseg_done = 0;
+        Cands cd;
         Counts cn = {0.f, 0.f, 0.f, {0.f, 0.f, 0.f, 0.f}, 0};
         float delta = B.delta_p, tau = B.tau_p;
         for (int seg = 0; seg < nseg; seg++) {
@@ -437,8 +472,10 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
             Best32 h;
             float tlo = seg == 0 ? 0.0f : B.eps32;
             nseg_done++;
-            if (!nearest32<COUNT>(B, r, seg == 0, uc, vc, tlo, skip, delta, tau, h, cn)) { clean = false; break; }
+            if (!nearest32<COUNT>(B, r, seg == 0, uc, vc, tlo, skip, delta, tau, h, cn, cd)) { clean = false; break; }
+            if (cd.n > 0) resolve64(B, N, i, j, seg, hpt, skip, cd, h);  // rare: settle in FP64
             if (h.part < 0) break;
+            hpt[seg] = (h.part << 24) | h.tl;
             const float4 *tr = B.part[h.part].tri + (size_t)h.tl * 3;
             float4 a0 = __ldg(tr), a1 = __ldg(tr + 1), a2 = __ldg(tr + 2);
             int orig = __float_as_int(a0.w);
@@ -514,35 +551,6 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
     }
 }
 
-// Exclusive scan of the per-tile hand-off counts of one slot (one block per
-// slot): each thread scans a contiguous chunk, the chunk totals are scanned
-// across the block, then added back.
-__global__ void __launch_bounds__(1024) k_amb_scan(TraceArgs a)
-{
-    __shared__ int tot[1024];
-    const int s = blockIdx.x, n = a.sd[s].tiles, t = threadIdx.x;
-    const int *cnt = a.amb_count + (size_t)s * a.n_blocks_x;
-    int *off = a.amb_off + (size_t)s * (a.n_blocks_x + 1);
-    const int chunk = (n + 1023) / 1024;
-    const int b0 = min(t * chunk, n), b1 = min(b0 + chunk, n);
-    int sum = 0;
-    for (int b = b0; b < b1; b++) sum += cnt[b];
-    tot[t] = sum;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        int x = t >= o ? tot[t - o] : 0;
-        __syncthreads();
-        tot[t] += x;
-        __syncthreads();
-    }
-    int run = tot[t] - sum;
-    for (int b = b0; b < b1; b++) {
-        off[b] = run;
-        run += cnt[b];
-    }
-    if (t == 1023) off[n] = tot[1023];
-}
-
 // ------------------------------------------------------------- FP64 path
 struct Ray64 {
     double o[3], d[3];
@@ -572,6 +580,81 @@ __device__ void tri_v64(const TraceCtx &B, int p, int tl, double *v)
         int vi = B.tri_vidx[3 * t + c] - pv.vert_begin;
         for (int k = 0; k < 3; k++) v[3 * c + k] = pv.v64[3 * vi + k];
     }
+}
+
+// FP64 watertight edge functions and scaled depth of triangle v against ray r.
+__device__ __forceinline__ void wt64(const Ray64 &r, const double *v, double &U, double &V, double &W, double &det,
+                                     double &T)
+{
+    double A[3], Bv[3], C[3];
+    for (int k = 0; k < 3; k++) { A[k] = v[k] - r.o[k]; Bv[k] = v[3 + k] - r.o[k]; C[k] = v[6 + k] - r.o[k]; }
+    double Akz = pickd(A[0], A[1], A[2], r.kz), Bkz = pickd(Bv[0], Bv[1], Bv[2], r.kz), Ckz = pickd(C[0], C[1], C[2], r.kz);
+    double Ax = pickd(A[0], A[1], A[2], r.kx) - r.Sx * Akz, Ay = pickd(A[0], A[1], A[2], r.ky) - r.Sy * Akz;
+    double Bx = pickd(Bv[0], Bv[1], Bv[2], r.kx) - r.Sx * Bkz, By = pickd(Bv[0], Bv[1], Bv[2], r.ky) - r.Sy * Bkz;
+    double Cx = pickd(C[0], C[1], C[2], r.kx) - r.Sx * Ckz, Cy = pickd(C[0], C[1], C[2], r.ky) - r.Sy * Ckz;
+    U = __dsub_rn(__dmul_rn(Cx, By), __dmul_rn(Cy, Bx));
+    V = __dsub_rn(__dmul_rn(Ax, Cy), __dmul_rn(Ay, Cx));
+    W = __dsub_rn(__dmul_rn(Bx, Ay), __dmul_rn(By, Ax));
+    det = U + V + W;
+    T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+}
+
+// Settle one segment's uncertain FP32 decisions in FP64: the segment's ray
+// from the pixel definition (for a specular segment, the FP64 chain through
+// the earlier segments' hit triangles), then the FP64 watertight test of each
+// candidate and of the nearest certain FP32 hit; the nearest t above the
+// self-hit threshold wins, equal t goes to the lowest original triangle id (the
+// rule of the FP64 re-trace).  Every other triangle was certainly missed,
+// certainly farther, or culled beyond the certain hit plus its band.
+__device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, int seg, const int *hpt, int skip,
+                                       const Cands &cd, Best32 &best)
+{
+    Ray64 r;
+    double uc = B.umin + ((double)i + 0.5) * B.Du / N;
+    double vc = B.vmin + ((double)j + 0.5) * B.Dv / N;
+    double w0 = B.wmin - kStandoff;
+    for (int k = 0; k < 3; k++) { r.o[k] = uc * B.u[k] + vc * B.v[k] + w0 * B.d[k]; r.d[k] = B.d[k]; }
+    double v[9], U, V, W, det, T;
+    for (int s = 0; s < seg; s++) {
+        tri_v64(B, hpt[s] >> 24, hpt[s] & 0xffffff, v);
+        ray64_setup(r);
+        wt64(r, v, U, V, W, det, T);
+        double t = T / det;
+        double e1[3], e2[3], n[3];
+        for (int k = 0; k < 3; k++) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int k = 0; k < 3; k++) n[k] /= nl;
+        double dn = r.d[0] * n[0] + r.d[1] * n[1] + r.d[2] * n[2];
+        for (int k = 0; k < 3; k++) { r.o[k] = r.o[k] + t * r.d[k]; r.d[k] = r.d[k] - 2.0 * dn * n[k]; }
+    }
+    ray64_setup(r);
+    const double tlo = seg == 0 ? 0.0 : B.eps;
+    double bt = INFINITY, b1 = 0.0, b2 = 0.0;
+    int bp = -1, btl = -1, bo = 0x7fffffff;
+    for (int c = 0; c <= cd.n; c++) {
+        int p, tl;
+        if (c < cd.n) { p = cd.id[c] >> 24; tl = cd.id[c] & 0xffffff; }
+        else if (best.part >= 0) { p = best.part; tl = best.tl; }
+        else break;
+        int orig = __float_as_int(__ldg(B.part[p].tri + (size_t)tl * 3).w);
+        if (orig == skip) continue;
+        tri_v64(B, p, tl, v);
+        wt64(r, v, U, V, W, det, T);
+        bool out = (U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0);
+        if (out || det == 0.0) continue;
+        double t = T / det;
+        if (t > tlo && (t < bt || (t == bt && orig < bo))) {
+            bt = t; bp = p; btl = tl; bo = orig; b1 = V / det; b2 = W / det;
+        }
+    }
+    best.t = (float)bt;
+    best.part = bp;
+    best.tl = btl;
+    best.b1 = (float)b1;
+    best.b2 = (float)b2;
 }
 
 // True when the FP32 world-frame test shows the triangle certainly misses the
@@ -732,31 +815,32 @@ __device__ void refine_ray(const TraceCtx &B, const TraceArgs &a, int s, int ray
     acc[7] += (double)nseg_done;
 }
 
-// Threads walk the dense hand-off list of their slot in a fixed order.
+// Rays the trace could not settle (a walk bound, or more uncertain triangles
+// than the candidate list holds; rare) are re-traced here.  Each thread walks
+// a fixed, strided set of its slot's tiles and re-traces the listed rays of
+// each in order, so the sums are reproducible; a small grid, because the work
+// is almost always empty and a large one would take SM resources the trace
+// launches of the other lanes need.
 __global__ void __launch_bounds__(256) k_refine(TraceArgs a)
 {
     __shared__ TraceCtx B;
     __shared__ int blk_flags;
     const int s = blockIdx.y;
     const int nt = a.sd[s].tiles;
-    const int *off = a.amb_off + (size_t)s * (a.n_blocks_x + 1);
-    const int total = a.pose[s].skip ? 0 : off[nt];
     double acc[kPart];
     for (int k = 0; k < kPart; k++) acc[k] = 0.0;
-    if ((int)(blockIdx.x * blockDim.x) < total) {
+    if (!a.pose[s].skip) {
         if (threadIdx.x == 0) blk_flags = 0;
         load_ctx(B, a, s);
         __syncthreads();
         int flags = 0;
-        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-            // tile holding item g: largest b with off[b] <= g
-            int lo = 0, hi = nt - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (off[mid] <= g) lo = mid; else hi = mid - 1;
+        const int *cnt = a.amb_count + (size_t)s * a.n_blocks_x;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+            const int c = cnt[t];
+            for (int q = 0; q < c; q++) {
+                int ray = a.amb_list[((size_t)s * a.n_blocks_x + t) * kTileRays + q];
+                refine_ray(B, a, s, ray, acc, flags);
             }
-            int ray = a.amb_list[((size_t)s * a.n_blocks_x + lo) * kTileRays + (g - off[lo])];
-            refine_ray(B, a, s, ray, acc, flags);
         }
         if (flags) atomicOr(&blk_flags, flags);
         __syncthreads();
@@ -844,7 +928,6 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
 
 cudaError_t launch_refine(const TraceArgs &a, int S, cudaStream_t st)
 {
-    k_amb_scan<<<S, 1024, 0, st>>>(a);
     dim3 grid(a.n_blocks_ref, S);
     k_refine<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
