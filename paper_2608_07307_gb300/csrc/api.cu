@@ -178,6 +178,7 @@ srp_status ensure_slots(srp_ctx *ctx, Mesh *m, int S)
     SlotBufs &b = m->sb;
     CK(ctx, dmalloc(m->slot_allocs, &b.vert64, (size_t)S * h.n_dyn_verts * 3));
     CK(ctx, dmalloc(m->slot_allocs, &b.vview, (size_t)S * h.n_verts));
+    CK(ctx, dmalloc(m->slot_allocs, &b.vview64, (size_t)S * h.n_verts * 3));
     CK(ctx, dmalloc(m->slot_allocs, &b.tri, (size_t)S * h.n_dyn_tris * 3));
     CK(ctx, dmalloc(m->slot_allocs, &b.node, (size_t)S * h.n_dyn_nodes * 4));
     CK(ctx, dmalloc(m->slot_allocs, &b.counter, (size_t)S * h.n_dyn_nodes));
@@ -285,6 +286,7 @@ SlotBufs slot_bufs(const MeshDev &h, const SlotBufs &base, size_t k)
     SlotBufs b = base;
     b.vert64 += k * h.n_dyn_verts * 3;
     b.vview += k * h.n_verts;
+    b.vview64 += k * h.n_verts * 3;
     b.tri += k * h.n_dyn_tris * 3;
     b.node += k * h.n_dyn_nodes * 4;
     b.counter += k * h.n_dyn_nodes;
@@ -1552,7 +1554,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         nnode += (size_t)h.n_dyn_nodes;
     }
     const int nbr = std::max(1, std::min(8, 152 / n));
-    double *v64, *io, *ang, *cfg;
+    double *v64, *vv64, *io, *ang, *cfg;
     float4 *vview, *trec, *nodes;
     unsigned *cnt;
     float *rbox;
@@ -1564,6 +1566,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     PropState *S;
     CK(ctx, dmalloc(owned, &v64, std::max<size_t>(n64, 1)));
     CK(ctx, dmalloc(owned, &vview, nview));
+    CK(ctx, dmalloc(owned, &vv64, nview * 3));
     CK(ctx, dmalloc(owned, &trec, std::max<size_t>(ntri, 1)));
     CK(ctx, dmalloc(owned, &nodes, std::max<size_t>(nnode * 4, 1)));
     CK(ctx, dmalloc(owned, &cnt, std::max<size_t>(nnode, 1)));
@@ -1595,6 +1598,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         d.mesh = m->d;
         d.sb.vert64 = v64 + o64;
         d.sb.vview = vview + oview;
+        d.sb.vview64 = vv64 + oview * 3;
         d.sb.tri = trec + otri;
         d.sb.node = nodes + onode * 4;
         d.sb.counter = cnt + onode;

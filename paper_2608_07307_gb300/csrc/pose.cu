@@ -156,6 +156,9 @@ __global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *
         }
         // view-frame position of the vertex for the primary-ray test, rounded once
         slot.vview[k] = make_float4((float)pr[0], (float)pr[1], (float)pr[2], 0.f);
+        slot.vview64[3 * (size_t)k] = pr[0];
+        slot.vview64[3 * (size_t)k + 1] = pr[1];
+        slot.vview64[3 * (size_t)k + 2] = pr[2];
     }
     __shared__ double smn[3][8], smx[3][8];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;

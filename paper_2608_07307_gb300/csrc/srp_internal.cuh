@@ -101,6 +101,7 @@ struct MeshDev {
 struct SlotBufs {
     double *vert64;     // [S][n_dyn_verts][3] posed FP64
     float4 *vview;      // [S][n_verts] (u.x, v.x, d.x, 0) of every posed vertex, FP32 rounded from FP64
+    double *vview64;    // [S][n_verts][3] the same projections in FP64 (settling uncertain primary decisions)
     float4 *tri;        // [S][n_dyn_tris][3]
     float4 *node;       // [S][n_dyn_nodes][4]
     unsigned *counter;  // [S][n_dyn_nodes] refit arrival counters (never reset; parity of the count)

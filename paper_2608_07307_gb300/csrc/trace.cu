@@ -78,6 +78,7 @@ struct TraceCtx {
     int n_parts, n_mats;
     int skip;              // evaluation skipped: trace blocks only clear their hand-off count
     const float4 *vview;   // slot's view-frame vertices
+    const double *vview64; // the same in FP64
     const float2 *mat32;
     const double *mat64;
     const unsigned *tri_mat;
@@ -151,6 +152,7 @@ __global__ void k_frame(TraceArgs a)
     B.n_parts = m->n_parts;
     B.n_mats = m->n_mats;
     B.vview = sb.vview;
+    B.vview64 = sb.vview64;
     B.mat32 = m->mat32;
     B.mat64 = m->mat64;
     B.tri_mat = m->tri_mat;
@@ -567,9 +569,10 @@ __device__ void ray64_setup(Ray64 &r)
     double dz = pickd(r.d[0], r.d[1], r.d[2], kz);
     if (dz < 0.0) { int t = kx; kx = ky; ky = t; }
     r.kx = kx; r.ky = ky; r.kz = kz;
-    r.Sx = pickd(r.d[0], r.d[1], r.d[2], kx) / dz;
-    r.Sy = pickd(r.d[0], r.d[1], r.d[2], ky) / dz;
-    r.Sz = 1.0 / dz;
+    const double rz = 1.0 / dz;
+    r.Sx = pickd(r.d[0], r.d[1], r.d[2], kx) * rz;
+    r.Sy = pickd(r.d[0], r.d[1], r.d[2], ky) * rz;
+    r.Sz = rz;
 }
 
 __device__ void tri_v64(const TraceCtx &B, int p, int tl, double *v)
@@ -599,62 +602,82 @@ __device__ __forceinline__ void wt64(const Ray64 &r, const double *v, double &U,
     T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
 }
 
-// Settle one segment's uncertain FP32 decisions in FP64: the segment's ray
-// from the pixel definition (for a specular segment, the FP64 chain through
-// the earlier segments' hit triangles), then the FP64 watertight test of each
-// candidate and of the nearest certain FP32 hit; the nearest t above the
-// self-hit threshold wins, equal t goes to the lowest original triangle id (the
-// rule of the FP64 re-trace).  Every other triangle was certainly missed,
-// certainly farther, or culled beyond the certain hit plus its band.
+// Settle one segment's uncertain FP32 decisions in FP64: the FP64 test of each
+// candidate and of the nearest certain FP32 hit against the segment's exact
+// ray; the nearest t above the self-hit threshold wins, equal t goes to the
+// lowest original triangle id (the rule of the FP64 re-trace).  Every other
+// triangle was certainly missed, certainly farther, or culled beyond the
+// certain hit plus its band.  Primary segments are tested in the view frame
+// (the ray is the line through the FP64 pixel centre along d; vertex
+// projections computed once per evaluation in FP64); a specular segment's ray
+// is the FP64 chain through the earlier segments' hit triangles, tested with
+// the FP64 watertight test.  FP64 is slow on this GPU: no square roots, one
+// division per candidate, barycentric weights for the winner only.
 __device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, int seg, const int *hpt, int skip,
                                        const Cands &cd, Best32 &best)
 {
-    Ray64 r;
-    double uc = B.umin + ((double)i + 0.5) * B.Du / N;
-    double vc = B.vmin + ((double)j + 0.5) * B.Dv / N;
-    double w0 = B.wmin - kStandoff;
-    for (int k = 0; k < 3; k++) { r.o[k] = uc * B.u[k] + vc * B.v[k] + w0 * B.d[k]; r.d[k] = B.d[k]; }
-    double v[9], U, V, W, det, T;
-    for (int s = 0; s < seg; s++) {
-        tri_v64(B, hpt[s] >> 24, hpt[s] & 0xffffff, v);
-        ray64_setup(r);
-        wt64(r, v, U, V, W, det, T);
-        double t = T / det;
-        double e1[3], e2[3], n[3];
-        for (int k = 0; k < 3; k++) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
-        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
-        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
-        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
-        double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        for (int k = 0; k < 3; k++) n[k] /= nl;
-        double dn = r.d[0] * n[0] + r.d[1] * n[1] + r.d[2] * n[2];
-        for (int k = 0; k < 3; k++) { r.o[k] = r.o[k] + t * r.d[k]; r.d[k] = r.d[k] - 2.0 * dn * n[k]; }
-    }
-    ray64_setup(r);
-    const double tlo = seg == 0 ? 0.0 : B.eps;
-    double bt = INFINITY, b1 = 0.0, b2 = 0.0;
+    double bt = INFINITY, bU = 0.0, bV = 0.0, bW = 0.0;
     int bp = -1, btl = -1, bo = 0x7fffffff;
+    const double uc = B.umin + ((double)i + 0.5) * B.Du / N;
+    const double vc = B.vmin + ((double)j + 0.5) * B.Dv / N;
+    const double w0 = B.wmin - kStandoff;
+    Ray64 r;
+    double tlo = 0.0;
+    if (seg > 0) {
+        for (int k = 0; k < 3; k++) { r.o[k] = uc * B.u[k] + vc * B.v[k] + w0 * B.d[k]; r.d[k] = B.d[k]; }
+        double v[9];
+        for (int s = 0; s < seg; s++) {
+            // hit point on the plane of the segment's triangle, then the specular direction
+            tri_v64(B, hpt[s] >> 24, hpt[s] & 0xffffff, v);
+            double e1[3], e2[3], m[3], ao[3];
+            for (int k = 0; k < 3; k++) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; ao[k] = v[k] - r.o[k]; }
+            m[0] = e1[1] * e2[2] - e1[2] * e2[1];
+            m[1] = e1[2] * e2[0] - e1[0] * e2[2];
+            m[2] = e1[0] * e2[1] - e1[1] * e2[0];
+            double dm = r.d[0] * m[0] + r.d[1] * m[1] + r.d[2] * m[2];
+            double t = (ao[0] * m[0] + ao[1] * m[1] + ao[2] * m[2]) / dm;
+            double f = 2.0 * dm / (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            for (int k = 0; k < 3; k++) { r.o[k] = r.o[k] + t * r.d[k]; r.d[k] = r.d[k] - f * m[k]; }
+        }
+        ray64_setup(r);
+        tlo = B.eps;
+    }
     for (int c = 0; c <= cd.n; c++) {
         int p, tl;
         if (c < cd.n) { p = cd.id[c] >> 24; tl = cd.id[c] & 0xffffff; }
         else if (best.part >= 0) { p = best.part; tl = best.tl; }
         else break;
-        int orig = __float_as_int(__ldg(B.part[p].tri + (size_t)tl * 3).w);
+        const PartView &pv = B.part[p];
+        int orig = __float_as_int(__ldg(pv.tri + (size_t)tl * 3).w);
         if (orig == skip) continue;
-        tri_v64(B, p, tl, v);
-        wt64(r, v, U, V, W, det, T);
+        double U, V, W, det, T;
+        if (seg == 0) {
+            int4 vi = __ldg(pv.v4 + tl);
+            const double *a = B.vview64 + 3 * (size_t)vi.x, *b = B.vview64 + 3 * (size_t)vi.y,
+                         *q = B.vview64 + 3 * (size_t)vi.z;
+            double Ax = a[0] - uc, Ay = a[1] - vc, Bx = b[0] - uc, By = b[1] - vc, Cx = q[0] - uc, Cy = q[1] - vc;
+            U = __dsub_rn(__dmul_rn(Cx, By), __dmul_rn(Cy, Bx));
+            V = __dsub_rn(__dmul_rn(Ax, Cy), __dmul_rn(Ay, Cx));
+            W = __dsub_rn(__dmul_rn(Bx, Ay), __dmul_rn(By, Ax));
+            det = U + V + W;
+            T = U * (a[2] - w0) + V * (b[2] - w0) + W * (q[2] - w0);
+        } else {
+            double v[9];
+            tri_v64(B, p, tl, v);
+            wt64(r, v, U, V, W, det, T);
+        }
         bool out = (U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0);
         if (out || det == 0.0) continue;
         double t = T / det;
         if (t > tlo && (t < bt || (t == bt && orig < bo))) {
-            bt = t; bp = p; btl = tl; bo = orig; b1 = V / det; b2 = W / det;
+            bt = t; bp = p; btl = tl; bo = orig; bU = det; bV = V; bW = W;
         }
     }
     best.t = (float)bt;
     best.part = bp;
     best.tl = btl;
-    best.b1 = (float)b1;
-    best.b2 = (float)b2;
+    best.b1 = bp >= 0 ? (float)(bV / bU) : 0.f;
+    best.b2 = bp >= 0 ? (float)(bW / bU) : 0.f;
 }
 
 // True when the FP32 world-frame test shows the triangle certainly misses the
