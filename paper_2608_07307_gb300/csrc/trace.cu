@@ -236,8 +236,8 @@ struct Best32 {
 };
 
 struct Counts {
-    float nodes, tris, boxes;
-    float why[4];  // hand-offs: primary edge, secondary edge, near tie, self-hit band
+    unsigned nodes, tris, boxes;
+    unsigned why[4];  // uncertain FP32 decisions: primary edge, secondary edge, near tie, self-hit band
     int flags;
 };
 
@@ -275,12 +275,12 @@ __device__ __forceinline__ bool classify(float U, float V, float W, float eU, fl
         // near an edge: matters unless the plane is certainly behind the origin or beyond the best hit
         bool far = (fabsf(det) > 1e-30f) && (t > best.t + tau || t < tlo - tau);
         if (far) return true;
-        if (COUNT) cn.why[primary ? 0 : 1] += 1.f;
+        if (COUNT) cn.why[primary ? 0 : 1]++;
         return push_cand(cd, p, tl);
     }
     bool amb = false;
-    if (fabsf(t - tlo) <= tau) { amb = true; if (COUNT) cn.why[3] += 1.f; }
-    else if (fabsf(t - best.t) <= tau) { amb = true; if (COUNT) cn.why[2] += 1.f; }
+    if (fabsf(t - tlo) <= tau) { amb = true; if (COUNT) cn.why[3]++; }
+    else if (fabsf(t - best.t) <= tau) { amb = true; if (COUNT) cn.why[2]++; }
     if (amb && !push_cand(cd, p, tl)) return false;
     if (t > tlo && t < best.t) {
         if (amb && best.part >= 0 && !push_cand(cd, best.part, best.tl)) return false;
@@ -383,7 +383,7 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
             ref = stack[--sp];
         }
     }
-    if (COUNT) { cn.nodes += (float)n_nodes; cn.tris += (float)n_tris; cn.boxes += (float)n_boxes; }
+    if (COUNT) { cn.nodes += n_nodes; cn.tris += n_tris; cn.boxes += n_boxes; }
     return clean;
 }
 
@@ -446,8 +446,9 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
     const int tw = D.tile_w, lw = __ffs(tw) - 1;
     const int i = (tile_id % D.tiles_x) * tw + (lane & (tw - 1));
     const int j = (tile_id / D.tiles_x) * (kTileRays >> lw) + (lane >> lw);
-    double acc64[kPart];
-    for (int k = 0; k < kPart; k++) acc64[k] = 0.0;
+    // per-ray results: force / torque in FP32 (at most 1 + bounces terms), counts as integers
+    float fac[6] = {0, 0, 0, 0, 0, 0};
+    unsigned cnt[kPart] = {0};
     bool handoff = false;
     int flags = 0;
     const int ray = i * N + j;
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
         bool clean = true;
         int nseg_done = 0;
         Cands cd;
-        Counts cn = {0.f, 0.f, 0.f, {0.f, 0.f, 0.f, 0.f}, 0};
+        Counts cn = {0u, 0u, 0u, {0u, 0u, 0u, 0u}, 0};
         float delta = B.delta_p, tau = B.tau_p;
         for (int seg = 0; seg < nseg; seg++) {
             ray_setup(r);
@@ -521,31 +522,40 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
         }
         flags = cn.flags;
         if (clean) {
-            for (int k = 0; k < 6; k++) acc64[k] = (double)acc[k];
-            acc64[7] = (double)nseg_done;
-            for (int k = 0; k < nseg; k++) acc64[8 + k] = hits[k] >= 0 ? 1.0 : 0.0;
+            for (int k = 0; k < 6; k++) fac[k] = acc[k];
+            cnt[7] = nseg_done;
+            for (int k = 0; k < nseg; k++) cnt[8 + k] = hits[k] >= 0 ? 1u : 0u;
             if (a.hits) {
                 int32_t *hq = a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride;
                 for (int k = 0; k < nseg; k++) hq[k] = hits[k];
             }
         } else {
             handoff = true;
-            acc64[6] = 1.0;
+            cnt[6] = 1;
         }
         if (COUNT) {
-            acc64[13] = cn.nodes; acc64[14] = cn.tris; acc64[15] = cn.boxes;
-            for (int k = 0; k < 4; k++) acc64[16 + k] = cn.why[k];
+            cnt[13] = cn.nodes; cnt[14] = cn.tris; cnt[15] = cn.boxes;
+            for (int k = 0; k < 4; k++) cnt[16 + k] = cn.why[k];
         }
     }
     // tile-ordered list of the rays handed to the FP64 path
     const size_t tile = (size_t)s * a.n_blocks_x + tile_id;
     unsigned bal = __ballot_sync(0xffffffffu, handoff);
     if (handoff) a.amb_list[tile * kTileRays + __popc(bal & ((1u << lane) - 1u))] = ray;
-    // tile sum (fixed shuffle order), one partial per tile
-    for (int k = 0; k < kPart; k++) {
-        double x = warp_sum(acc64[k]);
-        if (lane == 0) a.partials[tile * kPart + k] = x;
+    // tile sums, one FP64 partial per tile: force and torque by a fixed FP32
+    // butterfly over the 32 rays (FP64 shuffles would occupy GB300's slow FP64
+    // pipe), counts by integer reductions; every sum above the tile is FP64
+    for (int k = 0; k < 6; k++) {
+        float x = fac[k];
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) a.partials[tile * kPart + k] = (double)x;
     }
+    for (int k = 6; k < (COUNT ? kPart : 13); k++) {
+        unsigned x = __reduce_add_sync(0xffffffffu, cnt[k]);
+        if (lane == 0) a.partials[tile * kPart + k] = (double)x;
+    }
+    if (!COUNT && lane == 0)
+        for (int k = 13; k < kPart; k++) a.partials[tile * kPart + k] = 0.0;
     int fl = __reduce_or_sync(0xffffffffu, flags);
     if (lane == 0) {
         a.amb_count[tile] = __popc(bal);

@@ -6,7 +6,8 @@ attitudes in one pipeline per integrator stage.  Each trajectory's result must
 equal srp_propagate's for that trajectory alone, bit for bit (the same kernels
 and per-slot sums; the batch only changes which slot a trajectory sits in),
 including after the batch compacts its finished trajectories away.  The tile
-shape changes neither hit decisions nor forces beyond the order of FP64 sums.
+shape changes no hit decision; forces change only by the rounding of the
+32-ray FP32 tile sums (at most 31 x 2^-24 ~ 2e-6 relative).
 """
 import math
 
@@ -120,8 +121,8 @@ def test_autotune_and_tile_shapes_keep_decisions():
             assert np.array_equal(H, ref[2]), tw
             for k in range(len(dirs)):
                 fn = np.linalg.norm(ref[0][k])
-                assert np.linalg.norm(F[k] - ref[0][k]) <= 1e-12 * fn, (tw, k)
-                assert np.linalg.norm(T[k] - ref[1][k]) <= 1e-12 * max(np.linalg.norm(ref[1][k]), fn), (tw, k)
+                assert np.linalg.norm(F[k] - ref[0][k]) <= 2e-6 * fn, (tw, k)
+                assert np.linalg.norm(T[k] - ref[1][k]) <= 2e-6 * max(np.linalg.norm(ref[1][k]), fn), (tw, k)
         # and against the oracle for one direction, with the narrowest tiles
         ctx.set_tile_shape(mid, 100, 2, 4)
         F, T, H = ctx.eval_batch(mid, dirs[:1], N=100, bounces=2, hits=True)
