@@ -38,6 +38,9 @@ METRIC = "SRP evals/s (200k-triangle spacecraft, 1024^2 rays, 2 specular bounces
 #   + 3 sub (edge functions) + 6 compare + 2 add (det) + 3 mul + 3 FMA (depth)
 #   + 1 div + 2 compare = 50
 FLOP_BOX, FLOP_TRI = 23, 50
+# DRAM bytes (read + write) of one k_trace launch of this workload (2 evaluations),
+# from one ncu capture of the current kernel
+TRACE_DRAM_BYTES_PER_LAUNCH = 36.791296e6 + 30.918144e6
 # FP32 peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -462,7 +465,9 @@ def run_native(a):
         "phases_ms_per_step": {"geometry": ms_geom / a.steps, "trace": ms_trace / a.steps,
                                "refine": ms_refine / a.steps, "reduce": ms_reduce / a.steps},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
+                     "frac": achieved / PEAK_FP32_TFLOPS, "traffic": TRACE_DRAM_BYTES_PER_LAUNCH,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one k_trace launch of 2 "
+                                       "evaluations of this workload (profiles/launches_spacecraft200k_N1024_b2.md)",
                      "kernel": "k_trace", "ms_per_launch": ms_per_launch, "evals_per_launch": evals_per_launch,
                      "flop_per_eval": flop_per_eval,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},

@@ -130,7 +130,8 @@ typedef struct {
      * (Sec. 8.2, Eq. 4): */
     double ms_geometry;       /* joint angles, posing, window, refit                     */
     double ms_trace;          /* FP32 first-hit traversal, shading, bounces              */
-    double ms_refine;         /* FP64 re-trace of rays near an FP32 decision bound       */
+    double ms_refine;         /* 0: the FP64 settling runs inside the trace and the rare FP64
+                                 re-trace inside the reduction (kept for layout)           */
     double ms_reduce;         /* fixed-order FP64 reduction to force / torque            */
     double ms_transfer;       /* host <-> device copies made by the call                 */
 } srp_eval_stats;

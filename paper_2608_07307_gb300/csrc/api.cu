@@ -44,8 +44,6 @@ struct srp_ctx {
     size_t pose_cap = 0;
     double *partials = nullptr;
     size_t partials_cap = 0;
-    double *partials_ref = nullptr;
-    size_t partials_ref_cap = 0;
     int *amb_list = nullptr;
     size_t amb_list_cap = 0;
     double *partials1 = nullptr;
@@ -214,7 +212,7 @@ srp_status check_eval_params(srp_ctx *ctx, const srp_eval_params *prm)
 
 // Launch shape of a batch of n evaluations.
 struct EvalPlan {
-    int N, nseg, S, nchunks, lanes, nbx, nbr, tw;
+    int N, nseg, S, nchunks, lanes, nbx, tw;
     size_t R, SL;
     int nba = 0, wa = 0;  // adjoint: ray blocks per slot, doubles per block partial
 };
@@ -333,13 +331,10 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     pl.tw = tuned_tile_w(ctx, m, pl.N, pl.nseg);
     int tiles_x = 0;
     tile_grid(pl.N, pl.tw, tiles_x, pl.nbx);
-    // FP64 re-trace grid: a few blocks per slot (the hand-offs are rare)
-    pl.nbr = std::max(1, std::min(8, 152 / pl.S));
     pl.SL = (size_t)pl.S * pl.lanes;
     const size_t SL = pl.SL;
     CK(ctx, grow(&ctx->pose, &ctx->pose_cap, SL, false));
     CK(ctx, grow(&ctx->partials, &ctx->partials_cap, SL * pl.nbx * kPart, false));
-    CK(ctx, grow(&ctx->partials_ref, &ctx->partials_ref_cap, SL * pl.nbr * kPart, false));
     CK(ctx, grow(&ctx->amb_list, &ctx->amb_list_cap, SL * pl.nbx * kTileRays, false));
     CK(ctx, grow(&ctx->partials1, &ctx->partials1_cap, SL * kRed1 * kPart, false));
     CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
@@ -380,7 +375,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
                         const AdjBatch *adj = nullptr)
 {
     cudaStream_t st = ctx->stream;
-    const int S = pl.S, nbx = pl.nbx, nbr = pl.nbr, nseg = pl.nseg;
+    const int S = pl.S, nbx = pl.nbx, nseg = pl.nseg;
     const size_t R = pl.R;
     CK(ctx, cudaEventRecord(ctx->ev_fork, st));
     for (int b = 0; b < pl.lanes; b++) CK(ctx, cudaStreamWaitEvent(ctx->lane[b], ctx->ev_fork, 0));
@@ -402,11 +397,9 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         a.seg_stride = nseg;
         a.eps_rel = prm->eps_rel;
         a.n_blocks_x = nbx;
-        a.n_blocks_ref = nbr;
         a.partials = ctx->partials + s0 * nbx * kPart;
         a.partials1 = ctx->partials1 + s0 * kRed1 * kPart;
         a.tctx = ctx->tctx + s0 * trace_ctx_bytes();
-        a.partials_ref = ctx->partials_ref + s0 * nbr * kPart;
         a.amb_list = ctx->amb_list + s0 * nbx * kTileRays;
         a.amb_count = ctx->amb_count + s0 * nbx;
         a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
@@ -423,11 +416,10 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         int g1 = tm.mark(ls);
         CK(ctx, launch_trace(a, Sc, ls));
         int g2 = tm.mark(ls);
-        CK(ctx, launch_refine(a, Sc, ls));
-        int g3 = tm.mark(ls);
+        int g3 = g2;  // the FP64 re-trace of overflowing rays runs inside the first reduction level
         CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
         int g4 = tm.mark(ls);
-        launches += 6;  // frame, trace, hand-off scan, refine, two reduction levels
+        launches += 4;  // frame, trace, two reduction levels
         trace_launches++;
         if (adj) {
             AdjArgs g{};
@@ -631,7 +623,6 @@ void srp_destroy(srp_ctx *ctx)
     for (Mesh *m : ctx->meshes) free_mesh(m);
     cudaFree(ctx->pose);
     cudaFree(ctx->partials);
-    cudaFree(ctx->partials_ref);
     cudaFree(ctx->amb_list);
     cudaFree(ctx->partials1);
     cudaFree(ctx->tctx);
@@ -1553,14 +1544,13 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         ntri += (size_t)h.n_dyn_tris * 3;
         nnode += (size_t)h.n_dyn_nodes;
     }
-    const int nbr = std::max(1, std::min(8, 152 / n));
     double *v64, *vv64, *io, *ang, *cfg;
     float4 *vview, *trec, *nodes;
     unsigned *cnt;
     float *rbox;
     SlotPose *pose;
     unsigned char *tctx;
-    double *part, *part1, *partr;
+    double *part, *part1;
     int *alist, *acount;
     SlotDesc *sd;
     PropState *S;
@@ -1578,7 +1568,6 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &tctx, (size_t)n * trace_ctx_bytes()));
     CK(ctx, dmalloc(owned, &part, (size_t)n * nbx * kPart));
     CK(ctx, dmalloc(owned, &part1, (size_t)n * kRed1 * kPart));
-    CK(ctx, dmalloc(owned, &partr, (size_t)n * nbr * kPart));
     CK(ctx, dmalloc(owned, &alist, (size_t)n * nbx * kTileRays));
     CK(ctx, dmalloc(owned, &acount, (size_t)n * nbx));
     CK(ctx, dmalloc(owned, &sd, (size_t)n));
@@ -1679,8 +1668,6 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         a.n_blocks_x = nbx;
         a.partials = part;
         a.partials1 = part1;
-        a.partials_ref = partr;
-        a.n_blocks_ref = nbr;
         a.amb_list = alist;
         a.amb_count = acount;
         cudaGraph_t graph = nullptr;
@@ -1693,7 +1680,6 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
                 if (e == cudaSuccess) e = launch_vertices(sd, pose, na, mv, st);
                 if (e == cudaSuccess) e = launch_refit(sd, pose, na, md, st);
                 if (e == cudaSuccess) e = launch_trace(a, na, st);
-                if (e == cudaSuccess) e = launch_refine(a, na, st);
                 if (e == cudaSuccess) e = launch_reduce(a, na, 0, d_f, d_t, ctx->err_flags, nullptr, st);
             }
             if (e == cudaSuccess) e = launch_prop_accel(S, na, P, sg, d_f, st);
@@ -1718,7 +1704,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     srp_status rc = capture(na);
     if (rc) return rc;
     const int poll_max = p->poll > 0 ? p->poll : 16;
-    const int per_step = nstage * (p->srp ? 12 : 2) + 1;
+    const int per_step = nstage * (p->srp ? 10 : 2) + 1;
     for (int64_t round = 0; round < p->max_steps + 2 && na > 0; round++) {
         int done = 0;
         CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -147,8 +147,6 @@ struct TraceArgs {
     int n_blocks_x;              // stride of the per-tile arrays: the largest tile count of a slot
     double *partials;            // [S][n_blocks_x][kPart] one partial per tile
     double *partials1;           // [S][kRed1][kPart] first-level sums of the tile partials
-    double *partials_ref;        // [S][n_blocks_ref][kPart]
-    int n_blocks_ref;
     int *amb_list;               // [S][n_blocks_x][kTileRays] rays handed to the FP64 path, per tile
     int *amb_count;              // [S][n_blocks_x]
     int32_t *hits;               // [S][ray_stride][seg_stride] or null
@@ -239,7 +237,6 @@ cudaError_t launch_refit_static(const MeshDev *mesh_d, const MeshDev &mh, float4
 
 // trace.cu
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st);
-cudaError_t launch_refine(const TraceArgs &a, int S, cudaStream_t st);
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
                           unsigned long long *stats_accum, cudaStream_t st);
 

@@ -36,15 +36,15 @@
 // again in FP64 against the exact ray of the segment (rare: ~0.5% of the rays
 // of a 200k-triangle mesh at 1024^2).
 //
-// k_refine (FP64 path).  A ray whose uncertain triangles overflow the
+// FP64 re-trace (in k_reduce1).  A ray whose uncertain triangles overflow the
 // candidate list is re-traced from its pixel definition with FP64 rays and
 // vertices, the same BVH (boxes padded well beyond the FP32 rounding of the
 // ray; leaves pre-tested in FP32 with a bound, so only triangles not certainly
 // missed are tested in FP64) and the same watertight test in FP64.
 //
 // k_reduce1 + k_reduce.  Fixed-order FP64 sums: contiguous ranges of tile
-// partials per first-level block, then those and the refine partials per
-// evaluation, scaled by P0 / dist^2 times the pixel area.  No atomics on data:
+// partials (and the re-traced rays of those tiles) per first-level block, then
+// those per evaluation, scaled by P0 / dist^2 times the pixel area.  No atomics on data:
 // results are bit-reproducible for a given launch shape.
 #include <math.h>
 #include <stddef.h>
@@ -848,45 +848,12 @@ __device__ void refine_ray(const TraceCtx &B, const TraceArgs &a, int s, int ray
     acc[7] += (double)nseg_done;
 }
 
-// Rays the trace could not settle (a walk bound, or more uncertain triangles
-// than the candidate list holds; rare) are re-traced here.  Each thread walks
-// a fixed, strided set of its slot's tiles and re-traces the listed rays of
-// each in order, so the sums are reproducible; a small grid, because the work
-// is almost always empty and a large one would take SM resources the trace
-// launches of the other lanes need.
-__global__ void __launch_bounds__(256) k_refine(TraceArgs a)
-{
-    __shared__ TraceCtx B;
-    __shared__ int blk_flags;
-    const int s = blockIdx.y;
-    const int nt = a.sd[s].tiles;
-    double acc[kPart];
-    for (int k = 0; k < kPart; k++) acc[k] = 0.0;
-    if (!a.pose[s].skip) {
-        if (threadIdx.x == 0) blk_flags = 0;
-        load_ctx(B, a, s);
-        __syncthreads();
-        int flags = 0;
-        const int *cnt = a.amb_count + (size_t)s * a.n_blocks_x;
-        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-            const int c = cnt[t];
-            for (int q = 0; q < c; q++) {
-                int ray = a.amb_list[((size_t)s * a.n_blocks_x + t) * kTileRays + q];
-                refine_ray(B, a, s, ray, acc, flags);
-            }
-        }
-        if (flags) atomicOr(&blk_flags, flags);
-        __syncthreads();
-        if (threadIdx.x == 0 && blk_flags) atomicOr(&a.pose[s].flags, blk_flags);
-    }
-    __shared__ double out[kPart];
-    block_sum(acc, out);
-    if (threadIdx.x < kPart)
-        a.partials_ref[((size_t)s * a.n_blocks_ref + blockIdx.x) * kPart + threadIdx.x] = out[threadIdx.x];
-}
-
 // ------------------------------------------------------------- reduce
-// First level: block b of slot s sums tiles [b * chunk, (b + 1) * chunk).
+// First level: block b of slot s sums tiles [b * chunk, (b + 1) * chunk), and
+// re-traces in FP64 the rays its tiles handed off (a walk bound, or more
+// uncertain triangles than the candidate list holds; rare: the traversal
+// context is loaded only when the block has any).  Each thread takes a fixed,
+// strided set of tiles in order, so the sums are reproducible.
 __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
 {
     const int s = blockIdx.y, b = blockIdx.x;
@@ -894,16 +861,38 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
     const int nt = a.sd[s].tiles;
     const int chunk = (nt + kRed1 - 1) / kRed1;
     const int t0 = b * chunk, t1 = min(t0 + chunk, nt);
+    const size_t base = (size_t)s * a.n_blocks_x;
     double acc[kPart];
     for (int k = 0; k < kPart; k++) acc[k] = 0.0;
-    for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x)
-        for (int k = 0; k < kPart; k++) acc[k] += a.partials[((size_t)s * a.n_blocks_x + t) * kPart + k];
+    int mine = 0;
+    for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
+        const double *pt = a.partials + (base + t) * kPart;
+        // slot 6: the tile's hand-off flags; the re-trace below counts the rays it does
+        for (int k = 0; k < kPart; k++)
+            if (k != 6) acc[k] += pt[k];
+        mine |= a.amb_count[base + t];
+    }
+    __shared__ TraceCtx B;
+    __shared__ int blk_flags;
+    if (__syncthreads_or(mine)) {
+        if (threadIdx.x == 0) blk_flags = 0;
+        load_ctx(B, a, s);
+        __syncthreads();
+        int flags = 0;
+        for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
+            const int c = a.amb_count[base + t];
+            for (int q = 0; q < c; q++) refine_ray(B, a, s, a.amb_list[(base + t) * kTileRays + q], acc, flags);
+        }
+        if (flags) atomicOr(&blk_flags, flags);
+        __syncthreads();
+        if (threadIdx.x == 0 && blk_flags) atomicOr(&a.pose[s].flags, blk_flags);
+    }
     __shared__ double out[kPart];
     block_sum(acc, out);
     if (threadIdx.x < kPart) a.partials1[((size_t)s * kRed1 + b) * kPart + threadIdx.x] = out[threadIdx.x];
 }
 
-// One block per slot: the first-level sums and the refine partials.
+// One block per slot: the first-level sums.
 // stats_accum[16]: 0 evals, 1 rays, 2 refined rays, 3 segments, 4..8 hits per
 // segment, 9 nodes, 10 triangles, 11 box tests, 12..15 hand-offs by cause.
 __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *force, double *torque, int *err_flags,
@@ -917,12 +906,8 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
     }
     double acc[kPart];
     for (int k = 0; k < kPart; k++) acc[k] = 0.0;
-    // slot 6: the trace side counts hand-offs, the refine side the rays it did
     for (int b = threadIdx.x; b < kRed1; b += blockDim.x)
-        for (int k = 0; k < kPart; k++)
-            if (k != 6) acc[k] += a.partials1[((size_t)s * kRed1 + b) * kPart + k];
-    for (int b = threadIdx.x; b < a.n_blocks_ref; b += blockDim.x)
-        for (int k = 0; k < kPart; k++) acc[k] += a.partials_ref[((size_t)s * a.n_blocks_ref + b) * kPart + k];
+        for (int k = 0; k < kPart; k++) acc[k] += a.partials1[((size_t)s * kRed1 + b) * kPart + k];
     __shared__ double red[kPart];
     block_sum(acc, red);
     if (threadIdx.x == 0) {
@@ -956,13 +941,6 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
     if (a.n_tiles <= 0) return cudaGetLastError();
     if (a.count) k_trace<true><<<a.n_tiles, kTileRays, 0, st>>>(a);
     else k_trace<false><<<a.n_tiles, kTileRays, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refine(const TraceArgs &a, int S, cudaStream_t st)
-{
-    dim3 grid(a.n_blocks_ref, S);
-    k_refine<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

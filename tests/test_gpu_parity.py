@@ -205,3 +205,26 @@ def test_closed_form_plate_and_retroreflector(ctx):
     vid = ctx.load_mesh(v)
     F, T = ctx.eval_batch(vid, np.array([[0, 0, 1.0]]), N=64, bounces=1)
     assert np.linalg.norm(F[0] - 2 * P0 * 3.0 * np.array([0, 0, -1.0])) < 1e-6 * 2 * P0 * 3.0
+
+
+def test_candidate_overflow_goes_to_the_fp64_retrace(ctx):
+    """A flat fan of 16 triangles whose hub vertex lies on the centre pixel's
+    ray: that ray's FP32 decision is uncertain for all 16 (more than the
+    candidate list holds), so it is re-traced in FP64.  Every other pixel of the
+    fan is settled in the trace.  All triangles share one plane and material, so
+    the force does not depend on which of them the hub ray is given to."""
+    k = 16
+    ang = np.arange(k) * 2 * math.pi / k
+    verts = np.concatenate([[[0.0, 0.0, 0.0]], np.stack([np.cos(ang), np.sin(ang), np.zeros(k)], 1)])
+    tri = np.array([[0, 1 + i, 1 + (i + 1) % k] for i in range(k)], np.int32)
+    from paper_2608_07307_gb300 import inputs as In
+    m = In.Mesh(verts, tri, np.zeros(k, np.int32), np.zeros((k, 2), np.int32), np.array([[0.3, 0.2]]),
+                **In._parts(1, [-1]), name="fan")
+    mid = ctx.load_mesh(m)
+    s = np.array([[0.0, 0.0, 1.0]])
+    N = 63
+    F, T = ctx.eval_batch(mid, s, N=N, bounces=1)
+    st = ctx.eval_stats()
+    assert st["refined"] >= 1, st
+    r = O.evaluate(m, s[0], N, 1)
+    check_force(F, T, r["F"][None], r["T"][None])
