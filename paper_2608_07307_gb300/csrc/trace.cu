@@ -307,11 +307,24 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
     unsigned n_nodes = 0, n_tris = 0, n_boxes = 0;
     bool clean = true;
     const float u4 = 4.0f * kU;
+    // parts in the order the ray enters their root boxes: a near hit then culls
+    // the parts behind it at their root
+    float te[kMaxParts];
+    int po[kMaxParts], np = 0;
     for (int p = 0; p < B.n_parts; p++) {
         const PartView &pv = B.part[p];
-        if (box_enter(pv.box[0], pv.box[3], pv.box[1], pv.box[4], pv.box[2], pv.box[5], r.inv, r.oi, tlo - tau,
-                      best.t + tau) == INFINITY)
-            continue;
+        float t = box_enter(pv.box[0], pv.box[3], pv.box[1], pv.box[4], pv.box[2], pv.box[5], r.inv, r.oi, tlo - tau,
+                            INFINITY);
+        if (t == INFINITY) continue;
+        int k = np++;
+        while (k > 0 && te[k - 1] > t) { te[k] = te[k - 1]; po[k] = po[k - 1]; k--; }
+        te[k] = t;
+        po[k] = p;
+    }
+    for (int q = 0; q < np; q++) {
+        if (te[q] > best.t + tau) break;  // this part and every later one start beyond the best hit
+        const int p = po[q];
+        const PartView &pv = B.part[p];
         int sp = 0, iters = 0;
         int ref = pv.root;
         while (true) {
