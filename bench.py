@@ -40,7 +40,7 @@ METRIC = "SRP evals/s (200k-triangle spacecraft, 1024^2 rays, 2 specular bounces
 FLOP_BOX, FLOP_TRI = 23, 50
 # DRAM bytes (read + write) of one k_trace launch of this workload (2 evaluations),
 # from one ncu capture of the current kernel
-TRACE_DRAM_BYTES_PER_LAUNCH = 36.791296e6 + 30.918144e6
+TRACE_DRAM_BYTES_PER_LAUNCH = 36.82688e6 + 99.849984e6
 # FP32 peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <string>
 #include <tuple>
@@ -23,7 +24,7 @@ struct Mesh {
     MeshDev h{};                 // host copy holding device pointers
     MeshDev *d = nullptr;        // device copy
     std::vector<void *> allocs;  // device allocations owned by the mesh
-    int4 *node_refs_dyn = nullptr;
+    float4 *node_tmpl_dyn = nullptr;  // 4-wide nodes of the dynamic parts: refs, meta, empty boxes
     double *angles_d = nullptr;  // commanded angles / offsets [n_parts]
     double mass = 0.0;
     int slots = 0;
@@ -178,18 +179,111 @@ srp_status ensure_slots(srp_ctx *ctx, Mesh *m, int S)
     CK(ctx, dmalloc(m->slot_allocs, &b.vview, (size_t)S * h.n_verts));
     CK(ctx, dmalloc(m->slot_allocs, &b.vview64, (size_t)S * h.n_verts * 3));
     CK(ctx, dmalloc(m->slot_allocs, &b.tri, (size_t)S * h.n_dyn_tris * 3));
-    CK(ctx, dmalloc(m->slot_allocs, &b.node, (size_t)S * h.n_dyn_nodes * 4));
+    CK(ctx, dmalloc(m->slot_allocs, &b.node, (size_t)S * h.n_dyn_nodes * kNode4));
     CK(ctx, dmalloc(m->slot_allocs, &b.counter, (size_t)S * h.n_dyn_nodes));
     CK(ctx, dmalloc(m->slot_allocs, &b.root_box, (size_t)S * kMaxParts * 6));
     CK(ctx, cudaMemset(b.counter, 0, sizeof(unsigned) * std::max<size_t>((size_t)S * h.n_dyn_nodes, 1)));
     CK(ctx, cudaMemset(b.root_box, 0, sizeof(float) * (size_t)S * kMaxParts * 6));
     for (int s = 0; s < S && h.n_dyn_nodes > 0; s++) {
-        // child refs of the dynamic nodes, the fourth float4 of every node
-        CK(ctx, cudaMemcpy2D(b.node + (size_t)s * h.n_dyn_nodes * 4 + 3, 4 * sizeof(float4), m->node_refs_dyn,
-                             sizeof(int4), sizeof(int4), h.n_dyn_nodes, cudaMemcpyDeviceToDevice));
+        // child refs, links and empty boxes of the dynamic nodes (the refit fills the used boxes)
+        CK(ctx, cudaMemcpy(b.node + (size_t)s * h.n_dyn_nodes * kNode4, m->node_tmpl_dyn,
+                           sizeof(float4) * kNode4 * h.n_dyn_nodes, cudaMemcpyDeviceToDevice));
     }
     m->slots = S;
     return SRP_OK;
+}
+
+// Collapse one part's binary radix tree (part-local refs: x, y children, >= 0
+// internal, < 0 ~leaf) into 4-wide nodes appended to tmpl (kNode4 float4 each:
+// empty child boxes, child refs, (parent, slot, children, 0)).  A node takes
+// its binary node's two children and keeps splitting the internal child whose
+// rest-pose box has the largest surface area until it holds four.  lp4 gets
+// (node << 2) | slot of every leaf.  Returns the depth of the 4-wide tree.
+int collapse_part(const int4 *br, int tc, int tb, const std::vector<int> &svidx, const std::vector<double> &rest,
+                  std::vector<float4> &tmpl, int *lp4)
+{
+    if (tc < 2) return 0;
+    const int nbin = tc - 1;
+    const double inf = std::numeric_limits<double>::infinity();
+    std::vector<double> bx(6 * (size_t)nbin);
+    std::vector<float> area(nbin, 0.f);
+    auto child_box = [&](int ref, double *b) {
+        if (ref >= 0) {
+            for (int k = 0; k < 6; k++) b[k] = bx[6 * (size_t)ref + k];
+            return;
+        }
+        for (int k = 0; k < 3; k++) { b[k] = inf; b[3 + k] = -inf; }
+        for (int c = 0; c < 3; c++) {
+            const double *x = &rest[3 * (size_t)svidx[3 * (size_t)(tb + ~ref) + c]];
+            for (int k = 0; k < 3; k++) { b[k] = std::min(b[k], x[k]); b[3 + k] = std::max(b[3 + k], x[k]); }
+        }
+    };
+    // rest-pose boxes of the binary nodes, children before parents
+    std::vector<std::pair<int, int>> stk;
+    stk.push_back({0, 0});
+    while (!stk.empty()) {
+        const int n = stk.back().first, state = stk.back().second;
+        if (state < 2) {
+            stk.back().second = state + 1;
+            const int c = state == 0 ? br[n].x : br[n].y;
+            if (c >= 0) stk.push_back({c, 0});
+            continue;
+        }
+        double a[6], b[6];
+        child_box(br[n].x, a);
+        child_box(br[n].y, b);
+        for (int k = 0; k < 3; k++) {
+            bx[6 * (size_t)n + k] = std::min(a[k], b[k]);
+            bx[6 * (size_t)n + 3 + k] = std::max(a[3 + k], b[3 + k]);
+        }
+        const double dx = bx[6 * (size_t)n + 3] - bx[6 * (size_t)n], dy = bx[6 * (size_t)n + 4] - bx[6 * (size_t)n + 1],
+                     dz = bx[6 * (size_t)n + 5] - bx[6 * (size_t)n + 2];
+        area[n] = (float)(2.0 * (dx * dy + dy * dz + dz * dx));
+        stk.pop_back();
+    }
+    const int base = (int)(tmpl.size() / kNode4);
+    const float finf = std::numeric_limits<float>::infinity();
+    struct Item { int bin, parent, slot, depth; };
+    std::vector<Item> todo{{0, -1, 0, 1}};
+    int maxd = 0;
+    while (!todo.empty()) {
+        const Item it = todo.back();
+        todo.pop_back();
+        const int me = (int)(tmpl.size() / kNode4) - base;
+        int ch[4] = {br[it.bin].x, br[it.bin].y, kEmptyChild, kEmptyChild};
+        int n = 2;
+        while (n < 4) {
+            int best = -1;
+            float ba = -1.f;
+            for (int k = 0; k < n; k++)
+                if (ch[k] >= 0 && area[ch[k]] > ba) { ba = area[ch[k]]; best = k; }
+            if (best < 0) break;
+            const int c = ch[best];
+            for (int k = n; k > best + 1; k--) ch[k] = ch[k - 1];
+            ch[best] = br[c].x;
+            ch[best + 1] = br[c].y;
+            n++;
+        }
+        tmpl.resize(tmpl.size() + kNode4);
+        float4 *nd = &tmpl[tmpl.size() - kNode4];
+        for (int k = 0; k < 6; k++) {
+            const float v = (k % 2 == 0) ? finf : -finf;  // lo.x hi.x lo.y hi.y lo.z hi.z: empty
+            nd[k] = make_float4(v, v, v, v);
+        }
+        int4 refs = make_int4(ch[0], ch[1], ch[2], ch[3]), meta = make_int4(it.parent, it.slot, n, 0);
+        memcpy(&nd[6], &refs, sizeof refs);
+        memcpy(&nd[7], &meta, sizeof meta);
+        if (it.parent >= 0) {
+            int *pr = reinterpret_cast<int *>(&tmpl[(size_t)(base + it.parent) * kNode4 + 6]);
+            pr[it.slot] = me;
+        }
+        for (int k = 0; k < n; k++) {
+            if (ch[k] < 0) lp4[~ch[k]] = (me << 2) | k;
+            else todo.push_back({ch[k], me, k, it.depth + 1});
+        }
+        maxd = std::max(maxd, it.depth);
+    }
+    return maxd;
 }
 
 Mesh *get_mesh(srp_ctx *ctx, int32_t id)
@@ -286,7 +380,7 @@ SlotBufs slot_bufs(const MeshDev &h, const SlotBufs &base, size_t k)
     b.vview += k * h.n_verts;
     b.vview64 += k * h.n_verts * 3;
     b.tri += k * h.n_dyn_tris * 3;
-    b.node += k * h.n_dyn_nodes * 4;
+    b.node += k * h.n_dyn_nodes * kNode4;
     b.counter += k * h.n_dyn_nodes;
     b.root_box += k * kMaxParts * 6;
     return b;
@@ -731,6 +825,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     std::vector<double> rest;
     std::vector<int> vert_part;
     int nv = 0, tb = 0, nb = 0;
+    std::vector<int> bin_begin(NP, 0);
     double rmax = 0.0, piv = 0.0;
     for (int r = 0; r < NP; r++) {
         int p = order[r];
@@ -758,19 +853,17 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
         pi.tri_begin = tb;
         pi.tri_count = (int)ptris[p].size();
         tb += pi.tri_count;
-        pi.node_begin = nb;
+        bin_begin[p] = nb;  // binary radix tree nodes of the part (collapsed to 4-wide after the build)
         nb += std::max(pi.tri_count - 1, 0);
         if (movable[p]) piv += std::sqrt(pi.pivot[0] * pi.pivot[0] + pi.pivot[1] * pi.pivot[1] + pi.pivot[2] * pi.pivot[2]);
-        if (!dynamic[p]) { h.n_static_tris = tb; h.n_static_nodes = nb; h.n_static_verts = nv; }
+        if (!dynamic[p]) { h.n_static_tris = tb; h.n_static_verts = nv; }
     }
     h.n_verts = nv;
     h.n_dyn_tris = NT - h.n_static_tris;
-    h.n_dyn_nodes = nb - h.n_static_nodes;
     h.n_dyn_verts = nv - h.n_static_verts;
     for (int p = 0; p < NP; p++) {
         PartInfo &pi = h.part[p];
         pi.dyn_tri_off = pi.dynamic ? pi.tri_begin - h.n_static_tris : 0;
-        pi.dyn_node_off = pi.dynamic ? pi.node_begin - h.n_static_nodes : 0;
         pi.dyn_vert_off = pi.dynamic ? pi.vert_begin - h.n_static_verts : 0;
         h.part_order[rank[p]] = p;
     }
@@ -823,11 +916,10 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     MK(dmalloc(m->allocs, &h.tri_mat, (size_t)NT));
     MK(dmalloc(m->allocs, &h.leaf_parent, (size_t)NT));
     MK(dmalloc(m->allocs, &h.tri_static, (size_t)std::max(h.n_static_tris, 1) * 3));
-    MK(dmalloc(m->allocs, &h.node_static, (size_t)std::max(h.n_static_nodes, 1) * 4));
     MK(dmalloc(m->allocs, &h.mat32, (size_t)NM));
     MK(dmalloc(m->allocs, &h.mat64, (size_t)NM * 2));
     MK(dmalloc(m->allocs, &m->angles_d, (size_t)NP));
-    MK(dmalloc(m->allocs, &node_refs, (size_t)std::max(nb, 1)));
+    MK(dmalloc(tmp, &node_refs, (size_t)std::max(nb, 1)));
     MK(dmalloc(tmp, &d_tvidx0, (size_t)NT * 3));
     MK(dmalloc(tmp, &d_tpart, (size_t)NT));
     MK(dmalloc(tmp, &d_rank, (size_t)NP));
@@ -844,7 +936,6 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     MK(dmalloc(tmp, &d_nodepart, (size_t)std::max(nb, 1)));
     MK(dmalloc(tmp, &d_nodebase, (size_t)std::max(nb, 1)));
     MK(dmalloc(tmp, &d_depth, 1));
-    MK(dmalloc(tmp, &cnt_static, (size_t)std::max(h.n_static_nodes, 1)));
     MK(cudaMemcpyAsync(h.rest64, rest.data(), sizeof(double) * rest.size(), cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(h.vert_part, vert_part.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(d_tvidx0, tvidx.data(), sizeof(int) * tvidx.size(), cudaMemcpyHostToDevice, st));
@@ -887,7 +978,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     for (int p = 0; p < NP; p++) {
         ptb[p] = h.part[p].tri_begin;
         ptc[p] = h.part[p].tri_count;
-        pnb[p] = h.part[p].node_begin;
+        pnb[p] = bin_begin[p];
         for (int g = pnb[p]; g < pnb[p] + std::max(ptc[p] - 1, 0); g++) { nodepart[g] = p; nodebase[g] = pnb[p]; }
     }
     std::vector<int4> refs0(std::max(nb, 1), make_int4(0, 0, -1, 0));
@@ -911,11 +1002,47 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
         free_mesh(m);
         return fail(ctx, SRP_ERR_MESH, "BVH depth %d exceeds the traversal stack (%d)", depth, kStack);
     }
-    // static nodes: child refs into the fourth float4; dynamic refs kept for the slots
-    if (h.n_static_nodes > 0)
-        MK(cudaMemcpy2DAsync(h.node_static + 3, 4 * sizeof(float4), node_refs, sizeof(int4), sizeof(int4),
-                             h.n_static_nodes, cudaMemcpyDeviceToDevice, st));
-    m->node_refs_dyn = node_refs + h.n_static_nodes;
+    // collapse every part's binary tree into 4-wide nodes (host, O(n)); the
+    // refit fills the boxes (static parts below, dynamic parts per evaluation)
+    {
+        std::vector<int4> brefs(std::max(nb, 1));
+        MK(cudaMemcpy(brefs.data(), node_refs, sizeof(int4) * std::max(nb, 1), cudaMemcpyDeviceToHost));
+        std::vector<int> lp4(NT, -1);
+        std::vector<float4> tmpl;
+        int n4 = 0, depth4 = 0;
+        for (int r = 0; r < NP; r++) {
+            const int p = order[r];
+            PartInfo &pi = h.part[p];
+            pi.node_begin = n4;
+            int d4 = collapse_part(brefs.data() + bin_begin[p], pi.tri_count, pi.tri_begin, svidx, rest, tmpl,
+                                   lp4.data() + pi.tri_begin);
+            pi.node_count = (int)(tmpl.size() / kNode4) - n4;
+            n4 += pi.node_count;
+            depth4 = std::max(depth4, d4);
+            if (!pi.dynamic) h.n_static_nodes = n4;
+        }
+        h.n_dyn_nodes = n4 - h.n_static_nodes;
+        for (int p = 0; p < NP; p++) {
+            PartInfo &pi = h.part[p];
+            pi.dyn_node_off = pi.dynamic ? pi.node_begin - h.n_static_nodes : 0;
+        }
+        if (3 * depth4 + 1 > kStack) {
+            free_tmp();
+            free_mesh(m);
+            return fail(ctx, SRP_ERR_MESH, "4-wide BVH depth %d exceeds the traversal stack (%d)", depth4, kStack);
+        }
+        MK(cudaMemcpyAsync(h.leaf_parent, lp4.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
+        MK(dmalloc(m->allocs, &h.node_static, (size_t)std::max(h.n_static_nodes, 1) * kNode4));
+        MK(dmalloc(m->allocs, &m->node_tmpl_dyn, (size_t)std::max(h.n_dyn_nodes, 1) * kNode4));
+        MK(dmalloc(tmp, &cnt_static, (size_t)std::max(h.n_static_nodes, 1)));
+        if (h.n_static_nodes > 0)
+            MK(cudaMemcpyAsync(h.node_static, tmpl.data(), sizeof(float4) * kNode4 * h.n_static_nodes,
+                               cudaMemcpyHostToDevice, st));
+        if (h.n_dyn_nodes > 0)
+            MK(cudaMemcpyAsync(m->node_tmpl_dyn, tmpl.data() + (size_t)kNode4 * h.n_static_nodes,
+                               sizeof(float4) * kNode4 * h.n_dyn_nodes, cudaMemcpyHostToDevice, st));
+        MK(cudaStreamSynchronize(st));  // tmpl and lp4 leave scope
+    }
     // materials and angles
     std::vector<float2> m32(NM);
     for (int i = 0; i < NM; i++) m32[i] = make_float2((float)D->mat[2 * i], (float)D->mat[2 * i + 1]);
@@ -1558,7 +1685,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &vview, nview));
     CK(ctx, dmalloc(owned, &vv64, nview * 3));
     CK(ctx, dmalloc(owned, &trec, std::max<size_t>(ntri, 1)));
-    CK(ctx, dmalloc(owned, &nodes, std::max<size_t>(nnode * 4, 1)));
+    CK(ctx, dmalloc(owned, &nodes, std::max<size_t>(nnode * kNode4, 1)));
     CK(ctx, dmalloc(owned, &cnt, std::max<size_t>(nnode, 1)));
     CK(ctx, dmalloc(owned, &rbox, (size_t)n * kMaxParts * 6));
     CK(ctx, dmalloc(owned, &io, (size_t)n * 18));
@@ -1589,12 +1716,12 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         d.sb.vview = vview + oview;
         d.sb.vview64 = vv64 + oview * 3;
         d.sb.tri = trec + otri;
-        d.sb.node = nodes + onode * 4;
+        d.sb.node = nodes + onode * kNode4;
         d.sb.counter = cnt + onode;
         d.sb.root_box = rbox + (size_t)i * kMaxParts * 6;
         if (h.n_dyn_nodes > 0)
-            CK(ctx, cudaMemcpy2DAsync(d.sb.node + 3, 4 * sizeof(float4), m->node_refs_dyn, sizeof(int4), sizeof(int4),
-                                      h.n_dyn_nodes, cudaMemcpyDeviceToDevice, st));
+            CK(ctx, cudaMemcpyAsync(d.sb.node, m->node_tmpl_dyn, sizeof(float4) * kNode4 * h.n_dyn_nodes,
+                                    cudaMemcpyDeviceToDevice, st));
         o64 += (size_t)h.n_dyn_verts * 3;
         oview += h.n_verts;
         otri += (size_t)h.n_dyn_tris * 3;

@@ -186,33 +186,6 @@ cudaError_t launch_vertices(const SlotDesc *sd, SlotPose *pose, int S, int max_v
 }
 
 // ---------------------------------------------------------------- refit
-__device__ inline void store_child_box(float4 *node, int which, const float *b)
-{
-    // child 0: a = (lo.x hi.x lo.y hi.y), b.xy = (lo.z hi.z); child 1: b.zw = (lo.x hi.x), c = (lo.y hi.y lo.z hi.z)
-    float *f = reinterpret_cast<float *>(node);
-    if (which == 0) {
-        *reinterpret_cast<float4 *>(f) = make_float4(b[0], b[3], b[1], b[4]);
-        *reinterpret_cast<float2 *>(f + 4) = make_float2(b[2], b[5]);
-    } else {
-        *reinterpret_cast<float2 *>(f + 6) = make_float2(b[0], b[3]);
-        *reinterpret_cast<float4 *>(f + 8) = make_float4(b[1], b[4], b[2], b[5]);
-    }
-}
-
-__device__ inline void load_child_box_cg(const float4 *node, int which, float *b)
-{
-    const float *f = reinterpret_cast<const float *>(node);
-    if (which == 0) {
-        float4 x = __ldcg(reinterpret_cast<const float4 *>(f));
-        float2 y = __ldcg(reinterpret_cast<const float2 *>(f + 4));
-        b[0] = x.x; b[3] = x.y; b[1] = x.z; b[4] = x.w; b[2] = y.x; b[5] = y.y;
-    } else {
-        float2 x = __ldcg(reinterpret_cast<const float2 *>(f + 6));
-        float4 y = __ldcg(reinterpret_cast<const float4 *>(f + 8));
-        b[0] = x.x; b[3] = x.y; b[1] = y.x; b[4] = y.y; b[2] = y.z; b[5] = y.w;
-    }
-}
-
 // Thread per sorted triangle: the static parts of one mesh (sd == null, at
 // load) or the dynamic parts of every slot's mesh.
 __global__ void __launch_bounds__(256) k_refit(const SlotDesc *sd, const SlotPose *pose, const MeshDev *static_mesh,
@@ -243,12 +216,12 @@ __global__ void __launch_bounds__(256) k_refit(const SlotDesc *sd, const SlotPos
     float *root;
     int tl = t - pi.tri_begin;
     if (dyn) {
-        nodes = slot.node + (size_t)pi.dyn_node_off * 4;
+        nodes = slot.node + (size_t)pi.dyn_node_off * kNode4;
         tris = slot.tri + (size_t)pi.dyn_tri_off * 3;
         cnt = slot.counter + pi.dyn_node_off;
         root = slot.root_box + (size_t)p * 6;
     } else {
-        nodes = node_static + (size_t)pi.node_begin * 4;
+        nodes = node_static + (size_t)pi.node_begin * kNode4;
         tris = tri_static + (size_t)pi.tri_begin * 3;
         cnt = counter_static + pi.node_begin;
         root = root_static + p * 6;
@@ -274,26 +247,36 @@ __global__ void __launch_bounds__(256) k_refit(const SlotDesc *sd, const SlotPos
         box[k] = fminf(fminf(v[0][k], v[1][k]), v[2][k]) - pad;
         box[3 + k] = fmaxf(fmaxf(v[0][k], v[1][k]), v[2][k]) + pad;
     }
-    int child = ~tl;
-    int node = mesh->leaf_parent[t];
-    for (int guard = 0; node >= 0; guard++) {
+    // walk up the 4-wide tree: every child stores its box in its slot of the
+    // parent; the last of the parent's children to arrive forms the parent's
+    // box and resets the counter for the next refit
+    int up = mesh->leaf_parent[t];  // (node << 2) | slot, or -1 for a one-triangle part
+    for (int guard = 0; up >= 0; guard++) {
         if (guard > kStack + 4) return;  // cannot happen for a tree that passed the depth check
-        float4 *nd = nodes + (size_t)node * 4;
-        int4 refs = *reinterpret_cast<const int4 *>(nd + 3);
-        int which = (refs.x == child) ? 0 : 1;
-        store_child_box(nd, which, box);
+        const int node = up >> 2, slot = up & 3;
+        float4 *nd = nodes + (size_t)node * kNode4;
+        float *f = reinterpret_cast<float *>(nd);
+        f[slot] = box[0];
+        f[4 + slot] = box[3];
+        f[8 + slot] = box[1];
+        f[12 + slot] = box[4];
+        f[16 + slot] = box[2];
+        f[20 + slot] = box[5];
+        const int4 meta = *reinterpret_cast<const int4 *>(nd + 7);  // parent, slot in it, children
         __threadfence();
         unsigned old = atomicAdd(cnt + node, 1u);
-        if ((old & 1u) == 0u) return;  // first arrival: the sibling finishes this node
+        if (old + 1u < (unsigned)meta.z) return;  // a sibling still has to arrive
+        cnt[node] = 0u;
         __threadfence();
-        float sib[6];
-        load_child_box_cg(nd, 1 - which, sib);
-        for (int k = 0; k < 3; k++) {
-            box[k] = fminf(box[k], sib[k]);
-            box[3 + k] = fmaxf(box[3 + k], sib[3 + k]);
-        }
-        child = node;
-        node = refs.z;
+        float4 c[6];
+        for (int k = 0; k < 6; k++) c[k] = __ldcg(nd + k);
+        box[0] = fminf(fminf(c[0].x, c[0].y), fminf(c[0].z, c[0].w));
+        box[3] = fmaxf(fmaxf(c[1].x, c[1].y), fmaxf(c[1].z, c[1].w));
+        box[1] = fminf(fminf(c[2].x, c[2].y), fminf(c[2].z, c[2].w));
+        box[4] = fmaxf(fmaxf(c[3].x, c[3].y), fmaxf(c[3].z, c[3].w));
+        box[2] = fminf(fminf(c[4].x, c[4].y), fminf(c[4].z, c[4].w));
+        box[5] = fmaxf(fmaxf(c[5].x, c[5].y), fmaxf(c[5].z, c[5].w));
+        up = meta.x < 0 ? -1 : ((meta.x << 2) | meta.y);
     }
     for (int k = 0; k < 6; k++) root[k] = box[k];
 }

@@ -3,8 +3,10 @@
 // Layout in HBM (one mesh):
 //   * triangles are sorted part-major (static parts first, then parts whose
 //     pose depends on a joint angle), Morton order within a part;
-//   * each part has its own binary LBVH over its triangles: n-1 internal
-//     nodes of 64 B (two child boxes + child refs), leaves are triangles;
+//   * each part has its own LBVH over its triangles, built as a binary radix
+//     tree and collapsed to 4-wide nodes of 128 B (four child boxes as six
+//     float4 in SoA order, four child refs, parent / slot / child count);
+//     leaves are triangles;
 //   * a triangle record is 48 B: three FP32 vertices + original id +
 //     packed front/back material;
 //   * FP64 copies of the vertices (rest pose for static parts, posed per slot
@@ -22,7 +24,9 @@ namespace srp {
 constexpr int kMaxParts = SRP_MAX_PARTS;
 constexpr int kMaxMats = SRP_MAX_MATS;
 constexpr int kMaxBounces = SRP_MAX_BOUNCES;
-constexpr int kStack = 64;          // traversal stack entries (>= tree depth, checked at load)
+constexpr int kStack = 96;          // traversal stack entries (>= 3 x 4-wide tree depth + 1, checked at load)
+constexpr int kNode4 = 8;           // float4 per 4-wide node
+constexpr int kEmptyChild = (int)0x80000000;  // child ref of an unused slot (its box is empty)
 constexpr int kTraceThreads = 256;  // 16 x 16 pixel tile per block
 constexpr int kTile = 16;
 constexpr double kStandoff = 1.0;   // ray origins start 1 m in front of the nearest vertex
@@ -37,13 +41,13 @@ struct PartInfo {
     int dynamic;        // pose depends on some joint angle (itself or an ancestor)
     int tri_begin;      // first sorted triangle of the part (global sorted index)
     int tri_count;
-    int node_begin;     // first internal node of the part within its node array
+    int node_begin;     // first 4-wide node of the part within its node array
     int vert_begin;     // first vertex of the part (global, part-major re-indexed)
     int vert_count;
     int dyn_tri_off;    // offset of the part in the per-slot dynamic arrays (dynamic only)
     int dyn_node_off;
     int dyn_vert_off;
-    int pad_;
+    int node_count;     // 4-wide nodes of the part (0 for a part of fewer than 2 triangles)
     double pivot[3], axis[3], lim[2], n0[3];
 };
 
@@ -89,9 +93,10 @@ struct MeshDev {
     int *tri_orig;         // [n_tris] sorted -> original triangle id
     int *tri_pos;          // [n_tris] original triangle id -> sorted position
     unsigned *tri_mat;     // [n_tris] sorted -> (front | back << 16)
-    int *leaf_parent;      // [n_tris] sorted -> parent internal node (part-local), -1 for a single-leaf part
+    int *leaf_parent;      // [n_tris] sorted -> (parent 4-wide node (part-local) << 2) | slot, -1 for a
+                           // single-leaf part
     float4 *tri_static;    // [n_static_tris][3]
-    float4 *node_static;   // [n_static_nodes][4]
+    float4 *node_static;   // [n_static_nodes][kNode4]
     float2 *mat32;         // [n_mats] (rho_s, rho_d) FP32
     double *mat64;         // [n_mats][2]
     float root_box_static[kMaxParts][6];
@@ -103,8 +108,8 @@ struct SlotBufs {
     float4 *vview;      // [S][n_verts] (u.x, v.x, d.x, 0) of every posed vertex, FP32 rounded from FP64
     double *vview64;    // [S][n_verts][3] the same projections in FP64 (settling uncertain primary decisions)
     float4 *tri;        // [S][n_dyn_tris][3]
-    float4 *node;       // [S][n_dyn_nodes][4]
-    unsigned *counter;  // [S][n_dyn_nodes] refit arrival counters (never reset; parity of the count)
+    float4 *node;       // [S][n_dyn_nodes][kNode4]
+    unsigned *counter;  // [S][n_dyn_nodes] refit arrival counters (the last arrival resets them)
     float *root_box;    // [S][kMaxParts][6]
 };
 

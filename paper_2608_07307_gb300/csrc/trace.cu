@@ -61,7 +61,7 @@ struct PartView {
     const int4 *v4;      // vertex ids of the part's sorted triangles
     const double *v64;   // v64[3 * (vi - vert_begin) + c]
     int root;            // 0, or ~0 for a one-triangle part
-    int limit;           // bound on loop iterations of one part walk (2 n - 1 items)
+    int limit;           // bound on loop iterations of one part walk (nodes + triangles)
     int tri_begin, vert_begin;
     float box[6];
     int pad_[2];
@@ -161,18 +161,18 @@ __global__ void k_frame(TraceArgs a)
         const PartInfo &pi = m->part[p];
         PartView &pv = B.part[p];
         pv.root = pi.tri_count > 1 ? 0 : ~0;
-        pv.limit = 2 * pi.tri_count + 8;
+        pv.limit = pi.node_count + pi.tri_count + 8;
         pv.tri_begin = pi.tri_begin;
         pv.vert_begin = pi.vert_begin;
         pv.v4 = m->tri_v4 + pi.tri_begin;
         if (pi.dynamic) {
-            pv.node = sb.node + (size_t)pi.dyn_node_off * 4;
+            pv.node = sb.node + (size_t)pi.dyn_node_off * kNode4;
             pv.tri = sb.tri + (size_t)pi.dyn_tri_off * 3;
             pv.v64 = sb.vert64 + (size_t)pi.dyn_vert_off * 3;
             const float *rb = sb.root_box + (size_t)p * 6;
             for (int k = 0; k < 6; k++) pv.box[k] = rb[k];
         } else {
-            pv.node = m->node_static + (size_t)pi.node_begin * 4;
+            pv.node = m->node_static + (size_t)pi.node_begin * kNode4;
             pv.tri = m->tri_static + (size_t)pi.tri_begin * 3;
             pv.v64 = m->rest64 + (size_t)pi.vert_begin * 3;
             for (int k = 0; k < 6; k++) pv.box[k] = m->root_box_static[p][k];
@@ -203,10 +203,63 @@ __device__ __forceinline__ float box_enter(float lx, float hx, float ly, float h
     return tn <= tf ? tn : INFINITY;
 }
 
+// Slab test of one box given its near and far plane on each axis (the planes
+// the ray meets first and last): no per-axis ordering needed.
+__device__ __forceinline__ float box_enter_nf(float nx, float fx, float ny, float fy, float nz, float fz,
+                                              const float *inv, const float *oi, float tlo, float thi)
+{
+    float tn = fmaxf(fmaxf(fmaf(nx, inv[0], -oi[0]), fmaf(ny, inv[1], -oi[1])), fmaxf(fmaf(nz, inv[2], -oi[2]), tlo));
+    float tf = fminf(fminf(fmaf(fx, inv[0], -oi[0]), fmaf(fy, inv[1], -oi[1])), fminf(fmaf(fz, inv[2], -oi[2]), thi));
+    return tn <= tf ? tn : INFINITY;
+}
+
+__device__ __forceinline__ void cswap(float &ta, int &ra, float &tb, int &rb)
+{
+    if (tb < ta) {
+        float t = ta; ta = tb; tb = t;
+        int r = ra; ra = rb; rb = r;
+    }
+}
+
+// One 4-wide node: slab tests of its four child boxes (lo.x, hi.x, lo.y, hi.y,
+// lo.z, hi.z in float4 0..5, one lane per child; child refs in float4 6).
+// oct[k] is 1 where the ray runs backwards along axis k: the near plane is then
+// the box's upper bound, so picking the float4 by address replaces the per-axis
+// min/max of the slab test.  An unused slot's box (+inf, -inf) is entered at
+// +inf and never hit.  Continues with the nearest child entered and pushes the
+// others, farthest first.  Returns the number of children entered (0: pop the
+// stack), -1 when the stack would overflow.
+__device__ __forceinline__ int node4_step(const float4 *nd, const float *inv, const float *oi, const int *oct,
+                                          float tlo, float thi, int &ref, int *stack, int &sp)
+{
+    float4 nx = __ldg(nd + oct[0]), fx = __ldg(nd + 1 - oct[0]), ny = __ldg(nd + 2 + oct[1]),
+           fy = __ldg(nd + 3 - oct[1]), nz = __ldg(nd + 4 + oct[2]), fz = __ldg(nd + 5 - oct[2]);
+    int4 c = __ldg(reinterpret_cast<const int4 *>(nd + 6));
+    float ta = box_enter_nf(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, inv, oi, tlo, thi);
+    float tb = box_enter_nf(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, inv, oi, tlo, thi);
+    float tc = box_enter_nf(nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, inv, oi, tlo, thi);
+    float td = box_enter_nf(nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, inv, oi, tlo, thi);
+    int ra = c.x, rb = c.y, rc = c.z, rd = c.w;
+    cswap(ta, ra, tb, rb);
+    cswap(tc, rc, td, rd);
+    cswap(ta, ra, tc, rc);
+    cswap(tb, rb, td, rd);
+    cswap(tb, rb, tc, rc);
+    if (ta == INFINITY) return 0;
+    const int n = 1 + (tb != INFINITY) + (tc != INFINITY) + (td != INFINITY);
+    if (sp + n - 1 > kStack) return -1;
+    if (td != INFINITY) stack[sp++] = rd;
+    if (tc != INFINITY) stack[sp++] = rc;
+    if (tb != INFINITY) stack[sp++] = rb;
+    ref = ra;
+    return n;
+}
+
 struct Ray32 {
     float o[3], d[3], inv[3], oi[3];
     float Sx, Sy, Sz;
     int kx, ky, kz;
+    int oct[3];  // 1 where the direction component is negative
 };
 
 __device__ __forceinline__ void ray_setup(Ray32 &r)
@@ -216,6 +269,7 @@ __device__ __forceinline__ void ray_setup(Ray32 &r)
         float ds = fabsf(dk) < 1e-20f ? copysignf(1e-20f, dk) : dk;
         r.inv[k] = 1.0f / ds;
         r.oi[k] = r.o[k] * r.inv[k];
+        r.oct[k] = r.inv[k] < 0.f ? 1 : 0;
     }
     float ax = fabsf(r.d[0]), ay = fabsf(r.d[1]), az = fabsf(r.d[2]);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
@@ -330,22 +384,11 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
         while (true) {
             if (++iters > pv.limit) { clean = false; cn.flags |= kFlagStack; break; }
             if (ref >= 0) {
-                const float4 *nd = pv.node + (size_t)ref * 4;
-                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
-                int4 c = __ldg(reinterpret_cast<const int4 *>(nd + 3));
-                float th = best.t + tau;
-                float t0 = box_enter(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r.inv, r.oi, tlo - tau, th);
-                float t1 = box_enter(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r.inv, r.oi, tlo - tau, th);
-                if (COUNT) { n_nodes++; n_boxes += 2; }
-                bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
-                if (h0 && h1) {
-                    int nr = t0 <= t1 ? c.x : c.y, fr = t0 <= t1 ? c.y : c.x;
-                    if (sp >= kStack) { clean = false; cn.flags |= kFlagStack; break; }
-                    stack[sp++] = fr;
-                    ref = nr;
-                    continue;
-                } else if (h0) { ref = c.x; continue; }
-                else if (h1) { ref = c.y; continue; }
+                const int n = node4_step(pv.node + (size_t)ref * kNode4, r.inv, r.oi, r.oct, tlo - tau, best.t + tau, ref,
+                                         stack, sp);
+                if (COUNT) { n_nodes++; n_boxes += 4; }
+                if (n < 0) { clean = false; cn.flags |= kFlagStack; break; }
+                if (n > 0) continue;
             } else {
                 int tl = ~ref;
                 if (COUNT) n_tris++;
@@ -756,20 +799,10 @@ __device__ void nearest64(const TraceCtx &B, const Ray64 &r, double tlo, int ski
         while (true) {
             if (++iters > pv.limit) { flags |= kFlagStack; break; }
             if (ref >= 0) {
-                const float4 *nd = pv.node + (size_t)ref * 4;
-                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
-                int4 c = __ldg(reinterpret_cast<const int4 *>(nd + 3));
-                float th = (float)bt + slack;
-                float t0 = box_enter(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, q.inv, q.oi, (float)tlo - slack, th);
-                float t1 = box_enter(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, q.inv, q.oi, (float)tlo - slack, th);
-                bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
-                if (h0 && h1) {
-                    if (sp >= kStack) { flags |= kFlagStack; break; }
-                    stack[sp++] = t0 <= t1 ? c.y : c.x;
-                    ref = t0 <= t1 ? c.x : c.y;
-                    continue;
-                } else if (h0) { ref = c.x; continue; }
-                else if (h1) { ref = c.y; continue; }
+                const int n = node4_step(pv.node + (size_t)ref * kNode4, q.inv, q.oi, q.oct, (float)tlo - slack,
+                                         (float)bt + slack, ref, stack, sp);
+                if (n < 0) { flags |= kFlagStack; break; }
+                if (n > 0) continue;
             } else {
                 int tl = ~ref;
                 const float4 *tr = pv.tri + (size_t)tl * 3;
