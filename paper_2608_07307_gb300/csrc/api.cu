@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libsrp (include/srp.h): validation, device memory,
 // mesh build and the per-batch launch sequence.  No exception crosses the ABI.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -193,17 +194,80 @@ srp_status ensure_slots(srp_ctx *ctx, Mesh *m, int S)
     return SRP_OK;
 }
 
+constexpr int kGroupMin = 64;  // smallest coplanar group given a subtree of its own
+
+// Coplanar groups of one part, rest pose, FP64: triangles whose three vertices
+// lie within 1e-13 of the part's extent of one plane.  Candidates share a
+// quantised plane (unit normal with its largest component positive, offset);
+// each group is then checked against its first triangle's plane.  Writes the
+// group number (1, 2, ...; 0 = none) of each triangle into tgrp and the group's
+// largest vertex deviation (metres) into tdev.  A ray leaving a plane meets no
+// triangle lying in it, so a reflected ray may skip its origin's group.
+void coplanar_groups(const std::vector<int> &tris, const int *tri, const std::vector<double> &xyz, double ext,
+                     std::vector<int> &tgrp, std::vector<double> &tdev)
+{
+    ext = std::max(ext, 1e-300);
+    const double tol = 1e-13 * ext;
+    auto plane = [&](int t, double *n, double &d) {
+        const double *a = &xyz[3 * (size_t)tri[3 * t]], *b = &xyz[3 * (size_t)tri[3 * t + 1]],
+                     *c = &xyz[3 * (size_t)tri[3 * t + 2]];
+        double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        int k = 0;
+        for (int q = 1; q < 3; q++) if (std::fabs(n[q]) > std::fabs(n[k])) k = q;
+        if (n[k] < 0.0) l = -l;
+        for (int q = 0; q < 3; q++) n[q] /= l;
+        d = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
+    };
+    std::map<std::array<long long, 4>, std::vector<int>> bucket;
+    for (int t : tris) {
+        double n[3], d;
+        plane(t, n, d);
+        const double q = 1048576.0;
+        bucket[{std::llround(n[0] * q), std::llround(n[1] * q), std::llround(n[2] * q), std::llround(d / ext * q)}]
+            .push_back(t);
+    }
+    int g = 0;
+    for (auto &kv : bucket) {
+        if ((int)kv.second.size() < kGroupMin || g >= 0xffff) continue;
+        double n[3], d;
+        plane(kv.second[0], n, d);
+        std::vector<int> keep;
+        double dmax = 0.0;
+        for (int t : kv.second) {
+            double e = 0.0;
+            for (int c = 0; c < 3; c++) {
+                const double *v = &xyz[3 * (size_t)tri[3 * t + c]];
+                e = std::max(e, std::fabs(n[0] * v[0] + n[1] * v[1] + n[2] * v[2] - d));
+            }
+            if (e <= tol) { keep.push_back(t); dmax = std::max(dmax, e); }
+        }
+        if ((int)keep.size() < kGroupMin) continue;
+        g++;
+        for (int t : keep) { tgrp[t] = g; tdev[t] = dmax; }
+    }
+}
+
 // Collapse one part's binary radix tree (part-local refs: x, y children, >= 0
 // internal, < 0 ~leaf) into 4-wide nodes appended to tmpl (kNode4 float4 each:
 // empty child boxes, child refs, (parent, slot, children, 0)).  A node takes
 // its binary node's two children and keeps splitting the internal child whose
-// rest-pose box has the largest surface area until it holds four.  lp4 gets
+// rest-pose box has the largest surface area until it holds four.  A binary
+// node whose leaves are exactly one of the ranges in `pin` is never split into
+// its parent: it heads a 4-wide node of its own, whose part-local ref goes to
+// pin_ref (kEmptyChild where no binary node covers the range).  lp4 gets
 // (node << 2) | slot of every leaf.  Returns the depth of the 4-wide tree.
 int collapse_part(const int4 *br, int tc, int tb, const std::vector<int> &svidx, const std::vector<double> &rest,
-                  std::vector<float4> &tmpl, int *lp4)
+                  const std::vector<std::pair<int, int>> &pin, std::vector<int> &pin_ref, std::vector<float4> &tmpl,
+                  int *lp4)
 {
+    pin_ref.assign(pin.size(), kEmptyChild);
     if (tc < 2) return 0;
     const int nbin = tc - 1;
+    std::vector<int> rlo(nbin), rhi(nbin), pin_of(nbin, -1);
     const double inf = std::numeric_limits<double>::infinity();
     std::vector<double> bx(6 * (size_t)nbin);
     std::vector<float> area(nbin, 0.f);
@@ -232,6 +296,8 @@ int collapse_part(const int4 *br, int tc, int tb, const std::vector<int> &svidx,
         double a[6], b[6];
         child_box(br[n].x, a);
         child_box(br[n].y, b);
+        rlo[n] = std::min(br[n].x >= 0 ? rlo[br[n].x] : ~br[n].x, br[n].y >= 0 ? rlo[br[n].y] : ~br[n].y);
+        rhi[n] = std::max(br[n].x >= 0 ? rhi[br[n].x] : ~br[n].x, br[n].y >= 0 ? rhi[br[n].y] : ~br[n].y);
         for (int k = 0; k < 3; k++) {
             bx[6 * (size_t)n + k] = std::min(a[k], b[k]);
             bx[6 * (size_t)n + 3 + k] = std::max(a[3 + k], b[3 + k]);
@@ -240,6 +306,14 @@ int collapse_part(const int4 *br, int tc, int tb, const std::vector<int> &svidx,
                      dz = bx[6 * (size_t)n + 5] - bx[6 * (size_t)n + 2];
         area[n] = (float)(2.0 * (dx * dy + dy * dz + dz * dx));
         stk.pop_back();
+    }
+    if (!pin.empty()) {
+        std::map<std::pair<int, int>, int> by_range;
+        for (int n = 0; n < nbin; n++) by_range[{rlo[n], rhi[n]}] = n;
+        for (size_t i = 0; i < pin.size(); i++) {
+            auto it = by_range.find(pin[i]);
+            if (it != by_range.end()) pin_of[it->second] = (int)i;
+        }
     }
     const int base = (int)(tmpl.size() / kNode4);
     const float finf = std::numeric_limits<float>::infinity();
@@ -250,13 +324,14 @@ int collapse_part(const int4 *br, int tc, int tb, const std::vector<int> &svidx,
         const Item it = todo.back();
         todo.pop_back();
         const int me = (int)(tmpl.size() / kNode4) - base;
+        if (pin_of[it.bin] >= 0) pin_ref[pin_of[it.bin]] = me;
         int ch[4] = {br[it.bin].x, br[it.bin].y, kEmptyChild, kEmptyChild};
         int n = 2;
         while (n < 4) {
             int best = -1;
             float ba = -1.f;
             for (int k = 0; k < n; k++)
-                if (ch[k] >= 0 && area[ch[k]] > ba) { ba = area[ch[k]]; best = k; }
+                if (ch[k] >= 0 && pin_of[ch[k]] < 0 && area[ch[k]] > ba) { ba = area[ch[k]]; best = k; }
             if (best < 0) break;
             const int c = ch[best];
             for (int k = n; k > best + 1; k--) ch[k] = ch[k - 1];
@@ -887,6 +962,12 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
         for (int c = 0; c < 3; c++) tvidx[3 * (size_t)t + c] = newv[D->tri[3 * t + c]];
     std::vector<int> rank_v(rank.begin(), rank.end());
     std::vector<int> tpart(D->tri_part, D->tri_part + NT);
+    std::vector<int> tgrp(NT, 0);
+    std::vector<double> tdev(NT, 0.0);
+    for (int p = 0; p < NP; p++) {
+        double ext = std::max(std::max(pext[3 * p], pext[3 * p + 1]), pext[3 * p + 2]);
+        coplanar_groups(ptris[p], D->tri, xyz, ext, tgrp, tdev);
+    }
 
     cudaStream_t st = ctx->stream;
     std::vector<void *> tmp;  // build-only device buffers
@@ -901,7 +982,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
         cudaError_t e_ = (x);                                                                               \
         if (e_ != cudaSuccess) return bail(e_ == cudaErrorMemoryAllocation ? SRP_ERR_OOM : SRP_ERR_CUDA, #x, e_); \
     } while (0)
-    int *d_tvidx0, *d_tpart, *d_rank, *vals, *vals2, *scratch, *d_ptb, *d_ptc, *d_pnb, *d_nodepart, *d_nodebase, *d_depth;
+    int *d_tvidx0, *d_tpart, *d_tgrp, *d_rank, *vals, *vals2, *scratch, *d_ptb, *d_ptc, *d_pnb, *d_nodepart, *d_nodebase, *d_depth;
     unsigned long long *keys, *keys2;
     float *d_plo, *d_pext;
     int4 *node_refs;
@@ -922,6 +1003,8 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     MK(dmalloc(tmp, &node_refs, (size_t)std::max(nb, 1)));
     MK(dmalloc(tmp, &d_tvidx0, (size_t)NT * 3));
     MK(dmalloc(tmp, &d_tpart, (size_t)NT));
+    MK(dmalloc(tmp, &d_tgrp, (size_t)NT));
+    MK(dmalloc(m->allocs, &h.grp, (size_t)NT));
     MK(dmalloc(tmp, &d_rank, (size_t)NP));
     MK(dmalloc(tmp, &keys, (size_t)NT));
     MK(dmalloc(tmp, &keys2, (size_t)NT));
@@ -940,12 +1023,13 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
     MK(cudaMemcpyAsync(h.vert_part, vert_part.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(d_tvidx0, tvidx.data(), sizeof(int) * tvidx.size(), cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(d_tpart, tpart.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
+    MK(cudaMemcpyAsync(d_tgrp, tgrp.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(d_rank, rank_v.data(), sizeof(int) * NP, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(d_plo, plo.data(), sizeof(float) * plo.size(), cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(d_pext, pext.data(), sizeof(float) * pext.size(), cudaMemcpyHostToDevice, st));
-    // 1-2: Morton codes and sort (bits 0..39 hold the code and the part rank)
-    MK(launch_morton(h.rest64, d_tvidx0, d_tpart, d_rank, d_plo, d_pext, NT, keys, vals, st));
-    MK(radix_sort_pairs(keys, vals, keys2, vals2, NT, 0, 40, scratch, sc_ints, st));
+    // 1-2: Morton codes and sort (bits 0..51 hold the code, the coplanar group and the part rank)
+    MK(launch_morton(h.rest64, d_tvidx0, d_tpart, d_rank, d_tgrp, d_plo, d_pext, NT, keys, vals, st));
+    MK(radix_sort_pairs(keys, vals, keys2, vals2, NT, 0, 56, scratch, sc_ints, st));
     std::vector<int> sorted(NT);
     MK(cudaMemcpyAsync(sorted.data(), vals, sizeof(int) * NT, cudaMemcpyDeviceToHost, st));
     MK(cudaStreamSynchronize(st));
@@ -1008,14 +1092,42 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
         std::vector<int4> brefs(std::max(nb, 1));
         MK(cudaMemcpy(brefs.data(), node_refs, sizeof(int4) * std::max(nb, 1), cudaMemcpyDeviceToHost));
         std::vector<int> lp4(NT, -1);
+        std::vector<int2> grp(NT, make_int2(kEmptyChild, 0));
         std::vector<float4> tmpl;
         int n4 = 0, depth4 = 0;
+        const double pose_err = 1e-14 * h.R;  // bound on the FP64 posing error of a vertex
         for (int r = 0; r < NP; r++) {
             const int p = order[r];
             PartInfo &pi = h.part[p];
             pi.node_begin = n4;
-            int d4 = collapse_part(brefs.data() + bin_begin[p], pi.tri_count, pi.tri_begin, svidx, rest, tmpl,
-                                   lp4.data() + pi.tri_begin);
+            // each coplanar group is a contiguous run of the part's sorted triangles
+            std::map<int, std::array<int, 3>> runs;  // group -> first, last, count
+            for (int k = 0; k < pi.tri_count; k++) {
+                const int g = tgrp[sorig[pi.tri_begin + k]];
+                if (g == 0) continue;
+                auto it = runs.find(g);
+                if (it == runs.end()) runs[g] = {k, k, 1};
+                else { it->second[1] = k; it->second[2]++; }
+            }
+            std::vector<std::pair<int, int>> pin;
+            std::vector<int> pin_g, pin_ref;
+            for (auto &kv : runs)
+                if (kv.second[1] - kv.second[0] + 1 == kv.second[2]) {
+                    pin.push_back({kv.second[0], kv.second[1]});
+                    pin_g.push_back(kv.first);
+                }
+            int d4 = collapse_part(brefs.data() + bin_begin[p], pi.tri_count, pi.tri_begin, svidx, rest, pin, pin_ref,
+                                   tmpl, lp4.data() + pi.tri_begin);
+            for (size_t i = 0; i < pin.size(); i++) {
+                if (pin_ref[i] == kEmptyChild) continue;
+                for (int k = pin[i].first; k <= pin[i].second; k++) {
+                    const int t = pi.tri_begin + k;
+                    const float dev = (float)((tdev[sorig[t]] + pose_err) * 1.001);
+                    int bits;
+                    memcpy(&bits, &dev, sizeof bits);
+                    grp[t] = make_int2(pin_ref[i], bits);
+                }
+            }
             pi.node_count = (int)(tmpl.size() / kNode4) - n4;
             n4 += pi.node_count;
             depth4 = std::max(depth4, d4);
@@ -1032,6 +1144,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
             return fail(ctx, SRP_ERR_MESH, "4-wide BVH depth %d exceeds the traversal stack (%d)", depth4, kStack);
         }
         MK(cudaMemcpyAsync(h.leaf_parent, lp4.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
+        MK(cudaMemcpyAsync(h.grp, grp.data(), sizeof(int2) * NT, cudaMemcpyHostToDevice, st));
         MK(dmalloc(m->allocs, &h.node_static, (size_t)std::max(h.n_static_nodes, 1) * kNode4));
         MK(dmalloc(m->allocs, &m->node_tmpl_dyn, (size_t)std::max(h.n_dyn_nodes, 1) * kNode4));
         MK(dmalloc(tmp, &cnt_static, (size_t)std::max(h.n_static_nodes, 1)));

@@ -25,7 +25,8 @@ __device__ inline unsigned spread3(unsigned v)
 }
 
 __global__ void k_morton(const double *rest64, const int *tri_vidx, const int *tri_part, const int *rank_of_part,
-                         const float *part_lo, const float *part_ext, int n_tris, unsigned long long *keys, int *vals)
+                         const int *tri_grp, const float *part_lo, const float *part_ext, int n_tris,
+                         unsigned long long *keys, int *vals)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tris) return;
@@ -44,16 +45,18 @@ __global__ void k_morton(const double *rest64, const int *tri_vidx, const int *t
         q[k] = min((unsigned)(f * 1024.f), 1023u);
     }
     unsigned m = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
-    keys[t] = ((unsigned long long)rank_of_part[p] << 32) | m;
+    // part rank, then coplanar group (0: none), then the Morton code: every group
+    // of a part is one subtree of the part's radix tree
+    keys[t] = ((unsigned long long)rank_of_part[p] << 48) | ((unsigned long long)(tri_grp[t] & 0xffff) << 32) | m;
     vals[t] = t;
 }
 
 cudaError_t launch_morton(const double *rest64, const int *tri_vidx, const int *tri_part, const int *rank_of_part,
-                          const float *part_lo, const float *part_ext, int n_tris, unsigned long long *keys,
-                          int *vals, cudaStream_t st)
+                          const int *tri_grp, const float *part_lo, const float *part_ext, int n_tris,
+                          unsigned long long *keys, int *vals, cudaStream_t st)
 {
-    k_morton<<<(n_tris + 255) / 256, 256, 0, st>>>(rest64, tri_vidx, tri_part, rank_of_part, part_lo, part_ext,
-                                                   n_tris, keys, vals);
+    k_morton<<<(n_tris + 255) / 256, 256, 0, st>>>(rest64, tri_vidx, tri_part, rank_of_part, tri_grp, part_lo,
+                                                   part_ext, n_tris, keys, vals);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,9 @@ struct MeshDev {
                            // single-leaf part
     float4 *tri_static;    // [n_static_tris][3]
     float4 *node_static;   // [n_static_nodes][kNode4]
+    int2 *grp;             // [n_tris] sorted -> (part-local 4-wide ref of the subtree holding the triangle's
+                           // coplanar group or kEmptyChild, FP32 bits of the group's deviation from its plane
+                           // plus the posing error bound, metres)
     float2 *mat32;         // [n_mats] (rho_s, rho_d) FP32
     double *mat64;         // [n_mats][2]
     float root_box_static[kMaxParts][6];
@@ -220,8 +223,8 @@ __host__ __device__ inline double ord_to_dbl(unsigned long long o)
 // ---------------------------------------------------------------- launchers
 // build.cu
 cudaError_t launch_morton(const double *rest64, const int *tri_vidx, const int *tri_part, const int *rank_of_part,
-                          const float *part_lo, const float *part_ext, int n_tris, unsigned long long *keys,
-                          int *vals, cudaStream_t st);
+                          const int *tri_grp, const float *part_lo, const float *part_ext, int n_tris,
+                          unsigned long long *keys, int *vals, cudaStream_t st);
 cudaError_t radix_sort_pairs(unsigned long long *keys, int *vals, unsigned long long *keys_tmp, int *vals_tmp,
                              int n, int lo_bit, int hi_bit, int *scratch, size_t scratch_ints, cudaStream_t st);
 size_t radix_sort_scratch_ints(int n);

@@ -83,6 +83,7 @@ struct TraceCtx {
     const double *mat64;
     const unsigned *tri_mat;
     const int *tri_vidx;
+    const int2 *grp;  // per sorted triangle: subtree of its coplanar group, deviation bound
     // FP64 window and basis for the FP64 path
     double umin, vmin, wmin, Du, Dv, Lw, eps;
     double u[3], v[3], d[3], c_ref[3];
@@ -157,6 +158,7 @@ __global__ void k_frame(TraceArgs a)
     B.mat64 = m->mat64;
     B.tri_mat = m->tri_mat;
     B.tri_vidx = m->tri_vidx;
+    B.grp = m->grp;
     for (int p = 0; p < m->n_parts; p++) {
         const PartInfo &pi = m->part[p];
         PartView &pv = B.part[p];
@@ -348,10 +350,12 @@ __device__ __forceinline__ bool classify(float U, float V, float W, float eU, fl
 // centre (uc, vc); otherwise the world-frame test.  Triangles whose decision
 // was within its error bound are collected in cd (settled in FP64 afterwards);
 // returns false when they overflow the list or a walk bound is reached (the ray
-// then goes to the FP64 re-trace).
+// then goes to the FP64 re-trace).  A secondary ray leaving the plane of its
+// origin's coplanar group passes the group's subtree (ref gskip of part gpart)
+// by: none of its triangles can be hit beyond the origin.
 template <bool COUNT>
 __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float uc, float vc, float tlo, int skip,
-                          float delta, float tau, Best32 &best, Counts &cn, Cands &cd)
+                          int gpart, int gskip, float delta, float tau, Best32 &best, Counts &cn, Cands &cd)
 {
     best.t = INFINITY;
     best.part = -1;
@@ -367,6 +371,7 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
     int po[kMaxParts], np = 0;
     for (int p = 0; p < B.n_parts; p++) {
         const PartView &pv = B.part[p];
+        if (p == gpart && pv.root == gskip) continue;  // the whole part is the origin's plane
         float t = box_enter(pv.box[0], pv.box[3], pv.box[1], pv.box[4], pv.box[2], pv.box[5], r.inv, r.oi, tlo - tau,
                             INFINITY);
         if (t == INFINITY) continue;
@@ -379,16 +384,19 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
         if (te[q] > best.t + tau) break;  // this part and every later one start beyond the best hit
         const int p = po[q];
         const PartView &pv = B.part[p];
+        const int gs = p == gpart ? gskip : kEmptyChild;
         int sp = 0, iters = 0;
         int ref = pv.root;
         while (true) {
             if (++iters > pv.limit) { clean = false; cn.flags |= kFlagStack; break; }
             if (ref >= 0) {
-                const int n = node4_step(pv.node + (size_t)ref * kNode4, r.inv, r.oi, r.oct, tlo - tau, best.t + tau, ref,
-                                         stack, sp);
-                if (COUNT) { n_nodes++; n_boxes += 4; }
-                if (n < 0) { clean = false; cn.flags |= kFlagStack; break; }
-                if (n > 0) continue;
+                if (ref != gs) {
+                    const int n = node4_step(pv.node + (size_t)ref * kNode4, r.inv, r.oi, r.oct, tlo - tau,
+                                             best.t + tau, ref, stack, sp);
+                    if (COUNT) { n_nodes++; n_boxes += 4; }
+                    if (n < 0) { clean = false; cn.flags |= kFlagStack; break; }
+                    if (n > 0) continue;
+                }
             } else {
                 int tl = ~ref;
                 if (COUNT) n_tris++;
@@ -517,7 +525,7 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
         const float uc = fmaf((float)i + 0.5f, B.du32, B.umin32);
         const float vc = fmaf((float)j + 0.5f, B.dv32, B.vmin32);
         float wgt = 1.0f;
-        int skip = -1;
+        int skip = -1, gpart = -1, gskip = kEmptyChild;
         float acc[6] = {0, 0, 0, 0, 0, 0};
         int hits[kMaxBounces + 1], hpt[kMaxBounces + 1];
         for (int k = 0; k <= kMaxBounces; k++) hits[k] = -1;
@@ -531,7 +539,10 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
             Best32 h;
             float tlo = seg == 0 ? 0.0f : B.eps32;
             nseg_done++;
-            if (!nearest32<COUNT>(B, r, seg == 0, uc, vc, tlo, skip, delta, tau, h, cn, cd)) { clean = false; break; }
+            if (!nearest32<COUNT>(B, r, seg == 0, uc, vc, tlo, skip, gpart, gskip, delta, tau, h, cn, cd)) {
+                clean = false;
+                break;
+            }
             if (cd.n > 0) resolve64(B, N, i, j, seg, hpt, skip, cd, h);  // rare: settle in FP64
             if (h.part < 0) break;
             hpt[seg] = (h.part << 24) | h.tl;
@@ -572,6 +583,11 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
                 r.d[k] = r.d[k] - 2.0f * dn * n[k];
             }
             skip = orig;
+            // the reflected ray leaves the hit triangle's plane at |dn|: its coplanar group can
+            // only be met within dev / |dn| of the origin, inside the self-hit distance eps
+            const int2 g = __ldg(B.grp + B.part[h.part].tri_begin + h.tl);
+            gpart = h.part;
+            gskip = fabsf(dn) * B.eps32 > 16.0f * __int_as_float(g.y) ? g.x : kEmptyChild;
             // next segment: world-frame test; the origin error grows with the previous bound
             delta = B.delta_s + 2.0f * delta;
             tau = 64.0f * delta + 32.0f * kU * (B.R + B.L);
