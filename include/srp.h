@@ -110,6 +110,15 @@ typedef struct {
 
 #define SRP_EVAL_COUNT 1  /* gather traversal counters (slower kernel variant)        */
 #define SRP_EVAL_TIMING 2 /* time each phase with CUDA events on the context stream   */
+/* Primary visibility by BVH traversal of every pixel's ray instead of the
+ * default rasterisation.  All primary rays of an evaluation are parallel
+ * (Sec. 4.3: one independent ray per pixel, all along d), so the default
+ * projects each triangle into the window and applies the same FP32 test to the
+ * pixel centres it covers, keeping per pixel the nearest certain hit and the
+ * triangles the test could not settle (resolved in FP64 as after a traversal).
+ * Both give the same hits and the same force bits; this flag is for testing
+ * that and for meshes whose triangles each cover much of the window. */
+#define SRP_EVAL_TRAVERSE 8
 
 /* Counters of the last srp_eval_batch call (summed over its evaluations). */
 typedef struct {

@@ -54,6 +54,19 @@ struct srp_ctx {
     size_t tctx_cap = 0;
     int *amb_count = nullptr;
     size_t amb_count_cap = 0;
+    // rasterised primary visibility: pixel buffers (kept cleared), per-lane chunk lists
+    unsigned long long *pix_key = nullptr;
+    size_t pix_key_cap = 0;
+    unsigned *pix_cnt = nullptr;
+    size_t pix_cnt_cap = 0;
+    unsigned *pix_cand = nullptr;
+    size_t pix_cand_cap = 0;
+    int4 *big = nullptr;
+    size_t big_cap = 0;
+    unsigned *big_count = nullptr;
+    size_t big_count_cap = 0;
+    int *rast_bad = nullptr;
+    size_t rast_bad_cap = 0;
     double *io = nullptr;
     size_t io_cap = 0;
     int32_t *hits = nullptr;
@@ -156,6 +169,19 @@ cudaError_t grow(T **p, size_t *cap, size_t need, bool zero)
     }
     *cap = n;
     return cudaSuccess;
+}
+
+// grow, then set every byte of a new buffer to `byte` before any later work
+// on any stream can touch it.
+template <class T>
+cudaError_t grow_fill(T **p, size_t *cap, size_t need, int byte)
+{
+    if (need <= *cap) return cudaSuccess;
+    cudaError_t e = grow(p, cap, need, false);
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(*p, byte, *cap * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaDeviceSynchronize();
 }
 
 void free_mesh(Mesh *m)
@@ -508,6 +534,14 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     CK(ctx, grow(&ctx->partials1, &ctx->partials1_cap, SL * kRed1 * kPart, false));
     CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
     CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * pl.nbx, false));
+    if (!(prm->flags & SRP_EVAL_TRAVERSE)) {
+        CK(ctx, grow(&ctx->pix_key, &ctx->pix_key_cap, SL * pl.R, false));
+        CK(ctx, grow(&ctx->pix_cnt, &ctx->pix_cnt_cap, SL * pl.R, false));
+        CK(ctx, grow(&ctx->pix_cand, &ctx->pix_cand_cap, SL * pl.R * kPixCand, false));
+        CK(ctx, grow(&ctx->big, &ctx->big_cap, (size_t)pl.lanes * pl.S * kBigPerSlot, false));
+        CK(ctx, grow_fill(&ctx->big_count, &ctx->big_count_cap, (size_t)kLanes, 0));
+        CK(ctx, grow_fill(&ctx->rast_bad, &ctx->rast_bad_cap, SL, 0));
+    }
     if (want_hits || adjoint) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
     // every slot evaluates this mesh on this grid; lane b owns slots [b S, (b + 1) S)
     std::vector<SlotDesc> sd(SL);
@@ -546,6 +580,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
     cudaStream_t st = ctx->stream;
     const int S = pl.S, nbx = pl.nbx, nseg = pl.nseg;
     const size_t R = pl.R;
+    const int h_tris = m->h.n_tris;
     CK(ctx, cudaEventRecord(ctx->ev_fork, st));
     for (int b = 0; b < pl.lanes; b++) CK(ctx, cudaStreamWaitEvent(ctx->lane[b], ctx->ev_fork, 0));
     for (int c = 0; c < pl.nchunks; c++) {
@@ -572,6 +607,17 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         a.amb_list = ctx->amb_list + s0 * nbx * kTileRays;
         a.amb_count = ctx->amb_count + s0 * nbx;
         a.count = (prm->flags & SRP_EVAL_COUNT) ? 1 : 0;
+        if (!(prm->flags & SRP_EVAL_TRAVERSE)) {
+            a.raster = 1;
+            a.rast_tris = h_tris;
+            a.pix_key = ctx->pix_key + s0 * R;
+            a.pix_cnt = ctx->pix_cnt + s0 * R;
+            a.pix_cand = ctx->pix_cand + s0 * R * kPixCand;
+            a.big_cap = S * kBigPerSlot;
+            a.big = ctx->big + (size_t)b * a.big_cap;
+            a.big_count = ctx->big_count + b;
+            a.rast_bad = ctx->rast_bad + s0;
+        }
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
         a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : (adj ? stage : nullptr);
         int g0 = tm.mark(ls);
@@ -589,6 +635,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
         int g4 = tm.mark(ls);
         launches += 4;  // frame, trace, two reduction levels
+        if (a.raster) launches += 4;  // two raster passes, small and large triangles
         trace_launches++;
         if (adj) {
             AdjArgs g{};
@@ -801,6 +848,12 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->prop_replay);
     cudaFree(ctx->prop_done);
     cudaFree(ctx->amb_count);
+    cudaFree(ctx->pix_key);
+    cudaFree(ctx->pix_cnt);
+    cudaFree(ctx->pix_cand);
+    cudaFree(ctx->big);
+    cudaFree(ctx->big_count);
+    cudaFree(ctx->rast_bad);
     cudaFree(ctx->io);
     cudaFree(ctx->hits);
     cudaFree(ctx->adj_partials);
@@ -1791,9 +1844,20 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     SlotPose *pose;
     unsigned char *tctx;
     double *part, *part1;
-    int *alist, *acount;
+    int *alist, *acount, *rbad;
+    unsigned long long *pkey;
+    unsigned *pcnt, *pcand, *bcount;
+    int4 *blist;
     SlotDesc *sd;
     PropState *S;
+    size_t Rmax = 1;
+    int max_tris = 0;
+    for (int i = 0; i < n; i++) {
+        Rmax = std::max(Rmax, (size_t)tr[i].N * tr[i].N);
+        max_tris = std::max(max_tris, mk[i]->h.n_tris);
+    }
+    const bool raster = !(p->eval.flags & SRP_EVAL_TRAVERSE);
+    const size_t bcap = std::min<size_t>((size_t)n * kBigPerSlot, (size_t)1 << 22);
     CK(ctx, dmalloc(owned, &v64, std::max<size_t>(n64, 1)));
     CK(ctx, dmalloc(owned, &vview, nview));
     CK(ctx, dmalloc(owned, &vv64, nview * 3));
@@ -1812,6 +1876,14 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &acount, (size_t)n * nbx));
     CK(ctx, dmalloc(owned, &sd, (size_t)n));
     CK(ctx, dmalloc(owned, &S, (size_t)n));
+    CK(ctx, dmalloc(owned, &pkey, raster ? (size_t)n * Rmax : 1));
+    CK(ctx, dmalloc(owned, &pcnt, raster ? (size_t)n * Rmax : 1));
+    CK(ctx, dmalloc(owned, &pcand, raster ? (size_t)n * Rmax * kPixCand : 1));
+    CK(ctx, dmalloc(owned, &blist, raster ? bcap : 1));
+    CK(ctx, dmalloc(owned, &bcount, 1));
+    CK(ctx, dmalloc(owned, &rbad, (size_t)n));
+    CK(ctx, cudaMemsetAsync(bcount, 0, sizeof(unsigned), st));
+    CK(ctx, cudaMemsetAsync(rbad, 0, sizeof(int) * n, st));
     double *d_sun = io, *d_dist = io + 3 * (size_t)n, *d_f = d_dist + n, *d_t = d_f + 3 * (size_t)n,
            *d_y0 = d_t + 3 * (size_t)n, *d_t01 = d_y0 + 6 * (size_t)n;
     CK(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned) * std::max<size_t>(nnode, 1), st));
@@ -1910,6 +1982,18 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         a.partials1 = part1;
         a.amb_list = alist;
         a.amb_count = acount;
+        a.ray_stride = Rmax;
+        if (raster) {
+            a.raster = 1;
+            a.rast_tris = max_tris;
+            a.pix_key = pkey;
+            a.pix_cnt = pcnt;
+            a.pix_cand = pcand;
+            a.big = blist;
+            a.big_cap = (int)bcap;
+            a.big_count = bcount;
+            a.rast_bad = rbad;
+        }
         cudaGraph_t graph = nullptr;
         CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;

@@ -159,7 +159,23 @@ struct TraceArgs {
     int *amb_count;              // [S][n_blocks_x]
     int32_t *hits;               // [S][ray_stride][seg_stride] or null
     int count;                   // gather traversal counters
+    // rasterised primary visibility (raster != 0); the pixel buffers are
+    // cleared before each launch's raster passes
+    int raster;
+    int rast_tris;               // largest triangle count of a slot's mesh (raster grid width)
+    unsigned long long *pix_key; // [S][ray_stride] nearest certain FP32 hit: t bits << 32 | part << 24 | tl; ~0 none
+    unsigned *pix_cnt;           // [S][ray_stride] uncertain triangles of the pixel's primary ray
+    unsigned *pix_cand;          // [S][ray_stride][kPixCand] the first kPixCand of them
+    int4 *big;                   // [big_cap] (slot, sorted triangle, chunk column, chunk row) of large triangles
+    unsigned *big_count;         // entries claimed in big (reset by k_frame)
+    int big_cap;
+    int *rast_bad;               // [S] 1: a slot's list entry did not fit; every ray of it traverses
 };
+constexpr int kPixCand = 2;      // uncertain triangles kept per pixel (more: the ray traverses)
+constexpr int kRastSmall = 64;   // largest pixel box one thread rasterises
+constexpr int kRastChunk = 32;   // larger triangles: chunks of 32 x 32 pixels, one block each
+constexpr int kRastBigBlocks = 304;
+constexpr int kBigPerSlot = 8192;  // chunk-list entries reserved per slot
 size_t trace_ctx_bytes();
 
 // Propagation settings as seen by the device (from srp_prop_params).

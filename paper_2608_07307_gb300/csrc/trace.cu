@@ -107,6 +107,10 @@ __global__ void k_frame(TraceArgs a)
     const SlotPose &P = a.pose[s];
     TraceCtx &B = reinterpret_cast<TraceCtx *>(a.tctx)[s];
     B.skip = P.skip;
+    if (a.raster) {
+        a.rast_bad[s] = 0;
+        if (s == 0) *a.big_count = 0u;
+    }
     B.n_parts = m->n_parts;
     if (P.skip) return;
     double umin = ord_to_dbl(P.wmin_bits[0]), umax = ord_to_dbl(P.wmax_bits[0]);
@@ -285,6 +289,31 @@ __device__ __forceinline__ void ray_setup(Ray32 &r)
     r.Sz = 1.0f / dz;
 }
 
+// FP32 view-frame test of one triangle against the primary ray through pixel
+// centre (uc, vc): the ray is the third axis, so the edge functions are 2-D
+// cross products of the projected vertices (u, v, depth in a, b, c) relative
+// to the centre.  Error bounds from the coordinate error delta of the rounded
+// projections and centre, plus the rounding of the products.
+struct Prim32 {
+    float U, V, W, eU, eV, eW, det, T;
+};
+
+__device__ __forceinline__ Prim32 prim_test(float4 a, float4 b, float4 c, float uc, float vc, float delta, float w0)
+{
+    const float u4 = 4.0f * kU;
+    Prim32 q;
+    float Ax = a.x - uc, Ay = a.y - vc, Bx = b.x - uc, By = b.y - vc, Cx = c.x - uc, Cy = c.y - vc;
+    q.U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    q.V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    q.W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    q.eU = delta * (fabsf(Bx) + fabsf(By) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Cx * By) + fabsf(Cy * Bx));
+    q.eV = delta * (fabsf(Ax) + fabsf(Ay) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Ax * Cy) + fabsf(Ay * Cx));
+    q.eW = delta * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + u4 * (fabsf(Bx * Ay) + fabsf(By * Ax));
+    q.det = q.U + q.V + q.W;
+    q.T = fmaf(q.U, a.z - w0, fmaf(q.V, b.z - w0, q.W * (c.z - w0)));
+    return q;
+}
+
 struct Best32 {
     float t;
     int part, tl;
@@ -402,18 +431,13 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
                 if (COUNT) n_tris++;
                 if (primary) {
                     int4 vi = __ldg(pv.v4 + tl);
-                    float4 a = __ldg(B.vview + vi.x), b = __ldg(B.vview + vi.y), c = __ldg(B.vview + vi.z);
-                    // view frame: the ray is the third axis through (uc, vc)
-                    float Ax = a.x - uc, Ay = a.y - vc, Bx = b.x - uc, By = b.y - vc, Cx = c.x - uc, Cy = c.y - vc;
-                    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-                    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-                    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-                    float eU = delta * (fabsf(Bx) + fabsf(By) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Cx * By) + fabsf(Cy * Bx));
-                    float eV = delta * (fabsf(Ax) + fabsf(Ay) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Ax * Cy) + fabsf(Ay * Cx));
-                    float eW = delta * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + u4 * (fabsf(Bx * Ay) + fabsf(By * Ax));
-                    float det = U + V + W;
-                    float T = fmaf(U, a.z - B.w0_32, fmaf(V, b.z - B.w0_32, W * (c.z - B.w0_32)));
-                    if (!classify<COUNT>(U, V, W, eU, eV, eW, T, det, tlo, tau, p, tl, best, true, cn, cd)) { clean = false; sp = 0; }
+                    const Prim32 q = prim_test(__ldg(B.vview + vi.x), __ldg(B.vview + vi.y), __ldg(B.vview + vi.z), uc,
+                                               vc, delta, B.w0_32);
+                    if (!classify<COUNT>(q.U, q.V, q.W, q.eU, q.eV, q.eW, q.T, q.det, tlo, tau, p, tl, best, true, cn,
+                                         cd)) {
+                        clean = false;
+                        sp = 0;
+                    }
                 } else {
                     const float4 *tr = pv.tri + (size_t)tl * 3;
                     float4 a = __ldg(tr), b = __ldg(tr + 1), c = __ldg(tr + 2);
@@ -492,6 +516,161 @@ __device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, i
 // One warp per block, one 32-pixel tile (tile_w x 32 / tile_w) per block; the
 // blocks of all slots form one flat grid.  Latency bound: 32 warps per SM at
 // the kernel's 64 registers (no spills).
+// ------------------------------------------------------------- raster
+// Primary visibility by rasterisation.  Every primary ray of an evaluation runs
+// along the same direction d from its pixel centre, so the nearest hit of a
+// pixel is the nearest triangle whose view-frame projection covers the centre:
+// each triangle visits the pixel centres of its projected box and applies the
+// very test the traversal would (prim_test).  Pass 0 keeps, per pixel, the
+// nearest certain hit (64-bit atomic minimum of depth bits and triangle).
+// Pass 1 lists the pixel's triangles the FP32 test could not settle against
+// that minimum: uncertain edge decisions not certainly beyond it, and certain
+// hits within its depth band (what the traversal sends to its FP64
+// resolution).  The trace then settles those candidates in FP64 exactly as
+// after a traversal; a pixel with more than kPixCand of them traverses.
+
+struct RastView {
+    const float4 *vview;
+    float umin32, vmin32, du32, dv32, w0, delta, tau;
+    int N;
+};
+
+__device__ __forceinline__ RastView rast_view(const TraceArgs &a, int s)
+{
+    const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
+    RastView V;
+    V.vview = g->vview;
+    V.umin32 = g->umin32; V.vmin32 = g->vmin32; V.du32 = g->du32; V.dv32 = g->dv32;
+    V.w0 = g->w0_32; V.delta = g->delta_p; V.tau = g->tau_p;
+    V.N = a.sd[s].N;
+    return V;
+}
+
+// Pixels whose centre lies within the triangle's projected box widened by a
+// hundredth of a pixel plus 64 delta: every other centre is outside the exact
+// projection by more than the coordinate error, so the pixel cannot be hit.
+__device__ __forceinline__ bool rast_box(const RastView &V, float4 a, float4 b, float4 c, int &i0, int &i1, int &j0,
+                                         int &j1)
+{
+    const float mu = 0.01f * V.du32 + 64.0f * V.delta, mv = 0.01f * V.dv32 + 64.0f * V.delta;
+    const float lim = (float)V.N + 1.0f;
+    float ulo = (fminf(fminf(a.x, b.x), c.x) - mu - V.umin32) / V.du32 - 0.5f;
+    float uhi = (fmaxf(fmaxf(a.x, b.x), c.x) + mu - V.umin32) / V.du32 - 0.5f;
+    float vlo = (fminf(fminf(a.y, b.y), c.y) - mv - V.vmin32) / V.dv32 - 0.5f;
+    float vhi = (fmaxf(fmaxf(a.y, b.y), c.y) + mv - V.vmin32) / V.dv32 - 0.5f;
+    ulo = fminf(fmaxf(ulo, -1.0f), lim); uhi = fminf(fmaxf(uhi, -1.0f), lim);
+    vlo = fminf(fmaxf(vlo, -1.0f), lim); vhi = fminf(fmaxf(vhi, -1.0f), lim);
+    i0 = max((int)ceilf(ulo), 0); i1 = min((int)floorf(uhi), V.N - 1);
+    j0 = max((int)ceilf(vlo), 0); j1 = min((int)floorf(vhi), V.N - 1);
+    return i0 <= i1 && j0 <= j1;
+}
+
+template <int PASS>
+__device__ __forceinline__ void rast_pixel(const RastView &V, unsigned long long *key, unsigned *cnt, unsigned *cand,
+                                           int i, int j, float4 a, float4 b, float4 c, unsigned id)
+{
+    const float uc = fmaf((float)i + 0.5f, V.du32, V.umin32);
+    const float vc = fmaf((float)j + 0.5f, V.dv32, V.vmin32);
+    const Prim32 q = prim_test(a, b, c, uc, vc, V.delta, V.w0);
+    const bool neg = (q.U < -q.eU) || (q.V < -q.eV) || (q.W < -q.eW);
+    const bool pos = (q.U > q.eU) || (q.V > q.eV) || (q.W > q.eW);
+    if (neg && pos) return;  // certainly outside
+    const bool unsure = fabsf(q.U) <= q.eU || fabsf(q.V) <= q.eV || fabsf(q.W) <= q.eW;
+    const float t = q.T / q.det;
+    const size_t px = (size_t)i * V.N + j;
+    if (PASS == 0) {
+        // primary rays start at the window (tlo = 0); t > 0 orders as its bits
+        if (!unsure && t > 0.0f) atomicMin(key + px, ((unsigned long long)__float_as_uint(t) << 32) | id);
+        return;
+    }
+    const unsigned long long k = key[px];
+    const float tmin = k == ~0ull ? INFINITY : __uint_as_float((unsigned)(k >> 32));
+    bool take;
+    if (unsure) take = !(fabsf(q.det) > 1e-30f && (t > tmin + V.tau || t < -V.tau));
+    else take = fabsf(t) <= V.tau || ((unsigned)k != id && fabsf(t - tmin) <= V.tau);
+    if (take) {
+        const unsigned n = atomicAdd(cnt + px, 1u);
+        if (n < (unsigned)kPixCand) cand[px * kPixCand + n] = id;
+    }
+}
+
+__device__ __forceinline__ int part_of_sorted(const MeshDev *m, int t)
+{
+    int p = 0;
+    for (int q = 0; q < m->n_parts; q++)
+        if (t >= m->part[q].tri_begin && t < m->part[q].tri_begin + m->part[q].tri_count) p = q;
+    return p;
+}
+
+// Thread per (slot, sorted triangle): small projected boxes in place; larger
+// ones are split into chunks listed for k_raster_big (pass 0 lists them, pass 1
+// reuses the list).
+template <int PASS>
+__global__ void __launch_bounds__(128) k_raster(TraceArgs a)
+{
+    const int s = blockIdx.y;
+    const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
+    if (g->skip) return;
+    const MeshDev *m = a.sd[s].mesh;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m->n_tris) return;
+    const RastView V = rast_view(a, s);
+    if (!(V.du32 > 0.0f && V.dv32 > 0.0f)) {
+        if (PASS == 0 && t == 0) a.rast_bad[s] = 1;
+        return;
+    }
+    const int4 vi = __ldg(m->tri_v4 + t);
+    const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
+    int i0, i1, j0, j1;
+    if (!rast_box(V, A, B, C, i0, i1, j0, j1)) return;
+    const int w = i1 - i0 + 1, h = j1 - j0 + 1;
+    if (w * h > kRastSmall) {
+        if (PASS == 0) {
+            const int cw = (w + kRastChunk - 1) / kRastChunk, ch = (h + kRastChunk - 1) / kRastChunk;
+            const unsigned n = (unsigned)(cw * ch);
+            const unsigned at = atomicAdd(a.big_count, n);
+            if (at > (unsigned)a.big_cap || n > (unsigned)a.big_cap - at) {
+                a.rast_bad[s] = 1;
+                return;
+            }
+            for (int k = 0; k < (int)n; k++) a.big[at + k] = make_int4(s, t, k % cw, k / cw);
+        }
+        return;
+    }
+    const int p = part_of_sorted(m, t);
+    const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
+    const size_t off = (size_t)s * a.ray_stride;
+    for (int i = i0; i <= i1; i++)
+        for (int j = j0; j <= j1; j++)
+            rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);
+}
+
+// Block per listed chunk of a large triangle (grid-stride over the list).
+template <int PASS>
+__global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
+{
+    const unsigned n = min(__ldcg(a.big_count), (unsigned)a.big_cap);
+    for (unsigned e = blockIdx.x; e < n; e += gridDim.x) {
+        const int4 E = a.big[e];
+        const int s = E.x, t = E.y;
+        const MeshDev *m = a.sd[s].mesh;
+        const RastView V = rast_view(a, s);
+        const int4 vi = __ldg(m->tri_v4 + t);
+        const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
+        int i0, i1, j0, j1;
+        if (!rast_box(V, A, B, C, i0, i1, j0, j1)) continue;
+        const int p = part_of_sorted(m, t);
+        const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
+        const size_t off = (size_t)s * a.ray_stride;
+        const int ib = i0 + E.z * kRastChunk, jb = j0 + E.w * kRastChunk;
+        for (int q = threadIdx.x; q < kRastChunk * kRastChunk; q += blockDim.x) {
+            const int i = ib + q / kRastChunk, j = jb + q % kRastChunk;
+            if (i <= i1 && j <= j1)
+                rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);
+        }
+    }
+}
+
 template <bool COUNT>
 __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
 {
@@ -534,12 +713,43 @@ __global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
         Cands cd;
         Counts cn = {0u, 0u, 0u, {0u, 0u, 0u, 0u}, 0};
         float delta = B.delta_p, tau = B.tau_p;
+        // rasterised primary visibility of this pixel
+        bool rast = false;
+        unsigned long long pk = ~0ull;
+        if (a.raster) {
+            const size_t px = (size_t)s * a.ray_stride + ray;
+            pk = __ldcs(a.pix_key + px);
+            const unsigned pn = __ldcs(a.pix_cnt + px);
+            rast = pn <= (unsigned)kPixCand && !a.rast_bad[s];
+            if (rast) {
+                cd.n = (int)pn;
+                for (int c = 0; c < (int)pn; c++) cd.id[c] = (int)a.pix_cand[px * kPixCand + c];
+                if (COUNT) cn.why[0] += pn;
+            }
+        }
         for (int seg = 0; seg < nseg; seg++) {
             ray_setup(r);
             Best32 h;
             float tlo = seg == 0 ? 0.0f : B.eps32;
             nseg_done++;
-            if (!nearest32<COUNT>(B, r, seg == 0, uc, vc, tlo, skip, gpart, gskip, delta, tau, h, cn, cd)) {
+            if (seg == 0 && rast) {
+                // the raster's nearest certain hit; its barycentric weights as the traversal forms them
+                h.t = INFINITY;
+                h.part = -1;
+                h.tl = -1;
+                if (pk != ~0ull) {
+                    const unsigned id = (unsigned)pk;
+                    h.part = (int)(id >> 24);
+                    h.tl = (int)(id & 0xffffffu);
+                    const int4 vi = __ldg(B.part[h.part].v4 + h.tl);
+                    const Prim32 q = prim_test(__ldg(B.vview + vi.x), __ldg(B.vview + vi.y), __ldg(B.vview + vi.z), uc,
+                                               vc, delta, B.w0_32);
+                    const float id32 = 1.0f / q.det;
+                    h.t = q.T / q.det;
+                    h.b1 = q.V * id32;
+                    h.b2 = q.W * id32;
+                }
+            } else if (!nearest32<COUNT>(B, r, seg == 0, uc, vc, tlo, skip, gpart, gskip, delta, tau, h, cn, cd)) {
                 clean = false;
                 break;
             }
@@ -1001,6 +1211,18 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
 {
     k_frame<<<S, 32, 0, st>>>(a);
     if (a.n_tiles <= 0) return cudaGetLastError();
+    if (a.raster && a.rast_tris > 0) {
+        // cleared pixel buffers of the launch's slots
+        const size_t px = (size_t)S * a.ray_stride;
+        cudaError_t e = cudaMemsetAsync(a.pix_key, 0xff, sizeof(unsigned long long) * px, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.pix_cnt, 0, sizeof(unsigned) * px, st);
+        if (e != cudaSuccess) return e;
+        dim3 grid((a.rast_tris + 127) / 128, S);
+        k_raster<0><<<grid, 128, 0, st>>>(a);
+        k_raster_big<0><<<kRastBigBlocks, 256, 0, st>>>(a);
+        k_raster<1><<<grid, 128, 0, st>>>(a);
+        k_raster_big<1><<<kRastBigBlocks, 256, 0, st>>>(a);
+    }
     if (a.count) k_trace<true><<<a.n_tiles, kTileRays, 0, st>>>(a);
     else k_trace<false><<<a.n_tiles, kTileRays, 0, st>>>(a);
     return cudaGetLastError();

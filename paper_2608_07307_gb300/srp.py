@@ -21,6 +21,7 @@ SRP_F32, SRP_F64 = 0, 1
 PANELS_TRACK, PANELS_SET, PANELS_TRACK_OFFSET = 0, 1, 2
 EVAL_COUNT = 1
 EVAL_TIMING = 2
+EVAL_TRAVERSE = 8  # primary hits by BVH traversal instead of rasterisation (same results)
 EVAL_AUTOTUNE = 4
 MAX_BOUNCES = 4
 
@@ -262,7 +263,7 @@ class Context:
 
     def eval_batch(self, mesh_id: int, sun_dirs, sun_dist=None, N: int = 256, bounces: int = 1, P0: float = 4.56e-6,
                    eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, hits: bool = False, count: bool = False,
-                   timing: bool = False, out=None):
+                   timing: bool = False, out=None, traverse: bool = False):
         """Force [n,3] (N) and torque [n,3] (N m); with hits=True also the per-ray
         hit triangle ids [n, N*N, bounces+1].  Outputs live where the input lives
         (CUDA tensor in, CUDA tensors out; numpy in, numpy out) unless `out`
@@ -289,7 +290,8 @@ class Context:
         else:
             force, torque = np.empty((n, 3)), np.empty((n, 3))
             hit = np.empty((n, N * N, nseg), np.int32) if hits else None
-        p = EvalParams(N, bounces, P0, eps_rel, panel_mode, (EVAL_COUNT if count else 0) | (EVAL_TIMING if timing else 0))
+        p = EvalParams(N, bounces, P0, eps_rel, panel_mode, (EVAL_COUNT if count else 0) | (EVAL_TIMING if timing else 0)
+                       | (EVAL_TRAVERSE if traverse else 0))
         ps, k1 = _ptr(sun_dirs)
         pd, k2 = _ptr(sun_dist)
         pf, k3 = _ptr(force)
