@@ -565,6 +565,32 @@ __device__ __forceinline__ bool rast_box(const RastView &V, float4 a, float4 b, 
     return i0 <= i1 && j0 <= j1;
 }
 
+// Can pixel centres [ib, ie] x [jb, je] meet the projected triangle?  False
+// only when all four corners lie more than a pixel outside one edge line.
+__device__ __forceinline__ bool chunk_meets(const RastView &V, float4 a, float4 b, float4 c, int ib, int ie, int jb,
+                                            int je)
+{
+    const float u0 = fmaf((float)ib + 0.5f, V.du32, V.umin32), u1 = fmaf((float)ie + 0.5f, V.du32, V.umin32);
+    const float v0 = fmaf((float)jb + 0.5f, V.dv32, V.vmin32), v1 = fmaf((float)je + 0.5f, V.dv32, V.vmin32);
+    const float area = (b.x - a.x) * (c.y - a.y) - (b.y - a.y) * (c.x - a.x);
+    const float pix = V.du32 + V.dv32;
+    if (!(fabsf(area) > 1e-3f * pix * pix)) return true;  // sliver: keep every chunk
+    const float sg = area > 0.0f ? 1.0f : -1.0f;
+    const float px[3] = {a.x, b.x, c.x}, py[3] = {a.y, b.y, c.y};
+    for (int e = 0; e < 3; e++) {
+        const int f = e == 2 ? 0 : e + 1;
+        const float ex = px[f] - px[e], ey = py[f] - py[e];
+        const float m = pix * (fabsf(ex) + fabsf(ey));
+        // edge function, positive inside: sg ((q - p) x (x - p))
+        const float e00 = sg * (ex * (v0 - py[e]) - ey * (u0 - px[e]));
+        const float e01 = sg * (ex * (v1 - py[e]) - ey * (u0 - px[e]));
+        const float e10 = sg * (ex * (v0 - py[e]) - ey * (u1 - px[e]));
+        const float e11 = sg * (ex * (v1 - py[e]) - ey * (u1 - px[e]));
+        if (fmaxf(fmaxf(e00, e01), fmaxf(e10, e11)) < -m) return false;
+    }
+    return true;
+}
+
 template <int PASS>
 __device__ __forceinline__ void rast_pixel(const RastView &V, unsigned long long *key, unsigned *cnt, unsigned *cand,
                                            int i, int j, float4 a, float4 b, float4 c, unsigned id)
@@ -603,8 +629,8 @@ __device__ __forceinline__ int part_of_sorted(const MeshDev *m, int t)
 }
 
 // Thread per (slot, sorted triangle): small projected boxes in place; larger
-// ones are split into chunks listed for k_raster_big (pass 0 lists them, pass 1
-// reuses the list).
+// ones are split into chunks of 32 x 32 pixels listed for k_raster_big (pass 0
+// lists them, pass 1 reuses the list).
 template <int PASS>
 __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
 {
@@ -645,7 +671,8 @@ __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
             rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);
 }
 
-// Block per listed chunk of a large triangle (grid-stride over the list).
+// Block per listed chunk of a large triangle (grid-stride over the list); a
+// chunk that cannot meet the triangle is passed over at once.
 template <int PASS>
 __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
 {
@@ -659,13 +686,15 @@ __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
         const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
         int i0, i1, j0, j1;
         if (!rast_box(V, A, B, C, i0, i1, j0, j1)) continue;
+        const int ib = i0 + E.z * kRastChunk, jb = j0 + E.w * kRastChunk;
+        const int ie = min(ib + kRastChunk - 1, i1), je = min(jb + kRastChunk - 1, j1);
+        if (!chunk_meets(V, A, B, C, ib, ie, jb, je)) continue;  // uniform over the block
         const int p = part_of_sorted(m, t);
         const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
         const size_t off = (size_t)s * a.ray_stride;
-        const int ib = i0 + E.z * kRastChunk, jb = j0 + E.w * kRastChunk;
         for (int q = threadIdx.x; q < kRastChunk * kRastChunk; q += blockDim.x) {
             const int i = ib + q / kRastChunk, j = jb + q % kRastChunk;
-            if (i <= i1 && j <= j1)
+            if (i <= ie && j <= je)
                 rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);
         }
     }

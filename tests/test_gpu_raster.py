@@ -9,7 +9,8 @@ that the raster settles in FP32 when the two meet different candidates): 2e-6
 relative.  Covers small triangles (spacecraft), window-sized ones (box-wing,
 chunked), a one-part scene reflecting onto itself, a fan whose hub pixel has
 too many candidates (that pixel traverses), and a stack of window-sized plates
-whose chunk list overflows (every pixel of the evaluation traverses)."""
+whose list of large triangles overflows (every pixel of the evaluation
+traverses)."""
 import math
 
 import numpy as np
