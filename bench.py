@@ -33,14 +33,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SRP evals/s (200k-triangle spacecraft, 1024^2 rays, 2 specular bounces, tracking panels)"
 # Algorithmic FP32 work per test (FMA = 2 FLOP; add, mul, min, max, compare = 1):
-#   ray/box slab test: 3 x (2 FMA + min + max) + 2 max + 2 min + 1 compare = 23
+#   ray/box slab test with the near and far planes picked by the ray's octant:
+#   6 FMA + 3 max + 3 min + 1 compare = 19
 #   watertight ray/triangle test (published form): 9 sub + 6 FMA (shear) + 6 mul
 #   + 3 sub (edge functions) + 6 compare + 2 add (det) + 3 mul + 3 FMA (depth)
 #   + 1 div + 2 compare = 50
-FLOP_BOX, FLOP_TRI = 23, 50
+FLOP_BOX, FLOP_TRI = 19, 50
+NODE_BYTES, TRI_BYTES = 128, 48  # one 4-wide BVH node, one FP32 triangle record
 # DRAM bytes (read + write) of one k_trace launch of this workload (2 evaluations),
-# from one ncu capture of the current kernel
-TRACE_DRAM_BYTES_PER_LAUNCH = 36.82688e6 + 99.849984e6
+# from one ncu capture of the current kernel (None until captured)
+TRACE_DRAM_BYTES_PER_LAUNCH = 55.201024e6 + 113.996288e6
 # FP32 peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -401,7 +403,7 @@ def run_native(a):
         clk_proc, clk_path = start_clocks(local)
         time.sleep(0.3)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-        ms_trace = ms_refine = ms_geom = ms_reduce = 0.0
+        ms_trace = ms_refine = ms_geom = ms_reduce = ms_raster = 0.0
         launches = trace_launches = refined = rays = segments = 0
         for k in range(a.steps):
             flush.zero_()
@@ -411,7 +413,7 @@ def run_native(a):
             ev[k][1].record(stream)
             st = ctx.eval_stats()
             ms_trace += st["ms_trace"]; ms_refine += st["ms_refine"]; ms_geom += st["ms_geometry"]
-            ms_reduce += st["ms_reduce"]
+            ms_reduce += st["ms_reduce"]; ms_raster += st["ms_raster"]
             launches += st["launches"]; trace_launches += st["trace_launches"]
             refined += st["refined"]; rays += st["rays"]; segments += st["segments"]
         stream.synchronize()
@@ -448,7 +450,7 @@ def run_native(a):
     evals_per_launch = B * a.steps / trace_launches
     ms_per_launch = ms_trace / trace_launches
     achieved = flop_per_eval * evals_per_launch / (ms_per_launch / 1000.0) / 1e12
-    bytes_per_eval = (64 * cnt["nodes_visited"] + 48 * cnt["tris_tested"]) / n_ev
+    bytes_per_eval = (NODE_BYTES * cnt["nodes_visited"] + TRI_BYTES * cnt["tris_tested"]) / n_ev
     l2_gbs = bytes_per_eval * evals_per_launch / (ms_per_launch / 1000.0) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -462,8 +464,10 @@ def run_native(a):
         "rays_per_s": value * a.N * a.N,
         "segments_per_s": segments / (total_ms / 1000.0) * world,
         "refined_fraction": refined / max(rays, 1),
-        "phases_ms_per_step": {"geometry": ms_geom / a.steps, "trace": ms_trace / a.steps,
-                               "refine": ms_refine / a.steps, "reduce": ms_reduce / a.steps},
+        "phases_ms_per_step": {"geometry": ms_geom / a.steps, "raster": ms_raster / a.steps,
+                               "trace": ms_trace / a.steps, "reduce": ms_reduce / a.steps,
+                               "note": "spans between events on each pipeline lane; lanes overlap, so the "
+                                       "phases add up to more than the step"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / PEAK_FP32_TFLOPS, "traffic": TRACE_DRAM_BYTES_PER_LAUNCH,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one k_trace launch of 2 "
@@ -472,7 +476,8 @@ def run_native(a):
                      "flop_per_eval": flop_per_eval,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
         "roofline_l2": {"algorithmic_bytes_per_eval": bytes_per_eval, "achieved_gbs": l2_gbs,
-                        "note": "node (64 B) and triangle (48 B) fetches per eval; served mostly by L1/L2"},
+                        "note": "4-wide node (128 B) and triangle (48 B) fetches per eval of the trace's "
+                                "traversals; served mostly by L1/L2"},
         "gpu_launches": launches,
         "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": B * 3 * 8,
                 "d2h_bytes_per_step": B * 6 * 8},

@@ -137,12 +137,13 @@ typedef struct {
     /* GPU time per phase, milliseconds (SRP_EVAL_TIMING only), after the
      * paper's split of an evaluation into compute, transfer and reduction
      * (Sec. 8.2, Eq. 4): */
-    double ms_geometry;       /* joint angles, posing, window, refit                     */
-    double ms_trace;          /* FP32 first-hit traversal, shading, bounces              */
+    double ms_geometry;       /* joint angles, posing, window bounds, refit              */
+    double ms_trace;          /* FP32 trace: first hits, shading, bounces                */
     double ms_refine;         /* 0: the FP64 settling runs inside the trace and the rare FP64
                                  re-trace inside the reduction (kept for layout)           */
     double ms_reduce;         /* fixed-order FP64 reduction to force / torque            */
     double ms_transfer;       /* host <-> device copies made by the call                 */
+    double ms_raster;         /* window frame and primary visibility by rasterisation    */
 } srp_eval_stats;
 
 /*

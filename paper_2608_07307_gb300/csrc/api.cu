@@ -424,7 +424,7 @@ struct Timing {
     srp_ctx *ctx;
     bool on;
     int n = 0;
-    std::vector<std::pair<int, int>> spans[5];  // geometry, trace, refine, reduce, transfer
+    std::vector<std::pair<int, int>> spans[6];  // geometry, trace, refine, reduce, transfer, raster
     Timing(srp_ctx *c, bool o) : ctx(c), on(o) {}
     int mark(cudaStream_t s)
     {
@@ -441,8 +441,8 @@ struct Timing {
     void collect(srp_eval_stats &L)
     {
         if (!on) return;
-        double *ms[5] = {&L.ms_geometry, &L.ms_trace, &L.ms_refine, &L.ms_reduce, &L.ms_transfer};
-        for (int p = 0; p < 5; p++)
+        double *ms[6] = {&L.ms_geometry, &L.ms_trace, &L.ms_refine, &L.ms_reduce, &L.ms_transfer, &L.ms_raster};
+        for (int p = 0; p < 6; p++)
             for (auto &sp : spans[p]) {
                 float t = 0.f;
                 if (sp.first >= 0 && sp.second >= 0 &&
@@ -629,6 +629,8 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             launches++;
         }
         int g1 = tm.mark(ls);
+        CK(ctx, launch_frame(a, Sc, ls));
+        int g1r = tm.mark(ls);
         CK(ctx, launch_trace(a, Sc, ls));
         int g2 = tm.mark(ls);
         int g3 = g2;  // the FP64 re-trace of overflowing rays runs inside the first reduction level
@@ -663,7 +665,8 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             launches += 3;  // window vertices, rays, finish
         }
         tm.span(0, g0, g1);
-        tm.span(1, g1, g2);
+        tm.span(5, g1, g1r);
+        tm.span(1, g1r, g2);
         tm.span(2, g2, g3);
         tm.span(3, g3, g4);
         if (hit_tri && !h_dev) {
@@ -2003,6 +2006,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
                 if (e == cudaSuccess) e = launch_pose(sd, d_sun, d_dist, p->eval.P0, 0, na, pose, st);
                 if (e == cudaSuccess) e = launch_vertices(sd, pose, na, mv, st);
                 if (e == cudaSuccess) e = launch_refit(sd, pose, na, md, st);
+                if (e == cudaSuccess) e = launch_frame(a, na, st);
                 if (e == cudaSuccess) e = launch_trace(a, na, st);
                 if (e == cudaSuccess) e = launch_reduce(a, na, 0, d_f, d_t, ctx->err_flags, nullptr, st);
             }

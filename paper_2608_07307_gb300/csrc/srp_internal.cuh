@@ -260,6 +260,9 @@ cudaError_t launch_refit_static(const MeshDev *mesh_d, const MeshDev &mh, float4
                                 unsigned *counter_static, float *root_static, cudaStream_t st);
 
 // trace.cu
+// Per-slot window frame and, when rasterising, the primary visibility passes.
+cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st);
+// The FP32 trace (after launch_frame on the same stream).
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st);
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
                           unsigned long long *stats_accum, cudaStream_t st);

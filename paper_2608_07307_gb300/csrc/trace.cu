@@ -1236,7 +1236,7 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
 }
 
 // ------------------------------------------------------------ launchers
-cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
+cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
 {
     k_frame<<<S, 32, 0, st>>>(a);
     if (a.n_tiles <= 0) return cudaGetLastError();
@@ -1252,6 +1252,13 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
         k_raster<1><<<grid, 128, 0, st>>>(a);
         k_raster_big<1><<<kRastBigBlocks, 256, 0, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
+{
+    (void)S;
+    if (a.n_tiles <= 0) return cudaSuccess;
     if (a.count) k_trace<true><<<a.n_tiles, kTileRays, 0, st>>>(a);
     else k_trace<false><<<a.n_tiles, kTileRays, 0, st>>>(a);
     return cudaGetLastError();

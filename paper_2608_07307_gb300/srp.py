@@ -66,7 +66,8 @@ class EvalStats(C.Structure):
                 ("tris_tested", C.c_int64), ("box_tests", C.c_int64), ("handoff_cause", C.c_int64 * 4),
                 ("launches", C.c_int64),
                 ("trace_launches", C.c_int64), ("ms_geometry", C.c_double), ("ms_trace", C.c_double),
-                ("ms_refine", C.c_double), ("ms_reduce", C.c_double), ("ms_transfer", C.c_double)]
+                ("ms_refine", C.c_double), ("ms_reduce", C.c_double), ("ms_transfer", C.c_double),
+                ("ms_raster", C.c_double)]
 
 
 RKF78, RK4 = 0, 1
@@ -436,4 +437,5 @@ class Context:
         return dict(evals=s.evals, rays=s.rays, segments=s.segments, hits=list(s.hits), refined=s.refined,
                     nodes_visited=s.nodes_visited, tris_tested=s.tris_tested, box_tests=s.box_tests,
                     handoff_cause=list(s.handoff_cause), launches=s.launches, trace_launches=s.trace_launches, ms_geometry=s.ms_geometry,
-                    ms_trace=s.ms_trace, ms_refine=s.ms_refine, ms_reduce=s.ms_reduce, ms_transfer=s.ms_transfer)
+                    ms_trace=s.ms_trace, ms_refine=s.ms_refine, ms_reduce=s.ms_reduce, ms_transfer=s.ms_transfer,
+                    ms_raster=s.ms_raster)
