@@ -17,13 +17,16 @@
 
 namespace srp {
 
-__device__ inline void rot_axis(const double *a, double th, double *R)
+// Rotation by the angle whose cosine and sine are c, s about unit axis a.
+__device__ inline void rot_axis_cs(const double *a, double c, double s, double *R)
 {
-    double c = cos(th), s = sin(th), k = 1.0 - c;
+    const double k = 1.0 - c;
     R[0] = c + k * a[0] * a[0];        R[1] = k * a[0] * a[1] - s * a[2]; R[2] = k * a[0] * a[2] + s * a[1];
     R[3] = k * a[1] * a[0] + s * a[2]; R[4] = c + k * a[1] * a[1];        R[5] = k * a[1] * a[2] - s * a[0];
     R[6] = k * a[2] * a[0] - s * a[1]; R[7] = k * a[2] * a[1] + s * a[0]; R[8] = c + k * a[2] * a[2];
 }
+
+constexpr double kPiPose = 3.14159265358979323846;
 
 __global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist, double P0, int eval0, int S,
                        SlotPose *pose)
@@ -54,11 +57,14 @@ __global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double 
         if (p == 0) {
             for (int k = 0; k < 9; k++) M[k] = (k % 4 == 0) ? 1.0 : 0.0;
             T[0] = T[1] = T[2] = 0.0;
-            P.angle[0] = 0.0;
             continue;
         }
         int q = pi.parent;
         const double *Mq = P.M[q], *Tq = P.T[q];
+        // cosine and sine of the joint angle: from the tracking direction itself
+        // when the limits cannot clamp it (no FP64 transcendentals), else from the angle
+        double cth = 1.0, sth = 0.0;
+        bool have_cs = false;
         if (pi.movable) {
             if (panel_mode != SRP_PANELS_SET) {
                 // Sun in the parent's current frame: Mq^T s
@@ -70,18 +76,28 @@ __global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double 
                 double b[3] = {a[1] * n[2] - a[2] * n[1], a[2] * n[0] - a[0] * n[2], a[0] * n[1] - a[1] * n[0]};
                 double x = n[0] * sl[0] + n[1] * sl[1] + n[2] * sl[2];
                 double y = b[0] * sl[0] + b[1] * sl[1] + b[2] * sl[2];
-                th = (x == 0.0 && y == 0.0) ? 0.0 : atan2(y, x);
                 if (!(x == 0.0 && y == 0.0)) P.track_mask |= 1u << p;
+                const bool plain = panel_mode == SRP_PANELS_TRACK || !angles;
+                if (plain && pi.lim[0] <= -kPiPose && pi.lim[1] >= kPiPose && !(x < 0.0 && fabs(y) <= 1e-12 * -x)) {
+                    // atan2(y, x) lies strictly inside (-pi, pi): never clamped, always free
+                    const double r = sqrt(x * x + y * y);
+                    if (r > 0.0) { cth = x / r; sth = y / r; }
+                    have_cs = true;
+                    P.free_mask |= 1u << p;
+                }
+                th = (x == 0.0 && y == 0.0) ? 0.0 : (have_cs ? 0.0 : atan2(y, x));
                 if (panel_mode == SRP_PANELS_TRACK_OFFSET && angles) th += angles[p];
             } else {
                 th = angles ? angles[p] : 0.0;
             }
-            if (th > pi.lim[0] && th < pi.lim[1]) P.free_mask |= 1u << p;
-            th = fmin(fmax(th, pi.lim[0]), pi.lim[1]);
+            if (!have_cs) {
+                if (th > pi.lim[0] && th < pi.lim[1]) P.free_mask |= 1u << p;
+                th = fmin(fmax(th, pi.lim[0]), pi.lim[1]);
+                sincos(th, &sth, &cth);
+            }
         }
-        P.angle[p] = th;
         double R[9];
-        if (pi.movable) rot_axis(pi.axis, th, R);
+        if (pi.movable) rot_axis_cs(pi.axis, cth, sth, R);
         else for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.0 : 0.0;
         for (int i = 0; i < 3; i++)
             for (int j = 0; j < 3; j++) M[3 * i + j] = Mq[3 * i] * R[j] + Mq[3 * i + 1] * R[3 + j] + Mq[3 * i + 2] * R[6 + j];

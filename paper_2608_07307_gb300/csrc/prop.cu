@@ -67,12 +67,18 @@ __device__ void sun_pos(double mjd_tt, double *r)
     const double deg = kPi / 180.0;
     double T = (mjd_tt - 51544.5) / 36525.0;
     double M = fmod(357.5256 + 35999.049 * T, 360.0) * deg;
-    double lam = 282.94 * deg + M + (6892.0 * sin(M) + 72.0 * sin(2.0 * M)) * (deg / 3600.0);
-    double rr = 149.619e9 - 2.499e9 * cos(M) - 0.021e9 * cos(2.0 * M);
-    double ce = cos(23.43929111 * deg), se = sin(23.43929111 * deg);
-    r[0] = rr * cos(lam);
-    r[1] = rr * sin(lam) * ce;
-    r[2] = rr * sin(lam) * se;
+    // two FP64 sincos calls (slow on this GPU's FP64 pipe); the double angle by identity
+    double sM, cM;
+    sincos(M, &sM, &cM);
+    const double s2M = 2.0 * sM * cM, c2M = (cM - sM) * (cM + sM);
+    double lam = 282.94 * deg + M + (6892.0 * sM + 72.0 * s2M) * (deg / 3600.0);
+    double rr = 149.619e9 - 2.499e9 * cM - 0.021e9 * c2M;
+    const double ce = 0.9174820620768958, se = 0.3977771559141214;  // cos, sin of the obliquity 23.43929111 deg
+    double sl, cl;
+    sincos(lam, &sl, &cl);
+    r[0] = rr * cl;
+    r[1] = rr * sl * ce;
+    r[2] = rr * sl * se;
 }
 
 // rotation of the normalised scalar-first quaternion q, row-major

@@ -55,7 +55,6 @@ struct PartInfo {
 struct SlotPose {
     double M[kMaxParts][9];   // part rotation (row-major), body = M x_rest + T
     double T[kMaxParts][3];
-    double angle[kMaxParts];
     double s[3];              // unit Sun direction, body frame
     double u[3], v[3], d[3];  // image-plane basis, d = -s
     unsigned long long wmin_bits[3];  // ordered-int encodings of min(u.x), min(v.x), min(d.x)
