@@ -19,7 +19,7 @@ using namespace srp;
 namespace {
 
 // Evaluation chunks rotate over this many lane streams.
-constexpr int kLanes = 3;
+constexpr int kLanes = 4;
 
 struct Mesh {
     MeshDev h{};                 // host copy holding device pointers
@@ -513,7 +513,7 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     pl.nseg = prm->bounces + 1;
     pl.R = (size_t)pl.N * pl.N;
     // concurrent evaluations: enough rays in flight to fill the GPU several times
-    pl.S = (int)std::min<size_t>(std::max<size_t>((size_t)(1u << 21) / pl.R, 1), 64);
+    pl.S = (int)std::min<size_t>(std::max<size_t>((size_t)(1u << 23) / pl.R, 1), 32);
     pl.S = std::min(pl.S, std::max(n, 1));
     // chunks of S evaluations alternate between lane streams with their own
     // slots and buffers, so the short, latency-bound tail of one chunk (FP64
