@@ -556,7 +556,7 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
         d.tile_w = pl.tw;
         d.tiles_x = tiles_x;
         d.tiles = pl.nbx;
-        d.tile0 = (int)(k % pl.S) * pl.nbx;
+        d.tile0 = (int)(k % pl.S) * trace_blocks(pl.nbx);
     }
     rc = upload_slots(ctx, sd);
     if (rc) return rc;
@@ -595,7 +595,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         TraceArgs a{};
         a.sd = sd;
         a.n_slots = Sc;
-        a.n_tiles = Sc * nbx;
+        a.n_tiles = Sc * trace_blocks(nbx);
         a.pose = pose;
         a.ray_stride = R;
         a.seg_stride = nseg;
@@ -1967,7 +1967,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         for (int k = 0; k < na; k++) {
             dd[k] = desc[act[k]];
             dd[k].tile0 = t0;
-            t0 += dd[k].tiles;
+            t0 += trace_blocks(dd[k].tiles);
             mv = std::max(mv, mk[act[k]]->h.n_verts);
             md = std::max(md, mk[act[k]]->h.n_dyn_tris);
         }

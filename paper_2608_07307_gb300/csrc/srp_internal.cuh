@@ -126,7 +126,7 @@ struct SlotDesc {
     int panel_mode;        // SRP_PANELS_*
     int tile_w;            // trace tile width in pixels (4, 8, 16 or 32); height 32 / tile_w
     int tiles_x, tiles;    // trace tiles across the window, in total
-    int tile0;             // first flattened trace block of the slot
+    int tile0;             // first flattened trace block of the slot (blocks of kTraceWarps tiles)
     int pad_;
 };
 
@@ -137,15 +137,17 @@ struct SlotDesc {
 //   edge, near tie, self-hit band).
 constexpr int kPart = 20;
 
-// Arguments of the trace / refine kernels.  A trace block is one warp over an
-// 8 x 4 pixel tile (kTileRays rays).
+// Arguments of the trace / refine kernels.  A trace warp covers one tile of
+// kTileRays rays (4 x 8, 8 x 4, 16 x 2 or 32 x 1 pixels).
 constexpr int kTileRays = 32;
+constexpr int kTraceWarps = 4;  // trace tiles (warps) per block, sharing one context copy
+inline int trace_blocks(int tiles) { return (tiles + kTraceWarps - 1) / kTraceWarps; }
 constexpr int kRed1 = 64;  // first-level reduction blocks per slot
 
 struct TraceArgs {
     const SlotDesc *sd;          // [S] what each slot evaluates
     int n_slots;                 // S
-    int n_tiles;                 // trace blocks of the launch (sum of the slots' tiles)
+    int n_tiles;                 // trace blocks of the launch (sum over slots of ceil(tiles / kTraceWarps))
     SlotPose *pose;              // [S] (trace / refine OR their error flags into it)
     unsigned char *tctx;         // [S] per-slot traversal context (k_frame output)
     double eps_rel;

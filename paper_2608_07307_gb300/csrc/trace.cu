@@ -700,17 +700,20 @@ __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
     }
 }
 
+// A block is kTraceWarps warps over consecutive tiles of one slot, sharing
+// one copy of the slot's context; a warp past the slot's last tile idles.
 template <bool COUNT>
-__global__ void __launch_bounds__(kTileRays, 32) k_trace(TraceArgs a)
+__global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_trace(TraceArgs a)
 {
     __shared__ TraceCtx B;
     const int s = slot_of_block(a.sd, a.n_slots, blockIdx.x);
     const SlotDesc &D = a.sd[s];
-    const int tile_id = blockIdx.x - D.tile0;
+    const int tile_id = (blockIdx.x - D.tile0) * kTraceWarps + (int)(threadIdx.x >> 5);
     load_ctx(B, a, s);
-    __syncwarp();
+    __syncthreads();
+    if (tile_id >= D.tiles) return;
     const int N = D.N, nseg = D.nseg;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     if (B.skip) {
         if (lane == 0) a.amb_count[(size_t)s * a.n_blocks_x + tile_id] = 0;
         return;
@@ -1259,8 +1262,8 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
 {
     (void)S;
     if (a.n_tiles <= 0) return cudaSuccess;
-    if (a.count) k_trace<true><<<a.n_tiles, kTileRays, 0, st>>>(a);
-    else k_trace<false><<<a.n_tiles, kTileRays, 0, st>>>(a);
+    if (a.count) k_trace<true><<<a.n_tiles, kTileRays * kTraceWarps, 0, st>>>(a);
+    else k_trace<false><<<a.n_tiles, kTileRays * kTraceWarps, 0, st>>>(a);
     return cudaGetLastError();
 }
 
