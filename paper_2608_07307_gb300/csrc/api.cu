@@ -44,8 +44,10 @@ struct srp_ctx {
     // workspace, grown on demand
     SlotPose *pose = nullptr;
     size_t pose_cap = 0;
-    double *partials = nullptr;
+    float *partials = nullptr;
     size_t partials_cap = 0;
+    unsigned *pcounts = nullptr;
+    size_t pcounts_cap = 0;
     int *amb_list = nullptr;
     size_t amb_list_cap = 0;
     double *partials1 = nullptr;
@@ -529,7 +531,8 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     pl.SL = (size_t)pl.S * pl.lanes;
     const size_t SL = pl.SL;
     CK(ctx, grow(&ctx->pose, &ctx->pose_cap, SL, false));
-    CK(ctx, grow(&ctx->partials, &ctx->partials_cap, SL * pl.nbx * kPart, false));
+    CK(ctx, grow(&ctx->partials, &ctx->partials_cap, SL * pl.nbx * 6, false));
+    CK(ctx, grow(&ctx->pcounts, &ctx->pcounts_cap, SL * pl.nbx * kCnt, false));
     CK(ctx, grow(&ctx->amb_list, &ctx->amb_list_cap, SL * pl.nbx * kTileRays, false));
     CK(ctx, grow(&ctx->partials1, &ctx->partials1_cap, SL * kRed1 * kPart, false));
     CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
@@ -601,7 +604,8 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         a.seg_stride = nseg;
         a.eps_rel = prm->eps_rel;
         a.n_blocks_x = nbx;
-        a.partials = ctx->partials + s0 * nbx * kPart;
+        a.partials = ctx->partials + s0 * nbx * 6;
+        a.pcounts = ctx->pcounts + s0 * nbx * kCnt;
         a.partials1 = ctx->partials1 + s0 * kRed1 * kPart;
         a.tctx = ctx->tctx + s0 * trace_ctx_bytes();
         a.amb_list = ctx->amb_list + s0 * nbx * kTileRays;
@@ -842,6 +846,7 @@ void srp_destroy(srp_ctx *ctx)
     for (Mesh *m : ctx->meshes) free_mesh(m);
     cudaFree(ctx->pose);
     cudaFree(ctx->partials);
+    cudaFree(ctx->pcounts);
     cudaFree(ctx->amb_list);
     cudaFree(ctx->partials1);
     cudaFree(ctx->tctx);
@@ -1846,10 +1851,11 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     float *rbox;
     SlotPose *pose;
     unsigned char *tctx;
-    double *part, *part1;
+    float *part;
+    double *part1;
     int *alist, *acount, *rbad;
     unsigned long long *pkey;
-    unsigned *pcnt, *pcand, *bcount;
+    unsigned *pcnt, *pcand, *bcount, *pcnt_blk;
     int4 *blist;
     SlotDesc *sd;
     PropState *S;
@@ -1873,7 +1879,8 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &cfg, (size_t)n * 8));
     CK(ctx, dmalloc(owned, &pose, (size_t)n));
     CK(ctx, dmalloc(owned, &tctx, (size_t)n * trace_ctx_bytes()));
-    CK(ctx, dmalloc(owned, &part, (size_t)n * nbx * kPart));
+    CK(ctx, dmalloc(owned, &part, (size_t)n * nbx * 6));
+    CK(ctx, dmalloc(owned, &pcnt_blk, (size_t)n * nbx * kCnt));
     CK(ctx, dmalloc(owned, &part1, (size_t)n * kRed1 * kPart));
     CK(ctx, dmalloc(owned, &alist, (size_t)n * nbx * kTileRays));
     CK(ctx, dmalloc(owned, &acount, (size_t)n * nbx));
@@ -1982,6 +1989,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         a.eps_rel = p->eval.eps_rel;
         a.n_blocks_x = nbx;
         a.partials = part;
+        a.pcounts = pcnt_blk;
         a.partials1 = part1;
         a.amb_list = alist;
         a.amb_count = acount;

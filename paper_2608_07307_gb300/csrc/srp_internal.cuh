@@ -136,6 +136,7 @@ struct SlotDesc {
 //   15 box tests, 16..19 FP64 hand-offs by cause (primary edge, secondary
 //   edge, near tie, self-hit band).
 constexpr int kPart = 20;
+constexpr int kCnt = kPart - 6;  // the integer counts (6..19) of a tile partial
 
 // Arguments of the trace / refine kernels.  A trace warp covers one tile of
 // kTileRays rays (4 x 8, 8 x 4, 16 x 2 or 32 x 1 pixels).
@@ -154,7 +155,8 @@ struct TraceArgs {
     size_t ray_stride;           // hits: [S][ray_stride][seg_stride]
     int seg_stride;
     int n_blocks_x;              // stride of the per-tile arrays: the largest tile count of a slot
-    double *partials;            // [S][n_blocks_x][kPart] one partial per tile
+    float *partials;             // [S][n_blocks_x][6] force and torque per tile (FP32 tile sums)
+    unsigned *pcounts;           // [S][n_blocks_x][kCnt] counts 6..19 per tile
     double *partials1;           // [S][kRed1][kPart] first-level sums of the tile partials
     int *amb_list;               // [S][n_blocks_x][kTileRays] rays handed to the FP64 path, per tile
     int *amb_count;              // [S][n_blocks_x]

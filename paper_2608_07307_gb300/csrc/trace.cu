@@ -856,20 +856,18 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
     const size_t tile = (size_t)s * a.n_blocks_x + tile_id;
     unsigned bal = __ballot_sync(0xffffffffu, handoff);
     if (handoff) a.amb_list[tile * kTileRays + __popc(bal & ((1u << lane) - 1u))] = ray;
-    // tile sums, one FP64 partial per tile: force and torque by a fixed FP32
+    // tile sums, one partial per tile: force and torque by a fixed FP32
     // butterfly over the 32 rays (FP64 shuffles would occupy GB300's slow FP64
     // pipe), counts by integer reductions; every sum above the tile is FP64
     for (int k = 0; k < 6; k++) {
         float x = fac[k];
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) a.partials[tile * kPart + k] = (double)x;
+        if (lane == 0) a.partials[tile * 6 + k] = x;
     }
-    for (int k = 6; k < (COUNT ? kPart : 13); k++) {
-        unsigned x = __reduce_add_sync(0xffffffffu, cnt[k]);
-        if (lane == 0) a.partials[tile * kPart + k] = (double)x;
+    for (int k = 0; k < kCnt; k++) {
+        const unsigned x = (COUNT || k < 7) ? __reduce_add_sync(0xffffffffu, cnt[6 + k]) : 0u;
+        if (lane == 0) a.pcounts[tile * kCnt + k] = x;
     }
-    if (!COUNT && lane == 0)
-        for (int k = 13; k < kPart; k++) a.partials[tile * kPart + k] = 0.0;
     int fl = __reduce_or_sync(0xffffffffu, flags);
     if (lane == 0) {
         a.amb_count[tile] = __popc(bal);
@@ -1166,14 +1164,14 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
     const int chunk = (nt + kRed1 - 1) / kRed1;
     const int t0 = b * chunk, t1 = min(t0 + chunk, nt);
     const size_t base = (size_t)s * a.n_blocks_x;
-    double acc[kPart];
-    for (int k = 0; k < kPart; k++) acc[k] = 0.0;
+    double f[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long c[kCnt];
+    for (int k = 0; k < kCnt; k++) c[k] = 0ull;
     int mine = 0;
     for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
-        const double *pt = a.partials + (base + t) * kPart;
-        // slot 6: the tile's hand-off flags; the re-trace below counts the rays it does
-        for (int k = 0; k < kPart; k++)
-            if (k != 6) acc[k] += pt[k];
+        for (int k = 0; k < 6; k++) f[k] += (double)a.partials[(base + t) * 6 + k];
+        // count 0: the tile's hand-off flags; the re-trace below counts the rays it does
+        for (int k = 1; k < kCnt; k++) c[k] += a.pcounts[(base + t) * kCnt + k];
         mine |= a.amb_count[base + t];
     }
     __shared__ TraceCtx B;
@@ -1183,17 +1181,43 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
         load_ctx(B, a, s);
         __syncthreads();
         int flags = 0;
+        double acc[kPart];
+        for (int k = 0; k < kPart; k++) acc[k] = 0.0;
         for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
-            const int c = a.amb_count[base + t];
-            for (int q = 0; q < c; q++) refine_ray(B, a, s, a.amb_list[(base + t) * kTileRays + q], acc, flags);
+            const int n = a.amb_count[base + t];
+            for (int q = 0; q < n; q++) refine_ray(B, a, s, a.amb_list[(base + t) * kTileRays + q], acc, flags);
         }
+        for (int k = 0; k < 6; k++) f[k] += acc[k];
+        for (int k = 0; k < kCnt; k++) c[k] += (unsigned long long)acc[6 + k];
         if (flags) atomicOr(&blk_flags, flags);
         __syncthreads();
         if (threadIdx.x == 0 && blk_flags) atomicOr(&a.pose[s].flags, blk_flags);
     }
-    __shared__ double out[kPart];
-    block_sum(acc, out);
-    if (threadIdx.x < kPart) a.partials1[((size_t)s * kRed1 + b) * kPart + threadIdx.x] = out[threadIdx.x];
+    // block sums in a fixed order: FP64 for force and torque, integers for counts
+    __shared__ double rf[6][8];
+    __shared__ unsigned long long rc[kCnt][8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < 6; k++) {
+        const double x = warp_sum(f[k]);
+        if (lane == 0) rf[k][w] = x;
+    }
+    for (int k = 0; k < kCnt; k++) {
+        unsigned long long x = c[k];
+        for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) rc[k][w] = x;
+    }
+    __syncthreads();
+    const int nw = (int)(blockDim.x >> 5);
+    double *out = a.partials1 + ((size_t)s * kRed1 + b) * kPart;
+    if (threadIdx.x < 6) {
+        double x = 0.0;
+        for (int q = 0; q < nw; q++) x += rf[threadIdx.x][q];
+        out[threadIdx.x] = x;
+    } else if (threadIdx.x < kPart) {
+        unsigned long long x = 0ull;
+        for (int q = 0; q < nw; q++) x += rc[threadIdx.x - 6][q];
+        out[threadIdx.x] = (double)x;
+    }
 }
 
 // One block per slot: the first-level sums.
