@@ -67,6 +67,10 @@ struct srp_ctx {
     size_t big_cap = 0;
     unsigned *big_count = nullptr;
     size_t big_count_cap = 0;
+    int2 *bigt = nullptr;
+    size_t bigt_cap = 0;
+    unsigned *bigt_count = nullptr;
+    size_t bigt_count_cap = 0;
     int *rast_bad = nullptr;
     size_t rast_bad_cap = 0;
     double *io = nullptr;
@@ -543,6 +547,8 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
         CK(ctx, grow(&ctx->pix_cand, &ctx->pix_cand_cap, SL * pl.R * kPixCand, false));
         CK(ctx, grow(&ctx->big, &ctx->big_cap, (size_t)pl.lanes * pl.S * kBigPerSlot, false));
         CK(ctx, grow_fill(&ctx->big_count, &ctx->big_count_cap, (size_t)kLanes, 0));
+        CK(ctx, grow(&ctx->bigt, &ctx->bigt_cap, (size_t)pl.lanes * pl.S * kBigPerSlot, false));
+        CK(ctx, grow_fill(&ctx->bigt_count, &ctx->bigt_count_cap, (size_t)kLanes, 0));
         CK(ctx, grow_fill(&ctx->rast_bad, &ctx->rast_bad_cap, SL, 0));
     }
     if (want_hits || adjoint) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
@@ -620,6 +626,8 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             a.big_cap = S * kBigPerSlot;
             a.big = ctx->big + (size_t)b * a.big_cap;
             a.big_count = ctx->big_count + b;
+            a.bigt = ctx->bigt + (size_t)b * a.big_cap;
+            a.bigt_count = ctx->bigt_count + b;
             a.rast_bad = ctx->rast_bad + s0;
         }
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
@@ -641,7 +649,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
         int g4 = tm.mark(ls);
         launches += 4;  // frame, trace, two reduction levels
-        if (a.raster) launches += 4;  // two raster passes, small and large triangles
+        if (a.raster) launches += 5;  // two raster passes over small and large triangles, chunk listing
         trace_launches++;
         if (adj) {
             AdjArgs g{};
@@ -861,6 +869,8 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->pix_cand);
     cudaFree(ctx->big);
     cudaFree(ctx->big_count);
+    cudaFree(ctx->bigt);
+    cudaFree(ctx->bigt_count);
     cudaFree(ctx->rast_bad);
     cudaFree(ctx->io);
     cudaFree(ctx->hits);
@@ -1857,6 +1867,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     unsigned long long *pkey;
     unsigned *pcnt, *pcand, *bcount, *pcnt_blk;
     int4 *blist;
+    int2 *btlist;
     SlotDesc *sd;
     PropState *S;
     size_t Rmax = 1;
@@ -1890,9 +1901,10 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &pcnt, raster ? (size_t)n * Rmax : 1));
     CK(ctx, dmalloc(owned, &pcand, raster ? (size_t)n * Rmax * kPixCand : 1));
     CK(ctx, dmalloc(owned, &blist, raster ? bcap : 1));
-    CK(ctx, dmalloc(owned, &bcount, 1));
+    CK(ctx, dmalloc(owned, &btlist, raster ? bcap : 1));
+    CK(ctx, dmalloc(owned, &bcount, 2));
     CK(ctx, dmalloc(owned, &rbad, (size_t)n));
-    CK(ctx, cudaMemsetAsync(bcount, 0, sizeof(unsigned), st));
+    CK(ctx, cudaMemsetAsync(bcount, 0, 2 * sizeof(unsigned), st));
     CK(ctx, cudaMemsetAsync(rbad, 0, sizeof(int) * n, st));
     double *d_sun = io, *d_dist = io + 3 * (size_t)n, *d_f = d_dist + n, *d_t = d_f + 3 * (size_t)n,
            *d_y0 = d_t + 3 * (size_t)n, *d_t01 = d_y0 + 6 * (size_t)n;
@@ -2003,6 +2015,8 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
             a.big = blist;
             a.big_cap = (int)bcap;
             a.big_count = bcount;
+            a.bigt = btlist;
+            a.bigt_count = bcount + 1;
             a.rast_bad = rbad;
         }
         cudaGraph_t graph = nullptr;

@@ -169,8 +169,11 @@ struct TraceArgs {
     unsigned long long *pix_key; // [S][ray_stride] nearest certain FP32 hit: t bits << 32 | part << 24 | tl; ~0 none
     unsigned *pix_cnt;           // [S][ray_stride] uncertain triangles of the pixel's primary ray
     unsigned *pix_cand;          // [S][ray_stride][kPixCand] the first kPixCand of them
-    int4 *big;                   // [big_cap] (slot, sorted triangle, chunk column, chunk row) of large triangles
+    int4 *big;                   // [big_cap] (slot, sorted triangle, chunk column, chunk row): chunks of large
+                                 // triangles that can meet them
     unsigned *big_count;         // entries claimed in big (reset by k_frame)
+    int2 *bigt;                  // [big_cap] (slot, sorted triangle) of the large triangles
+    unsigned *bigt_count;        // entries claimed in bigt (reset by k_frame)
     int big_cap;
     int *rast_bad;               // [S] 1: a slot's list entry did not fit; every ray of it traverses
 };

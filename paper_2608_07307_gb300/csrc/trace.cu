@@ -109,7 +109,7 @@ __global__ void k_frame(TraceArgs a)
     B.skip = P.skip;
     if (a.raster) {
         a.rast_bad[s] = 0;
-        if (s == 0) *a.big_count = 0u;
+        if (s == 0) { *a.big_count = 0u; *a.bigt_count = 0u; }
     }
     B.n_parts = m->n_parts;
     if (P.skip) return;
@@ -652,14 +652,13 @@ __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
     const int w = i1 - i0 + 1, h = j1 - j0 + 1;
     if (w * h > kRastSmall) {
         if (PASS == 0) {
-            const int cw = (w + kRastChunk - 1) / kRastChunk, ch = (h + kRastChunk - 1) / kRastChunk;
-            const unsigned n = (unsigned)(cw * ch);
-            const unsigned at = atomicAdd(a.big_count, n);
-            if (at > (unsigned)a.big_cap || n > (unsigned)a.big_cap - at) {
+            // listed for k_raster_chunks, which lists its chunks
+            const unsigned at = atomicAdd(a.bigt_count, 1u);
+            if (at >= (unsigned)a.big_cap) {
                 a.rast_bad[s] = 1;
                 return;
             }
-            for (int k = 0; k < (int)n; k++) a.big[at + k] = make_int4(s, t, k % cw, k / cw);
+            a.bigt[at] = make_int2(s, t);
         }
         return;
     }
@@ -671,8 +670,45 @@ __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
             rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);
 }
 
-// Block per listed chunk of a large triangle (grid-stride over the list); a
-// chunk that cannot meet the triangle is passed over at once.
+// Warp per listed large triangle: its 32 x 32-pixel chunks that can meet it,
+// tested a chunk per lane and appended with one atomic per warp pass.
+__global__ void __launch_bounds__(256) k_raster_chunks(TraceArgs a)
+{
+    const unsigned n = min(__ldcg(a.bigt_count), (unsigned)a.big_cap);
+    const unsigned lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x >> 5);
+    for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) {
+        const int2 E = a.bigt[e];
+        const int s = E.x, t = E.y;
+        const MeshDev *m = a.sd[s].mesh;
+        const RastView V = rast_view(a, s);
+        const int4 vi = __ldg(m->tri_v4 + t);
+        const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
+        int i0, i1, j0, j1;
+        if (!rast_box(V, A, B, C, i0, i1, j0, j1)) continue;
+        const int cw = (i1 - i0 + kRastChunk) / kRastChunk, ch = (j1 - j0 + kRastChunk) / kRastChunk;
+        for (int k0 = 0; k0 < cw * ch; k0 += 32) {
+            const int k = k0 + (int)lane;
+            bool meets = false;
+            if (k < cw * ch) {
+                const int ib = i0 + (k % cw) * kRastChunk, jb = j0 + (k / cw) * kRastChunk;
+                meets = chunk_meets(V, A, B, C, ib, min(ib + kRastChunk - 1, i1), jb, min(jb + kRastChunk - 1, j1));
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, meets);
+            if (!bal) continue;
+            unsigned at = 0u;
+            if (lane == 0) at = atomicAdd(a.big_count, (unsigned)__popc(bal));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            const unsigned cnt = (unsigned)__popc(bal);
+            if (at > (unsigned)a.big_cap || cnt > (unsigned)a.big_cap - at) {
+                if (lane == 0) a.rast_bad[s] = 1;
+                break;
+            }
+            if (meets) a.big[at + __popc(bal & ((1u << lane) - 1u))] = make_int4(s, t, k % cw, k / cw);
+        }
+    }
+}
+
+// Block per listed chunk of a large triangle (grid-stride over the list).
 template <int PASS>
 __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
 {
@@ -688,7 +724,6 @@ __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
         if (!rast_box(V, A, B, C, i0, i1, j0, j1)) continue;
         const int ib = i0 + E.z * kRastChunk, jb = j0 + E.w * kRastChunk;
         const int ie = min(ib + kRastChunk - 1, i1), je = min(jb + kRastChunk - 1, j1);
-        if (!chunk_meets(V, A, B, C, ib, ie, jb, je)) continue;  // uniform over the block
         const int p = part_of_sorted(m, t);
         const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
         const size_t off = (size_t)s * a.ray_stride;
@@ -1275,6 +1310,7 @@ cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
         if (e != cudaSuccess) return e;
         dim3 grid((a.rast_tris + 127) / 128, S);
         k_raster<0><<<grid, 128, 0, st>>>(a);
+        k_raster_chunks<<<kRastBigBlocks / 8, 256, 0, st>>>(a);
         k_raster_big<0><<<kRastBigBlocks, 256, 0, st>>>(a);
         k_raster<1><<<grid, 128, 0, st>>>(a);
         k_raster_big<1><<<kRastBigBlocks, 256, 0, st>>>(a);
