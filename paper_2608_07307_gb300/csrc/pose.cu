@@ -131,29 +131,44 @@ cudaError_t launch_pose(const SlotDesc *sd, const double *sun_dirs, const double
 }
 
 // ------------------------------------------------------------- vertices
-__device__ inline double warp_min(double x)
+constexpr int kVertsPerThread = 4;
+
+__device__ inline unsigned long long warp_min_u64(unsigned long long x)
 {
-    for (int o = 16; o; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y < x ? y : x;
+    }
     return x;
 }
-__device__ inline double warp_max(double x)
+__device__ inline unsigned long long warp_max_u64(unsigned long long x)
 {
-    for (int o = 16; o; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y > x ? y : x;
+    }
     return x;
 }
 
+// kVertsPerThread vertices a thread (strided by the block for coalescing).
+// The window bounds are reduced as order-preserving integer images of the
+// FP64 projections (exact, order independent, and off the slow FP64 pipe).
 __global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *pose)
 {
-    int s = blockIdx.y;
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
     SlotPose &P = pose[s];
     const MeshDev *mesh = sd[s].mesh;
     const SlotBufs &slot = sd[s].sb;
     const int n_verts = mesh->n_verts;
-    if (P.skip || (int)(blockIdx.x * blockDim.x) >= n_verts) return;  // uniform over the block
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    if (k < n_verts) {
-        int p = mesh->vert_part[k];
+    const int k0 = blockIdx.x * blockDim.x * kVertsPerThread;
+    if (P.skip || k0 >= n_verts) return;  // uniform over the block
+    unsigned long long mn[3], mx[3];
+    for (int c = 0; c < 3; c++) { mn[c] = ~0ull; mx[c] = 0ull; }
+    const double *ax[3] = {P.u, P.v, P.d};
+    for (int q = 0; q < kVertsPerThread; q++) {
+        const int k = k0 + q * blockDim.x + threadIdx.x;
+        if (k >= n_verts) break;
+        const int p = mesh->vert_part[k];
         const PartInfo &pi = mesh->part[p];
         double x[3] = {mesh->rest64[3 * k], mesh->rest64[3 * k + 1], mesh->rest64[3 * k + 2]};
         if (pi.dynamic) {
@@ -164,11 +179,12 @@ __global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *
             slot.vert64[o] = y[0]; slot.vert64[o + 1] = y[1]; slot.vert64[o + 2] = y[2];
             x[0] = y[0]; x[1] = y[1]; x[2] = y[2];
         }
-        const double *ax[3] = {P.u, P.v, P.d};
         double pr[3];
         for (int c = 0; c < 3; c++) {
             pr[c] = ax[c][0] * x[0] + ax[c][1] * x[1] + ax[c][2] * x[2];
-            mn[c] = pr[c]; mx[c] = pr[c];
+            const unsigned long long o = dbl_to_ord(pr[c]);
+            mn[c] = o < mn[c] ? o : mn[c];
+            mx[c] = o > mx[c] ? o : mx[c];
         }
         // view-frame position of the vertex for the primary-ray test, rounded once
         slot.vview[k] = make_float4((float)pr[0], (float)pr[1], (float)pr[2], 0.f);
@@ -176,27 +192,31 @@ __global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *
         slot.vview64[3 * (size_t)k + 1] = pr[1];
         slot.vview64[3 * (size_t)k + 2] = pr[2];
     }
-    __shared__ double smn[3][8], smx[3][8];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ unsigned long long smn[3][8], smx[3][8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c = 0; c < 3; c++) {
-        double a = warp_min(mn[c]), b = warp_max(mx[c]);
+        const unsigned long long a = warp_min_u64(mn[c]), b = warp_max_u64(mx[c]);
         if (lane == 0) { smn[c][w] = a; smx[c][w] = b; }
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        int c = threadIdx.x;
-        double a = smn[c][0], b = smx[c][0];
-        for (int i = 1; i < (int)(blockDim.x >> 5); i++) { a = fmin(a, smn[c][i]); b = fmax(b, smx[c][i]); }
+        const int c = threadIdx.x;
+        unsigned long long a = smn[c][0], b = smx[c][0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+            a = smn[c][i] < a ? smn[c][i] : a;
+            b = smx[c][i] > b ? smx[c][i] : b;
+        }
         if (a <= b) {
-            atomicMin(&P.wmin_bits[c], dbl_to_ord(a));
-            atomicMax(&P.wmax_bits[c], dbl_to_ord(b));
+            atomicMin(&P.wmin_bits[c], a);
+            atomicMax(&P.wmax_bits[c], b);
         }
     }
 }
 
 cudaError_t launch_vertices(const SlotDesc *sd, SlotPose *pose, int S, int max_verts, cudaStream_t st)
 {
-    dim3 grid((max_verts + 255) / 256, S);
+    const int per_block = 256 * kVertsPerThread;
+    dim3 grid((max_verts + per_block - 1) / per_block, S);
     k_vertices<<<grid, 256, 0, st>>>(sd, pose);
     return cudaGetLastError();
 }
