@@ -40,9 +40,9 @@ METRIC = "SRP evals/s (200k-triangle spacecraft, 1024^2 rays, 2 specular bounces
 #   + 1 div + 2 compare = 50
 FLOP_BOX, FLOP_TRI = 19, 50
 NODE_BYTES, TRI_BYTES = 128, 48  # one 4-wide BVH node, one FP32 triangle record
-# DRAM bytes (read + write) of one k_trace launch of this workload (2 evaluations),
+# DRAM bytes (read + write) of one k_trace launch of this workload (8 evaluations),
 # from one ncu capture of the current kernel (None until captured)
-TRACE_DRAM_BYTES_PER_LAUNCH = 55.201024e6 + 113.996288e6
+TRACE_DRAM_BYTES_PER_LAUNCH = 196.130048e6 + 168.49792e6
 # FP32 peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -470,7 +470,7 @@ def run_native(a):
                                        "phases add up to more than the step"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / PEAK_FP32_TFLOPS, "traffic": TRACE_DRAM_BYTES_PER_LAUNCH,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one k_trace launch of 2 "
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one k_trace launch of 8 "
                                        "evaluations of this workload (profiles/launches_spacecraft200k_N1024_b2.md)",
                      "kernel": "k_trace", "ms_per_launch": ms_per_launch, "evals_per_launch": evals_per_launch,
                      "flop_per_eval": flop_per_eval,
