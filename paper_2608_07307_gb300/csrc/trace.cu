@@ -795,10 +795,10 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
             }
         }
         for (int seg = 0; seg < nseg; seg++) {
-            ray_setup(r);
             Best32 h;
             float tlo = seg == 0 ? 0.0f : B.eps32;
             nseg_done++;
+            if (seg > 0 || !rast) ray_setup(r);  // the raster's primary segment needs no ray frame
             if (seg == 0 && rast) {
                 // the raster's nearest certain hit; its barycentric weights as the traversal forms them
                 h.t = INFINITY;
@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
                     const Prim32 q = prim_test(__ldg(B.vview + vi.x), __ldg(B.vview + vi.y), __ldg(B.vview + vi.z), uc,
                                                vc, delta, B.w0_32);
                     const float id32 = 1.0f / q.det;
-                    h.t = q.T / q.det;
+                    h.t = q.T * id32;  // not used past this point; the weights are the traversal's
                     h.b1 = q.V * id32;
                     h.b2 = q.W * id32;
                 }
@@ -873,7 +873,8 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
         if (clean) {
             for (int k = 0; k < 6; k++) fac[k] = acc[k];
             cnt[7] = nseg_done;
-            for (int k = 0; k < nseg; k++) cnt[8 + k] = hits[k] >= 0 ? 1u : 0u;
+#pragma unroll
+            for (int k = 0; k <= kMaxBounces; k++) cnt[8 + k] = (k < nseg && hits[k] >= 0) ? 1u : 0u;
             if (a.hits) {
                 int32_t *hq = a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride;
                 for (int k = 0; k < nseg; k++) hq[k] = hits[k];
