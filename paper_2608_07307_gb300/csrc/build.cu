@@ -37,9 +37,12 @@ __global__ void k_morton(const double *rest64, const int *tri_vidx, const int *t
                    rest64[3 * tri_vidx[3 * t + 2] + k];
         c[k] = (float)(s / 3.0);
     }
+    // one scale for all three axes (the part's largest extent): per-axis scaling
+    // would give a thin axis as many code bits as a long one, and the radix tree
+    // would split thin structures (a panel's frame) into overlapping halves
+    const float e = fmaxf(fmaxf(part_ext[3 * p], part_ext[3 * p + 1]), part_ext[3 * p + 2]);
     unsigned q[3];
     for (int k = 0; k < 3; k++) {
-        float e = part_ext[3 * p + k];
         float f = e > 0.f ? (c[k] - part_lo[3 * p + k]) / e : 0.5f;
         f = fminf(fmaxf(f, 0.f), 1.f);
         q[k] = min((unsigned)(f * 1024.f), 1023u);

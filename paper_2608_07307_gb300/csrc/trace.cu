@@ -86,11 +86,15 @@ struct TraceCtx {
     const int2 *grp;  // per sorted triangle: subtree of its coplanar group, deviation bound
     // FP64 window and basis for the FP64 path
     double umin, vmin, wmin, Du, Dv, Lw, eps;
+    double rN;  // 1 / N when N is a power of two (dividing by N is then exactly this product), else 0
     double u[3], v[3], d[3], c_ref[3];
     PartView part[kMaxParts];
 };
 
 size_t trace_ctx_bytes() { return sizeof(TraceCtx); }
+
+// x / N, as a product when N is a power of two (the same value, without an FP64 division)
+__device__ __forceinline__ double pix64(double x, double rN, int N) { return rN != 0.0 ? x * rN : x / N; }
 
 __device__ __forceinline__ float pick(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
 __device__ __forceinline__ double pickd(double x, double y, double z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
@@ -117,6 +121,7 @@ __global__ void k_frame(TraceArgs a)
     double vmin = ord_to_dbl(P.wmin_bits[1]), vmax = ord_to_dbl(P.wmax_bits[1]);
     double wmin = ord_to_dbl(P.wmin_bits[2]), wmax = ord_to_dbl(P.wmax_bits[2]);
     B.umin = umin; B.vmin = vmin; B.wmin = wmin;
+    B.rN = (N & (N - 1)) == 0 ? 1.0 / N : 0.0;
     B.Du = umax - umin; B.Dv = vmax - vmin;
     double Dw = wmax - wmin;
     B.Lw = sqrt(B.Du * B.Du + B.Dv * B.Dv + Dw * Dw);
@@ -976,8 +981,8 @@ __device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, i
 {
     double bt = INFINITY, bU = 0.0, bV = 0.0, bW = 0.0;
     int bp = -1, btl = -1, bo = 0x7fffffff;
-    const double uc = B.umin + ((double)i + 0.5) * B.Du / N;
-    const double vc = B.vmin + ((double)j + 0.5) * B.Dv / N;
+    const double uc = B.umin + pix64(((double)i + 0.5) * B.Du, B.rN, N);
+    const double vc = B.vmin + pix64(((double)j + 0.5) * B.Dv, B.rN, N);
     const double w0 = B.wmin - kStandoff;
     Ray64 r;
     double tlo = 0.0;
@@ -1136,8 +1141,8 @@ __device__ void refine_ray(const TraceCtx &B, const TraceArgs &a, int s, int ray
     const int N = a.sd[s].N, nseg = a.sd[s].nseg;
     int i = ray / N, j = ray % N;
     Ray64 r;
-    double uc = B.umin + ((double)i + 0.5) * B.Du / N;
-    double vc = B.vmin + ((double)j + 0.5) * B.Dv / N;
+    double uc = B.umin + pix64(((double)i + 0.5) * B.Du, B.rN, N);
+    double vc = B.vmin + pix64(((double)j + 0.5) * B.Dv, B.rN, N);
     double w0 = B.wmin - kStandoff;
     for (int k = 0; k < 3; k++) { r.o[k] = uc * B.u[k] + vc * B.v[k] + w0 * B.d[k]; r.d[k] = B.d[k]; }
     double wgt = 1.0;
