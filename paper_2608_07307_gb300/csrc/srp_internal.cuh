@@ -179,9 +179,9 @@ struct TraceArgs {
 };
 constexpr int kPixCand = 2;      // uncertain triangles kept per pixel (more: the ray traverses)
 constexpr int kRastSmall = 64;   // largest pixel box one thread rasterises
-constexpr int kRastChunk = 32;   // larger triangles: chunks of 32 x 32 pixels, one block each
-constexpr int kRastBigBlocks = 2048;  // k_raster_big grid: about one listed chunk per block
-constexpr int kBigPerSlot = 8192;  // chunk-list entries reserved per slot
+constexpr int kRastChunk = 16;   // larger triangles: chunks of 16 x 16 pixels, one warp each
+constexpr int kRastBigBlocks = 2048;  // k_raster_big grid (8 warps a block, one listed chunk a warp)
+constexpr int kBigPerSlot = 65536;  // chunk-list entries reserved per slot
 size_t trace_ctx_bytes();
 
 // Propagation settings as seen by the device (from srp_prop_params).

@@ -634,8 +634,8 @@ __device__ __forceinline__ int part_of_sorted(const MeshDev *m, int t)
 }
 
 // Thread per (slot, sorted triangle): small projected boxes in place; larger
-// ones are split into chunks of 32 x 32 pixels listed for k_raster_big (pass 0
-// lists them, pass 1 reuses the list).
+// ones are listed for k_raster_chunks, which lists their 16 x 16-pixel chunks
+// that can meet them for k_raster_big (pass 0 lists, pass 1 reuses the lists).
 template <int PASS>
 __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
 {
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
             rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);
 }
 
-// Warp per listed large triangle: its 32 x 32-pixel chunks that can meet it,
+// Warp per listed large triangle: its 16 x 16-pixel chunks that can meet it,
 // tested a chunk per lane and appended with one atomic per warp pass.
 __global__ void __launch_bounds__(256) k_raster_chunks(TraceArgs a)
 {
@@ -713,12 +713,13 @@ __global__ void __launch_bounds__(256) k_raster_chunks(TraceArgs a)
     }
 }
 
-// Block per listed chunk of a large triangle (grid-stride over the list).
+// Warp per listed chunk of a large triangle (grid-stride over the list).
 template <int PASS>
 __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
 {
     const unsigned n = min(__ldcg(a.big_count), (unsigned)a.big_cap);
-    for (unsigned e = blockIdx.x; e < n; e += gridDim.x) {
+    const unsigned lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x >> 5);
+    for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) {
         const int4 E = a.big[e];
         const int s = E.x, t = E.y;
         const MeshDev *m = a.sd[s].mesh;
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
         const int p = part_of_sorted(m, t);
         const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
         const size_t off = (size_t)s * a.ray_stride;
-        for (int q = threadIdx.x; q < kRastChunk * kRastChunk; q += blockDim.x) {
+        for (int q = (int)lane; q < kRastChunk * kRastChunk; q += 32) {
             const int i = ib + q / kRastChunk, j = jb + q % kRastChunk;
             if (i <= ie && j <= je)
                 rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);

@@ -38,7 +38,7 @@ def _fan(k=16):
                   **I._parts(1, [-1]), name="fan")
 
 
-def _stack(n=150):
+def _stack(n=600):
     b = I._Builder()
     for k in range(n):
         v = np.array([[-1.0, -1.0, 0.01 * k], [1.0, -1.0, 0.01 * k], [1.0, 1.0, 0.01 * k], [-1.0, 1.0, 0.01 * k]])
