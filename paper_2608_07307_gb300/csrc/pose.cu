@@ -4,13 +4,13 @@
 //               commanded, or tracking + offset; clamped), part transforms
 //               composed down the kinematic tree (Sec. 4.4.1), image-plane
 //               basis, window accumulators reset.
-//   k_vertices  one thread per vertex and slot: posed FP64 position of dynamic
+//   k_vertices  four vertices a thread, per slot: posed FP64 position of dynamic
 //               vertices; FP64 projections on (u, v, d) reduced to the window
 //               min / max (exact, order independent).
 //   k_refit     one thread per triangle of the refitted parts: FP32 triangle
 //               record from the posed FP64 vertices, leaf box, then bottom-up
-//               box refit: the second child to arrive at a node (counted with
-//               an atomic whose parity flips twice per pass) fits the parent.
+//               refit of the 4-wide nodes: the last child to arrive at a node
+//               (an acquire-release counter it resets) fits the parent.
 #include <math.h>
 
 #include "srp_internal.cuh"
@@ -222,6 +222,13 @@ cudaError_t launch_vertices(const SlotDesc *sd, SlotPose *pose, int S, int max_v
 }
 
 // ---------------------------------------------------------------- refit
+__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // Thread per sorted triangle: the static parts of one mesh (sd == null, at
 // load) or the dynamic parts of every slot's mesh.
 __global__ void __launch_bounds__(256) k_refit(const SlotDesc *sd, const SlotPose *pose, const MeshDev *static_mesh,
@@ -299,11 +306,11 @@ __global__ void __launch_bounds__(256) k_refit(const SlotDesc *sd, const SlotPos
         f[16 + slot] = box[2];
         f[20 + slot] = box[5];
         const int4 meta = *reinterpret_cast<const int4 *>(nd + 7);  // parent, slot in it, children
-        __threadfence();
-        unsigned old = atomicAdd(cnt + node, 1u);
+        // release: the box above is visible to whoever arrives last; acquire: the
+        // last arrival sees every sibling's box
+        const unsigned old = atomic_add_acq_rel(cnt + node, 1u);
         if (old + 1u < (unsigned)meta.z) return;  // a sibling still has to arrive
         cnt[node] = 0u;
-        __threadfence();
         float4 c[6];
         for (int k = 0; k < 6; k++) c[k] = __ldcg(nd + k);
         box[0] = fminf(fminf(c[0].x, c[0].y), fminf(c[0].z, c[0].w));
