@@ -42,7 +42,10 @@ FLOP_BOX, FLOP_TRI = 19, 50
 NODE_BYTES, TRI_BYTES = 128, 48  # one 4-wide BVH node, one FP32 triangle record
 # DRAM bytes (read + write) of one k_trace launch of this workload (8 evaluations),
 # from one ncu capture of the current kernel (None until captured)
-TRACE_DRAM_BYTES_PER_LAUNCH = 196.130048e6 + 168.49792e6
+TRACE_DRAM_BYTES_PER_LAUNCH = 179.927552e6 + 53.48224e6
+# the same capture's unit throughputs, % of the GB300's peak for each unit
+TRACE_NCU_PCT_OF_PEAK = {"l1tex": 64.8, "l2": 31.0, "dram": 3.8, "sm_issue_active": 60.5,
+                         "l2_bytes_per_launch": 4.699e9, "l1_bytes_per_launch": 6.048e9}
 # FP32 peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -477,7 +480,8 @@ def run_native(a):
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
         "roofline_l2": {"algorithmic_bytes_per_eval": bytes_per_eval, "achieved_gbs": l2_gbs,
                         "note": "4-wide node (128 B) and triangle (48 B) fetches per eval of the trace's "
-                                "traversals; served mostly by L1/L2"},
+                                "traversals; served mostly by L1/L2",
+                        "ncu_k_trace_pct_of_peak": TRACE_NCU_PCT_OF_PEAK},
         "gpu_launches": launches,
         "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": B * 3 * 8,
                 "d2h_bytes_per_step": B * 6 * 8},
