@@ -2,7 +2,8 @@
 //
 // Layout in HBM (one mesh):
 //   * triangles are sorted part-major (static parts first, then parts whose
-//     pose depends on a joint angle), Morton order within a part;
+//     pose depends on a joint angle), then by coplanar group, then in Morton
+//     order (one scale for all three axes of the part);
 //   * each part has its own LBVH over its triangles, built as a binary radix
 //     tree and collapsed to 4-wide nodes of 128 B (four child boxes as six
 //     float4 in SoA order, four child refs, parent / slot / child count);

@@ -5,22 +5,33 @@
 // FP32 ray generation, the error bounds of the FP32 decisions and the
 // per-part traversal views, into a small context every trace block copies.
 //
-// k_trace (FP32 fast path).  A block is one warp over a 32-pixel tile (8 x 4
-// by default; the shape is chosen per mesh, grid and bounce count by the
-// autotuner), so no warp ever waits for another: the hardware block scheduler
-// balances the load at 32-ray granularity.  The tiles of every slot of a
-// launch form one flat grid, so one launch can trace different meshes, grid
-// sizes and bounce counts.  Per segment: stack traversal of each part's
-// binary LBVH (64 B nodes fetched as four float4; child boxes slab-tested
-// against the segment's current best t) with the watertight ray/triangle test
-// (Woop, Benthin and Wald, "Watertight ray/triangle intersection", JCGT 2(1),
-// 2013):
+// k_raster / k_raster_big / k_raster_chunks (primary visibility).  All primary
+// rays of an evaluation are parallel, so each triangle applies the trace's own
+// FP32 view-frame test (prim_test) to the pixel centres inside its projected
+// box: pass 0 keeps the nearest certain hit per pixel (64-bit atomic minimum of
+// depth bits and triangle), pass 1 lists the triangles whose decision there was
+// uncertain against it.  Large projected triangles are rasterised in 16 x 16
+// pixel chunks, a warp each, listing only the chunks that can meet them.
+//
+// k_trace (FP32 fast path).  A block is four warps, each over a 32-pixel tile
+// (8 x 4 by default; the shape is chosen per mesh, grid and bounce count by the
+// autotuner), sharing one copy of the slot context.  The tiles of every slot of
+// a launch form one flat grid, so one launch can trace different meshes, grid
+// sizes and bounce counts.  The primary segment takes the raster's nearest
+// certain hit and candidates (a pixel with too many candidates, or every pixel
+// when rasterisation is off, traverses instead).  Every traversed segment walks
+// each part's 4-wide BVH (128 B nodes: six float4 of child boxes in SoA order,
+// the near and far planes picked by the ray's octant, and the child refs),
+// parts in the order the ray enters their root boxes, with the watertight
+// ray/triangle test (Woop, Benthin and Wald, "Watertight ray/triangle
+// intersection", JCGT 2(1), 2013):
 //   * primary rays share the direction d, so their test runs in the view frame
 //     (u, v, d): per-vertex projections computed in FP64 and rounded once to
 //     FP32, the ray is the line through the pixel centre (uc, vc) along the
 //     third axis, and the watertight shear vanishes;
 //   * secondary (specular) rays use the world-frame test with the shear; their
-//     origin is rebuilt from the hit's barycentric weights.
+//     origin is rebuilt from the hit's barycentric weights, and they pass over
+//     the subtree of their origin's coplanar group.
 // Every FP32 decision carries an error bound: when an edge function, the
 // nearest-hit comparison or the self-hit threshold is within its bound, the
 // triangle is settled in FP64 at the end of the segment (resolve64); only a ray
@@ -28,8 +39,8 @@
 // nothing here.  Per hit:
 // absorbed + specular + Lambertian momentum, torque about c_ref, specular ray
 // of weight w rho_s.  Per-ray sums in FP32 (at most 1 + bounces terms), tile
-// sums in FP64 by warp shuffles, one FP64 partial per tile; the tile's
-// handed-off rays go to its own list slot.
+// sums by an FP32 butterfly and integer reductions, one partial per tile; the
+// tile's handed-off rays go to its own list slot.
 //
 // resolve64 (FP64, inside k_trace).  When a segment had FP32 decisions within
 // their bounds, its uncertain triangles and its nearest certain hit are tested
