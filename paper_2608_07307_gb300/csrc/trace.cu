@@ -314,6 +314,20 @@ struct Prim32 {
     float U, V, W, eU, eV, eW, det, T;
 };
 
+// The edge functions, determinant and scaled depth without the bounds.
+__device__ __forceinline__ Prim32 prim_core(float4 a, float4 b, float4 c, float uc, float vc, float w0)
+{
+    Prim32 q;
+    float Ax = a.x - uc, Ay = a.y - vc, Bx = b.x - uc, By = b.y - vc, Cx = c.x - uc, Cy = c.y - vc;
+    q.U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    q.V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    q.W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    q.eU = q.eV = q.eW = 0.0f;
+    q.det = q.U + q.V + q.W;
+    q.T = fmaf(q.U, a.z - w0, fmaf(q.V, b.z - w0, q.W * (c.z - w0)));
+    return q;
+}
+
 __device__ __forceinline__ Prim32 prim_test(float4 a, float4 b, float4 c, float uc, float vc, float delta, float w0)
 {
     const float u4 = 4.0f * kU;
@@ -607,17 +621,40 @@ __device__ __forceinline__ bool chunk_meets(const RastView &V, float4 a, float4 
     return true;
 }
 
+// An upper bound, over the pixel centres [i0, i1] x [j0, j1], of the error
+// bounds prim_test forms for the triangle: every coordinate relative to a
+// centre is at most xm (u) or ym (v) in size, and FP32 rounding is monotone.
+__device__ __forceinline__ float rast_bound(const RastView &V, float4 a, float4 b, float4 c, int i0, int i1, int j0,
+                                            int j1)
+{
+    const float u0 = fmaf((float)i0 + 0.5f, V.du32, V.umin32), u1 = fmaf((float)i1 + 0.5f, V.du32, V.umin32);
+    const float v0 = fmaf((float)j0 + 0.5f, V.dv32, V.vmin32), v1 = fmaf((float)j1 + 0.5f, V.dv32, V.vmin32);
+    const float xm = fmaxf(fmaxf(fmaxf(fabsf(a.x - u0), fabsf(a.x - u1)), fmaxf(fabsf(b.x - u0), fabsf(b.x - u1))),
+                           fmaxf(fabsf(c.x - u0), fabsf(c.x - u1)));
+    const float ym = fmaxf(fmaxf(fmaxf(fabsf(a.y - v0), fabsf(a.y - v1)), fmaxf(fabsf(b.y - v0), fabsf(b.y - v1))),
+                           fmaxf(fabsf(c.y - v0), fabsf(c.y - v1)));
+    return (V.delta * (2.0f * xm + 2.0f * ym) + 4.0f * kU * (2.0f * xm * ym)) * 1.001f;
+}
+
+// One (triangle, pixel centre) pair.  E bounds the pair's error bounds: a
+// decision certain against E is certain against them, so the exact bounds are
+// formed only near an edge; the decisions are those of prim_test.
 template <int PASS>
 __device__ __forceinline__ void rast_pixel(const RastView &V, unsigned long long *key, unsigned *cnt, unsigned *cand,
-                                           int i, int j, float4 a, float4 b, float4 c, unsigned id)
+                                           int i, int j, float4 a, float4 b, float4 c, unsigned id, float E)
 {
     const float uc = fmaf((float)i + 0.5f, V.du32, V.umin32);
     const float vc = fmaf((float)j + 0.5f, V.dv32, V.vmin32);
-    const Prim32 q = prim_test(a, b, c, uc, vc, V.delta, V.w0);
-    const bool neg = (q.U < -q.eU) || (q.V < -q.eV) || (q.W < -q.eW);
-    const bool pos = (q.U > q.eU) || (q.V > q.eV) || (q.W > q.eW);
-    if (neg && pos) return;  // certainly outside
-    const bool unsure = fabsf(q.U) <= q.eU || fabsf(q.V) <= q.eV || fabsf(q.W) <= q.eW;
+    Prim32 q = prim_core(a, b, c, uc, vc, V.w0);
+    if (((q.U < -E) || (q.V < -E) || (q.W < -E)) && ((q.U > E) || (q.V > E) || (q.W > E))) return;
+    bool unsure = false;
+    if (!(fabsf(q.U) > E && fabsf(q.V) > E && fabsf(q.W) > E)) {
+        q = prim_test(a, b, c, uc, vc, V.delta, V.w0);
+        const bool neg = (q.U < -q.eU) || (q.V < -q.eV) || (q.W < -q.eW);
+        const bool pos = (q.U > q.eU) || (q.V > q.eV) || (q.W > q.eW);
+        if (neg && pos) return;  // certainly outside
+        unsure = fabsf(q.U) <= q.eU || fabsf(q.V) <= q.eV || fabsf(q.W) <= q.eW;
+    }
     const float t = q.T / q.det;
     const size_t px = (size_t)i * V.N + j;
     if (PASS == 0) {
@@ -681,9 +718,10 @@ __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
     const int p = part_of_sorted(m, t);
     const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
     const size_t off = (size_t)s * a.ray_stride;
+    const float eb = rast_bound(V, A, B, C, i0, i1, j0, j1);
     for (int i = i0; i <= i1; i++)
         for (int j = j0; j <= j1; j++)
-            rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);
+            rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id, eb);
 }
 
 // Warp per listed large triangle: its 16 x 16-pixel chunks that can meet it,
@@ -744,10 +782,12 @@ __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
         const int p = part_of_sorted(m, t);
         const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
         const size_t off = (size_t)s * a.ray_stride;
+        const float eb = rast_bound(V, A, B, C, ib, ie, jb, je);
         for (int q = (int)lane; q < kRastChunk * kRastChunk; q += 32) {
             const int i = ib + q / kRastChunk, j = jb + q % kRastChunk;
             if (i <= ie && j <= je)
-                rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id);
+                rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id,
+                                 eb);
         }
     }
 }
