@@ -821,10 +821,7 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
     const int ray = i * N + j;
     if (i < N && j < N) {
         Ray32 r;
-        for (int k = 0; k < 3; k++) {
-            r.o[k] = fmaf((float)i + 0.5f, B.du[k], fmaf((float)j + 0.5f, B.dv[k], B.org[k]));
-            r.d[k] = B.dir[k];
-        }
+        for (int k = 0; k < 3; k++) r.d[k] = B.dir[k];
         const float uc = fmaf((float)i + 0.5f, B.du32, B.umin32);
         const float vc = fmaf((float)j + 0.5f, B.dv32, B.vmin32);
         float wgt = 1.0f;
@@ -855,6 +852,8 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
             Best32 h;
             float tlo = seg == 0 ? 0.0f : B.eps32;
             nseg_done++;
+            if (seg == 0 && !rast)  // a traversed primary segment starts at its pixel on the window
+                for (int k = 0; k < 3; k++) r.o[k] = fmaf((float)i + 0.5f, B.du[k], fmaf((float)j + 0.5f, B.dv[k], B.org[k]));
             if (seg > 0 || !rast) ray_setup(r);  // the raster's primary segment needs no ray frame
             if (seg == 0 && rast) {
                 // the raster's nearest certain hit; its barycentric weights as the traversal forms them
@@ -866,8 +865,8 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
                     h.part = (int)(id >> 24);
                     h.tl = (int)(id & 0xffffffu);
                     const int4 vi = __ldg(B.part[h.part].v4 + h.tl);
-                    const Prim32 q = prim_test(__ldg(B.vview + vi.x), __ldg(B.vview + vi.y), __ldg(B.vview + vi.z), uc,
-                                               vc, delta, B.w0_32);
+                    const Prim32 q = prim_core(__ldg(B.vview + vi.x), __ldg(B.vview + vi.y), __ldg(B.vview + vi.z), uc,
+                                               vc, B.w0_32);
                     const float id32 = 1.0f / q.det;
                     h.t = q.T * id32;  // not used past this point; the weights are the traversal's
                     h.b1 = q.V * id32;
