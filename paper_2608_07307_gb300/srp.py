@@ -24,6 +24,7 @@ EVAL_TIMING = 2
 EVAL_TRAVERSE = 8  # primary hits by BVH traversal instead of rasterisation (same results)
 EVAL_AUTOTUNE = 4
 MAX_BOUNCES = 4
+MAX_N = 8192  # SRP_MAX_N: rays per window side
 
 # Symbols declared in include/srp.h (checked by the tests against the library).
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",

@@ -272,3 +272,31 @@ def test_coplanar_groups_keep_same_part_hits(ctx):
     ctx.eval_batch(jid, dirs, N=N, bounces=B, count=True)
     broken = ctx.eval_stats()["nodes_visited"]
     assert grouped < 0.8 * broken, (grouped, broken)
+
+
+def test_maximum_grid_and_bounces(ctx):
+    """The largest window (SRP_MAX_N rays a side, 67 M rays; the plate's four
+    window-sized triangles give more chunks than the raster's list holds, so
+    the pixels traverse) keeps the flat plate's closed form, and the largest
+    bounce count equals two bounces on the V-trough, whose rays leave after
+    two."""
+    from paper_2608_07307_gb300 import srp
+    mat = ((0.3, 0.2), (0.1, 0.4))
+    m = I.flat_plate(2.0, 1.0, mat=mat)
+    mid = ctx.load_mesh(m)
+    th = 0.7
+    s = np.array([[math.sin(th), 0, math.cos(th)]])
+    F, T = ctx.eval_batch(mid, s, N=srp.MAX_N, bounces=0)
+    c = math.cos(th)
+    Fcf = -P0 * 2.0 * c * ((1 - 0.3) * s[0] + 2 * (0.3 * c + 0.2 / 3) * np.array([0, 0, 1.0]))
+    assert np.linalg.norm(F[0] - Fcf) < 1e-6 * np.linalg.norm(Fcf)
+    ctx.free_mesh(mid)
+    v = I.v_trough(1.0, 1.5, mat=((0.7, 0.1),))
+    vid = ctx.load_mesh(v)
+    d = np.array([[0.1, 0.05, 1.0]])
+    F2, T2 = ctx.eval_batch(vid, d, N=256, bounces=2)
+    F4, T4 = ctx.eval_batch(vid, d, N=256, bounces=srp.MAX_BOUNCES)
+    assert np.array_equal(F2, F4) and np.array_equal(T2, T4)
+    st = ctx.eval_stats()
+    assert st["hits"][3] == 0 and st["hits"][4] == 0 and st["hits"][1] > 0
+    ctx.free_mesh(vid)
