@@ -2054,7 +2054,9 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     srp_status rc = capture(na);
     if (rc) return rc;
     const int poll_max = p->poll > 0 ? p->poll : 16;
-    const int per_step = nstage * (p->srp ? 10 : 2) + 1;
+    // per stage: stage and acceleration, plus pose, vertices, refit, frame, the
+    // raster passes, trace and two reduction levels when the SRP runs; then step control
+    const int per_step = nstage * (2 + (p->srp ? 7 + (raster ? 5 : 0) : 0)) + 1;
     for (int64_t round = 0; round < p->max_steps + 2 && na > 0; round++) {
         int done = 0;
         CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));
