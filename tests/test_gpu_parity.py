@@ -300,3 +300,30 @@ def test_maximum_grid_and_bounces(ctx):
     st = ctx.eval_stats()
     assert st["hits"][3] == 0 and st["hits"][4] == 0 and st["hits"][1] > 0
     ctx.free_mesh(vid)
+
+
+def test_headline_size_sampled_rays(ctx):
+    """The 200k-triangle spacecraft at 1024^2 rays and 2 bounces, 32 Fibonacci
+    directions in one call (the benchmark's launch configuration: chunks of
+    eight evaluations over four lanes, rasterised primaries): per-ray hit ids
+    of sampled rays of two directions against the oracle traced ray by
+    ray (2048 a direction: about 20 s of single-threaded oracle work each).
+    Mismatches only at edges (R13)."""
+    m = I.spacecraft(0.025)
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_fibonacci(4096)[:32]
+    N, B = 1024, 2
+    F, T, H = ctx.eval_batch(mid, dirs, N=N, bounces=B, hits=True)
+    rng = np.random.default_rng(5)
+    for k in (0, 17):
+        rays = np.sort(rng.choice(N * N, size=2048, replace=False))
+        r = O.eval_rays(m, dirs[k], rays, N, B)
+        L = O.evaluate(m, dirs[k], 1, 0)["win"][6]
+        gh = np.asarray(H[k])[rays]
+        diff = np.nonzero((gh != r["hits"]).any(axis=1))[0]
+        for q in diff:
+            seg = int(np.argmax(gh[q] != r["hits"][q]))
+            assert r["edge"][q, seg] < 1e-6 * L, (k, rays[q], gh[q], r["hits"][q])
+        assert len(diff) <= 1, (k, len(diff))
+        assert (r["hits"][:, 0] >= 0).sum() > 1000
+    ctx.free_mesh(mid)
