@@ -327,3 +327,41 @@ def test_headline_size_sampled_rays(ctx):
         assert len(diff) <= 1, (k, len(diff))
         assert (r["hits"][:, 0] >= 0).sum() > 1000
     ctx.free_mesh(mid)
+
+
+def _fullsize_golden():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_forces.txt")
+    rows = []
+    with open(path) as f:
+        for ln in f:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            v = ln.split()
+            rows.append((float(v[0]), int(v[1]), int(v[2]), int(v[3]), np.array([float(x) for x in v[4:10]])))
+    return rows
+
+
+def test_fullsize_forces_against_stored_oracle():
+    """Whole evaluations at the benchmark sizes (the ~50k-triangle precision
+    form and the ~200k-triangle headline, 1024^2 rays, 2 bounces), each inside
+    a call of 32 Fibonacci directions: force and torque within 1e-4 of the
+    oracle's values stored by tests/golden/make_fullsize.py (R14 for torque)."""
+    from paper_2608_07307_gb300 import srp
+    rows = _fullsize_golden()
+    dirs = I.sun_dirs_fibonacci(4096)
+    with srp.Context(0) as c:
+        for h in sorted({r[0] for r in rows}):
+            m = I.spacecraft(h)
+            mid = c.load_mesh(m)
+            mine = [r for r in rows if r[0] == h]
+            N, B = mine[0][1], mine[0][2]
+            ks = [r[3] for r in mine]
+            batch = np.concatenate([dirs[ks], dirs[:32 - len(ks)]])
+            F, T = c.eval_batch(mid, batch, N=N, bounces=B)
+            for q, r in enumerate(mine):
+                Fo, To = r[4][:3], r[4][3:]
+                fn = np.linalg.norm(Fo)
+                assert np.linalg.norm(F[q] - Fo) <= 1e-4 * fn, (h, r[3], F[q], Fo)
+                assert np.linalg.norm(T[q] - To) <= 1e-4 * max(np.linalg.norm(To), fn), (h, r[3], T[q], To)
+            c.free_mesh(mid)
