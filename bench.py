@@ -46,6 +46,8 @@ TRACE_DRAM_BYTES_PER_LAUNCH = 177.726464e6 + 49.465344e6
 # the same capture's unit throughputs, % of the GB300's peak for each unit
 TRACE_NCU_PCT_OF_PEAK = {"l1tex": 62.2, "l2": 27.9, "dram": 3.5, "sm_issue_active": 62.4,
                          "l2_bytes_per_launch": 4.476e9, "l1_bytes_per_launch": 6.018e9}
+# L2 bandwidth implied by that capture: L2 bytes / (L2 throughput % / 100) / duration
+L2_PEAK_GBS = 4.476e9 / 0.279 / 812.48e-6 / 1e9
 # FP32 peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -479,6 +481,8 @@ def run_native(a):
                      "flop_per_eval": flop_per_eval,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
         "roofline_l2": {"algorithmic_bytes_per_eval": bytes_per_eval, "achieved_gbs": l2_gbs,
+                        "peak_gbs": L2_PEAK_GBS, "frac": l2_gbs / L2_PEAK_GBS,
+                        "peak_source": "implied by the ncu capture: lts__t_bytes / L2 throughput % / duration",
                         "note": "4-wide node (128 B) and triangle (48 B) fetches per eval of the trace's "
                                 "traversals; served mostly by L1/L2",
                         "ncu_k_trace_pct_of_peak": TRACE_NCU_PCT_OF_PEAK},
