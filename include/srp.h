@@ -356,7 +356,8 @@ typedef struct {
  *   params  shared settings: method, j2, sun3, srp, epoch, tolerances, h0,
  *           h_min, h_max, max_steps, poll, eval.P0, eval.eps_rel; eval.flags may
  *           hold SRP_EVAL_AUTOTUNE (tune the tile shape of every new (mesh, N,
- *           bounces) key first, see srp_autotune).  Its central, attitude, q,
+ *           bounces) key first, see srp_autotune) and SRP_EVAL_TRAVERSE (primary
+ *           hits by traversal, as for srp_eval_batch).  Its central, attitude, q,
  *           eval.N, eval.bounces, eval.panel_mode, h_replay and host_loop are
  *           ignored: each srp_traj supplies its own.
  *   traj    [n] host

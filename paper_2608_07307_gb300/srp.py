@@ -308,7 +308,7 @@ class Context:
                   atol_vel: float = 1e-9, h0: float = 60.0, h_min: float = 1e-6, h_max: float = 0.0,
                   max_steps: int = 10_000_000, poll: int = 16, N: int = 64, bounces: int = 1, P0: float = 4.56e-6,
                   eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, h_cap: int = 0, h_replay=None,
-                  host_loop: bool = False):
+                  host_loop: bool = False, traverse: bool = False):
         """srp_propagate: y1 [n, 6], per-trajectory stats (list of dicts) and,
         with h_cap > 0, the accepted step sizes [n, h_cap] (NaN padded).
         h_replay [n, k]: take exactly these RKF7(8) steps (replay)."""
@@ -318,7 +318,7 @@ class Context:
         hr = None if h_replay is None else np.ascontiguousarray(np.asarray(h_replay, np.float64).reshape(n, -1))
         p = PropParams(method, central, int(j2), int(sun3), int(srp_on), attitude, (C.c_double * 4)(*q),
                        epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, int(host_loop),
-                       EvalParams(N, bounces, P0, eps_rel, panel_mode, 0),
+                       EvalParams(N, bounces, P0, eps_rel, panel_mode, EVAL_TRAVERSE if traverse else 0),
                        hr.ctypes.data if hr is not None else None, 0 if hr is None else hr.shape[1])
         y1 = np.empty((n, 6))
         st = (PropStats * n)()
@@ -396,7 +396,7 @@ class Context:
                         epoch_mjd_tt: float = 61041.0, rtol: float = 1e-12, atol_pos: float = 1e-6,
                         atol_vel: float = 1e-9, h0: float = 60.0, h_min: float = 1e-6, h_max: float = 0.0,
                         max_steps: int = 10_000_000, poll: int = 16, P0: float = 4.56e-6, eps_rel: float = 1e-9,
-                        autotune: bool = False):
+                        autotune: bool = False, traverse: bool = False):
         """srp_propagate_batch over a list of trajectory dicts with keys mesh_id,
         N, bounces, panel_mode, angles (or None), central, attitude, q, y0, t0,
         t1.  Returns (y1 [n, 6], stats list)."""
@@ -413,7 +413,8 @@ class Context:
                           (C.c_double * 6)(*[float(x) for x in t["y0"]]), float(t["t0"]), float(t["t1"]))
         p = PropParams(method, 0, int(j2), int(sun3), int(srp_on), 0, (C.c_double * 4)(1.0, 0.0, 0.0, 0.0),
                        epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, 0,
-                       EvalParams(1, 0, P0, eps_rel, 0, EVAL_AUTOTUNE if autotune else 0), None, 0)
+                       EvalParams(1, 0, P0, eps_rel, 0, (EVAL_AUTOTUNE if autotune else 0)
+                                  | (EVAL_TRAVERSE if traverse else 0)), None, 0)
         y1 = np.empty((n, 6))
         st = (PropStats * n)()
         self._check(self.lib.srp_propagate_batch(self.h, C.byref(p), n, arr, y1.ctypes.data, st))
