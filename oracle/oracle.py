@@ -23,7 +23,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["srp_oracle.c", "frozen_oracle.c", "prop_oracle.c"]
+SOURCES = ["srp_oracle.c", "frozen_oracle.c", "prop_oracle.c", "spad_oracle.c"]
 HEADERS = ["srp_oracle.h"]
 LIB = os.path.join(BUILD, "liboracle.so")
 
@@ -338,14 +338,27 @@ class Prop(C.Structure):
         ("N", C.c_int32), ("bounces", C.c_int32), ("P0", C.c_double), ("eps_rel", C.c_double),
         ("method", C.c_int32), ("rtol", C.c_double), ("atol_pos", C.c_double), ("atol_vel", C.c_double),
         ("h0", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double), ("max_steps", C.c_int64),
+        ("spad_table", C.POINTER(C.c_double)), ("spad_n_az", C.c_int32), ("spad_n_el", C.c_int32),
+        ("spad_az0", C.c_double), ("spad_el0", C.c_double), ("spad_d_el", C.c_double),
     ]
 
 
 def prop_params(central=0, j2=False, sun3=False, srp=False, attitude=0, q=(1.0, 0.0, 0.0, 0.0),
                 epoch_mjd_tt=61041.0, mass=1000.0, N=64, bounces=1, P0=4.56e-6, eps_rel=1e-9, method=0,
-                rtol=1e-12, atol_pos=1e-6, atol_vel=1e-9, h0=60.0, h_min=1e-6, h_max=0.0, max_steps=10_000_000):
-    return Prop(central, int(j2), int(sun3), int(srp), attitude, (C.c_double * 4)(*q), epoch_mjd_tt, mass, N,
-                bounces, P0, eps_rel, method, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps)
+                rtol=1e-12, atol_pos=1e-6, atol_vel=1e-9, h0=60.0, h_min=1e-6, h_max=0.0, max_steps=10_000_000,
+                spad=None):
+    """spad = (grid, table): the SRP force comes from the SPAD interpolant
+    (spad_interp) of `table` instead of the ray tracer."""
+    pp = Prop(central, int(j2), int(sun3), int(srp), attitude, (C.c_double * 4)(*q), epoch_mjd_tt, mass, N,
+              bounces, P0, eps_rel, method, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps)
+    if spad is not None:
+        g, tab = spad
+        tab = np.ascontiguousarray(np.asarray(tab, np.float64).reshape(g["n_el"], g["n_az"], 6))
+        pp._spad_keep = tab
+        pp.spad_table = _dp(tab)
+        pp.spad_n_az, pp.spad_n_el = g["n_az"], g["n_el"]
+        pp.spad_az0, pp.spad_el0, pp.spad_d_el = g["az0"], g["el0"], g["d_el"]
+    return pp
 
 
 def rkf78_tableau():
@@ -497,3 +510,42 @@ def arc_frozen_grad(mesh, pp, t0, t1, y0, lam, offsets=None, angles=None, h=1e-6
         qm.q[c] -= h
         g_q[c] = (L(pp_=qp) - L(pp_=qm)) / (2 * h)
     return dict(y0=g_y0, mat=g_mat, angle=g_ang, q=g_q, y1=y1, record=rec)
+
+
+# ------------------------------------------------ SPAD interpolation (Sec. 6)
+def spad_dirs(grid):
+    """Body-frame Sun directions of the SPAD samples, [n_el][n_az][3]."""
+    n_az, n_el = grid["n_az"], grid["n_el"]
+    out = np.zeros((n_el, n_az, 3))
+    for j in range(n_el):
+        for i in range(n_az):
+            s = np.zeros(3)
+            lib().orc_spad_dir(C.c_int32(n_az), C.c_double(grid["az0"]), C.c_double(grid["el0"]),
+                               C.c_double(grid["d_el"]), C.c_int32(i), C.c_int32(j), _dp(s))
+            out[j, i] = s
+    return out
+
+
+def spad_table(mesh, grid, N, bounces=1, P0=4.56e-6, eps_rel=1e-9, procs=1):
+    """The SPAD table: force and torque of `evaluate` at 1 AU for every
+    sample direction, [n_el][n_az][6]."""
+    d = spad_dirs(grid)
+    tab = np.zeros(d.shape[:2] + (6,))
+    for j in range(d.shape[0]):
+        for i in range(d.shape[1]):
+            r = evaluate(mesh, d[j, i], N, bounces, P0=P0, dist_au=1.0, eps_rel=eps_rel, procs=procs)
+            tab[j, i, :3], tab[j, i, 3:] = r["F"], r["T"]
+    return tab
+
+
+def spad_interp(grid, table, s, dist_au=1.0):
+    """Bilinear SPAD interpolant at body-frame direction s: [F (3), T (3)]."""
+    tab = np.ascontiguousarray(np.asarray(table, np.float64).reshape(grid["n_el"], grid["n_az"], 6))
+    s = np.ascontiguousarray(np.asarray(s, np.float64))
+    out = np.zeros(6)
+    rc = lib().orc_spad_interp(C.c_int32(grid["n_az"]), C.c_int32(grid["n_el"]), C.c_double(grid["az0"]),
+                               C.c_double(grid["el0"]), C.c_double(grid["d_el"]), _dp(tab), _dp(s),
+                               C.c_double(dist_au), _dp(out))
+    if rc != 0:
+        raise ValueError(f"orc_spad_interp failed: {rc}")
+    return out

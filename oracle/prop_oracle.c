@@ -15,7 +15,8 @@
  *   - gravity: central body point mass; optional Earth J2 (z = pole) and Sun
  *     as a third body with the low-precision analytic solar coordinates of
  *     Montenbruck & Gill (Satellite Orbits, Sec. 3.3.2);
- *   - SRP: the force of srp_oracle.c for the Sun direction in the body frame,
+ *   - SRP: the force of srp_oracle.c for the Sun direction in the body frame
+ *     (or the SPAD interpolant of spad_oracle.c when a table is given),
  *     rotated to inertial and divided by the mass; zero inside a cylindrical
  *     Earth shadow;
  *   - attitude: the LVLH frame (z to nadir, y along minus the orbit normal)
@@ -49,6 +50,9 @@ typedef struct {
     int32_t method;      /* 0 RKF7(8) adaptive, 1 RK4 fixed step h0            */
     double rtol, atol_pos, atol_vel, h0, h_min, h_max;
     int64_t max_steps;
+    const double *spad_table; /* NULL: trace rays; else the SPAD table (spad_oracle.c) */
+    int32_t spad_n_az, spad_n_el;
+    double spad_az0, spad_el0, spad_d_el;
 } orc_prop;
 
 /* Fehlberg 7(8) coefficients (NASA TR R-287, Table X). */
@@ -194,11 +198,21 @@ int orc_accel(const orc_mesh *mesh, const orc_prop *pp, double t, const double y
     double R[9], sb[3];
     orc_attitude(pp, y, R);
     for (int k = 0; k < 3; k++) sb[k] = R[k] * sv[0] + R[3 + k] * sv[1] + R[6 + k] * sv[2];
-    orc_params ep = {pp->N, pp->bounces, pp->P0, dist, pp->eps_rel, 1, NULL};
-    double acc[6] = {0, 0, 0, 0, 0, 0}, scale = 0.0;
-    int rc = orc_eval_range(mesh, &ep, sb, 0, (int64_t)pp->N * pp->N, acc, &scale, NULL, NULL, NULL, NULL, NULL);
-    if (rc) return rc;
-    double Fb[3] = {acc[0] * scale, acc[1] * scale, acc[2] * scale};
+    double Fb[3];
+    if (pp->spad_table) {
+        /* interpolated force (Sec. 6): the table replaces the ray tracer */
+        double out[6];
+        int rc = orc_spad_interp(pp->spad_n_az, pp->spad_n_el, pp->spad_az0, pp->spad_el0, pp->spad_d_el,
+                                 pp->spad_table, sb, dist, out);
+        if (rc) return rc;
+        for (int k = 0; k < 3; k++) Fb[k] = out[k];
+    } else {
+        orc_params ep = {pp->N, pp->bounces, pp->P0, dist, pp->eps_rel, 1, NULL};
+        double acc[6] = {0, 0, 0, 0, 0, 0}, scale = 0.0;
+        int rc = orc_eval_range(mesh, &ep, sb, 0, (int64_t)pp->N * pp->N, acc, &scale, NULL, NULL, NULL, NULL, NULL);
+        if (rc) return rc;
+        for (int k = 0; k < 3; k++) Fb[k] = acc[k] * scale;
+    }
     for (int k = 0; k < 3; k++) a[k] += (R[3 * k] * Fb[0] + R[3 * k + 1] * Fb[1] + R[3 * k + 2] * Fb[2]) / pp->mass;
     if (aux) { aux[0] = sb[0]; aux[1] = sb[1]; aux[2] = sb[2]; aux[3] = dist; aux[5] = Fb[0]; aux[6] = Fb[1]; aux[7] = Fb[2]; }
     return 0;
@@ -347,6 +361,7 @@ int orc_rk4_arc(const orc_mesh *mesh, const orc_prop *pp, int32_t track, const d
 {
     if (!pp || !y0 || !y1 || t1 < t0 || pp->method != 1 || !(pp->h0 > 0.0)) return -1;
     if (pp->srp && (!mesh || !hits || !ids || !lit)) return -1;
+    if (pp->spad_table) return ORC_ERR_ARG; /* frozen-hit arcs trace rays; no SPAD table */
     const int64_t rays = (int64_t)pp->N * pp->N, nseg = pp->bounces + 1;
     double y[6], k[4][6], ys[6];
     memcpy(y, y0, sizeof y);

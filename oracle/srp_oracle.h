@@ -45,4 +45,7 @@ typedef struct {
 int orc_eval_range(const orc_mesh *m, const orc_params *p, const double s[3], int64_t r0, int64_t r1, double *acc,
                    double *scale, double *win, double *angles, int32_t *hits, double *edge, int64_t *nhit);
 
+int orc_spad_interp(int32_t n_az, int32_t n_el, double az0, double el0, double d_el, const double *table,
+                    const double s[3], double dist_au, double out[6]);
+
 #endif

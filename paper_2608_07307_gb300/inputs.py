@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "Mesh", "splitmix64", "uniform01", "sun_dirs_uniform", "sun_dirs_fibonacci",
     "box_wing", "spacecraft", "flat_plate", "two_plates", "box", "icosphere",
-    "v_trough", "random_soup", "merge",
+    "v_trough", "random_soup", "merge", "spad_grid", "SPAD_20x10", "SPAD_20x10S",
 ]
 
 _MASK = (1 << 64) - 1
@@ -64,6 +64,21 @@ def sun_dirs_uniform(n: int, seed: int = 0) -> np.ndarray:
     phi = 2.0 * math.pi * u[:, 1]
     r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
     return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def spad_grid(n_az: int, n_el: int, az0_deg: float, el0_deg: float, d_el_deg: float | None = None) -> dict:
+    """A SPAD sampling grid (Sec. 6, Sec. 8.1): n_az azimuths from az0, spaced
+    360/n_az degrees around the circle, and n_el elevations from el0, spaced
+    d_el (default 180/n_el) degrees.  Angles in radians in the result."""
+    d_el = 180.0 / n_el if d_el_deg is None else d_el_deg
+    return {"n_az": int(n_az), "n_el": int(n_el), "az0": math.radians(az0_deg), "el0": math.radians(el0_deg),
+            "d_el": math.radians(d_el)}
+
+
+# the two tables of the paper's comparison: from (-180, -90) degrees, and
+# shifted by 5 degrees on both axes (no sample at 0 degrees elevation)
+SPAD_20x10 = spad_grid(20, 10, -180.0, -90.0)
+SPAD_20x10S = spad_grid(20, 10, -175.0, -85.0)
 
 
 def sun_dirs_fibonacci(n: int) -> np.ndarray:
