@@ -66,6 +66,7 @@ def parse():
     p.add_argument("--no-prop", action="store_true", help="skip the propagation measurement")
     p.add_argument("--no-grad", action="store_true", help="skip the differentiated-form measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    p.add_argument("--no-spad", action="store_true", help="skip the SPAD interpolation measurement")
     p.add_argument("--batch-traj", type=int, default=256, help="trajectories of the batched form")
     p.add_argument("--grad-arc-steps", type=int, default=1000,
                    help="RK4 steps of the timed adjoint arc (the full differentiated arc is 10000)")
@@ -192,10 +193,48 @@ def bench_propagation(ctx, mid, mesh, arc_s=6 * 3600.0, N=512, bounces=1):
         dt = time.perf_counter() - t0
         out[name] = {"steps": st[0]["steps"], "rejects": st[0]["rejects"], "evals": st[0]["evals"], "seconds": dt,
                      "steps_per_s": st[0]["steps"] / dt, "evals_per_s": st[0]["evals"] / dt}
-    return {"workload": f"GEO {arc_s / 3600:g} h arc, {mesh.n_tris} triangles, N={N}, bounces={bounces}, "
-                        f"RKF7(8) rtol 1e-12, J2 + Sun + SRP",
-            "steps_per_s": out["graph"]["steps_per_s"], "steps_per_s_host_loop": out["host_loop"]["steps_per_s"],
-            "speedup_vs_host_loop": out["graph"]["steps_per_s"] / out["host_loop"]["steps_per_s"], "runs": out}
+        if name == "graph":
+            y_direct = y1[0]
+    res = {"workload": f"GEO {arc_s / 3600:g} h arc, {mesh.n_tris} triangles, N={N}, bounces={bounces}, "
+                       f"RKF7(8) rtol 1e-12, J2 + Sun + SRP",
+           "steps_per_s": out["graph"]["steps_per_s"], "steps_per_s_host_loop": out["host_loop"]["steps_per_s"],
+           "speedup_vs_host_loop": out["graph"]["steps_per_s"] / out["host_loop"]["steps_per_s"], "runs": out}
+    return res, dict(y0=y0, y_direct=y_direct, arc_s=arc_s, kw=kw, direct_s=out["graph"]["seconds"])
+
+
+# ------------------------------------------------------ SPAD interpolation
+def bench_spad(ctx, mid, direct):
+    """The paper's RQ1 comparison (Sec. 6, Sec. 8.1) on the propagation
+    workload above: build the 20 x 10 SPAD tables (from -180/-90 degrees and
+    shifted by 5 degrees) with the same ray grid, propagate the same arc with
+    the interpolated force, and report the table build time, the SPAD
+    propagation's steps/s and the position gap to the direct arc; then the
+    SPAD propagation of a 30-day arc (the workload the paper times)."""
+    import numpy as np
+    from paper_2608_07307_gb300 import inputs as I
+    kw = dict(direct["kw"])
+    N, bounces = kw.pop("N"), kw.pop("bounces")
+    y0, arc_s = direct["y0"], direct["arc_s"]
+    out = {}
+    for name, g in (("20x10", I.SPAD_20x10), ("20x10S", I.SPAD_20x10S)):
+        ctx.spad_build(mid, g, N=N, bounces=bounces)  # warm-up
+        t0 = time.perf_counter()
+        tab = ctx.spad_build(mid, g, N=N, bounces=bounces)
+        build_s = time.perf_counter() - t0
+        ctx.propagate(mid, y0, [0.0, 1800.0], spad=(g, tab), **kw)  # warm-up
+        t0 = time.perf_counter()
+        y1, st, _ = ctx.propagate(mid, y0, [0.0, arc_s], spad=(g, tab), **kw)
+        dt = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        y30, st30, _ = ctx.propagate(mid, y0, [0.0, 30 * 86400.0], spad=(g, tab), **kw)
+        dt30 = time.perf_counter() - t0
+        out[name] = {"table_build_ms": build_s * 1e3, "table_evals": g["n_az"] * g["n_el"],
+                     "steps": st[0]["steps"], "seconds": dt, "steps_per_s": st[0]["steps"] / dt,
+                     "speedup_vs_direct": direct["direct_s"] / dt,
+                     "gap_to_direct_m": float(np.linalg.norm(y1[0, :3] - direct["y_direct"][:3])),
+                     "arc_30d_steps": st30[0]["steps"], "arc_30d_ms": dt30 * 1e3}
+    return {"workload": f"the propagation workload's arc with the SRP force interpolated from 20 x 10 SPAD tables "
+                        f"built at N={N}, bounces={bounces}; plus a 30-day SPAD arc", "tables": out}
 
 
 # --------------------------------------------------------- differentiated
@@ -492,7 +531,9 @@ def run_native(a):
         "clocks": clocks,
     }
     if not a.no_prop:
-        line["propagation"] = bench_propagation(ctx, mid, mesh)
+        line["propagation"], direct = bench_propagation(ctx, mid, mesh)
+        if not a.no_spad:
+            line["spad"] = bench_spad(ctx, mid, direct)
     if not a.no_grad:
         line["differentiated"] = bench_differentiated(ctx, stream, a.grad_arc_steps)
     if not a.no_batch:

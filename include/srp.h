@@ -255,6 +255,52 @@ srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *params
                     const double *g_torque, double *force, double *torque, double *g_sun, double *g_dist,
                     double *g_mat, double *g_angle);
 
+/* ---------------------------------------------------- SPAD interpolation */
+/*
+ * A SPAD table (Sec. 6, Sec. 8.1): the force and torque of srp_eval_batch at
+ * 1 AU, precomputed for a grid of body-frame Sun directions and interpolated
+ * bilinearly in (azimuth, elevation) wherever an SRP force is needed instead
+ * of tracing rays.  Sample (i, j), 0 <= i < n_az, 0 <= j < n_el, is the
+ * direction (cos el cos az, cos el sin az, sin el) with
+ *     az = az0 + i 2 pi / n_az      (periodic: the full circle)
+ *     el = el0 + j d_el
+ * The paper's tables: n_az = 20, n_el = 10, d_el = pi / 10, from
+ * (az0, el0) = (-pi, -pi/2), and shifted by 5 degrees on both axes.
+ * Interpolation at a direction s (any length > 0): az = atan2(s_y, s_x),
+ * el = atan2(s_z, hypot(s_x, s_y)); azimuth cells wrap from the last sample to
+ * the first; beyond the first or last elevation row the row itself is used
+ * (no extrapolation).  Force and torque scale as (1 AU / r)^2.
+ * Table layout: [n_el][n_az][6] doubles, Fx Fy Fz (N) Tx Ty Tz (N m).
+ */
+typedef struct {
+    int32_t n_az;  /* azimuth samples around the circle (1 .. 2^20)          */
+    int32_t n_el;  /* elevation samples (1 .. 2^20); n_az n_el <= 2^24       */
+    double az0;    /* first azimuth (rad)                                     */
+    double el0;    /* first elevation (rad)                                   */
+    double d_el;   /* elevation spacing (rad, > 0)                            */
+} srp_spad_grid;
+
+/*
+ * Build a SPAD table: one srp_eval_batch evaluation (params: grid N, bounces,
+ * P0, panel mode, flags) per sample direction at 1 AU.
+ *   table  [n_el][n_az][6] out (host or device; caller-owned)
+ * Errors: SRP_ERR_ARG (bad grid or params, NULL table), SRP_ERR_STATE (bad
+ * mesh id), and those of srp_eval_batch.
+ */
+srp_status srp_spad_build(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *params, const srp_spad_grid *grid,
+                          double *table);
+
+/*
+ * Interpolate a SPAD table at n body-frame Sun directions.
+ *   table        [n_el][n_az][6] (host or device; read only)
+ *   sun_dir_body [n][3], sun_dist_au [n] or NULL (= 1 AU; a negative
+ *                distance gives zeros)
+ *   force, torque [n][3] out (host or device)
+ * Errors: SRP_ERR_ARG (bad grid, NULL pointer), SRP_ERR_CUDA.
+ */
+srp_status srp_spad_eval(srp_ctx *ctx, const srp_spad_grid *grid, const double *table, int32_t n,
+                         const double *sun_dir_body, const double *sun_dist_au, double *force, double *torque);
+
 /* ------------------------------------------------------------ propagation */
 #define SRP_RKF78 0           /* Fehlberg 7(8) embedded pair, adaptive step      */
 #define SRP_RK4 1             /* classical RK4, fixed step h0                    */
@@ -292,6 +338,11 @@ typedef struct {
                                and ends after n_replay steps (t1 is ignored); this reproduces
                                another integrator's accepted steps                            */
     int64_t n_replay;
+    const double *spad_table; /* NULL: trace rays in every stage; else a SPAD table for
+                                 spad_grid ([n_el][n_az][6], host or device): the SRP force
+                                 is its interpolant (srp_spad_eval) and eval is not used
+                                 (srp_propagate only)                                      */
+    srp_spad_grid spad_grid;
 } srp_prop_params;
 
 typedef struct {
@@ -311,7 +362,10 @@ typedef struct {
  * (fixed step).  Every trajectory evaluates the SRP force in every stage; the
  * whole step (stage states, Sun directions, the SRP pipeline for all
  * trajectories, accelerations, step control) is captured once in a CUDA graph
- * and relaunched until every trajectory reached its end time.
+ * and relaunched until every trajectory reached its end time.  With
+ * params->spad_table the SRP force of every stage is the SPAD interpolant of
+ * that table (Sec. 6) instead of a ray-traced evaluation: the step is then
+ * the stage, acceleration and control kernels alone.
  *   y0     [n_traj][6]  initial position (m) and velocity (m/s), inertial
  *   t0_t1  [n_traj][2]  start and end time (s after the epoch)
  *   y1     [n_traj][6]  out: state at t1 (or where the trajectory stopped)
@@ -359,7 +413,7 @@ typedef struct {
  *           bounces) key first, see srp_autotune) and SRP_EVAL_TRAVERSE (primary
  *           hits by traversal, as for srp_eval_batch).  Its central, attitude, q,
  *           eval.N, eval.bounces, eval.panel_mode, h_replay and host_loop are
- *           ignored: each srp_traj supplies its own.
+ *           ignored: each srp_traj supplies its own.  spad_table must be NULL.
  *   traj    [n] host
  *   y1      [n][6] out; stats [n] out (may be NULL)
  * Errors: SRP_ERR_ARG (a bad field; its index in srp_last_error), SRP_ERR_STATE
@@ -416,8 +470,8 @@ srp_status srp_set_tile_shape(srp_ctx *ctx, int32_t mesh_id, int32_t N, int32_t 
  *   g_mat    [n_mats][2], g_angle [n_parts], g_q [4]: out (may be NULL), summed
  *                         over the trajectories; g_q is orthogonal to q
  *   stats    [n_traj]     out (may be NULL)
- * Errors: SRP_ERR_ARG (not RK4, step replay, unequal step counts,
- * ckpt_every < 1), SRP_ERR_STEP (more than max_steps steps), SRP_ERR_OOM,
+ * Errors: SRP_ERR_ARG (not RK4, step replay, a SPAD table, unequal step
+ * counts, ckpt_every < 1), SRP_ERR_STEP (more than max_steps steps), SRP_ERR_OOM,
  * and those of srp_propagate.
  */
 srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *params, int32_t n_traj,

@@ -84,6 +84,8 @@ struct srp_ctx {
     // propagation
     double *prop_io = nullptr;
     size_t prop_io_cap = 0;
+    double *spad_buf = nullptr;  // SPAD: sample directions and results, or a staged table
+    size_t spad_cap = 0;
     PropState *prop_state = nullptr;
     size_t prop_state_cap = 0;
     double *prop_hlog = nullptr;
@@ -802,6 +804,29 @@ srp_status finish_propagate(srp_ctx *ctx, int n, const PropState *S, double *y1,
 }  // namespace
 
 // ======================================================================= ABI
+srp_status check_spad_grid(srp_ctx *ctx, const srp_spad_grid *g)
+{
+    if (!g) return fail(ctx, SRP_ERR_ARG, "null SPAD grid");
+    if (g->n_az < 1 || g->n_el < 1 || g->n_az > (1 << 20) || g->n_el > (1 << 20) ||
+        (int64_t)g->n_az * g->n_el > (int64_t)1 << 24)
+        return fail(ctx, SRP_ERR_ARG, "SPAD grid needs 1 <= n_az, n_el <= 2^20 and n_az n_el <= 2^24");
+    if (!std::isfinite(g->az0) || !std::isfinite(g->el0) || !std::isfinite(g->d_el) || !(g->d_el > 0.0))
+        return fail(ctx, SRP_ERR_ARG, "SPAD grid needs finite az0, el0 and d_el > 0");
+    return SRP_OK;
+}
+
+SpadDev spad_dev(const srp_spad_grid *g, const double *table)
+{
+    SpadDev d{};
+    d.table = table;
+    d.n_az = g->n_az;
+    d.n_el = g->n_el;
+    d.az0 = g->az0;
+    d.el0 = g->el0;
+    d.d_el = g->d_el;
+    return d;
+}
+
 extern "C" {
 
 srp_status srp_create(srp_ctx **out, int32_t device, void *cuda_stream)
@@ -859,6 +884,7 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->partials1);
     cudaFree(ctx->tctx);
     cudaFree(ctx->prop_io);
+    cudaFree(ctx->spad_buf);
     cudaFree(ctx->prop_state);
     cudaFree(ctx->prop_hlog);
     cudaFree(ctx->prop_replay);
@@ -1336,7 +1362,8 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     Mesh *m = get_mesh(ctx, mesh_id);
     if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
     if (!p) return fail(ctx, SRP_ERR_ARG, "null params");
-    srp_status rc = check_eval_params(ctx, &p->eval);
+    const bool spad = p->spad_table != nullptr;
+    srp_status rc = spad ? check_spad_grid(ctx, &p->spad_grid) : check_eval_params(ctx, &p->eval);
     if (rc) return rc;
     if (n <= 0 || !y0 || !t0_t1 || !y1) return fail(ctx, SRP_ERR_ARG, "need n > 0, y0, t0_t1 and y1");
     if (p->method != SRP_RKF78 && p->method != SRP_RK4) return fail(ctx, SRP_ERR_ARG, "bad method");
@@ -1351,8 +1378,10 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     cudaStream_t st = ctx->stream;
     memset(&ctx->last, 0, sizeof ctx->last);
     EvalPlan pl;
-    rc = eval_plan(ctx, m, &p->eval, n, false, pl);
-    if (rc) return rc;
+    if (!spad) {
+        rc = eval_plan(ctx, m, &p->eval, n, false, pl);
+        if (rc) return rc;
+    }
     // device buffers (grown, kept by the context)
     size_t need = (size_t)n * (3 + 1 + 3 + 3 + 6 + 2);
     CK(ctx, grow(&ctx->prop_io, &ctx->prop_io_cap, need, false));
@@ -1367,6 +1396,14 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     CK(ctx, cudaMemsetAsync(ctx->prop_done, 0, sizeof(int), st));
     PropState *S = ctx->prop_state;
     PropDev P = prop_dev(p, m);
+    if (spad) {
+        // the SPAD table replaces the ray tracer (Sec. 6): staged once on the device
+        const size_t nt = (size_t)p->spad_grid.n_az * p->spad_grid.n_el * 6;
+        CK(ctx, grow(&ctx->spad_buf, &ctx->spad_cap, nt, false));
+        CK(ctx, cudaMemcpyAsync(ctx->spad_buf, p->spad_table, sizeof(double) * nt, cudaMemcpyDefault, st));
+        P.spad = spad_dev(&p->spad_grid, ctx->spad_buf);
+    }
+    const bool trace = p->srp && !spad;
     CK(ctx, launch_prop_init(S, n, d_y0, d_t01, P, nullptr, ctx->prop_done, st));
     if (p->h_replay && p->n_replay > 0) {
         if (p->method != SRP_RKF78) return fail(ctx, SRP_ERR_ARG, "step replay needs SRP_RKF78");
@@ -1388,13 +1425,13 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
             if (done >= n) break;
             for (int sg = 0; sg < nstage; sg++) {
                 CK(ctx, launch_prop_stage(S, n, P, sg, d_sun, d_dist, st));
-                if (p->srp) {
+                if (trace) {
                     srp_status erc = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, nullptr, false,
                                                   off, launches, trace_launches);
                     if (erc) return erc;
                 }
                 CK(ctx, cudaStreamSynchronize(st));
-                CK(ctx, launch_prop_accel(S, n, P, sg, d_f, st));
+                CK(ctx, launch_prop_accel(S, n, P, sg, d_f, st, d_sun, d_dist));
             }
             CK(ctx, launch_prop_control(S, n, P, ctx->prop_done, h_log ? ctx->prop_hlog : nullptr, h_cap, st));
         }
@@ -1407,9 +1444,9 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     srp_status crc = SRP_OK;
     for (int sg = 0; sg < nstage && crc == SRP_OK; sg++) {
         if (launch_prop_stage(S, n, P, sg, d_sun, d_dist, st) != cudaSuccess) { crc = SRP_ERR_CUDA; break; }
-        if (p->srp) crc = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, nullptr, false, off, launches,
-                                       trace_launches);
-        if (crc == SRP_OK && launch_prop_accel(S, n, P, sg, d_f, st) != cudaSuccess) crc = SRP_ERR_CUDA;
+        if (trace) crc = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, nullptr, false, off, launches,
+                                      trace_launches);
+        if (crc == SRP_OK && launch_prop_accel(S, n, P, sg, d_f, st, d_sun, d_dist) != cudaSuccess) crc = SRP_ERR_CUDA;
     }
     if (crc == SRP_OK && launch_prop_control(S, n, P, ctx->prop_done, h_log ? ctx->prop_hlog : nullptr, h_cap, st) !=
                              cudaSuccess)
@@ -1453,6 +1490,70 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     }
     cudaGraphExecDestroy(exec);
     return finish_propagate(ctx, n, S, y1, stats, h_log, h_cap);
+}
+
+srp_status srp_spad_build(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, const srp_spad_grid *g,
+                          double *table)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    srp_status rc = check_spad_grid(ctx, g);
+    if (rc) return rc;
+    if (!prm || !table) return fail(ctx, SRP_ERR_ARG, "null params or table");
+    if (!get_mesh(ctx, mesh_id)) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int n = g->n_az * g->n_el;
+    CK(ctx, grow(&ctx->spad_buf, &ctx->spad_cap, (size_t)n * 9, false));
+    double *d_dir = ctx->spad_buf, *d_f = d_dir + 3 * (size_t)n, *d_t = d_f + 3 * (size_t)n;
+    CK(ctx, launch_spad_dirs(spad_dev(g, nullptr), d_dir, st));
+    // one evaluation per sample direction at 1 AU, through the evaluation pipeline
+    rc = srp_eval_batch(ctx, mesh_id, prm, n, d_dir, nullptr, d_f, d_t, nullptr);
+    if (rc) return rc;
+    // [n][3] force and torque interleaved into the table's [n][6]
+    const size_t v3 = 3 * sizeof(double), v6 = 6 * sizeof(double);
+    CK(ctx, cudaMemcpy2DAsync(table, v6, d_f, v3, v3, n, cudaMemcpyDefault, st));
+    CK(ctx, cudaMemcpy2DAsync(table + 3, v6, d_t, v3, v3, n, cudaMemcpyDefault, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    return SRP_OK;
+}
+
+srp_status srp_spad_eval(srp_ctx *ctx, const srp_spad_grid *g, const double *table, int32_t n,
+                         const double *sun_dir_body, const double *sun_dist_au, double *force, double *torque)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    srp_status rc = check_spad_grid(ctx, g);
+    if (rc) return rc;
+    if (n < 0) return fail(ctx, SRP_ERR_ARG, "n < 0");
+    if (n == 0) return SRP_OK;
+    if (!table || !sun_dir_body || !force || !torque) return fail(ctx, SRP_ERR_ARG, "null table, input or output");
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t nt = (size_t)g->n_az * g->n_el * 6, n3 = 3 * (size_t)n;
+    const bool tab_dev = is_device_ptr(table), in_dev = is_device_ptr(sun_dir_body);
+    const bool dist_dev = sun_dist_au && is_device_ptr(sun_dist_au);
+    const bool f_dev = is_device_ptr(force), t_dev = is_device_ptr(torque);
+    const size_t need = (tab_dev ? 0 : nt) + (in_dev ? 0 : n3) + (sun_dist_au && !dist_dev ? (size_t)n : 0) +
+                        (f_dev ? 0 : n3) + (t_dev ? 0 : n3);
+    CK(ctx, grow(&ctx->spad_buf, &ctx->spad_cap, need, false));
+    double *q = ctx->spad_buf;
+    const double *d_tab = table, *d_dir = sun_dir_body, *d_dist = sun_dist_au;
+    if (!tab_dev) { CK(ctx, cudaMemcpyAsync(q, table, sizeof(double) * nt, cudaMemcpyHostToDevice, st)); d_tab = q; q += nt; }
+    if (!in_dev) { CK(ctx, cudaMemcpyAsync(q, sun_dir_body, sizeof(double) * n3, cudaMemcpyHostToDevice, st)); d_dir = q; q += n3; }
+    if (sun_dist_au && !dist_dev) {
+        CK(ctx, cudaMemcpyAsync(q, sun_dist_au, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        d_dist = q;
+        q += n;
+    }
+    double *d_f = force, *d_t = torque;
+    if (!f_dev) { d_f = q; q += n3; }
+    if (!t_dev) { d_t = q; q += n3; }
+    CK(ctx, launch_spad_eval(spad_dev(g, d_tab), n, d_dir, d_dist, d_f, d_t, st));
+    if (!f_dev) CK(ctx, cudaMemcpyAsync(force, d_f, sizeof(double) * n3, cudaMemcpyDeviceToHost, st));
+    if (!t_dev) CK(ctx, cudaMemcpyAsync(torque, d_t, sizeof(double) * n3, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    return SRP_OK;
 }
 
 srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out)
@@ -1575,6 +1676,7 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     if (n <= 0 || !y0 || !t0_t1 || !g_y1) return fail(ctx, SRP_ERR_ARG, "need n > 0, y0, t0_t1 and g_y1");
     if (p->method != SRP_RK4) return fail(ctx, SRP_ERR_ARG, "the propagation adjoint needs SRP_RK4 (fixed steps)");
     if (p->h_replay && p->n_replay > 0) return fail(ctx, SRP_ERR_ARG, "step replay is not differentiated");
+    if (p->spad_table) return fail(ctx, SRP_ERR_ARG, "the propagation adjoint traces rays; no SPAD table");
     if (p->central != SRP_CENTRAL_EARTH && p->central != SRP_CENTRAL_SUN) return fail(ctx, SRP_ERR_ARG, "bad central body");
     if (p->attitude != SRP_ATT_LVLH && p->attitude != SRP_ATT_INERTIAL) return fail(ctx, SRP_ERR_ARG, "bad attitude");
     if (!(p->h0 > 0.0) || p->max_steps <= 0) return fail(ctx, SRP_ERR_ARG, "bad step settings");
@@ -1807,6 +1909,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     if (!ctx) return SRP_ERR_ARG;
     ctx->err.clear();
     if (!p || !tr || !y1 || n <= 0) return fail(ctx, SRP_ERR_ARG, "need params, n > 0 trajectories and y1");
+    if (p->spad_table) return fail(ctx, SRP_ERR_ARG, "srp_propagate_batch takes no SPAD table");
     if (p->method != SRP_RKF78 && p->method != SRP_RK4) return fail(ctx, SRP_ERR_ARG, "bad method");
     if (!(p->h0 > 0.0) || !(p->h_min >= 0.0) || p->max_steps <= 0) return fail(ctx, SRP_ERR_ARG, "bad step settings");
     if (p->method == SRP_RKF78 && (!(p->rtol > 0.0) || !(p->atol_pos > 0.0) || !(p->atol_vel > 0.0)))

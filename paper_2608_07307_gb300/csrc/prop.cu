@@ -227,7 +227,8 @@ __global__ void k_prop_stage(PropState *S, int n, PropDev P, int stage, double *
     sun_dist[i] = (X.done || X.shadow || !P.srp) ? -1.0 : sd / kAU;
 }
 
-__global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const double *force)
+__global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const double *force, const double *sun_dir,
+                             const double *sun_dist)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -235,7 +236,13 @@ __global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const do
     double a[3];
     gravity(P, X.central, X.ys, X.rsun, a);
     if (P.srp && !X.shadow) {
+        double Fs[6];
         const double *F = force + 3 * i;
+        if (P.spad.table) {
+            // SPAD interpolation (Sec. 6) at this stage's body-frame Sun direction
+            spad_lookup(P.spad, sun_dir + 3 * i, sun_dist[i], Fs);
+            F = Fs;
+        }
         for (int k = 0; k < 3; k++) a[k] += (X.R[3 * k] * F[0] + X.R[3 * k + 1] * F[1] + X.R[3 * k + 2] * F[2]) / X.mass;
     }
     for (int k = 0; k < 3; k++) { X.k[stage][k] = X.ys[3 + k]; X.k[stage][3 + k] = a[k]; }
@@ -525,9 +532,10 @@ cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, 
     k_prop_stage<<<(n + 63) / 64, 64, 0, st>>>(S, n, P, stage, sun_dir, sun_dist);
     return cudaGetLastError();
 }
-cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st)
+cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st,
+                              const double *sun_dir, const double *sun_dist)
 {
-    k_prop_accel<<<(n + 63) / 64, 64, 0, st>>>(S, n, P, stage, force);
+    k_prop_accel<<<(n + 63) / 64, 64, 0, st>>>(S, n, P, stage, force, sun_dir, sun_dist);
     return cudaGetLastError();
 }
 cudaError_t launch_prop_control(PropState *S, int n, const PropDev &P, int *n_done, double *h_log, int64_t h_cap,

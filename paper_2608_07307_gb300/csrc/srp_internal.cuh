@@ -185,6 +185,50 @@ constexpr int kRastBigBlocks = 2048;  // k_raster_big grid (8 warps a block, one
 constexpr int kBigPerSlot = 65536;  // chunk-list entries reserved per slot
 size_t trace_ctx_bytes();
 
+// SPAD table (Sec. 6): force and torque at 1 AU for a grid of body-frame Sun
+// directions, [n_el][n_az][6] (srp_spad_grid gives the sample directions).
+struct SpadDev {
+    const double *table;  // device; null when the SRP force is ray-traced
+    int n_az, n_el;
+    double az0, el0, d_el;
+};
+
+// Bilinear interpolant of the SPAD table at body-frame direction s and Sun
+// distance dist (AU; negative gives zeros): out = [F, T] scaled by 1/dist^2.
+// Azimuth is periodic over n_az cells; elevation clamps to the outer rows.
+__device__ __forceinline__ void spad_lookup(const SpadDev &g, const double *s, double dist, double out[6])
+{
+    if (dist < 0.0) {
+        for (int k = 0; k < 6; k++) out[k] = 0.0;
+        return;
+    }
+    const double az = atan2(s[1], s[0]);
+    const double el = atan2(s[2], hypot(s[0], s[1]));
+    double u = (az - g.az0) * (g.n_az * 0.15915494309189535);  // cells of 2 pi / n_az
+    u -= floor(u / g.n_az) * g.n_az;                          // into [0, n_az]
+    const int i0 = min((int)u, g.n_az - 1);
+    const double fa = u - i0;
+    const int i1 = i0 + 1 == g.n_az ? 0 : i0 + 1;
+    const double v = (el - g.el0) / g.d_el;
+    int j0 = 0, j1 = 0;
+    double fe = 0.0;
+    if (g.n_el > 1 && v > 0.0) {
+        if (v >= g.n_el - 1) {
+            j0 = j1 = g.n_el - 1;
+        } else {
+            j0 = (int)v;
+            j1 = j0 + 1;
+            fe = v - j0;
+        }
+    }
+    const double w00 = (1.0 - fa) * (1.0 - fe), w01 = fa * (1.0 - fe), w10 = (1.0 - fa) * fe, w11 = fa * fe;
+    const double *t00 = g.table + 6 * ((size_t)j0 * g.n_az + i0), *t01 = g.table + 6 * ((size_t)j0 * g.n_az + i1);
+    const double *t10 = g.table + 6 * ((size_t)j1 * g.n_az + i0), *t11 = g.table + 6 * ((size_t)j1 * g.n_az + i1);
+    const double r2 = 1.0 / (dist * dist);
+    for (int k = 0; k < 6; k++)
+        out[k] = (w00 * __ldg(t00 + k) + w01 * __ldg(t01 + k) + w10 * __ldg(t10 + k) + w11 * __ldg(t11 + k)) * r2;
+}
+
 // Propagation settings as seen by the device (from srp_prop_params).
 struct PropDev {
     int method, central, j2, sun3, srp, attitude;
@@ -194,6 +238,7 @@ struct PropDev {
     long long max_steps;
     const double *h_replay;  // [n][n_replay] device, or null
     long long n_replay;
+    SpadDev spad;            // SPAD table in place of the ray tracer, or spad.table null
 };
 
 // Per-trajectory integrator state (device).
@@ -306,7 +351,12 @@ cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double
                              const double *cfg, int *n_done, cudaStream_t st);
 cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, double *sun_dir, double *sun_dist,
                               cudaStream_t st);
-cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st);
+cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st,
+                              const double *sun_dir = nullptr, const double *sun_dist = nullptr);
+// SPAD (csrc/spad.cu): the sample directions, [n_el][n_az][3]; the interpolant at n directions.
+cudaError_t launch_spad_dirs(const SpadDev &g, double *dirs, cudaStream_t st);
+cudaError_t launch_spad_eval(const SpadDev &g, int n, const double *dirs, const double *dist, double *force,
+                             double *torque, cudaStream_t st);
 cudaError_t launch_prop_control(PropState *S, int n, const PropDev &P, int *n_done, double *h_log, int64_t h_cap,
                                 cudaStream_t st);
 // propagation adjoint (RK4): checkpoints, stage records, reverse stage sweep

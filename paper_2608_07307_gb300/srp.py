@@ -17,6 +17,7 @@ from . import build as _build
 SRP_OK = 0
 ERRORS = {-1: "SRP_ERR_ARG", -2: "SRP_ERR_OOM", -3: "SRP_ERR_CUDA", -4: "SRP_ERR_MESH", -5: "SRP_ERR_STACK",
           -6: "SRP_ERR_TIMEOUT", -7: "SRP_ERR_STEP", -8: "SRP_ERR_STATE"}
+globals().update({name: code for code, name in ERRORS.items()})
 SRP_F32, SRP_F64 = 0, 1
 PANELS_TRACK, PANELS_SET, PANELS_TRACK_OFFSET = 0, 1, 2
 EVAL_COUNT = 1
@@ -29,7 +30,8 @@ MAX_N = 8192  # SRP_MAX_N: rays per window side
 # Symbols declared in include/srp.h (checked by the tests against the library).
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",
            "srp_eval_batch", "srp_eval_stats_get", "srp_propagate", "srp_eval_noalloc", "srp_set_materials",
-           "srp_grad", "srp_prop_grad", "srp_propagate_batch", "srp_autotune", "srp_set_tile_shape"]
+           "srp_grad", "srp_prop_grad", "srp_propagate_batch", "srp_autotune", "srp_set_tile_shape",
+           "srp_spad_build", "srp_spad_eval"]
 
 
 class Traj(C.Structure):
@@ -76,12 +78,25 @@ CENTRAL_EARTH, CENTRAL_SUN = 0, 1
 ATT_LVLH, ATT_INERTIAL = 0, 1
 
 
+class SpadGrid(C.Structure):
+    _fields_ = [("n_az", C.c_int32), ("n_el", C.c_int32), ("az0", C.c_double), ("el0", C.c_double),
+                ("d_el", C.c_double)]
+
+
+def spad_grid_struct(g) -> SpadGrid:
+    """srp_spad_grid from a dict with n_az, n_el, az0, el0, d_el (radians)."""
+    if isinstance(g, SpadGrid):
+        return g
+    return SpadGrid(int(g["n_az"]), int(g["n_el"]), float(g["az0"]), float(g["el0"]), float(g["d_el"]))
+
+
 class PropParams(C.Structure):
     _fields_ = [("method", C.c_int32), ("central", C.c_int32), ("j2", C.c_int32), ("sun3", C.c_int32),
                 ("srp", C.c_int32), ("attitude", C.c_int32), ("q", C.c_double * 4), ("epoch_mjd_tt", C.c_double),
                 ("rtol", C.c_double), ("atol_pos", C.c_double), ("atol_vel", C.c_double), ("h0", C.c_double),
                 ("h_min", C.c_double), ("h_max", C.c_double), ("max_steps", C.c_int64), ("poll", C.c_int32),
-                ("host_loop", C.c_int32), ("eval", EvalParams), ("h_replay", C.c_void_p), ("n_replay", C.c_int64)]
+                ("host_loop", C.c_int32), ("eval", EvalParams), ("h_replay", C.c_void_p), ("n_replay", C.c_int64),
+                ("spad_table", C.c_void_p), ("spad_grid", SpadGrid)]
 
 
 class PropStats(C.Structure):
@@ -127,6 +142,9 @@ def load(build_if_needed: bool = True):
                                       C.c_void_p, C.POINTER(PropStats)]
         lib.srp_propagate.argtypes = [C.c_void_p, C.c_int32, C.POINTER(PropParams), C.c_int32, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(PropStats), C.c_void_p, C.c_int64]
+        lib.srp_spad_build.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.POINTER(SpadGrid), C.c_void_p]
+        lib.srp_spad_eval.argtypes = [C.c_void_p, C.POINTER(SpadGrid), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]
         lib.srp_eval_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                          C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double), C.c_int32,
                                          C.c_int32, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -198,6 +216,7 @@ class Context:
         if rc != SRP_OK:
             raise SrpError(rc, f"srp_create(device={device}) failed")
         self.h = h
+        self.device = device
         self.meshes = {}
         self.mesh_info = {}
 
@@ -308,10 +327,12 @@ class Context:
                   atol_vel: float = 1e-9, h0: float = 60.0, h_min: float = 1e-6, h_max: float = 0.0,
                   max_steps: int = 10_000_000, poll: int = 16, N: int = 64, bounces: int = 1, P0: float = 4.56e-6,
                   eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, h_cap: int = 0, h_replay=None,
-                  host_loop: bool = False, traverse: bool = False):
+                  host_loop: bool = False, traverse: bool = False, spad=None):
         """srp_propagate: y1 [n, 6], per-trajectory stats (list of dicts) and,
         with h_cap > 0, the accepted step sizes [n, h_cap] (NaN padded).
-        h_replay [n, k]: take exactly these RKF7(8) steps (replay)."""
+        h_replay [n, k]: take exactly these RKF7(8) steps (replay).
+        spad = (grid, table): the SRP force is the SPAD interpolant of the
+        table (spad_build) instead of a ray-traced evaluation."""
         y0 = np.ascontiguousarray(np.asarray(y0, np.float64).reshape(-1, 6))
         n = len(y0)
         t01 = np.ascontiguousarray(np.asarray(t0_t1, np.float64).reshape(n, 2))
@@ -320,6 +341,12 @@ class Context:
                        epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, int(host_loop),
                        EvalParams(N, bounces, P0, eps_rel, panel_mode, EVAL_TRAVERSE if traverse else 0),
                        hr.ctypes.data if hr is not None else None, 0 if hr is None else hr.shape[1])
+        keep = None
+        if spad is not None:
+            grid, table = spad
+            table = self._spad_table_arg(table)
+            p.spad_table, keep = _ptr(table)
+            p.spad_grid = spad_grid_struct(grid)
         y1 = np.empty((n, 6))
         st = (PropStats * n)()
         hl = np.full((n, h_cap), np.nan) if h_cap > 0 else None
@@ -331,6 +358,57 @@ class Context:
             for i, s in enumerate(stats):
                 hl[i, min(s["steps"], h_cap):] = np.nan
         return y1, stats, hl
+
+    @staticmethod
+    def _spad_table_arg(table):
+        if _is_cuda(table):
+            return table.detach().to(dtype=__import__("torch").float64).contiguous()
+        if hasattr(table, "detach"):
+            table = table.detach().cpu().numpy()
+        return np.ascontiguousarray(np.asarray(table, np.float64))
+
+    def spad_build(self, mesh_id: int, grid, N: int = 256, bounces: int = 1, P0: float = 4.56e-6,
+                   eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, traverse: bool = False, device=False):
+        """srp_spad_build: the SPAD table [n_el, n_az, 6] (F, T at 1 AU) of the
+        grid (a dict with n_az, n_el, az0, el0, d_el in radians); a CUDA
+        tensor when device=True, else a numpy array."""
+        g = spad_grid_struct(grid)
+        if device:
+            import torch
+            table = torch.empty((g.n_el, g.n_az, 6), dtype=torch.float64, device=f"cuda:{self.device}")
+        else:
+            table = np.empty((g.n_el, g.n_az, 6))
+        p = EvalParams(N, bounces, P0, eps_rel, panel_mode, EVAL_TRAVERSE if traverse else 0)
+        pt, k = _ptr(table)
+        self._check(self.lib.srp_spad_build(self.h, mesh_id, C.byref(p), C.byref(g), pt))
+        return table
+
+    def spad_eval(self, grid, table, sun_dirs, sun_dist=None):
+        """srp_spad_eval: (force [n, 3], torque [n, 3]) of the SPAD interpolant;
+        CUDA tensors in give CUDA tensors out."""
+        g = spad_grid_struct(grid)
+        table = self._spad_table_arg(table)
+        if _is_cuda(sun_dirs):
+            import torch
+            sun_dirs = sun_dirs.detach().to(dtype=torch.float64).contiguous()
+            if sun_dist is not None:
+                sun_dist = sun_dist.detach().to(device=sun_dirs.device, dtype=torch.float64).contiguous()
+            n = sun_dirs.shape[0]
+            force = torch.empty((n, 3), dtype=torch.float64, device=sun_dirs.device)
+            torque = torch.empty_like(force)
+        else:
+            sun_dirs = np.ascontiguousarray(np.asarray(sun_dirs, np.float64).reshape(-1, 3))
+            if sun_dist is not None:
+                sun_dist = np.ascontiguousarray(np.asarray(sun_dist, np.float64).reshape(-1))
+            n = sun_dirs.shape[0]
+            force, torque = np.empty((n, 3)), np.empty((n, 3))
+        pg, k0 = _ptr(table)
+        ps, k1 = _ptr(sun_dirs)
+        pd, k2 = _ptr(sun_dist)
+        pf, k3 = _ptr(force)
+        pt, k4 = _ptr(torque)
+        self._check(self.lib.srp_spad_eval(self.h, C.byref(g), pg, n, ps, pd, pf, pt))
+        return force, torque
 
     def set_materials(self, mesh_id: int, mat):
         """srp_set_materials: new (rho_s, rho_d) per material, [n_mats, 2]."""

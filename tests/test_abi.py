@@ -43,3 +43,32 @@ def test_create_fails_loudly_without_a_device():
     with pytest.raises(srp.SrpError) as e:
         srp.Context(0)
     assert e.value.code == -3
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror of an include/srp.h struct has the C size and the C
+    offset for each field (gcc compiles a probe of the header here)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    from paper_2608_07307_gb300 import srp
+    pairs = {"srp_mesh_desc": srp.MeshDesc, "srp_eval_params": srp.EvalParams, "srp_eval_stats": srp.EvalStats,
+             "srp_spad_grid": srp.SpadGrid, "srp_prop_params": srp.PropParams, "srp_prop_stats": srp.PropStats,
+             "srp_traj": srp.Traj}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "srp.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
