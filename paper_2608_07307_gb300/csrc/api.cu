@@ -1442,15 +1442,23 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     cudaGraphExec_t exec = nullptr;
     CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     srp_status crc = SRP_OK;
-    for (int sg = 0; sg < nstage && crc == SRP_OK; sg++) {
-        if (launch_prop_stage(S, n, P, sg, d_sun, d_dist, st) != cudaSuccess) { crc = SRP_ERR_CUDA; break; }
-        if (trace) crc = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, nullptr, false, off, launches,
-                                      trace_launches);
-        if (crc == SRP_OK && launch_prop_accel(S, n, P, sg, d_f, st, d_sun, d_dist) != cudaSuccess) crc = SRP_ERR_CUDA;
+    if (!trace) {
+        // no ray-traced evaluation between the stages: the whole step is one kernel
+        if (launch_prop_step(S, n, P, d_sun, d_dist, ctx->prop_done, h_log ? ctx->prop_hlog : nullptr, h_cap, st) !=
+            cudaSuccess)
+            crc = SRP_ERR_CUDA;
+    } else {
+        for (int sg = 0; sg < nstage && crc == SRP_OK; sg++) {
+            if (launch_prop_stage(S, n, P, sg, d_sun, d_dist, st) != cudaSuccess) { crc = SRP_ERR_CUDA; break; }
+            crc = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, nullptr, false, off, launches,
+                               trace_launches);
+            if (crc == SRP_OK && launch_prop_accel(S, n, P, sg, d_f, st, d_sun, d_dist) != cudaSuccess)
+                crc = SRP_ERR_CUDA;
+        }
+        if (crc == SRP_OK &&
+            launch_prop_control(S, n, P, ctx->prop_done, h_log ? ctx->prop_hlog : nullptr, h_cap, st) != cudaSuccess)
+            crc = SRP_ERR_CUDA;
     }
-    if (crc == SRP_OK && launch_prop_control(S, n, P, ctx->prop_done, h_log ? ctx->prop_hlog : nullptr, h_cap, st) !=
-                             cudaSuccess)
-        crc = SRP_ERR_CUDA;
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (crc != SRP_OK || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

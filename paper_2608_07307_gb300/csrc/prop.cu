@@ -95,21 +95,19 @@ __device__ void quat_matrix(const double *q, double *Q)
 // LVLH frame at y: columns x_b = y_b x z_b, y_b = -orbit normal, z_b = nadir
 __device__ void lvlh_matrix(const double *y, double *L)
 {
-    double rn = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+    const double irn = -1.0 / sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
     double h[3] = {y[1] * y[5] - y[2] * y[4], y[2] * y[3] - y[0] * y[5], y[0] * y[4] - y[1] * y[3]};
-    double hn = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-    double zb[3] = {-y[0] / rn, -y[1] / rn, -y[2] / rn};
-    double yb[3] = {-h[0] / hn, -h[1] / hn, -h[2] / hn};
+    const double ihn = -1.0 / sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    double zb[3] = {y[0] * irn, y[1] * irn, y[2] * irn};
+    double yb[3] = {h[0] * ihn, h[1] * ihn, h[2] * ihn};
     double xb[3] = {yb[1] * zb[2] - yb[2] * zb[1], yb[2] * zb[0] - yb[0] * zb[2], yb[0] * zb[1] - yb[1] * zb[0]};
     for (int k = 0; k < 3; k++) { L[3 * k] = xb[k]; L[3 * k + 1] = yb[k]; L[3 * k + 2] = zb[k]; }
 }
 
-// body -> inertial rotation, row-major: Q(q) (inertial attitude) or
-// LVLH(y) Q(q) (the LVLH frame turned by the constant quaternion q)
-__device__ void body_to_inertial(int attitude, const double *q, const double *y, double *R)
+// body -> inertial rotation, row-major: Q (inertial attitude) or LVLH(y) Q
+// (the LVLH frame turned by the constant quaternion whose rotation is Q)
+__device__ void body_to_inertial(int attitude, const double *Q, const double *y, double *R)
 {
-    double Q[9];
-    quat_matrix(q, Q);
     if (attitude == 1) {
         for (int k = 0; k < 9; k++) R[k] = Q[k];
         return;
@@ -125,10 +123,12 @@ __device__ void gravity(const PropDev &P, int central, const double *y, const do
 {
     double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2], r = sqrt(r2);
     double mu = central == 1 ? kMuSun : kMuEarth;
-    for (int k = 0; k < 3; k++) a[k] = -mu * y[k] / (r2 * r);
+    const double ir3 = 1.0 / (r2 * r);
+    for (int k = 0; k < 3; k++) a[k] = -mu * y[k] * ir3;
     if (central == 0 && P.j2) {
-        double z2 = y[2] * y[2] / r2;
-        double f = -1.5 * kJ2 * kMuEarth * kREarth * kREarth / (r2 * r2 * r);
+        const double ir2 = 1.0 / r2;
+        double z2 = y[2] * y[2] * ir2;
+        double f = -1.5 * kJ2 * kMuEarth * kREarth * kREarth * (ir3 * ir2);
         a[0] += f * y[0] * (1.0 - 5.0 * z2);
         a[1] += f * y[1] * (1.0 - 5.0 * z2);
         a[2] += f * y[2] * (3.0 - 5.0 * z2);
@@ -137,8 +137,8 @@ __device__ void gravity(const PropDev &P, int central, const double *y, const do
         double d[3] = {rs[0] - y[0], rs[1] - y[1], rs[2] - y[2]};
         double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         double sn = sqrt(rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2]);
-        double d3 = dn * dn * dn, s3 = sn * sn * sn;
-        for (int k = 0; k < 3; k++) a[k] += kMuSun * (d[k] / d3 - rs[k] / s3);
+        const double id3 = 1.0 / (dn * dn * dn), is3 = 1.0 / (sn * sn * sn);
+        for (int k = 0; k < 3; k++) a[k] += kMuSun * (d[k] * id3 - rs[k] * is3);
     }
 }
 
@@ -162,6 +162,7 @@ __global__ void k_prop_init(PropState *S, int n, const double *y0, const double 
         for (int k = 0; k < 4; k++) X.q[k] = P.q[k];
         X.mass = P.mass;
     }
+    quat_matrix(X.q, X.Qm);
     for (int k = 0; k < 6; k++) X.y[k] = y0[6 * i + k];
     X.t = t01[2 * i];
     X.t1 = t01[2 * i + 1];
@@ -177,24 +178,66 @@ __global__ void k_prop_init(PropState *S, int n, const double *y0, const double 
     if (X.done) atomicAdd(n_done, 1);
 }
 
-// Stage state, Sun direction (body frame) and distance for the SRP call.
-__global__ void k_prop_stage(PropState *S, int n, PropDev P, int stage, double *sun_dir, double *sun_dist)
+// Lane 0's part of a stage: time, Sun direction in the body frame and
+// distance (negative to skip the SRP call), shadow, attitude.
+__device__ __forceinline__ void stage_tail(PropState &X, int i, const PropDev &P, int stage, double *sun_dir,
+                                           double *sun_dist)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    PropState &X = S[i];
     const int rk4 = P.method == 1;
-    double h = X.h;
-    if (!X.done) {
-        if (P.n_replay > 0) {
-            h = X.steps < P.n_replay ? P.h_replay[(size_t)i * P.n_replay + X.steps] : 0.0;
-        } else if (X.t + h >= X.t1) {
-            h = X.t1 - X.t;  // land exactly on t1
-        }
-        X.hs = h;
+    X.ts = X.t + (rk4 ? cC4[stage] : cC[stage]) * X.hs;
+    // Sun direction and distance
+    double rs[3] = {0.0, 0.0, 0.0}, sv[3];
+    if (X.central == 0)
+        for (int k = 0; k < 3; k++) rs[k] = X.rs_st[stage][k];
+    for (int k = 0; k < 3; k++) { X.rsun[k] = rs[k]; sv[k] = rs[k] - X.ys[k]; }
+    double sd = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
+    for (int k = 0; k < 3; k++) sv[k] /= sd;
+    // cylindrical Earth shadow
+    X.shadow = 0;
+    if (X.central == 0) {
+        const double irsn = 1.0 / sqrt(rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2]);
+        double e[3] = {rs[0] * irsn, rs[1] * irsn, rs[2] * irsn};
+        double pr = X.ys[0] * e[0] + X.ys[1] * e[1] + X.ys[2] * e[2];
+        double q[3] = {X.ys[0] - pr * e[0], X.ys[1] - pr * e[1], X.ys[2] - pr * e[2]};
+        if (pr < 0.0 && q[0] * q[0] + q[1] * q[1] + q[2] * q[2] < kREarth * kREarth) X.shadow = 1;
     }
-    double c = rk4 ? cC4[stage] : cC[stage];
-    for (int k = 0; k < 6; k++) {
+    double R[9];
+    body_to_inertial(X.attitude, X.Qm, X.ys, R);
+    for (int k = 0; k < 9; k++) X.R[k] = R[k];
+    for (int k = 0; k < 3; k++) sun_dir[3 * i + k] = R[k] * sv[0] + R[3 + k] * sv[1] + R[6 + k] * sv[2];
+    // finished and shadowed trajectories skip their SRP evaluation (negative distance)
+    sun_dist[i] = (X.done || X.shadow || !P.srp) ? -1.0 : sd / kAU;
+}
+
+// Stage state, Sun direction (body frame) and distance for the SRP call; a
+// warp per trajectory.  At the first stage of a step, once the step size is
+// fixed, every stage time is known: lanes compute the Sun positions of all
+// stages at once.  Lanes 0-5 form the six components of the stage state; lane
+// 0 the rest.
+__device__ __forceinline__ void stage_body(PropState &X, int i, const PropDev &P, int stage, int lane, double *sun_dir,
+                                           double *sun_dist)
+{
+    const int rk4 = P.method == 1;
+    if (stage == 0) {
+        if (lane == 0 && !X.done) {
+            double h = X.h;
+            if (P.n_replay > 0) {
+                h = X.steps < P.n_replay ? P.h_replay[(size_t)i * P.n_replay + X.steps] : 0.0;
+            } else if (X.t + h >= X.t1) {
+                h = X.t1 - X.t;  // land exactly on t1
+            }
+            X.hs = h;
+        }
+        __syncwarp();
+        if (lane < (rk4 ? 4 : 13) && X.central == 0) {
+            const double ts = X.t + (rk4 ? cC4[lane] : cC[lane]) * X.hs;
+            double rs[3];
+            sun_pos(P.epoch_mjd_tt + ts / 86400.0, rs);
+            for (int k = 0; k < 3; k++) X.rs_st[lane][k] = rs[k];
+        }
+    }
+    if (lane < 6) {
+        const int k = lane;
         double acc = 0.0;
         if (rk4) {
             if (stage > 0) acc = 0.5 * X.k[stage - 1][k] * (stage == 3 ? 2.0 : 1.0);
@@ -203,36 +246,22 @@ __global__ void k_prop_stage(PropState *S, int n, PropDev P, int stage, double *
         }
         X.ys[k] = X.y[k] + X.hs * acc;
     }
-    X.ts = X.t + c * X.hs;
-    // Sun direction and distance
-    double rs[3] = {0.0, 0.0, 0.0}, sv[3];
-    if (X.central == 0) sun_pos(P.epoch_mjd_tt + X.ts / 86400.0, rs);
-    for (int k = 0; k < 3; k++) { X.rsun[k] = rs[k]; sv[k] = rs[k] - X.ys[k]; }
-    double sd = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
-    for (int k = 0; k < 3; k++) sv[k] /= sd;
-    // cylindrical Earth shadow
-    X.shadow = 0;
-    if (X.central == 0) {
-        double rsn = sqrt(rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2]);
-        double e[3] = {rs[0] / rsn, rs[1] / rsn, rs[2] / rsn};
-        double pr = X.ys[0] * e[0] + X.ys[1] * e[1] + X.ys[2] * e[2];
-        double q[3] = {X.ys[0] - pr * e[0], X.ys[1] - pr * e[1], X.ys[2] - pr * e[2]};
-        if (pr < 0.0 && sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) < kREarth) X.shadow = 1;
-    }
-    double R[9];
-    body_to_inertial(X.attitude, X.q, X.ys, R);
-    for (int k = 0; k < 9; k++) X.R[k] = R[k];
-    for (int k = 0; k < 3; k++) sun_dir[3 * i + k] = R[k] * sv[0] + R[3 + k] * sv[1] + R[6 + k] * sv[2];
-    // finished and shadowed trajectories skip their SRP evaluation (negative distance)
-    sun_dist[i] = (X.done || X.shadow || !P.srp) ? -1.0 : sd / kAU;
+    __syncwarp();
+    if (lane != 0) return;
+    stage_tail(X, i, P, stage, sun_dir, sun_dist);
 }
 
-__global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const double *force, const double *sun_dir,
-                             const double *sun_dist)
+__global__ void k_prop_stage(PropState *S, int n, PropDev P, int stage, double *sun_dir, double *sun_dist)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    PropState &X = S[i];
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // whole warps (blocks are multiples of 32 threads)
+    stage_body(S[i], i, P, stage, threadIdx.x & 31, sun_dir, sun_dist);
+}
+
+// Stage derivative: gravity plus the SRP force (traced, or the SPAD interpolant).
+__device__ __forceinline__ void accel_body(PropState &X, int i, const PropDev &P, int stage, const double *force,
+                                           const double *sun_dir, const double *sun_dist)
+{
     double a[3];
     gravity(P, X.central, X.ys, X.rsun, a);
     if (P.srp && !X.shadow) {
@@ -243,17 +272,25 @@ __global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const do
             spad_lookup(P.spad, sun_dir + 3 * i, sun_dist[i], Fs);
             F = Fs;
         }
-        for (int k = 0; k < 3; k++) a[k] += (X.R[3 * k] * F[0] + X.R[3 * k + 1] * F[1] + X.R[3 * k + 2] * F[2]) / X.mass;
+        const double im = 1.0 / X.mass;
+        for (int k = 0; k < 3; k++) a[k] += (X.R[3 * k] * F[0] + X.R[3 * k + 1] * F[1] + X.R[3 * k + 2] * F[2]) * im;
     }
     for (int k = 0; k < 3; k++) { X.k[stage][k] = X.ys[3 + k]; X.k[stage][3 + k] = a[k]; }
     if (!X.done) X.evals++;
 }
 
-__global__ void k_prop_control(PropState *S, int n, PropDev P, int *n_done, double *h_log, int64_t h_cap)
+__global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const double *force, const double *sun_dir,
+                             const double *sun_dist)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    PropState &X = S[i];
+    accel_body(S[i], i, P, stage, force, sun_dir, sun_dist);
+}
+
+// Step control: accept or reject, next step size, completion.
+__device__ __forceinline__ void control_body(PropState &X, int i, const PropDev &P, int *n_done, double *h_log,
+                                             int64_t h_cap)
+{
     if (X.done) return;
     const double h = X.hs;
     if (P.n_replay > 0) {
@@ -311,6 +348,33 @@ __global__ void k_prop_control(PropState *S, int n, PropDev P, int *n_done, doub
     if (X.t >= X.t1) X.done = 1;
     if (X.steps + X.rejects > P.max_steps && !X.done) { X.status = SRP_ERR_STEP; X.done = 1; }
     if (X.done) atomicAdd(n_done, 1);
+}
+
+__global__ void k_prop_control(PropState *S, int n, PropDev P, int *n_done, double *h_log, int64_t h_cap)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    control_body(S[i], i, P, n_done, h_log, h_cap);
+}
+
+// A whole step in one launch when no ray-traced evaluation sits between the
+// stages (SPAD table or SRP off): the stage, acceleration and control parts of
+// the kernels above, in their order, a warp per trajectory.
+__global__ void k_prop_step(PropState *S, int n, PropDev P, double *sun_dir, double *sun_dist, int *n_done,
+                            double *h_log, int64_t h_cap)
+{
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;  // whole warps
+    PropState &X = S[i];
+    const int nst = P.method == 1 ? 4 : 13;
+    for (int stage = 0; stage < nst; stage++) {
+        stage_body(X, i, P, stage, lane, sun_dir, sun_dist);
+        __syncwarp();
+        if (lane == 0) accel_body(X, i, P, stage, nullptr, sun_dir, sun_dist);
+        __syncwarp();
+    }
+    if (lane == 0) control_body(X, i, P, n_done, h_log, h_cap);
 }
 
 
@@ -529,13 +593,19 @@ cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double
 cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, double *sun_dir, double *sun_dist,
                               cudaStream_t st)
 {
-    k_prop_stage<<<(n + 63) / 64, 64, 0, st>>>(S, n, P, stage, sun_dir, sun_dist);
+    k_prop_stage<<<(n + 3) / 4, 128, 0, st>>>(S, n, P, stage, sun_dir, sun_dist);  // a warp per trajectory
     return cudaGetLastError();
 }
 cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st,
                               const double *sun_dir, const double *sun_dist)
 {
     k_prop_accel<<<(n + 63) / 64, 64, 0, st>>>(S, n, P, stage, force, sun_dir, sun_dist);
+    return cudaGetLastError();
+}
+cudaError_t launch_prop_step(PropState *S, int n, const PropDev &P, double *sun_dir, double *sun_dist, int *n_done,
+                             double *h_log, int64_t h_cap, cudaStream_t st)
+{
+    k_prop_step<<<(n + 3) / 4, 128, 0, st>>>(S, n, P, sun_dir, sun_dist, n_done, h_log, h_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_prop_control(PropState *S, int n, const PropDev &P, int *n_done, double *h_log, int64_t h_cap,

@@ -253,6 +253,8 @@ struct PropState {
     int done, status, shadow, pad_;
     int central, attitude;     // per-trajectory force model and attitude law
     double q[4], mass;         // attitude quaternion, spacecraft mass (kg)
+    double Qm[9];              // rotation of the normalised q, row-major (fixed per trajectory)
+    double rs_st[13][3];       // Sun position at every stage time of the current step
 };
 
 // One stage of an RK4 step, recorded for the reverse pass of the propagation adjoint.
@@ -353,6 +355,9 @@ cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, 
                               cudaStream_t st);
 cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st,
                               const double *sun_dir = nullptr, const double *sun_dist = nullptr);
+// A whole integrator step in one launch (no ray-traced SRP between the stages).
+cudaError_t launch_prop_step(PropState *S, int n, const PropDev &P, double *sun_dir, double *sun_dist, int *n_done,
+                             double *h_log, int64_t h_cap, cudaStream_t st);
 // SPAD (csrc/spad.cu): the sample directions, [n_el][n_az][3]; the interpolant at n directions.
 cudaError_t launch_spad_dirs(const SpadDev &g, double *dirs, cudaStream_t st);
 cudaError_t launch_spad_eval(const SpadDev &g, int n, const double *dirs, const double *dist, double *force,
