@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--no-grad", action="store_true", help="skip the differentiated-form measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     p.add_argument("--no-spad", action="store_true", help="skip the SPAD interpolation measurement")
+    p.add_argument("--no-panels", action="store_true", help="skip the fixed vs movable panel study")
     p.add_argument("--batch-traj", type=int, default=256, help="trajectories of the batched form")
     p.add_argument("--grad-arc-steps", type=int, default=1000,
                    help="RK4 steps of the timed adjoint arc (the full differentiated arc is 10000)")
@@ -172,8 +173,8 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------- propagation
-def bench_propagation(ctx, mid, mesh, arc_s=6 * 3600.0, N=512, bounces=1):
-    """GEO arc with the 200k-triangle spacecraft: two-body + J2 + Sun + SRP
+def bench_propagation(ctx, mid, mesh, arc_s=30 * 86400.0, N=512, bounces=1):
+    """30-day GEO arc with the 200k-triangle spacecraft: two-body + J2 + Sun + SRP
     (512^2 rays, 1 bounce, tracking panels), RKF7(8) rtol 1e-12.  Accepted
     steps per second with the graph-captured device step, and with the same
     kernels issued stage by stage while the host waits for each SRP result
@@ -195,7 +196,7 @@ def bench_propagation(ctx, mid, mesh, arc_s=6 * 3600.0, N=512, bounces=1):
                      "steps_per_s": st[0]["steps"] / dt, "evals_per_s": st[0]["evals"] / dt}
         if name == "graph":
             y_direct = y1[0]
-    res = {"workload": f"GEO {arc_s / 3600:g} h arc, {mesh.n_tris} triangles, N={N}, bounces={bounces}, "
+    res = {"workload": f"GEO {arc_s / 86400:g}-day arc, {mesh.n_tris} triangles, N={N}, bounces={bounces}, "
                        f"RKF7(8) rtol 1e-12, J2 + Sun + SRP",
            "steps_per_s": out["graph"]["steps_per_s"], "steps_per_s_host_loop": out["host_loop"]["steps_per_s"],
            "speedup_vs_host_loop": out["graph"]["steps_per_s"] / out["host_loop"]["steps_per_s"], "runs": out}
@@ -208,8 +209,8 @@ def bench_spad(ctx, mid, direct):
     workload above: build the 20 x 10 SPAD tables (from -180/-90 degrees and
     shifted by 5 degrees) with the same ray grid, propagate the same arc with
     the interpolated force, and report the table build time, the SPAD
-    propagation's steps/s and the position gap to the direct arc; then the
-    SPAD propagation of a 30-day arc (the workload the paper times)."""
+    propagation's steps/s and the position gap to the direct arc at its end;
+    then 1024 dispersed arcs with the interpolated force in one call."""
     import numpy as np
     from paper_2608_07307_gb300 import inputs as I
     kw = dict(direct["kw"])
@@ -225,14 +226,10 @@ def bench_spad(ctx, mid, direct):
         t0 = time.perf_counter()
         y1, st, _ = ctx.propagate(mid, y0, [0.0, arc_s], spad=(g, tab), **kw)
         dt = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        y30, st30, _ = ctx.propagate(mid, y0, [0.0, 30 * 86400.0], spad=(g, tab), **kw)
-        dt30 = time.perf_counter() - t0
         out[name] = {"table_build_ms": build_s * 1e3, "table_evals": g["n_az"] * g["n_el"],
                      "steps": st[0]["steps"], "seconds": dt, "steps_per_s": st[0]["steps"] / dt,
                      "speedup_vs_direct": direct["direct_s"] / dt,
-                     "gap_to_direct_m": float(np.linalg.norm(y1[0, :3] - direct["y_direct"][:3])),
-                     "arc_30d_steps": st30[0]["steps"], "arc_30d_ms": dt30 * 1e3}
+                     "gap_to_direct_m": float(np.linalg.norm(y1[0, :3] - direct["y_direct"][:3]))}
     # many trajectories at once: 1024 GEO states dispersed by 1 km / 1 m/s
     # (seeded Gaussian), 30 days each, one srp_propagate call, 20 x 10 table
     g, tab = I.SPAD_20x10, ctx.spad_build(mid, I.SPAD_20x10, N=N, bounces=bounces)
@@ -248,8 +245,53 @@ def bench_spad(ctx, mid, direct):
     many = {"trajectories": n_traj, "arc_days": 30, "steps": tot, "seconds": dtm,
             "trajectory_steps_per_s": tot / dtm}
     return {"workload": f"the propagation workload's arc with the SRP force interpolated from 20 x 10 SPAD tables "
-                        f"built at N={N}, bounces={bounces}; a 30-day SPAD arc; {n_traj} dispersed 30-day SPAD "
-                        f"arcs in one call", "tables": out, "many": many}
+                        f"built at N={N}, bounces={bounces}; {n_traj} dispersed 30-day SPAD arcs in one call",
+            "tables": out, "many": many}
+
+
+# ------------------------------------------------ fixed vs movable panels
+def bench_panels(ctx, N_a1=256, N_a2=128, bounces=1, days=30.0, sample_h=12.0):
+    """The movable-panel study (Sec. 7, metrics A1 and A2 of Sec. 5) on the
+    two-axis box-wing: A1 compares the SRP force with the panels held at their
+    rest angles against Sun-tracking panels over 1296 uniform directions
+    (mean squared difference, largest difference, and mean squared difference
+    relative to the tracking force's squared norm); A2 propagates a GEO arc
+    both ways and reports the separation of the two trajectories, sampled
+    every `sample_h` hours (each sample interval is one srp_propagate call)."""
+    import math
+
+    import numpy as np
+    from paper_2608_07307_gb300 import inputs as I
+    from paper_2608_07307_gb300 import srp
+    m = I.box_wing_two_axis()
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_uniform(1296, seed=0)
+    t0 = time.perf_counter()
+    Ft, _ = ctx.eval_batch(mid, dirs, N=N_a1, bounces=bounces, panel_mode=srp.PANELS_TRACK)
+    Ff, _ = ctx.eval_batch(mid, dirs, N=N_a1, bounces=bounces, panel_mode=srp.PANELS_SET)
+    a1_s = time.perf_counter() - t0
+    d2 = ((Ff - Ft) ** 2).sum(axis=1)
+    a1 = {"directions": len(dirs), "N": N_a1, "mse_N2": float(d2.mean()), "max_N": float(np.sqrt(d2.max())),
+          "mser": float((d2 / (Ft ** 2).sum(axis=1)).mean()), "seconds": a1_s}
+    a_geo, inc = 42164e3, math.radians(0.1)
+    v = math.sqrt(3.986004418e14 / a_geo)
+    y = {mode: np.array([a_geo, 0.0, 0.0, 0.0, v * math.cos(inc), v * math.sin(inc)])
+         for mode in (srp.PANELS_TRACK, srp.PANELS_SET)}
+    kw = dict(j2=True, sun3=True, N=N_a2, bounces=bounces, rtol=1e-12)
+    seps, steps = [], 0
+    dt = sample_h * 3600.0
+    t0 = time.perf_counter()
+    for k in range(int(round(days * 24 / sample_h))):
+        for mode in y:
+            y1, st, _ = ctx.propagate(mid, y[mode], [k * dt, (k + 1) * dt], panel_mode=mode, **kw)
+            y[mode] = y1[0]
+            steps += st[0]["steps"]
+        seps.append(float(np.linalg.norm(y[srp.PANELS_TRACK][:3] - y[srp.PANELS_SET][:3])))
+    a2 = {"arc_days": days, "sample_hours": sample_h, "N": N_a2, "min_m": min(seps), "max_m": max(seps),
+          "mean_m": float(np.mean(seps)), "final_m": seps[-1], "steps": steps,
+          "seconds": time.perf_counter() - t0}
+    return {"workload": f"two-axis box-wing ({m.n_tris} triangles), panels at rest angles vs Sun tracking, "
+                        f"{bounces} bounce", "A1": a1, "A2": a2}
 
 
 # --------------------------------------------------------- differentiated
@@ -549,6 +591,8 @@ def run_native(a):
         line["propagation"], direct = bench_propagation(ctx, mid, mesh)
         if not a.no_spad:
             line["spad"] = bench_spad(ctx, mid, direct)
+    if not a.no_panels:
+        line["panels"] = bench_panels(ctx)
     if not a.no_grad:
         line["differentiated"] = bench_differentiated(ctx, stream, a.grad_arc_steps)
     if not a.no_batch:

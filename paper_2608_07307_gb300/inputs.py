@@ -32,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "splitmix64", "uniform01", "sun_dirs_uniform", "sun_dirs_fibonacci",
-    "box_wing", "spacecraft", "flat_plate", "two_plates", "box", "icosphere",
+    "box_wing", "box_wing_two_axis", "spacecraft", "flat_plate", "two_plates", "box", "icosphere",
     "v_trough", "random_soup", "merge", "spad_grid", "SPAD_20x10", "SPAD_20x10S",
 ]
 
@@ -217,6 +217,31 @@ def box_wing() -> Mesh:
     parts = _parts(3, [-1, 0, 0], pivot=[[0, 0, 0], [0, 0.75, 0], [0, -0.75, 0]],
                    axis=[[0, 0, 0], [0, 1, 0], [0, 1, 0]])
     return Mesh(xyz, tri, tp, tm, mat, c_ref=np.zeros(3), mass=2269.0, name="box_wing", **parts)
+
+
+def box_wing_two_axis() -> Mesh:
+    """The box-wing with a two-axis array drive per wing (Sec. 7): a yoke
+    (a 0.1 m square strut, bus material, from y = 0.51 to 0.74 m) turns about
+    the body y axis within +-90 degrees and carries the 2 x 1 m panel, which
+    folds about the x axis through its inner edge (|y| = 0.75 m) within +-45
+    degrees.  Both joints track the Sun with reference normal +z.  Parts: bus,
+    yoke +y, yoke -y, panel +y, panel -y; 40 triangles; mass 2269 kg.
+    """
+    b = _Builder()
+    _add_box(b, (-0.5, -0.5, -0.5), (0.5, 0.5, 0.5), None, 0, 0, 0)
+    _add_box(b, (-0.05, 0.51, -0.05), (0.05, 0.74, 0.05), None, 1, 0, 0)
+    _add_box(b, (-0.05, -0.74, -0.05), (0.05, -0.51, 0.05), None, 2, 0, 0)
+    b.add(*_grid((-0.5, 0.75, 0.0), (1.0, 0, 0), (0, 2.0, 0), 1, 1), 3, 1, 2)
+    b.add(*_grid((-0.5, -2.75, 0.0), (1.0, 0, 0), (0, 2.0, 0), 1, 1), 4, 1, 2)
+    xyz, tri, tp, tm = b.arrays()
+    mat = np.array([[0.1, 0.2], [0.05, 0.05], [0.0, 0.1]])
+    half, quarter = math.pi / 2, math.pi / 4
+    parts = _parts(5, [-1, 0, 0, 1, 2],
+                   pivot=[[0, 0, 0], [0, 0.5, 0], [0, -0.5, 0], [0, 0.75, 0], [0, -0.75, 0]],
+                   axis=[[0, 0, 0], [0, 1, 0], [0, 1, 0], [1, 0, 0], [1, 0, 0]],
+                   limits=[[-math.pi, math.pi], [-half, half], [-half, half], [-quarter, quarter],
+                           [-quarter, quarter]])
+    return Mesh(xyz, tri, tp, tm, mat, c_ref=np.zeros(3), mass=2269.0, name="box_wing_two_axis", **parts)
 
 
 def spacecraft(h: float = 0.05, seed: int = 0) -> Mesh:

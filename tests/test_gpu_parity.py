@@ -365,3 +365,20 @@ def test_fullsize_forces_against_stored_oracle():
                 assert np.linalg.norm(F[q] - Fo) <= 1e-4 * fn, (h, r[3], F[q], Fo)
                 assert np.linalg.norm(T[q] - To) <= 1e-4 * max(np.linalg.norm(To), fn), (h, r[3], T[q], To)
             c.free_mesh(mid)
+
+
+def test_two_axis_box_wing_clamped_tracking(ctx):
+    """The two-axis array drive (support +-90 deg carrying a hinge +-45 deg,
+    Sec. 7): joint angles composed down the tree and clamped on the device;
+    Sun directions over the whole sphere, most of them clamping a joint."""
+    m = I.box_wing_two_axis()
+    mid = ctx.load_mesh(m)
+    dirs = I.sun_dirs_uniform(48, seed=5)
+    N, B = 96, 2
+    Fg, Tg, Hg = ctx.eval_batch(mid, dirs, N=N, bounces=B, hits=True)
+    Fo, To, Ho, Eo, L = oracle_batch(m, dirs, N, B, hits=True)
+    check_force(Fg, Tg, Fo, To)
+    for k in range(len(dirs)):
+        check_hits(Hg[k], Ho[k], Eo[k], L[k], f"dir {k}")
+    clamped = sum(1 for s in dirs if s[2] < 0 or abs(s[1]) > math.sin(math.pi / 4))
+    assert clamped > 10

@@ -346,3 +346,53 @@ def test_sharded_sum_matches_single_process():
     a = O.evaluate(m, s, 32, bounces=2)
     b = O.evaluate(m, s, 32, bounces=2, procs=2, chunks=3)
     assert rel(b["F"], a["F"]) < 1e-13
+
+
+def _panel_normal(m, xyz, part):
+    t = m.tri[m.tri_part == part][0]
+    n = np.cross(xyz[t[1]] - xyz[t[0]], xyz[t[2]] - xyz[t[0]])
+    return n / np.linalg.norm(n)
+
+
+def test_two_axis_drive_reaches_the_sun():
+    """Two-axis array drive (Sec. 7; support +-90 deg about y, hinge +-45 deg
+    about x): for a Sun direction within reach (s_z >= 0, |s_y| <= sin 45
+    deg) both panels face the Sun exactly, and the rigid parts do not move."""
+    m = I.box_wing_two_axis()
+    n_in = 0
+    for s in I.sun_dirs_uniform(400, seed=31):
+        if s[2] < 0.02 or abs(s[1]) > math.sin(math.radians(44)):
+            continue
+        n_in += 1
+        ang, xyz = O.pose(m, s)
+        for part in (3, 4):
+            assert np.linalg.norm(_panel_normal(m, xyz, part) - s) < 1e-12
+        assert np.all(np.abs(ang[1:3]) <= math.pi / 2 + 1e-15) and np.all(np.abs(ang[3:5]) <= math.pi / 4 + 1e-15)
+        bus = np.unique(m.tri[m.tri_part == 0])
+        assert np.array_equal(xyz[bus], m.xyz[bus])
+    assert n_in > 50
+
+
+def test_two_axis_drive_clamps_joint_by_joint():
+    """Out of reach, each joint holds the most sunward angle of its own
+    interval (a scan of rotations, not the tracking formula): the support
+    over +-90 deg for its reference normal, the hinge over +-45 deg given the
+    support's angle."""
+    m = I.box_wing_two_axis()
+    g1 = np.linspace(-math.pi / 2, math.pi / 2, 18001)
+    g2 = np.linspace(-math.pi / 4, math.pi / 4, 9001)
+    n_out = 0
+    for s in I.sun_dirs_uniform(120, seed=32):
+        if s[2] >= 0.0 and abs(s[1]) <= math.sin(math.radians(45)):
+            continue
+        n_out += 1
+        ang, xyz = O.pose(m, s)
+        for yoke, panel in ((1, 3), (2, 4)):
+            assert abs(ang[yoke]) <= math.pi / 2 + 1e-15 and abs(ang[panel]) <= math.pi / 4 + 1e-15
+            ref = Rotation.from_rotvec(np.outer(g1, [0, 1.0, 0])).apply([0, 0, 1.0])
+            n1 = Rotation.from_rotvec([0, ang[yoke], 0]).apply([0, 0, 1.0])
+            assert np.dot(n1, s) >= (ref @ s).max() - 1e-8
+            R1 = Rotation.from_rotvec([0, ang[yoke], 0])
+            cand = R1.apply(Rotation.from_rotvec(np.outer(g2, [1.0, 0, 0])).apply([0, 0, 1.0]))
+            assert np.dot(_panel_normal(m, xyz, panel), s) >= (cand @ s).max() - 1e-8
+    assert n_out > 30
