@@ -62,6 +62,7 @@ class _Params(C.Structure):
     _fields_ = [
         ("N", C.c_int32), ("bounces", C.c_int32), ("P0", C.c_double), ("dist_au", C.c_double),
         ("eps_rel", C.c_double), ("track", C.c_int32), ("angles", C.POINTER(C.c_double)),
+        ("n_diffuse", C.c_int32), ("diffuse_seed", C.c_uint32),
     ]
 
 
@@ -75,6 +76,8 @@ def lib():
         _lib.orc_window_ids.restype = C.c_int
         _lib.orc_eval_frozen.restype = C.c_int
         _lib.orc_rk4_arc.restype = C.c_int
+        _lib.orc_splitmix64.restype = C.c_uint64
+        _lib.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
     return _lib
 
 
@@ -110,14 +113,15 @@ class OMesh:
                        (C.c_double * 3)(*np.asarray(mesh.c_ref, np.float64)))
 
 
-def _params(N, bounces, P0, dist_au, eps_rel, angles, n_parts, offsets=None):
+def _params(N, bounces, P0, dist_au, eps_rel, angles, n_parts, offsets=None, n_diffuse=0, diffuse_seed=0):
     """Sun tracking (no angles), commanded angles, or tracking + offsets."""
     if angles is not None and offsets is not None:
         raise ValueError("give commanded angles or tracking offsets, not both")
     if angles is None and offsets is None:
-        return _Params(N, bounces, P0, dist_au, eps_rel, 1, None), None
+        return _Params(N, bounces, P0, dist_au, eps_rel, 1, None, n_diffuse, diffuse_seed), None
     a = np.ascontiguousarray(np.asarray(angles if offsets is None else offsets, np.float64).reshape(n_parts))
-    return _Params(N, bounces, P0, dist_au, eps_rel, 0 if offsets is None else 2, _dp(a)), a
+    return _Params(N, bounces, P0, dist_au, eps_rel, 0 if offsets is None else 2, _dp(a), n_diffuse,
+                   diffuse_seed), a
 
 
 def pose(mesh, s, angles=None, offsets=None):
@@ -136,13 +140,13 @@ def pose(mesh, s, angles=None, offsets=None):
 
 
 def eval_range(mesh, s, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None, r0=0, r1=None,
-               want_hits=False, want_edge=False, _om=None, offsets=None):
+               want_hits=False, want_edge=False, _om=None, offsets=None, n_diffuse=0, diffuse_seed=0):
     """Trace rays [r0, r1) of one direction.  Returns a dict with the unscaled
     sums `acc` (6), the `scale` P dA, the window `win` (8), joint `angles`,
     per-segment hit counts `nhit`, and optionally `hits` / `edge` per ray."""
     om = _om or OMesh(mesh)
     r1 = N * N if r1 is None else r1
-    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts, offsets)
+    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts, offsets, n_diffuse, diffuse_seed)
     s = np.ascontiguousarray(np.asarray(s, np.float64))
     acc = np.zeros(6)
     scale = np.zeros(1)
@@ -167,14 +171,15 @@ def _worker(args):
 
 
 def evaluate(mesh, s, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None, want_hits=False,
-             want_edge=False, procs=1, chunks=None, offsets=None):
+             want_edge=False, procs=1, chunks=None, offsets=None, n_diffuse=0, diffuse_seed=0):
     """Force F (N) and torque T (N m) about c_ref for one Sun direction.
 
     With procs > 1 the ray range is split into contiguous chunks traced by
     spawn-started worker processes (each single-threaded); the partial sums
     are added in chunk order, so the result does not depend on scheduling."""
     kw = dict(N=N, bounces=bounces, P0=P0, dist_au=dist_au, eps_rel=eps_rel, angles=angles,
-              want_hits=want_hits, want_edge=want_edge, offsets=offsets)
+              want_hits=want_hits, want_edge=want_edge, offsets=offsets, n_diffuse=n_diffuse,
+              diffuse_seed=diffuse_seed)
     R = N * N
     if procs <= 1:
         parts = [eval_range(mesh, s, **kw)]
@@ -200,11 +205,12 @@ def evaluate(mesh, s, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angle
     return out
 
 
-def eval_rays(mesh, s, rays, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None):
+def eval_rays(mesh, s, rays, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None, n_diffuse=0,
+              diffuse_seed=0):
     """Per-ray unscaled contributions [n, 6], hits [n, nseg] and edge proximity
     [n, nseg] for an explicit list of primary ray indices (sampled checks)."""
     om = OMesh(mesh)
-    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts)
+    p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts, None, n_diffuse, diffuse_seed)
     rays = np.ascontiguousarray(np.asarray(rays, np.int64))
     n = len(rays)
     nseg = bounces + 1
@@ -549,3 +555,18 @@ def spad_interp(grid, table, s, dist_au=1.0):
     if rc != 0:
         raise ValueError(f"orc_spad_interp failed: {rc}")
     return out
+
+
+# ------------------------------------------- diffuse secondary rays (Sec. 6.1)
+def splitmix64(seed, c):
+    """Output number c (from 0) of the oracle's SplitMix64 stream for `seed`."""
+    return int(lib().orc_splitmix64(C.c_uint64(seed), C.c_uint64(c)))
+
+
+def diffuse_dir(seed, c, nf):
+    """The oracle's cosine-weighted diffuse direction for sample counter c
+    about unit normal nf."""
+    nf = np.ascontiguousarray(np.asarray(nf, np.float64))
+    w = np.zeros(3)
+    lib().orc_diffuse_dir(C.c_uint64(seed), C.c_uint64(c), _dp(nf), _dp(w))
+    return w

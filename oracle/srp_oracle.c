@@ -58,6 +58,8 @@ typedef struct {
     double umin, umax, vmin, vmax, wmin, wmax;
     double L, eps;
     int32_t N, bounces;
+    int32_t n_diffuse;       /* diffuse secondary rays per hit                  */
+    uint64_t seed;           /* their sample stream                             */
 } orc_scene;
 
 /* ---------------------------------------------------------------- vectors */
@@ -193,6 +195,7 @@ static int scene_setup(orc_scene *sc, const orc_mesh *m, const double *xyz, cons
                        int32_t bounces, double eps_rel)
 {
     sc->m = m; sc->xyz = xyz; sc->N = N; sc->bounces = bounces;
+    sc->n_diffuse = 0; sc->seed = 0;
     for (int k = 0; k < 3; k++) sc->d[k] = -s[k];
     orc_onb(sc->d, sc->u, sc->v);
     sc->umin = sc->vmin = sc->wmin = INFINITY;
@@ -331,6 +334,72 @@ static double edge_distance(const orc_scene *sc, const double *o, const double *
     return best;
 }
 
+/* ---------------------------------------------- diffuse secondary rays */
+/* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number c (from 0) of
+ * the sequence seeded with `seed`: the state after c + 1 increments of the
+ * golden-ratio constant, mixed. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t c)
+{
+    uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Diffuse sample q of segment k of primary ray r (nseg segments, K samples):
+ * two uniforms in [0, 1) from outputs 2c and 2c + 1, c = (r nseg + k) K + q
+ * (top 53 bits), then a cosine-weighted direction about the unit normal nf
+ * (Malley's method: a uniform point of the unit disc lifted to the
+ * hemisphere), in the basis of Duff et al. around nf. */
+void orc_diffuse_dir(uint64_t seed, uint64_t c, const double nf[3], double w[3])
+{
+    double u1 = (double)(orc_splitmix64(seed, 2 * c) >> 11) * 0x1.0p-53;
+    double u2 = (double)(orc_splitmix64(seed, 2 * c + 1) >> 11) * 0x1.0p-53;
+    double rr = sqrt(u1), ph = 2.0 * 3.14159265358979323846 * u2;
+    double lx = rr * cos(ph), ly = rr * sin(ph), lz = sqrt(1.0 - u1);
+    double t1[3], t2[3];
+    orc_onb(nf, t1, t2);
+    for (int k = 0; k < 3; k++) w[k] = lx * t1[k] + ly * t2[k] + lz * nf[k];
+}
+
+/*
+ * Diffuse secondaries of one hit (reading of Sec. 6.1's diffuse rays): the
+ * light the facet reflects diffusely, w rho_d, leaves as K rays of weight
+ * w rho_d / K, cosine-distributed about nf, from the hit point x; each is
+ * traced once (never the emitting triangle, t > eps) and deposits at its hit
+ * the full per-hit law along its own direction; it spawns nothing further.
+ * The emitter's own recoil stays the analytic 2/3 rho_d term of the law.
+ */
+static void diffuse_hits(const orc_scene *sc, int64_t r, int k, const double x[3], const double nf[3], int32_t src,
+                         double wd, double *acc)
+{
+    const orc_mesh *m = sc->m;
+    int nseg = sc->bounces + 1;
+    for (int q = 0; q < sc->n_diffuse; q++) {
+        uint64_t c = ((uint64_t)r * (uint64_t)nseg + (uint64_t)k) * (uint64_t)sc->n_diffuse + (uint64_t)q;
+        double w[3], th;
+        orc_diffuse_dir(sc->seed, c, nf, w);
+        int32_t h = nearest_hit(sc, x, w, src, &th);
+        if (h < 0) continue;
+        const int32_t *f = m->tri + 3 * h;
+        const double *v0 = sc->xyz + 3 * f[0], *v1 = sc->xyz + 3 * f[1], *v2 = sc->xyz + 3 * f[2];
+        double e1[3], e2[3], n[3], nf2[3], x2[3], arm[3], F[3], Tq[3];
+        sub3(v1, v0, e1); sub3(v2, v0, e2); cross3(e1, e2, n);
+        double nl = sqrt(dot3(n, n));
+        for (int c3 = 0; c3 < 3; c3++) n[c3] /= nl;
+        int side = dot3(w, n) < 0.0 ? 0 : 1;
+        for (int c3 = 0; c3 < 3; c3++) nf2[c3] = side ? -n[c3] : n[c3];
+        int mi = m->tri_mat[2 * h + side];
+        double rs = m->mat[2 * mi], rd = m->mat[2 * mi + 1];
+        double cs = -dot3(nf2, w);
+        for (int c3 = 0; c3 < 3; c3++) F[c3] = wd * ((1.0 - rs) * w[c3] - 2.0 * (rs * cs + rd / 3.0) * nf2[c3]);
+        for (int c3 = 0; c3 < 3; c3++) x2[c3] = x[c3] + th * w[c3];
+        sub3(x2, m->c_ref, arm);
+        cross3(arm, F, Tq);
+        for (int c3 = 0; c3 < 3; c3++) { acc[c3] += F[c3]; acc[3 + c3] += Tq[c3]; }
+    }
+}
+
 /*
  * Trace primary ray r and its specular secondaries (Sec. 4.3: secondary rays
  * are handled iteratively).  Per hit, with n_f the unit facet normal turned
@@ -340,7 +409,9 @@ static double edge_distance(const orc_scene *sc, const double *o, const double *
  * (absorbed + Lambertian incidence along d; specular and diffuse reflection
  * recoil along -n_f), torque (x_hit - c_ref) x f.  The specular beam leaves
  * with direction d - 2 (d . n) n and weight w rho_s; segment k+1 is traced
- * only if segment k hit, k < bounces, and the new weight is non-zero.
+ * only if segment k hit, k < bounces, and the new weight is non-zero.  With
+ * n_diffuse > 0, every hit of a segment k < bounces also emits its diffuse
+ * secondaries (diffuse_hits) before the specular ray goes on.
  * acc[0..5] += (f, tau) summed over the segments (not yet scaled by P dA).
  */
 static void trace_ray(const orc_scene *sc, int64_t r, double *acc, int32_t *hits, double *edge, int64_t *nhit)
@@ -375,6 +446,7 @@ static void trace_ray(const orc_scene *sc, int64_t r, double *acc, int32_t *hits
         sub3(x, m->c_ref, arm);
         cross3(arm, F, Tq);
         for (int c = 0; c < 3; c++) { acc[c] += F[c]; acc[3 + c] += Tq[c]; }
+        if (k + 1 < nseg && sc->n_diffuse > 0 && rd > 0.0) diffuse_hits(sc, r, k, x, nf, h, w * rd / sc->n_diffuse, acc);
         w *= rs;
         if (k + 1 >= nseg || w == 0.0) break;
         double dn = dot3(d, n);
@@ -406,6 +478,8 @@ int orc_eval_range(const orc_mesh *m, const orc_params *p, const double s[3], in
     if (rc != ORC_OK) { free(xyz); return rc; }
     orc_scene sc;
     scene_setup(&sc, m, xyz, s, p->N, p->bounces, p->eps_rel);
+    sc.n_diffuse = p->n_diffuse > 0 ? p->n_diffuse : 0;
+    sc.seed = p->diffuse_seed;
     if (win) {
         win[0] = sc.umin; win[1] = sc.umax; win[2] = sc.vmin; win[3] = sc.vmax;
         win[4] = sc.wmin; win[5] = sc.wmax; win[6] = sc.L; win[7] = sc.eps;
@@ -431,6 +505,8 @@ int orc_eval_rays(const orc_mesh *m, const orc_params *p, const double s[3], int
     if (rc != ORC_OK) { free(xyz); return rc; }
     orc_scene sc;
     scene_setup(&sc, m, xyz, s, p->N, p->bounces, p->eps_rel);
+    sc.n_diffuse = p->n_diffuse > 0 ? p->n_diffuse : 0;
+    sc.seed = p->diffuse_seed;
     int nseg = p->bounces + 1;
     for (int64_t q = 0; q < n; q++) {
         if (rays[q] < 0 || rays[q] >= (int64_t)p->N * p->N) { free(xyz); return ORC_ERR_ARG; }

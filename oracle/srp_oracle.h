@@ -39,6 +39,8 @@ typedef struct {
     double eps_rel;          /* self-hit threshold, relative to window diagonal */
     int32_t track;           /* 1: Sun tracking; 0: angles[]; 2: tracking + angles[] */
     const double *angles;    /* [n_parts] commanded angles (0) or offsets (2)   */
+    int32_t n_diffuse;       /* diffuse secondary rays per hit (0: none)        */
+    uint32_t diffuse_seed;   /* seed of their SplitMix64 sample stream          */
 } orc_params;
 
 
