@@ -106,7 +106,28 @@ typedef struct {
     double eps_rel;      /* secondary-ray self-hit threshold / window diagonal (1e-9)    */
     int32_t panel_mode;  /* SRP_PANELS_*                                                 */
     int32_t flags;       /* 0, or SRP_EVAL_COUNT to gather srp_eval_stats counters       */
+    int32_t n_diffuse;   /* diffuse secondary rays per hit, 0..SRP_MAX_DIFFUSE (0: none;
+                            see below)                                                   */
+    uint32_t diffuse_seed; /* seed of the diffuse rays' sample stream                    */
 } srp_eval_params;
+
+/*
+ * Diffuse secondary rays (Sec. 6.1: the paper's configuration traces 16 per
+ * hit).  With n_diffuse = K > 0, the hit of every ray segment that has a next
+ * level (segment k < bounces) also emits K rays of weight w rho_d / K (w the
+ * segment's weight, rho_d that of the side hit) from the hit point, in
+ * cosine-weighted directions about the normal of the lit side; each is traced
+ * once (never onto the emitting triangle, t > eps) and deposits the full
+ * per-hit law at its hit, spawning nothing further.  The emitter keeps its
+ * analytic 2/3 rho_d recoil.  Sample q of segment k of ray r = i N + j uses
+ * outputs 2c and 2c + 1 of the SplitMix64 stream seeded with diffuse_seed,
+ * c = (r (bounces + 1) + k) K + q, as uniforms u1, u2 (top 53 bits): local
+ * direction (sqrt(u1) cos 2 pi u2, sqrt(u1) sin 2 pi u2, sqrt(1 - u1)) in the
+ * basis of Duff et al. around that normal.  The diffuse rays are traced with
+ * FP64 decisions.  srp_eval_batch and srp_propagate take them;
+ * srp_grad, srp_prop_grad and srp_propagate_batch need n_diffuse = 0.
+ */
+#define SRP_MAX_DIFFUSE 256
 
 #define SRP_EVAL_COUNT 1  /* gather traversal counters (slower kernel variant)        */
 #define SRP_EVAL_TIMING 2 /* time each phase with CUDA events on the context stream   */

@@ -52,6 +52,8 @@ struct srp_ctx {
     size_t amb_list_cap = 0;
     double *partials1 = nullptr;
     size_t partials1_cap = 0;
+    double *dpart = nullptr;  // diffuse-ray partial sums [SL][kDiffBlocks][6]
+    size_t dpart_cap = 0;
     unsigned char *tctx = nullptr;
     size_t tctx_cap = 0;
     int *amb_count = nullptr;
@@ -410,6 +412,8 @@ srp_status check_eval_params(srp_ctx *ctx, const srp_eval_params *prm)
     if (prm->bounces < 0 || prm->bounces > kMaxBounces) return fail(ctx, SRP_ERR_ARG, "bounces = %d", prm->bounces);
     if (!(prm->P0 >= 0.0) || !(prm->eps_rel >= 0.0)) return fail(ctx, SRP_ERR_ARG, "P0 and eps_rel must be >= 0");
     if (prm->panel_mode < 0 || prm->panel_mode > 2) return fail(ctx, SRP_ERR_ARG, "bad panel_mode");
+    if (prm->n_diffuse < 0 || prm->n_diffuse > SRP_MAX_DIFFUSE)
+        return fail(ctx, SRP_ERR_ARG, "n_diffuse = %d outside [0, %d]", prm->n_diffuse, SRP_MAX_DIFFUSE);
     return SRP_OK;
 }
 
@@ -553,7 +557,9 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
         CK(ctx, grow_fill(&ctx->bigt_count, &ctx->bigt_count_cap, (size_t)kLanes, 0));
         CK(ctx, grow_fill(&ctx->rast_bad, &ctx->rast_bad_cap, SL, 0));
     }
-    if (want_hits || adjoint) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
+    // the diffuse rays replay each ray's recorded hits
+    if (want_hits || adjoint || prm->n_diffuse > 0) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
+    if (prm->n_diffuse > 0) CK(ctx, grow(&ctx->dpart, &ctx->dpart_cap, SL * kDiffBlocks * 6, false));
     // every slot evaluates this mesh on this grid; lane b owns slots [b S, (b + 1) S)
     std::vector<SlotDesc> sd(SL);
     for (size_t k = 0; k < SL; k++) {
@@ -633,7 +639,12 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             a.rast_bad = ctx->rast_bad + s0;
         }
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
-        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : (adj ? stage : nullptr);
+        a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : ((adj || prm->n_diffuse > 0) ? stage : nullptr);
+        if (prm->n_diffuse > 0 && nseg > 1) {
+            a.n_diffuse = prm->n_diffuse;
+            a.diffuse_seed = prm->diffuse_seed;
+            a.dpart = ctx->dpart + s0 * kDiffBlocks * 6;
+        }
         int g0 = tm.mark(ls);
         CK(ctx, launch_pose(sd, d_sun, d_dist, prm->P0, e0, Sc, pose, ls));
         CK(ctx, launch_vertices(sd, pose, Sc, h.n_verts, ls));
@@ -652,6 +663,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         int g4 = tm.mark(ls);
         launches += 4;  // frame, trace, two reduction levels
         if (a.raster) launches += 5;  // two raster passes over small and large triangles, chunk listing
+        if (a.n_diffuse > 0) launches += 1;  // diffuse secondaries
         trace_launches++;
         if (adj) {
             AdjArgs g{};
@@ -882,6 +894,7 @@ void srp_destroy(srp_ctx *ctx)
     cudaFree(ctx->pcounts);
     cudaFree(ctx->amb_list);
     cudaFree(ctx->partials1);
+    cudaFree(ctx->dpart);
     cudaFree(ctx->tctx);
     cudaFree(ctx->prop_io);
     cudaFree(ctx->spad_buf);
@@ -1605,6 +1618,7 @@ srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, i
     if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
     srp_status rc = check_eval_params(ctx, prm);
     if (rc) return rc;
+    if (prm->n_diffuse != 0) return fail(ctx, SRP_ERR_ARG, "srp_grad takes no diffuse rays (n_diffuse = 0)");
     if (n < 0) return fail(ctx, SRP_ERR_ARG, "n < 0");
     if (g_dist && !sun_dist_au) return fail(ctx, SRP_ERR_ARG, "g_dist needs sun_dist_au");
     memset(&ctx->last, 0, sizeof ctx->last);
@@ -1685,6 +1699,7 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     if (p->method != SRP_RK4) return fail(ctx, SRP_ERR_ARG, "the propagation adjoint needs SRP_RK4 (fixed steps)");
     if (p->h_replay && p->n_replay > 0) return fail(ctx, SRP_ERR_ARG, "step replay is not differentiated");
     if (p->spad_table) return fail(ctx, SRP_ERR_ARG, "the propagation adjoint traces rays; no SPAD table");
+    if (p->eval.n_diffuse != 0) return fail(ctx, SRP_ERR_ARG, "the propagation adjoint takes no diffuse rays");
     if (p->central != SRP_CENTRAL_EARTH && p->central != SRP_CENTRAL_SUN) return fail(ctx, SRP_ERR_ARG, "bad central body");
     if (p->attitude != SRP_ATT_LVLH && p->attitude != SRP_ATT_INERTIAL) return fail(ctx, SRP_ERR_ARG, "bad attitude");
     if (!(p->h0 > 0.0) || p->max_steps <= 0) return fail(ctx, SRP_ERR_ARG, "bad step settings");
@@ -1918,6 +1933,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     ctx->err.clear();
     if (!p || !tr || !y1 || n <= 0) return fail(ctx, SRP_ERR_ARG, "need params, n > 0 trajectories and y1");
     if (p->spad_table) return fail(ctx, SRP_ERR_ARG, "srp_propagate_batch takes no SPAD table");
+    if (p->eval.n_diffuse != 0) return fail(ctx, SRP_ERR_ARG, "srp_propagate_batch takes no diffuse rays");
     if (p->method != SRP_RKF78 && p->method != SRP_RK4) return fail(ctx, SRP_ERR_ARG, "bad method");
     if (!(p->h0 > 0.0) || !(p->h_min >= 0.0) || p->max_steps <= 0) return fail(ctx, SRP_ERR_ARG, "bad step settings");
     if (p->method == SRP_RKF78 && (!(p->rtol > 0.0) || !(p->atol_pos > 0.0) || !(p->atol_vel > 0.0)))

@@ -177,7 +177,12 @@ struct TraceArgs {
     unsigned *bigt_count;        // entries claimed in bigt (reset by k_frame)
     int big_cap;
     int *rast_bad;               // [S] 1: a slot's list entry did not fit; every ray of it traverses
+    // diffuse secondary rays (n_diffuse > 0; hits must then be recorded)
+    int n_diffuse;
+    unsigned diffuse_seed;
+    double *dpart;               // [S][kDiffBlocks][6] unscaled force / torque of the diffuse rays
 };
+constexpr int kDiffBlocks = 64;  // k_diffuse blocks per slot (fixed: the sums have a fixed order)
 constexpr int kPixCand = 2;      // uncertain triangles kept per pixel (more: the ray traverses)
 constexpr int kRastSmall = 64;   // largest pixel box one thread rasterises
 constexpr int kRastChunk = 16;   // larger triangles: chunks of 16 x 16 pixels, one warp each

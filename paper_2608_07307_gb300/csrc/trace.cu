@@ -1242,6 +1242,152 @@ __device__ void refine_ray(const TraceCtx &B, const TraceArgs &a, int s, int ray
     acc[7] += (double)nseg_done;
 }
 
+// ------------------------------------------------------- diffuse rays
+// SplitMix64 output number c of the stream seeded with `seed` (Steele, Lea &
+// Flood, OOPSLA 2014): the state after c + 1 golden-ratio increments, mixed.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long c)
+{
+    unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Cosine-weighted direction about the unit normal nf for sample counter c:
+// uniforms from outputs 2c and 2c + 1 (top 53 bits), a uniform point of the
+// unit disc lifted to the hemisphere (Malley's method), in the orthonormal
+// basis of Duff et al. (JCGT 2017) around nf.
+__device__ __forceinline__ void diffuse_dir(unsigned long long seed, unsigned long long c, const double *nf, double *w)
+{
+    const double u1 = (double)(splitmix64_at(seed, 2ull * c) >> 11) * 0x1.0p-53;
+    const double u2 = (double)(splitmix64_at(seed, 2ull * c + 1ull) >> 11) * 0x1.0p-53;
+    double sp, cp;
+    sincos(6.283185307179586 * u2, &sp, &cp);
+    const double rr = sqrt(u1), lz = sqrt(1.0 - u1);
+    const double sign = copysign(1.0, nf[2]);
+    const double a = -1.0 / (sign + nf[2]);
+    const double b = nf[0] * nf[1] * a;
+    const double t1[3] = {1.0 + sign * nf[0] * nf[0] * a, sign * b, -sign * nf[0]};
+    const double t2[3] = {b, sign + nf[1] * nf[1] * a, -nf[1]};
+    for (int k = 0; k < 3; k++) w[k] = rr * cp * t1[k] + rr * sp * t2[k] + lz * nf[k];
+}
+
+// Unit normal of a triangle from its FP64 vertices (v0 v1 v2 row-major).
+__device__ __forceinline__ void tri_normal64(const double *v, double *n)
+{
+    double e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]}, e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double il = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int k = 0; k < 3; k++) n[k] *= il;
+}
+
+// Diffuse secondary rays of every ray of slot s (grid: kDiffBlocks x slots,
+// a thread per primary ray in turn).  The ray's segments are replayed in FP64
+// through the triangles the trace recorded (hit point on the triangle's
+// plane, specular direction), and each hit of a segment with a next level
+// emits K rays of weight w rho_d / K, cosine-distributed about the lit side's
+// normal, traced with the FP64 traversal; each deposits the per-hit law at
+// its hit.  Sums per block in a fixed order: the result is reproducible.
+__global__ void __launch_bounds__(128) k_diffuse(TraceArgs a)
+{
+    __shared__ TraceCtx B;
+    __shared__ double red[4][6];
+    const int s = blockIdx.y;
+    load_ctx(B, a, s);
+    __syncthreads();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    if (!B.skip) {
+        const SlotDesc &D = a.sd[s];
+        const int N = D.N, nseg = D.nseg, K = a.n_diffuse;
+        const size_t R = (size_t)N * N;
+        const int *tri_pos = D.mesh->tri_pos;
+        int flags = 0;
+        for (size_t ray = (size_t)blockIdx.x * blockDim.x + threadIdx.x; ray < R; ray += (size_t)gridDim.x * blockDim.x) {
+            const int32_t *hq = a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride;
+            const int i = (int)(ray / N), j = (int)(ray % N);
+            const double uc = B.umin + pix64(((double)i + 0.5) * B.Du, B.rN, N);
+            const double vc = B.vmin + pix64(((double)j + 0.5) * B.Dv, B.rN, N);
+            const double w0 = B.wmin - kStandoff;
+            double o[3], d[3];
+            for (int k = 0; k < 3; k++) { o[k] = uc * B.u[k] + vc * B.v[k] + w0 * B.d[k]; d[k] = B.d[k]; }
+            double wgt = 1.0;
+            for (int k = 0; k + 1 < nseg; k++) {
+                const int h = hq[k];
+                if (h < 0) break;
+                const int t = __ldg(tri_pos + h);
+                const int p = part_of_sorted(D.mesh, t);
+                const int tl = t - B.part[p].tri_begin;
+                double v[9], n[3];
+                tri_v64(B, p, tl, v);
+                tri_normal64(v, n);
+                // hit point on the triangle's plane
+                const double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+                const double th = ((v[0] - o[0]) * n[0] + (v[1] - o[1]) * n[1] + (v[2] - o[2]) * n[2]) / dn;
+                double x[3];
+                for (int c = 0; c < 3; c++) x[c] = o[c] + th * d[c];
+                const int side = dn < 0.0 ? 0 : 1;
+                const double sg = side ? -1.0 : 1.0;
+                const unsigned mt = B.tri_mat[B.part[p].tri_begin + tl];
+                const int mi = side ? (int)(mt >> 16) : (int)(mt & 0xffffu);
+                const double rs = B.mat64[2 * mi], rd = B.mat64[2 * mi + 1];
+                if (rd > 0.0) {
+                    const double nf[3] = {sg * n[0], sg * n[1], sg * n[2]};
+                    const double wd = wgt * rd / K;
+                    for (int q = 0; q < K; q++) {
+                        const unsigned long long c =
+                            ((unsigned long long)ray * (unsigned long long)nseg + (unsigned long long)k) *
+                                (unsigned long long)K + (unsigned long long)q;
+                        Ray64 r2;
+                        diffuse_dir((unsigned long long)a.diffuse_seed, c, nf, r2.d);
+                        for (int e = 0; e < 3; e++) r2.o[e] = x[e];
+                        ray64_setup(r2);
+                        double t2;
+                        int p2, tl2, o2;
+                        nearest64(B, r2, B.eps, h, t2, p2, tl2, o2, flags);
+                        if (p2 < 0) continue;
+                        double v2[9], n2[3];
+                        tri_v64(B, p2, tl2, v2);
+                        tri_normal64(v2, n2);
+                        const double dn2 = r2.d[0] * n2[0] + r2.d[1] * n2[1] + r2.d[2] * n2[2];
+                        const int side2 = dn2 < 0.0 ? 0 : 1;
+                        const double sg2 = side2 ? -1.0 : 1.0;
+                        const unsigned mt2 = B.tri_mat[B.part[p2].tri_begin + tl2];
+                        const int mi2 = side2 ? (int)(mt2 >> 16) : (int)(mt2 & 0xffffu);
+                        const double rs2 = B.mat64[2 * mi2], rd2 = B.mat64[2 * mi2 + 1];
+                        const double cs2 = -sg2 * dn2;
+                        double F[3], arm[3];
+                        for (int e = 0; e < 3; e++) {
+                            F[e] = wd * ((1.0 - rs2) * r2.d[e] - 2.0 * (rs2 * cs2 + rd2 / 3.0) * sg2 * n2[e]);
+                            arm[e] = x[e] + t2 * r2.d[e] - B.c_ref[e];
+                        }
+                        acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
+                        acc[3] += arm[1] * F[2] - arm[2] * F[1];
+                        acc[4] += arm[2] * F[0] - arm[0] * F[2];
+                        acc[5] += arm[0] * F[1] - arm[1] * F[0];
+                    }
+                }
+                wgt *= rs;
+                if (wgt == 0.0) break;
+                for (int c = 0; c < 3; c++) { d[c] = d[c] - 2.0 * dn * n[c]; o[c] = x[c]; }
+            }
+        }
+        if (flags) atomicOr(&a.pose[s].flags, flags);
+    }
+    // block sum in a fixed order: warps by shuffles, then the four warps in turn
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < 6; k++) {
+        const double x = warp_sum(acc[k]);
+        if (lane == 0) red[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        a.dpart[((size_t)s * kDiffBlocks + blockIdx.x) * 6 + k] = ((red[0][k] + red[1][k]) + red[2][k]) + red[3][k];
+    }
+}
+
 // ------------------------------------------------------------- reduce
 // First level: block b of slot s sums tiles [b * chunk, (b + 1) * chunk), and
 // re-traces in FP64 the rays its tiles handed off (a walk bound, or more
@@ -1331,6 +1477,9 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
     __shared__ double red[kPart];
     block_sum(acc, red);
     if (threadIdx.x == 0) {
+        if (a.n_diffuse > 0)
+            for (int b = 0; b < kDiffBlocks; b++)
+                for (int k = 0; k < 6; k++) red[k] += a.dpart[((size_t)s * kDiffBlocks + b) * 6 + k];
         const SlotPose &P = a.pose[s];
         double Du = ord_to_dbl(P.wmax_bits[0]) - ord_to_dbl(P.wmin_bits[0]);
         double Dv = ord_to_dbl(P.wmax_bits[1]) - ord_to_dbl(P.wmin_bits[1]);
@@ -1388,6 +1537,8 @@ cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, d
                           unsigned long long *stats_accum, cudaStream_t st)
 {
     k_reduce1<<<dim3(kRed1, S), 256, 0, st>>>(a);
+    // diffuse secondaries after the FP64 re-trace (which records the hits of the rays it takes)
+    if (a.n_diffuse > 0) k_diffuse<<<dim3(kDiffBlocks, S), 128, 0, st>>>(a);
     k_reduce<<<S, 256, 0, st>>>(a, eval0, force, torque, err_flags, stats_accum);
     return cudaGetLastError();
 }

@@ -60,7 +60,8 @@ class MeshDesc(C.Structure):
 
 class EvalParams(C.Structure):
     _fields_ = [("N", C.c_int32), ("bounces", C.c_int32), ("P0", C.c_double), ("eps_rel", C.c_double),
-                ("panel_mode", C.c_int32), ("flags", C.c_int32)]
+                ("panel_mode", C.c_int32), ("flags", C.c_int32), ("n_diffuse", C.c_int32),
+                ("diffuse_seed", C.c_uint32)]
 
 
 class EvalStats(C.Structure):
@@ -284,11 +285,13 @@ class Context:
 
     def eval_batch(self, mesh_id: int, sun_dirs, sun_dist=None, N: int = 256, bounces: int = 1, P0: float = 4.56e-6,
                    eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, hits: bool = False, count: bool = False,
-                   timing: bool = False, out=None, traverse: bool = False):
+                   timing: bool = False, out=None, traverse: bool = False, n_diffuse: int = 0,
+                   diffuse_seed: int = 0):
         """Force [n,3] (N) and torque [n,3] (N m); with hits=True also the per-ray
         hit triangle ids [n, N*N, bounces+1].  Outputs live where the input lives
         (CUDA tensor in, CUDA tensors out; numpy in, numpy out) unless `out`
-        = (force, torque[, hits]) is given."""
+        = (force, torque[, hits]) is given.  n_diffuse: diffuse secondary rays
+        per hit (srp_eval_params)."""
         n = int(sun_dirs.shape[0])
         cuda = _is_cuda(sun_dirs)
         if isinstance(sun_dirs, np.ndarray):
@@ -312,7 +315,7 @@ class Context:
             force, torque = np.empty((n, 3)), np.empty((n, 3))
             hit = np.empty((n, N * N, nseg), np.int32) if hits else None
         p = EvalParams(N, bounces, P0, eps_rel, panel_mode, (EVAL_COUNT if count else 0) | (EVAL_TIMING if timing else 0)
-                       | (EVAL_TRAVERSE if traverse else 0))
+                       | (EVAL_TRAVERSE if traverse else 0), n_diffuse, diffuse_seed)
         ps, k1 = _ptr(sun_dirs)
         pd, k2 = _ptr(sun_dist)
         pf, k3 = _ptr(force)
@@ -327,7 +330,8 @@ class Context:
                   atol_vel: float = 1e-9, h0: float = 60.0, h_min: float = 1e-6, h_max: float = 0.0,
                   max_steps: int = 10_000_000, poll: int = 16, N: int = 64, bounces: int = 1, P0: float = 4.56e-6,
                   eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, h_cap: int = 0, h_replay=None,
-                  host_loop: bool = False, traverse: bool = False, spad=None):
+                  host_loop: bool = False, traverse: bool = False, spad=None, n_diffuse: int = 0,
+                  diffuse_seed: int = 0):
         """srp_propagate: y1 [n, 6], per-trajectory stats (list of dicts) and,
         with h_cap > 0, the accepted step sizes [n, h_cap] (NaN padded).
         h_replay [n, k]: take exactly these RKF7(8) steps (replay).
@@ -339,7 +343,8 @@ class Context:
         hr = None if h_replay is None else np.ascontiguousarray(np.asarray(h_replay, np.float64).reshape(n, -1))
         p = PropParams(method, central, int(j2), int(sun3), int(srp_on), attitude, (C.c_double * 4)(*q),
                        epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, int(host_loop),
-                       EvalParams(N, bounces, P0, eps_rel, panel_mode, EVAL_TRAVERSE if traverse else 0),
+                       EvalParams(N, bounces, P0, eps_rel, panel_mode, EVAL_TRAVERSE if traverse else 0, n_diffuse,
+                                  diffuse_seed),
                        hr.ctypes.data if hr is not None else None, 0 if hr is None else hr.shape[1])
         keep = None
         if spad is not None:
