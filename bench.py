@@ -68,6 +68,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     p.add_argument("--no-spad", action="store_true", help="skip the SPAD interpolation measurement")
     p.add_argument("--no-panels", action="store_true", help="skip the fixed vs movable panel study")
+    p.add_argument("--no-diffuse", action="store_true", help="skip the diffuse-ray measurement")
     p.add_argument("--batch-traj", type=int, default=256, help="trajectories of the batched form")
     p.add_argument("--grad-arc-steps", type=int, default=1000,
                    help="RK4 steps of the timed adjoint arc (the full differentiated arc is 10000)")
@@ -247,6 +248,39 @@ def bench_spad(ctx, mid, direct):
     return {"workload": f"the propagation workload's arc with the SRP force interpolated from 20 x 10 SPAD tables "
                         f"built at N={N}, bounces={bounces}; {n_traj} dispersed 30-day SPAD arcs in one call",
             "tables": out, "many": many}
+
+
+# ------------------------------------------------- diffuse secondary rays
+def bench_diffuse(ctx, facet=0.05, N=256, bounces=2, K=16, n_dirs=64, reps=3):
+    """The paper's RayTrace GPU configuration (Sec. 8.1: a 256 x 256 window,
+    two levels of secondary reflections, 16 diffuse rays) on the 50k-triangle
+    spacecraft: evaluations/s with the diffuse rays against the same
+    evaluations with specular bounces only (srp_eval_batch, device inputs,
+    best of `reps`)."""
+    import numpy as np
+    import torch
+    from paper_2608_07307_gb300 import inputs as I
+    m = I.spacecraft(facet)
+    mid = ctx.load_mesh(m)
+    dirs = torch.tensor(I.sun_dirs_fibonacci(4096)[::4096 // n_dirs][:n_dirs], device="cuda")
+    out = {}
+    for name, k in (("specular", 0), ("diffuse", K)):
+        ctx.eval_batch(mid, dirs[:4], N=N, bounces=bounces, n_diffuse=k)  # warm-up
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.eval_batch(mid, dirs, N=N, bounces=bounces, n_diffuse=k, diffuse_seed=1)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        out[name] = {"evals_per_s": n_dirs / best, "seconds": best}
+    F0, _ = ctx.eval_batch(mid, dirs, N=N, bounces=bounces)
+    F1, _ = ctx.eval_batch(mid, dirs, N=N, bounces=bounces, n_diffuse=K, diffuse_seed=1)
+    rel = (torch.linalg.norm(F1 - F0, dim=1) / torch.linalg.norm(F0, dim=1)).cpu().numpy()
+    return {"workload": f"spacecraft facet {facet} m ({m.n_tris} triangles), N={N}, {bounces} levels, {K} diffuse "
+                        f"rays per hit, {n_dirs} Fibonacci directions",
+            "runs": out, "cost_vs_specular": out["specular"]["evals_per_s"] / out["diffuse"]["evals_per_s"],
+            "diffuse_share_of_force": {"median": float(np.median(rel)), "max": float(rel.max())}}
 
 
 # ------------------------------------------------ fixed vs movable panels
@@ -593,6 +627,8 @@ def run_native(a):
             line["spad"] = bench_spad(ctx, mid, direct)
     if not a.no_panels:
         line["panels"] = bench_panels(ctx)
+    if not a.no_diffuse:
+        line["diffuse"] = bench_diffuse(ctx)
     if not a.no_grad:
         line["differentiated"] = bench_differentiated(ctx, stream, a.grad_arc_steps)
     if not a.no_batch:
