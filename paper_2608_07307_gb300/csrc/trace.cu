@@ -1283,13 +1283,51 @@ __device__ __forceinline__ void tri_normal64(const double *v, double *n)
     for (int k = 0; k < 3; k++) n[k] *= il;
 }
 
-// Diffuse secondary rays of every ray of slot s (grid: kDiffBlocks x slots,
-// a thread per primary ray in turn).  The ray's segments are replayed in FP64
+// One diffuse sample (counter c) leaving hit point x of triangle `src` about
+// the lit side's normal nf with weight wd: traced with the FP64 traversal,
+// its per-hit force and torque about c_ref added to acc.
+__device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long long seed, unsigned long long c,
+                                               const double *x, const double *nf, int src, double wd, double *acc,
+                                               int &flags)
+{
+    Ray64 r;
+    diffuse_dir(seed, c, nf, r.d);
+    for (int e = 0; e < 3; e++) r.o[e] = x[e];
+    ray64_setup(r);
+    double t;
+    int p, tl, orig;
+    nearest64(B, r, B.eps, src, t, p, tl, orig, flags);
+    if (p < 0) return;
+    double v[9], n[3];
+    tri_v64(B, p, tl, v);
+    tri_normal64(v, n);
+    const double dn = r.d[0] * n[0] + r.d[1] * n[1] + r.d[2] * n[2];
+    const int side = dn < 0.0 ? 0 : 1;
+    const double sg = side ? -1.0 : 1.0;
+    const unsigned mt = B.tri_mat[B.part[p].tri_begin + tl];
+    const int mi = side ? (int)(mt >> 16) : (int)(mt & 0xffffu);
+    const double rs = B.mat64[2 * mi], rd = B.mat64[2 * mi + 1];
+    const double cs = -sg * dn;
+    double F[3], arm[3];
+    for (int e = 0; e < 3; e++) {
+        F[e] = wd * ((1.0 - rs) * r.d[e] - 2.0 * (rs * cs + rd / 3.0) * sg * n[e]);
+        arm[e] = x[e] + t * r.d[e] - B.c_ref[e];
+    }
+    acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
+    acc[3] += arm[1] * F[2] - arm[2] * F[1];
+    acc[4] += arm[2] * F[0] - arm[0] * F[2];
+    acc[5] += arm[0] * F[1] - arm[1] * F[0];
+}
+
+// Diffuse secondary rays of every ray of slot s (grid: kDiffBlocks x slots; a
+// thread per (primary ray, sample q) work item in turn, so the K lanes of one
+// ray share its control flow).  The ray's segments are replayed in FP64
 // through the triangles the trace recorded (hit point on the triangle's
-// plane, specular direction), and each hit of a segment with a next level
-// emits K rays of weight w rho_d / K, cosine-distributed about the lit side's
-// normal, traced with the FP64 traversal; each deposits the per-hit law at
-// its hit.  Sums per block in a fixed order: the result is reproducible.
+// plane, specular direction), and at each hit of a segment with a next level
+// sample q of the K rays of weight w rho_d / K, cosine-distributed about the
+// lit side's normal, is traced with the FP64 traversal and deposits the
+// per-hit law at its hit.  Sums per block in a fixed order: the result is
+// reproducible.
 __global__ void __launch_bounds__(128) k_diffuse(TraceArgs a)
 {
     __shared__ TraceCtx B;
@@ -1304,7 +1342,10 @@ __global__ void __launch_bounds__(128) k_diffuse(TraceArgs a)
         const size_t R = (size_t)N * N;
         const int *tri_pos = D.mesh->tri_pos;
         int flags = 0;
-        for (size_t ray = (size_t)blockIdx.x * blockDim.x + threadIdx.x; ray < R; ray += (size_t)gridDim.x * blockDim.x) {
+        const size_t items = R * (size_t)K;
+        for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (size_t)gridDim.x * blockDim.x) {
+            const size_t ray = it / K;
+            const int q = (int)(it - ray * K);
             const int32_t *hq = a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride;
             const int i = (int)(ray / N), j = (int)(ray % N);
             const double uc = B.umin + pix64(((double)i + 0.5) * B.Du, B.rN, N);
@@ -1334,39 +1375,10 @@ __global__ void __launch_bounds__(128) k_diffuse(TraceArgs a)
                 const double rs = B.mat64[2 * mi], rd = B.mat64[2 * mi + 1];
                 if (rd > 0.0) {
                     const double nf[3] = {sg * n[0], sg * n[1], sg * n[2]};
-                    const double wd = wgt * rd / K;
-                    for (int q = 0; q < K; q++) {
-                        const unsigned long long c =
-                            ((unsigned long long)ray * (unsigned long long)nseg + (unsigned long long)k) *
-                                (unsigned long long)K + (unsigned long long)q;
-                        Ray64 r2;
-                        diffuse_dir((unsigned long long)a.diffuse_seed, c, nf, r2.d);
-                        for (int e = 0; e < 3; e++) r2.o[e] = x[e];
-                        ray64_setup(r2);
-                        double t2;
-                        int p2, tl2, o2;
-                        nearest64(B, r2, B.eps, h, t2, p2, tl2, o2, flags);
-                        if (p2 < 0) continue;
-                        double v2[9], n2[3];
-                        tri_v64(B, p2, tl2, v2);
-                        tri_normal64(v2, n2);
-                        const double dn2 = r2.d[0] * n2[0] + r2.d[1] * n2[1] + r2.d[2] * n2[2];
-                        const int side2 = dn2 < 0.0 ? 0 : 1;
-                        const double sg2 = side2 ? -1.0 : 1.0;
-                        const unsigned mt2 = B.tri_mat[B.part[p2].tri_begin + tl2];
-                        const int mi2 = side2 ? (int)(mt2 >> 16) : (int)(mt2 & 0xffffu);
-                        const double rs2 = B.mat64[2 * mi2], rd2 = B.mat64[2 * mi2 + 1];
-                        const double cs2 = -sg2 * dn2;
-                        double F[3], arm[3];
-                        for (int e = 0; e < 3; e++) {
-                            F[e] = wd * ((1.0 - rs2) * r2.d[e] - 2.0 * (rs2 * cs2 + rd2 / 3.0) * sg2 * n2[e]);
-                            arm[e] = x[e] + t2 * r2.d[e] - B.c_ref[e];
-                        }
-                        acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
-                        acc[3] += arm[1] * F[2] - arm[2] * F[1];
-                        acc[4] += arm[2] * F[0] - arm[0] * F[2];
-                        acc[5] += arm[0] * F[1] - arm[1] * F[0];
-                    }
+                    const unsigned long long c =
+                        ((unsigned long long)ray * (unsigned long long)nseg + (unsigned long long)k) *
+                            (unsigned long long)K + (unsigned long long)q;
+                    diffuse_sample(B, (unsigned long long)a.diffuse_seed, c, x, nf, h, wgt * rd / K, acc, flags);
                 }
                 wgt *= rs;
                 if (wgt == 0.0) break;
