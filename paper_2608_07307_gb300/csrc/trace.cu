@@ -1283,9 +1283,41 @@ __device__ __forceinline__ void tri_normal64(const double *v, double *n)
     for (int k = 0; k < 3; k++) n[k] *= il;
 }
 
+// Settle an FP32 traversal's result in FP64: the FP64 watertight test of each
+// uncertain candidate and of the nearest certain FP32 hit against the exact
+// ray; the nearest t above tlo wins, equal t to the lowest original id.  Every
+// other triangle was certainly missed, certainly farther, or culled beyond
+// the certain hit plus its band.
+__device__ void settle64(const TraceCtx &B, const Ray64 &r, double tlo, int skip, const Cands &cd, const Best32 &best,
+                         double &bt, int &bp, int &btl)
+{
+    bt = INFINITY;
+    bp = -1;
+    btl = -1;
+    int bo = 0x7fffffff;
+    for (int c = 0; c <= cd.n; c++) {
+        int p, tl;
+        if (c < cd.n) { p = cd.id[c] >> 24; tl = cd.id[c] & 0xffffff; }
+        else if (best.part >= 0) { p = best.part; tl = best.tl; }
+        else break;
+        const int orig = __float_as_int(__ldg(B.part[p].tri + (size_t)tl * 3).w);
+        if (orig == skip) continue;
+        double v[9], U, V, W, det, T;
+        tri_v64(B, p, tl, v);
+        wt64(r, v, U, V, W, det, T);
+        const bool out = (U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0);
+        if (out || det == 0.0) continue;
+        const double t = T / det;
+        if (t > tlo && (t < bt || (t == bt && orig < bo))) { bt = t; bp = p; btl = tl; bo = orig; }
+    }
+}
+
 // One diffuse sample (counter c) leaving hit point x of triangle `src` about
-// the lit side's normal nf with weight wd: traced with the FP64 traversal,
-// its per-hit force and torque about c_ref added to acc.
+// the lit side's normal nf with weight wd: traced in FP32 with error-bounded
+// decisions (as a secondary segment of the trace, the origin error being the
+// rounding of the FP64 point), the uncertain ones settled in FP64; the FP64
+// traversal when the candidate list overflows.  Its per-hit force and torque
+// about c_ref are added to acc.
 __device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long long seed, unsigned long long c,
                                                const double *x, const double *nf, int src, double wd, double *acc,
                                                int &flags)
@@ -1295,8 +1327,24 @@ __device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long 
     for (int e = 0; e < 3; e++) r.o[e] = x[e];
     ray64_setup(r);
     double t;
-    int p, tl, orig;
-    nearest64(B, r, B.eps, src, t, p, tl, orig, flags);
+    int p, tl;
+    {
+        Ray32 q;
+        for (int e = 0; e < 3; e++) { q.o[e] = (float)r.o[e]; q.d[e] = (float)r.d[e]; }
+        ray_setup(q);
+        const float delta = 2.0f * B.delta_s;
+        const float tau = 64.0f * delta + 32.0f * kU * (B.R + B.L);
+        Best32 b;
+        Counts cn = {0u, 0u, 0u, {0u, 0u, 0u, 0u}, 0};
+        Cands cd;
+        if (nearest32<false>(B, q, false, 0.0f, 0.0f, B.eps32, src, -1, kEmptyChild, delta, tau, b, cn, cd)) {
+            settle64(B, r, B.eps, src, cd, b, t, p, tl);
+        } else {
+            int orig;
+            nearest64(B, r, B.eps, src, t, p, tl, orig, flags);
+        }
+        flags |= cn.flags;  // a walk bound is an error, as in the trace
+    }
     if (p < 0) return;
     double v[9], n[3];
     tri_v64(B, p, tl, v);
