@@ -140,6 +140,11 @@ typedef struct {
  * Both give the same hits and the same force bits; this flag is for testing
  * that and for meshes whose triangles each cover much of the window. */
 #define SRP_EVAL_TRAVERSE 8
+/* Test of the traversal's error path: every BVH walk is bounded at one step,
+ * so any evaluation that walks the tree stops there and returns
+ * SRP_ERR_STACK (a bounded loop that sets a device flag; nothing faults or
+ * waits).  For tests only. */
+#define SRP_EVAL_TEST_WALK_BOUND 16
 
 /* Counters of the last srp_eval_batch call (summed over its evaluations). */
 typedef struct {
@@ -540,6 +545,46 @@ srp_status srp_eval_noalloc(const double *tri_xyz, const int32_t *tri_mat, int32
                             int32_t n_mats, const double sun_dir[3], double sun_dist_au, const double c_ref[3],
                             int32_t N, int32_t bounces, double P0, double eps_rel, double *force, double *torque,
                             void *cuda_stream);
+
+/* ------------------------------------------------------------ diagnostics */
+/*
+ * Cap on the library's device memory in this process (every context and
+ * mesh), in bytes; 0 removes it.  An allocation that would exceed the cap
+ * fails with SRP_ERR_OOM, as a full device would; the context stays usable.
+ * srp_memory_usage reports the bytes the library holds and the cap.
+ * Errors: SRP_ERR_ARG (NULL ctx or outputs).
+ */
+srp_status srp_set_memory_limit(srp_ctx *ctx, uint64_t bytes);
+srp_status srp_memory_usage(srp_ctx *ctx, uint64_t *used, uint64_t *limit);
+
+/*
+ * The LSD radix sort of the BVH build (csrc/build.cu): sorts n (key, value)
+ * pairs in place by the key bits [0, key_bits), key_bits rounded up to whole
+ * bytes (8 bits per pass), stable (equal keys keep their input order).
+ * keys [n], vals [n]: host or device.
+ * Errors: SRP_ERR_ARG (n < 0, NULL arrays, key_bits outside 1..64),
+ * SRP_ERR_OOM, SRP_ERR_CUDA.
+ */
+srp_status srp_sort_pairs(srp_ctx *ctx, int32_t n, uint64_t *keys, int32_t *vals, int32_t key_bits);
+
+/*
+ * Structural check of a mesh's acceleration structure as evaluations use it:
+ * the mesh is posed for the body-frame Sun direction (tracking panels; NULL
+ * for +z) and refit as in srp_eval_batch, then each part's 4-wide tree is
+ * walked from its root on the device.
+ *   report [SRP_CHECK_N] out (host):
+ *     [0] leaf references (a correct tree has one per triangle: n_tris)
+ *     [1] triangles referenced by no leaf or by more than one
+ *     [2] child boxes not inside the box their parent holds for them (the
+ *         root's not inside the part's root box)
+ *     [3] leaf triangles with a vertex outside their leaf box
+ *     [4] nodes reached
+ *     [5] walks stopped by their bound
+ *     [6] triangles of the mesh, [7] parts
+ * Errors: SRP_ERR_ARG, SRP_ERR_STATE (bad mesh id), SRP_ERR_OOM, SRP_ERR_CUDA.
+ */
+#define SRP_CHECK_N 8
+srp_status srp_mesh_check(srp_ctx *ctx, int32_t mesh_id, const double *sun_dir_body, int64_t *report);
 
 #ifdef __cplusplus
 }

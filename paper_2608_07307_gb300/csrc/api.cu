@@ -8,8 +8,10 @@
 #include <cstring>
 #include <limits>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "srp_internal.cuh"
@@ -152,11 +154,50 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory of the library in this process, against an optional cap
+// (srp_set_memory_limit): every allocation and release of this file goes
+// through dalloc / dfree, which book the bytes.
+std::mutex g_mem_mu;
+size_t g_mem_limit = 0, g_mem_used = 0;
+std::unordered_map<void *, size_t> g_mem_sizes;
+
+cudaError_t dalloc_raw(void **p, size_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    *p = nullptr;
+    if (g_mem_limit && g_mem_used + bytes > g_mem_limit) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    g_mem_used += bytes;
+    g_mem_sizes[*p] = bytes;
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t bytes)
+{
+    return dalloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
+void dfree(void *p)
+{
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        auto it = g_mem_sizes.find(p);
+        if (it != g_mem_sizes.end()) {
+            g_mem_used -= it->second;
+            g_mem_sizes.erase(it);
+        }
+    }
+    cudaFree(p);
+}
+
 template <class T>
 cudaError_t dmalloc(std::vector<void *> &owner, T **p, size_t count)
 {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = dalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) return e;
     owner.push_back(q);
     *p = static_cast<T *>(q);
@@ -167,11 +208,11 @@ template <class T>
 cudaError_t grow(T **p, size_t *cap, size_t need, bool zero)
 {
     if (need <= *cap) return cudaSuccess;
-    if (*p) cudaFree(*p);
+    if (*p) dfree(*p);
     *p = nullptr;
     *cap = 0;
     size_t n = std::max<size_t>(need, 1);
-    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    cudaError_t e = dalloc((void **)p, n * sizeof(T));
     if (e != cudaSuccess) return e;
     if (zero) {
         e = cudaMemset(*p, 0, n * sizeof(T));
@@ -197,8 +238,8 @@ cudaError_t grow_fill(T **p, size_t *cap, size_t need, int byte)
 void free_mesh(Mesh *m)
 {
     if (!m) return;
-    for (void *p : m->slot_allocs) cudaFree(p);
-    for (void *p : m->allocs) cudaFree(p);
+    for (void *p : m->slot_allocs) dfree(p);
+    for (void *p : m->allocs) dfree(p);
     delete m;
 }
 
@@ -207,7 +248,7 @@ srp_status ensure_slots(srp_ctx *ctx, Mesh *m, int S)
 {
     if (m->slots >= S) return SRP_OK;
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    for (void *p : m->slot_allocs) cudaFree(p);
+    for (void *p : m->slot_allocs) dfree(p);
     m->slot_allocs.clear();
     m->slots = 0;
     const MeshDev &h = m->h;
@@ -640,6 +681,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         }
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
         a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : ((adj || prm->n_diffuse > 0) ? stage : nullptr);
+        a.walk_limit_test = (prm->flags & SRP_EVAL_TEST_WALK_BOUND) ? 1 : 0;
         if (prm->n_diffuse > 0 && nseg > 1) {
             a.n_diffuse = prm->n_diffuse;
             a.diffuse_seed = prm->diffuse_seed;
@@ -863,9 +905,9 @@ srp_status srp_create(srp_ctx **out, int32_t device, void *cuda_stream)
         }
         ctx->own_stream = true;
     }
-    if (cudaMalloc(&ctx->err_flags, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&ctx->stats, 16 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&ctx->prop_done, sizeof(int)) != cudaSuccess) {
+    if (dalloc(&ctx->err_flags, sizeof(int)) != cudaSuccess ||
+        dalloc(&ctx->stats, 16 * sizeof(unsigned long long)) != cudaSuccess ||
+        dalloc(&ctx->prop_done, sizeof(int)) != cudaSuccess) {
         srp_destroy(ctx);
         return SRP_ERR_OOM;
     }
@@ -889,38 +931,38 @@ void srp_destroy(srp_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (Mesh *m : ctx->meshes) free_mesh(m);
-    cudaFree(ctx->pose);
-    cudaFree(ctx->partials);
-    cudaFree(ctx->pcounts);
-    cudaFree(ctx->amb_list);
-    cudaFree(ctx->partials1);
-    cudaFree(ctx->dpart);
-    cudaFree(ctx->tctx);
-    cudaFree(ctx->prop_io);
-    cudaFree(ctx->spad_buf);
-    cudaFree(ctx->prop_state);
-    cudaFree(ctx->prop_hlog);
-    cudaFree(ctx->prop_replay);
-    cudaFree(ctx->prop_done);
-    cudaFree(ctx->amb_count);
-    cudaFree(ctx->pix_key);
-    cudaFree(ctx->pix_cnt);
-    cudaFree(ctx->pix_cand);
-    cudaFree(ctx->big);
-    cudaFree(ctx->big_count);
-    cudaFree(ctx->bigt);
-    cudaFree(ctx->bigt_count);
-    cudaFree(ctx->rast_bad);
-    cudaFree(ctx->io);
-    cudaFree(ctx->hits);
-    cudaFree(ctx->adj_partials);
-    cudaFree(ctx->win_ids);
-    cudaFree(ctx->gio);
-    cudaFree(ctx->sdesc);
-    cudaFree(ctx->arc_hits);
-    cudaFree(ctx->arc_buf);
-    cudaFree(ctx->err_flags);
-    cudaFree(ctx->stats);
+    dfree(ctx->pose);
+    dfree(ctx->partials);
+    dfree(ctx->pcounts);
+    dfree(ctx->amb_list);
+    dfree(ctx->partials1);
+    dfree(ctx->dpart);
+    dfree(ctx->tctx);
+    dfree(ctx->prop_io);
+    dfree(ctx->spad_buf);
+    dfree(ctx->prop_state);
+    dfree(ctx->prop_hlog);
+    dfree(ctx->prop_replay);
+    dfree(ctx->prop_done);
+    dfree(ctx->amb_count);
+    dfree(ctx->pix_key);
+    dfree(ctx->pix_cnt);
+    dfree(ctx->pix_cand);
+    dfree(ctx->big);
+    dfree(ctx->big_count);
+    dfree(ctx->bigt);
+    dfree(ctx->bigt_count);
+    dfree(ctx->rast_bad);
+    dfree(ctx->io);
+    dfree(ctx->hits);
+    dfree(ctx->adj_partials);
+    dfree(ctx->win_ids);
+    dfree(ctx->gio);
+    dfree(ctx->sdesc);
+    dfree(ctx->arc_hits);
+    dfree(ctx->arc_buf);
+    dfree(ctx->err_flags);
+    dfree(ctx->stats);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     for (int b = 0; b < kLanes; b++) {
         if (ctx->lane[b]) cudaStreamSynchronize(ctx->lane[b]), cudaStreamDestroy(ctx->lane[b]);
@@ -1081,7 +1123,7 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
 
     cudaStream_t st = ctx->stream;
     std::vector<void *> tmp;  // build-only device buffers
-    auto free_tmp = [&]() { cudaStreamSynchronize(st); for (void *p : tmp) cudaFree(p); tmp.clear(); };
+    auto free_tmp = [&]() { cudaStreamSynchronize(st); for (void *p : tmp) dfree(p); tmp.clear(); };
     auto bail = [&](srp_status c, const char *what, cudaError_t e) {
         free_tmp();
         free_mesh(m);
@@ -1577,6 +1619,101 @@ srp_status srp_spad_eval(srp_ctx *ctx, const srp_spad_grid *g, const double *tab
     return SRP_OK;
 }
 
+srp_status srp_set_memory_limit(srp_ctx *ctx, uint64_t bytes)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    g_mem_limit = (size_t)bytes;
+    return SRP_OK;
+}
+
+srp_status srp_memory_usage(srp_ctx *ctx, uint64_t *used, uint64_t *limit)
+{
+    if (!ctx || !used || !limit) return SRP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    *used = g_mem_used;
+    *limit = g_mem_limit;
+    return SRP_OK;
+}
+
+srp_status srp_sort_pairs(srp_ctx *ctx, int32_t n, uint64_t *keys, int32_t *vals, int32_t key_bits)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    if (n < 0 || (n > 0 && (!keys || !vals)) || key_bits < 1 || key_bits > 64)
+        return fail(ctx, SRP_ERR_ARG, "need n >= 0, keys, vals and 1 <= key_bits <= 64");
+    if (n <= 1) return SRP_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    struct Tmp {
+        std::vector<void *> v;
+        ~Tmp() { for (void *q : v) dfree(q); }
+    } tmp;
+    const size_t sc = radix_sort_scratch_ints(n);
+    unsigned long long *k0, *k1;
+    int *v0, *v1, *scr;
+    CK(ctx, dmalloc(tmp.v, &k0, (size_t)n));
+    CK(ctx, dmalloc(tmp.v, &k1, (size_t)n));
+    CK(ctx, dmalloc(tmp.v, &v0, (size_t)n));
+    CK(ctx, dmalloc(tmp.v, &v1, (size_t)n));
+    CK(ctx, dmalloc(tmp.v, &scr, sc));
+    CK(ctx, cudaMemcpyAsync(k0, keys, sizeof(unsigned long long) * n, cudaMemcpyDefault, st));
+    CK(ctx, cudaMemcpyAsync(v0, vals, sizeof(int) * n, cudaMemcpyDefault, st));
+    CK(ctx, radix_sort_pairs(k0, v0, k1, v1, n, 0, (key_bits + 7) / 8 * 8, scr, sc, st));
+    CK(ctx, cudaMemcpyAsync(keys, k0, sizeof(unsigned long long) * n, cudaMemcpyDefault, st));
+    CK(ctx, cudaMemcpyAsync(vals, v0, sizeof(int) * n, cudaMemcpyDefault, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    return SRP_OK;
+}
+
+srp_status srp_mesh_check(srp_ctx *ctx, int32_t mesh_id, const double *sun_dir_body, int64_t *report)
+{
+    if (!ctx) return SRP_ERR_ARG;
+    ctx->err.clear();
+    if (!report) return fail(ctx, SRP_ERR_ARG, "null report");
+    Mesh *m = get_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, SRP_ERR_STATE, "bad mesh id %d", mesh_id);
+    double s[3] = {0.0, 0.0, 1.0};
+    if (sun_dir_body) for (int k = 0; k < 3; k++) s[k] = sun_dir_body[k];
+    // one evaluation poses the mesh and refits its tree in slot 0 (one slot, one lane)
+    srp_eval_params prm{};
+    prm.N = 1;
+    prm.bounces = 0;
+    prm.P0 = 4.56e-6;
+    prm.eps_rel = 1e-9;
+    prm.panel_mode = SRP_PANELS_TRACK;
+    prm.flags = SRP_EVAL_TRAVERSE;
+    double F[3], T[3];
+    srp_status rc = srp_eval_batch(ctx, mesh_id, &prm, 1, s, nullptr, F, T, nullptr);
+    if (rc) return rc;
+    cudaStream_t st = ctx->stream;
+    struct Tmp {
+        std::vector<void *> v;
+        ~Tmp() { for (void *q : v) dfree(q); }
+    } tmp;
+    const int nt = m->h.n_tris;
+    int *seen;
+    unsigned long long *rep;
+    CK(ctx, dmalloc(tmp.v, &seen, (size_t)nt));
+    CK(ctx, dmalloc(tmp.v, &rep, (size_t)8));
+    CK(ctx, cudaMemsetAsync(seen, 0, sizeof(int) * nt, st));
+    CK(ctx, cudaMemsetAsync(rep, 0, sizeof(unsigned long long) * 8, st));
+    CK(ctx, launch_bvh_check(ctx->tctx, m->h.n_parts, seen, rep, st));
+    std::vector<int> hs(nt);
+    unsigned long long hr[8];
+    CK(ctx, cudaMemcpyAsync(hs.data(), seen, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(hr, rep, sizeof hr, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    int64_t bad = 0;
+    for (int c : hs) bad += c != 1;
+    report[0] = (int64_t)hr[0];
+    report[1] = bad;
+    for (int k = 2; k < 6; k++) report[k] = (int64_t)hr[k];
+    report[6] = nt;
+    report[7] = m->h.n_parts;
+    return SRP_OK;
+}
+
 srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out)
 {
     if (!ctx || !out) return SRP_ERR_ARG;
@@ -1878,8 +2015,8 @@ srp_status srp_autotune(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *pr
         dirs[3 * i] = r * std::cos(ph); dirs[3 * i + 1] = r * std::sin(ph); dirs[3 * i + 2] = z;
     }
     double *d = nullptr;
-    CK(ctx, cudaMalloc(&d, sizeof(double) * 9 * nd));
-    struct Free { double *p; ~Free() { cudaFree(p); } } fr{d};
+    CK(ctx, dalloc(&d, sizeof(double) * 9 * nd));
+    struct Free { double *p; ~Free() { dfree(p); } } fr{d};
     CK(ctx, cudaMemcpy(d, dirs.data(), sizeof(double) * 3 * nd, cudaMemcpyHostToDevice));
     srp_eval_params q = *prm;
     q.flags = 0;
@@ -1968,7 +2105,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     std::vector<void *> owned;
     struct Owner {
         std::vector<void *> &v;
-        ~Owner() { for (void *q : v) cudaFree(q); }
+        ~Owner() { for (void *q : v) dfree(q); }
     } owner{owned};
     int nbx = 0, max_verts = 0, max_dyn = 0;
     size_t n64 = 0, nview = 0, ntri = 0, nnode = 0;

@@ -181,6 +181,7 @@ struct TraceArgs {
     int n_diffuse;
     unsigned diffuse_seed;
     double *dpart;               // [S][kDiffBlocks][6] unscaled force / torque of the diffuse rays
+    int walk_limit_test;         // 1: every BVH walk is bounded at one step (tests of the bound's error path)
 };
 constexpr int kDiffBlocks = 64;  // k_diffuse blocks per slot (fixed: the sums have a fixed order)
 constexpr int kPixCand = 2;      // uncertain triangles kept per pixel (more: the ray traverses)
@@ -360,6 +361,11 @@ cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, 
                               cudaStream_t st);
 cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st,
                               const double *sun_dir = nullptr, const double *sun_dist = nullptr);
+// Structural check of slot 0's BVH (csrc/trace.cu, srp_mesh_check): per part a
+// walk from the root; tri_seen[n_tris] counts the leaf references of each
+// sorted triangle; report[8] (see srp_mesh_check) accumulates violations.
+cudaError_t launch_bvh_check(const unsigned char *tctx, int n_parts, int *tri_seen, unsigned long long *report,
+                             cudaStream_t st);
 // A whole integrator step in one launch (no ray-traced SRP between the stages).
 cudaError_t launch_prop_step(PropState *S, int n, const PropDev &P, double *sun_dir, double *sun_dist, int *n_done,
                              double *h_log, int64_t h_cap, cudaStream_t st);

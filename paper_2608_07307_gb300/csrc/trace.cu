@@ -183,7 +183,7 @@ __global__ void k_frame(TraceArgs a)
         const PartInfo &pi = m->part[p];
         PartView &pv = B.part[p];
         pv.root = pi.tri_count > 1 ? 0 : ~0;
-        pv.limit = pi.node_count + pi.tri_count + 8;
+        pv.limit = a.walk_limit_test ? 1 : pi.node_count + pi.tri_count + 8;
         pv.tri_begin = pi.tri_begin;
         pv.vert_begin = pi.vert_begin;
         pv.v4 = m->tri_v4 + pi.tri_begin;
@@ -1561,6 +1561,93 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
             for (int k = 0; k < 4; k++) atomicAdd(&stats_accum[12 + k], (unsigned long long)red[16 + k]);
         }
     }
+}
+
+// ------------------------------------------------------------ BVH check
+// One thread per part walks the part's 4-wide tree of slot 0 from the root:
+// every child box of a reached node must lie inside the box its parent holds
+// for that node (the root's inside the part's root box), every leaf
+// triangle's three vertices inside its leaf box; each leaf reference is
+// counted per triangle.  report: [0] leaf references, [2] child boxes outside
+// the parent's, [3] leaf triangles outside their box, [4] nodes reached,
+// [5] walks stopped by their bound ([1], [6], [7] are filled on the host).
+__global__ void k_bvh_check(const unsigned char *tctx, int *tri_seen, unsigned long long *report)
+{
+    const TraceCtx &B = *reinterpret_cast<const TraceCtx *>(tctx);
+    const PartView &pv = B.part[blockIdx.x];
+    if (threadIdx.x != 0) return;
+    unsigned long long refs = 0, outside_box = 0, outside_tri = 0, nodes = 0, bound = 0;
+    auto inside = [](const float *in, const float *out) {
+        return in[0] >= out[0] && in[1] <= out[1] && in[2] >= out[2] && in[3] <= out[3] && in[4] >= out[4] &&
+               in[5] <= out[5];
+    };
+    auto tri_inside = [&](int tl, const float *bx) {
+        const float4 *tr = pv.tri + (size_t)tl * 3;
+        bool ok = true;
+        for (int c = 0; c < 3; c++) {
+            const float4 v = tr[c];
+            ok = ok && v.x >= bx[0] && v.x <= bx[1] && v.y >= bx[2] && v.y <= bx[3] && v.z >= bx[4] && v.z <= bx[5];
+        }
+        atomicAdd(tri_seen + pv.tri_begin + tl, 1);
+        refs++;
+        if (!ok) outside_tri++;
+    };
+    const float root_box[6] = {pv.box[0], pv.box[3], pv.box[1], pv.box[4], pv.box[2], pv.box[5]};
+    if (pv.root < 0) {
+        tri_inside(~pv.root, root_box);
+    } else {
+        // stack of (node, parent slot box) pairs: the box is re-read from the parent node
+        constexpr int kCheckStack = 256;
+        int st_node[kCheckStack], st_par[kCheckStack];
+        int sp = 0, iters = 0;
+        st_node[sp] = pv.root;
+        st_par[sp] = -1;
+        sp++;
+        const int limit = pv.limit;
+        while (sp > 0) {
+            if (++iters > limit) { bound++; break; }
+            sp--;
+            const int nd = st_node[sp], par = st_par[sp];
+            float pbox[6];
+            if (par < 0) {
+                for (int k = 0; k < 6; k++) pbox[k] = root_box[k];
+            } else {
+                const float4 *pn = pv.node + (size_t)(par >> 2) * kNode4;
+                const int c = par & 3;
+                for (int k = 0; k < 6; k++) pbox[k] = reinterpret_cast<const float *>(pn + k)[c];
+            }
+            const float4 *n = pv.node + (size_t)nd * kNode4;
+            const int4 refs4 = *reinterpret_cast<const int4 *>(n + 6);
+            const int rf[4] = {refs4.x, refs4.y, refs4.z, refs4.w};
+            nodes++;
+            for (int c = 0; c < 4; c++) {
+                if (rf[c] == kEmptyChild) continue;
+                float bx[6];
+                for (int k = 0; k < 6; k++) bx[k] = reinterpret_cast<const float *>(n + k)[c];
+                if (!inside(bx, pbox)) outside_box++;
+                if (rf[c] >= 0) {
+                    if (sp >= kCheckStack) { bound++; continue; }
+                    st_node[sp] = rf[c];
+                    st_par[sp] = nd * 4 + c;
+                    sp++;
+                } else {
+                    tri_inside(~rf[c], bx);
+                }
+            }
+        }
+    }
+    atomicAdd(report + 0, refs);
+    atomicAdd(report + 2, outside_box);
+    atomicAdd(report + 3, outside_tri);
+    atomicAdd(report + 4, nodes);
+    atomicAdd(report + 5, bound);
+}
+
+cudaError_t launch_bvh_check(const unsigned char *tctx, int n_parts, int *tri_seen, unsigned long long *report,
+                             cudaStream_t st)
+{
+    k_bvh_check<<<n_parts, 32, 0, st>>>(tctx, tri_seen, report);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ launchers

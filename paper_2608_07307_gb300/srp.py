@@ -23,6 +23,7 @@ PANELS_TRACK, PANELS_SET, PANELS_TRACK_OFFSET = 0, 1, 2
 EVAL_COUNT = 1
 EVAL_TIMING = 2
 EVAL_TRAVERSE = 8  # primary hits by BVH traversal instead of rasterisation (same results)
+EVAL_TEST_WALK_BOUND = 16  # tests of the walk bound's error path: every BVH walk stops after one step
 EVAL_AUTOTUNE = 4
 MAX_BOUNCES = 4
 MAX_N = 8192  # SRP_MAX_N: rays per window side
@@ -31,7 +32,8 @@ MAX_N = 8192  # SRP_MAX_N: rays per window side
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",
            "srp_eval_batch", "srp_eval_stats_get", "srp_propagate", "srp_eval_noalloc", "srp_set_materials",
            "srp_grad", "srp_prop_grad", "srp_propagate_batch", "srp_autotune", "srp_set_tile_shape",
-           "srp_spad_build", "srp_spad_eval"]
+           "srp_spad_build", "srp_spad_eval", "srp_set_memory_limit", "srp_memory_usage", "srp_sort_pairs",
+           "srp_mesh_check"]
 
 
 class Traj(C.Structure):
@@ -146,6 +148,10 @@ def load(build_if_needed: bool = True):
         lib.srp_spad_build.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.POINTER(SpadGrid), C.c_void_p]
         lib.srp_spad_eval.argtypes = [C.c_void_p, C.POINTER(SpadGrid), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]
+        lib.srp_set_memory_limit.argtypes = [C.c_void_p, C.c_uint64]
+        lib.srp_memory_usage.argtypes = [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+        lib.srp_sort_pairs.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]
+        lib.srp_mesh_check.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int64)]
         lib.srp_eval_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                          C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double), C.c_int32,
                                          C.c_int32, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -286,7 +292,7 @@ class Context:
     def eval_batch(self, mesh_id: int, sun_dirs, sun_dist=None, N: int = 256, bounces: int = 1, P0: float = 4.56e-6,
                    eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, hits: bool = False, count: bool = False,
                    timing: bool = False, out=None, traverse: bool = False, n_diffuse: int = 0,
-                   diffuse_seed: int = 0):
+                   diffuse_seed: int = 0, flags: int = 0):
         """Force [n,3] (N) and torque [n,3] (N m); with hits=True also the per-ray
         hit triangle ids [n, N*N, bounces+1].  Outputs live where the input lives
         (CUDA tensor in, CUDA tensors out; numpy in, numpy out) unless `out`
@@ -315,7 +321,7 @@ class Context:
             force, torque = np.empty((n, 3)), np.empty((n, 3))
             hit = np.empty((n, N * N, nseg), np.int32) if hits else None
         p = EvalParams(N, bounces, P0, eps_rel, panel_mode, (EVAL_COUNT if count else 0) | (EVAL_TIMING if timing else 0)
-                       | (EVAL_TRAVERSE if traverse else 0), n_diffuse, diffuse_seed)
+                       | (EVAL_TRAVERSE if traverse else 0) | flags, n_diffuse, diffuse_seed)
         ps, k1 = _ptr(sun_dirs)
         pd, k2 = _ptr(sun_dist)
         pf, k3 = _ptr(force)
@@ -414,6 +420,35 @@ class Context:
         pt, k4 = _ptr(torque)
         self._check(self.lib.srp_spad_eval(self.h, C.byref(g), pg, n, ps, pd, pf, pt))
         return force, torque
+
+    def set_memory_limit(self, nbytes: int):
+        """srp_set_memory_limit: cap on the library's device memory (0: none)."""
+        self._check(self.lib.srp_set_memory_limit(self.h, int(nbytes)))
+
+    def memory_usage(self):
+        """srp_memory_usage: (bytes held, cap)."""
+        u, l = C.c_uint64(), C.c_uint64()
+        self._check(self.lib.srp_memory_usage(self.h, C.byref(u), C.byref(l)))
+        return int(u.value), int(l.value)
+
+    def sort_pairs(self, keys, vals, key_bits: int = 64):
+        """srp_sort_pairs: the build's stable radix sort, on copies; returns
+        (keys, vals) sorted by key bits [0, key_bits)."""
+        k = np.ascontiguousarray(np.asarray(keys, np.uint64)).copy()
+        v = np.ascontiguousarray(np.asarray(vals, np.int32)).copy()
+        if len(k) != len(v):
+            raise ValueError("keys and vals differ in length")
+        self._check(self.lib.srp_sort_pairs(self.h, len(k), k.ctypes.data, v.ctypes.data, int(key_bits)))
+        return k, v
+
+    def mesh_check(self, mesh_id: int, sun_dir=None):
+        """srp_mesh_check: dict of the BVH structure counts after posing."""
+        rep = (C.c_int64 * 8)()
+        s = None if sun_dir is None else np.ascontiguousarray(np.asarray(sun_dir, np.float64).reshape(3))
+        self._check(self.lib.srp_mesh_check(self.h, mesh_id, s.ctypes.data if s is not None else None, rep))
+        names = ["leaf_refs", "tris_not_once", "boxes_outside_parent", "tris_outside_leaf", "nodes", "walk_bound",
+                 "n_tris", "n_parts"]
+        return dict(zip(names, [int(x) for x in rep]))
 
     def set_materials(self, mesh_id: int, mat):
         """srp_set_materials: new (rho_s, rho_d) per material, [n_mats, 2]."""
