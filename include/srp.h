@@ -376,6 +376,9 @@ typedef struct {
     double t;                      /* time reached (s)                                          */
     int32_t status;                /* SRP_OK or SRP_ERR_STEP                                    */
     int32_t reserved;
+    double h_next;                 /* RKF7(8): the step size proposed after the last accepted
+                                      step; passing it as h0 with t and y1 resumes the arc as the
+                                      integrator would have continued it (RK4: h0)              */
 } srp_prop_stats;
 
 /*

@@ -844,6 +844,7 @@ srp_status finish_propagate(srp_ctx *ctx, int n, const PropState *S, double *y1,
             stats[i].t = hs[i].t;
             stats[i].status = hs[i].status;
             stats[i].reserved = 0;
+            stats[i].h_next = hs[i].h;
         }
         if (hs[i].status) out = SRP_ERR_STEP;
         if (!hs[i].done) out = fail(ctx, SRP_ERR_STEP, "trajectory %d did not finish within the step budget", i);
@@ -1990,6 +1991,7 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
             stats[i].t = fin[i].t;
             stats[i].status = fin[i].status;
             stats[i].reserved = 0;
+            stats[i].h_next = fin[i].h;
         }
     ctx->last.launches = launches;
     ctx->last.trace_launches = trace_launches;

@@ -104,7 +104,7 @@ class PropParams(C.Structure):
 
 class PropStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("rejects", C.c_int64), ("evals", C.c_int64), ("t", C.c_double),
-                ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("status", C.c_int32), ("reserved", C.c_int32), ("h_next", C.c_double)]
 
 
 _lib = None
@@ -364,7 +364,7 @@ class Context:
         self._check(self.lib.srp_propagate(self.h, mesh_id, C.byref(p), n, y0.ctypes.data, t01.ctypes.data,
                                            y1.ctypes.data, st, hl.ctypes.data if hl is not None else None,
                                            h_cap))
-        stats = [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status) for s in st]
+        stats = [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status, h_next=s.h_next) for s in st]
         if hl is not None:
             for i, s in enumerate(stats):
                 hl[i, min(s["steps"], h_cap):] = np.nan
@@ -507,7 +507,7 @@ class Context:
                                            g1.ctypes.data, int(ckpt_every), out["y1"].ctypes.data,
                                            out["y0"].ctypes.data, out["mat"].ctypes.data, out["angle"].ctypes.data,
                                            out["q"].ctypes.data, st))
-        out["stats"] = [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status) for s in st]
+        out["stats"] = [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status, h_next=s.h_next) for s in st]
         return out
 
     def propagate_batch(self, trajs, method: int = RKF78, j2=False, sun3=False, srp_on=True,
@@ -536,7 +536,7 @@ class Context:
         y1 = np.empty((n, 6))
         st = (PropStats * n)()
         self._check(self.lib.srp_propagate_batch(self.h, C.byref(p), n, arr, y1.ctypes.data, st))
-        return y1, [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status) for s in st]
+        return y1, [dict(steps=s.steps, rejects=s.rejects, evals=s.evals, t=s.t, status=s.status, h_next=s.h_next) for s in st]
 
     def autotune(self, mesh_id: int, N: int, bounces: int, P0: float = 4.56e-6, eps_rel: float = 1e-9,
                  panel_mode: int = PANELS_TRACK):

@@ -155,3 +155,35 @@ def test_propagate_argument_errors(ctx):
     with pytest.raises(srp.SrpError) as e:
         ctx.propagate(mid, GEO, [0.0, 1e6], max_steps=3, srp_on=False)
     assert e.value.code == -7
+
+
+def test_resume_a_fixed_step_arc_exactly(ctx):
+    """Checkpoint / resume: an RK4 arc split at a step boundary, the second half
+    started from the first half's state, equals the whole arc bit for bit."""
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    kw = dict(method=1, h0=60.0, j2=True, sun3=True, N=32, bounces=1)
+    y_all, s_all, _ = ctx.propagate(mid, GEO, [0.0, 7200.0], **kw)
+    y_a, s_a, _ = ctx.propagate(mid, GEO, [0.0, 3600.0], **kw)
+    y_b, s_b, _ = ctx.propagate(mid, y_a[0], [3600.0, 7200.0], **kw)
+    assert s_a[0]["steps"] + s_b[0]["steps"] == s_all[0]["steps"] == 120
+    assert np.array_equal(y_b, y_all)
+
+
+def test_resume_an_adaptive_arc_with_the_proposed_step(ctx):
+    """RKF7(8): split at the end of an accepted step of the whole arc and resume
+    with h0 = the first half's h_next: the same steps, the same end state
+    (up to the rounding of the shortened last step of the first half)."""
+    m = I.box_wing()
+    mid = ctx.load_mesh(m)
+    kw = dict(j2=True, sun3=True, N=32, bounces=1)
+    y_all, s_all, hl = ctx.propagate(mid, GEO, [0.0, 43200.0], h_cap=256, **kw)
+    t_m = 0.0
+    for h in hl[0, :12]:
+        t_m += h
+    y_a, s_a, _ = ctx.propagate(mid, GEO, [0.0, t_m], **kw)
+    assert s_a[0]["steps"] == 12 and s_a[0]["t"] == t_m
+    assert abs(s_a[0]["h_next"] / hl[0, 12] - 1.0) < 1e-6 or s_a[0]["h_next"] >= hl[0, 12]
+    y_b, s_b, _ = ctx.propagate(mid, y_a[0], [t_m, 43200.0], h0=s_a[0]["h_next"], **kw)
+    assert s_a[0]["steps"] + s_b[0]["steps"] == s_all[0]["steps"]
+    assert np.linalg.norm(y_b[0, :3] - y_all[0, :3]) < 1e-4
