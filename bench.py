@@ -173,6 +173,30 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ parity
+def parity_record(ctx, mid, a):
+    """Force and torque of the benchmark workload against the oracle's whole
+    evaluations stored in tests/golden/fullsize_forces.txt (written by
+    tests/golden/make_fullsize.py from the oracle alone) for the directions it
+    holds at this facet size, grid and bounce count; None when it holds none."""
+    import numpy as np
+    from paper_2608_07307_gb300 import inputs as I
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "fullsize_forces.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    rows = [r for r in rows if float(r[0]) == a.facet and int(r[1]) == a.N and int(r[2]) == a.bounces]
+    if not rows:
+        return None
+    ks = [int(r[3]) for r in rows]
+    F, T = ctx.eval_batch(mid, I.sun_dirs_fibonacci(4096)[ks], N=a.N, bounces=a.bounces)
+    Fo = np.array([[float(x) for x in r[4:7]] for r in rows])
+    To = np.array([[float(x) for x in r[7:10]] for r in rows])
+    fn = np.linalg.norm(Fo, axis=1)
+    rel_f = np.linalg.norm(F - Fo, axis=1) / fn
+    rel_t = np.linalg.norm(T - To, axis=1) / np.maximum(np.linalg.norm(To, axis=1), fn * 1.0)
+    return {"force_rel_err_max": float(rel_f.max()), "torque_rel_err_max": float(rel_t.max()), "bar": 1e-4,
+            "directions": ks, "source": "oracle whole evaluations, tests/golden/fullsize_forces.txt"}
+
+
 # ------------------------------------------------------------- propagation
 def bench_propagation(ctx, mid, mesh, arc_s=30 * 86400.0, N=512, bounces=1):
     """30-day GEO arc with the 200k-triangle spacecraft: two-body + J2 + Sun + SRP
@@ -621,6 +645,7 @@ def run_native(a):
                 "d2h_bytes_per_step": B * 6 * 8},
         "clocks": clocks,
     }
+    line["parity"] = parity_record(ctx, mid, a)
     if not a.no_prop:
         line["propagation"], direct = bench_propagation(ctx, mid, mesh)
         if not a.no_spad:
