@@ -60,7 +60,7 @@ typedef int32_t srp_status;
 #define SRP_F32 0
 #define SRP_F64 1
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define SRP_MAX_PARTS 16
 #define SRP_MAX_MATS 256
 #define SRP_MAX_BOUNCES 4
