@@ -515,6 +515,24 @@ def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7):
 
 
 # ------------------------------------------------------------------ native
+def shard(table, rank, world):
+    """Rank `rank`'s share of the direction table: every world-th row from
+    row `rank` (replicas: the ranks exchange nothing on the data path)."""
+    import numpy as np
+    return np.ascontiguousarray(table[rank::world])
+
+
+def job_totals(local_ms, local_e2e_s, evals_per_rank, world, reduce_max=None):
+    """Whole-job timing of the replicas: the slowest rank's device time and
+    end-to-end time (max over ranks through `reduce_max`, which takes and
+    returns a list), and the value = every rank's evaluations / that time."""
+    total_ms, e2e_s = local_ms, local_e2e_s
+    if world > 1:
+        total_ms, e2e_s = reduce_max([local_ms, local_e2e_s])
+    evals = evals_per_rank * world
+    return total_ms, e2e_s, evals, evals / (total_ms / 1000.0)
+
+
 def run_native(a):
     import numpy as np
     import torch
@@ -530,7 +548,7 @@ def run_native(a):
 
     mesh = I.spacecraft(a.facet)
     table = I.sun_dirs_fibonacci(4096)
-    mine = np.ascontiguousarray(table[rank::world])
+    mine = shard(table, rank, world)
     stream = torch.cuda.Stream(device=dev)
     ctx = srp.Context(local, stream=stream)
     mid = ctx.load_mesh(mesh)
@@ -591,13 +609,13 @@ def run_native(a):
             t0 = time.perf_counter()
             ctx.eval_batch(mid, hd, N=a.N, bounces=a.bounces, out=(hF, hT))
             e2e_s += time.perf_counter() - t0
-    if world > 1:
+    def reduce_max(xs):
         import torch.distributed as dist
-        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+        t = torch.tensor(xs, dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_s = float(t[0]), float(t[1])
-    evals = B * a.steps * world
-    value = evals / (total_ms / 1000.0)
+        return [float(x) for x in t]
+
+    total_ms, e2e_s, evals, value = job_totals(total_ms, e2e_s, B * a.steps, world, reduce_max)
     if rank != 0:
         ctx.close()
         if world > 1:
