@@ -956,8 +956,9 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) a.partials[tile * 6 + k] = x;
     }
-    for (int k = 0; k < kCnt; k++) {
-        const unsigned x = (COUNT || k < 7) ? __reduce_add_sync(0xffffffffu, cnt[6 + k]) : 0u;
+    // counts 0..6 always; the traversal counters only in the counting variant
+    for (int k = 0; k < (COUNT ? kCnt : 7); k++) {
+        const unsigned x = __reduce_add_sync(0xffffffffu, cnt[6 + k]);
         if (lane == 0) a.pcounts[tile * kCnt + k] = x;
     }
     int fl = __reduce_or_sync(0xffffffffu, flags);
@@ -1465,11 +1466,12 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
     double f[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long c[kCnt];
     for (int k = 0; k < kCnt; k++) c[k] = 0ull;
+    const int kc = a.count ? kCnt : 7;  // the trace writes the traversal counters only when counting
     int mine = 0;
     for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
         for (int k = 0; k < 6; k++) f[k] += (double)a.partials[(base + t) * 6 + k];
         // count 0: the tile's hand-off flags; the re-trace below counts the rays it does
-        for (int k = 1; k < kCnt; k++) c[k] += a.pcounts[(base + t) * kCnt + k];
+        for (int k = 1; k < kc; k++) c[k] += a.pcounts[(base + t) * kCnt + k];
         mine |= a.amb_count[base + t];
     }
     __shared__ TraceCtx B;
