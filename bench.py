@@ -42,7 +42,7 @@ FLOP_BOX, FLOP_TRI = 19, 50
 NODE_BYTES, TRI_BYTES = 128, 48  # one 4-wide BVH node, one FP32 triangle record
 # DRAM bytes (read + write) of one k_trace launch of this workload (8 evaluations),
 # from one ncu capture of the current kernel (None until captured)
-TRACE_DRAM_BYTES_PER_LAUNCH = 182.706e6 + 49.735e6  # mean of three launches, ncu dram__bytes_read/write.sum
+TRACE_DRAM_BYTES_PER_LAUNCH = 193.570e6 + 50.163e6  # mean of three launches, ncu dram__bytes_read/write.sum
 # the same capture's unit throughputs, % of the GB300's peak for each unit
 TRACE_NCU_PCT_OF_PEAK = {"l1tex": 62.2, "l2": 27.9, "dram": 3.5, "sm_issue_active": 62.4,
                          "l2_bytes_per_launch": 4.476e9, "l1_bytes_per_launch": 6.018e9}
