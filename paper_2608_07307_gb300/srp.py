@@ -27,6 +27,7 @@ EVAL_TEST_WALK_BOUND = 16  # tests of the walk bound's error path: every BVH wal
 EVAL_AUTOTUNE = 4
 MAX_BOUNCES = 4
 MAX_N = 8192  # SRP_MAX_N: rays per window side
+MAX_DIFFUSE = 256  # diffuse secondary rays per hit (srp_eval_params.n_diffuse)
 
 # Symbols declared in include/srp.h (checked by the tests against the library).
 EXPORTS = ["srp_create", "srp_destroy", "srp_last_error", "srp_mesh_load", "srp_mesh_free", "srp_set_panel_angles",

@@ -72,3 +72,19 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def test_binding_constants_match_the_header():
+    """Every #define of include/srp.h that the binding mirrors (under its own
+    name or without the SRP_ prefix) has the header's value."""
+    from paper_2608_07307_gb300 import srp
+    text = open(os.path.join(ROOT, "include", "srp.h")).read()
+    defs = dict(re.findall(r"^#define\s+(SRP_\w+)\s+\(?(-?\d+)\)?", text, flags=re.M))
+    checked = 0
+    for name, val in defs.items():
+        for py in (name, name[len("SRP_"):]):
+            if hasattr(srp, py) and isinstance(getattr(srp, py), int):
+                assert getattr(srp, py) == int(val), (name, py, getattr(srp, py), val)
+                checked += 1
+                break
+    assert checked >= 15, checked
