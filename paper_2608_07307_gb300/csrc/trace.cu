@@ -57,6 +57,16 @@
 // partials (and the re-traced rays of those tiles) per first-level block, then
 // those per evaluation, scaled by P0 / dist^2 times the pixel area.  No atomics on data:
 // results are bit-reproducible for a given launch shape.
+//
+// k_diffuse (optional, Sec. 6.1's diffuse rays).  After the re-trace, a thread per
+// (primary ray, sample) replays the ray's specular chain in FP64 through the recorded
+// hit triangles and, at each hit with a next level, traces its sample of the K
+// cosine-weighted diffuse rays (SplitMix64 stream) in FP32 with the same error bounds,
+// settling the uncertain triangles in FP64 (settle64); its per-block FP64 sums are added
+// by k_reduce in a fixed order.
+//
+// k_bvh_check (diagnostics).  One thread per part walks slot 0's 4-wide tree and counts
+// leaf references, child boxes outside their parent's and triangles outside their leaf.
 #include <math.h>
 #include <stddef.h>
 
