@@ -9,6 +9,11 @@
 // trajectory, k_prop_accel forms the stage derivative; k_prop_control then
 // accepts or rejects the step and picks the next step size.  All state lives
 // on the device; the host only relaunches the graph and polls a done counter.
+// k_prop_stage runs a warp per trajectory: at the first stage of a step, lanes
+// compute the Sun positions of all stages (their times are fixed with the step
+// size), lanes 0-5 form the stage state.  Without ray tracing between the
+// stages (a SPAD table, read by spad_lookup in the acceleration, or SRP off)
+// the whole step is one kernel, k_prop_step, built from the same parts.
 //
 // Integrators: Fehlberg's 7(8) pair (13 stages, NASA TR R-287, 1968),
 // propagating the 7th-order solution, error norm
