@@ -205,10 +205,27 @@ def evaluate(mesh, s, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angle
     return out
 
 
+def _rays_worker(args):
+    mesh, s, rays, N, kw = args
+    return eval_rays(mesh, s, rays, N, **kw)
+
+
 def eval_rays(mesh, s, rays, N, bounces=1, P0=4.56e-6, dist_au=1.0, eps_rel=1e-9, angles=None, n_diffuse=0,
-              diffuse_seed=0):
+              diffuse_seed=0, procs=1):
     """Per-ray unscaled contributions [n, 6], hits [n, nseg] and edge proximity
-    [n, nseg] for an explicit list of primary ray indices (sampled checks)."""
+    [n, nseg] for an explicit list of primary ray indices (sampled checks).
+    With procs > 1 the list is split into contiguous pieces traced by
+    spawn-started worker processes and the results are concatenated in order."""
+    if procs > 1 and len(rays) > 1:
+        import multiprocessing as mp
+        kw = dict(bounces=bounces, P0=P0, dist_au=dist_au, eps_rel=eps_rel, angles=angles, n_diffuse=n_diffuse,
+                  diffuse_seed=diffuse_seed)
+        rays = np.asarray(rays, np.int64)
+        n = min(len(rays), procs * 4)
+        bounds = [len(rays) * k // n for k in range(n + 1)]
+        with mp.get_context("spawn").Pool(procs) as pool:
+            parts = pool.map(_rays_worker, [(mesh, s, rays[bounds[k]:bounds[k + 1]], N, kw) for k in range(n)])
+        return {key: np.concatenate([q[key] for q in parts]) for key in ("contrib", "hits", "edge")}
     om = OMesh(mesh)
     p, keep = _params(N, bounces, P0, dist_au, eps_rel, angles, om.n_parts, None, n_diffuse, diffuse_seed)
     rays = np.ascontiguousarray(np.asarray(rays, np.int64))
@@ -346,17 +363,27 @@ class Prop(C.Structure):
         ("h0", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double), ("max_steps", C.c_int64),
         ("spad_table", C.POINTER(C.c_double)), ("spad_n_az", C.c_int32), ("spad_n_el", C.c_int32),
         ("spad_az0", C.c_double), ("spad_el0", C.c_double), ("spad_d_el", C.c_double),
+        ("track", C.c_int32), ("angles", C.POINTER(C.c_double)),
     ]
 
 
 def prop_params(central=0, j2=False, sun3=False, srp=False, attitude=0, q=(1.0, 0.0, 0.0, 0.0),
                 epoch_mjd_tt=61041.0, mass=1000.0, N=64, bounces=1, P0=4.56e-6, eps_rel=1e-9, method=0,
                 rtol=1e-12, atol_pos=1e-6, atol_vel=1e-9, h0=60.0, h_min=1e-6, h_max=0.0, max_steps=10_000_000,
-                spad=None):
+                spad=None, angles=None, offsets=None):
     """spad = (grid, table): the SRP force comes from the SPAD interpolant
-    (spad_interp) of `table` instead of the ray tracer."""
+    (spad_interp) of `table` instead of the ray tracer.  Joints track the Sun
+    unless commanded `angles` or tracking `offsets` (one per part) are given."""
     pp = Prop(central, int(j2), int(sun3), int(srp), attitude, (C.c_double * 4)(*q), epoch_mjd_tt, mass, N,
               bounces, P0, eps_rel, method, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps)
+    pp.track = 1
+    if angles is not None or offsets is not None:
+        if angles is not None and offsets is not None:
+            raise ValueError("give commanded angles or tracking offsets, not both")
+        a = np.ascontiguousarray(np.asarray(angles if offsets is None else offsets, np.float64).ravel())
+        pp._angles_keep = a
+        pp.angles = _dp(a)
+        pp.track = 0 if offsets is None else 2
     if spad is not None:
         g, tab = spad
         tab = np.ascontiguousarray(np.asarray(tab, np.float64).reshape(g["n_el"], g["n_az"], 6))

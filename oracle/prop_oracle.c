@@ -53,6 +53,9 @@ typedef struct {
     const double *spad_table; /* NULL: trace rays; else the SPAD table (spad_oracle.c) */
     int32_t spad_n_az, spad_n_el;
     double spad_az0, spad_el0, spad_d_el;
+    int32_t track;            /* joint mode of every evaluation (Sec. 4.4.2): 1 Sun tracking,
+                                 2 tracking + angles[] offsets, 0 commanded angles[] */
+    const double *angles;     /* [n_parts] offsets (2) or commanded angles (0)  */
 } orc_prop;
 
 /* Fehlberg 7(8) coefficients (NASA TR R-287, Table X). */
@@ -207,7 +210,7 @@ int orc_accel(const orc_mesh *mesh, const orc_prop *pp, double t, const double y
         if (rc) return rc;
         for (int k = 0; k < 3; k++) Fb[k] = out[k];
     } else {
-        orc_params ep = {pp->N, pp->bounces, pp->P0, dist, pp->eps_rel, 1, NULL};
+        orc_params ep = {pp->N, pp->bounces, pp->P0, dist, pp->eps_rel, pp->track, pp->angles};
         double acc[6] = {0, 0, 0, 0, 0, 0}, scale = 0.0;
         int rc = orc_eval_range(mesh, &ep, sb, 0, (int64_t)pp->N * pp->N, acc, &scale, NULL, NULL, NULL, NULL, NULL);
         if (rc) return rc;
