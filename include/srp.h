@@ -145,6 +145,12 @@ typedef struct {
  * SRP_ERR_STACK (a bounded loop that sets a device flag; nothing faults or
  * waits).  For tests only. */
 #define SRP_EVAL_TEST_WALK_BOUND 16
+/* Run every chunk of evaluations on one pipeline lane, in order, instead of
+ * overlapping chunks on several lanes.  With SRP_EVAL_TIMING each phase's
+ * time is then the GPU time of its own kernels (no other chunk runs beside
+ * them), e.g. the trace kernel's duration per launch for a roofline.  Results
+ * are the same bits either way. */
+#define SRP_EVAL_SERIAL 32
 
 /* Counters of the last srp_eval_batch call (summed over its evaluations). */
 typedef struct {
@@ -216,19 +222,26 @@ srp_status srp_set_panel_angles(srp_ctx *ctx, int32_t mesh_id, int32_t n, const 
  * traced for `bounces` more levels (weight times rho_s; a secondary ray never
  * hits the triangle it leaves); sum of all pixels times P0 / dist^2 times the
  * pixel area.
- *   sun_dir_body [n][3]   unit vectors towards the Sun, body frame
+ *   sun_dir_body [n][3]   unit vectors towards the Sun, body frame; with quat,
+ *                         the Sun direction in the inertial frame instead
+ *   quat         [n][4]   NULL, or the attitude per evaluation: scalar-first
+ *                         quaternion body -> inertial (normalised here).  The
+ *                         body-frame direction is then R(q)^T sun_dir and
+ *                         `force` receives the SRP acceleration of the state,
+ *                         R(q) F_body / mass (m/s^2, inertial frame; Sec. 3
+ *                         Eq. 1), mass from the mesh description (must be > 0)
  *   sun_dist_au  [n]      Sun distance (AU); NULL means 1; a negative entry skips
  *                         that evaluation (force and torque 0, hit ids untouched)
- *   force        [n][3]   out, N
- *   torque       [n][3]   out, N m about c_ref
+ *   force        [n][3]   out, N (body frame), or m/s^2 (inertial) with quat
+ *   torque       [n][3]   out, N m about c_ref, body frame
  *   hit_tri      [n][N*N][bounces+1] out, original triangle id per ray segment,
  *                         -1 when that segment missed or was not traced; NULL
  *                         to skip (debug output, large)
  * Errors: SRP_ERR_ARG, SRP_ERR_STATE (bad mesh id), SRP_ERR_STACK, SRP_ERR_CUDA.
  */
 srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *params, int32_t n,
-                          const double *sun_dir_body, const double *sun_dist_au, double *force, double *torque,
-                          int32_t *hit_tri);
+                          const double *sun_dir_body, const double *quat, const double *sun_dist_au, double *force,
+                          double *torque, int32_t *hit_tri);
 
 /* Counters of the last srp_eval_batch on ctx. */
 srp_status srp_eval_stats_get(srp_ctx *ctx, srp_eval_stats *out);
@@ -266,24 +279,32 @@ srp_status srp_set_materials(srp_ctx *ctx, int32_t mesh_id, int32_t n_mats, cons
  *                    to the tracking angle (SRP_PANELS_TRACK_OFFSET; for
  *                    SRP_PANELS_TRACK the offset at 0).  Zero for rigid parts
  *                    and for joints held at a limit of their interval.
+ *   g_quat   [n][4]  out: each quat entry as given (before the normalisation;
+ *                    so g_quat[k] . quat[k] = 0); needs quat.
+ * With quat (as in srp_eval_batch: sun_dir in the inertial frame, the force
+ * output the acceleration R(q) F_body / mass) the cotangent g_force is that of
+ * the acceleration and g_sun that of the inertial direction; the attitude
+ * enters twice, through the body-frame Sun direction and through the rotation
+ * of the force, and g_quat holds both.
  * Sun tracking is differentiated: a tracking joint's angle moves with the Sun
  * direction, and with the angles of the joints above it.
  *   g_force, g_torque [n][3]  in: cotangents (host or device).
  *   force, torque     [n][3]  out (may be NULL): the evaluation itself, equal
  *                    to srp_eval_batch's.
- * Any of g_sun, g_dist, g_mat, g_angle may be NULL.  An entry skipped with a
+ * Any of g_sun, g_dist, g_mat, g_angle, g_quat may be NULL.  An entry skipped with a
  * negative distance contributes nothing and gets zero gradients.  The result
  * is deterministic (every sum has a fixed order).
- * Errors: as srp_eval_batch; SRP_ERR_ARG when g_force or g_torque is NULL.
+ * Errors: as srp_eval_batch; SRP_ERR_ARG when g_force or g_torque is NULL, or
+ * g_quat is given without quat.
  */
 srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *params, int32_t n,
-                    const double *sun_dir_body, const double *sun_dist_au, const double *g_force,
+                    const double *sun_dir_body, const double *quat, const double *sun_dist_au, const double *g_force,
                     const double *g_torque, double *force, double *torque, double *g_sun, double *g_dist,
-                    double *g_mat, double *g_angle);
+                    double *g_mat, double *g_angle, double *g_quat);
 
 /* ---------------------------------------------------- SPAD interpolation */
 /*
- * A SPAD table (Sec. 6, Sec. 8.1): the force and torque of srp_eval_batch at
+ * A SPAD table (Sec. 4.2, Sec. 6.1): the force and torque of srp_eval_batch at
  * 1 AU, precomputed for a grid of body-frame Sun directions and interpolated
  * bilinearly in (azimuth, elevation) wherever an SRP force is needed instead
  * of tracing rays.  Sample (i, j), 0 <= i < n_az, 0 <= j < n_el, is the
@@ -393,7 +414,7 @@ typedef struct {
  * trajectories, accelerations, step control) is captured once in a CUDA graph
  * and relaunched until every trajectory reached its end time.  With
  * params->spad_table the SRP force of every stage is the SPAD interpolant of
- * that table (Sec. 6) instead of a ray-traced evaluation: the step is then
+ * that table (Sec. 4.2) instead of a ray-traced evaluation: the step is then
  * the stage, acceleration and control kernels alone.
  *   y0     [n_traj][6]  initial position (m) and velocity (m/s), inertial
  *   t0_t1  [n_traj][2]  start and end time (s after the epoch)
@@ -516,10 +537,10 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
  *
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory while they run, e.g. flight or real-time code
- * whose memory budget is fixed at start-up, work issued inside a CUDA stream
- * capture (an allocation there would break the capture), or hosts whose memory
- * only comes from their own pool.  It needs no srp_ctx (creating one allocates)
- * and calls no cudaMalloc, cudaFree or allocating library routine.
+ * whose memory budget is fixed at start-up (an allocation could fail or stall
+ * in mid-mission), or hosts whose memory only comes from their own pool.  It
+ * needs no srp_ctx (creating one allocates) and calls no cudaMalloc, cudaFree
+ * or allocating library routine.
  *
  * It computes the same force and torque as srp_eval_batch for one Sun
  * direction, for a mesh already posed by the caller (no joints), by testing
@@ -528,7 +549,10 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
  * doubles (about 256 KiB) in the library's device globals, which every GPU that
  * loads the library holds until the process exits.
  *   tri_xyz  [n_tris][3][3] device, posed vertices (m), counter-clockwise front
- *   tri_mat  [n_tris][2]    device, material of the front, back side
+ *   tri_mat  [n_tris][2]    device, material of the front, back side; every
+ *                           index must lie in [0, n_mats): the kernel reads no
+ *                           material for an index outside it, and a ray that
+ *                           hits such a side makes force and torque NaN
  *   mat      [n_mats][2]    device, rho_s, rho_d
  *   sun_dir  [3] host, towards the Sun, body frame (normalised here)
  *   c_ref    [3] host, torque reference point
@@ -536,8 +560,10 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
  *   cuda_stream    stream to launch on (NULL = legacy default stream)
  * Work runs on the current CUDA device and is asynchronous: synchronise the
  * stream before reading the outputs.  The first call on a device looks up the
- * scratch array's device address (once per device); make that first call
- * before any stream capture.  All calls share the scratch array, which keeps
+ * scratch array's device address (kept once it succeeds; a failed lookup is
+ * tried again on the next call); make that first call before any stream
+ * capture.  A launch error left pending by earlier, unrelated work on the
+ * calling thread is cleared, not reported.  All calls share the scratch array, which keeps
  * the last call's contents (each call rewrites all it reads), so calls whose
  * work overlaps on the GPU (other streams, other host threads) race.
  * Errors: SRP_ERR_ARG (null pointer, n_tris outside [1, SRP_NOALLOC_MAX_TRIS],

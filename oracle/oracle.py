@@ -545,7 +545,7 @@ def arc_frozen_grad(mesh, pp, t0, t1, y0, lam, offsets=None, angles=None, h=1e-6
     return dict(y0=g_y0, mat=g_mat, angle=g_ang, q=g_q, y1=y1, record=rec)
 
 
-# ------------------------------------------------ SPAD interpolation (Sec. 6)
+# ---------------------------------------------- SPAD interpolation (Sec. 4.2)
 def spad_dirs(grid):
     """Body-frame Sun directions of the SPAD samples, [n_el][n_az][3]."""
     n_az, n_el = grid["n_az"], grid["n_el"]

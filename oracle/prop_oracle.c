@@ -203,7 +203,7 @@ int orc_accel(const orc_mesh *mesh, const orc_prop *pp, double t, const double y
     for (int k = 0; k < 3; k++) sb[k] = R[k] * sv[0] + R[3 + k] * sv[1] + R[6 + k] * sv[2];
     double Fb[3];
     if (pp->spad_table) {
-        /* interpolated force (Sec. 6): the table replaces the ray tracer */
+        /* interpolated force (Sec. 4.2): the table replaces the ray tracer */
         double out[6];
         int rc = orc_spad_interp(pp->spad_n_az, pp->spad_n_el, pp->spad_az0, pp->spad_el0, pp->spad_d_el,
                                  pp->spad_table, sb, dist, out);

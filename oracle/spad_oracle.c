@@ -2,7 +2,7 @@
  * spad_oracle.c -- double-precision reference of the SPAD interpolation model
  * (TEST INFRASTRUCTURE ONLY; see srp_oracle.c).
  *
- * Sec. 6 (interpolation-based SRP) and Sec. 8.1: instead of tracing rays in
+ * Sec. 4.2 (interpolation-based SRP) and Sec. 6.1 (the two tables): instead of tracing rays in
  * every integrator stage, the SRP force is read from a table precomputed by
  * the ray tracer over a grid of Sun directions in the body frame (azimuth x
  * elevation), interpolated bilinearly.  The paper fixes the grid only by its

@@ -4,10 +4,9 @@ Forward runs srp_eval_batch; backward runs srp_grad, the hand-written adjoint
 with the hit set frozen (each ray keeps the triangles it hit, the window keeps
 its extreme vertices), which returns the gradients with respect to the Sun
 direction, the Sun distance, the optical coefficients (rho_s, rho_d) of every
-material and the joint angle parameters.  All arithmetic runs in libsrp's
-kernels; this module only moves tensors across the C ABI, except the attitude
-composition of ``srp_accel_inertial`` (a 3 x 3 rotation built from the
-quaternion with torch operations, differentiated by torch).
+material, the joint angle parameters and, for the inertial-frame
+acceleration, the attitude quaternion.  All arithmetic runs in libsrp's
+kernels; this module only moves tensors across the C ABI.
 """
 from __future__ import annotations
 
@@ -58,23 +57,42 @@ def srp_force(handle, mesh_id, sun_dirs, sun_dist, mat, angles, N=256, bounces=1
     return SRPForceFunction.apply(sun_dirs, sun_dist, mat, angles, handle, mesh_id, opts)
 
 
-def quat_to_matrix(q):
-    """Rotation matrices [n,3,3] (body -> inertial) of scalar-first quaternions
-    [n,4], normalised first (the gradient is that of the normalised map)."""
-    q = q / q.norm(dim=-1, keepdim=True)
-    w, x, y, z = q.unbind(-1)
-    return torch.stack([
-        torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
-        torch.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
-        torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
+class SRPAccelFunction(torch.autograd.Function):
+    """(q [n,4], sun_inertial [n,3], sun_dist [n], mat [M,2], angles [P]) ->
+    (acceleration [n,3] m/s^2 inertial frame, torque [n,3] N m body frame)."""
+
+    @staticmethod
+    def forward(ctx, q, sun_inertial, sun_dist, mat, angles, handle, mesh_id, opts):
+        handle.set_materials(mesh_id, mat)
+        handle.set_panel_angles(mesh_id, angles)
+        a, T = handle.eval_batch(mesh_id, sun_inertial.detach().contiguous(), sun_dist.detach().contiguous(),
+                                 quat=q.detach().contiguous(), **opts)
+        ctx.save_for_backward(q, sun_inertial, sun_dist, mat, angles)
+        ctx.handle, ctx.mesh_id, ctx.opts = handle, mesh_id, opts
+        return _t(a, sun_inertial), _t(T, sun_inertial)
+
+    @staticmethod
+    def backward(ctx, ga, gT):
+        q, s_in, dist, mat, angles = ctx.saved_tensors
+        h = ctx.handle
+        h.set_materials(ctx.mesh_id, mat)
+        h.set_panel_angles(ctx.mesh_id, angles)
+        ga = torch.zeros_like(s_in) if ga is None else ga
+        gT = torch.zeros_like(s_in) if gT is None else gT
+        g = h.grad(ctx.mesh_id, s_in.detach().contiguous(), ga.detach().to(s_in.dtype).contiguous(),
+                   gT.detach().to(s_in.dtype).contiguous(), dist.detach().contiguous(), quat=q.detach().contiguous(),
+                   **ctx.opts)
+        return (_t(g["quat"], s_in).to(q.dtype), _t(g["sun"], s_in), _t(g["dist"], s_in),
+                _t(g["mat"], s_in).to(mat.device, mat.dtype), _t(g["angle"], s_in).to(angles.device, angles.dtype),
+                None, None, None)
 
 
-def srp_accel_inertial(handle, mesh_id, q, sun_inertial, sun_dist, mat, angles, mass, **opts):
-    """SRP acceleration in the inertial frame for attitudes q [n,4] (body ->
-    inertial): the Sun direction is rotated into the body frame, the force is
-    evaluated there and rotated back, divided by the mass.  Differentiable in
-    q, the Sun direction and distance, the coefficients and the angles."""
-    R = quat_to_matrix(q)
-    s_body = torch.einsum("nji,nj->ni", R, sun_inertial)
-    F, T = srp_force(handle, mesh_id, s_body, sun_dist, mat, angles, **opts)
-    return torch.einsum("nij,nj->ni", R, F) / mass, T
+def srp_accel_inertial(handle, mesh_id, q, sun_inertial, sun_dist, mat, angles, N=256, bounces=1, P0=4.56e-6,
+                       eps_rel=1e-9, panel_mode=_srp.PANELS_TRACK_OFFSET):
+    """SRP acceleration in the inertial frame, R(q) F_body / mass (mass of the
+    loaded mesh), and the body-frame torque, for attitudes q [n,4] (body ->
+    inertial, scalar first) and inertial Sun directions [n,3].
+    Differentiable in q, the Sun direction and distance, the coefficients and
+    the angles; the rotation and its derivative run in the library."""
+    opts = dict(N=N, bounces=bounces, P0=P0, eps_rel=eps_rel, panel_mode=panel_mode)
+    return SRPAccelFunction.apply(q, sun_inertial, sun_dist, mat, angles, handle, mesh_id, opts)

@@ -501,8 +501,13 @@ __global__ void k_adj_sum(const double *g_eval, int n, int width, double *g_mat,
 
 int adj_blocks(int S, size_t rays)
 {
+    // about four blocks per SM over the S evaluations of a chunk
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        sms = 1;
     size_t need = (rays + kAdjThreads - 1) / kAdjThreads;
-    size_t cap = (size_t)std::max(1, 4 * 152 / std::max(S, 1));
+    size_t cap = (size_t)std::max(1, 4 * sms / std::max(S, 1));
     return (int)std::max<size_t>(1, std::min(need, cap));
 }
 

@@ -572,7 +572,7 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     // slots and buffers, so the short, latency-bound tail of one chunk (FP64
     // re-trace, reduction) overlaps the traversal of the next
     pl.nchunks = (n + pl.S - 1) / pl.S;
-    pl.lanes = std::max(1, std::min(pl.nchunks, kLanes));
+    pl.lanes = (prm->flags & SRP_EVAL_SERIAL) ? 1 : std::max(1, std::min(pl.nchunks, kLanes));
     srp_status rc = ensure_slots(ctx, m, pl.S * pl.lanes);
     if (rc) return rc;
     // trace tiles of 32 pixels, one warp each (shape from the autotuner, else 8 x 4)
@@ -1354,8 +1354,8 @@ srp_status srp_set_panel_angles(srp_ctx *ctx, int32_t mesh_id, int32_t n, const 
 }
 
 srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, int32_t n,
-                          const double *sun_dir_body, const double *sun_dist_au, double *force, double *torque,
-                          int32_t *hit_tri)
+                          const double *sun_dir_body, const double *quat, const double *sun_dist_au, double *force,
+                          double *torque, int32_t *hit_tri)
 {
     if (!ctx) return SRP_ERR_ARG;
     ctx->err.clear();
@@ -1367,6 +1367,7 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     memset(&ctx->last, 0, sizeof ctx->last);
     if (n == 0) return SRP_OK;
     if (!sun_dir_body || !force || !torque) return fail(ctx, SRP_ERR_ARG, "null input or output");
+    if (quat && !(m->mass > 0.0)) return fail(ctx, SRP_ERR_ARG, "an attitude quaternion needs the mesh mass > 0");
     CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     EvalPlan pl;
@@ -1377,22 +1378,37 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     bool dist_dev = sun_dist_au && is_device_ptr(sun_dist_au);
     bool f_dev = is_device_ptr(force), t_dev = is_device_ptr(torque);
     bool h_dev = hit_tri && is_device_ptr(hit_tri);
-    size_t io_need = (size_t)n * 3 * 3 + (size_t)n;
+    bool q_dev = quat && is_device_ptr(quat);
+    // io: sun (3n) dist (n) force (3n) torque (3n); with a quaternion also q (4n),
+    // the body-frame direction (3n) and the body-frame force (3n)
+    size_t io_need = (size_t)n * (quat ? 20 : 10);
     CK(ctx, grow(&ctx->io, &ctx->io_cap, io_need, false));
     double *d_sun = in_dev ? const_cast<double *>(sun_dir_body) : ctx->io;
     double *d_dist = sun_dist_au ? (dist_dev ? const_cast<double *>(sun_dist_au) : ctx->io + (size_t)n * 3) : nullptr;
     double *d_f = f_dev ? force : ctx->io + (size_t)n * 4;
     double *d_t = t_dev ? torque : ctx->io + (size_t)n * 7;
+    double *d_q = quat ? (q_dev ? const_cast<double *>(quat) : ctx->io + (size_t)n * 10) : nullptr;
+    double *d_sb = ctx->io + (size_t)n * 14, *d_fb = ctx->io + (size_t)n * 17;
     int t_in0 = tm.mark(st);
     if (!in_dev) CK(ctx, cudaMemcpyAsync(d_sun, sun_dir_body, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     if (sun_dist_au && !dist_dev)
         CK(ctx, cudaMemcpyAsync(d_dist, sun_dist_au, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    if (quat && !q_dev) CK(ctx, cudaMemcpyAsync(d_q, quat, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
     tm.span(4, t_in0, tm.mark(st));
     CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
     CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
     int64_t launches = 0, trace_launches = 0;
-    rc = eval_enqueue(ctx, m, prm, pl, n, d_sun, d_dist, d_f, d_t, hit_tri, h_dev, tm, launches, trace_launches);
+    if (quat) {
+        CK(ctx, launch_att_in(n, d_q, d_sun, d_sb, nullptr, nullptr, m->mass, st));
+        launches++;
+    }
+    rc = eval_enqueue(ctx, m, prm, pl, n, quat ? d_sb : d_sun, d_dist, quat ? d_fb : d_f, d_t, hit_tri, h_dev, tm,
+                      launches, trace_launches);
     if (rc) return rc;
+    if (quat) {
+        CK(ctx, launch_att_out(n, d_q, d_fb, d_f, m->mass, st));
+        launches++;
+    }
     int t_out0 = tm.mark(st);
     if (!f_dev) CK(ctx, cudaMemcpyAsync(force, d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     if (!t_dev) CK(ctx, cudaMemcpyAsync(torque, d_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
@@ -1453,7 +1469,7 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     PropState *S = ctx->prop_state;
     PropDev P = prop_dev(p, m);
     if (spad) {
-        // the SPAD table replaces the ray tracer (Sec. 6): staged once on the device
+        // the SPAD table replaces the ray tracer (Sec. 4.2): staged once on the device
         const size_t nt = (size_t)p->spad_grid.n_az * p->spad_grid.n_el * 6;
         CK(ctx, grow(&ctx->spad_buf, &ctx->spad_cap, nt, false));
         CK(ctx, cudaMemcpyAsync(ctx->spad_buf, p->spad_table, sizeof(double) * nt, cudaMemcpyDefault, st));
@@ -1572,7 +1588,7 @@ srp_status srp_spad_build(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     double *d_dir = ctx->spad_buf, *d_f = d_dir + 3 * (size_t)n, *d_t = d_f + 3 * (size_t)n;
     CK(ctx, launch_spad_dirs(spad_dev(g, nullptr), d_dir, st));
     // one evaluation per sample direction at 1 AU, through the evaluation pipeline
-    rc = srp_eval_batch(ctx, mesh_id, prm, n, d_dir, nullptr, d_f, d_t, nullptr);
+    rc = srp_eval_batch(ctx, mesh_id, prm, n, d_dir, nullptr, nullptr, d_f, d_t, nullptr);
     if (rc) return rc;
     // [n][3] force and torque interleaved into the table's [n][6]
     const size_t v3 = 3 * sizeof(double), v6 = 6 * sizeof(double);
@@ -1685,7 +1701,7 @@ srp_status srp_mesh_check(srp_ctx *ctx, int32_t mesh_id, const double *sun_dir_b
     prm.panel_mode = SRP_PANELS_TRACK;
     prm.flags = SRP_EVAL_TRAVERSE;
     double F[3], T[3];
-    srp_status rc = srp_eval_batch(ctx, mesh_id, &prm, 1, s, nullptr, F, T, nullptr);
+    srp_status rc = srp_eval_batch(ctx, mesh_id, &prm, 1, s, nullptr, nullptr, F, T, nullptr);
     if (rc) return rc;
     cudaStream_t st = ctx->stream;
     struct Tmp {
@@ -1747,8 +1763,9 @@ srp_status srp_set_materials(srp_ctx *ctx, int32_t mesh_id, int32_t n_mats, cons
 }
 
 srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, int32_t n, const double *sun_dir_body,
-                    const double *sun_dist_au, const double *g_force, const double *g_torque, double *force,
-                    double *torque, double *g_sun, double *g_dist, double *g_mat, double *g_angle)
+                    const double *quat, const double *sun_dist_au, const double *g_force, const double *g_torque,
+                    double *force, double *torque, double *g_sun, double *g_dist, double *g_mat, double *g_angle,
+                    double *g_quat)
 {
     if (!ctx) return SRP_ERR_ARG;
     ctx->err.clear();
@@ -1759,6 +1776,8 @@ srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, i
     if (prm->n_diffuse != 0) return fail(ctx, SRP_ERR_ARG, "srp_grad takes no diffuse rays (n_diffuse = 0)");
     if (n < 0) return fail(ctx, SRP_ERR_ARG, "n < 0");
     if (g_dist && !sun_dist_au) return fail(ctx, SRP_ERR_ARG, "g_dist needs sun_dist_au");
+    if (g_quat && !quat) return fail(ctx, SRP_ERR_ARG, "g_quat needs quat");
+    if (quat && !(m->mass > 0.0)) return fail(ctx, SRP_ERR_ARG, "an attitude quaternion needs the mesh mass > 0");
     memset(&ctx->last, 0, sizeof ctx->last);
     const int NM2 = 2 * m->h.n_mats, NP = m->h.n_parts, GE = NM2 + NP;
     CK(ctx, cudaSetDevice(ctx->device));
@@ -1778,16 +1797,18 @@ srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, i
     const size_t n3 = (size_t)n * 3;
     size_t off_sun = 0, off_dist = n3, off_gf = off_dist + n, off_gt = off_gf + n3, off_f = off_gt + n3,
            off_t = off_f + n3, off_gs = off_t + n3, off_gd = off_gs + n3, off_ge = off_gd + n,
-           off_sum = off_ge + (size_t)n * GE, need = off_sum + GE;
+           off_sum = off_ge + (size_t)n * GE, off_q = off_sum + GE, off_gq = off_q + 4 * (size_t)n,
+           off_sb = off_gq + 4 * (size_t)n, off_gfb = off_sb + n3, off_fb = off_gfb + n3, off_gsb = off_fb + n3,
+           need = quat ? off_gsb + n3 : off_q;
     CK(ctx, grow(&ctx->gio, &ctx->gio_cap, need, false));
     double *G = ctx->gio;
     struct In {
         const double *src;
         size_t off, count;
-    } ins[4] = {{sun_dir_body, off_sun, n3}, {sun_dist_au, off_dist, (size_t)n}, {g_force, off_gf, n3},
-                {g_torque, off_gt, n3}};
-    const double *dev[4];
-    for (int k = 0; k < 4; k++) {
+    } ins[5] = {{sun_dir_body, off_sun, n3}, {sun_dist_au, off_dist, (size_t)n}, {g_force, off_gf, n3},
+                {g_torque, off_gt, n3}, {quat, off_q, 4 * (size_t)n}};
+    const double *dev[5];
+    for (int k = 0; k < 5; k++) {
         if (!ins[k].src) { dev[k] = nullptr; continue; }
         if (is_device_ptr(ins[k].src)) { dev[k] = ins[k].src; continue; }
         CK(ctx, cudaMemcpyAsync(G + ins[k].off, ins[k].src, sizeof(double) * ins[k].count, cudaMemcpyHostToDevice, st));
@@ -1795,19 +1816,33 @@ srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, i
     }
     CK(ctx, cudaMemsetAsync(ctx->err_flags, 0, sizeof(int), st));
     CK(ctx, cudaMemsetAsync(ctx->stats, 0, 16 * sizeof(unsigned long long), st));
-    AdjBatch ab{dev[0], dev[1], dev[2], dev[3], G + off_gs, g_dist ? G + off_gd : nullptr, G + off_ge, prm->panel_mode};
-    Timing tm(ctx, false);
     int64_t launches = 0, trace_launches = 0;
-    rc = eval_enqueue(ctx, m, prm, pl, n, dev[0], dev[1], G + off_f, G + off_t, nullptr, false, tm, launches,
+    // with a quaternion the evaluation runs on the body-frame direction and the
+    // body-frame force cotangent; the attitude is differentiated around it
+    const double *e_sun = dev[0], *e_gf = dev[2];
+    double *e_f = G + off_f, *e_gs = G + off_gs;
+    if (quat) {
+        CK(ctx, launch_att_in(n, dev[4], dev[0], G + off_sb, dev[2], G + off_gfb, m->mass, st));
+        launches++;
+        e_sun = G + off_sb; e_gf = G + off_gfb; e_f = G + off_fb; e_gs = G + off_gsb;
+    }
+    AdjBatch ab{e_sun, dev[1], e_gf, dev[3], e_gs, g_dist ? G + off_gd : nullptr, G + off_ge, prm->panel_mode};
+    Timing tm(ctx, false);
+    rc = eval_enqueue(ctx, m, prm, pl, n, e_sun, dev[1], e_f, G + off_t, nullptr, false, tm, launches,
                       trace_launches, &ab);
     if (rc) return rc;
     CK(ctx, launch_adj_sum(G + off_ge, n, m->h.n_mats, NP, G + off_sum, G + off_sum + NM2, st));
     launches++;
+    if (quat) {
+        CK(ctx, launch_att_grad(n, dev[4], dev[0], e_f, dev[2], e_gs, G + off_gs, G + off_gq, m->mass, st));
+        CK(ctx, launch_att_out(n, dev[4], e_f, G + off_f, m->mass, st));
+        launches += 2;
+    }
     struct Out {
         double *dst;
         size_t off, count;
-    } outs[6] = {{force, off_f, n3}, {torque, off_t, n3}, {g_sun, off_gs, n3}, {g_dist, off_gd, (size_t)n},
-                 {g_mat, off_sum, (size_t)NM2}, {g_angle, off_sum + NM2, (size_t)NP}};
+    } outs[7] = {{force, off_f, n3}, {torque, off_t, n3}, {g_sun, off_gs, n3}, {g_dist, off_gd, (size_t)n},
+                 {g_mat, off_sum, (size_t)NM2}, {g_angle, off_sum + NM2, (size_t)NP}, {g_quat, off_gq, 4 * (size_t)n}};
     for (auto &o : outs)
         if (o.dst) CK(ctx, cudaMemcpyAsync(o.dst, G + o.off, sizeof(double) * o.count, cudaMemcpyDefault, st));
     int flags = 0;
@@ -2034,7 +2069,7 @@ srp_status srp_autotune(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *pr
         double tmin = INFINITY;
         for (int rep = 0; rep < 3; rep++) {
             CK(ctx, cudaEventRecord(e0, ctx->stream));
-            rc = srp_eval_batch(ctx, mesh_id, &q, nd, d, nullptr, d + 3 * nd, d + 6 * nd, nullptr);
+            rc = srp_eval_batch(ctx, mesh_id, &q, nd, d, nullptr, nullptr, d + 3 * nd, d + 6 * nd, nullptr);
             if (rc) break;
             CK(ctx, cudaEventRecord(e1, ctx->stream));
             CK(ctx, cudaEventSynchronize(e1));

@@ -1,11 +1,10 @@
 // noalloc.cu -- srp_eval_noalloc: an SRP evaluation that allocates no memory.
 //
 // For callers that cannot allocate device memory at run time: flight or
-// real-time software whose memory is fixed at start-up, code running inside a
-// CUDA stream capture (where cudaMalloc would break the capture), or a host
-// that only hands out memory through its own pool.  The caller passes every
-// input and output; the only scratch is the file-scope array below, reserved
-// when the library is loaded.
+// real-time software whose memory is fixed at start-up (an allocation could
+// fail or stall mid-mission), or a host that only hands out memory through its
+// own pool.  The caller passes every input and output; the only scratch is the
+// file-scope array below, reserved when the library is loaded.
 //
 // It is a variant of the FP64 re-trace kernel of trace.cu without the BVH:
 // each ray is tested against every triangle (small meshes only), in FP64, so
@@ -144,6 +143,13 @@ __global__ void __launch_bounds__(kNaThreads) k_na_trace(NaArgs a, double *scrat
         int side = dn < 0.0 ? 0 : 1;
         double sg = side ? -1.0 : 1.0;
         int mi = a.tmat[2 * best + side];
+        if (mi < 0 || mi >= a.n_mats) {
+            // a material index the caller left out of range: no read of mat; the
+            // result becomes NaN so the caller sees it
+            for (int k = 0; k < 6; k++) acc[k] += NAN;
+            live = false;
+            continue;
+        }
         double rs = a.mat[2 * mi], rd = a.mat[2 * mi + 1];
         double c = -sg * dn, F[3], hp[3];
         for (int k = 0; k < 3; k++) {
@@ -193,11 +199,21 @@ __global__ void __launch_bounds__(kNaThreads) k_na_reduce(NaArgs a, int nblocks,
     }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array per device.  Only a successful lookup
+// is kept; a failed one is tried again on the next call.
 constexpr int kNaMaxDevices = 64;
 double *g_na_ptr[kNaMaxDevices];
-cudaError_t g_na_err[kNaMaxDevices];
-std::once_flag g_na_once[kNaMaxDevices];
+std::mutex g_na_mu[kNaMaxDevices];
+
+double *na_scratch(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_na_mu[dev]);
+    if (!g_na_ptr[dev]) {
+        double *p = nullptr;
+        if (cudaGetSymbolAddress((void **)&p, g_na_scratch) == cudaSuccess) g_na_ptr[dev] = p;
+    }
+    return g_na_ptr[dev];
+}
 
 }  // namespace
 }  // namespace srp
@@ -217,11 +233,8 @@ extern "C" srp_status srp_eval_noalloc(const double *tri_xyz, const int32_t *tri
     if (!(sn > 0.0)) return SRP_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return SRP_ERR_CUDA;
-    std::call_once(g_na_once[dev], [dev]() {
-        g_na_err[dev] = cudaGetSymbolAddress((void **)&g_na_ptr[dev], g_na_scratch);
-    });
-    if (g_na_err[dev] != cudaSuccess || !g_na_ptr[dev]) return SRP_ERR_CUDA;
-    double *scratch = g_na_ptr[dev];
+    double *scratch = na_scratch(dev);
+    if (!scratch) return SRP_ERR_CUDA;
     NaArgs a{};
     a.xyz = tri_xyz; a.tmat = tri_mat; a.mat = mat;
     a.n_tris = n_tris; a.n_mats = n_mats; a.N = N; a.nseg = bounces + 1;
@@ -235,8 +248,15 @@ extern "C" srp_status srp_eval_noalloc(const double *tri_xyz, const int32_t *tri
     a.scale = P0 / (sun_dist_au * sun_dist_au);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     int nblocks = (int)(((size_t)N * N + kNaThreads - 1) / kNaThreads);
+    // A launch error left pending by earlier, unrelated work on this thread is
+    // cleared here so that it is not reported as this call's failure (an error
+    // that poisons the context makes the launches below fail as well).
+    (void)cudaGetLastError();
     k_na_window<<<1, kNaThreads, 0, st>>>(a, scratch);
+    if (cudaPeekAtLastError() != cudaSuccess) return SRP_ERR_CUDA;
     k_na_trace<<<nblocks, kNaThreads, 0, st>>>(a, scratch);
+    if (cudaPeekAtLastError() != cudaSuccess) return SRP_ERR_CUDA;
     k_na_reduce<<<1, kNaThreads, 0, st>>>(a, nblocks, scratch, force, torque);
-    return cudaGetLastError() == cudaSuccess ? SRP_OK : SRP_ERR_CUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return SRP_ERR_CUDA;
+    return SRP_OK;
 }

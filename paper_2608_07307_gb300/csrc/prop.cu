@@ -86,17 +86,6 @@ __device__ void sun_pos(double mjd_tt, double *r)
     r[2] = rr * sl * se;
 }
 
-// rotation of the normalised scalar-first quaternion q, row-major
-__device__ void quat_matrix(const double *q, double *Q)
-{
-    double w = q[0], x = q[1], yy = q[2], z = q[3];
-    double qn = sqrt(w * w + x * x + yy * yy + z * z);
-    w /= qn; x /= qn; yy /= qn; z /= qn;
-    Q[0] = 1.0 - 2.0 * (yy * yy + z * z); Q[1] = 2.0 * (x * yy - w * z);       Q[2] = 2.0 * (x * z + w * yy);
-    Q[3] = 2.0 * (x * yy + w * z);       Q[4] = 1.0 - 2.0 * (x * x + z * z);   Q[5] = 2.0 * (yy * z - w * x);
-    Q[6] = 2.0 * (x * z - w * yy);       Q[7] = 2.0 * (yy * z + w * x);       Q[8] = 1.0 - 2.0 * (x * x + yy * yy);
-}
-
 // LVLH frame at y: columns x_b = y_b x z_b, y_b = -orbit normal, z_b = nadir
 __device__ void lvlh_matrix(const double *y, double *L)
 {
@@ -273,7 +262,7 @@ __device__ __forceinline__ void accel_body(PropState &X, int i, const PropDev &P
         double Fs[6];
         const double *F = force + 3 * i;
         if (P.spad.table) {
-            // SPAD interpolation (Sec. 6) at this stage's body-frame Sun direction
+            // SPAD interpolation (Sec. 4.2) at this stage's body-frame Sun direction
             spad_lookup(P.spad, sun_dir + 3 * i, sun_dist[i], Fs);
             F = Fs;
         }
@@ -553,19 +542,9 @@ __global__ void k_adj_prop_out(int n, PropDev P, int stage, const StageRec *rec,
             for (int k = 0; k < 3; k++) rb[k] += -(zbb[k] - zd * rh[k]) / rn;
         }
         // Q of the normalised quaternion, differentiated
-        double qn = sqrt(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
-        double w0 = P.q[0] / qn, x = P.q[1] / qn, yy = P.q[2] / qn, z = P.q[3] / qn;
         double g[4];
-        g[0] = -2 * z * Qb[1] + 2 * yy * Qb[2] + 2 * z * Qb[3] - 2 * x * Qb[5] - 2 * yy * Qb[6] + 2 * x * Qb[7];
-        g[1] = 2 * yy * Qb[1] + 2 * z * Qb[2] + 2 * yy * Qb[3] - 4 * x * Qb[4] - 2 * w0 * Qb[5] + 2 * z * Qb[6] +
-               2 * w0 * Qb[7] - 4 * x * Qb[8];
-        g[2] = -4 * yy * Qb[0] + 2 * x * Qb[1] + 2 * w0 * Qb[2] + 2 * x * Qb[3] + 2 * z * Qb[5] - 2 * w0 * Qb[6] +
-               2 * z * Qb[7] - 4 * yy * Qb[8];
-        g[3] = -4 * z * Qb[0] - 2 * w0 * Qb[1] + 2 * x * Qb[2] + 2 * w0 * Qb[3] - 4 * z * Qb[4] + 2 * yy * Qb[5] +
-               2 * x * Qb[6] + 2 * yy * Qb[7];
-        double qh[4] = {w0, x, yy, z};
-        double gd = g[0] * qh[0] + g[1] * qh[1] + g[2] * qh[2] + g[3] * qh[3];
-        for (int k = 0; k < 4; k++) X.qbar[k] += (g[k] - gd * qh[k]) / qn;
+        quat_matrix_vjp(P.q, Qb, g);
+        for (int k = 0; k < 4; k++) X.qbar[k] += g[k];
     }
     for (int k = 0; k < 3; k++) { X.ybar[stage][k] = rb[k]; X.ybar[stage][3 + k] = vb[k]; }
 }

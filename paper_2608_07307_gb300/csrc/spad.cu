@@ -1,4 +1,4 @@
-// SPAD interpolation model (Sec. 6, Sec. 8.1): the sample directions of a
+// SPAD interpolation model (Sec. 4.2, Sec. 6.1): the sample directions of a
 // table and its bilinear interpolant at arbitrary body-frame directions.  The
 // table itself is built by the evaluation pipeline (srp_spad_build) and read
 // inside propagation by k_prop_accel through spad_lookup.

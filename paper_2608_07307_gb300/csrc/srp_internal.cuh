@@ -35,6 +35,38 @@ constexpr double kStandoff = 1.0;   // ray origins start 1 m in front of the nea
 // Device error flags (bits of SlotPose::flags / the context error word).
 constexpr int kFlagStack = 1;
 
+// Rotation of the normalised scalar-first quaternion q, row-major.
+__device__ __forceinline__ void quat_matrix(const double *q, double *Q)
+{
+    double w = q[0], x = q[1], yy = q[2], z = q[3];
+    double qn = sqrt(w * w + x * x + yy * yy + z * z);
+    w /= qn; x /= qn; yy /= qn; z /= qn;
+    Q[0] = 1.0 - 2.0 * (yy * yy + z * z); Q[1] = 2.0 * (x * yy - w * z);       Q[2] = 2.0 * (x * z + w * yy);
+    Q[3] = 2.0 * (x * yy + w * z);       Q[4] = 1.0 - 2.0 * (x * x + z * z);   Q[5] = 2.0 * (yy * z - w * x);
+    Q[6] = 2.0 * (x * z - w * yy);       Q[7] = 2.0 * (yy * z + w * x);       Q[8] = 1.0 - 2.0 * (x * x + yy * yy);
+}
+
+// Cotangent g[4] of the quaternion q as given (before its normalisation) from
+// the cotangent Qb[9] of its rotation matrix: the derivative of each entry of
+// quat_matrix in the normalised components, then the projection of the
+// normalisation (g is orthogonal to q).
+__device__ __forceinline__ void quat_matrix_vjp(const double *q, const double *Qb, double *out)
+{
+    double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double w0 = q[0] / qn, x = q[1] / qn, yy = q[2] / qn, z = q[3] / qn;
+    double g[4];
+    g[0] = -2 * z * Qb[1] + 2 * yy * Qb[2] + 2 * z * Qb[3] - 2 * x * Qb[5] - 2 * yy * Qb[6] + 2 * x * Qb[7];
+    g[1] = 2 * yy * Qb[1] + 2 * z * Qb[2] + 2 * yy * Qb[3] - 4 * x * Qb[4] - 2 * w0 * Qb[5] + 2 * z * Qb[6] +
+           2 * w0 * Qb[7] - 4 * x * Qb[8];
+    g[2] = -4 * yy * Qb[0] + 2 * x * Qb[1] + 2 * w0 * Qb[2] + 2 * x * Qb[3] + 2 * z * Qb[5] - 2 * w0 * Qb[6] +
+           2 * z * Qb[7] - 4 * yy * Qb[8];
+    g[3] = -4 * z * Qb[0] - 2 * w0 * Qb[1] + 2 * x * Qb[2] + 2 * w0 * Qb[3] - 4 * z * Qb[4] + 2 * yy * Qb[5] +
+           2 * x * Qb[6] + 2 * yy * Qb[7];
+    double qh[4] = {w0, x, yy, z};
+    double gd = g[0] * qh[0] + g[1] * qh[1] + g[2] * qh[2] + g[3] * qh[3];
+    for (int k = 0; k < 4; k++) out[k] = (g[k] - gd * qh[k]) / qn;
+}
+
 // Static per-part description (host and device copies).
 struct PartInfo {
     int parent;         // -1 for the root
@@ -191,7 +223,7 @@ constexpr int kRastBigBlocks = 2048;  // k_raster_big grid (8 warps a block, one
 constexpr int kBigPerSlot = 65536;  // chunk-list entries reserved per slot
 size_t trace_ctx_bytes();
 
-// SPAD table (Sec. 6): force and torque at 1 AU for a grid of body-frame Sun
+// SPAD table (Sec. 4.2, Sec. 6.1): force and torque at 1 AU for a grid of body-frame Sun
 // directions, [n_el][n_az][6] (srp_spad_grid gives the sample directions).
 struct SpadDev {
     const double *table;  // device; null when the SRP force is ray-traced
@@ -385,5 +417,16 @@ cudaError_t launch_adj_prop_out(int n, const PropDev &P, int stage, const StageR
                                 const double *g_sun, const double *g_dist, cudaStream_t st);
 cudaError_t launch_adj_prop_step(int n, PropAdj *A, cudaStream_t st);
 cudaError_t launch_adj_prop_qsum(int n, const PropAdj *A, double *out, cudaStream_t st);
+
+// attitude.cu: evaluations given in the inertial frame with a body -> inertial
+// quaternion per evaluation.  att_in: s_body = R(q)^T s_in (and, when g_in is
+// given, g_body = R(q)^T g_in / mass); att_out: force = R(q) F_body / mass;
+// att_grad: additionally g_sun = R g_sbody and the quaternion cotangent of
+// L = g_acc . R F_body / mass + g_sbody . R^T s_in.
+cudaError_t launch_att_in(int n, const double *q, const double *s_in, double *s_body, const double *g_in,
+                          double *g_body, double mass, cudaStream_t st);
+cudaError_t launch_att_out(int n, const double *q, const double *f_body, double *acc, double mass, cudaStream_t st);
+cudaError_t launch_att_grad(int n, const double *q, const double *s_in, const double *f_body, const double *g_acc,
+                            const double *g_sbody, double *g_sun, double *g_q, double mass, cudaStream_t st);
 
 }  // namespace srp

@@ -67,7 +67,7 @@ def sun_dirs_uniform(n: int, seed: int = 0) -> np.ndarray:
 
 
 def spad_grid(n_az: int, n_el: int, az0_deg: float, el0_deg: float, d_el_deg: float | None = None) -> dict:
-    """A SPAD sampling grid (Sec. 6, Sec. 8.1): n_az azimuths from az0, spaced
+    """A SPAD sampling grid (Sec. 4.2, Sec. 6.1): n_az azimuths from az0, spaced
     360/n_az degrees around the circle, and n_el elevations from el0, spaced
     d_el (default 180/n_el) degrees.  Angles in radians in the result."""
     d_el = 180.0 / n_el if d_el_deg is None else d_el_deg
@@ -220,7 +220,7 @@ def box_wing() -> Mesh:
 
 
 def box_wing_two_axis() -> Mesh:
-    """The box-wing with a two-axis array drive per wing (Sec. 7): a yoke
+    """The box-wing with a two-axis array drive per wing (Sec. 9): a yoke
     (a 0.1 m square strut, bus material, from y = 0.51 to 0.74 m) turns about
     the body y axis within +-90 degrees and carries the 2 x 1 m panel, which
     folds about the x axis through its inner edge (|y| = 0.75 m) within +-45

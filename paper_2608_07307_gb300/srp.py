@@ -25,6 +25,7 @@ EVAL_TIMING = 2
 EVAL_TRAVERSE = 8  # primary hits by BVH traversal instead of rasterisation (same results)
 EVAL_TEST_WALK_BOUND = 16  # tests of the walk bound's error path: every BVH walk stops after one step
 EVAL_AUTOTUNE = 4
+EVAL_SERIAL = 32  # one pipeline lane: with timing, each phase's time is its own kernels' GPU time
 MAX_BOUNCES = 4
 MAX_N = 8192  # SRP_MAX_N: rays per window side
 MAX_DIFFUSE = 256  # diffuse secondary rays per hit (srp_eval_params.n_diffuse)
@@ -132,10 +133,10 @@ def load(build_if_needed: bool = True):
         lib.srp_mesh_free.argtypes = [C.c_void_p, C.c_int32]
         lib.srp_set_panel_angles.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
         lib.srp_eval_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32, C.c_void_p,
-                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.srp_eval_stats_get.argtypes = [C.c_void_p, C.POINTER(EvalStats)]
         lib.srp_set_materials.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
-        lib.srp_grad.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32] + [C.c_void_p] * 10
+        lib.srp_grad.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.c_int32] + [C.c_void_p] * 12
         lib.srp_propagate_batch.argtypes = [C.c_void_p, C.POINTER(PropParams), C.c_int32, C.POINTER(Traj),
                                             C.c_void_p, C.POINTER(PropStats)]
         lib.srp_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(EvalParams), C.POINTER(C.c_int32),
@@ -170,6 +171,16 @@ def eval_noalloc(tri_xyz, tri_mat, mat, sun_dir, sun_dist_au, c_ref, N, bounces,
     import torch
     lib = load()
     st = stream if stream is not None else torch.cuda.current_stream()
+    n = int(tri_xyz.shape[0]) if tri_xyz.dim() >= 1 else 0
+    m = int(mat.shape[0]) if mat.dim() >= 1 else 0
+    want = ((tri_xyz, torch.float64, (n, 9)), (tri_mat, torch.int32, (n, 2)), (mat, torch.float64, (m, 2)),
+            (force, torch.float64, (3,)), (torque, torch.float64, (3,)))
+    for k, (t, dt, shape) in enumerate(want):
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+            raise SrpError(SRP_ERR_ARG, f"srp_eval_noalloc: argument {k} must be a contiguous {dt} tensor of "
+                                        f"shape {shape}")
+        if t.device.type != "cuda" or t.device != st.device:
+            raise SrpError(SRP_ERR_ARG, f"srp_eval_noalloc: argument {k} must live on the stream's device {st.device}")
     s = (C.c_double * 3)(*[float(x) for x in sun_dir])
     c = (C.c_double * 3)(*[float(x) for x in c_ref])
     rc = lib.srp_eval_noalloc(tri_xyz.data_ptr(), tri_mat.data_ptr(), int(tri_xyz.shape[0]), mat.data_ptr(),
@@ -293,22 +304,19 @@ class Context:
     def eval_batch(self, mesh_id: int, sun_dirs, sun_dist=None, N: int = 256, bounces: int = 1, P0: float = 4.56e-6,
                    eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, hits: bool = False, count: bool = False,
                    timing: bool = False, out=None, traverse: bool = False, n_diffuse: int = 0,
-                   diffuse_seed: int = 0, flags: int = 0):
+                   diffuse_seed: int = 0, flags: int = 0, quat=None):
         """Force [n,3] (N) and torque [n,3] (N m); with hits=True also the per-ray
         hit triangle ids [n, N*N, bounces+1].  Outputs live where the input lives
         (CUDA tensor in, CUDA tensors out; numpy in, numpy out) unless `out`
         = (force, torque[, hits]) is given.  n_diffuse: diffuse secondary rays
-        per hit (srp_eval_params)."""
+        per hit (srp_eval_params).  quat [n,4] (body -> inertial, scalar
+        first): sun_dirs are then inertial and the first output is the SRP
+        acceleration R(q) F / mass (m/s^2, inertial frame)."""
         n = int(sun_dirs.shape[0])
         cuda = _is_cuda(sun_dirs)
-        if isinstance(sun_dirs, np.ndarray):
-            sun_dirs = np.ascontiguousarray(sun_dirs, np.float64)
-        else:
-            sun_dirs = sun_dirs.contiguous()
-        if isinstance(sun_dist, np.ndarray):
-            sun_dist = np.ascontiguousarray(sun_dist, np.float64)
-        elif sun_dist is not None:
-            sun_dist = sun_dist.contiguous()
+        conv = lambda x: None if x is None else (np.ascontiguousarray(x, np.float64) if isinstance(x, np.ndarray)  # noqa: E731
+                                                 else x.contiguous())
+        sun_dirs, sun_dist, quat = conv(sun_dirs), conv(sun_dist), conv(quat)
         nseg = bounces + 1
         if out is not None:
             force, torque = out[0], out[1]
@@ -324,11 +332,12 @@ class Context:
         p = EvalParams(N, bounces, P0, eps_rel, panel_mode, (EVAL_COUNT if count else 0) | (EVAL_TIMING if timing else 0)
                        | (EVAL_TRAVERSE if traverse else 0) | flags, n_diffuse, diffuse_seed)
         ps, k1 = _ptr(sun_dirs)
+        pq, k0 = _ptr(quat)
         pd, k2 = _ptr(sun_dist)
         pf, k3 = _ptr(force)
         pt, k4 = _ptr(torque)
         ph, k5 = _ptr(hit)
-        self._check(self.lib.srp_eval_batch(self.h, mesh_id, C.byref(p), n, ps, pd, pf, pt, ph))
+        self._check(self.lib.srp_eval_batch(self.h, mesh_id, C.byref(p), n, ps, pq, pd, pf, pt, ph))
         return (force, torque, hit) if hits else (force, torque)
 
     def propagate(self, mesh_id: int, y0, t0_t1, method: int = RKF78, central: int = CENTRAL_EARTH, j2=False,
@@ -463,25 +472,29 @@ class Context:
 
     def grad(self, mesh_id: int, sun_dirs, g_force, g_torque, sun_dist=None, N: int = 256, bounces: int = 1,
              P0: float = 4.56e-6, eps_rel: float = 1e-9, panel_mode: int = PANELS_TRACK, n_mats=None,
-             n_parts=None):
+             n_parts=None, quat=None):
         """srp_grad: force, torque and the frozen-hit gradients of
         L = sum g_force . F + g_torque . T.  Returns a dict with F, T [n,3],
-        sun [n,3], dist [n] (when sun_dist is given), mat [n_mats,2] and
-        angle [n_parts].  CUDA tensors in, CUDA tensors out; numpy otherwise."""
+        sun [n,3], dist [n] (when sun_dist is given), mat [n_mats,2],
+        angle [n_parts] and, with quat [n,4], quat [n,4] (F is then the
+        inertial SRP acceleration R(q) F / mass and sun_dirs are inertial).
+        CUDA tensors in, CUDA tensors out; numpy otherwise."""
         n = int(sun_dirs.shape[0])
         cuda = _is_cuda(sun_dirs)
         mk = _maker(sun_dirs)
         conv = lambda x: None if x is None else (np.ascontiguousarray(x, np.float64) if isinstance(x, np.ndarray)  # noqa: E731
                                                  else x.contiguous())
-        sun_dirs, g_force, g_torque, sun_dist = map(conv, (sun_dirs, g_force, g_torque, sun_dist))
+        sun_dirs, g_force, g_torque, sun_dist, quat = map(conv, (sun_dirs, g_force, g_torque, sun_dist, quat))
         M = self.mesh_info[mesh_id]["n_mats"] if n_mats is None else n_mats
         P = self.mesh_info[mesh_id]["n_parts"] if n_parts is None else n_parts
         out = dict(F=mk((n, 3)), T=mk((n, 3)), sun=mk((n, 3)), mat=mk((M, 2)), angle=mk((P,)))
         if sun_dist is not None:
             out["dist"] = mk((n,))
+        if quat is not None:
+            out["quat"] = mk((n, 4))
         p = EvalParams(N, bounces, P0, eps_rel, panel_mode, 0)
-        args = [sun_dirs, sun_dist, g_force, g_torque, out["F"], out["T"], out["sun"], out.get("dist"), out["mat"],
-                out["angle"]]
+        args = [sun_dirs, quat, sun_dist, g_force, g_torque, out["F"], out["T"], out["sun"], out.get("dist"),
+                out["mat"], out["angle"], out.get("quat")]
         ptrs = [_ptr(x) for x in args]
         self._check(self.lib.srp_grad(self.h, mesh_id, C.byref(p), n, *[q[0] for q in ptrs]))
         return out

@@ -306,27 +306,32 @@ def test_headline_size_sampled_rays(ctx):
     """The 200k-triangle spacecraft at 1024^2 rays and 2 bounces, 32 Fibonacci
     directions in one call (the benchmark's launch configuration: chunks of
     eight evaluations over four lanes, rasterised primaries): per-ray hit ids
-    of sampled rays of two directions against the oracle traced ray by
-    ray (2048 a direction: about 20 s of single-threaded oracle work each).
-    Mismatches only at edges (R13)."""
+    of sampled rays against the oracle traced ray by ray, 100 000 rays of
+    direction 0 (enough to resolve the 1e-5 mismatch bar; the oracle's rays
+    are sharded over the host's cores) and 4096 of direction 17.  No sampled
+    ray may differ; a difference is reported with its edge proximity (R13)."""
+    import os
     m = I.spacecraft(0.025)
     mid = ctx.load_mesh(m)
     dirs = I.sun_dirs_fibonacci(4096)[:32]
     N, B = 1024, 2
     F, T, H = ctx.eval_batch(mid, dirs, N=N, bounces=B, hits=True)
+    H = np.asarray(H)
+    ctx.free_mesh(mid)
     rng = np.random.default_rng(5)
-    for k in (0, 17):
-        rays = np.sort(rng.choice(N * N, size=2048, replace=False))
-        r = O.eval_rays(m, dirs[k], rays, N, B)
+    procs = max(1, min(16, os.cpu_count() or 1))
+    for k, n in ((0, 100000), (17, 4096)):
+        rays = np.sort(rng.choice(N * N, size=n, replace=False))
+        r = O.eval_rays(m, dirs[k], rays, N, B, procs=procs)
         L = O.evaluate(m, dirs[k], 1, 0)["win"][6]
-        gh = np.asarray(H[k])[rays]
+        gh = H[k][rays]
         diff = np.nonzero((gh != r["hits"]).any(axis=1))[0]
+        report = []
         for q in diff:
             seg = int(np.argmax(gh[q] != r["hits"][q]))
-            assert r["edge"][q, seg] < 1e-6 * L, (k, rays[q], gh[q], r["hits"][q])
-        assert len(diff) <= 1, (k, len(diff))
-        assert (r["hits"][:, 0] >= 0).sum() > 1000
-    ctx.free_mesh(mid)
+            report.append((int(rays[q]), gh[q].tolist(), r["hits"][q].tolist(), float(r["edge"][q, seg] / L)))
+        assert len(diff) == 0, (k, report)
+        assert (r["hits"][:, 0] >= 0).sum() > n // 2
 
 
 def _fullsize_golden():
@@ -369,7 +374,7 @@ def test_fullsize_forces_against_stored_oracle():
 
 def test_two_axis_box_wing_clamped_tracking(ctx):
     """The two-axis array drive (support +-90 deg carrying a hinge +-45 deg,
-    Sec. 7): joint angles composed down the tree and clamped on the device;
+    Sec. 9): joint angles composed down the tree and clamped on the device;
     Sun directions over the whole sphere, most of them clamping a joint."""
     m = I.box_wing_two_axis()
     mid = ctx.load_mesh(m)

@@ -124,13 +124,13 @@ def test_several_trajectories_of_uneven_length(ctx):
 
 
 def test_thirty_day_geo_within_ten_metres(ctx):
-    """Box-wing in GEO, tracking panels, two-body + J2 + Sun + SRP (64 x 64 rays,
+    """Box-wing in GEO, tracking panels, two-body + J2 + Sun + SRP (128 x 128 rays,
     1 bounce), RKF7(8) rtol 1e-12 over 30 days: GPU vs oracle."""
     m = I.box_wing()
     mid = ctx.load_mesh(m)
     T = 30 * 86400.0
-    y1, st, _ = ctx.propagate(mid, GEO, [0.0, T], j2=True, sun3=True, N=64, bounces=1)
-    pp = O.prop_params(central=0, j2=True, sun3=True, srp=True, mass=m.mass, N=64, bounces=1)
+    y1, st, _ = ctx.propagate(mid, GEO, [0.0, T], j2=True, sun3=True, N=128, bounces=1)
+    pp = O.prop_params(central=0, j2=True, sun3=True, srp=True, mass=m.mass, N=128, bounces=1)
     yo, so, _ = O.propagate(m, pp, 0.0, T, GEO)
     assert np.linalg.norm(y1[0, :3] - yo[:3]) < 10.0
     assert abs(st[0]["steps"] - so[0]) <= 0.05 * so[0]

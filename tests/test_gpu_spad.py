@@ -1,4 +1,4 @@
-"""GPU parity of the SPAD interpolation model (Sec. 6, Sec. 8.1) against the
+"""GPU parity of the SPAD interpolation model (Sec. 4.2, Sec. 6.1) against the
 oracle: the table built by the evaluation pipeline, the interpolant at
 arbitrary directions, and propagation with the interpolated force.
 
@@ -140,7 +140,7 @@ def test_propagation_zero_table_is_srp_off(ctx):
 
 
 def test_denser_tables_track_the_direct_propagation_closer(ctx):
-    """The paper's RQ1 comparison in miniature (Sec. 8.1): GEO day with
+    """The paper's RQ1 comparison in miniature (Sec. 7): GEO day with
     tracking panels, direct ray tracing against SPAD tables of three
     densities built from the same evaluations; the position gap to the
     direct arc shrinks as the grid refines and stays a small part of the

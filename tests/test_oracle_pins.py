@@ -355,7 +355,7 @@ def _panel_normal(m, xyz, part):
 
 
 def test_two_axis_drive_reaches_the_sun():
-    """Two-axis array drive (Sec. 7; support +-90 deg about y, hinge +-45 deg
+    """Two-axis array drive (Sec. 9; support +-90 deg about y, hinge +-45 deg
     about x): for a Sun direction within reach (s_z >= 0, |s_y| <= sin 45
     deg) both panels face the Sun exactly, and the rigid parts do not move."""
     m = I.box_wing_two_axis()

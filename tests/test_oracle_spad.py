@@ -1,4 +1,4 @@
-"""Pins of the oracle's SPAD interpolation model (Sec. 6, Sec. 8.1).
+"""Pins of the oracle's SPAD interpolation model (Sec. 4.2, Sec. 6.1).
 
 The interpolant is pinned by what bilinear interpolation on an azimuth /
 elevation grid must do, whatever the code: reproduce the samples, be exact
@@ -37,7 +37,7 @@ def _bilinear_table(g, coef):
 
 def test_grid_directions_of_the_paper_sets():
     """20 x 10 from (-180, -90) degrees has a row at 0 degrees elevation and
-    the shifted set does not (Sec. 8.1); every direction is a unit vector with
+    the shifted set does not (Sec. 6.1); every direction is a unit vector with
     the stated azimuth and elevation."""
     for g, has_zero in ((I.SPAD_20x10, True), (I.SPAD_20x10S, False)):
         d = O.spad_dirs(g)
