@@ -63,8 +63,6 @@ struct srp_ctx {
     // rasterised primary visibility: pixel buffers (kept cleared), per-lane chunk lists
     unsigned long long *pix_key = nullptr;
     size_t pix_key_cap = 0;
-    unsigned *pix_cnt = nullptr;
-    size_t pix_cnt_cap = 0;
     unsigned *pix_cand = nullptr;
     size_t pix_cand_cap = 0;
     int4 *big = nullptr;
@@ -590,7 +588,6 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * pl.nbx, false));
     if (!(prm->flags & SRP_EVAL_TRAVERSE)) {
         CK(ctx, grow(&ctx->pix_key, &ctx->pix_key_cap, SL * pl.R, false));
-        CK(ctx, grow(&ctx->pix_cnt, &ctx->pix_cnt_cap, SL * pl.R, false));
         CK(ctx, grow(&ctx->pix_cand, &ctx->pix_cand_cap, SL * pl.R * kPixCand, false));
         CK(ctx, grow(&ctx->big, &ctx->big_cap, (size_t)pl.lanes * pl.S * kBigPerSlot, false));
         CK(ctx, grow_fill(&ctx->big_count, &ctx->big_count_cap, (size_t)kLanes, 0));
@@ -670,7 +667,6 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             a.raster = 1;
             a.rast_tris = h_tris;
             a.pix_key = ctx->pix_key + s0 * R;
-            a.pix_cnt = ctx->pix_cnt + s0 * R;
             a.pix_cand = ctx->pix_cand + s0 * R * kPixCand;
             a.big_cap = S * kBigPerSlot;
             a.big = ctx->big + (size_t)b * a.big_cap;
@@ -947,7 +943,6 @@ void srp_destroy(srp_ctx *ctx)
     dfree(ctx->prop_done);
     dfree(ctx->amb_count);
     dfree(ctx->pix_key);
-    dfree(ctx->pix_cnt);
     dfree(ctx->pix_cand);
     dfree(ctx->big);
     dfree(ctx->big_count);
@@ -2166,7 +2161,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     double *part1;
     int *alist, *acount, *rbad;
     unsigned long long *pkey;
-    unsigned *pcnt, *pcand, *bcount, *pcnt_blk;
+    unsigned *pcand, *bcount, *pcnt_blk;
     int4 *blist;
     int2 *btlist;
     SlotDesc *sd;
@@ -2199,7 +2194,6 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &sd, (size_t)n));
     CK(ctx, dmalloc(owned, &S, (size_t)n));
     CK(ctx, dmalloc(owned, &pkey, raster ? (size_t)n * Rmax : 1));
-    CK(ctx, dmalloc(owned, &pcnt, raster ? (size_t)n * Rmax : 1));
     CK(ctx, dmalloc(owned, &pcand, raster ? (size_t)n * Rmax * kPixCand : 1));
     CK(ctx, dmalloc(owned, &blist, raster ? bcap : 1));
     CK(ctx, dmalloc(owned, &btlist, raster ? bcap : 1));
@@ -2311,7 +2305,6 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
             a.raster = 1;
             a.rast_tris = max_tris;
             a.pix_key = pkey;
-            a.pix_cnt = pcnt;
             a.pix_cand = pcand;
             a.big = blist;
             a.big_cap = (int)bcap;

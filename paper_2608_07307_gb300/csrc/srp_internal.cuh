@@ -199,9 +199,9 @@ struct TraceArgs {
     // cleared before each launch's raster passes
     int raster;
     int rast_tris;               // largest triangle count of a slot's mesh (raster grid width)
-    unsigned long long *pix_key; // [S][ray_stride] nearest certain FP32 hit: t bits << 32 | part << 24 | tl; ~0 none
-    unsigned *pix_cnt;           // [S][ray_stride] uncertain triangles of the pixel's primary ray
-    unsigned *pix_cand;          // [S][ray_stride][kPixCand] the first kPixCand of them
+    unsigned long long *pix_key; // [S][ray_stride] nearest certain FP32 hit: t bits << 32 | 7 - (uncertain
+                                 // triangles, at most kPixCand + 1) << 29 | part << 24 | tl; ~0 none
+    unsigned *pix_cand;          // [S][ray_stride][kPixCand] the first kPixCand uncertain triangles
     int4 *big;                   // [big_cap] (slot, sorted triangle, chunk column, chunk row): chunks of large
                                  // triangles that can meet them
     unsigned *big_count;         // entries claimed in big (reset by k_frame)

@@ -255,17 +255,18 @@ __device__ __forceinline__ void cswap(float &ta, int &ra, float &tb, int &rb)
 
 // One 4-wide node: slab tests of its four child boxes (lo.x, hi.x, lo.y, hi.y,
 // lo.z, hi.z in float4 0..5, one lane per child; child refs in float4 6).
-// oct[k] is 1 where the ray runs backwards along axis k: the near plane is then
+// Bit k of oct is 1 where the ray runs backwards along axis k: the near plane is then
 // the box's upper bound, so picking the float4 by address replaces the per-axis
 // min/max of the slab test.  An unused slot's box (+inf, -inf) is entered at
 // +inf and never hit.  Continues with the nearest child entered and pushes the
 // others, farthest first.  Returns the number of children entered (0: pop the
 // stack), -1 when the stack would overflow.
-__device__ __forceinline__ int node4_step(const float4 *nd, const float *inv, const float *oi, const int *oct,
+__device__ __forceinline__ int node4_step(const float4 *nd, const float *inv, const float *oi, int oct,
                                           float tlo, float thi, int &ref, int *stack, int &sp)
 {
-    float4 nx = __ldg(nd + oct[0]), fx = __ldg(nd + 1 - oct[0]), ny = __ldg(nd + 2 + oct[1]),
-           fy = __ldg(nd + 3 - oct[1]), nz = __ldg(nd + 4 + oct[2]), fz = __ldg(nd + 5 - oct[2]);
+    const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
+    float4 nx = __ldg(nd + ox), fx = __ldg(nd + 1 - ox), ny = __ldg(nd + 2 + oy),
+           fy = __ldg(nd + 3 - oy), nz = __ldg(nd + 4 + oz), fz = __ldg(nd + 5 - oz);
     int4 c = __ldg(reinterpret_cast<const int4 *>(nd + 6));
     float ta = box_enter_nf(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, inv, oi, tlo, thi);
     float tb = box_enter_nf(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, inv, oi, tlo, thi);
@@ -290,18 +291,24 @@ __device__ __forceinline__ int node4_step(const float4 *nd, const float *inv, co
 struct Ray32 {
     float o[3], d[3], inv[3], oi[3];
     float Sx, Sy, Sz;
-    int kx, ky, kz;
-    int oct[3];  // 1 where the direction component is negative
+    // bits 0-2: 1 where the direction component is negative (the ray's octant);
+    // bits 3-4, 5-6, 7-8: the axes kx, ky, kz of the watertight test (one
+    // register instead of six)
+    int code;
+    __device__ __forceinline__ int kx() const { return (code >> 3) & 3; }
+    __device__ __forceinline__ int ky() const { return (code >> 5) & 3; }
+    __device__ __forceinline__ int kz() const { return (code >> 7) & 3; }
 };
 
 __device__ __forceinline__ void ray_setup(Ray32 &r)
 {
+    int oct = 0;
     for (int k = 0; k < 3; k++) {
         float dk = r.d[k];
         float ds = fabsf(dk) < 1e-20f ? copysignf(1e-20f, dk) : dk;
         r.inv[k] = 1.0f / ds;
         r.oi[k] = r.o[k] * r.inv[k];
-        r.oct[k] = r.inv[k] < 0.f ? 1 : 0;
+        oct |= (r.inv[k] < 0.f ? 1 : 0) << k;
     }
     float ax = fabsf(r.d[0]), ay = fabsf(r.d[1]), az = fabsf(r.d[2]);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
@@ -309,7 +316,7 @@ __device__ __forceinline__ void ray_setup(Ray32 &r)
     int ky = kx == 2 ? 0 : kx + 1;
     float dz = pick(r.d[0], r.d[1], r.d[2], kz);
     if (dz < 0.f) { int t = kx; kx = ky; ky = t; }
-    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.code = oct | (kx << 3) | (ky << 5) | (kz << 7);
     r.Sx = pick(r.d[0], r.d[1], r.d[2], kx) / dz;
     r.Sy = pick(r.d[0], r.d[1], r.d[2], ky) / dz;
     r.Sz = 1.0f / dz;
@@ -367,17 +374,22 @@ struct Counts {
 };
 
 // Triangles whose FP32 decision was not certain, for the FP64 resolution at the
-// end of the segment (part << 24 | part-local triangle).
+// end of the segment (part << 24 | part-local triangle).  The list lives in
+// shared memory, one column per thread (entry c at id[c * kLaneStride]) of a
+// block-wide array: a per-thread array indexed at run time would sit in local
+// memory, and its traffic would compete with the node fetches in L1.
 constexpr int kCand = 8;
+constexpr int kLaneStride = 128;  // threads of the kernels that keep per-thread columns in shared memory
 struct Cands {
     int n;
-    int id[kCand];
+    int *id;
 };
 
 __device__ __forceinline__ bool push_cand(Cands &c, int p, int tl)
 {
     if (c.n >= kCand) return false;
-    c.id[c.n++] = (p << 24) | tl;
+    c.id[c.n * kLaneStride] = (p << 24) | tl;
+    c.n++;
     return true;
 }
 
@@ -422,9 +434,10 @@ __device__ __forceinline__ bool classify(float U, float V, float W, float eU, fl
 // then goes to the FP64 re-trace).  A secondary ray leaving the plane of its
 // origin's coplanar group passes the group's subtree (ref gskip of part gpart)
 // by: none of its triangles can be hit beyond the origin.
-template <bool COUNT>
-__device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float uc, float vc, float tlo, int skip,
-                          int gpart, int gskip, float delta, float tau, Best32 &best, Counts &cn, Cands &cd)
+template <bool COUNT, bool PRIMARY>
+__device__ __forceinline__ bool nearest32(const TraceCtx &B, const Ray32 &r, float uc, float vc, float tlo, int skip,
+                                          int gpart, int gskip, float delta, float tau, Best32 &best, Counts &cn,
+                                          Cands &cd)
 {
     best.t = INFINITY;
     best.part = -1;
@@ -460,7 +473,7 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
             if (++iters > pv.limit) { clean = false; cn.flags |= kFlagStack; break; }
             if (ref >= 0) {
                 if (ref != gs) {
-                    const int n = node4_step(pv.node + (size_t)ref * kNode4, r.inv, r.oi, r.oct, tlo - tau,
+                    const int n = node4_step(pv.node + (size_t)ref * kNode4, r.inv, r.oi, r.code, tlo - tau,
                                              best.t + tau, ref, stack, sp);
                     if (COUNT) { n_nodes++; n_boxes += 4; }
                     if (n < 0) { clean = false; cn.flags |= kFlagStack; break; }
@@ -469,7 +482,7 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
             } else {
                 int tl = ~ref;
                 if (COUNT) n_tris++;
-                if (primary) {
+                if (PRIMARY) {
                     int4 vi = __ldg(pv.v4 + tl);
                     const Prim32 q = prim_test(__ldg(B.vview + vi.x), __ldg(B.vview + vi.y), __ldg(B.vview + vi.z), uc,
                                                vc, delta, B.w0_32);
@@ -485,10 +498,10 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
                         float A0 = a.x - r.o[0], A1 = a.y - r.o[1], A2 = a.z - r.o[2];
                         float B0 = b.x - r.o[0], B1 = b.y - r.o[1], B2 = b.z - r.o[2];
                         float C0 = c.x - r.o[0], C1 = c.y - r.o[1], C2 = c.z - r.o[2];
-                        float Akz = pick(A0, A1, A2, r.kz), Bkz = pick(B0, B1, B2, r.kz), Ckz = pick(C0, C1, C2, r.kz);
-                        float Ax = fmaf(-r.Sx, Akz, pick(A0, A1, A2, r.kx)), Ay = fmaf(-r.Sy, Akz, pick(A0, A1, A2, r.ky));
-                        float Bx = fmaf(-r.Sx, Bkz, pick(B0, B1, B2, r.kx)), By = fmaf(-r.Sy, Bkz, pick(B0, B1, B2, r.ky));
-                        float Cx = fmaf(-r.Sx, Ckz, pick(C0, C1, C2, r.kx)), Cy = fmaf(-r.Sy, Ckz, pick(C0, C1, C2, r.ky));
+                        float Akz = pick(A0, A1, A2, r.kz()), Bkz = pick(B0, B1, B2, r.kz()), Ckz = pick(C0, C1, C2, r.kz());
+                        float Ax = fmaf(-r.Sx, Akz, pick(A0, A1, A2, r.kx())), Ay = fmaf(-r.Sy, Akz, pick(A0, A1, A2, r.ky()));
+                        float Bx = fmaf(-r.Sx, Bkz, pick(B0, B1, B2, r.kx())), By = fmaf(-r.Sy, Bkz, pick(B0, B1, B2, r.ky()));
+                        float Cx = fmaf(-r.Sx, Ckz, pick(C0, C1, C2, r.kx())), Cy = fmaf(-r.Sy, Ckz, pick(C0, C1, C2, r.ky()));
                         float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
                         float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
                         float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -513,6 +526,27 @@ __device__ bool nearest32(const TraceCtx &B, const Ray32 &r, bool primary, float
     }
     if (COUNT) { cn.nodes += n_nodes; cn.tris += n_tris; cn.boxes += n_boxes; }
     return clean;
+}
+
+// The primary segment's traversal (a pixel whose raster result is not usable:
+// too many uncertain candidates, or rasterisation off): rare, so kept out of
+// line, where its registers do not weigh on the rest of the trace kernel.
+struct Near32 {
+    Best32 b;
+    Counts cn;
+    int cand_n;
+    int ok;
+};
+
+template <bool COUNT>
+__device__ __noinline__ Near32 nearest32_primary(const TraceCtx &B, const Ray32 r, float uc, float vc, float delta,
+                                                 float tau, Counts cn, Cands cd)
+{
+    Near32 o;
+    o.ok = nearest32<COUNT, true>(B, r, uc, vc, 0.0f, -1, -1, kEmptyChild, delta, tau, o.b, cn, cd) ? 1 : 0;
+    o.cn = cn;
+    o.cand_n = cd.n;
+    return o;
 }
 
 __device__ inline double warp_sum(double x)
@@ -550,8 +584,8 @@ __device__ __forceinline__ int slot_of_block(const SlotDesc *sd, int S, int g)
     return lo;
 }
 
-__device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, int seg, const int *hpt, int skip,
-                                       const Cands &cd, Best32 &best);
+__device__ __noinline__ Best32 resolve64(const TraceCtx &B, int N, int i, int j, int seg, const int *hpt, int skip,
+                                         Cands cd, Best32 best);
 
 // One warp per block, one 32-pixel tile (tile_w x 32 / tile_w) per block; the
 // blocks of all slots form one flat grid.  Latency bound: 32 warps per SM at
@@ -646,12 +680,25 @@ __device__ __forceinline__ float rast_bound(const RastView &V, float4 a, float4 
     return (V.delta * (2.0f * xm + 2.0f * ym) + 4.0f * kU * (2.0f * xm * ym)) * 1.001f;
 }
 
+// The pixel key (one 64-bit word per pixel): the nearest certain hit's depth
+// bits in the high word; in the low word a 3-bit field (bits 29-31) holding 7
+// minus the number of uncertain candidates pass 1 listed (saturating at 4:
+// more than kPixCand, the ray then traverses) and the hit as part << 24 |
+// part-local triangle (bits 0-27).  All ones: no certain hit, no candidate.
+// Pass 0 writes its keys with the field at 7, so the 64-bit minimum orders by
+// depth, then triangle; pass 1 only lowers the field.
+static_assert(kMaxParts <= 16, "the pixel key holds the part in 4 bits");
+constexpr unsigned kKeyId = 0x0fffffffu;
+constexpr unsigned kKeyField = 29;
+__device__ __forceinline__ bool key_none(unsigned long long k) { return (unsigned)(k >> 32) == 0xffffffffu; }
+__device__ __forceinline__ unsigned key_cands(unsigned long long k) { return 7u - ((unsigned)(k >> kKeyField) & 7u); }
+
 // One (triangle, pixel centre) pair.  E bounds the pair's error bounds: a
 // decision certain against E is certain against them, so the exact bounds are
 // formed only near an edge; the decisions are those of prim_test.
 template <int PASS>
-__device__ __forceinline__ void rast_pixel(const RastView &V, unsigned long long *key, unsigned *cnt, unsigned *cand,
-                                           int i, int j, float4 a, float4 b, float4 c, unsigned id, float E)
+__device__ __forceinline__ void rast_pixel(const RastView &V, unsigned long long *key, unsigned *cand, int i, int j,
+                                           float4 a, float4 b, float4 c, unsigned id, float E)
 {
     const float uc = fmaf((float)i + 0.5f, V.du32, V.umin32);
     const float vc = fmaf((float)j + 0.5f, V.dv32, V.vmin32);
@@ -669,17 +716,33 @@ __device__ __forceinline__ void rast_pixel(const RastView &V, unsigned long long
     const size_t px = (size_t)i * V.N + j;
     if (PASS == 0) {
         // primary rays start at the window (tlo = 0); t > 0 orders as its bits
-        if (!unsure && t > 0.0f) atomicMin(key + px, ((unsigned long long)__float_as_uint(t) << 32) | id);
+        if (!unsure && t > 0.0f)
+            atomicMin(key + px, ((unsigned long long)__float_as_uint(t) << 32) | (7u << kKeyField) | id);
         return;
     }
+    // (other pass-1 threads may lower this key's candidate field meanwhile:
+    // depth and triangle stay as pass 0 left them)
     const unsigned long long k = key[px];
-    const float tmin = k == ~0ull ? INFINITY : __uint_as_float((unsigned)(k >> 32));
+    const float tmin = key_none(k) ? INFINITY : __uint_as_float((unsigned)(k >> 32));
     bool take;
     if (unsure) take = !(fabsf(q.det) > 1e-30f && (t > tmin + V.tau || t < -V.tau));
-    else take = fabsf(t) <= V.tau || ((unsigned)k != id && fabsf(t - tmin) <= V.tau);
+    else take = fabsf(t) <= V.tau || (((unsigned)k & kKeyId) != id && fabsf(t - tmin) <= V.tau);
     if (take) {
-        const unsigned n = atomicAdd(cnt + px, 1u);
-        if (n < (unsigned)kPixCand) cand[px * kPixCand + n] = id;
+        // claim a candidate slot by lowering the key's field; every failed
+        // compare-and-swap means another thread's succeeded, and the loop is
+        // bounded all the same: past the bound the field is cleared, which
+        // sends the ray to the traversal (always correct)
+        unsigned long long old = k;
+        int slot = kPixCand;
+        for (int it = 0; it < 64; it++) {
+            const unsigned f = (unsigned)(old >> kKeyField) & 7u;
+            if (7u - f >= (unsigned)kPixCand + 1u) break;  // saturated: the ray traverses
+            const unsigned long long seen = atomicCAS(key + px, old, old - (1ull << kKeyField));
+            if (seen == old) { slot = (int)(7u - f); break; }
+            old = seen;
+            if (it == 63) atomicAnd(key + px, ~(7ull << kKeyField));
+        }
+        if (slot < kPixCand) cand[px * kPixCand + slot] = id;
     }
 }
 
@@ -731,7 +794,7 @@ __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
     const float eb = rast_bound(V, A, B, C, i0, i1, j0, j1);
     for (int i = i0; i <= i1; i++)
         for (int j = j0; j <= j1; j++)
-            rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id, eb);
+            rast_pixel<PASS>(V, a.pix_key + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id, eb);
 }
 
 // Warp per listed large triangle: its 16 x 16-pixel chunks that can meet it,
@@ -796,18 +859,23 @@ __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
         for (int q = (int)lane; q < kRastChunk * kRastChunk; q += 32) {
             const int i = ib + q / kRastChunk, j = jb + q % kRastChunk;
             if (i <= ie && j <= je)
-                rast_pixel<PASS>(V, a.pix_key + off, a.pix_cnt + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id,
-                                 eb);
+                rast_pixel<PASS>(V, a.pix_key + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id, eb);
         }
     }
 }
 
 // A block is kTraceWarps warps over consecutive tiles of one slot, sharing
 // one copy of the slot's context; a warp past the slot's last tile idles.
-template <bool COUNT>
+template <bool COUNT, bool HITS>
 __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_trace(TraceArgs a)
 {
+    static_assert(kTileRays * kTraceWarps == kLaneStride, "per-thread shared columns assume 128 threads");
     __shared__ TraceCtx B;
+    // per-thread columns (entry k of thread x at [k * kLaneStride + x]): the
+    // candidates of the FP64 resolution, and each segment's hit as (part,
+    // triangle) for the FP64 replay of the specular chain and the hit record
+    __shared__ int s_cand[kCand * kLaneStride];
+    __shared__ int s_hpt[(kMaxBounces + 1) * kLaneStride];
     const int s = slot_of_block(a.sd, a.n_slots, blockIdx.x);
     const SlotDesc &D = a.sd[s];
     const int tile_id = (blockIdx.x - D.tile0) * kTraceWarps + (int)(threadIdx.x >> 5);
@@ -823,12 +891,15 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
     const int tw = D.tile_w, lw = __ffs(tw) - 1;
     const int i = (tile_id % D.tiles_x) * tw + (lane & (tw - 1));
     const int j = (tile_id / D.tiles_x) * (kTileRays >> lw) + (lane >> lw);
-    // per-ray results: force / torque in FP32 (at most 1 + bounces terms), counts as integers
+    // per-ray results: force / torque in FP32 (at most 1 + bounces terms); counts
+    // as scalars (a hand-off flag, the segments traced, a bit per segment hit)
     float fac[6] = {0, 0, 0, 0, 0, 0};
-    unsigned cnt[kPart] = {0};
+    unsigned c_handoff = 0u, c_segs = 0u, c_hitbits = 0u;
     bool handoff = false;
     int flags = 0;
     const int ray = i * N + j;
+    int *hpt = s_hpt + threadIdx.x;
+    Counts cn = {0u, 0u, 0u, {0u, 0u, 0u, 0u}, 0};
     if (i < N && j < N) {
         Ray32 r;
         for (int k = 0; k < 3; k++) r.d[k] = B.dir[k];
@@ -837,12 +908,12 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
         float wgt = 1.0f;
         int skip = -1, gpart = -1, gskip = kEmptyChild;
         float acc[6] = {0, 0, 0, 0, 0, 0};
-        int hits[kMaxBounces + 1], hpt[kMaxBounces + 1];
-        for (int k = 0; k <= kMaxBounces; k++) hits[k] = -1;
+        unsigned hitbits = 0u;
         bool clean = true;
         int nseg_done = 0;
         Cands cd;
-        Counts cn = {0u, 0u, 0u, {0u, 0u, 0u, 0u}, 0};
+        cd.n = 0;
+        cd.id = s_cand + threadIdx.x;
         float delta = B.delta_p, tau = B.tau_p;
         // rasterised primary visibility of this pixel
         bool rast = false;
@@ -850,11 +921,11 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
         if (a.raster) {
             const size_t px = (size_t)s * a.ray_stride + ray;
             pk = __ldcs(a.pix_key + px);
-            const unsigned pn = __ldcs(a.pix_cnt + px);
+            const unsigned pn = key_cands(pk);
             rast = pn <= (unsigned)kPixCand && !a.rast_bad[s];
             if (rast) {
                 cd.n = (int)pn;
-                for (int c = 0; c < (int)pn; c++) cd.id[c] = (int)a.pix_cand[px * kPixCand + c];
+                for (int c = 0; c < (int)pn; c++) cd.id[c * kLaneStride] = (int)a.pix_cand[px * kPixCand + c];
                 if (COUNT) cn.why[0] += pn;
             }
         }
@@ -870,8 +941,8 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
                 h.t = INFINITY;
                 h.part = -1;
                 h.tl = -1;
-                if (pk != ~0ull) {
-                    const unsigned id = (unsigned)pk;
+                if (!key_none(pk)) {
+                    const unsigned id = (unsigned)pk & kKeyId;
                     h.part = (int)(id >> 24);
                     h.tl = (int)(id & 0xffffffu);
                     const int4 vi = __ldg(B.part[h.part].v4 + h.tl);
@@ -882,18 +953,30 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
                     h.b1 = q.V * id32;
                     h.b2 = q.W * id32;
                 }
-            } else if (!nearest32<COUNT>(B, r, seg == 0, uc, vc, tlo, skip, gpart, gskip, delta, tau, h, cn, cd)) {
-                clean = false;
-                break;
+            } else {
+                bool ok;
+                if (seg == 0) {
+                    const Near32 o = nearest32_primary<COUNT>(B, r, uc, vc, delta, tau, cn, cd);
+                    h = o.b;
+                    cn = o.cn;
+                    cd.n = o.cand_n;
+                    ok = o.ok != 0;
+                } else {
+                    ok = nearest32<COUNT, false>(B, r, uc, vc, tlo, skip, gpart, gskip, delta, tau, h, cn, cd);
+                }
+                if (!ok) {
+                    clean = false;
+                    break;
+                }
             }
-            if (cd.n > 0) resolve64(B, N, i, j, seg, hpt, skip, cd, h);  // rare: settle in FP64
+            if (cd.n > 0) h = resolve64(B, N, i, j, seg, hpt, skip, cd, h);  // rare: settle in FP64
             if (h.part < 0) break;
-            hpt[seg] = (h.part << 24) | h.tl;
+            hpt[seg * kLaneStride] = (h.part << 24) | h.tl;
             const float4 *tr = B.part[h.part].tri + (size_t)h.tl * 3;
             float4 a0 = __ldg(tr), a1 = __ldg(tr + 1), a2 = __ldg(tr + 2);
             int orig = __float_as_int(a0.w);
             unsigned mt = __float_as_uint(a1.w);
-            hits[seg] = orig;
+            hitbits |= 1u << seg;
             float e1[3] = {a1.x - a0.x, a1.y - a0.y, a1.z - a0.z};
             float e2[3] = {a2.x - a0.x, a2.y - a0.y, a2.z - a0.z};
             float n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -938,20 +1021,22 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
         flags = cn.flags;
         if (clean) {
             for (int k = 0; k < 6; k++) fac[k] = acc[k];
-            cnt[7] = nseg_done;
-#pragma unroll
-            for (int k = 0; k <= kMaxBounces; k++) cnt[8 + k] = (k < nseg && hits[k] >= 0) ? 1u : 0u;
-            if (a.hits) {
+            c_segs = nseg_done;
+            c_hitbits = hitbits;
+            if (HITS) {
                 int32_t *hq = a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride;
-                for (int k = 0; k < nseg; k++) hq[k] = hits[k];
+                for (int k = 0; k < nseg; k++) {
+                    int o = -1;
+                    if ((hitbits >> k) & 1u) {
+                        const int hk = hpt[k * kLaneStride];
+                        o = __float_as_int(__ldg(B.part[hk >> 24].tri + (size_t)(hk & 0xffffff) * 3).w);
+                    }
+                    hq[k] = o;
+                }
             }
         } else {
             handoff = true;
-            cnt[6] = 1;
-        }
-        if (COUNT) {
-            cnt[13] = cn.nodes; cnt[14] = cn.tris; cnt[15] = cn.boxes;
-            for (int k = 0; k < 4; k++) cnt[16 + k] = cn.why[k];
+            c_handoff = 1u;
         }
     }
     // tile-ordered list of the rays handed to the FP64 path
@@ -966,9 +1051,19 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) a.partials[tile * 6 + k] = x;
     }
-    // counts 0..6 always; the traversal counters only in the counting variant
+    // counts 0..6 always (hand-offs, segments, hits per segment level); the
+    // traversal counters only in the counting variant
+#pragma unroll
     for (int k = 0; k < (COUNT ? kCnt : 7); k++) {
-        const unsigned x = __reduce_add_sync(0xffffffffu, cnt[6 + k]);
+        unsigned v;
+        if (k == 0) v = c_handoff;
+        else if (k == 1) v = c_segs;
+        else if (k <= 2 + kMaxBounces) v = (c_hitbits >> (k - 2)) & 1u;
+        else if (k == 7) v = cn.nodes;
+        else if (k == 8) v = cn.tris;
+        else if (k == 9) v = cn.boxes;
+        else v = cn.why[k - 10];
+        const unsigned x = __reduce_add_sync(0xffffffffu, v);
         if (lane == 0) a.pcounts[tile * kCnt + k] = x;
     }
     int fl = __reduce_or_sync(0xffffffffu, flags);
@@ -1038,8 +1133,9 @@ __device__ __forceinline__ void wt64(const Ray64 &r, const double *v, double &U,
 // is the FP64 chain through the earlier segments' hit triangles, tested with
 // the FP64 watertight test.  FP64 is slow on this GPU: no square roots, one
 // division per candidate, barycentric weights for the winner only.
-__device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, int seg, const int *hpt, int skip,
-                                       const Cands &cd, Best32 &best)
+// hpt: this thread's column of the block's hit records (segment s at hpt[s * kLaneStride]).
+__device__ __noinline__ Best32 resolve64(const TraceCtx &B, int N, int i, int j, int seg, const int *hpt, int skip,
+                                         Cands cd, Best32 best)
 {
     double bt = INFINITY, bU = 0.0, bV = 0.0, bW = 0.0;
     int bp = -1, btl = -1, bo = 0x7fffffff;
@@ -1053,7 +1149,8 @@ __device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, i
         double v[9];
         for (int s = 0; s < seg; s++) {
             // hit point on the plane of the segment's triangle, then the specular direction
-            tri_v64(B, hpt[s] >> 24, hpt[s] & 0xffffff, v);
+            const int hs = hpt[s * kLaneStride];
+            tri_v64(B, hs >> 24, hs & 0xffffff, v);
             double e1[3], e2[3], m[3], ao[3];
             for (int k = 0; k < 3; k++) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; ao[k] = v[k] - r.o[k]; }
             m[0] = e1[1] * e2[2] - e1[2] * e2[1];
@@ -1069,7 +1166,7 @@ __device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, i
     }
     for (int c = 0; c <= cd.n; c++) {
         int p, tl;
-        if (c < cd.n) { p = cd.id[c] >> 24; tl = cd.id[c] & 0xffffff; }
+        if (c < cd.n) { const int id = cd.id[c * kLaneStride]; p = id >> 24; tl = id & 0xffffff; }
         else if (best.part >= 0) { p = best.part; tl = best.tl; }
         else break;
         const PartView &pv = B.part[p];
@@ -1103,6 +1200,7 @@ __device__ __noinline__ void resolve64(const TraceCtx &B, int N, int i, int j, i
     best.tl = btl;
     best.b1 = bp >= 0 ? (float)(bV / bU) : 0.f;
     best.b2 = bp >= 0 ? (float)(bW / bU) : 0.f;
+    return best;
 }
 
 // True when the FP32 world-frame test shows the triangle certainly misses the
@@ -1114,10 +1212,10 @@ __device__ __forceinline__ bool outside32(const Ray32 &r, float4 a, float4 b, fl
     float A0 = a.x - r.o[0], A1 = a.y - r.o[1], A2 = a.z - r.o[2];
     float B0 = b.x - r.o[0], B1 = b.y - r.o[1], B2 = b.z - r.o[2];
     float C0 = c.x - r.o[0], C1 = c.y - r.o[1], C2 = c.z - r.o[2];
-    float Akz = pick(A0, A1, A2, r.kz), Bkz = pick(B0, B1, B2, r.kz), Ckz = pick(C0, C1, C2, r.kz);
-    float Ax = fmaf(-r.Sx, Akz, pick(A0, A1, A2, r.kx)), Ay = fmaf(-r.Sy, Akz, pick(A0, A1, A2, r.ky));
-    float Bx = fmaf(-r.Sx, Bkz, pick(B0, B1, B2, r.kx)), By = fmaf(-r.Sy, Bkz, pick(B0, B1, B2, r.ky));
-    float Cx = fmaf(-r.Sx, Ckz, pick(C0, C1, C2, r.kx)), Cy = fmaf(-r.Sy, Ckz, pick(C0, C1, C2, r.ky));
+    float Akz = pick(A0, A1, A2, r.kz()), Bkz = pick(B0, B1, B2, r.kz()), Ckz = pick(C0, C1, C2, r.kz());
+    float Ax = fmaf(-r.Sx, Akz, pick(A0, A1, A2, r.kx())), Ay = fmaf(-r.Sy, Akz, pick(A0, A1, A2, r.ky()));
+    float Bx = fmaf(-r.Sx, Bkz, pick(B0, B1, B2, r.kx())), By = fmaf(-r.Sy, Bkz, pick(B0, B1, B2, r.ky()));
+    float Cx = fmaf(-r.Sx, Ckz, pick(C0, C1, C2, r.kx())), Cy = fmaf(-r.Sy, Ckz, pick(C0, C1, C2, r.ky()));
     float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
     float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
     float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -1158,7 +1256,7 @@ __device__ void nearest64(const TraceCtx &B, const Ray64 &r, double tlo, int ski
         while (true) {
             if (++iters > pv.limit) { flags |= kFlagStack; break; }
             if (ref >= 0) {
-                const int n = node4_step(pv.node + (size_t)ref * kNode4, q.inv, q.oi, q.oct, (float)tlo - slack,
+                const int n = node4_step(pv.node + (size_t)ref * kNode4, q.inv, q.oi, q.code, (float)tlo - slack,
                                          (float)bt + slack, ref, stack, sp);
                 if (n < 0) { flags |= kFlagStack; break; }
                 if (n > 0) continue;
@@ -1308,7 +1406,7 @@ __device__ void settle64(const TraceCtx &B, const Ray64 &r, double tlo, int skip
     int bo = 0x7fffffff;
     for (int c = 0; c <= cd.n; c++) {
         int p, tl;
-        if (c < cd.n) { p = cd.id[c] >> 24; tl = cd.id[c] & 0xffffff; }
+        if (c < cd.n) { const int id = cd.id[c * kLaneStride]; p = id >> 24; tl = id & 0xffffff; }
         else if (best.part >= 0) { p = best.part; tl = best.tl; }
         else break;
         const int orig = __float_as_int(__ldg(B.part[p].tri + (size_t)tl * 3).w);
@@ -1331,7 +1429,7 @@ __device__ void settle64(const TraceCtx &B, const Ray64 &r, double tlo, int skip
 // about c_ref are added to acc.
 __device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long long seed, unsigned long long c,
                                                const double *x, const double *nf, int src, double wd, double *acc,
-                                               int &flags)
+                                               int &flags, int *cand_col)
 {
     Ray64 r;
     diffuse_dir(seed, c, nf, r.d);
@@ -1348,7 +1446,9 @@ __device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long 
         Best32 b;
         Counts cn = {0u, 0u, 0u, {0u, 0u, 0u, 0u}, 0};
         Cands cd;
-        if (nearest32<false>(B, q, false, 0.0f, 0.0f, B.eps32, src, -1, kEmptyChild, delta, tau, b, cn, cd)) {
+        cd.n = 0;
+        cd.id = cand_col;
+        if (nearest32<false, false>(B, q, 0.0f, 0.0f, B.eps32, src, -1, kEmptyChild, delta, tau, b, cn, cd)) {
             settle64(B, r, B.eps, src, cd, b, t, p, tl);
         } else {
             int orig;
@@ -1387,10 +1487,11 @@ __device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long 
 // lit side's normal, is traced with the FP64 traversal and deposits the
 // per-hit law at its hit.  Sums per block in a fixed order: the result is
 // reproducible.
-__global__ void __launch_bounds__(128) k_diffuse(TraceArgs a)
+__global__ void __launch_bounds__(kLaneStride) k_diffuse(TraceArgs a)
 {
     __shared__ TraceCtx B;
     __shared__ double red[4][6];
+    __shared__ int s_cand[kCand * kLaneStride];  // per-thread candidate columns (see Cands)
     const int s = blockIdx.y;
     load_ctx(B, a, s);
     __syncthreads();
@@ -1437,7 +1538,8 @@ __global__ void __launch_bounds__(128) k_diffuse(TraceArgs a)
                     const unsigned long long c =
                         ((unsigned long long)ray * (unsigned long long)nseg + (unsigned long long)k) *
                             (unsigned long long)K + (unsigned long long)q;
-                    diffuse_sample(B, (unsigned long long)a.diffuse_seed, c, x, nf, h, wgt * rd / K, acc, flags);
+                    diffuse_sample(B, (unsigned long long)a.diffuse_seed, c, x, nf, h, wgt * rd / K, acc, flags,
+                                   s_cand + threadIdx.x);
                 }
                 wgt *= rs;
                 if (wgt == 0.0) break;
@@ -1671,7 +1773,6 @@ cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
         // cleared pixel buffers of the launch's slots
         const size_t px = (size_t)S * a.ray_stride;
         cudaError_t e = cudaMemsetAsync(a.pix_key, 0xff, sizeof(unsigned long long) * px, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(a.pix_cnt, 0, sizeof(unsigned) * px, st);
         if (e != cudaSuccess) return e;
         dim3 grid((a.rast_tris + 127) / 128, S);
         k_raster<0><<<grid, 128, 0, st>>>(a);
@@ -1687,8 +1788,16 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
 {
     (void)S;
     if (a.n_tiles <= 0) return cudaSuccess;
-    if (a.count) k_trace<true><<<a.n_tiles, kTileRays * kTraceWarps, 0, st>>>(a);
-    else k_trace<false><<<a.n_tiles, kTileRays * kTraceWarps, 0, st>>>(a);
+    // the hit records and the traversal counters are separate kernel variants:
+    // code a launch never runs still costs registers in the others
+    const dim3 g(a.n_tiles), b(kTileRays * kTraceWarps);
+    if (a.count) {
+        if (a.hits) k_trace<true, true><<<g, b, 0, st>>>(a);
+        else k_trace<true, false><<<g, b, 0, st>>>(a);
+    } else {
+        if (a.hits) k_trace<false, true><<<g, b, 0, st>>>(a);
+        else k_trace<false, false><<<g, b, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -1697,7 +1806,7 @@ cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, d
 {
     k_reduce1<<<dim3(kRed1, S), 256, 0, st>>>(a);
     // diffuse secondaries after the FP64 re-trace (which records the hits of the rays it takes)
-    if (a.n_diffuse > 0) k_diffuse<<<dim3(kDiffBlocks, S), 128, 0, st>>>(a);
+    if (a.n_diffuse > 0) k_diffuse<<<dim3(kDiffBlocks, S), kLaneStride, 0, st>>>(a);
     k_reduce<<<S, 256, 0, st>>>(a, eval0, force, torque, err_flags, stats_accum);
     return cudaGetLastError();
 }
