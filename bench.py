@@ -123,6 +123,8 @@ def parse():
     p.add_argument("--grad-arc-steps", type=int, default=10000,
                    help="RK4 steps of the timed adjoint arc (the differentiated workload's arc: 10000 at 60 s)")
     p.add_argument("--no-boxwing", action="store_true", help="skip the box-wing (16 triangles, 256 directions) form")
+    p.add_argument("--queue", action="store_true",
+                   help="headline evaluations with the work-queue schedule (second raster pass + trace in one launch)")
     p.add_argument("--no-precision", action="store_true", help="skip the 50k-triangle precision form")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     return p.parse_args()
@@ -733,11 +735,12 @@ def run_native(a):
 
     # the library's autotuner picks the trace tile shape for this (mesh, N, bounces)
     tile_w, tile_ms = ctx.autotune(mid, a.N, a.bounces)
+    qf = srp.EVAL_QUEUE if a.queue else 0
     with torch.cuda.stream(stream):
         for k in range(a.warmup):
-            ctx.eval_batch(mid, batch(k), N=a.N, bounces=a.bounces, out=(F, T))
+            ctx.eval_batch(mid, batch(k), N=a.N, bounces=a.bounces, out=(F, T), flags=qf)
         # traversal counters of one step (separate counting kernel, not timed)
-        ctx.eval_batch(mid, batch(0), N=a.N, bounces=a.bounces, out=(F, T), count=True)
+        ctx.eval_batch(mid, batch(0), N=a.N, bounces=a.bounces, out=(F, T), count=True, flags=qf)
         cnt = ctx.eval_stats()
         stream.synchronize()
         barrier()
@@ -749,7 +752,7 @@ def run_native(a):
             flush.zero_()
             stream.synchronize()
             ev[k][0].record(stream)
-            ctx.eval_batch(mid, batch(a.warmup + k), N=a.N, bounces=a.bounces, out=(F, T))
+            ctx.eval_batch(mid, batch(a.warmup + k), N=a.N, bounces=a.bounces, out=(F, T), flags=qf)
             ev[k][1].record(stream)
             st = ctx.eval_stats()
             launches += st["launches"]; trace_launches += st["trace_launches"]
@@ -770,7 +773,7 @@ def run_native(a):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             ctx.eval_batch(mid, batch(a.warmup + k), N=a.N, bounces=a.bounces, out=(F, T), timing=True,
-                           flags=srp.EVAL_SERIAL)
+                           flags=srp.EVAL_SERIAL | qf)
             e1.record(stream)
             stream.synchronize()
             ph_ms += e0.elapsed_time(e1)
@@ -788,7 +791,7 @@ def run_native(a):
             flush.zero_()
             stream.synchronize()
             t0 = time.perf_counter()
-            ctx.eval_batch(mid, hd, N=a.N, bounces=a.bounces, out=(hF, hT))
+            ctx.eval_batch(mid, hd, N=a.N, bounces=a.bounces, out=(hF, hT), flags=qf)
             e2e_s += time.perf_counter() - t0
     def reduce_max(xs):
         import torch.distributed as dist

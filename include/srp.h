@@ -151,6 +151,19 @@ typedef struct {
  * them), e.g. the trace kernel's duration per launch for a roofline.  Results
  * are the same bits either way. */
 #define SRP_EVAL_SERIAL 32
+/* Run the raster's second pass and the trace of each chunk as one persistent
+ * launch over a device-side work queue: items (second pass over 128 small
+ * triangles, over 4 chunks of large triangles, a block of 4 trace tiles) are
+ * handed out in that order, and a trace item waits until its slot's second
+ * pass is complete.  Every wait is bounded (2 s of device time); a wait that
+ * gives up makes the call return SRP_ERR_TIMEOUT (its tiles contribute
+ * nothing) and leaves the context usable.  Results are the same bits as
+ * without the flag. */
+#define SRP_EVAL_QUEUE 64
+/* Test of the work queue's bounded wait: every trace item waits for a count
+ * that is never reached, with a 2 ms bound, so the call returns
+ * SRP_ERR_TIMEOUT.  Implies SRP_EVAL_QUEUE.  For tests only. */
+#define SRP_EVAL_TEST_WAIT_TIMEOUT 128
 
 /* Counters of the last srp_eval_batch call (summed over its evaluations). */
 typedef struct {

@@ -63,6 +63,8 @@ struct srp_ctx {
     // rasterised primary visibility: pixel buffers (kept cleared), per-lane chunk lists
     unsigned long long *pix_key = nullptr;
     size_t pix_key_cap = 0;
+    unsigned *qstate = nullptr;  // work-queue state, qstate_words(S) per lane
+    size_t qstate_cap = 0;
     unsigned *pix_cand = nullptr;
     size_t pix_cand_cap = 0;
     int4 *big = nullptr;
@@ -594,6 +596,8 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
         CK(ctx, grow(&ctx->bigt, &ctx->bigt_cap, (size_t)pl.lanes * pl.S * kBigPerSlot, false));
         CK(ctx, grow_fill(&ctx->bigt_count, &ctx->bigt_count_cap, (size_t)kLanes, 0));
         CK(ctx, grow_fill(&ctx->rast_bad, &ctx->rast_bad_cap, SL, 0));
+        if (prm->flags & (SRP_EVAL_QUEUE | SRP_EVAL_TEST_WAIT_TIMEOUT))
+            CK(ctx, grow(&ctx->qstate, &ctx->qstate_cap, (size_t)pl.lanes * qstate_words(pl.S), false));
     }
     // the diffuse rays replay each ray's recorded hits
     if (want_hits || adjoint || prm->n_diffuse > 0) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
@@ -612,6 +616,7 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
         d.tiles_x = tiles_x;
         d.tiles = pl.nbx;
         d.tile0 = (int)(k % pl.S) * trace_blocks(pl.nbx);
+        d.rast0 = (int)(k % pl.S) * ((m->h.n_tris + 127) / 128);
     }
     rc = upload_slots(ctx, sd);
     if (rc) return rc;
@@ -674,6 +679,12 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             a.bigt = ctx->bigt + (size_t)b * a.big_cap;
             a.bigt_count = ctx->bigt_count + b;
             a.rast_bad = ctx->rast_bad + s0;
+            if (prm->flags & (SRP_EVAL_QUEUE | SRP_EVAL_TEST_WAIT_TIMEOUT)) {
+                a.queue = 1;
+                a.wait_test = (prm->flags & SRP_EVAL_TEST_WAIT_TIMEOUT) ? 1 : 0;
+                a.n_small_items = Sc * ((h_tris + 127) / 128);
+                a.qstate = ctx->qstate + (size_t)b * qstate_words(S);
+            }
         }
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
         a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : ((adj || prm->n_diffuse > 0) ? stage : nullptr);
@@ -847,6 +858,7 @@ srp_status finish_propagate(srp_ctx *ctx, int n, const PropState *S, double *y1,
     }
     CK(ctx, cudaMemcpy(y1, yo.data(), sizeof(double) * 6 * n, cudaMemcpyDefault));
     fill_stats(ctx->last, st16);
+    if (flags & kFlagTimeout) return fail(ctx, SRP_ERR_TIMEOUT, "a work-queue wait gave up");
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
     if (out == SRP_ERR_STEP && ctx->err.empty()) fail(ctx, SRP_ERR_STEP, "a trajectory hit h_min or max_steps");
     return out;
@@ -943,6 +955,7 @@ void srp_destroy(srp_ctx *ctx)
     dfree(ctx->prop_done);
     dfree(ctx->amb_count);
     dfree(ctx->pix_key);
+    dfree(ctx->qstate);
     dfree(ctx->pix_cand);
     dfree(ctx->big);
     dfree(ctx->big_count);
@@ -1417,6 +1430,7 @@ srp_status srp_eval_batch(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *
     ctx->last.launches = launches;
     ctx->last.trace_launches = trace_launches;
     tm.collect(ctx->last);
+    if (flags & kFlagTimeout) return fail(ctx, SRP_ERR_TIMEOUT, "a work-queue wait gave up");
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
     return SRP_OK;
 }
@@ -1848,6 +1862,7 @@ srp_status srp_grad(srp_ctx *ctx, int32_t mesh_id, const srp_eval_params *prm, i
     fill_stats(ctx->last, stats);
     ctx->last.launches = launches;
     ctx->last.trace_launches = trace_launches;
+    if (flags & kFlagTimeout) return fail(ctx, SRP_ERR_TIMEOUT, "a work-queue wait gave up");
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
     return SRP_OK;
 }
@@ -2025,6 +2040,7 @@ srp_status srp_prop_grad(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
         }
     ctx->last.launches = launches;
     ctx->last.trace_launches = trace_launches;
+    if (flags & kFlagTimeout) return fail(ctx, SRP_ERR_TIMEOUT, "a work-queue wait gave up");
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
     return SRP_OK;
 }
@@ -2199,6 +2215,9 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &btlist, raster ? bcap : 1));
     CK(ctx, dmalloc(owned, &bcount, 2));
     CK(ctx, dmalloc(owned, &rbad, (size_t)n));
+    const bool queue = raster && (p->eval.flags & (SRP_EVAL_QUEUE | SRP_EVAL_TEST_WAIT_TIMEOUT));
+    unsigned *qst = nullptr;
+    CK(ctx, dmalloc(owned, &qst, queue ? qstate_words((size_t)n) : 1));
     CK(ctx, cudaMemsetAsync(bcount, 0, 2 * sizeof(unsigned), st));
     CK(ctx, cudaMemsetAsync(rbad, 0, sizeof(int) * n, st));
     double *d_sun = io, *d_dist = io + 3 * (size_t)n, *d_f = d_dist + n, *d_t = d_f + 3 * (size_t)n,
@@ -2277,11 +2296,13 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     auto capture = [&](int na) -> srp_status {
         // descriptors of the running trajectories, their tiles laid end to end
         std::vector<SlotDesc> dd(na);
-        int t0 = 0, mv = 0, md = 0;
+        int t0 = 0, r0 = 0, mv = 0, md = 0;
         for (int k = 0; k < na; k++) {
             dd[k] = desc[act[k]];
             dd[k].tile0 = t0;
             t0 += trace_blocks(dd[k].tiles);
+            dd[k].rast0 = r0;
+            r0 += (mk[act[k]]->h.n_tris + 127) / 128;
             mv = std::max(mv, mk[act[k]]->h.n_verts);
             md = std::max(md, mk[act[k]]->h.n_dyn_tris);
         }
@@ -2312,6 +2333,12 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
             a.bigt = btlist;
             a.bigt_count = bcount + 1;
             a.rast_bad = rbad;
+            if (queue) {
+                a.queue = 1;
+                a.wait_test = (p->eval.flags & SRP_EVAL_TEST_WAIT_TIMEOUT) ? 1 : 0;
+                a.n_small_items = r0;
+                a.qstate = qst;
+            }
         }
         cudaGraph_t graph = nullptr;
         CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -2407,6 +2434,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, cudaMemcpy(y1, yo.data(), sizeof(double) * 6 * n, cudaMemcpyDefault));
     ctx->last.launches = launches;
     ctx->last.trace_launches = trace_launches;
+    if (flags & kFlagTimeout) return fail(ctx, SRP_ERR_TIMEOUT, "a work-queue wait gave up");
     if (flags & kFlagStack) return fail(ctx, SRP_ERR_STACK, "traversal stack bound reached");
     if (out) return fail(ctx, SRP_ERR_STEP, "a trajectory hit h_min or max_steps");
     (void)graphs;

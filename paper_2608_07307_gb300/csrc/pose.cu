@@ -50,17 +50,23 @@ __global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double 
     P.skip = dist < 0.0 ? 1 : 0;  // a negative distance asks to skip this evaluation
     if (P.skip) return;
     int np = mesh->n_parts;
+    // the parts' transforms are composed in this thread's own (L1-cached) copy
+    // and stored to the slot's pose as they are done: a parent's transform is
+    // read back from here, not from global memory
+    double Ml[kMaxParts][9], Tl[kMaxParts][3];
     for (int p = 0; p < np; p++) {
         const PartInfo &pi = mesh->part[p];
         double th = 0.0;
-        double *M = P.M[p], *T = P.T[p];
+        double *M = Ml[p], *T = Tl[p];
         if (p == 0) {
             for (int k = 0; k < 9; k++) M[k] = (k % 4 == 0) ? 1.0 : 0.0;
             T[0] = T[1] = T[2] = 0.0;
+            for (int k = 0; k < 9; k++) P.M[p][k] = M[k];
+            for (int k = 0; k < 3; k++) P.T[p][k] = T[k];
             continue;
         }
         int q = pi.parent;
-        const double *Mq = P.M[q], *Tq = P.T[q];
+        const double *Mq = Ml[q], *Tq = Tl[q];
         // cosine and sine of the joint angle: from the tracking direction itself
         // when the limits cannot clamp it (no FP64 transcendentals), else from the angle
         double cth = 1.0, sth = 0.0;
@@ -105,6 +111,8 @@ __global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double 
         double w[3];
         for (int i = 0; i < 3; i++) w[i] = pv[i] - (R[3 * i] * pv[0] + R[3 * i + 1] * pv[1] + R[3 * i + 2] * pv[2]);
         for (int i = 0; i < 3; i++) T[i] = Mq[3 * i] * w[0] + Mq[3 * i + 1] * w[1] + Mq[3 * i + 2] * w[2] + Tq[i];
+        for (int k = 0; k < 9; k++) P.M[p][k] = M[k];
+        for (int k = 0; k < 3; k++) P.T[p][k] = T[k];
     }
     // basis of the image plane around d = -s (Duff et al., JCGT 2017)
     double d[3] = {-s[0], -s[1], -s[2]};

@@ -34,6 +34,7 @@ constexpr double kStandoff = 1.0;   // ray origins start 1 m in front of the nea
 
 // Device error flags (bits of SlotPose::flags / the context error word).
 constexpr int kFlagStack = 1;
+constexpr int kFlagTimeout = 2;  // a bounded device-side wait gave up (work queue)
 
 // Rotation of the normalised scalar-first quaternion q, row-major.
 __device__ __forceinline__ void quat_matrix(const double *q, double *Q)
@@ -160,7 +161,7 @@ struct SlotDesc {
     int tile_w;            // trace tile width in pixels (4, 8, 16 or 32); height 32 / tile_w
     int tiles_x, tiles;    // trace tiles across the window, in total
     int tile0;             // first flattened trace block of the slot (blocks of kTraceWarps tiles)
-    int pad_;
+    int rast0;             // work queue: first second-pass raster item of the slot (128 triangles an item)
 };
 
 // Partial sums per block (FP64; integer counts are exact below 2^53):
@@ -214,7 +215,17 @@ struct TraceArgs {
     unsigned diffuse_seed;
     double *dpart;               // [S][kDiffBlocks][6] unscaled force / torque of the diffuse rays
     int walk_limit_test;         // 1: every BVH walk is bounded at one step (tests of the bound's error path)
+    // work queue (queue != 0): the raster's second pass and the trace as one
+    // persistent launch; qstate = [head, abort, then per slot: second-pass
+    // items done, large-triangle chunks done, chunks listed]
+    int queue;
+    int n_small_items;           // second-pass items over small triangles, all slots
+    int wait_test;               // 1: every trace item's wait targets a count never reached (timeout tests)
+    unsigned *qstate;
 };
+constexpr int kQHead = 0, kQAbort = 1, kQSlot = 2;  // qstate layout; 3 words per slot from kQSlot
+constexpr int kQueueBlocksPerSM = 8;
+inline size_t qstate_words(size_t slots) { return (size_t)kQSlot + 3 * slots; }
 constexpr int kDiffBlocks = 64;  // k_diffuse blocks per slot (fixed: the sums have a fixed order)
 constexpr int kPixCand = 2;      // uncertain triangles kept per pixel (more: the ray traverses)
 constexpr int kRastSmall = 64;   // largest pixel box one thread rasterises

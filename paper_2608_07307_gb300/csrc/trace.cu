@@ -70,6 +70,8 @@
 #include <math.h>
 #include <stddef.h>
 
+#include <algorithm>
+
 #include "srp_internal.cuh"
 
 namespace srp {
@@ -123,21 +125,49 @@ __device__ __forceinline__ double pickd(double x, double y, double z, int k) { r
 // ------------------------------------------------------------- k_frame
 __global__ void k_frame(TraceArgs a)
 {
-    int s = blockIdx.x;
-    if (threadIdx.x != 0) return;
+    const int s = blockIdx.x;
     const SlotDesc &D = a.sd[s];
     const MeshDev *m = D.mesh;
     const SlotBufs &sb = D.sb;
     const int N = D.N;
     const SlotPose &P = a.pose[s];
     TraceCtx &B = reinterpret_cast<TraceCtx *>(a.tctx)[s];
-    B.skip = P.skip;
-    if (a.raster) {
-        a.rast_bad[s] = 0;
-        if (s == 0) { *a.big_count = 0u; *a.bigt_count = 0u; }
+    if (threadIdx.x == 0) {
+        B.skip = P.skip;
+        if (a.raster) {
+            a.rast_bad[s] = 0;
+            if (s == 0) { *a.big_count = 0u; *a.bigt_count = 0u; }
+        }
+        if (a.queue) {
+            for (int k = 0; k < 3; k++) a.qstate[kQSlot + 3 * s + k] = 0u;
+            if (s == 0) { a.qstate[kQHead] = 0u; a.qstate[kQAbort] = 0u; }
+        }
+        B.n_parts = m->n_parts;
     }
-    B.n_parts = m->n_parts;
     if (P.skip) return;
+    // the parts' traversal views, a lane each
+    for (int p = threadIdx.x; p < m->n_parts; p += blockDim.x) {
+        const PartInfo &pi = m->part[p];
+        PartView &pv = B.part[p];
+        pv.root = pi.tri_count > 1 ? 0 : ~0;
+        pv.limit = a.walk_limit_test ? 1 : pi.node_count + pi.tri_count + 8;
+        pv.tri_begin = pi.tri_begin;
+        pv.vert_begin = pi.vert_begin;
+        pv.v4 = m->tri_v4 + pi.tri_begin;
+        if (pi.dynamic) {
+            pv.node = sb.node + (size_t)pi.dyn_node_off * kNode4;
+            pv.tri = sb.tri + (size_t)pi.dyn_tri_off * 3;
+            pv.v64 = sb.vert64 + (size_t)pi.dyn_vert_off * 3;
+            const float *rb = sb.root_box + (size_t)p * 6;
+            for (int k = 0; k < 6; k++) pv.box[k] = rb[k];
+        } else {
+            pv.node = m->node_static + (size_t)pi.node_begin * kNode4;
+            pv.tri = m->tri_static + (size_t)pi.tri_begin * 3;
+            pv.v64 = m->rest64 + (size_t)pi.vert_begin * 3;
+            for (int k = 0; k < 6; k++) pv.box[k] = m->root_box_static[p][k];
+        }
+    }
+    if (threadIdx.x != 0) return;
     double umin = ord_to_dbl(P.wmin_bits[0]), umax = ord_to_dbl(P.wmax_bits[0]);
     double vmin = ord_to_dbl(P.wmin_bits[1]), vmax = ord_to_dbl(P.wmax_bits[1]);
     double wmin = ord_to_dbl(P.wmin_bits[2]), wmax = ord_to_dbl(P.wmax_bits[2]);
@@ -189,27 +219,6 @@ __global__ void k_frame(TraceArgs a)
     B.tri_mat = m->tri_mat;
     B.tri_vidx = m->tri_vidx;
     B.grp = m->grp;
-    for (int p = 0; p < m->n_parts; p++) {
-        const PartInfo &pi = m->part[p];
-        PartView &pv = B.part[p];
-        pv.root = pi.tri_count > 1 ? 0 : ~0;
-        pv.limit = a.walk_limit_test ? 1 : pi.node_count + pi.tri_count + 8;
-        pv.tri_begin = pi.tri_begin;
-        pv.vert_begin = pi.vert_begin;
-        pv.v4 = m->tri_v4 + pi.tri_begin;
-        if (pi.dynamic) {
-            pv.node = sb.node + (size_t)pi.dyn_node_off * kNode4;
-            pv.tri = sb.tri + (size_t)pi.dyn_tri_off * 3;
-            pv.v64 = sb.vert64 + (size_t)pi.dyn_vert_off * 3;
-            const float *rb = sb.root_box + (size_t)p * 6;
-            for (int k = 0; k < 6; k++) pv.box[k] = rb[k];
-        } else {
-            pv.node = m->node_static + (size_t)pi.node_begin * kNode4;
-            pv.tri = m->tri_static + (size_t)pi.tri_begin * 3;
-            pv.v64 = m->rest64 + (size_t)pi.vert_begin * 3;
-            for (int k = 0; k < 6; k++) pv.box[k] = m->root_box_static[p][k];
-        }
-    }
 }
 
 // Copy the slot context (header + the parts in use) into shared memory.
@@ -758,13 +767,11 @@ __device__ __forceinline__ int part_of_sorted(const MeshDev *m, int t)
 // ones are listed for k_raster_chunks, which lists their 16 x 16-pixel chunks
 // that can meet them for k_raster_big (pass 0 lists, pass 1 reuses the lists).
 template <int PASS>
-__global__ void __launch_bounds__(128) k_raster(TraceArgs a)
+__device__ __forceinline__ void raster_tri(const TraceArgs &a, int s, int t)
 {
-    const int s = blockIdx.y;
     const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
     if (g->skip) return;
     const MeshDev *m = a.sd[s].mesh;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m->n_tris) return;
     const RastView V = rast_view(a, s);
     if (!(V.du32 > 0.0f && V.dv32 > 0.0f)) {
@@ -797,6 +804,12 @@ __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
             rast_pixel<PASS>(V, a.pix_key + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id, eb);
 }
 
+template <int PASS>
+__global__ void __launch_bounds__(128) k_raster(TraceArgs a)
+{
+    raster_tri<PASS>(a, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Warp per listed large triangle: its 16 x 16-pixel chunks that can meet it,
 // tested a chunk per lane and appended with one atomic per warp pass.
 __global__ void __launch_bounds__(256) k_raster_chunks(TraceArgs a)
@@ -826,13 +839,48 @@ __global__ void __launch_bounds__(256) k_raster_chunks(TraceArgs a)
             if (lane == 0) at = atomicAdd(a.big_count, (unsigned)__popc(bal));
             at = __shfl_sync(0xffffffffu, at, 0);
             const unsigned cnt = (unsigned)__popc(bal);
-            if (at > (unsigned)a.big_cap || cnt > (unsigned)a.big_cap - at) {
+            const unsigned room = at < (unsigned)a.big_cap ? (unsigned)a.big_cap - at : 0u;
+            if (cnt > room) {
+                // the list is full: the slot's pixels traverse instead; the part of this
+                // warp's range below the capacity is filled with placeholders (slot -1)
+                // so that every entry a reader sees was written
+                const unsigned idx = at + __popc(bal & ((1u << lane) - 1u));
+                if (meets && idx < (unsigned)a.big_cap) a.big[idx] = make_int4(-1, 0, 0, 0);
                 if (lane == 0) a.rast_bad[s] = 1;
                 break;
             }
             if (meets) a.big[at + __popc(bal & ((1u << lane) - 1u))] = make_int4(s, t, k % cw, k / cw);
+            if (a.queue && lane == 0) atomicAdd(a.qstate + kQSlot + 3 * s + 2, cnt);
         }
     }
+}
+
+// One listed chunk of a large triangle, by the calling warp.  Returns the
+// entry's slot, or -1 for a placeholder of a full list.
+template <int PASS>
+__device__ __forceinline__ int raster_big_entry(const TraceArgs &a, unsigned e, unsigned lane)
+{
+    const int4 E = a.big[e];
+    const int s = E.x, t = E.y;
+    if (s < 0) return -1;
+    const MeshDev *m = a.sd[s].mesh;
+    const RastView V = rast_view(a, s);
+    const int4 vi = __ldg(m->tri_v4 + t);
+    const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
+    int i0, i1, j0, j1;
+    if (!rast_box(V, A, B, C, i0, i1, j0, j1)) return s;
+    const int ib = i0 + E.z * kRastChunk, jb = j0 + E.w * kRastChunk;
+    const int ie = min(ib + kRastChunk - 1, i1), je = min(jb + kRastChunk - 1, j1);
+    const int p = part_of_sorted(m, t);
+    const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
+    const size_t off = (size_t)s * a.ray_stride;
+    const float eb = rast_bound(V, A, B, C, ib, ie, jb, je);
+    for (int q = (int)lane; q < kRastChunk * kRastChunk; q += 32) {
+        const int i = ib + q / kRastChunk, j = jb + q % kRastChunk;
+        if (i <= ie && j <= je)
+            rast_pixel<PASS>(V, a.pix_key + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id, eb);
+    }
+    return s;
 }
 
 // Warp per listed chunk of a large triangle (grid-stride over the list).
@@ -841,44 +889,25 @@ __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
 {
     const unsigned n = min(__ldcg(a.big_count), (unsigned)a.big_cap);
     const unsigned lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x >> 5);
-    for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) {
-        const int4 E = a.big[e];
-        const int s = E.x, t = E.y;
-        const MeshDev *m = a.sd[s].mesh;
-        const RastView V = rast_view(a, s);
-        const int4 vi = __ldg(m->tri_v4 + t);
-        const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
-        int i0, i1, j0, j1;
-        if (!rast_box(V, A, B, C, i0, i1, j0, j1)) continue;
-        const int ib = i0 + E.z * kRastChunk, jb = j0 + E.w * kRastChunk;
-        const int ie = min(ib + kRastChunk - 1, i1), je = min(jb + kRastChunk - 1, j1);
-        const int p = part_of_sorted(m, t);
-        const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
-        const size_t off = (size_t)s * a.ray_stride;
-        const float eb = rast_bound(V, A, B, C, ib, ie, jb, je);
-        for (int q = (int)lane; q < kRastChunk * kRastChunk; q += 32) {
-            const int i = ib + q / kRastChunk, j = jb + q % kRastChunk;
-            if (i <= ie && j <= je)
-                rast_pixel<PASS>(V, a.pix_key + off, a.pix_cand + off * kPixCand, i, j, A, B, C, id, eb);
-        }
-    }
+    for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) raster_big_entry<PASS>(a, e, lane);
 }
 
 // A block is kTraceWarps warps over consecutive tiles of one slot, sharing
 // one copy of the slot's context; a warp past the slot's last tile idles.
-template <bool COUNT, bool HITS>
-__global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_trace(TraceArgs a)
+// The trace of flattened block vb (kTraceWarps tiles of one slot).  B, s_cand
+// and s_hpt are the block's shared context copy and per-thread columns (entry k
+// of thread x at [k * kLaneStride + x]): the candidates of the FP64 resolution,
+// and each segment's hit as (part, triangle) for the FP64 replay of the
+// specular chain and the hit record.  QUEUE: run inside the work queue, where
+// this SM may hold stale L1 copies of pixel keys another SM's second raster
+// pass has changed since, so the raster's results are read from L2.
+template <bool COUNT, bool HITS, bool QUEUE>
+__device__ __forceinline__ void trace_block(const TraceArgs &a, int vb, TraceCtx &B, int *s_cand, int *s_hpt)
 {
     static_assert(kTileRays * kTraceWarps == kLaneStride, "per-thread shared columns assume 128 threads");
-    __shared__ TraceCtx B;
-    // per-thread columns (entry k of thread x at [k * kLaneStride + x]): the
-    // candidates of the FP64 resolution, and each segment's hit as (part,
-    // triangle) for the FP64 replay of the specular chain and the hit record
-    __shared__ int s_cand[kCand * kLaneStride];
-    __shared__ int s_hpt[(kMaxBounces + 1) * kLaneStride];
-    const int s = slot_of_block(a.sd, a.n_slots, blockIdx.x);
+    const int s = slot_of_block(a.sd, a.n_slots, vb);
     const SlotDesc &D = a.sd[s];
-    const int tile_id = (blockIdx.x - D.tile0) * kTraceWarps + (int)(threadIdx.x >> 5);
+    const int tile_id = (vb - D.tile0) * kTraceWarps + (int)(threadIdx.x >> 5);
     load_ctx(B, a, s);
     __syncthreads();
     if (tile_id >= D.tiles) return;
@@ -920,12 +949,13 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
         unsigned long long pk = ~0ull;
         if (a.raster) {
             const size_t px = (size_t)s * a.ray_stride + ray;
-            pk = __ldcs(a.pix_key + px);
+            pk = QUEUE ? __ldcg(a.pix_key + px) : __ldcs(a.pix_key + px);
             const unsigned pn = key_cands(pk);
             rast = pn <= (unsigned)kPixCand && !a.rast_bad[s];
             if (rast) {
                 cd.n = (int)pn;
-                for (int c = 0; c < (int)pn; c++) cd.id[c * kLaneStride] = (int)a.pix_cand[px * kPixCand + c];
+                for (int c = 0; c < (int)pn; c++)
+                    cd.id[c * kLaneStride] = (int)(QUEUE ? __ldcg(a.pix_cand + px * kPixCand + c) : a.pix_cand[px * kPixCand + c]);
                 if (COUNT) cn.why[0] += pn;
             }
         }
@@ -1070,6 +1100,151 @@ __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_t
     if (lane == 0) {
         a.amb_count[tile] = __popc(bal);
         if (fl) atomicOr(&a.pose[s].flags, fl);
+    }
+}
+
+template <bool COUNT, bool HITS>
+__global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_trace(TraceArgs a)
+{
+    __shared__ TraceCtx B;
+    __shared__ int s_cand[kCand * kLaneStride];
+    __shared__ int s_hpt[(kMaxBounces + 1) * kLaneStride];
+    trace_block<COUNT, HITS, false>(a, blockIdx.x, B, s_cand, s_hpt);
+}
+
+// ------------------------------------------------------------- work queue
+// The raster's second pass and the trace of a launch's slots as one persistent
+// kernel over a queue of work items, handed out in this order: the second pass
+// over small triangles (slot-major, 128 triangles an item), over the listed
+// chunks of large triangles (kTraceWarps chunks an item, a warp each), then the
+// trace blocks (kTraceWarps tiles an item).  A trace item of slot s may start
+// once every second-pass item of slot s has finished, which its block waits for
+// on the slot's completion counters.  Items are handed out in order and
+// second-pass items never wait, so the items a trace item waits for are held by
+// running blocks and every wait ends; each is bounded all the same (device
+// time): past the bound the block sets the slot's timeout flag and the queue's
+// abort flag (later waits give up at once), writes an empty result for its
+// tiles and goes on, and the call reports SRP_ERR_TIMEOUT.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long kQueueWaitNs = 2000000000ull;  // 2 s of device time
+constexpr unsigned long long kQueueTestWaitNs = 2000000ull; // 2 ms when a test makes the wait run out
+constexpr int kQueueBatch = 4;  // consecutive items a block claims at once
+
+// Slot of second-pass item it: the last slot whose first item is <= it.
+__device__ __forceinline__ int slot_of_rast_item(const SlotDesc *sd, int S, unsigned it)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if ((unsigned)__ldg(&sd[mid].rast0) <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Wait (thread 0 of a block) until slot s's second raster pass is complete; 1
+// when it is, 0 when the wait gave up.
+__device__ int queue_wait(const TraceArgs &a, int s)
+{
+    const unsigned *q = a.qstate + kQSlot + 3 * s;
+    const unsigned need_small = (unsigned)((a.sd[s].mesh->n_tris + 127) / 128) + (a.wait_test ? 1u : 0u);
+    const unsigned need_big = ld_acquire(q + 2);  // final: counted by the chunk listing, an earlier launch
+    const unsigned long long limit = a.wait_test ? kQueueTestWaitNs : kQueueWaitNs;
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    while (true) {
+        if (ld_acquire(q) >= need_small && ld_acquire(q + 1) >= need_big) return 1;
+        if (ld_acquire(a.qstate + kQAbort)) break;
+        if (global_ns() - t0 > limit) {
+            atomicExch(a.qstate + kQAbort, 1u);
+            break;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns *= 2;
+    }
+    atomicOr(&a.pose[s].flags, kFlagTimeout);
+    return 0;
+}
+
+// An empty result for trace block vb (its wait gave up): no force, no counts,
+// no hand-offs.
+__device__ void trace_block_empty(const TraceArgs &a, int vb)
+{
+    const int s = slot_of_block(a.sd, a.n_slots, vb);
+    const SlotDesc &D = a.sd[s];
+    const int tile_id = (vb - D.tile0) * kTraceWarps + (int)(threadIdx.x >> 5);
+    if (tile_id >= D.tiles || (threadIdx.x & 31) != 0) return;
+    const size_t tile = (size_t)s * a.n_blocks_x + tile_id;
+    for (int k = 0; k < 6; k++) a.partials[tile * 6 + k] = 0.0f;
+    for (int k = 0; k < kCnt; k++) a.pcounts[tile * kCnt + k] = 0u;
+    a.amb_count[tile] = 0;
+}
+
+template <bool COUNT, bool HITS>
+__global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_queue(TraceArgs a)
+{
+    __shared__ TraceCtx B;
+    __shared__ int s_cand[kCand * kLaneStride];
+    __shared__ int s_hpt[(kMaxBounces + 1) * kLaneStride];
+    __shared__ unsigned s_item;
+    __shared__ int s_ok, s_ready;  // s_ready: a slot whose second pass this block has seen complete
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned n_small = (unsigned)a.n_small_items;
+    const unsigned n_big_e = min(ld_acquire(a.big_count), (unsigned)a.big_cap);
+    const unsigned n_big = (n_big_e + kTraceWarps - 1) / kTraceWarps;
+    const unsigned total = n_small + n_big + (unsigned)a.n_tiles;
+    if (threadIdx.x == 0) s_ready = -1;
+    for (;;) {
+        __syncthreads();  // every warp is done with the previous item and its shared state
+        if (threadIdx.x == 0) s_item = atomicAdd(a.qstate + kQHead, (unsigned)kQueueBatch);
+        __syncthreads();
+        const unsigned it0 = s_item;
+        if (it0 >= total) break;
+        const unsigned it1 = min(it0 + (unsigned)kQueueBatch, total);
+        for (unsigned it = it0; it < it1; it++) {
+        if (it > it0) __syncthreads();
+        if (it < n_small) {
+            const int s = slot_of_rast_item(a.sd, a.n_slots, it);
+            raster_tri<1>(a, s, (int)(it - (unsigned)a.sd[s].rast0) * 128 + (int)threadIdx.x);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(a.qstate + kQSlot + 3 * s, 1u);
+            }
+        } else if (it < n_small + n_big) {
+            const unsigned e = (it - n_small) * kTraceWarps + (threadIdx.x >> 5);
+            if (e < n_big_e) {
+                const int s = raster_big_entry<1>(a, e, lane);
+                __syncwarp();
+                if (lane == 0 && s >= 0) {
+                    __threadfence();
+                    atomicAdd(a.qstate + kQSlot + 3 * s + 1, 1u);
+                }
+            }
+        } else {
+            const int vb = (int)(it - n_small - n_big);
+            if (threadIdx.x == 0) {
+                const int s = slot_of_block(a.sd, a.n_slots, vb);
+                s_ok = s == s_ready ? 1 : queue_wait(a, s);
+                if (s_ok) s_ready = s;
+            }
+            __syncthreads();
+            if (s_ok) trace_block<COUNT, HITS, true>(a, vb, B, s_cand, s_hpt);
+            else trace_block_empty(a, vb);
+        }
+        }
     }
 }
 
@@ -1778,8 +1953,10 @@ cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
         k_raster<0><<<grid, 128, 0, st>>>(a);
         k_raster_chunks<<<kRastBigBlocks / 8, 256, 0, st>>>(a);
         k_raster_big<0><<<kRastBigBlocks, 256, 0, st>>>(a);
-        k_raster<1><<<grid, 128, 0, st>>>(a);
-        k_raster_big<1><<<kRastBigBlocks, 256, 0, st>>>(a);
+        if (!a.queue) {  // the work queue runs the second pass with the trace
+            k_raster<1><<<grid, 128, 0, st>>>(a);
+            k_raster_big<1><<<kRastBigBlocks, 256, 0, st>>>(a);
+        }
     }
     return cudaGetLastError();
 }
@@ -1791,6 +1968,22 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
     // the hit records and the traversal counters are separate kernel variants:
     // code a launch never runs still costs registers in the others
     const dim3 g(a.n_tiles), b(kTileRays * kTraceWarps);
+    if (a.queue) {
+        // persistent: as many blocks as fit on the device at once
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const dim3 gq(std::max(1, sms) * kQueueBlocksPerSM);
+        if (a.count) {
+            if (a.hits) k_queue<true, true><<<gq, b, 0, st>>>(a);
+            else k_queue<true, false><<<gq, b, 0, st>>>(a);
+        } else {
+            if (a.hits) k_queue<false, true><<<gq, b, 0, st>>>(a);
+            else k_queue<false, false><<<gq, b, 0, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
     if (a.count) {
         if (a.hits) k_trace<true, true><<<g, b, 0, st>>>(a);
         else k_trace<true, false><<<g, b, 0, st>>>(a);

@@ -26,6 +26,8 @@ EVAL_TRAVERSE = 8  # primary hits by BVH traversal instead of rasterisation (sam
 EVAL_TEST_WALK_BOUND = 16  # tests of the walk bound's error path: every BVH walk stops after one step
 EVAL_AUTOTUNE = 4
 EVAL_SERIAL = 32  # one pipeline lane: with timing, each phase's time is its own kernels' GPU time
+EVAL_QUEUE = 64  # second raster pass and trace as one persistent launch over a work queue
+EVAL_TEST_WAIT_TIMEOUT = 128  # tests of the work queue's bounded wait (SRP_ERR_TIMEOUT)
 MAX_BOUNCES = 4
 MAX_N = 8192  # SRP_MAX_N: rays per window side
 MAX_DIFFUSE = 256  # diffuse secondary rays per hit (srp_eval_params.n_diffuse)
@@ -528,7 +530,7 @@ class Context:
                         epoch_mjd_tt: float = 61041.0, rtol: float = 1e-12, atol_pos: float = 1e-6,
                         atol_vel: float = 1e-9, h0: float = 60.0, h_min: float = 1e-6, h_max: float = 0.0,
                         max_steps: int = 10_000_000, poll: int = 16, P0: float = 4.56e-6, eps_rel: float = 1e-9,
-                        autotune: bool = False, traverse: bool = False):
+                        autotune: bool = False, traverse: bool = False, flags: int = 0):
         """srp_propagate_batch over a list of trajectory dicts with keys mesh_id,
         N, bounces, panel_mode, angles (or None), central, attitude, q, y0, t0,
         t1.  Returns (y1 [n, 6], stats list)."""
@@ -546,7 +548,7 @@ class Context:
         p = PropParams(method, 0, int(j2), int(sun3), int(srp_on), 0, (C.c_double * 4)(1.0, 0.0, 0.0, 0.0),
                        epoch_mjd_tt, rtol, atol_pos, atol_vel, h0, h_min, h_max, max_steps, poll, 0,
                        EvalParams(1, 0, P0, eps_rel, 0, (EVAL_AUTOTUNE if autotune else 0)
-                                  | (EVAL_TRAVERSE if traverse else 0)), None, 0)
+                                  | (EVAL_TRAVERSE if traverse else 0) | flags), None, 0)
         y1 = np.empty((n, 6))
         st = (PropStats * n)()
         self._check(self.lib.srp_propagate_batch(self.h, C.byref(p), n, arr, y1.ctypes.data, st))
