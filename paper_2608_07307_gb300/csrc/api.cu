@@ -56,6 +56,12 @@ struct srp_ctx {
     size_t partials1_cap = 0;
     double *dpart = nullptr;  // diffuse-ray partial sums [SL][kDiffBlocks][6]
     size_t dpart_cap = 0;
+    DEmit *demit = nullptr;   // diffuse emission records [SL][R][nseg - 1]
+    size_t demit_cap = 0;
+    int *dcnt = nullptr;      // their counts, then prefix, per ray [SL][R]
+    size_t dcnt_cap = 0;
+    int *dtot = nullptr;      // per slot [SL]
+    size_t dtot_cap = 0;
     unsigned char *tctx = nullptr;
     size_t tctx_cap = 0;
     int *amb_count = nullptr;
@@ -601,7 +607,14 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     }
     // the diffuse rays replay each ray's recorded hits
     if (want_hits || adjoint || prm->n_diffuse > 0) CK(ctx, grow(&ctx->hits, &ctx->hits_cap, SL * pl.R * pl.nseg, false));
-    if (prm->n_diffuse > 0) CK(ctx, grow(&ctx->dpart, &ctx->dpart_cap, SL * kDiffBlocks * 6, false));
+    if (prm->n_diffuse > 0) {
+        CK(ctx, grow(&ctx->dpart, &ctx->dpart_cap, SL * kDiffBlocks * 6, false));
+        if (pl.nseg > 1) {
+            CK(ctx, grow(&ctx->demit, &ctx->demit_cap, SL * pl.R * (size_t)(pl.nseg - 1), false));
+            CK(ctx, grow(&ctx->dcnt, &ctx->dcnt_cap, SL * pl.R, false));
+            CK(ctx, grow(&ctx->dtot, &ctx->dtot_cap, SL, false));
+        }
+    }
     // every slot evaluates this mesh on this grid; lane b owns slots [b S, (b + 1) S)
     std::vector<SlotDesc> sd(SL);
     for (size_t k = 0; k < SL; k++) {
@@ -693,6 +706,9 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             a.n_diffuse = prm->n_diffuse;
             a.diffuse_seed = prm->diffuse_seed;
             a.dpart = ctx->dpart + s0 * kDiffBlocks * 6;
+            a.demit = ctx->demit + s0 * R * (size_t)(nseg - 1);
+            a.dcnt = ctx->dcnt + s0 * R;
+            a.dtot = ctx->dtot + s0;
         }
         int g0 = tm.mark(ls);
         CK(ctx, launch_pose(sd, d_sun, d_dist, prm->P0, e0, Sc, pose, ls));
@@ -712,7 +728,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         int g4 = tm.mark(ls);
         launches += 4;  // frame, trace, two reduction levels
         if (a.raster) launches += 5;  // two raster passes over small and large triangles, chunk listing
-        if (a.n_diffuse > 0) launches += 1;  // diffuse secondaries
+        if (a.n_diffuse > 0) launches += 3;  // diffuse secondaries: emission records, their prefix, the rays
         trace_launches++;
         if (adj) {
             AdjArgs g{};
@@ -946,6 +962,9 @@ void srp_destroy(srp_ctx *ctx)
     dfree(ctx->amb_list);
     dfree(ctx->partials1);
     dfree(ctx->dpart);
+    dfree(ctx->demit);
+    dfree(ctx->dcnt);
+    dfree(ctx->dtot);
     dfree(ctx->tctx);
     dfree(ctx->prop_io);
     dfree(ctx->spad_buf);

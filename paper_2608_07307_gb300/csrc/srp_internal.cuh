@@ -214,6 +214,9 @@ struct TraceArgs {
     int n_diffuse;
     unsigned diffuse_seed;
     double *dpart;               // [S][kDiffBlocks][6] unscaled force / torque of the diffuse rays
+    struct DEmit *demit;         // [S][ray_stride][nseg - 1] emission records of the diffuse rays (dense)
+    int *dcnt;                   // [S][ray_stride] emissions of each primary ray, then their exclusive prefix
+    int *dtot;                   // [S] emissions of the slot
     int walk_limit_test;         // 1: every BVH walk is bounded at one step (tests of the bound's error path)
     // work queue (queue != 0): the raster's second pass and the trace as one
     // persistent launch; qstate = [head, abort, then per slot: second-pass
@@ -227,6 +230,14 @@ constexpr int kQHead = 0, kQAbort = 1, kQSlot = 2;  // qstate layout; 3 words pe
 constexpr int kQueueBlocksPerSM = 8;
 inline size_t qstate_words(size_t slots) { return (size_t)kQSlot + 3 * slots; }
 constexpr int kDiffBlocks = 64;  // k_diffuse blocks per slot (fixed: the sums have a fixed order)
+// One hit that emits diffuse secondary rays: the FP64 point and lit-side
+// normal from the replay of its ray's specular chain, the weight of one sample
+// (w rho_d / K), the emitting triangle and the sample counter of sample 0.
+struct DEmit {
+    double x[3], nf[3], wd;
+    int src, pad_;
+    unsigned long long c0;
+};
 constexpr int kPixCand = 2;      // uncertain triangles kept per pixel (more: the ray traverses)
 constexpr int kRastSmall = 64;   // largest pixel box one thread rasterises
 constexpr int kRastChunk = 16;   // larger triangles: chunks of 16 x 16 pixels, one warp each

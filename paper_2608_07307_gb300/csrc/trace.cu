@@ -1546,7 +1546,7 @@ __device__ __forceinline__ void diffuse_dir(unsigned long long seed, unsigned lo
     const double u1 = (double)(splitmix64_at(seed, 2ull * c) >> 11) * 0x1.0p-53;
     const double u2 = (double)(splitmix64_at(seed, 2ull * c + 1ull) >> 11) * 0x1.0p-53;
     double sp, cp;
-    sincos(6.283185307179586 * u2, &sp, &cp);
+    sincospi(2.0 * u2, &sp, &cp);  // the angle 2 pi u2, reduced exactly (2 u2 is exact)
     const double rr = sqrt(u1), lz = sqrt(1.0 - u1);
     const double sign = copysign(1.0, nf[2]);
     const double a = -1.0 / (sign + nf[2]);
@@ -1624,7 +1624,15 @@ __device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long 
         cd.n = 0;
         cd.id = cand_col;
         if (nearest32<false, false>(B, q, 0.0f, 0.0f, B.eps32, src, -1, kEmptyChild, delta, tau, b, cn, cd)) {
-            settle64(B, r, B.eps, src, cd, b, t, p, tl);
+            if (cd.n == 0) {
+                // every FP32 decision was certain: the FP32 nearest hit is the FP64 one,
+                // and its FP32 distance places the hit point for the torque arm
+                p = b.part;
+                tl = b.tl;
+                t = (double)b.t;
+            } else {
+                settle64(B, r, B.eps, src, cd, b, t, p, tl);
+            }
         } else {
             int orig;
             nearest64(B, r, B.eps, src, t, p, tl, orig, flags);
@@ -1662,26 +1670,26 @@ __device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long 
 // lit side's normal, is traced with the FP64 traversal and deposits the
 // per-hit law at its hit.  Sums per block in a fixed order: the result is
 // reproducible.
-__global__ void __launch_bounds__(kLaneStride) k_diffuse(TraceArgs a)
+// Diffuse rays, step 1: a thread per primary ray replays its specular chain in
+// FP64 through the recorded hit triangles and writes one record per hit that
+// emits (a segment with a next level, rho_d > 0) to the ray's slots of the
+// dense array, and the number of records.
+__global__ void __launch_bounds__(kLaneStride) k_demit(TraceArgs a)
 {
     __shared__ TraceCtx B;
-    __shared__ double red[4][6];
-    __shared__ int s_cand[kCand * kLaneStride];  // per-thread candidate columns (see Cands)
     const int s = blockIdx.y;
     load_ctx(B, a, s);
     __syncthreads();
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    if (!B.skip) {
-        const SlotDesc &D = a.sd[s];
-        const int N = D.N, nseg = D.nseg, K = a.n_diffuse;
-        const size_t R = (size_t)N * N;
-        const int *tri_pos = D.mesh->tri_pos;
-        int flags = 0;
-        const size_t items = R * (size_t)K;
-        for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (size_t)gridDim.x * blockDim.x) {
-            const size_t ray = it / K;
-            const int q = (int)(it - ray * K);
+    const SlotDesc &D = a.sd[s];
+    const int N = D.N, nseg = D.nseg, K = a.n_diffuse;
+    const size_t R = (size_t)N * N;
+    int *cnt = a.dcnt + (size_t)s * a.ray_stride;
+    for (size_t ray = (size_t)blockIdx.x * blockDim.x + threadIdx.x; ray < R; ray += (size_t)gridDim.x * blockDim.x) {
+        int ne = 0;
+        if (!B.skip) {
+            const int *tri_pos = D.mesh->tri_pos;
             const int32_t *hq = a.hits + ((size_t)s * a.ray_stride + ray) * a.seg_stride;
+            DEmit *out = a.demit + ((size_t)s * a.ray_stride + ray) * (size_t)(nseg - 1);
             const int i = (int)(ray / N), j = (int)(ray % N);
             const double uc = B.umin + pix64(((double)i + 0.5) * B.Du, B.rN, N);
             const double vc = B.vmin + pix64(((double)j + 0.5) * B.Dv, B.rN, N);
@@ -1709,17 +1717,84 @@ __global__ void __launch_bounds__(kLaneStride) k_diffuse(TraceArgs a)
                 const int mi = side ? (int)(mt >> 16) : (int)(mt & 0xffffu);
                 const double rs = B.mat64[2 * mi], rd = B.mat64[2 * mi + 1];
                 if (rd > 0.0) {
-                    const double nf[3] = {sg * n[0], sg * n[1], sg * n[2]};
-                    const unsigned long long c =
-                        ((unsigned long long)ray * (unsigned long long)nseg + (unsigned long long)k) *
-                            (unsigned long long)K + (unsigned long long)q;
-                    diffuse_sample(B, (unsigned long long)a.diffuse_seed, c, x, nf, h, wgt * rd / K, acc, flags,
-                                   s_cand + threadIdx.x);
+                    DEmit &e = out[ne++];
+                    for (int c = 0; c < 3; c++) { e.x[c] = x[c]; e.nf[c] = sg * n[c]; }
+                    e.wd = wgt * rd / K;
+                    e.src = h;
+                    e.c0 = ((unsigned long long)ray * (unsigned long long)nseg + (unsigned long long)k) *
+                           (unsigned long long)K;
                 }
                 wgt *= rs;
                 if (wgt == 0.0) break;
                 for (int c = 0; c < 3; c++) { d[c] = d[c] - 2.0 * dn * n[c]; o[c] = x[c]; }
             }
+        }
+        cnt[ray] = ne;
+    }
+}
+
+// Diffuse rays, step 2: a block per slot turns the per-ray record counts into
+// their exclusive prefix (each thread a contiguous range, then the block's
+// ranges in order) and the slot's total.
+__global__ void __launch_bounds__(1024) k_dscan(TraceArgs a)
+{
+    __shared__ int part[1024];
+    const int s = blockIdx.x;
+    const size_t R = (size_t)a.sd[s].N * a.sd[s].N;
+    int *cnt = a.dcnt + (size_t)s * a.ray_stride;
+    const size_t per = (R + blockDim.x - 1) / blockDim.x;
+    const size_t r0 = min(R, per * threadIdx.x), r1 = min(R, r0 + per);
+    int sum = 0;
+    for (size_t r = r0; r < r1; r++) sum += cnt[r];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive scan of the ranges' sums
+        const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - sum;
+    for (size_t r = r0; r < r1; r++) {
+        const int c = cnt[r];
+        cnt[r] = run;
+        run += c;
+    }
+    if (threadIdx.x == blockDim.x - 1) a.dtot[s] = part[threadIdx.x];
+}
+
+// Diffuse rays, step 3: a thread per (record, sample) work item, items in the
+// order of the records (ray-major), each record's K samples consecutive; the
+// record of item e K + q is found by binary search over the prefix.
+__global__ void __launch_bounds__(kLaneStride) k_diffuse(TraceArgs a)
+{
+    __shared__ TraceCtx B;
+    __shared__ double red[4][6];
+    __shared__ int s_cand[kCand * kLaneStride];  // per-thread candidate columns (see Cands)
+    const int s = blockIdx.y;
+    load_ctx(B, a, s);
+    __syncthreads();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    if (!B.skip) {
+        const SlotDesc &D = a.sd[s];
+        const int N = D.N, nseg = D.nseg, K = a.n_diffuse;
+        const size_t R = (size_t)N * N;
+        const int *off = a.dcnt + (size_t)s * a.ray_stride;
+        const DEmit *rec = a.demit + (size_t)s * a.ray_stride * (size_t)(nseg - 1);
+        int flags = 0;
+        const size_t items = (size_t)a.dtot[s] * (size_t)K;
+        for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (size_t)gridDim.x * blockDim.x) {
+            const int e = (int)(it / K);
+            const int q = (int)(it - (size_t)e * K);
+            // the last ray whose first record is <= e
+            size_t lo = 0, hi = R - 1;
+            while (lo < hi) {
+                const size_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(off + mid) <= e) lo = mid; else hi = mid - 1;
+            }
+            const DEmit &E = rec[lo * (size_t)(nseg - 1) + (size_t)(e - __ldg(off + lo))];
+            diffuse_sample(B, (unsigned long long)a.diffuse_seed, E.c0 + (unsigned long long)q, E.x, E.nf, E.src, E.wd,
+                           acc, flags, s_cand + threadIdx.x);
         }
         if (flags) atomicOr(&a.pose[s].flags, flags);
     }
@@ -1999,7 +2074,11 @@ cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, d
 {
     k_reduce1<<<dim3(kRed1, S), 256, 0, st>>>(a);
     // diffuse secondaries after the FP64 re-trace (which records the hits of the rays it takes)
-    if (a.n_diffuse > 0) k_diffuse<<<dim3(kDiffBlocks, S), kLaneStride, 0, st>>>(a);
+    if (a.n_diffuse > 0) {
+        k_demit<<<dim3(kDiffBlocks, S), kLaneStride, 0, st>>>(a);
+        k_dscan<<<S, 1024, 0, st>>>(a);
+        k_diffuse<<<dim3(kDiffBlocks, S), kLaneStride, 0, st>>>(a);
+    }
     k_reduce<<<S, 256, 0, st>>>(a, eval0, force, torque, err_flags, stats_accum);
     return cudaGetLastError();
 }
