@@ -43,12 +43,12 @@ NODE_BYTES, TRI_BYTES = 128, 48  # one 4-wide BVH node, one FP32 triangle record
 # DRAM bytes (read + write) of one k_trace launch of the headline workload (8
 # evaluations), from one ncu capture of the current kernel; None when the kernel
 # changed after the capture
-TRACE_DRAM_BYTES_PER_LAUNCH = 193.570e6 + 50.163e6  # mean of three launches, ncu dram__bytes_read/write.sum
+TRACE_DRAM_BYTES_PER_LAUNCH = 128.0e6 + 21.35e6  # mean of three launches, ncu dram__bytes_read/write.sum
 # the same capture's unit throughputs, % of the GB300's peak for each unit
-TRACE_NCU_PCT_OF_PEAK = {"l1tex": 62.2, "l2": 27.9, "dram": 3.5, "sm_issue_active": 62.4,
-                         "l2_bytes_per_launch": 4.476e9, "l1_bytes_per_launch": 6.018e9}
+TRACE_NCU_PCT_OF_PEAK = {"l1tex": 61.9, "l2": 23.2, "dram": 2.6, "sm_issue_active": 65.0,
+                         "l2_bytes_per_launch": 3.401e9, "l1_bytes_per_launch": 4.684e9}
 # L2 bandwidth implied by that capture: L2 bytes / (L2 throughput % / 100) / duration
-L2_PEAK_GBS = 4.476e9 / 0.279 / 812.48e-6 / 1e9
+L2_PEAK_GBS = 3.401e9 / 0.2324 / 720.5e-6 / 1e9
 HBM_FALLBACK_GBS = 6800.0  # the profiling recipe's fallback when no measured peak is present
 
 
@@ -583,7 +583,7 @@ def bench_differentiated(ctx, stream, arc_steps, facet=0.05, N=512, bounces=1, b
 
 
 # ---------------------------------------------------------------- batched
-def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7):
+def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7, flags=0):
     """The batched form: n_traj trajectories drawn from a seed, each with its
     own mesh (a pool of 8 spacecraft meshes of ~0.9k-200k triangles), ray grid
     (256-1024 per side), bounces (0-2), joint law (tracking, tracking + offsets,
@@ -644,9 +644,9 @@ def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7):
         w, _ = ctx.autotune(mid, N, b)
         shapes[w] = shapes.get(w, 0) + 1
     t_tune = time.perf_counter() - t0
-    ctx.propagate_batch(trajs[:8], **kw)  # warm-up (workspace, graph path)
+    ctx.propagate_batch(trajs[:8], flags=flags, **kw)  # warm-up (workspace, graph path)
     t0 = time.perf_counter()
-    y1, st = ctx.propagate_batch(trajs, **kw)
+    y1, st = ctx.propagate_batch(trajs, flags=flags, **kw)
     t_batch = time.perf_counter() - t0
     steps = sum(s["steps"] for s in st)
     evals = sum(s["evals"] for s in st)
