@@ -120,6 +120,8 @@ def parse():
     p.add_argument("--no-panels", action="store_true", help="skip the fixed vs movable panel study")
     p.add_argument("--no-diffuse", action="store_true", help="skip the diffuse-ray measurement")
     p.add_argument("--batch-traj", type=int, default=256, help="trajectories of the batched form")
+    p.add_argument("--batch-full-arcs", action="store_true",
+                   help="batched form with its full 1-30 day arcs (minutes) instead of 1-4 h / 1-10 d")
     p.add_argument("--grad-arc-steps", type=int, default=10000,
                    help="RK4 steps of the timed adjoint arc (the differentiated workload's arc: 10000 at 60 s)")
     p.add_argument("--no-boxwing", action="store_true", help="skip the box-wing (16 triangles, 256 directions) form")
@@ -583,13 +585,14 @@ def bench_differentiated(ctx, stream, arc_steps, facet=0.05, N=512, bounces=1, b
 
 
 # ---------------------------------------------------------------- batched
-def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7, flags=0):
+def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7, flags=0, full_arcs=False):
     """The batched form: n_traj trajectories drawn from a seed, each with its
     own mesh (a pool of 8 spacecraft meshes of ~0.9k-200k triangles), ray grid
     (256-1024 per side), bounces (0-2), joint law (tracking, tracking + offsets,
     commanded), orbit (GEO with an LVLH attitude turned by a random quaternion,
     or heliocentric at 0.7-1.2 AU with a random inertial quaternion; +-1 km /
-    1 m/s Gaussian perturbations) and arc (GEO 1-4 h, heliocentric 1-10 days),
+    1 m/s Gaussian perturbations) and arc (GEO 1-4 h, heliocentric 1-10 days;
+    with full_arcs, 1-30 days for both, the batched workload's own range),
     RKF7(8) rtol 1e-12 with J2 + Sun.  Aggregate accepted steps/s and SRP
     evaluations/s of one srp_propagate_batch call (tile shapes autotuned per
     (mesh, N, bounces) first, timed separately), against the plain GPU method
@@ -624,13 +627,13 @@ def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7, flags=0):
             ph, inc = rng.uniform(0, 2 * math.pi), math.radians(0.1)
             y0 = np.array([a * math.cos(ph), a * math.sin(ph), 0.0, -v * math.sin(ph) * math.cos(inc),
                            v * math.cos(ph) * math.cos(inc), v * math.sin(inc)])
-            central, att, t1 = 0, 0, rng.uniform(1, 4) * 3600.0
+            central, att, t1 = 0, 0, (rng.uniform(1, 30) * 86400.0 if full_arcs else rng.uniform(1, 4) * 3600.0)
         else:
             r = rng.uniform(0.7, 1.2) * au
             v = math.sqrt(mu_s / r)
             ph = rng.uniform(0, 2 * math.pi)
             y0 = np.array([r * math.cos(ph), r * math.sin(ph), 0.0, -v * math.sin(ph), v * math.cos(ph), 0.0])
-            central, att, t1 = 1, 1, rng.uniform(1, 10) * 86400.0
+            central, att, t1 = 1, 1, rng.uniform(1, 30 if full_arcs else 10) * 86400.0
         y0[:3] += rng.normal(scale=1e3, size=3)
         y0[3:] += rng.normal(scale=1.0, size=3)
         trajs.append(dict(mesh_id=mids[mi], N=int(rng.choice([256, 512, 768, 1024])), bounces=int(rng.integers(3)),
@@ -668,9 +671,10 @@ def bench_batched(ctx, n_traj=256, plain_sample=16, seed=7, flags=0):
     plain_steps_per_s = steps_plain / t_plain
     for mid in mids:
         ctx.free_mesh(mid)
+    arcs = "GEO and heliocentric 1-30 d arcs" if full_arcs else "GEO 1-4 h / heliocentric 1-10 d arcs"
     return {"workload": f"{n_traj} trajectories, meshes of {min(m.n_tris for m in meshes)}-"
-                        f"{max(m.n_tris for m in meshes)} triangles, N 256-1024, bounces 0-2, GEO 1-4 h / "
-                        f"heliocentric 1-10 d arcs, RKF7(8) rtol 1e-12, J2 + Sun + SRP",
+                        f"{max(m.n_tris for m in meshes)} triangles, N 256-1024, bounces 0-2, {arcs}, "
+                        f"RKF7(8) rtol 1e-12, J2 + Sun + SRP",
             "steps_per_s": steps / t_batch, "evals_per_s": evals / t_batch, "accepted_steps": steps,
             "srp_evals": evals, "seconds": t_batch,
             "plain_steps_per_s": plain_steps_per_s,
@@ -876,7 +880,7 @@ def run_native(a):
     if not a.no_grad:
         line["differentiated"] = bench_differentiated(ctx, stream, a.grad_arc_steps)
     if not a.no_batch:
-        line["batched"] = bench_batched(ctx, a.batch_traj)
+        line["batched"] = bench_batched(ctx, a.batch_traj, full_arcs=a.batch_full_arcs)
     if not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mesh, table[:8], a, a.cpu_seconds)
     print(json.dumps(line), flush=True)
