@@ -123,6 +123,9 @@ struct srp_ctx {
     std::map<std::tuple<const void *, int, int>, int> tile_w;
     cudaStream_t lane[kLanes] = {};  // pipeline lanes (forked from / joined to `stream`)
     cudaEvent_t ev_fork = nullptr, ev_join[kLanes] = {};
+    // a side stream per lane: the refit runs beside the frame and raster passes
+    cudaStream_t aux[kLanes] = {};
+    cudaEvent_t ev_refit_fork[kLanes] = {}, ev_refit_join[kLanes] = {};
 };
 
 namespace {
@@ -714,12 +717,19 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         CK(ctx, launch_pose(sd, d_sun, d_dist, prm->P0, e0, Sc, pose, ls));
         CK(ctx, launch_vertices(sd, pose, Sc, h.n_verts, ls));
         launches += 2;
-        if (h.n_dyn_tris > 0) {
-            CK(ctx, launch_refit(sd, pose, Sc, h.n_dyn_tris, ls));
+        // the refit feeds only the trace (the raster reads the posed view-frame
+        // vertices): it runs on the lane's side stream beside frame and raster
+        const bool refit = h.n_dyn_tris > 0;
+        if (refit) {
+            CK(ctx, cudaEventRecord(ctx->ev_refit_fork[b], ls));
+            CK(ctx, cudaStreamWaitEvent(ctx->aux[b], ctx->ev_refit_fork[b], 0));
+            CK(ctx, launch_refit(sd, pose, Sc, h.n_dyn_tris, ctx->aux[b]));
+            CK(ctx, cudaEventRecord(ctx->ev_refit_join[b], ctx->aux[b]));
             launches++;
         }
         int g1 = tm.mark(ls);
         CK(ctx, launch_frame(a, Sc, ls));
+        if (refit) CK(ctx, cudaStreamWaitEvent(ls, ctx->ev_refit_join[b], 0));
         int g1r = tm.mark(ls);
         CK(ctx, launch_trace(a, Sc, ls));
         int g2 = tm.mark(ls);
@@ -938,7 +948,10 @@ srp_status srp_create(srp_ctx **out, int32_t device, void *cuda_stream)
     }
     for (int b = 0; b < kLanes; b++)
         if (cudaStreamCreateWithFlags(&ctx->lane[b], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ctx->aux[b], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_refit_fork[b], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_refit_join[b], cudaEventDisableTiming) != cudaSuccess) {
             srp_destroy(ctx);
             return SRP_ERR_CUDA;
         }
@@ -995,6 +1008,9 @@ void srp_destroy(srp_ctx *ctx)
     for (int b = 0; b < kLanes; b++) {
         if (ctx->lane[b]) cudaStreamSynchronize(ctx->lane[b]), cudaStreamDestroy(ctx->lane[b]);
         if (ctx->ev_join[b]) cudaEventDestroy(ctx->ev_join[b]);
+        if (ctx->aux[b]) cudaStreamSynchronize(ctx->aux[b]), cudaStreamDestroy(ctx->aux[b]);
+        if (ctx->ev_refit_fork[b]) cudaEventDestroy(ctx->ev_refit_fork[b]);
+        if (ctx->ev_refit_join[b]) cudaEventDestroy(ctx->ev_refit_join[b]);
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -2367,8 +2383,13 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
             if (p->srp) {
                 if (e == cudaSuccess) e = launch_pose(sd, d_sun, d_dist, p->eval.P0, 0, na, pose, st);
                 if (e == cudaSuccess) e = launch_vertices(sd, pose, na, mv, st);
-                if (e == cudaSuccess) e = launch_refit(sd, pose, na, md, st);
+                // the refit beside frame and raster, joined before the trace
+                if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_refit_fork[0], st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux[0], ctx->ev_refit_fork[0], 0);
+                if (e == cudaSuccess) e = launch_refit(sd, pose, na, md, ctx->aux[0]);
+                if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_refit_join[0], ctx->aux[0]);
                 if (e == cudaSuccess) e = launch_frame(a, na, st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_refit_join[0], 0);
                 if (e == cudaSuccess) e = launch_trace(a, na, st);
                 if (e == cudaSuccess) e = launch_reduce(a, na, 0, d_f, d_t, ctx->err_flags, nullptr, st);
             }

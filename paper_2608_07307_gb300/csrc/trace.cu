@@ -86,8 +86,8 @@ struct PartView {
     int root;            // 0, or ~0 for a one-triangle part
     int limit;           // bound on loop iterations of one part walk (nodes + triangles)
     int tri_begin, vert_begin;
-    float box[6];
-    int pad_[2];
+    float box[6];        // root box (filled when a block loads the context, from box_src)
+    const float *box_src;  // the part's root box: the refit's output for a dynamic part
 };
 
 struct TraceCtx {
@@ -158,13 +158,12 @@ __global__ void k_frame(TraceArgs a)
             pv.node = sb.node + (size_t)pi.dyn_node_off * kNode4;
             pv.tri = sb.tri + (size_t)pi.dyn_tri_off * 3;
             pv.v64 = sb.vert64 + (size_t)pi.dyn_vert_off * 3;
-            const float *rb = sb.root_box + (size_t)p * 6;
-            for (int k = 0; k < 6; k++) pv.box[k] = rb[k];
+            pv.box_src = sb.root_box + (size_t)p * 6;
         } else {
             pv.node = m->node_static + (size_t)pi.node_begin * kNode4;
             pv.tri = m->tri_static + (size_t)pi.tri_begin * 3;
             pv.v64 = m->rest64 + (size_t)pi.vert_begin * 3;
-            for (int k = 0; k < 6; k++) pv.box[k] = m->root_box_static[p][k];
+            pv.box_src = m->root_box_static[p];
         }
     }
     if (threadIdx.x != 0) return;
@@ -230,6 +229,10 @@ __device__ __forceinline__ void load_ctx(TraceCtx &B, const TraceArgs &a, int s)
     const int *src = reinterpret_cast<const int *>(g);
     int *dst = reinterpret_cast<int *>(&B);
     for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = __ldg(src + k);
+    __syncthreads();
+    // the root boxes, from where the refit (or the mesh load) left them: the
+    // frame kernel that wrote the context did not wait for the refit
+    for (int k = threadIdx.x; k < 6 * np; k += blockDim.x) B.part[k / 6].box[k % 6] = B.part[k / 6].box_src[k % 6];
 }
 
 // Slab test of one box; returns entry t or +inf.
@@ -1956,7 +1959,8 @@ __global__ void k_bvh_check(const unsigned char *tctx, int *tri_seen, unsigned l
         refs++;
         if (!ok) outside_tri++;
     };
-    const float root_box[6] = {pv.box[0], pv.box[3], pv.box[1], pv.box[4], pv.box[2], pv.box[5]};
+    const float *bs = pv.box_src;
+    const float root_box[6] = {bs[0], bs[3], bs[1], bs[4], bs[2], bs[5]};
     if (pv.root < 0) {
         tri_inside(~pv.root, root_box);
     } else {
