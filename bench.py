@@ -361,6 +361,19 @@ def bench_precision(ctx, stream, flush, facet=0.05, N=1024, bounces=2, reps=3):
             "directions": ks, "force_rel_err": [float(x) for x in rf], "torque_rel_err": [float(x) for x in rt],
             "force_rel_err_max": float(rf.max()), "torque_rel_err_max": float(rt.max()), "bar": 1e-4,
             "source": "oracle whole evaluations, tests/golden/fullsize_forces.txt"}
+        # the sums above the 32-ray tile in compensated (Kahan-Babuska) or plain FP32
+        modes = {"fp64": {"force_rel_err_max": float(rf.max()), "torque_rel_err_max": float(rt.max()),
+                          "force_rel_err_median": float(np.median(rf)), "evals_per_s": out["evals_per_s"]}}
+        from paper_2608_07307_gb300 import srp
+        for name, flag in (("comp32", srp.EVAL_SUM_COMP32), ("fp32", srp.EVAL_SUM_FP32)):
+            with torch.cuda.stream(stream):
+                ms_m = _time_call(lambda: ctx.eval_batch(mid, dirs, N=N, bounces=bounces, out=(F, T), flags=flag),
+                                  stream, flush, 1)
+                stream.synchronize()
+            ef, et = _rel_errors(F.cpu().numpy()[ks], T.cpu().numpy()[ks], Fo, To)
+            modes[name] = {"force_rel_err_max": float(ef.max()), "torque_rel_err_max": float(et.max()),
+                           "force_rel_err_median": float(np.median(ef)), "evals_per_s": 4096 / (ms_m / 1000.0)}
+        out["sum_modes"] = modes
     ctx.free_mesh(mid)
     return out
 

@@ -164,6 +164,13 @@ typedef struct {
  * that is never reached, with a 2 ms bound, so the call returns
  * SRP_ERR_TIMEOUT.  Implies SRP_EVAL_QUEUE.  For tests only. */
 #define SRP_EVAL_TEST_WAIT_TIMEOUT 128
+/* Precision report (Sec. 4.3: the paper's shaders keep compensated (Kahan)
+ * FP32 sums): the sums above the 32-ray tile, normally FP64, in compensated
+ * FP32 (each addition's exact rounding error carried in a second FP32 word,
+ * the Kahan-Babuska form) or in plain FP32.  Per-ray and per-tile sums are
+ * FP32 in every mode; only the accumulation across tiles changes. */
+#define SRP_EVAL_SUM_COMP32 256
+#define SRP_EVAL_SUM_FP32 512
 
 /* Counters of the last srp_eval_batch call (summed over its evaluations). */
 typedef struct {

@@ -705,6 +705,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         int32_t *stage = ctx->hits ? ctx->hits + s0 * R * nseg : nullptr;
         a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : ((adj || prm->n_diffuse > 0) ? stage : nullptr);
         a.walk_limit_test = (prm->flags & SRP_EVAL_TEST_WALK_BOUND) ? 1 : 0;
+        a.sum_mode = (prm->flags & SRP_EVAL_SUM_COMP32) ? 1 : ((prm->flags & SRP_EVAL_SUM_FP32) ? 2 : 0);
         if (prm->n_diffuse > 0 && nseg > 1) {
             a.n_diffuse = prm->n_diffuse;
             a.diffuse_seed = prm->diffuse_seed;

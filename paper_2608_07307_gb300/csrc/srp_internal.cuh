@@ -218,6 +218,7 @@ struct TraceArgs {
     int *dcnt;                   // [S][ray_stride] emissions of each primary ray, then their exclusive prefix
     int *dtot;                   // [S] emissions of the slot
     int walk_limit_test;         // 1: every BVH walk is bounded at one step (tests of the bound's error path)
+    int sum_mode;                // sums above the tile: 0 FP64, 1 compensated FP32, 2 plain FP32
     // work queue (queue != 0): the raster's second pass and the trace as one
     // persistent launch; qstate = [head, abort, then per slot: second-pass
     // items done, large-triangle chunks done, chunks listed]
@@ -241,7 +242,7 @@ struct DEmit {
 constexpr int kPixCand = 2;      // uncertain triangles kept per pixel (more: the ray traverses)
 constexpr int kRastSmall = 64;   // largest pixel box one thread rasterises
 constexpr int kRastChunk = 16;   // larger triangles: chunks of 16 x 16 pixels, one warp each
-constexpr int kRastBigBlocks = 2048;  // k_raster_big grid (8 warps a block, one listed chunk a warp)
+constexpr int kRastBigBlocksPerSM = 2;  // k_raster_big grid: blocks of 8 warps per SM, one listed chunk a warp
 constexpr int kBigPerSlot = 65536;  // chunk-list entries reserved per slot
 size_t trace_ctx_bytes();
 

@@ -561,6 +561,28 @@ __device__ __noinline__ Near32 nearest32_primary(const TraceCtx &B, const Ray32 
     return o;
 }
 
+// Compensated FP32 sums (the Kahan-Babuska form of compensated summation):
+// the value is hi + lo, lo collecting the exact rounding error of every
+// addition into hi (Knuth's TwoSum), so the sum keeps about twice FP32's
+// precision without FP64 arithmetic.
+struct Comp32 {
+    float hi, lo;
+};
+__device__ __forceinline__ void comp_add(Comp32 &c, float x)
+{
+    const float s = __fadd_rn(c.hi, x);
+    const float bp = __fsub_rn(s, c.hi);
+    const float e = __fadd_rn(__fsub_rn(c.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    c.hi = s;
+    c.lo = __fadd_rn(c.lo, e);
+}
+__device__ __forceinline__ void comp_merge(Comp32 &c, const Comp32 &d)
+{
+    comp_add(c, d.hi);
+    c.lo = __fadd_rn(c.lo, d.lo);
+}
+__device__ __forceinline__ float comp_value(const Comp32 &c) { return __fadd_rn(c.hi, c.lo); }
+
 __device__ inline double warp_sum(double x)
 {
     for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -1829,12 +1851,20 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
     const int t0 = b * chunk, t1 = min(t0 + chunk, nt);
     const size_t base = (size_t)s * a.n_blocks_x;
     double f[6] = {0, 0, 0, 0, 0, 0};
+    Comp32 f32[6];  // the FP32 sum modes
+    for (int k = 0; k < 6; k++) f32[k] = Comp32{0.0f, 0.0f};
+    const int mode = a.sum_mode;
     unsigned long long c[kCnt];
     for (int k = 0; k < kCnt; k++) c[k] = 0ull;
     const int kc = a.count ? kCnt : 7;  // the trace writes the traversal counters only when counting
     int mine = 0;
     for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
-        for (int k = 0; k < 6; k++) f[k] += (double)a.partials[(base + t) * 6 + k];
+        for (int k = 0; k < 6; k++) {
+            const float p = a.partials[(base + t) * 6 + k];
+            if (mode == 0) f[k] += (double)p;
+            else if (mode == 1) comp_add(f32[k], p);
+            else f32[k].hi = __fadd_rn(f32[k].hi, p);
+        }
         // count 0: the tile's hand-off flags; the re-trace below counts the rays it does
         for (int k = 1; k < kc; k++) c[k] += a.pcounts[(base + t) * kCnt + k];
         mine |= a.amb_count[base + t];
@@ -1852,19 +1882,29 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
             const int n = a.amb_count[base + t];
             for (int q = 0; q < n; q++) refine_ray(B, a, s, a.amb_list[(base + t) * kTileRays + q], acc, flags);
         }
-        for (int k = 0; k < 6; k++) f[k] += acc[k];
+        for (int k = 0; k < 6; k++) {
+            if (mode == 0) f[k] += acc[k];
+            else if (mode == 1) comp_add(f32[k], (float)acc[k]);
+            else f32[k].hi = __fadd_rn(f32[k].hi, (float)acc[k]);
+        }
         for (int k = 0; k < kCnt; k++) c[k] += (unsigned long long)acc[6 + k];
         if (flags) atomicOr(&blk_flags, flags);
         __syncthreads();
         if (threadIdx.x == 0 && blk_flags) atomicOr(&a.pose[s].flags, blk_flags);
     }
-    // block sums in a fixed order: FP64 for force and torque, integers for counts
+    // block sums in a fixed order: FP64 for force and torque (or the FP32
+    // modes' sums, threads in turn by one thread), integers for counts
     __shared__ double rf[6][8];
     __shared__ unsigned long long rc[kCnt][8];
+    __shared__ Comp32 r32[6][256];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = 0; k < 6; k++) {
-        const double x = warp_sum(f[k]);
-        if (lane == 0) rf[k][w] = x;
+    if (mode == 0) {
+        for (int k = 0; k < 6; k++) {
+            const double x = warp_sum(f[k]);
+            if (lane == 0) rf[k][w] = x;
+        }
+    } else {
+        for (int k = 0; k < 6; k++) r32[k][threadIdx.x] = f32[k];
     }
     for (int k = 0; k < kCnt; k++) {
         unsigned long long x = c[k];
@@ -1875,9 +1915,18 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
     const int nw = (int)(blockDim.x >> 5);
     double *out = a.partials1 + ((size_t)s * kRed1 + b) * kPart;
     if (threadIdx.x < 6) {
-        double x = 0.0;
-        for (int q = 0; q < nw; q++) x += rf[threadIdx.x][q];
-        out[threadIdx.x] = x;
+        if (mode == 0) {
+            double x = 0.0;
+            for (int q = 0; q < nw; q++) x += rf[threadIdx.x][q];
+            out[threadIdx.x] = x;
+        } else {
+            Comp32 x{0.0f, 0.0f};
+            for (int q = 0; q < (int)blockDim.x; q++) {
+                if (mode == 1) comp_merge(x, r32[threadIdx.x][q]);
+                else x.hi = __fadd_rn(x.hi, r32[threadIdx.x][q].hi);
+            }
+            out[threadIdx.x] = (double)comp_value(x);  // an FP32 value, exact in FP64
+        }
     } else if (threadIdx.x < kPart) {
         unsigned long long x = 0ull;
         for (int q = 0; q < nw; q++) x += rc[threadIdx.x - 6][q];
@@ -1904,9 +1953,27 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
     __shared__ double red[kPart];
     block_sum(acc, red);
     if (threadIdx.x == 0) {
-        if (a.n_diffuse > 0)
+        if (a.sum_mode != 0) {
+            // the FP32 modes: the first-level sums again, in order, in FP32
+            for (int k = 0; k < 6; k++) {
+                Comp32 x{0.0f, 0.0f};
+                for (int b = 0; b < kRed1; b++) {
+                    const float p = (float)a.partials1[((size_t)s * kRed1 + b) * kPart + k];
+                    if (a.sum_mode == 1) comp_add(x, p);
+                    else x.hi = __fadd_rn(x.hi, p);
+                }
+                if (a.n_diffuse > 0)
+                    for (int b = 0; b < kDiffBlocks; b++) {
+                        const float p = (float)a.dpart[((size_t)s * kDiffBlocks + b) * 6 + k];
+                        if (a.sum_mode == 1) comp_add(x, p);
+                        else x.hi = __fadd_rn(x.hi, p);
+                    }
+                red[k] = (double)comp_value(x);
+            }
+        } else if (a.n_diffuse > 0) {
             for (int b = 0; b < kDiffBlocks; b++)
                 for (int k = 0; k < 6; k++) red[k] += a.dpart[((size_t)s * kDiffBlocks + b) * 6 + k];
+        }
         const SlotPose &P = a.pose[s];
         double Du = ord_to_dbl(P.wmax_bits[0]) - ord_to_dbl(P.wmin_bits[0]);
         double Dv = ord_to_dbl(P.wmax_bits[1]) - ord_to_dbl(P.wmin_bits[1]);
@@ -2029,12 +2096,17 @@ cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
         cudaError_t e = cudaMemsetAsync(a.pix_key, 0xff, sizeof(unsigned long long) * px, st);
         if (e != cudaSuccess) return e;
         dim3 grid((a.rast_tris + 127) / 128, S);
+        // the chunk lists are short: a grid the size of the device, not of the list's capacity
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+        const int big_blocks = std::max(1, sms) * kRastBigBlocksPerSM;
         k_raster<0><<<grid, 128, 0, st>>>(a);
-        k_raster_chunks<<<kRastBigBlocks / 8, 256, 0, st>>>(a);
-        k_raster_big<0><<<kRastBigBlocks, 256, 0, st>>>(a);
+        k_raster_chunks<<<std::max(1, big_blocks / 4), 256, 0, st>>>(a);
+        k_raster_big<0><<<big_blocks, 256, 0, st>>>(a);
         if (!a.queue) {  // the work queue runs the second pass with the trace
             k_raster<1><<<grid, 128, 0, st>>>(a);
-            k_raster_big<1><<<kRastBigBlocks, 256, 0, st>>>(a);
+            k_raster_big<1><<<big_blocks, 256, 0, st>>>(a);
         }
     }
     return cudaGetLastError();

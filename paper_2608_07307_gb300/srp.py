@@ -28,6 +28,8 @@ EVAL_AUTOTUNE = 4
 EVAL_SERIAL = 32  # one pipeline lane: with timing, each phase's time is its own kernels' GPU time
 EVAL_QUEUE = 64  # second raster pass and trace as one persistent launch over a work queue
 EVAL_TEST_WAIT_TIMEOUT = 128  # tests of the work queue's bounded wait (SRP_ERR_TIMEOUT)
+EVAL_SUM_COMP32 = 256  # sums above the tile in compensated FP32 instead of FP64 (precision report)
+EVAL_SUM_FP32 = 512  # sums above the tile in plain FP32 (precision report)
 MAX_BOUNCES = 4
 MAX_N = 8192  # SRP_MAX_N: rays per window side
 MAX_DIFFUSE = 256  # diffuse secondary rays per hit (srp_eval_params.n_diffuse)

@@ -372,6 +372,38 @@ def test_fullsize_forces_against_stored_oracle():
             c.free_mesh(mid)
 
 
+def test_fullsize_sum_modes():
+    """The precision report's accumulation variants (Sec. 4.3 keeps compensated
+    FP32 sums): the sums above the 32-ray tile in compensated FP32
+    (SRP_EVAL_SUM_COMP32) and in plain FP32 (SRP_EVAL_SUM_FP32) on the
+    ~50k-triangle precision form at 1024^2 rays, 2 bounces.  Both stay within
+    the 1e-4 bar of the stored oracle values; the compensated sums stay within
+    1e-6 of the FP64 sums (two FP32 roundings of a compensated value per
+    evaluation, about 1.2e-7 each); the plain sums drift further from the FP64
+    sums than the compensated ones (a plain FP32 sum of ~3e4 tile values
+    gathers rounding error with their count)."""
+    from paper_2608_07307_gb300 import srp
+    rows = [r for r in _fullsize_golden() if r[0] == 0.05]
+    dirs = I.sun_dirs_fibonacci(4096)
+    ks = [r[3] for r in rows]
+    Fo = np.array([r[4][:3] for r in rows])
+    To = np.array([r[4][3:] for r in rows])
+    fn = np.linalg.norm(Fo, axis=1)
+    tn = np.maximum(np.linalg.norm(To, axis=1), fn)
+    with srp.Context(0) as c:
+        mid = c.load_mesh(I.spacecraft(0.05))
+        res = {name: c.eval_batch(mid, dirs[ks], N=1024, bounces=2, flags=f)
+               for name, f in (("fp64", 0), ("comp32", srp.EVAL_SUM_COMP32), ("fp32", srp.EVAL_SUM_FP32))}
+        c.free_mesh(mid)
+    dev = {}
+    for name, (F, T) in res.items():
+        assert np.all(np.linalg.norm(F - Fo, axis=1) <= 1e-4 * fn), name
+        assert np.all(np.linalg.norm(T - To, axis=1) <= 1e-4 * tn), name
+        dev[name] = float(np.max(np.linalg.norm(F - res["fp64"][0], axis=1) / fn))
+    assert dev["comp32"] <= 1e-6, dev
+    assert dev["fp32"] > 2.0 * dev["comp32"], dev
+
+
 def test_two_axis_box_wing_clamped_tracking(ctx):
     """The two-axis array drive (support +-90 deg carrying a hinge +-45 deg,
     Sec. 9): joint angles composed down the tree and clamped on the device;
