@@ -738,7 +738,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
         int g4 = tm.mark(ls);
         launches += 4;  // frame, trace, two reduction levels
-        if (a.raster) launches += 5;  // two raster passes over small and large triangles, chunk listing
+        if (a.raster) launches += a.queue ? 4 : 6;  // key clear, two raster passes over small and large triangles, chunk listing
         if (a.n_diffuse > 0) launches += 3;  // diffuse secondaries: emission records, their prefix, the rays
         trace_launches++;
         if (adj) {
@@ -2418,7 +2418,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     const int poll_max = p->poll > 0 ? p->poll : 16;
     // per stage: stage and acceleration, plus pose, vertices, refit, frame, the
     // raster passes, trace and two reduction levels when the SRP runs; then step control
-    const int per_step = nstage * (2 + (p->srp ? 7 + (raster ? 5 : 0) : 0)) + 1;
+    const int per_step = nstage * (2 + (p->srp ? 7 + (raster ? 6 : 0) : 0)) + 1;
     for (int64_t round = 0; round < p->max_steps + 2 && na > 0; round++) {
         int done = 0;
         CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -31,6 +31,7 @@ constexpr double kPiPose = 3.14159265358979323846;
 __global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist, double P0, int eval0, int S,
                        SlotPose *pose)
 {
+    pdl_enter();
     int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= S) return;
     SlotPose &P = pose[slot];
@@ -134,8 +135,7 @@ __global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double 
 cudaError_t launch_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist, double P0, int eval0,
                         int S, SlotPose *pose, cudaStream_t st)
 {
-    k_pose<<<(S + 31) / 32, 32, 0, st>>>(sd, sun_dirs, sun_dist, P0, eval0, S, pose);
-    return cudaGetLastError();
+    return launch_chained(k_pose, dim3((S + 31) / 32), dim3(32), 0, st, sd, sun_dirs, sun_dist, P0, eval0, S, pose);
 }
 
 // ------------------------------------------------------------- vertices
@@ -163,6 +163,7 @@ __device__ inline unsigned long long warp_max_u64(unsigned long long x)
 // FP64 projections (exact, order independent, and off the slow FP64 pipe).
 __global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *pose)
 {
+    pdl_enter();
     const int s = blockIdx.y;
     SlotPose &P = pose[s];
     const MeshDev *mesh = sd[s].mesh;
@@ -225,8 +226,7 @@ cudaError_t launch_vertices(const SlotDesc *sd, SlotPose *pose, int S, int max_v
 {
     const int per_block = 256 * kVertsPerThread;
     dim3 grid((max_verts + per_block - 1) / per_block, S);
-    k_vertices<<<grid, 256, 0, st>>>(sd, pose);
-    return cudaGetLastError();
+    return launch_chained(k_vertices, grid, dim3(256), 0, st, sd, pose);
 }
 
 // ---------------------------------------------------------------- refit

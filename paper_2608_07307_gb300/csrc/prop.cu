@@ -247,6 +247,7 @@ __device__ __forceinline__ void stage_body(PropState &X, int i, const PropDev &P
 
 __global__ void k_prop_stage(PropState *S, int n, PropDev P, int stage, double *sun_dir, double *sun_dist)
 {
+    pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;  // whole warps (blocks are multiples of 32 threads)
     stage_body(S[i], i, P, stage, threadIdx.x & 31, sun_dir, sun_dist);
@@ -276,6 +277,7 @@ __device__ __forceinline__ void accel_body(PropState &X, int i, const PropDev &P
 __global__ void k_prop_accel(PropState *S, int n, PropDev P, int stage, const double *force, const double *sun_dir,
                              const double *sun_dist)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     accel_body(S[i], i, P, stage, force, sun_dir, sun_dist);
@@ -346,6 +348,7 @@ __device__ __forceinline__ void control_body(PropState &X, int i, const PropDev 
 
 __global__ void k_prop_control(PropState *S, int n, PropDev P, int *n_done, double *h_log, int64_t h_cap)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     control_body(S[i], i, P, n_done, h_log, h_cap);
@@ -357,6 +360,7 @@ __global__ void k_prop_control(PropState *S, int n, PropDev P, int *n_done, doub
 __global__ void k_prop_step(PropState *S, int n, PropDev P, double *sun_dir, double *sun_dist, int *n_done,
                             double *h_log, int64_t h_cap)
 {
+    pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;  // whole warps
@@ -577,26 +581,22 @@ cudaError_t launch_prop_init(PropState *S, int n, const double *y0, const double
 cudaError_t launch_prop_stage(PropState *S, int n, const PropDev &P, int stage, double *sun_dir, double *sun_dist,
                               cudaStream_t st)
 {
-    k_prop_stage<<<(n + 3) / 4, 128, 0, st>>>(S, n, P, stage, sun_dir, sun_dist);  // a warp per trajectory
-    return cudaGetLastError();
+    return launch_chained(k_prop_stage, dim3((n + 3) / 4), dim3(128), 0, st, S, n, P, stage, sun_dir, sun_dist);  // a warp per trajectory
 }
 cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, const double *force, cudaStream_t st,
                               const double *sun_dir, const double *sun_dist)
 {
-    k_prop_accel<<<(n + 63) / 64, 64, 0, st>>>(S, n, P, stage, force, sun_dir, sun_dist);
-    return cudaGetLastError();
+    return launch_chained(k_prop_accel, dim3((n + 63) / 64), dim3(64), 0, st, S, n, P, stage, force, sun_dir, sun_dist);
 }
 cudaError_t launch_prop_step(PropState *S, int n, const PropDev &P, double *sun_dir, double *sun_dist, int *n_done,
                              double *h_log, int64_t h_cap, cudaStream_t st)
 {
-    k_prop_step<<<(n + 3) / 4, 128, 0, st>>>(S, n, P, sun_dir, sun_dist, n_done, h_log, h_cap);
-    return cudaGetLastError();
+    return launch_chained(k_prop_step, dim3((n + 3) / 4), dim3(128), 0, st, S, n, P, sun_dir, sun_dist, n_done, h_log, h_cap);
 }
 cudaError_t launch_prop_control(PropState *S, int n, const PropDev &P, int *n_done, double *h_log, int64_t h_cap,
                                 cudaStream_t st)
 {
-    k_prop_control<<<(n + 63) / 64, 64, 0, st>>>(S, n, P, n_done, h_log, h_cap);
-    return cudaGetLastError();
+    return launch_chained(k_prop_control, dim3((n + 63) / 64), dim3(64), 0, st, S, n, P, n_done, h_log, h_cap);
 }
 
 cudaError_t launch_prop_ckpt(PropState *S, int n, double *buf, bool save, double h0, cudaStream_t st)

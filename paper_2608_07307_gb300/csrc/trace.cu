@@ -125,6 +125,7 @@ __device__ __forceinline__ double pickd(double x, double y, double z, int k) { r
 // ------------------------------------------------------------- k_frame
 __global__ void k_frame(TraceArgs a)
 {
+    pdl_enter();
     const int s = blockIdx.x;
     const SlotDesc &D = a.sd[s];
     const MeshDev *m = D.mesh;
@@ -832,6 +833,7 @@ __device__ __forceinline__ void raster_tri(const TraceArgs &a, int s, int t)
 template <int PASS>
 __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
 {
+    pdl_enter();
     raster_tri<PASS>(a, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -839,6 +841,7 @@ __global__ void __launch_bounds__(128) k_raster(TraceArgs a)
 // tested a chunk per lane and appended with one atomic per warp pass.
 __global__ void __launch_bounds__(256) k_raster_chunks(TraceArgs a)
 {
+    pdl_enter();
     const unsigned n = min(__ldcg(a.bigt_count), (unsigned)a.big_cap);
     const unsigned lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x >> 5);
     for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) {
@@ -912,6 +915,7 @@ __device__ __forceinline__ int raster_big_entry(const TraceArgs &a, unsigned e, 
 template <int PASS>
 __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
 {
+    pdl_enter();
     const unsigned n = min(__ldcg(a.big_count), (unsigned)a.big_cap);
     const unsigned lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x >> 5);
     for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) raster_big_entry<PASS>(a, e, lane);
@@ -1131,6 +1135,7 @@ __device__ __forceinline__ void trace_block(const TraceArgs &a, int vb, TraceCtx
 template <bool COUNT, bool HITS>
 __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_trace(TraceArgs a)
 {
+    pdl_enter();
     __shared__ TraceCtx B;
     __shared__ int s_cand[kCand * kLaneStride];
     __shared__ int s_hpt[(kMaxBounces + 1) * kLaneStride];
@@ -1220,6 +1225,7 @@ __device__ void trace_block_empty(const TraceArgs &a, int vb)
 template <bool COUNT, bool HITS>
 __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_queue(TraceArgs a)
 {
+    pdl_enter();
     __shared__ TraceCtx B;
     __shared__ int s_cand[kCand * kLaneStride];
     __shared__ int s_hpt[(kMaxBounces + 1) * kLaneStride];
@@ -1701,6 +1707,7 @@ __device__ __forceinline__ void diffuse_sample(const TraceCtx &B, unsigned long 
 // dense array, and the number of records.
 __global__ void __launch_bounds__(kLaneStride) k_demit(TraceArgs a)
 {
+    pdl_enter();
     __shared__ TraceCtx B;
     const int s = blockIdx.y;
     load_ctx(B, a, s);
@@ -1763,6 +1770,7 @@ __global__ void __launch_bounds__(kLaneStride) k_demit(TraceArgs a)
 // ranges in order) and the slot's total.
 __global__ void __launch_bounds__(1024) k_dscan(TraceArgs a)
 {
+    pdl_enter();
     __shared__ int part[1024];
     const int s = blockIdx.x;
     const size_t R = (size_t)a.sd[s].N * a.sd[s].N;
@@ -1793,6 +1801,7 @@ __global__ void __launch_bounds__(1024) k_dscan(TraceArgs a)
 // record of item e K + q is found by binary search over the prefix.
 __global__ void __launch_bounds__(kLaneStride) k_diffuse(TraceArgs a)
 {
+    pdl_enter();
     __shared__ TraceCtx B;
     __shared__ double red[4][6];
     __shared__ int s_cand[kCand * kLaneStride];  // per-thread candidate columns (see Cands)
@@ -1844,6 +1853,7 @@ __global__ void __launch_bounds__(kLaneStride) k_diffuse(TraceArgs a)
 // strided set of tiles in order, so the sums are reproducible.
 __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
 {
+    pdl_enter();
     const int s = blockIdx.y, b = blockIdx.x;
     if (a.pose[s].skip) return;  // uniform over the block
     const int nt = a.sd[s].tiles;
@@ -1940,6 +1950,7 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
 __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *force, double *torque, int *err_flags,
                                                 unsigned long long *stats_accum)
 {
+    pdl_enter();
     const int s = blockIdx.x;
     if (a.pose[s].skip) {
         // a skipped evaluation outputs zero force and torque
@@ -2086,30 +2097,46 @@ cudaError_t launch_bvh_check(const unsigned char *tctx, int n_parts, int *tri_se
 }
 
 // ------------------------------------------------------------ launchers
+// All-ones pixel keys (no hit, no candidate) before the first raster pass.
+__global__ void __launch_bounds__(256) k_clear_keys(unsigned long long *key, size_t n)
+{
+    pdl_enter();
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        key[i] = ~0ull;
+}
+
+static int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return std::max(1, sms);
+}
+
 cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
 {
-    k_frame<<<S, 32, 0, st>>>(a);
-    if (a.n_tiles <= 0) return cudaGetLastError();
+    cudaError_t e = launch_chained(k_frame, dim3(S), dim3(32), 0, st, a);
+    if (e != cudaSuccess || a.n_tiles <= 0) return e;
     if (a.raster && a.rast_tris > 0) {
-        // cleared pixel buffers of the launch's slots
+        const int sms = device_sms();
+        // cleared pixel keys of the launch's slots (a kernel, so that the chain stays programmatic)
         const size_t px = (size_t)S * a.ray_stride;
-        cudaError_t e = cudaMemsetAsync(a.pix_key, 0xff, sizeof(unsigned long long) * px, st);
+        const size_t kb = std::min((px + 255) / 256, (size_t)sms * 8);
+        e = launch_chained(k_clear_keys, dim3((unsigned)std::max<size_t>(1, kb)), dim3(256), 0, st, a.pix_key, px);
         if (e != cudaSuccess) return e;
-        dim3 grid((a.rast_tris + 127) / 128, S);
+        const dim3 grid((a.rast_tris + 127) / 128, S);
         // the chunk lists are short: a grid the size of the device, not of the list's capacity
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms = 1;
-        const int big_blocks = std::max(1, sms) * kRastBigBlocksPerSM;
-        k_raster<0><<<grid, 128, 0, st>>>(a);
-        k_raster_chunks<<<std::max(1, big_blocks / 4), 256, 0, st>>>(a);
-        k_raster_big<0><<<big_blocks, 256, 0, st>>>(a);
+        const int big_blocks = sms * kRastBigBlocksPerSM;
+        if ((e = launch_chained(k_raster<0>, grid, dim3(128), 0, st, a)) != cudaSuccess) return e;
+        if ((e = launch_chained(k_raster_chunks, dim3(std::max(1, big_blocks / 4)), dim3(256), 0, st, a)) != cudaSuccess)
+            return e;
+        if ((e = launch_chained(k_raster_big<0>, dim3(big_blocks), dim3(256), 0, st, a)) != cudaSuccess) return e;
         if (!a.queue) {  // the work queue runs the second pass with the trace
-            k_raster<1><<<grid, 128, 0, st>>>(a);
-            k_raster_big<1><<<big_blocks, 256, 0, st>>>(a);
+            if ((e = launch_chained(k_raster<1>, grid, dim3(128), 0, st, a)) != cudaSuccess) return e;
+            if ((e = launch_chained(k_raster_big<1>, dim3(big_blocks), dim3(256), 0, st, a)) != cudaSuccess) return e;
         }
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
@@ -2121,42 +2148,26 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
     const dim3 g(a.n_tiles), b(kTileRays * kTraceWarps);
     if (a.queue) {
         // persistent: as many blocks as fit on the device at once
-        int dev = 0, sms = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        const dim3 gq(std::max(1, sms) * kQueueBlocksPerSM);
-        if (a.count) {
-            if (a.hits) k_queue<true, true><<<gq, b, 0, st>>>(a);
-            else k_queue<true, false><<<gq, b, 0, st>>>(a);
-        } else {
-            if (a.hits) k_queue<false, true><<<gq, b, 0, st>>>(a);
-            else k_queue<false, false><<<gq, b, 0, st>>>(a);
-        }
-        return cudaGetLastError();
+        const dim3 gq(device_sms() * kQueueBlocksPerSM);
+        if (a.count) return launch_chained(a.hits ? k_queue<true, true> : k_queue<true, false>, gq, b, 0, st, a);
+        return launch_chained(a.hits ? k_queue<false, true> : k_queue<false, false>, gq, b, 0, st, a);
     }
-    if (a.count) {
-        if (a.hits) k_trace<true, true><<<g, b, 0, st>>>(a);
-        else k_trace<true, false><<<g, b, 0, st>>>(a);
-    } else {
-        if (a.hits) k_trace<false, true><<<g, b, 0, st>>>(a);
-        else k_trace<false, false><<<g, b, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    if (a.count) return launch_chained(a.hits ? k_trace<true, true> : k_trace<true, false>, g, b, 0, st, a);
+    return launch_chained(a.hits ? k_trace<false, true> : k_trace<false, false>, g, b, 0, st, a);
 }
 
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
                           unsigned long long *stats_accum, cudaStream_t st)
 {
-    k_reduce1<<<dim3(kRed1, S), 256, 0, st>>>(a);
+    cudaError_t e = launch_chained(k_reduce1, dim3(kRed1, S), dim3(256), 0, st, a);
+    if (e != cudaSuccess) return e;
     // diffuse secondaries after the FP64 re-trace (which records the hits of the rays it takes)
     if (a.n_diffuse > 0) {
-        k_demit<<<dim3(kDiffBlocks, S), kLaneStride, 0, st>>>(a);
-        k_dscan<<<S, 1024, 0, st>>>(a);
-        k_diffuse<<<dim3(kDiffBlocks, S), kLaneStride, 0, st>>>(a);
+        if ((e = launch_chained(k_demit, dim3(kDiffBlocks, S), dim3(kLaneStride), 0, st, a)) != cudaSuccess) return e;
+        if ((e = launch_chained(k_dscan, dim3(S), dim3(1024), 0, st, a)) != cudaSuccess) return e;
+        if ((e = launch_chained(k_diffuse, dim3(kDiffBlocks, S), dim3(kLaneStride), 0, st, a)) != cudaSuccess) return e;
     }
-    k_reduce<<<S, 256, 0, st>>>(a, eval0, force, torque, err_flags, stats_accum);
-    return cudaGetLastError();
+    return launch_chained(k_reduce, dim3(S), dim3(256), 0, st, a, eval0, force, torque, err_flags, stats_accum);
 }
 
 }  // namespace srp
