@@ -54,6 +54,8 @@ struct srp_ctx {
     size_t amb_list_cap = 0;
     double *partials1 = nullptr;
     size_t partials1_cap = 0;
+    unsigned *red_ticket = nullptr;
+    size_t red_ticket_cap = 0;
     double *dpart = nullptr;  // diffuse-ray partial sums [SL][kDiffBlocks][6]
     size_t dpart_cap = 0;
     DEmit *demit = nullptr;   // diffuse emission records [SL][R][nseg - 1]
@@ -595,6 +597,7 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
     CK(ctx, grow(&ctx->pcounts, &ctx->pcounts_cap, SL * pl.nbx * kCnt, false));
     CK(ctx, grow(&ctx->amb_list, &ctx->amb_list_cap, SL * pl.nbx * kTileRays, false));
     CK(ctx, grow(&ctx->partials1, &ctx->partials1_cap, SL * kRed1 * kPart, false));
+    CK(ctx, grow(&ctx->red_ticket, &ctx->red_ticket_cap, SL, true));
     CK(ctx, grow(&ctx->tctx, &ctx->tctx_cap, SL * trace_ctx_bytes(), false));
     CK(ctx, grow(&ctx->amb_count, &ctx->amb_count_cap, SL * pl.nbx, false));
     if (!(prm->flags & SRP_EVAL_TRAVERSE)) {
@@ -680,6 +683,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         a.partials = ctx->partials + s0 * nbx * 6;
         a.pcounts = ctx->pcounts + s0 * nbx * kCnt;
         a.partials1 = ctx->partials1 + s0 * kRed1 * kPart;
+        a.red_ticket = ctx->red_ticket + s0;
         a.tctx = ctx->tctx + s0 * trace_ctx_bytes();
         a.amb_list = ctx->amb_list + s0 * nbx * kTileRays;
         a.amb_count = ctx->amb_count + s0 * nbx;
@@ -737,7 +741,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         int g3 = g2;  // the FP64 re-trace of overflowing rays runs inside the first reduction level
         CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
         int g4 = tm.mark(ls);
-        launches += 4;  // frame, trace, two reduction levels
+        launches += a.n_diffuse > 0 ? 4 : 3;  // frame, trace, the reduction (two levels in one launch without diffuse rays)
         if (a.raster) launches += a.queue ? 4 : 6;  // key clear, two raster passes over small and large triangles, chunk listing
         if (a.n_diffuse > 0) launches += 3;  // diffuse secondaries: emission records, their prefix, the rays
         trace_launches++;
@@ -975,6 +979,7 @@ void srp_destroy(srp_ctx *ctx)
     dfree(ctx->pcounts);
     dfree(ctx->amb_list);
     dfree(ctx->partials1);
+    dfree(ctx->red_ticket);
     dfree(ctx->dpart);
     dfree(ctx->demit);
     dfree(ctx->dcnt);
@@ -1565,16 +1570,15 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
             cudaSuccess)
             crc = SRP_ERR_CUDA;
     } else {
+        // a step starts from its first stage's state, made by the previous step's
+        // last launch (or, before the first step, by the launch after the capture)
         for (int sg = 0; sg < nstage && crc == SRP_OK; sg++) {
-            if (launch_prop_stage(S, n, P, sg, d_sun, d_dist, st) != cudaSuccess) { crc = SRP_ERR_CUDA; break; }
             crc = eval_enqueue(ctx, m, &p->eval, pl, n, d_sun, d_dist, d_f, d_t, nullptr, false, off, launches,
                                trace_launches);
-            if (crc == SRP_OK && launch_prop_accel(S, n, P, sg, d_f, st, d_sun, d_dist) != cudaSuccess)
+            if (crc == SRP_OK && launch_prop_next(S, n, P, sg, d_f, d_sun, d_dist, ctx->prop_done,
+                                                  h_log ? ctx->prop_hlog : nullptr, h_cap, st) != cudaSuccess)
                 crc = SRP_ERR_CUDA;
         }
-        if (crc == SRP_OK &&
-            launch_prop_control(S, n, P, ctx->prop_done, h_log ? ctx->prop_hlog : nullptr, h_cap, st) != cudaSuccess)
-            crc = SRP_ERR_CUDA;
     }
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (crc != SRP_OK || ce != cudaSuccess) {
@@ -1585,6 +1589,10 @@ srp_status srp_propagate(srp_ctx *ctx, int32_t mesh_id, const srp_prop_params *p
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return fail(ctx, SRP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    if (trace && launch_prop_stage(S, n, P, 0, d_sun, d_dist, st) != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return fail(ctx, SRP_ERR_CUDA, "first stage launch failed");
+    }
     // relaunch until every trajectory is done.  Each round launches about as many
     // steps as the furthest trajectory still needs at its current step size
     // (at most `poll`), so finished work is rarely repeated; finished and
@@ -2211,6 +2219,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     unsigned char *tctx;
     float *part;
     double *part1;
+    unsigned *rticket;
     int *alist, *acount, *rbad;
     unsigned long long *pkey;
     unsigned *pcand, *bcount, *pcnt_blk;
@@ -2241,6 +2250,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     CK(ctx, dmalloc(owned, &part, (size_t)n * nbx * 6));
     CK(ctx, dmalloc(owned, &pcnt_blk, (size_t)n * nbx * kCnt));
     CK(ctx, dmalloc(owned, &part1, (size_t)n * kRed1 * kPart));
+    CK(ctx, dmalloc(owned, &rticket, (size_t)n));
     CK(ctx, dmalloc(owned, &alist, (size_t)n * nbx * kTileRays));
     CK(ctx, dmalloc(owned, &acount, (size_t)n * nbx));
     CK(ctx, dmalloc(owned, &sd, (size_t)n));
@@ -2355,6 +2365,7 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         a.partials = part;
         a.pcounts = pcnt_blk;
         a.partials1 = part1;
+        a.red_ticket = rticket;
         a.amb_list = alist;
         a.amb_count = acount;
         a.ray_stride = Rmax;
@@ -2379,8 +2390,11 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         cudaGraph_t graph = nullptr;
         CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
+        // without ray tracing a stage's acceleration and the next stage share no
+        // launch; with it, a step starts from its first stage's state, made by the
+        // previous step's last launch or by the launch after this capture
         for (int sg = 0; sg < nstage && e == cudaSuccess; sg++) {
-            e = launch_prop_stage(S, na, P, sg, d_sun, d_dist, st);
+            if (!p->srp) e = launch_prop_stage(S, na, P, sg, d_sun, d_dist, st);
             if (p->srp) {
                 if (e == cudaSuccess) e = launch_pose(sd, d_sun, d_dist, p->eval.P0, 0, na, pose, st);
                 if (e == cudaSuccess) e = launch_vertices(sd, pose, na, mv, st);
@@ -2393,10 +2407,12 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_refit_join[0], 0);
                 if (e == cudaSuccess) e = launch_trace(a, na, st);
                 if (e == cudaSuccess) e = launch_reduce(a, na, 0, d_f, d_t, ctx->err_flags, nullptr, st);
+                if (e == cudaSuccess) e = launch_prop_next(S, na, P, sg, d_f, d_sun, d_dist, ctx->prop_done, nullptr, 0, st);
+            } else if (e == cudaSuccess) {
+                e = launch_prop_accel(S, na, P, sg, d_f, st);
             }
-            if (e == cudaSuccess) e = launch_prop_accel(S, na, P, sg, d_f, st);
         }
-        if (e == cudaSuccess) e = launch_prop_control(S, na, P, ctx->prop_done, nullptr, 0, st);
+        if (e == cudaSuccess && !p->srp) e = launch_prop_control(S, na, P, ctx->prop_done, nullptr, 0, st);
         cudaError_t ce = cudaStreamEndCapture(st, &graph);
         if (e != cudaSuccess || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -2410,15 +2426,18 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) return fail(ctx, SRP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
         graphs++;
+        // the first stage of the running trajectories' next step, in their (new) slots
+        if (p->srp) CK(ctx, launch_prop_stage(S, na, P, 0, d_sun, d_dist, st));
         return SRP_OK;
     };
     int na = n;
     srp_status rc = capture(na);
     if (rc) return rc;
     const int poll_max = p->poll > 0 ? p->poll : 16;
-    // per stage: stage and acceleration, plus pose, vertices, refit, frame, the
-    // raster passes, trace and two reduction levels when the SRP runs; then step control
-    const int per_step = nstage * (2 + (p->srp ? 7 + (raster ? 6 : 0) : 0)) + 1;
+    // per stage with the SRP: pose, vertices, refit, frame, the raster passes
+    // and their key clear, trace, the reduction, then the acceleration with
+    // the next stage (control at the last); without it stage, acceleration, and control
+    const int per_step = p->srp ? nstage * (1 + 6 + (raster ? 6 : 0)) : nstage * 2 + 1;
     for (int64_t round = 0; round < p->max_steps + 2 && na > 0; round++) {
         int done = 0;
         CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -1,6 +1,6 @@
 // pose.cu -- per-evaluation geometry update (Sec. 4.4.2) and window bounds.
 //
-//   k_pose      one thread per evaluation slot: joint angles (Sun tracking,
+//   k_pose      a warp per evaluation slot, a lane per part: joint angles (Sun tracking,
 //               commanded, or tracking + offset; clamped), part transforms
 //               composed down the kinematic tree (Sec. 4.4.1), image-plane
 //               basis, window accumulators reset.
@@ -28,93 +28,113 @@ __device__ inline void rot_axis_cs(const double *a, double c, double s, double *
 
 constexpr double kPiPose = 3.14159265358979323846;
 
-__global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist, double P0, int eval0, int S,
-                       SlotPose *pose)
+__global__ void __launch_bounds__(32) k_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist,
+                                             double P0, int eval0, int S, SlotPose *pose)
 {
     pdl_enter();
-    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    // a warp per slot, a lane per part: the parts of one tree level are posed
+    // together (their FP64 chains overlap), each reading its parent's transform
+    // from shared memory
+    const int slot = blockIdx.x, lane = threadIdx.x;
     if (slot >= S) return;
+    __shared__ double sM[kMaxParts][9], sT[kMaxParts][3];
     SlotPose &P = pose[slot];
     const MeshDev *mesh = sd[slot].mesh;
     const double *angles = sd[slot].angles;
     const int panel_mode = sd[slot].panel_mode;
-    int e = eval0 + slot;
+    const int e = eval0 + slot;
     double s[3] = {sun_dirs[3 * e], sun_dirs[3 * e + 1], sun_dirs[3 * e + 2]};
-    double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    const double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
     for (int k = 0; k < 3; k++) s[k] /= sn;
-    double dist = sun_dist ? sun_dist[e] : 1.0;
-    P.eval = e;
-    P.flags = 0;
-    P.s_norm = sn;
-    P.free_mask = 0;
-    P.track_mask = 0;
-    P.skip = dist < 0.0 ? 1 : 0;  // a negative distance asks to skip this evaluation
-    if (P.skip) return;
-    int np = mesh->n_parts;
-    // the parts' transforms are composed in this thread's own (L1-cached) copy
-    // and stored to the slot's pose as they are done: a parent's transform is
-    // read back from here, not from global memory
-    double Ml[kMaxParts][9], Tl[kMaxParts][3];
-    for (int p = 0; p < np; p++) {
-        const PartInfo &pi = mesh->part[p];
-        double th = 0.0;
-        double *M = Ml[p], *T = Tl[p];
-        if (p == 0) {
-            for (int k = 0; k < 9; k++) M[k] = (k % 4 == 0) ? 1.0 : 0.0;
-            T[0] = T[1] = T[2] = 0.0;
+    const double dist = sun_dist ? sun_dist[e] : 1.0;
+    const int skip = dist < 0.0 ? 1 : 0;  // a negative distance asks to skip this evaluation
+    if (lane == 0) {
+        P.eval = e;
+        P.flags = 0;
+        P.s_norm = sn;
+        P.free_mask = 0;
+        P.track_mask = 0;
+        P.skip = skip;
+    }
+    if (skip) return;
+    const int np = mesh->n_parts;
+    const int p = lane;
+    PartInfo pi{};
+    if (p < np) pi = mesh->part[p];
+    // depth of each part in the kinematic tree (parents precede children)
+    const int par = (p < np && p > 0) ? pi.parent : -1;
+    int depth = 0;
+    for (int q = par, it = 0; it < kMaxParts && __any_sync(0xffffffffu, q >= 0); it++) {
+        const int up = __shfl_sync(0xffffffffu, par, q >= 0 ? q : 0);
+        if (q >= 0) depth++;
+        q = q >= 0 ? up : -1;
+    }
+    const int levels = __reduce_max_sync(0xffffffffu, p < np ? depth : 0);
+    bool track = false, freej = false;
+    for (int L = 0; L <= levels; L++) {
+        if (p < np && depth == L) {
+            double *M = sM[p], *T = sT[p];
+            if (p == 0) {
+                for (int k = 0; k < 9; k++) M[k] = (k % 4 == 0) ? 1.0 : 0.0;
+                T[0] = T[1] = T[2] = 0.0;
+            } else {
+                const double *Mq = sM[par], *Tq = sT[par];
+                // cosine and sine of the joint angle: from the tracking direction itself
+                // when the limits cannot clamp it (no FP64 transcendentals), else from the angle
+                double th = 0.0, cth = 1.0, sth = 0.0;
+                bool have_cs = false;
+                if (pi.movable) {
+                    if (panel_mode != SRP_PANELS_SET) {
+                        // Sun in the parent's current frame: Mq^T s
+                        double sl[3];
+                        for (int k = 0; k < 3; k++) sl[k] = Mq[k] * s[0] + Mq[3 + k] * s[1] + Mq[6 + k] * s[2];
+                        const double *a = pi.axis, *n0 = pi.n0;
+                        const double na = n0[0] * a[0] + n0[1] * a[1] + n0[2] * a[2];
+                        const double n[3] = {n0[0] - na * a[0], n0[1] - na * a[1], n0[2] - na * a[2]};
+                        const double b[3] = {a[1] * n[2] - a[2] * n[1], a[2] * n[0] - a[0] * n[2], a[0] * n[1] - a[1] * n[0]};
+                        const double x = n[0] * sl[0] + n[1] * sl[1] + n[2] * sl[2];
+                        const double y = b[0] * sl[0] + b[1] * sl[1] + b[2] * sl[2];
+                        track = !(x == 0.0 && y == 0.0);
+                        const bool plain = panel_mode == SRP_PANELS_TRACK || !angles;
+                        if (plain && pi.lim[0] <= -kPiPose && pi.lim[1] >= kPiPose && !(x < 0.0 && fabs(y) <= 1e-12 * -x)) {
+                            // atan2(y, x) lies strictly inside (-pi, pi): never clamped, always free
+                            const double r = sqrt(x * x + y * y);
+                            if (r > 0.0) { cth = x / r; sth = y / r; }
+                            have_cs = true;
+                            freej = true;
+                        }
+                        th = (x == 0.0 && y == 0.0) ? 0.0 : (have_cs ? 0.0 : atan2(y, x));
+                        if (panel_mode == SRP_PANELS_TRACK_OFFSET && angles) th += angles[p];
+                    } else {
+                        th = angles ? angles[p] : 0.0;
+                    }
+                    if (!have_cs) {
+                        if (th > pi.lim[0] && th < pi.lim[1]) freej = true;
+                        th = fmin(fmax(th, pi.lim[0]), pi.lim[1]);
+                        sincos(th, &sth, &cth);
+                    }
+                }
+                double R[9];
+                if (pi.movable) rot_axis_cs(pi.axis, cth, sth, R);
+                else for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++)
+                        M[3 * i + j] = Mq[3 * i] * R[j] + Mq[3 * i + 1] * R[3 + j] + Mq[3 * i + 2] * R[6 + j];
+                const double *pv = pi.pivot;
+                double w[3];
+                for (int i = 0; i < 3; i++) w[i] = pv[i] - (R[3 * i] * pv[0] + R[3 * i + 1] * pv[1] + R[3 * i + 2] * pv[2]);
+                for (int i = 0; i < 3; i++) T[i] = Mq[3 * i] * w[0] + Mq[3 * i + 1] * w[1] + Mq[3 * i + 2] * w[2] + Tq[i];
+            }
             for (int k = 0; k < 9; k++) P.M[p][k] = M[k];
             for (int k = 0; k < 3; k++) P.T[p][k] = T[k];
-            continue;
         }
-        int q = pi.parent;
-        const double *Mq = Ml[q], *Tq = Tl[q];
-        // cosine and sine of the joint angle: from the tracking direction itself
-        // when the limits cannot clamp it (no FP64 transcendentals), else from the angle
-        double cth = 1.0, sth = 0.0;
-        bool have_cs = false;
-        if (pi.movable) {
-            if (panel_mode != SRP_PANELS_SET) {
-                // Sun in the parent's current frame: Mq^T s
-                double sl[3];
-                for (int k = 0; k < 3; k++) sl[k] = Mq[k] * s[0] + Mq[3 + k] * s[1] + Mq[6 + k] * s[2];
-                const double *a = pi.axis, *n0 = pi.n0;
-                double na = n0[0] * a[0] + n0[1] * a[1] + n0[2] * a[2];
-                double n[3] = {n0[0] - na * a[0], n0[1] - na * a[1], n0[2] - na * a[2]};
-                double b[3] = {a[1] * n[2] - a[2] * n[1], a[2] * n[0] - a[0] * n[2], a[0] * n[1] - a[1] * n[0]};
-                double x = n[0] * sl[0] + n[1] * sl[1] + n[2] * sl[2];
-                double y = b[0] * sl[0] + b[1] * sl[1] + b[2] * sl[2];
-                if (!(x == 0.0 && y == 0.0)) P.track_mask |= 1u << p;
-                const bool plain = panel_mode == SRP_PANELS_TRACK || !angles;
-                if (plain && pi.lim[0] <= -kPiPose && pi.lim[1] >= kPiPose && !(x < 0.0 && fabs(y) <= 1e-12 * -x)) {
-                    // atan2(y, x) lies strictly inside (-pi, pi): never clamped, always free
-                    const double r = sqrt(x * x + y * y);
-                    if (r > 0.0) { cth = x / r; sth = y / r; }
-                    have_cs = true;
-                    P.free_mask |= 1u << p;
-                }
-                th = (x == 0.0 && y == 0.0) ? 0.0 : (have_cs ? 0.0 : atan2(y, x));
-                if (panel_mode == SRP_PANELS_TRACK_OFFSET && angles) th += angles[p];
-            } else {
-                th = angles ? angles[p] : 0.0;
-            }
-            if (!have_cs) {
-                if (th > pi.lim[0] && th < pi.lim[1]) P.free_mask |= 1u << p;
-                th = fmin(fmax(th, pi.lim[0]), pi.lim[1]);
-                sincos(th, &sth, &cth);
-            }
-        }
-        double R[9];
-        if (pi.movable) rot_axis_cs(pi.axis, cth, sth, R);
-        else for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.0 : 0.0;
-        for (int i = 0; i < 3; i++)
-            for (int j = 0; j < 3; j++) M[3 * i + j] = Mq[3 * i] * R[j] + Mq[3 * i + 1] * R[3 + j] + Mq[3 * i + 2] * R[6 + j];
-        const double *pv = pi.pivot;
-        double w[3];
-        for (int i = 0; i < 3; i++) w[i] = pv[i] - (R[3 * i] * pv[0] + R[3 * i + 1] * pv[1] + R[3 * i + 2] * pv[2]);
-        for (int i = 0; i < 3; i++) T[i] = Mq[3 * i] * w[0] + Mq[3 * i + 1] * w[1] + Mq[3 * i + 2] * w[2] + Tq[i];
-        for (int k = 0; k < 9; k++) P.M[p][k] = M[k];
-        for (int k = 0; k < 3; k++) P.T[p][k] = T[k];
+        __syncwarp();
     }
+    const unsigned track_mask = __ballot_sync(0xffffffffu, track);
+    const unsigned free_mask = __ballot_sync(0xffffffffu, freej);
+    if (lane != 0) return;
+    P.track_mask = track_mask;
+    P.free_mask = free_mask;
     // basis of the image plane around d = -s (Duff et al., JCGT 2017)
     double d[3] = {-s[0], -s[1], -s[2]};
     double sg = copysign(1.0, d[2]);
@@ -128,14 +148,12 @@ __global__ void k_pose(const SlotDesc *sd, const double *sun_dirs, const double 
         P.wmax_bits[k] = dbl_to_ord(-INFINITY);
     }
     P.scale = P0 / (dist * dist);
-    P.eval = e;
-    P.flags = 0;
 }
 
 cudaError_t launch_pose(const SlotDesc *sd, const double *sun_dirs, const double *sun_dist, double P0, int eval0,
                         int S, SlotPose *pose, cudaStream_t st)
 {
-    return launch_chained(k_pose, dim3((S + 31) / 32), dim3(32), 0, st, sd, sun_dirs, sun_dist, P0, eval0, S, pose);
+    return launch_chained(k_pose, dim3(S), dim3(32), 0, st, sd, sun_dirs, sun_dist, P0, eval0, S, pose);
 }
 
 // ------------------------------------------------------------- vertices

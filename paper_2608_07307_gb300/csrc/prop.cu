@@ -354,6 +354,29 @@ __global__ void k_prop_control(PropState *S, int n, PropDev P, int *n_done, doub
     control_body(S[i], i, P, n_done, h_log, h_cap);
 }
 
+// The stage derivative of `stage` and, in the same launch, the state of the
+// next stage; after the last stage, step control and the first stage of the
+// next step (which the captured step then starts from).  A warp per trajectory.
+__global__ void k_prop_next(PropState *S, int n, PropDev P, int stage, const double *force, double *sun_dir,
+                            double *sun_dist, int *n_done, double *h_log, int64_t h_cap)
+{
+    pdl_enter();
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;  // whole warps
+    PropState &X = S[i];
+    const int nst = P.method == 1 ? 4 : 13;
+    if (lane == 0) accel_body(X, i, P, stage, force, sun_dir, sun_dist);
+    __syncwarp();
+    if (stage + 1 < nst) {
+        stage_body(X, i, P, stage + 1, lane, sun_dir, sun_dist);
+        return;
+    }
+    if (lane == 0) control_body(X, i, P, n_done, h_log, h_cap);
+    __syncwarp();
+    stage_body(X, i, P, 0, lane, sun_dir, sun_dist);
+}
+
 // A whole step in one launch when no ray-traced evaluation sits between the
 // stages (SPAD table or SRP off): the stage, acceleration and control parts of
 // the kernels above, in their order, a warp per trajectory.
@@ -587,6 +610,12 @@ cudaError_t launch_prop_accel(PropState *S, int n, const PropDev &P, int stage, 
                               const double *sun_dir, const double *sun_dist)
 {
     return launch_chained(k_prop_accel, dim3((n + 63) / 64), dim3(64), 0, st, S, n, P, stage, force, sun_dir, sun_dist);
+}
+cudaError_t launch_prop_next(PropState *S, int n, const PropDev &P, int stage, const double *force, double *sun_dir,
+                             double *sun_dist, int *n_done, double *h_log, int64_t h_cap, cudaStream_t st)
+{
+    return launch_chained(k_prop_next, dim3((n + 3) / 4), dim3(128), 0, st, S, n, P, stage, force, sun_dir, sun_dist,
+                          n_done, h_log, h_cap);
 }
 cudaError_t launch_prop_step(PropState *S, int n, const PropDev &P, double *sun_dir, double *sun_dist, int *n_done,
                              double *h_log, int64_t h_cap, cudaStream_t st)

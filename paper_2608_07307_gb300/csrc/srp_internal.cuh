@@ -222,6 +222,7 @@ struct TraceArgs {
     float *partials;             // [S][n_blocks_x][6] force and torque per tile (FP32 tile sums)
     unsigned *pcounts;           // [S][n_blocks_x][kCnt] counts 6..19 per tile
     double *partials1;           // [S][kRed1][kPart] first-level sums of the tile partials
+    unsigned *red_ticket;        // [S] first-level blocks done (the last one adds their sums); reset by the frame kernel
     int *amb_list;               // [S][n_blocks_x][kTileRays] rays handed to the FP64 path, per tile
     int *amb_count;              // [S][n_blocks_x]
     int32_t *hits;               // [S][ray_stride][seg_stride] or null
@@ -458,6 +459,10 @@ cudaError_t launch_prop_step(PropState *S, int n, const PropDev &P, double *sun_
 cudaError_t launch_spad_dirs(const SpadDev &g, double *dirs, cudaStream_t st);
 cudaError_t launch_spad_eval(const SpadDev &g, int n, const double *dirs, const double *dist, double *force,
                              double *torque, cudaStream_t st);
+// The acceleration of `stage`, then the next stage's state; after the last
+// stage, step control and the next step's first stage (captured steps).
+cudaError_t launch_prop_next(PropState *S, int n, const PropDev &P, int stage, const double *force, double *sun_dir,
+                             double *sun_dist, int *n_done, double *h_log, int64_t h_cap, cudaStream_t st);
 cudaError_t launch_prop_control(PropState *S, int n, const PropDev &P, int *n_done, double *h_log, int64_t h_cap,
                                 cudaStream_t st);
 // propagation adjoint (RK4): checkpoints, stage records, reverse stage sweep

@@ -126,15 +126,49 @@ __device__ __forceinline__ double pickd(double x, double y, double z, int k) { r
 __global__ void k_frame(TraceArgs a)
 {
     pdl_enter();
-    const int s = blockIdx.x;
+    // every load first, then the arithmetic and the stores: a load placed after
+    // a store it might alias waits for everything before it, and a chain of such
+    // round trips, not the arithmetic, would set this kernel's duration
+    const int s = blockIdx.x, lane = threadIdx.x;
     const SlotDesc &D = a.sd[s];
     const MeshDev *m = D.mesh;
-    const SlotBufs &sb = D.sb;
+    const SlotBufs sb = D.sb;
     const int N = D.N;
     const SlotPose &P = a.pose[s];
+    const int skip = P.skip;
+    const int np = m->n_parts;
+    PartInfo pi{};
+    if (lane < kMaxParts) pi = m->part[lane];
+    const float *box_static = lane < kMaxParts ? m->root_box_static[lane] : nullptr;
+    const int4 *tri_v4 = m->tri_v4;
+    const float4 *node_static = m->node_static, *tri_static = m->tri_static;
+    const double *rest64 = m->rest64;
+    double wlo[3], whi[3], u3[3], v3[3], d3[3], cref[3], Rm = 0.0, pad = 0.0;
+    int n_mats = 0;
+    const float2 *mat32 = nullptr;
+    const double *mat64 = nullptr;
+    const unsigned *tri_mat = nullptr;
+    const int *tri_vidx = nullptr;
+    const int2 *grp = nullptr;
+    if (lane == 0) {
+        for (int k = 0; k < 3; k++) {
+            wlo[k] = ord_to_dbl(P.wmin_bits[k]);
+            whi[k] = ord_to_dbl(P.wmax_bits[k]);
+            u3[k] = P.u[k]; v3[k] = P.v[k]; d3[k] = P.d[k];
+            cref[k] = m->c_ref[k];
+        }
+        Rm = m->R;
+        pad = m->pad;
+        n_mats = m->n_mats;
+        mat32 = m->mat32;
+        mat64 = m->mat64;
+        tri_mat = m->tri_mat;
+        tri_vidx = m->tri_vidx;
+        grp = m->grp;
+    }
     TraceCtx &B = reinterpret_cast<TraceCtx *>(a.tctx)[s];
-    if (threadIdx.x == 0) {
-        B.skip = P.skip;
+    if (lane == 0) {
+        B.skip = skip;
         if (a.raster) {
             a.rast_bad[s] = 0;
             if (s == 0) { *a.big_count = 0u; *a.bigt_count = 0u; }
@@ -143,82 +177,81 @@ __global__ void k_frame(TraceArgs a)
             for (int k = 0; k < 3; k++) a.qstate[kQSlot + 3 * s + k] = 0u;
             if (s == 0) { a.qstate[kQHead] = 0u; a.qstate[kQAbort] = 0u; }
         }
-        B.n_parts = m->n_parts;
+        B.n_parts = np;
+        if (a.red_ticket) a.red_ticket[s] = 0u;
     }
-    if (P.skip) return;
+    if (skip) return;
     // the parts' traversal views, a lane each
-    for (int p = threadIdx.x; p < m->n_parts; p += blockDim.x) {
-        const PartInfo &pi = m->part[p];
-        PartView &pv = B.part[p];
+    if (lane < np) {
+        PartView &pv = B.part[lane];
         pv.root = pi.tri_count > 1 ? 0 : ~0;
         pv.limit = a.walk_limit_test ? 1 : pi.node_count + pi.tri_count + 8;
         pv.tri_begin = pi.tri_begin;
         pv.vert_begin = pi.vert_begin;
-        pv.v4 = m->tri_v4 + pi.tri_begin;
+        pv.v4 = tri_v4 + pi.tri_begin;
         if (pi.dynamic) {
             pv.node = sb.node + (size_t)pi.dyn_node_off * kNode4;
             pv.tri = sb.tri + (size_t)pi.dyn_tri_off * 3;
             pv.v64 = sb.vert64 + (size_t)pi.dyn_vert_off * 3;
-            pv.box_src = sb.root_box + (size_t)p * 6;
+            pv.box_src = sb.root_box + (size_t)lane * 6;
         } else {
-            pv.node = m->node_static + (size_t)pi.node_begin * kNode4;
-            pv.tri = m->tri_static + (size_t)pi.tri_begin * 3;
-            pv.v64 = m->rest64 + (size_t)pi.vert_begin * 3;
-            pv.box_src = m->root_box_static[p];
+            pv.node = node_static + (size_t)pi.node_begin * kNode4;
+            pv.tri = tri_static + (size_t)pi.tri_begin * 3;
+            pv.v64 = rest64 + (size_t)pi.vert_begin * 3;
+            pv.box_src = box_static;
         }
     }
-    if (threadIdx.x != 0) return;
-    double umin = ord_to_dbl(P.wmin_bits[0]), umax = ord_to_dbl(P.wmax_bits[0]);
-    double vmin = ord_to_dbl(P.wmin_bits[1]), vmax = ord_to_dbl(P.wmax_bits[1]);
-    double wmin = ord_to_dbl(P.wmin_bits[2]), wmax = ord_to_dbl(P.wmax_bits[2]);
+    if (lane != 0) return;
+    const double umin = wlo[0], umax = whi[0], vmin = wlo[1], vmax = whi[1], wmin = wlo[2], wmax = whi[2];
+    const double Du = umax - umin, Dv = vmax - vmin, Dw = wmax - wmin;
+    const double Lw = sqrt(Du * Du + Dv * Dv + Dw * Dw);
+    const double eps = a.eps_rel * Lw;
     B.umin = umin; B.vmin = vmin; B.wmin = wmin;
     B.rN = (N & (N - 1)) == 0 ? 1.0 / N : 0.0;
-    B.Du = umax - umin; B.Dv = vmax - vmin;
-    double Dw = wmax - wmin;
-    B.Lw = sqrt(B.Du * B.Du + B.Dv * B.Dv + Dw * Dw);
-    B.eps = a.eps_rel * B.Lw;
-    B.eps32 = (float)B.eps;
-    double w0 = wmin - kStandoff;
+    B.Du = Du; B.Dv = Dv;
+    B.Lw = Lw;
+    B.eps = eps;
+    B.eps32 = (float)eps;
+    const double w0 = wmin - kStandoff;
     for (int k = 0; k < 3; k++) {
-        double o = umin * P.u[k] + vmin * P.v[k] + w0 * P.d[k];
+        double o = umin * u3[k] + vmin * v3[k] + w0 * d3[k];
         B.org[k] = (float)o;
-        B.du[k] = (float)(B.Du / N * P.u[k]);
-        B.dv[k] = (float)(B.Dv / N * P.v[k]);
-        B.dir[k] = (float)P.d[k];
-        B.u[k] = P.u[k]; B.v[k] = P.v[k]; B.d[k] = P.d[k];
-        B.c_ref[k] = m->c_ref[k];
-        B.cref32[k] = (float)m->c_ref[k];
+        B.du[k] = (float)(Du / N * u3[k]);
+        B.dv[k] = (float)(Dv / N * v3[k]);
+        B.dir[k] = (float)d3[k];
+        B.u[k] = u3[k]; B.v[k] = v3[k]; B.d[k] = d3[k];
+        B.c_ref[k] = cref[k];
+        B.cref32[k] = (float)cref[k];
     }
     B.umin32 = (float)umin; B.vmin32 = (float)vmin;
-    B.du32 = (float)(B.Du / N); B.dv32 = (float)(B.Dv / N);
+    B.du32 = (float)(Du / N); B.dv32 = (float)(Dv / N);
     B.w0_32 = (float)w0;
     const double u = 5.9604644775390625e-8;
     // Primary (view frame): vertex projections rounded once (|p| u/2), pixel
     // centres from rounded umin, du and one FMA, differences rounded; the bound
     // doubles that sum.
-    double Mw = fmax(fmax(fabs(umin), fabs(umax)), fmax(fabs(vmin), fabs(vmax)));
-    double Dm = fmax(B.Du, B.Dv);
-    B.delta_p = (float)(2.0 * u * (3.0 * Mw + 2.0 * Dm));
-    double Wm = fmax(fabs(wmin), fabs(wmax)) + kStandoff;
-    B.tau_p = (float)(16.0 * u * Wm + 32.0 * B.delta_p);
+    const double Mw = fmax(fmax(fabs(umin), fabs(umax)), fmax(fabs(vmin), fabs(vmax)));
+    const double Dm = fmax(Du, Dv);
+    const float delta_p = (float)(2.0 * u * (3.0 * Mw + 2.0 * Dm));
+    B.delta_p = delta_p;
+    const double Wm = fmax(fabs(wmin), fabs(wmax)) + kStandoff;
+    B.tau_p = (float)(16.0 * u * Wm + 32.0 * delta_p);
     // Secondary (world frame): the origin is rebuilt from the hit's barycentric
     // weights (error ~2 x the previous bound + rounding at |x| <= R, plus the
     // rounding of posed vertices); the per-triangle terms (subtraction, shear,
     // reflected direction) are added in the test from that triangle's distance.
-    double R = m->R;
-    B.delta_s = (float)(6.0 * u * R);
-    B.R = (float)R;
-    B.L = (float)B.Lw;
-    B.pad = (float)m->pad;
-    B.n_parts = m->n_parts;
-    B.n_mats = m->n_mats;
+    B.delta_s = (float)(6.0 * u * Rm);
+    B.R = (float)Rm;
+    B.L = (float)Lw;
+    B.pad = (float)pad;
+    B.n_mats = n_mats;
     B.vview = sb.vview;
     B.vview64 = sb.vview64;
-    B.mat32 = m->mat32;
-    B.mat64 = m->mat64;
-    B.tri_mat = m->tri_mat;
-    B.tri_vidx = m->tri_vidx;
-    B.grp = m->grp;
+    B.mat32 = mat32;
+    B.mat64 = mat64;
+    B.tri_mat = tri_mat;
+    B.tri_vidx = tri_vidx;
+    B.grp = grp;
 }
 
 // Copy the slot context (header + the parts in use) into shared memory.
@@ -1851,11 +1884,19 @@ __global__ void __launch_bounds__(kLaneStride) k_diffuse(TraceArgs a)
 // uncertain triangles than the candidate list holds; rare: the traversal
 // context is loaded only when the block has any).  Each thread takes a fixed,
 // strided set of tiles in order, so the sums are reproducible.
-__global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
+__device__ void final_reduce(const TraceArgs &a, int s, int eval0, double *force, double *torque, int *err_flags,
+                             unsigned long long *stats_accum, bool cg);
+
+__global__ void __launch_bounds__(256) k_reduce1(TraceArgs a, int eval0, double *force, double *torque,
+                                                 int *err_flags, unsigned long long *stats_accum, int fuse)
 {
     pdl_enter();
     const int s = blockIdx.y, b = blockIdx.x;
-    if (a.pose[s].skip) return;  // uniform over the block
+    if (a.pose[s].skip) {  // uniform over the block
+        // a skipped evaluation outputs zero force and torque
+        if (fuse && b == 0 && threadIdx.x < 6) (threadIdx.x < 3 ? force : torque)[3 * (eval0 + s) + threadIdx.x % 3] = 0.0;
+        return;
+    }
     const int nt = a.sd[s].tiles;
     const int chunk = (nt + kRed1 - 1) / kRed1;
     const int t0 = b * chunk, t1 = min(t0 + chunk, nt);
@@ -1942,12 +1983,100 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a)
         for (int q = 0; q < nw; q++) x += rc[threadIdx.x - 6][q];
         out[threadIdx.x] = (double)x;
     }
+    if (!fuse) return;
+    // the last of the slot's blocks to finish adds the first-level sums, in
+    // block order whichever block that is (the second level, without a launch)
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.red_ticket[s], 1u) == (unsigned)(kRed1 - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    final_reduce(a, s, eval0, force, torque, err_flags, stats_accum, true);
 }
 
-// One block per slot: the first-level sums.
-// stats_accum[16]: 0 evals, 1 rays, 2 refined rays, 3 segments, 4..8 hits per
-// segment, 9 nodes, 10 triangles, 11 box tests, 12..15 hand-offs by cause.
-__global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *force, double *torque, int *err_flags,
+// The second level for slot s: its kRed1 first-level sums added in block order
+// (FP64; the FP32 modes add them again in FP32), the diffuse blocks' sums, the
+// pixel-area scale, the stores.  Threads below kRed1 of the calling block hold
+// the sums (whole warps); `cg` reads what other blocks of the same launch wrote
+// through L2.  stats_accum[16]: 0 evals, 1 rays, 2 refined rays, 3 segments,
+// 4..8 hits per segment, 9 nodes, 10 triangles, 11 box tests, 12..15 hand-offs
+// by cause.
+__device__ void final_reduce(const TraceArgs &a, int s, int eval0, double *force, double *torque, int *err_flags,
+                             unsigned long long *stats_accum, bool cg)
+{
+    // what the last step needs, loaded before the sums (a load is not moved across the barriers)
+    const SlotPose &P = a.pose[s];
+    double Du = 0.0, Dv = 0.0, scale = 0.0;
+    int N = 0, pflags = 0;
+    if (threadIdx.x == 0) {
+        Du = ord_to_dbl(P.wmax_bits[0]) - ord_to_dbl(P.wmin_bits[0]);
+        Dv = ord_to_dbl(P.wmax_bits[1]) - ord_to_dbl(P.wmin_bits[1]);
+        scale = P.scale;
+        pflags = cg ? __ldcg(&P.flags) : P.flags;
+        N = a.sd[s].N;
+    }
+    __shared__ double red2[kPart][kRed1 / 32];
+    __shared__ double red[kPart];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < kRed1) {
+        const double *src = a.partials1 + ((size_t)s * kRed1 + threadIdx.x) * kPart;
+        for (int k = 0; k < kPart; k++) {
+            const double x = warp_sum(cg ? __ldcg(src + k) : src[k]);
+            if (lane == 0) red2[k][w] = x;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kPart) {
+        double x = 0.0;
+        for (int q = 0; q < kRed1 / 32; q++) x += red2[threadIdx.x][q];
+        red[threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (a.sum_mode != 0) {
+        // the FP32 modes: the first-level sums again, in order, in FP32
+        for (int k = 0; k < 6; k++) {
+            Comp32 x{0.0f, 0.0f};
+            for (int b = 0; b < kRed1; b++) {
+                const double *src = a.partials1 + ((size_t)s * kRed1 + b) * kPart + k;
+                const float p = (float)(cg ? __ldcg(src) : *src);
+                if (a.sum_mode == 1) comp_add(x, p);
+                else x.hi = __fadd_rn(x.hi, p);
+            }
+            if (a.n_diffuse > 0)
+                for (int b = 0; b < kDiffBlocks; b++) {
+                    const float p = (float)a.dpart[((size_t)s * kDiffBlocks + b) * 6 + k];
+                    if (a.sum_mode == 1) comp_add(x, p);
+                    else x.hi = __fadd_rn(x.hi, p);
+                }
+            red[k] = (double)comp_value(x);
+        }
+    } else if (a.n_diffuse > 0) {
+        for (int b = 0; b < kDiffBlocks; b++)
+            for (int k = 0; k < 6; k++) red[k] += a.dpart[((size_t)s * kDiffBlocks + b) * 6 + k];
+    }
+    const double sc = scale * (Du * Dv) / ((double)N * (double)N);
+    const int e = eval0 + s;
+    for (int k = 0; k < 3; k++) {
+        force[3 * e + k] = red[k] * sc;
+        torque[3 * e + k] = red[3 + k] * sc;
+    }
+    if (pflags) atomicOr(err_flags, pflags);
+    if (stats_accum) {
+        atomicAdd(&stats_accum[0], 1ull);
+        atomicAdd(&stats_accum[1], (unsigned long long)N * (unsigned long long)N);
+        atomicAdd(&stats_accum[2], (unsigned long long)red[6]);
+        atomicAdd(&stats_accum[3], (unsigned long long)red[7]);
+        for (int k = 0; k < 5; k++) atomicAdd(&stats_accum[4 + k], (unsigned long long)red[8 + k]);
+        for (int k = 0; k < 3; k++) atomicAdd(&stats_accum[9 + k], (unsigned long long)red[13 + k]);
+        for (int k = 0; k < 4; k++) atomicAdd(&stats_accum[12 + k], (unsigned long long)red[16 + k]);
+    }
+}
+
+// The second level as its own launch (after the diffuse rays), a block per slot.
+__global__ void __launch_bounds__(kRed1) k_reduce(TraceArgs a, int eval0, double *force, double *torque, int *err_flags,
                                                 unsigned long long *stats_accum)
 {
     pdl_enter();
@@ -1957,55 +2086,7 @@ __global__ void __launch_bounds__(256) k_reduce(TraceArgs a, int eval0, double *
         if (threadIdx.x < 6) (threadIdx.x < 3 ? force : torque)[3 * (eval0 + s) + threadIdx.x % 3] = 0.0;
         return;
     }
-    double acc[kPart];
-    for (int k = 0; k < kPart; k++) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < kRed1; b += blockDim.x)
-        for (int k = 0; k < kPart; k++) acc[k] += a.partials1[((size_t)s * kRed1 + b) * kPart + k];
-    __shared__ double red[kPart];
-    block_sum(acc, red);
-    if (threadIdx.x == 0) {
-        if (a.sum_mode != 0) {
-            // the FP32 modes: the first-level sums again, in order, in FP32
-            for (int k = 0; k < 6; k++) {
-                Comp32 x{0.0f, 0.0f};
-                for (int b = 0; b < kRed1; b++) {
-                    const float p = (float)a.partials1[((size_t)s * kRed1 + b) * kPart + k];
-                    if (a.sum_mode == 1) comp_add(x, p);
-                    else x.hi = __fadd_rn(x.hi, p);
-                }
-                if (a.n_diffuse > 0)
-                    for (int b = 0; b < kDiffBlocks; b++) {
-                        const float p = (float)a.dpart[((size_t)s * kDiffBlocks + b) * 6 + k];
-                        if (a.sum_mode == 1) comp_add(x, p);
-                        else x.hi = __fadd_rn(x.hi, p);
-                    }
-                red[k] = (double)comp_value(x);
-            }
-        } else if (a.n_diffuse > 0) {
-            for (int b = 0; b < kDiffBlocks; b++)
-                for (int k = 0; k < 6; k++) red[k] += a.dpart[((size_t)s * kDiffBlocks + b) * 6 + k];
-        }
-        const SlotPose &P = a.pose[s];
-        double Du = ord_to_dbl(P.wmax_bits[0]) - ord_to_dbl(P.wmin_bits[0]);
-        double Dv = ord_to_dbl(P.wmax_bits[1]) - ord_to_dbl(P.wmin_bits[1]);
-        const int N = a.sd[s].N;
-        double sc = P.scale * (Du * Dv) / ((double)N * (double)N);
-        int e = eval0 + s;
-        for (int k = 0; k < 3; k++) {
-            force[3 * e + k] = red[k] * sc;
-            torque[3 * e + k] = red[3 + k] * sc;
-        }
-        if (P.flags) atomicOr(err_flags, P.flags);
-        if (stats_accum) {
-            atomicAdd(&stats_accum[0], 1ull);
-            atomicAdd(&stats_accum[1], (unsigned long long)N * (unsigned long long)N);
-            atomicAdd(&stats_accum[2], (unsigned long long)red[6]);
-            atomicAdd(&stats_accum[3], (unsigned long long)red[7]);
-            for (int k = 0; k < 5; k++) atomicAdd(&stats_accum[4 + k], (unsigned long long)red[8 + k]);
-            for (int k = 0; k < 3; k++) atomicAdd(&stats_accum[9 + k], (unsigned long long)red[13 + k]);
-            for (int k = 0; k < 4; k++) atomicAdd(&stats_accum[12 + k], (unsigned long long)red[16 + k]);
-        }
-    }
+    final_reduce(a, s, eval0, force, torque, err_flags, stats_accum, false);
 }
 
 // ------------------------------------------------------------ BVH check
@@ -2159,15 +2240,18 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
                           unsigned long long *stats_accum, cudaStream_t st)
 {
-    cudaError_t e = launch_chained(k_reduce1, dim3(kRed1, S), dim3(256), 0, st, a);
-    if (e != cudaSuccess) return e;
+    // without diffuse rays the last first-level block of a slot does the second level
+    const int fuse = (a.n_diffuse <= 0 && a.red_ticket) ? 1 : 0;
+    cudaError_t e = launch_chained(k_reduce1, dim3(kRed1, S), dim3(256), 0, st, a, eval0, force, torque, err_flags,
+                                   stats_accum, fuse);
+    if (e != cudaSuccess || fuse) return e;
     // diffuse secondaries after the FP64 re-trace (which records the hits of the rays it takes)
     if (a.n_diffuse > 0) {
         if ((e = launch_chained(k_demit, dim3(kDiffBlocks, S), dim3(kLaneStride), 0, st, a)) != cudaSuccess) return e;
         if ((e = launch_chained(k_dscan, dim3(S), dim3(1024), 0, st, a)) != cudaSuccess) return e;
         if ((e = launch_chained(k_diffuse, dim3(kDiffBlocks, S), dim3(kLaneStride), 0, st, a)) != cudaSuccess) return e;
     }
-    return launch_chained(k_reduce, dim3(S), dim3(256), 0, st, a, eval0, force, torque, err_flags, stats_accum);
+    return launch_chained(k_reduce, dim3(S), dim3(kRed1), 0, st, a, eval0, force, torque, err_flags, stats_accum);
 }
 
 }  // namespace srp
