@@ -742,7 +742,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         CK(ctx, launch_reduce(a, Sc, e0, d_f, d_t, ctx->err_flags, ctx->stats, ls));
         int g4 = tm.mark(ls);
         launches += a.n_diffuse > 0 ? 4 : 3;  // frame, trace, the reduction (two levels in one launch without diffuse rays)
-        if (a.raster) launches += a.queue ? 4 : 6;  // key clear, two raster passes over small and large triangles, chunk listing
+        if (a.raster) launches += raster_launches(Sc, a.queue != 0);
         if (a.n_diffuse > 0) launches += 3;  // diffuse secondaries: emission records, their prefix, the rays
         trace_launches++;
         if (adj) {
@@ -2434,10 +2434,10 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     srp_status rc = capture(na);
     if (rc) return rc;
     const int poll_max = p->poll > 0 ? p->poll : 16;
-    // per stage with the SRP: pose, vertices, refit, frame, the raster passes
-    // and their key clear, trace, the reduction, then the acceleration with
+    // per stage with the SRP: pose, vertices, refit, frame, the raster launches,
+    // trace, the reduction, then the acceleration with
     // the next stage (control at the last); without it stage, acceleration, and control
-    const int per_step = p->srp ? nstage * (1 + 6 + (raster ? 6 : 0)) : nstage * 2 + 1;
+    const int per_step = p->srp ? nstage * (1 + 6 + (raster ? raster_launches(n, queue) : 0)) : nstage * 2 + 1;
     for (int64_t round = 0; round < p->max_steps + 2 && na > 0; round++) {
         int done = 0;
         CK(ctx, cudaMemcpyAsync(&done, ctx->prop_done, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -157,7 +157,10 @@ cudaError_t launch_pose(const SlotDesc *sd, const double *sun_dirs, const double
 }
 
 // ------------------------------------------------------------- vertices
-constexpr int kVertsPerThread = 4;
+// vertices a thread: one for a launch of few slots (latency: one vertex's
+// chain a thread), four for many (fewer blocks beside the other lanes' traces)
+constexpr int kVertsPerThreadMany = 4;
+constexpr int kManySlots = 4;
 
 __device__ inline unsigned long long warp_min_u64(unsigned long long x)
 {
@@ -176,10 +179,10 @@ __device__ inline unsigned long long warp_max_u64(unsigned long long x)
     return x;
 }
 
-// kVertsPerThread vertices a thread (strided by the block for coalescing).
+// vpt vertices a thread (strided by the block for coalescing).
 // The window bounds are reduced as order-preserving integer images of the
 // FP64 projections (exact, order independent, and off the slow FP64 pipe).
-__global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *pose)
+__global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *pose, int vpt)
 {
     pdl_enter();
     const int s = blockIdx.y;
@@ -187,12 +190,12 @@ __global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *
     const MeshDev *mesh = sd[s].mesh;
     const SlotBufs &slot = sd[s].sb;
     const int n_verts = mesh->n_verts;
-    const int k0 = blockIdx.x * blockDim.x * kVertsPerThread;
+    const int k0 = blockIdx.x * blockDim.x * vpt;
     if (P.skip || k0 >= n_verts) return;  // uniform over the block
     unsigned long long mn[3], mx[3];
     for (int c = 0; c < 3; c++) { mn[c] = ~0ull; mx[c] = 0ull; }
     const double *ax[3] = {P.u, P.v, P.d};
-    for (int q = 0; q < kVertsPerThread; q++) {
+    for (int q = 0; q < vpt; q++) {
         const int k = k0 + q * blockDim.x + threadIdx.x;
         if (k >= n_verts) break;
         const int p = mesh->vert_part[k];
@@ -242,9 +245,10 @@ __global__ void __launch_bounds__(256) k_vertices(const SlotDesc *sd, SlotPose *
 
 cudaError_t launch_vertices(const SlotDesc *sd, SlotPose *pose, int S, int max_verts, cudaStream_t st)
 {
-    const int per_block = 256 * kVertsPerThread;
+    const int vpt = S >= kManySlots ? kVertsPerThreadMany : 1;
+    const int per_block = 256 * vpt;
     dim3 grid((max_verts + per_block - 1) / per_block, S);
-    return launch_chained(k_vertices, grid, dim3(256), 0, st, sd, pose);
+    return launch_chained(k_vertices, grid, dim3(256), 0, st, sd, pose, vpt);
 }
 
 // ---------------------------------------------------------------- refit

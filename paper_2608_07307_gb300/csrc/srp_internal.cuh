@@ -407,6 +407,8 @@ cudaError_t launch_refit_static(const MeshDev *mesh_d, const MeshDev &mh, float4
 
 // trace.cu
 // Per-slot window frame and, when rasterising, the primary visibility passes.
+// Raster-related launches of one launch_frame call of S slots (for launch counts).
+int raster_launches(int S, bool queue);
 cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st);
 // The FP32 trace (after launch_frame on the same stream).
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st);

@@ -85,7 +85,7 @@ struct PartView {
     const double *v64;   // v64[3 * (vi - vert_begin) + c]
     int root;            // 0, or ~0 for a one-triangle part
     int limit;           // bound on loop iterations of one part walk (nodes + triangles)
-    int tri_begin, vert_begin;
+    int tri_begin, tri_count, vert_begin;
     float box[6];        // root box (filled when a block loads the context, from box_src)
     const float *box_src;  // the part's root box: the refit's output for a dynamic part
 };
@@ -107,6 +107,8 @@ struct TraceCtx {
     const unsigned *tri_mat;
     const int *tri_vidx;
     const int2 *grp;  // per sorted triangle: subtree of its coplanar group, deviation bound
+    const int4 *tri_v4;    // vertex ids of the sorted triangles (the raster's first load)
+    int n_tris;
     // FP64 window and basis for the FP64 path
     double umin, vmin, wmin, Du, Dv, Lw, eps;
     double rN;  // 1 / N when N is a power of two (dividing by N is then exactly this product), else 0
@@ -130,6 +132,14 @@ __global__ void k_frame(TraceArgs a)
     // a store it might alias waits for everything before it, and a chain of such
     // round trips, not the arithmetic, would set this kernel's duration
     const int s = blockIdx.x, lane = threadIdx.x;
+    // launches of few slots: every block of the slot sets the pixel keys to all
+    // ones (no hit, no candidate) for the raster
+    if (a.raster && a.pix_key) {
+        unsigned long long *key = a.pix_key + (size_t)s * a.ray_stride;
+        const size_t stride = (size_t)gridDim.y * blockDim.x;
+        for (size_t i = (size_t)blockIdx.y * blockDim.x + threadIdx.x; i < a.ray_stride; i += stride) key[i] = ~0ull;
+    }
+    if (blockIdx.y != 0 || lane >= 32) return;  // the context: one warp of the slot
     const SlotDesc &D = a.sd[s];
     const MeshDev *m = D.mesh;
     const SlotBufs sb = D.sb;
@@ -141,6 +151,7 @@ __global__ void k_frame(TraceArgs a)
     if (lane < kMaxParts) pi = m->part[lane];
     const float *box_static = lane < kMaxParts ? m->root_box_static[lane] : nullptr;
     const int4 *tri_v4 = m->tri_v4;
+    const int n_tris = m->n_tris;
     const float4 *node_static = m->node_static, *tri_static = m->tri_static;
     const double *rest64 = m->rest64;
     double wlo[3], whi[3], u3[3], v3[3], d3[3], cref[3], Rm = 0.0, pad = 0.0;
@@ -187,6 +198,7 @@ __global__ void k_frame(TraceArgs a)
         pv.root = pi.tri_count > 1 ? 0 : ~0;
         pv.limit = a.walk_limit_test ? 1 : pi.node_count + pi.tri_count + 8;
         pv.tri_begin = pi.tri_begin;
+        pv.tri_count = pi.tri_count;
         pv.vert_begin = pi.vert_begin;
         pv.v4 = tri_v4 + pi.tri_begin;
         if (pi.dynamic) {
@@ -252,14 +264,17 @@ __global__ void k_frame(TraceArgs a)
     B.tri_mat = tri_mat;
     B.tri_vidx = tri_vidx;
     B.grp = grp;
+    B.tri_v4 = tri_v4;
+    B.n_tris = n_tris;
 }
 
 // Copy the slot context (header + the parts in use) into shared memory.
 __device__ __forceinline__ void load_ctx(TraceCtx &B, const TraceArgs &a, int s)
 {
     const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
-    int np = a.sd[s].mesh->n_parts;
-    int words = (int)((offsetof(TraceCtx, part) + np * sizeof(PartView)) / 4);
+    // the record up to its last used part view (the part count from the record itself)
+    const int np = __ldg(&g->n_parts);
+    const int words = (int)((offsetof(TraceCtx, part) + np * sizeof(PartView)) / 4);
     const int *src = reinterpret_cast<const int *>(g);
     int *dst = reinterpret_cast<int *>(&B);
     for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = __ldg(src + k);
@@ -822,6 +837,22 @@ __device__ __forceinline__ int part_of_sorted(const MeshDev *m, int t)
     return p;
 }
 
+// Part of sorted triangle t from the context's part views (parts are
+// contiguous ranges of the sorted order); tb: the part's first triangle.
+__device__ __forceinline__ int part_of_view(const TraceCtx *g, int np, int t, int &tb)
+{
+    int p = 0;
+    tb = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxParts; q++) {
+        if (q < np) {
+            const int b0 = g->part[q].tri_begin, c0 = g->part[q].tri_count;
+            if (t >= b0 && t < b0 + c0) { p = q; tb = b0; }
+        }
+    }
+    return p;
+}
+
 // Thread per (slot, sorted triangle): small projected boxes in place; larger
 // ones are listed for k_raster_chunks, which lists their 16 x 16-pixel chunks
 // that can meet them for k_raster_big (pass 0 lists, pass 1 reuses the lists).
@@ -829,16 +860,19 @@ template <int PASS>
 __device__ __forceinline__ void raster_tri(const TraceArgs &a, int s, int t)
 {
     const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
-    if (g->skip) return;
-    const MeshDev *m = a.sd[s].mesh;
-    if (t >= m->n_tris) return;
+    // the slot's context in one round of loads (nothing read from the mesh record)
+    const int skip = g->skip, n_tris = g->n_tris, np = g->n_parts;
+    const int4 *tv4 = g->tri_v4;
     const RastView V = rast_view(a, s);
+    if (skip || t >= n_tris) return;
     if (!(V.du32 > 0.0f && V.dv32 > 0.0f)) {
         if (PASS == 0 && t == 0) a.rast_bad[s] = 1;
         return;
     }
-    const int4 vi = __ldg(m->tri_v4 + t);
+    const int4 vi = __ldg(tv4 + t);
     const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
+    int tb = 0;
+    const int p = part_of_view(g, np, t, tb);
     int i0, i1, j0, j1;
     if (!rast_box(V, A, B, C, i0, i1, j0, j1)) return;
     const int w = i1 - i0 + 1, h = j1 - j0 + 1;
@@ -854,8 +888,7 @@ __device__ __forceinline__ void raster_tri(const TraceArgs &a, int s, int t)
         }
         return;
     }
-    const int p = part_of_sorted(m, t);
-    const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
+    const unsigned id = ((unsigned)p << 24) | (unsigned)(t - tb);
     const size_t off = (size_t)s * a.ray_stride;
     const float eb = rast_bound(V, A, B, C, i0, i1, j0, j1);
     for (int i = i0; i <= i1; i++)
@@ -880,9 +913,10 @@ __global__ void __launch_bounds__(256) k_raster_chunks(TraceArgs a)
     for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) {
         const int2 E = a.bigt[e];
         const int s = E.x, t = E.y;
-        const MeshDev *m = a.sd[s].mesh;
+        const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
+        const int4 *tv4 = g->tri_v4;
         const RastView V = rast_view(a, s);
-        const int4 vi = __ldg(m->tri_v4 + t);
+        const int4 vi = __ldg(tv4 + t);
         const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
         int i0, i1, j0, j1;
         if (!rast_box(V, A, B, C, i0, i1, j0, j1)) continue;
@@ -924,16 +958,19 @@ __device__ __forceinline__ int raster_big_entry(const TraceArgs &a, unsigned e, 
     const int4 E = a.big[e];
     const int s = E.x, t = E.y;
     if (s < 0) return -1;
-    const MeshDev *m = a.sd[s].mesh;
+    const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
+    const int4 *tv4 = g->tri_v4;
+    const int np = g->n_parts;
     const RastView V = rast_view(a, s);
-    const int4 vi = __ldg(m->tri_v4 + t);
+    const int4 vi = __ldg(tv4 + t);
     const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
+    int tb = 0;
+    const int p = part_of_view(g, np, t, tb);
     int i0, i1, j0, j1;
     if (!rast_box(V, A, B, C, i0, i1, j0, j1)) return s;
     const int ib = i0 + E.z * kRastChunk, jb = j0 + E.w * kRastChunk;
     const int ie = min(ib + kRastChunk - 1, i1), je = min(jb + kRastChunk - 1, j1);
-    const int p = part_of_sorted(m, t);
-    const unsigned id = ((unsigned)p << 24) | (unsigned)(t - m->part[p].tri_begin);
+    const unsigned id = ((unsigned)p << 24) | (unsigned)(t - tb);
     const size_t off = (size_t)s * a.ray_stride;
     const float eb = rast_bound(V, A, B, C, ib, ie, jb, je);
     for (int q = (int)lane; q < kRastChunk * kRastChunk; q += 32) {
@@ -952,6 +989,22 @@ __global__ void __launch_bounds__(256) k_raster_big(TraceArgs a)
     const unsigned n = min(__ldcg(a.big_count), (unsigned)a.big_cap);
     const unsigned lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x >> 5);
     for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) raster_big_entry<PASS>(a, e, lane);
+}
+
+// The second raster pass in one launch: blocks below nbig take listed chunks
+// of large triangles (a warp per chunk, grid-stride over the list), the rest a
+// small triangle per thread (per_slot blocks a slot).
+__global__ void __launch_bounds__(128) k_raster_pass1(TraceArgs a, int nbig, int per_slot)
+{
+    pdl_enter();
+    if ((int)blockIdx.x < nbig) {
+        const unsigned n = min(__ldcg(a.big_count), (unsigned)a.big_cap);
+        const unsigned lane = threadIdx.x & 31u, nw = (unsigned)nbig * (blockDim.x >> 5);
+        for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) raster_big_entry<1>(a, e, lane);
+        return;
+    }
+    const int b = (int)blockIdx.x - nbig;
+    raster_tri<1>(a, b / per_slot, (b % per_slot) * (int)blockDim.x + (int)threadIdx.x);
 }
 
 // A block is kTraceWarps warps over consecutive tiles of one slot, sharing
@@ -2194,30 +2247,58 @@ static int device_sms()
     return std::max(1, sms);
 }
 
+// Launch shapes by batch: a launch of few slots (a propagation stage) is
+// latency-bound, so the frame kernel clears the pixel keys and the second
+// raster pass is one launch; with many slots the launches overlap other lanes'
+// traces, where a separate clear and separate second-pass launches measured faster.
+constexpr int kFewSlots = 4;
+
+int raster_launches(int S, bool queue)
+{
+    if (S < kFewSlots) return queue ? 3 : 4;  // first pass, chunk listing, chunks; the merged second pass
+    return queue ? 4 : 6;                     // key clear, first pass, listing, chunks; two second-pass launches
+}
+
 cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
 {
-    cudaError_t e = launch_chained(k_frame, dim3(S), dim3(32), 0, st, a);
-    if (e != cudaSuccess || a.n_tiles <= 0) return e;
-    if (a.raster && a.rast_tris > 0) {
-        const int sms = device_sms();
-        // cleared pixel keys of the launch's slots (a kernel, so that the chain stays programmatic)
+    const int sms = device_sms();
+    const bool raster = a.raster && a.rast_tris > 0 && a.n_tiles > 0;
+    const bool few = S < kFewSlots;
+    TraceArgs f = a;
+    if (!raster || !few) f.pix_key = nullptr;
+    cudaError_t e;
+    if (raster && few) {
+        // the frame kernel's blocks beyond the context's warp clear the pixel keys
+        const size_t per = (size_t)256 * 4;  // keys a block clears in one sweep of four
+        const int ky = (int)std::max<size_t>(1, std::min((a.ray_stride + per - 1) / per,
+                                                         (size_t)(sms * 4 + S - 1) / (size_t)S));
+        e = launch_chained(k_frame, dim3(S, ky), dim3(256), 0, st, f);
+    } else {
+        e = launch_chained(k_frame, dim3(S, 1), dim3(32), 0, st, f);
+    }
+    if (e != cudaSuccess || !raster) return e;
+    if (!few) {
         const size_t px = (size_t)S * a.ray_stride;
         const size_t kb = std::min((px + 255) / 256, (size_t)sms * 8);
         e = launch_chained(k_clear_keys, dim3((unsigned)std::max<size_t>(1, kb)), dim3(256), 0, st, a.pix_key, px);
         if (e != cudaSuccess) return e;
-        const dim3 grid((a.rast_tris + 127) / 128, S);
-        // the chunk lists are short: a grid the size of the device, not of the list's capacity
-        const int big_blocks = sms * kRastBigBlocksPerSM;
-        if ((e = launch_chained(k_raster<0>, grid, dim3(128), 0, st, a)) != cudaSuccess) return e;
-        if ((e = launch_chained(k_raster_chunks, dim3(std::max(1, big_blocks / 4)), dim3(256), 0, st, a)) != cudaSuccess)
-            return e;
-        if ((e = launch_chained(k_raster_big<0>, dim3(big_blocks), dim3(256), 0, st, a)) != cudaSuccess) return e;
-        if (!a.queue) {  // the work queue runs the second pass with the trace
-            if ((e = launch_chained(k_raster<1>, grid, dim3(128), 0, st, a)) != cudaSuccess) return e;
-            if ((e = launch_chained(k_raster_big<1>, dim3(big_blocks), dim3(256), 0, st, a)) != cudaSuccess) return e;
-        }
     }
-    return cudaSuccess;
+    const dim3 grid((a.rast_tris + 127) / 128, S);
+    // the chunk lists are short: a grid the size of the device, not of the list's capacity
+    const int big_blocks = sms * kRastBigBlocksPerSM;
+    if ((e = launch_chained(k_raster<0>, grid, dim3(128), 0, st, a)) != cudaSuccess) return e;
+    if ((e = launch_chained(k_raster_chunks, dim3(std::max(1, big_blocks / 4)), dim3(256), 0, st, a)) != cudaSuccess)
+        return e;
+    if ((e = launch_chained(k_raster_big<0>, dim3(big_blocks), dim3(256), 0, st, a)) != cudaSuccess) return e;
+    if (a.queue) return cudaSuccess;  // the work queue runs the second pass with the trace
+    if (few) {
+        // the second pass over large triangles' chunks and small triangles: one launch
+        const int nbig = 2 * big_blocks, per_slot = (int)grid.x;
+        const unsigned blocks = (unsigned)nbig + (unsigned)per_slot * (unsigned)S;
+        return launch_chained(k_raster_pass1, dim3(blocks), dim3(128), 0, st, a, nbig, per_slot);
+    }
+    if ((e = launch_chained(k_raster<1>, grid, dim3(128), 0, st, a)) != cudaSuccess) return e;
+    return launch_chained(k_raster_big<1>, dim3(big_blocks), dim3(256), 0, st, a);
 }
 
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
