@@ -273,7 +273,7 @@ struct DEmit {
 constexpr int kPixCand = 2;      // uncertain triangles kept per pixel (more: the ray traverses)
 constexpr int kRastSmall = 64;   // largest pixel box one thread rasterises
 constexpr int kRastChunk = 16;   // larger triangles: chunks of 16 x 16 pixels, one warp each
-constexpr int kRastBigBlocksPerSM = 2;  // k_raster_big grid: blocks of 8 warps per SM, one listed chunk a warp
+constexpr int kRastBigBlocksPerSM = 2;  // k_raster_big grid: blocks of 8 warps per SM and 8 slots, one listed chunk a warp
 constexpr int kBigPerSlot = 65536;  // chunk-list entries reserved per slot
 size_t trace_ctx_bytes();
 

@@ -2284,8 +2284,9 @@ cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     const dim3 grid((a.rast_tris + 127) / 128, S);
-    // the chunk lists are short: a grid the size of the device, not of the list's capacity
-    const int big_blocks = sms * kRastBigBlocksPerSM;
+    // the chunk lists grow with the slots: a grid of the device's size per eight
+    // slots, not of the lists' capacity
+    const int big_blocks = sms * kRastBigBlocksPerSM * std::max(1, (S + 7) / 8);
     if ((e = launch_chained(k_raster<0>, grid, dim3(128), 0, st, a)) != cudaSuccess) return e;
     if ((e = launch_chained(k_raster_chunks, dim3(std::max(1, big_blocks / 4)), dim3(256), 0, st, a)) != cudaSuccess)
         return e;
