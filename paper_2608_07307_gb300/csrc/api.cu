@@ -710,6 +710,8 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
         a.hits = hit_tri ? (h_dev ? hit_tri + (size_t)e0 * R * nseg : stage) : ((adj || prm->n_diffuse > 0) ? stage : nullptr);
         a.walk_limit_test = (prm->flags & SRP_EVAL_TEST_WALK_BOUND) ? 1 : 0;
         a.sum_mode = (prm->flags & SRP_EVAL_SUM_COMP32) ? 1 : ((prm->flags & SRP_EVAL_SUM_FP32) ? 2 : 0);
+        a.ctx_parts = h.n_parts;
+        a.hpt_segs = nseg;
         if (prm->n_diffuse > 0 && nseg > 1) {
             a.n_diffuse = prm->n_diffuse;
             a.diffuse_seed = prm->diffuse_seed;
@@ -936,6 +938,7 @@ srp_status srp_create(srp_ctx **out, int32_t device, void *cuda_stream)
     if (!ctx) return SRP_ERR_OOM;
     ctx->device = device;
     if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return SRP_ERR_CUDA; }
+    if (configure_trace_kernels() != cudaSuccess) { cudaGetLastError(); delete ctx; return SRP_ERR_CUDA; }
     if (cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -2342,9 +2345,11 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
     auto capture = [&](int na) -> srp_status {
         // descriptors of the running trajectories, their tiles laid end to end
         std::vector<SlotDesc> dd(na);
-        int t0 = 0, r0 = 0, mv = 0, md = 0;
+        int t0 = 0, r0 = 0, mv = 0, md = 0, mp = 0, ms = 0;
         for (int k = 0; k < na; k++) {
             dd[k] = desc[act[k]];
+            mp = std::max(mp, mk[act[k]]->h.n_parts);
+            ms = std::max(ms, dd[k].nseg);
             dd[k].tile0 = t0;
             t0 += trace_blocks(dd[k].tiles);
             dd[k].rast0 = r0;
@@ -2366,6 +2371,8 @@ srp_status srp_propagate_batch(srp_ctx *ctx, const srp_prop_params *p, int32_t n
         a.pcounts = pcnt_blk;
         a.partials1 = part1;
         a.red_ticket = rticket;
+        a.ctx_parts = mp;
+        a.hpt_segs = ms;
         a.amb_list = alist;
         a.amb_count = acount;
         a.ray_stride = Rmax;

@@ -250,6 +250,7 @@ struct TraceArgs {
     int *dtot;                   // [S] emissions of the slot
     int walk_limit_test;         // 1: every BVH walk is bounded at one step (tests of the bound's error path)
     int sum_mode;                // sums above the tile: 0 FP64, 1 compensated FP32, 2 plain FP32
+    int ctx_parts, hpt_segs;     // most parts / segments over the launch's slots (the trace kernels' shared memory; 0: the maxima)
     // work queue (queue != 0): the raster's second pass and the trace as one
     // persistent launch; qstate = [head, abort, then per slot: second-pass
     // items done, large-triangle chunks done, chunks listed]
@@ -411,6 +412,8 @@ cudaError_t launch_refit_static(const MeshDev *mesh_d, const MeshDev &mh, float4
 int raster_launches(int S, bool queue);
 cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st);
 // The FP32 trace (after launch_frame on the same stream).
+// The trace kernels' L1 / shared-memory split (once per process and device).
+cudaError_t configure_trace_kernels();
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st);
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
                           unsigned long long *stats_accum, cudaStream_t st);

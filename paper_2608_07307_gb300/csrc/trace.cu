@@ -118,6 +118,24 @@ struct TraceCtx {
 
 size_t trace_ctx_bytes() { return sizeof(TraceCtx); }
 
+// The trace kernels' dynamic shared memory: the slot context up to the most
+// parts of the launch's slots (16-byte rounded), then the per-thread hit
+// columns of the most segments; sized per launch so that the blocks an SM runs
+// fit the small shared-memory configuration the kernels ask for.
+__host__ __device__ __forceinline__ int trace_parts_cap(int ctx_parts)
+{
+    return ctx_parts > 0 && ctx_parts < kMaxParts ? ctx_parts : kMaxParts;
+}
+__host__ __device__ __forceinline__ size_t trace_ctx_dyn_bytes(int ctx_parts)
+{
+    return (offsetof(TraceCtx, part) + (size_t)trace_parts_cap(ctx_parts) * sizeof(PartView) + 15) / 16 * 16;
+}
+__host__ __device__ __forceinline__ size_t trace_dyn_bytes(int ctx_parts, int hpt_segs)
+{
+    const int ns = hpt_segs > 0 && hpt_segs < kMaxBounces + 1 ? hpt_segs : kMaxBounces + 1;
+    return trace_ctx_dyn_bytes(ctx_parts) + (size_t)ns * 128 * sizeof(int);
+}
+
 // x / N, as a product when N is a power of two (the same value, without an FP64 division)
 __device__ __forceinline__ double pix64(double x, double rN, int N) { return rN != 0.0 ? x * rN : x / N; }
 
@@ -1222,9 +1240,10 @@ template <bool COUNT, bool HITS>
 __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_trace(TraceArgs a)
 {
     pdl_enter();
-    __shared__ TraceCtx B;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    TraceCtx &B = *reinterpret_cast<TraceCtx *>(s_dyn);
+    int *s_hpt = reinterpret_cast<int *>(s_dyn + trace_ctx_dyn_bytes(a.ctx_parts));
     __shared__ int s_cand[kCand * kLaneStride];
-    __shared__ int s_hpt[(kMaxBounces + 1) * kLaneStride];
     trace_block<COUNT, HITS, false>(a, blockIdx.x, B, s_cand, s_hpt);
 }
 
@@ -1312,9 +1331,10 @@ template <bool COUNT, bool HITS>
 __global__ void __launch_bounds__(kTileRays * kTraceWarps, 32 / kTraceWarps) k_queue(TraceArgs a)
 {
     pdl_enter();
-    __shared__ TraceCtx B;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    TraceCtx &B = *reinterpret_cast<TraceCtx *>(s_dyn);
+    int *s_hpt = reinterpret_cast<int *>(s_dyn + trace_ctx_dyn_bytes(a.ctx_parts));
     __shared__ int s_cand[kCand * kLaneStride];
-    __shared__ int s_hpt[(kMaxBounces + 1) * kLaneStride];
     __shared__ unsigned s_item;
     __shared__ int s_ok, s_ready;  // s_ready: a slot whose second pass this block has seen complete
     const unsigned lane = threadIdx.x & 31u;
@@ -2302,6 +2322,32 @@ cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
     return launch_chained(k_raster_big<1>, dim3(big_blocks), dim3(256), 0, st, a);
 }
 
+// The trace kernels' split of the SM's 256 KB between L1 and shared memory: a
+// 64 KB shared-memory configuration leaves 192 KB of L1 for the hot tree nodes
+// and the traversal stacks (measured faster than the driver's default of 132
+// KB and than 100 KB); with the context and hit columns sized per launch, the
+// eight blocks the registers allow still fit it for meshes of few parts and
+// few bounces.  A percentage of the largest shared-memory configuration (228
+// KB), rounded up by the driver to a configuration it supports.
+constexpr int kTraceCarveoutPct = 27;
+
+cudaError_t configure_trace_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, kTraceCarveoutPct);
+    };
+    set((const void *)k_trace<false, false>);
+    set((const void *)k_trace<false, true>);
+    set((const void *)k_trace<true, false>);
+    set((const void *)k_trace<true, true>);
+    set((const void *)k_queue<false, false>);
+    set((const void *)k_queue<false, true>);
+    set((const void *)k_queue<true, false>);
+    set((const void *)k_queue<true, true>);
+    return e;
+}
+
 cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
 {
     (void)S;
@@ -2309,14 +2355,15 @@ cudaError_t launch_trace(const TraceArgs &a, int S, cudaStream_t st)
     // the hit records and the traversal counters are separate kernel variants:
     // code a launch never runs still costs registers in the others
     const dim3 g(a.n_tiles), b(kTileRays * kTraceWarps);
+    const size_t dyn = trace_dyn_bytes(a.ctx_parts, a.hpt_segs);
     if (a.queue) {
         // persistent: as many blocks as fit on the device at once
         const dim3 gq(device_sms() * kQueueBlocksPerSM);
-        if (a.count) return launch_chained(a.hits ? k_queue<true, true> : k_queue<true, false>, gq, b, 0, st, a);
-        return launch_chained(a.hits ? k_queue<false, true> : k_queue<false, false>, gq, b, 0, st, a);
+        if (a.count) return launch_chained(a.hits ? k_queue<true, true> : k_queue<true, false>, gq, b, dyn, st, a);
+        return launch_chained(a.hits ? k_queue<false, true> : k_queue<false, false>, gq, b, dyn, st, a);
     }
-    if (a.count) return launch_chained(a.hits ? k_trace<true, true> : k_trace<true, false>, g, b, 0, st, a);
-    return launch_chained(a.hits ? k_trace<false, true> : k_trace<false, false>, g, b, 0, st, a);
+    if (a.count) return launch_chained(a.hits ? k_trace<true, true> : k_trace<true, false>, g, b, dyn, st, a);
+    return launch_chained(a.hits ? k_trace<false, true> : k_trace<false, false>, g, b, dyn, st, a);
 }
 
 cudaError_t launch_reduce(const TraceArgs &a, int S, int eval0, double *force, double *torque, int *err_flags,
