@@ -586,9 +586,23 @@ __device__ __forceinline__ bool nearest32(const TraceCtx &B, const Ray32 &r, flo
                         float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
                         // coordinate error: origin error (delta) + subtraction, shear and
                         // reflected-direction rounding, growing with this triangle's distance
-                        float dz = fmaxf(fmaxf(fabsf(Akz), fabsf(Bkz)), fabsf(Ckz)) + fmaxf(fmaxf(fabsf(Ax), fabsf(Bx)), fabsf(Cx)) +
-                                   fmaxf(fmaxf(fabsf(Ay), fabsf(By)), fabsf(Cy));
+                        const float mxy = fmaxf(fmaxf(fabsf(Ax), fabsf(Bx)), fabsf(Cx)), myy = fmaxf(fmaxf(fabsf(Ay), fabsf(By)), fabsf(Cy));
+                        float dz = fmaxf(fmaxf(fabsf(Akz), fabsf(Bkz)), fabsf(Ckz)) + mxy + myy;
                         float dc = fmaf(16.0f * kU, dz, delta);
+                        // the common case first: with M the largest |x|, |y| of the three
+                        // vertices, every edge function's bound below is at most
+                        // 4 M dc + 2 M^2 u4 (the factor covers this sum's own rounding);
+                        // an edge function beyond it on each side is a certain miss, as
+                        // classify would find with the exact bounds
+                        const float Mv = fmaxf(mxy, myy);
+                        if (Mv > 1e-18f) {
+                            const float Eb = fmaf(dc, 4.0f * Mv, (2.0f * u4) * Mv * Mv) * 1.001f;
+                            if (fminf(fminf(U, V), W) < -Eb && fmaxf(fmaxf(U, V), W) > Eb) {
+                                if (sp == 0) break;
+                                ref = stack[--sp];
+                                continue;
+                            }
+                        }
                         float eU = dc * (fabsf(Bx) + fabsf(By) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Cx * By) + fabsf(Cy * Bx));
                         float eV = dc * (fabsf(Ax) + fabsf(Ay) + fabsf(Cx) + fabsf(Cy)) + u4 * (fabsf(Ax * Cy) + fabsf(Ay * Cx));
                         float eW = dc * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + u4 * (fabsf(Bx * Ay) + fabsf(By * Ax));
