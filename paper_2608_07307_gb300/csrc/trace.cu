@@ -2336,13 +2336,15 @@ cudaError_t launch_frame(const TraceArgs &a, int S, cudaStream_t st)
     return launch_chained(k_raster_big<1>, dim3(big_blocks), dim3(256), 0, st, a);
 }
 
-// The trace kernels' split of the SM's 256 KB between L1 and shared memory: a
-// 64 KB shared-memory configuration leaves 192 KB of L1 for the hot tree nodes
-// and the traversal stacks (measured faster than the driver's default of 132
-// KB and than 100 KB); with the context and hit columns sized per launch, the
-// eight blocks the registers allow still fit it for meshes of few parts and
-// few bounces.  A percentage of the largest shared-memory configuration (228
-// KB), rounded up by the driver to a configuration it supports.
+// The trace kernels' split of the SM's 256 KB between L1 and shared memory:
+// a request for a small shared-memory configuration, so that L1 keeps most of
+// the SM's memory for the hot tree nodes and the traversal stacks.  The
+// driver's default had been 132 KB of shared memory (L1 124 KB); with this
+// request and the context and hit columns sized per launch (7.4 KB a block of
+// the headline workload) it takes 100 KB for the eight blocks the registers
+// allow (L1 156 KB, L1 hit rate 68 -> 74%).  A percentage of the largest
+// shared-memory configuration (228 KB); the driver rounds it up to a
+// configuration that holds the blocks.
 constexpr int kTraceCarveoutPct = 27;
 
 cudaError_t configure_trace_kernels()
