@@ -102,3 +102,25 @@ def test_raster_against_oracle_spacecraft(ctx):
     for ray in diff:
         k = int(np.argmax(H[0][ray] != r["hits"][ray]))
         assert r["edge"][ray, k] < 1e-6 * r["win"][6]
+
+
+@pytest.mark.parametrize("name", ["spacecraft", "fan", "stack"])
+def test_launch_shapes_give_the_same_evaluation(ctx, name):
+    """A launch of fewer than four evaluations clears the pixel keys in the frame
+    kernel, runs the second raster pass as one launch and poses one vertex a
+    thread; larger launches use a clear kernel, two second-pass launches and
+    four vertices a thread.  Each evaluation's hits, force and torque are the
+    same bits either way (every decision and every sum is per slot, in a fixed
+    order)."""
+    make, dirs, N, B = CASES[name]
+    m = make()
+    dirs = np.asarray(dirs, np.float64)
+    dirs = dirs / np.linalg.norm(dirs, axis=1, keepdims=True)
+    many = np.concatenate([dirs] * (8 // len(dirs) + 1))[:8]
+    mid = ctx.load_mesh(m)
+    Fm, Tm, Hm = ctx.eval_batch(mid, many, N=N, bounces=B, hits=True)
+    for k in range(len(dirs)):
+        F1, T1, H1 = ctx.eval_batch(mid, many[k:k + 1], N=N, bounces=B, hits=True)
+        assert np.array_equal(H1[0], Hm[k]), (name, k)
+        assert np.array_equal(F1[0], Fm[k]) and np.array_equal(T1[0], Tm[k]), (name, k)
+    ctx.free_mesh(mid)
