@@ -1992,8 +1992,9 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a, int eval0, double 
     Comp32 f32[6];  // the FP32 sum modes
     for (int k = 0; k < 6; k++) f32[k] = Comp32{0.0f, 0.0f};
     const int mode = a.sum_mode;
-    unsigned long long c[kCnt];
-    for (int k = 0; k < kCnt; k++) c[k] = 0ull;
+    // counts of one block (at most 512 tiles of 32 rays) fit 32 bits
+    unsigned c[kCnt];
+    for (int k = 0; k < kCnt; k++) c[k] = 0u;
     const int kc = a.count ? kCnt : 7;  // the trace writes the traversal counters only when counting
     int mine = 0;
     for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
@@ -2025,7 +2026,7 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a, int eval0, double 
             else if (mode == 1) comp_add(f32[k], (float)acc[k]);
             else f32[k].hi = __fadd_rn(f32[k].hi, (float)acc[k]);
         }
-        for (int k = 0; k < kCnt; k++) c[k] += (unsigned long long)acc[6 + k];
+        for (int k = 0; k < kCnt; k++) c[k] += (unsigned)acc[6 + k];
         if (flags) atomicOr(&blk_flags, flags);
         __syncthreads();
         if (threadIdx.x == 0 && blk_flags) atomicOr(&a.pose[s].flags, blk_flags);
@@ -2045,8 +2046,10 @@ __global__ void __launch_bounds__(256) k_reduce1(TraceArgs a, int eval0, double 
         for (int k = 0; k < 6; k++) r32[k][threadIdx.x] = f32[k];
     }
     for (int k = 0; k < kCnt; k++) {
-        unsigned long long x = c[k];
-        for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        // only the live counts (kc is uniform over the launch)
+        unsigned x = c[k];
+        if (k < kc)
+            for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if (lane == 0) rc[k][w] = x;
     }
     __syncthreads();
