@@ -3,15 +3,18 @@
 //
 // k_frame.  Once per slot: the window (u, v bounds from the vertex pass), the
 // FP32 ray generation, the error bounds of the FP32 decisions and the
-// per-part traversal views, into a small context every trace block copies.
+// per-part traversal views, into a small context every trace block copies;
+// in launches of few slots its extra blocks also clear the pixel keys
+// (k_clear_keys otherwise).
 //
-// k_raster / k_raster_big / k_raster_chunks (primary visibility).  All primary
+// k_raster / k_raster_big / k_raster_chunks / k_raster_pass1 (primary visibility).  All primary
 // rays of an evaluation are parallel, so each triangle applies the trace's own
 // FP32 view-frame test (prim_test) to the pixel centres inside its projected
 // box: pass 0 keeps the nearest certain hit per pixel (64-bit atomic minimum of
 // depth bits and triangle), pass 1 lists the triangles whose decision there was
 // uncertain against it.  Large projected triangles are rasterised in 16 x 16
-// pixel chunks, a warp each, listing only the chunks that can meet them.
+// pixel chunks, a warp each, listing only the chunks that can meet them
+// (k_raster_pass1: the second pass over both kinds in one launch).
 //
 // k_trace (FP32 fast path).  A block is four warps, each over a 32-pixel tile
 // (8 x 4 by default; the shape is chosen per mesh, grid and bounce count by the
@@ -53,10 +56,12 @@
 // ray; leaves pre-tested in FP32 with a bound, so only triangles not certainly
 // missed are tested in FP64) and the same watertight test in FP64.
 //
-// k_reduce1 + k_reduce.  Fixed-order FP64 sums: contiguous ranges of tile
-// partials (and the re-traced rays of those tiles) per first-level block, then
-// those per evaluation, scaled by P0 / dist^2 times the pixel area.  No atomics on data:
-// results are bit-reproducible for a given launch shape.
+// k_reduce1 (+ k_reduce after diffuse rays).  Fixed-order FP64 sums: contiguous
+// ranges of tile partials (and the re-traced rays of those tiles) per
+// first-level block, then those per evaluation in block order, by the last
+// first-level block of the evaluation to finish (an atomic ticket; without
+// diffuse rays) or by k_reduce, scaled by P0 / dist^2 times the pixel area.  No
+// atomics on data: results are bit-reproducible.
 //
 // k_diffuse (optional, Sec. 6.1's diffuse rays).  After the re-trace, a thread per
 // (primary ray, sample) replays the ray's specular chain in FP64 through the recorded
