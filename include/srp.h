@@ -217,7 +217,8 @@ const char *srp_last_error(const srp_ctx *ctx);
  * its boxes to the rest pose.  mesh_id receives a handle >= 0.
  * Errors: SRP_ERR_ARG (NULL pointers, counts <= 0, limits exceeded),
  * SRP_ERR_MESH (index out of range, parent order, shared vertex, degenerate
- * triangle, material coefficients outside [0, 1] or summing above 1).
+ * triangle, material coefficients outside [0, 1] or summing above 1, a part
+ * of 2^24 triangles or more).
  */
 srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *desc, int32_t *mesh_id);
 

@@ -1088,6 +1088,14 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
         double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
         if (!(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] > 0.0)) return fail(ctx, SRP_ERR_MESH, "triangle %d is degenerate", t);
     }
+    {
+        // a hit is recorded as (part << 24) | the triangle's index within its part
+        std::vector<int> per_part(NP, 0);
+        for (int t = 0; t < NT; t++) per_part[D->tri_part[t]]++;
+        for (int p = 0; p < NP; p++)
+            if (per_part[p] >= (1 << 24))
+                return fail(ctx, SRP_ERR_MESH, "part %d has %d triangles (at most %d a part)", p, per_part[p], (1 << 24) - 1);
+    }
     // ---- layout: static parts first, then dynamic; vertices and triangles grouped by part
     std::vector<int> order;
     for (int p = 0; p < NP; p++) if (!dynamic[p]) order.push_back(p);
@@ -1254,8 +1262,15 @@ srp_status srp_mesh_load(srp_ctx *ctx, const srp_mesh_desc *D, int32_t *mesh_id)
             if (D->tri_part[sorig[k]] != order[r]) return bail(SRP_ERR_CUDA, "sort mixed parts", cudaErrorUnknown);
     }
     MK(cudaMemcpyAsync(h.tri_vidx, svidx.data(), sizeof(int) * svidx.size(), cudaMemcpyHostToDevice, st));
+    // vertex ids, and in the fourth word the triangle's hit record (part << 24) |
+    // index within the part, which the raster writes into the pixel keys
     std::vector<int4> sv4(NT);
     for (int k = 0; k < NT; k++) sv4[k] = make_int4(svidx[3 * (size_t)k], svidx[3 * (size_t)k + 1], svidx[3 * (size_t)k + 2], 0);
+    for (int r = 0; r < NP; r++) {
+        const int p = order[r];
+        const PartInfo &pi = h.part[p];
+        for (int k = pi.tri_begin; k < pi.tri_begin + pi.tri_count; k++) sv4[k].w = (p << 24) | (k - pi.tri_begin);
+    }
     MK(cudaMemcpyAsync(h.tri_v4, sv4.data(), sizeof(int4) * NT, cudaMemcpyHostToDevice, st));
     MK(cudaMemcpyAsync(h.tri_orig, sorig.data(), sizeof(int) * NT, cudaMemcpyHostToDevice, st));
     std::vector<int> spos(NT);

@@ -152,7 +152,7 @@ struct MeshDev {
     double *rest64;        // [n_verts][3] rest pose FP64 (part-major)
     int *vert_part;        // [n_verts]
     int *tri_vidx;         // [n_tris][3] sorted triangles -> global vertex index
-    int4 *tri_v4;          // [n_tris] the same, padded to one 16-byte load
+    int4 *tri_v4;          // [n_tris] the same, and (part << 24) | index within the part in .w
     int *tri_orig;         // [n_tris] sorted -> original triangle id
     int *tri_pos;          // [n_tris] original triangle id -> sorted position
     unsigned *tri_mat;     // [n_tris] sorted -> (front | back << 16)

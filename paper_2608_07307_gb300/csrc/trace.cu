@@ -90,7 +90,7 @@ struct PartView {
     const double *v64;   // v64[3 * (vi - vert_begin) + c]
     int root;            // 0, or ~0 for a one-triangle part
     int limit;           // bound on loop iterations of one part walk (nodes + triangles)
-    int tri_begin, tri_count, vert_begin;
+    int tri_begin, vert_begin;
     float box[6];        // root box (filled when a block loads the context, from box_src)
     const float *box_src;  // the part's root box: the refit's output for a dynamic part
 };
@@ -221,7 +221,6 @@ __global__ void k_frame(TraceArgs a)
         pv.root = pi.tri_count > 1 ? 0 : ~0;
         pv.limit = a.walk_limit_test ? 1 : pi.node_count + pi.tri_count + 8;
         pv.tri_begin = pi.tri_begin;
-        pv.tri_count = pi.tri_count;
         pv.vert_begin = pi.vert_begin;
         pv.v4 = tri_v4 + pi.tri_begin;
         if (pi.dynamic) {
@@ -874,22 +873,6 @@ __device__ __forceinline__ int part_of_sorted(const MeshDev *m, int t)
     return p;
 }
 
-// Part of sorted triangle t from the context's part views (parts are
-// contiguous ranges of the sorted order); tb: the part's first triangle.
-__device__ __forceinline__ int part_of_view(const TraceCtx *g, int np, int t, int &tb)
-{
-    int p = 0;
-    tb = 0;
-#pragma unroll
-    for (int q = 0; q < kMaxParts; q++) {
-        if (q < np) {
-            const int b0 = g->part[q].tri_begin, c0 = g->part[q].tri_count;
-            if (t >= b0 && t < b0 + c0) { p = q; tb = b0; }
-        }
-    }
-    return p;
-}
-
 // Thread per (slot, sorted triangle): small projected boxes in place; larger
 // ones are listed for k_raster_chunks, which lists their 16 x 16-pixel chunks
 // that can meet them for k_raster_big (pass 0 lists, pass 1 reuses the lists).
@@ -898,7 +881,7 @@ __device__ __forceinline__ void raster_tri(const TraceArgs &a, int s, int t)
 {
     const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
     // the slot's context in one round of loads (nothing read from the mesh record)
-    const int skip = g->skip, n_tris = g->n_tris, np = g->n_parts;
+    const int skip = g->skip, n_tris = g->n_tris;
     const int4 *tv4 = g->tri_v4;
     const RastView V = rast_view(a, s);
     if (skip || t >= n_tris) return;
@@ -908,8 +891,6 @@ __device__ __forceinline__ void raster_tri(const TraceArgs &a, int s, int t)
     }
     const int4 vi = __ldg(tv4 + t);
     const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
-    int tb = 0;
-    const int p = part_of_view(g, np, t, tb);
     int i0, i1, j0, j1;
     if (!rast_box(V, A, B, C, i0, i1, j0, j1)) return;
     const int w = i1 - i0 + 1, h = j1 - j0 + 1;
@@ -925,7 +906,7 @@ __device__ __forceinline__ void raster_tri(const TraceArgs &a, int s, int t)
         }
         return;
     }
-    const unsigned id = ((unsigned)p << 24) | (unsigned)(t - tb);
+    const unsigned id = (unsigned)vi.w;  // (part << 24) | index within the part
     const size_t off = (size_t)s * a.ray_stride;
     const float eb = rast_bound(V, A, B, C, i0, i1, j0, j1);
     for (int i = i0; i <= i1; i++)
@@ -997,17 +978,14 @@ __device__ __forceinline__ int raster_big_entry(const TraceArgs &a, unsigned e, 
     if (s < 0) return -1;
     const TraceCtx *g = reinterpret_cast<const TraceCtx *>(a.tctx) + s;
     const int4 *tv4 = g->tri_v4;
-    const int np = g->n_parts;
     const RastView V = rast_view(a, s);
     const int4 vi = __ldg(tv4 + t);
     const float4 A = __ldg(V.vview + vi.x), B = __ldg(V.vview + vi.y), C = __ldg(V.vview + vi.z);
-    int tb = 0;
-    const int p = part_of_view(g, np, t, tb);
     int i0, i1, j0, j1;
     if (!rast_box(V, A, B, C, i0, i1, j0, j1)) return s;
     const int ib = i0 + E.z * kRastChunk, jb = j0 + E.w * kRastChunk;
     const int ie = min(ib + kRastChunk - 1, i1), je = min(jb + kRastChunk - 1, j1);
-    const unsigned id = ((unsigned)p << 24) | (unsigned)(t - tb);
+    const unsigned id = (unsigned)vi.w;  // (part << 24) | index within the part
     const size_t off = (size_t)s * a.ray_stride;
     const float eb = rast_bound(V, A, B, C, ib, ie, jb, je);
     for (int q = (int)lane; q < kRastChunk * kRastChunk; q += 32) {
