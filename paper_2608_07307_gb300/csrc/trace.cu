@@ -99,6 +99,7 @@ struct TraceCtx {
     // FP32 ray generation: o = org + (i+.5) du + (j+.5) dv; view-frame pixel centres
     float org[3], du[3], dv[3], dir[3];
     float umin32, vmin32, du32, dv32, w0_32;
+    float rdu32, rdv32;    // 1 / du32, 1 / dv32 (the raster's conservative pixel boxes)
     float delta_p, tau_p;  // primary: bound on view-frame coordinate error, band on t
     float delta_s;         // secondary: origin-error term added per segment
     float R, L, pad, eps32;
@@ -259,6 +260,7 @@ __global__ void k_frame(TraceArgs a)
     }
     B.umin32 = (float)umin; B.vmin32 = (float)vmin;
     B.du32 = (float)(Du / N); B.dv32 = (float)(Dv / N);
+    B.rdu32 = 1.0f / B.du32; B.rdv32 = 1.0f / B.dv32;
     B.w0_32 = (float)w0;
     const double u = 5.9604644775390625e-8;
     // Primary (view frame): vertex projections rounded once (|p| u/2), pixel
@@ -724,7 +726,7 @@ __device__ __noinline__ Best32 resolve64(const TraceCtx &B, int N, int i, int j,
 
 struct RastView {
     const float4 *vview;
-    float umin32, vmin32, du32, dv32, w0, delta, tau;
+    float umin32, vmin32, du32, dv32, rdu32, rdv32, w0, delta, tau;
     int N;
 };
 
@@ -734,6 +736,7 @@ __device__ __forceinline__ RastView rast_view(const TraceArgs &a, int s)
     RastView V;
     V.vview = g->vview;
     V.umin32 = g->umin32; V.vmin32 = g->vmin32; V.du32 = g->du32; V.dv32 = g->dv32;
+    V.rdu32 = g->rdu32; V.rdv32 = g->rdv32;
     V.w0 = g->w0_32; V.delta = g->delta_p; V.tau = g->tau_p;
     V.N = a.sd[s].N;
     return V;
@@ -747,10 +750,12 @@ __device__ __forceinline__ bool rast_box(const RastView &V, float4 a, float4 b, 
 {
     const float mu = 0.01f * V.du32 + 64.0f * V.delta, mv = 0.01f * V.dv32 + 64.0f * V.delta;
     const float lim = (float)V.N + 1.0f;
-    float ulo = (fminf(fminf(a.x, b.x), c.x) - mu - V.umin32) / V.du32 - 0.5f;
-    float uhi = (fmaxf(fmaxf(a.x, b.x), c.x) + mu - V.umin32) / V.du32 - 0.5f;
-    float vlo = (fminf(fminf(a.y, b.y), c.y) - mv - V.vmin32) / V.dv32 - 0.5f;
-    float vhi = (fmaxf(fmaxf(a.y, b.y), c.y) + mv - V.vmin32) / V.dv32 - 0.5f;
+    // products with the reciprocal pixel sizes: their rounding (~1e-4 pixel at
+    // N = 1024) is far inside the hundredth of a pixel the box is widened by
+    float ulo = (fminf(fminf(a.x, b.x), c.x) - mu - V.umin32) * V.rdu32 - 0.5f;
+    float uhi = (fmaxf(fmaxf(a.x, b.x), c.x) + mu - V.umin32) * V.rdu32 - 0.5f;
+    float vlo = (fminf(fminf(a.y, b.y), c.y) - mv - V.vmin32) * V.rdv32 - 0.5f;
+    float vhi = (fmaxf(fmaxf(a.y, b.y), c.y) + mv - V.vmin32) * V.rdv32 - 0.5f;
     ulo = fminf(fmaxf(ulo, -1.0f), lim); uhi = fminf(fmaxf(uhi, -1.0f), lim);
     vlo = fminf(fmaxf(vlo, -1.0f), lim); vhi = fminf(fmaxf(vhi, -1.0f), lim);
     i0 = max((int)ceilf(ulo), 0); i1 = min((int)floorf(uhi), V.N - 1);
