@@ -43,12 +43,12 @@ NODE_BYTES, TRI_BYTES = 128, 48  # one 4-wide BVH node, one FP32 triangle record
 # DRAM bytes (read + write) of one k_trace launch of the headline workload (8
 # evaluations), from one ncu capture of the current kernel; None when the kernel
 # changed after the capture
-TRACE_DRAM_BYTES_PER_LAUNCH = 124.8e6 + 21.0e6  # mean of three launches, ncu dram__bytes_read/write.sum
+TRACE_DRAM_BYTES_PER_LAUNCH = 124.2e6 + 20.6e6  # mean of three launches, ncu dram__bytes_read/write.sum
 # the same capture's unit throughputs, % of the GB300's peak for each unit
-TRACE_NCU_PCT_OF_PEAK = {"l1tex": 62.7, "l2": 23.5, "dram": 2.5, "sm_issue_active": 65.4,
-                         "l2_bytes_per_launch": 3.401e9, "l1_bytes_per_launch": 4.687e9}
+TRACE_NCU_PCT_OF_PEAK = {"l1tex": 61.4, "l2": 23.0, "dram": 2.6, "sm_issue_active": 66.3,
+                         "l2_bytes_per_launch": 3.272e9, "l1_bytes_per_launch": 4.678e9}
 # L2 bandwidth implied by that capture: L2 bytes / (L2 throughput % / 100) / duration
-L2_PEAK_GBS = 3.401e9 / 0.2350 / 729.2e-6 / 1e9
+L2_PEAK_GBS = 3.272e9 / 0.2300 / 712.5e-6 / 1e9
 HBM_FALLBACK_GBS = 6800.0  # the profiling recipe's fallback when no measured peak is present
 
 
