@@ -5,7 +5,8 @@
 // angles (hence the joint offsets and, through Sun tracking, the Sun
 // direction), the Sun direction and the Sun distance (Sec. 4.3, 4.4.2, 6.1).
 //
-//   k_adj_window  one block per slot: the posed vertices extreme along u and v
+//   k_adj_window  blocks per slot over the posed vertices, extreme along u and v
+//                 (k_adj_window_merge: the blocks' extremes in block order)
 //                 (lowest vertex index among equal projections).
 //   k_adj_rays    grid-stride over the rays of every slot: per ray, the
 //                 segments are replayed forward in FP32 from the recorded hits,
@@ -98,7 +99,7 @@ __device__ inline void warp_scatter(int key, const double *val, double *row)
 // ------------------------------------------------------------- window
 __global__ void __launch_bounds__(kAdjThreads) k_adj_window(AdjArgs a)
 {
-    const int s = blockIdx.x;
+    const int s = blockIdx.y, b = blockIdx.x, G = gridDim.x;
     const SlotPose &P = a.pose[s];
     if (P.skip) return;
     const MeshDev &m = *a.sd[s].mesh;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_window(AdjArgs a)
     V3 u = ld3(P.u), v = ld3(P.v);
     double best[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
     int id[4] = {-1, -1, -1, -1};
-    for (int k = threadIdx.x; k < m.n_verts; k += blockDim.x) {  // ascending k per thread
+    for (int k = b * blockDim.x + threadIdx.x; k < m.n_verts; k += G * blockDim.x) {  // ascending k per thread
         V3 x = vertex(m, sb, k);
         double pu = dot(u, x), pv = dot(v, x);
         if (pu < best[0]) { best[0] = pu; id[0] = k; }
@@ -132,7 +133,32 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_window(AdjArgs a)
         }
         __syncthreads();
     }
-    if (threadIdx.x < 4) a.win_ids[4 * s + threadIdx.x] = si[threadIdx.x][0];
+    if (threadIdx.x < 4) {
+        const size_t o = ((size_t)s * G + b) * 4 + threadIdx.x;
+        a.win_val[o] = sv[threadIdx.x][0];
+        a.win_pid[o] = si[threadIdx.x][0];
+    }
+}
+
+// The blocks' extremes of a slot merged in block order: the extreme value, the
+// lowest vertex id among equal values (the single-block search's result).
+__global__ void k_adj_window_merge(AdjArgs a, int G)
+{
+    const int s = blockIdx.x, c = threadIdx.x;
+    if (a.pose[s].skip || c >= 4) return;
+    double best = (c & 1) ? -INFINITY : INFINITY;
+    int id = -1;
+    for (int b = 0; b < G; b++) {
+        const size_t o = ((size_t)s * G + b) * 4 + c;
+        const double v = a.win_val[o];
+        const int i = a.win_pid[o];
+        const bool take = (c & 1) ? (v > best) : (v < best);
+        if (i >= 0 && (id < 0 || take || (v == best && i < id))) {
+            best = v;
+            id = i;
+        }
+    }
+    a.win_ids[4 * s + c] = id;
 }
 
 // --------------------------------------------------------------- rays
@@ -513,7 +539,11 @@ int adj_blocks(int S, size_t rays)
 
 cudaError_t launch_adjoint(const AdjArgs &a, int S, cudaStream_t st)
 {
-    k_adj_window<<<S, kAdjThreads, 0, st>>>(a);
+    // the window search over the vertices: several blocks a slot (four vertices
+    // a thread), merged in block order
+    const int G = std::max(1, std::min(kAdjWinBlocks, (a.n_verts + 4 * kAdjThreads - 1) / (4 * kAdjThreads)));
+    k_adj_window<<<dim3(G, S), kAdjThreads, 0, st>>>(a);
+    k_adj_window_merge<<<S, 32, 0, st>>>(a, G);
     size_t smem = sizeof(double) * (size_t)kAdjWarps * a.width;
     k_adj_rays<<<dim3(a.nb, S), kAdjThreads, smem, st>>>(a);
     k_adj_finish<<<S, 128, sizeof(double) * a.width, st>>>(a);

@@ -110,6 +110,10 @@ struct srp_ctx {
     size_t adj_partials_cap = 0;
     int *win_ids = nullptr;
     size_t win_ids_cap = 0;
+    double *win_val = nullptr;
+    size_t win_val_cap = 0;
+    int *win_pid = nullptr;
+    size_t win_pid_cap = 0;
     double *gio = nullptr;
     size_t gio_cap = 0;
     // propagation adjoint
@@ -644,6 +648,8 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
         pl.wa = kAdjFixed + 2 * m->h.n_mats + 6 * m->h.n_parts;
         CK(ctx, grow(&ctx->adj_partials, &ctx->adj_partials_cap, SL * pl.nba * pl.wa, false));
         CK(ctx, grow(&ctx->win_ids, &ctx->win_ids_cap, SL * 4, false));
+        CK(ctx, grow(&ctx->win_val, &ctx->win_val_cap, SL * kAdjWinBlocks * 4, false));
+        CK(ctx, grow(&ctx->win_pid, &ctx->win_pid_cap, SL * kAdjWinBlocks * 4, false));
     }
     return SRP_OK;
 }
@@ -765,12 +771,15 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             g.nb = pl.nba;
             g.width = pl.wa;
             g.win_ids = ctx->win_ids + s0 * 4;
+            g.win_val = ctx->win_val + s0 * kAdjWinBlocks * 4;
+            g.win_pid = ctx->win_pid + s0 * kAdjWinBlocks * 4;
+            g.n_verts = h.n_verts;
             g.partials = ctx->adj_partials + s0 * pl.nba * pl.wa;
             g.g_sun = adj->g_sun;
             g.g_dist = adj->g_dist;
             g.g_eval = adj->g_eval;
             CK(ctx, launch_adjoint(g, Sc, ls));
-            launches += 3;  // window vertices, rays, finish
+            launches += 4;  // window search and merge, rays, finish
         }
         tm.span(0, g0, g1);
         tm.span(5, g1, g1r);
@@ -822,12 +831,15 @@ srp_status adj_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const 
         g.nb = pl.nba;
         g.width = pl.wa;
         g.win_ids = ctx->win_ids;
+        g.win_val = ctx->win_val;
+        g.win_pid = ctx->win_pid;
+        g.n_verts = h.n_verts;
         g.partials = ctx->adj_partials;
         g.g_sun = ab.g_sun;
         g.g_dist = ab.g_dist;
         g.g_eval = ab.g_eval;
         CK(ctx, launch_adjoint(g, Sc, st));
-        launches += 5;
+        launches += 6;  // pose, vertices, window search and merge, rays, finish
     }
     return SRP_OK;
 }
@@ -1007,6 +1019,8 @@ void srp_destroy(srp_ctx *ctx)
     dfree(ctx->hits);
     dfree(ctx->adj_partials);
     dfree(ctx->win_ids);
+    dfree(ctx->win_val);
+    dfree(ctx->win_pid);
     dfree(ctx->gio);
     dfree(ctx->sdesc);
     dfree(ctx->arc_hits);
