@@ -388,7 +388,23 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rays(AdjArgs a)
 }
 
 // -------------------------------------------------------------- finish
-__global__ void __launch_bounds__(128) k_adj_finish(AdjArgs a)
+// The column sums of runs of kAdjSumRun ray-block partials, a block per (run,
+// slot): the first of two fixed-order levels when a slot has many ray blocks
+// (one evaluation a launch), so that no single thread adds hundreds of FP64
+// values in a row.
+__global__ void __launch_bounds__(128) k_adj_finish_sum(AdjArgs a)
+{
+    const int s = blockIdx.y, g = blockIdx.x, G = gridDim.x, W = a.width;
+    if (a.pose[s].skip) return;
+    const int b0 = g * kAdjSumRun, b1 = min(b0 + kAdjSumRun, a.nb);
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+        double x = 0.0;
+        for (int b = b0; b < b1; b++) x += a.partials[((size_t)s * a.nb + b) * W + k];
+        a.partials2[((size_t)s * G + g) * W + k] = x;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_adj_finish(AdjArgs a, int runs)
 {
     const int s = blockIdx.x;
     const SlotPose &P = a.pose[s];
@@ -403,9 +419,12 @@ __global__ void __launch_bounds__(128) k_adj_finish(AdjArgs a)
         return;
     }
     extern __shared__ double tot[];  // [W]
+    // the ray blocks' partials in block order, directly or as the runs' sums in run order
+    const double *src = runs > 0 ? a.partials2 : a.partials;
+    const int cnt = runs > 0 ? runs : a.nb;
     for (int k = threadIdx.x; k < W; k += blockDim.x) {
         double x = 0.0;
-        for (int b = 0; b < a.nb; b++) x += a.partials[((size_t)s * a.nb + b) * W + k];
+        for (int b = 0; b < cnt; b++) x += src[((size_t)s * cnt + b) * W + k];
         tot[k] = x;
     }
     __syncthreads();
@@ -546,7 +565,9 @@ cudaError_t launch_adjoint(const AdjArgs &a, int S, cudaStream_t st)
     k_adj_window_merge<<<S, 32, 0, st>>>(a, G);
     size_t smem = sizeof(double) * (size_t)kAdjWarps * a.width;
     k_adj_rays<<<dim3(a.nb, S), kAdjThreads, smem, st>>>(a);
-    k_adj_finish<<<S, 128, sizeof(double) * a.width, st>>>(a);
+    const int runs = a.nb > 2 * kAdjSumRun && a.partials2 ? (a.nb + kAdjSumRun - 1) / kAdjSumRun : 0;
+    if (runs > 0) k_adj_finish_sum<<<dim3(runs, S), 128, 0, st>>>(a);
+    k_adj_finish<<<S, 128, sizeof(double) * a.width, st>>>(a, runs);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,8 @@ struct srp_ctx {
     // adjoint
     double *adj_partials = nullptr;
     size_t adj_partials_cap = 0;
+    double *adj_partials2 = nullptr;
+    size_t adj_partials2_cap = 0;
     int *win_ids = nullptr;
     size_t win_ids_cap = 0;
     double *win_val = nullptr;
@@ -647,6 +649,8 @@ srp_status eval_plan(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, int n, b
         pl.nba = adj_blocks(pl.S, pl.R);
         pl.wa = kAdjFixed + 2 * m->h.n_mats + 6 * m->h.n_parts;
         CK(ctx, grow(&ctx->adj_partials, &ctx->adj_partials_cap, SL * pl.nba * pl.wa, false));
+        CK(ctx, grow(&ctx->adj_partials2, &ctx->adj_partials2_cap,
+                     SL * (size_t)((pl.nba + kAdjSumRun - 1) / kAdjSumRun) * pl.wa, false));
         CK(ctx, grow(&ctx->win_ids, &ctx->win_ids_cap, SL * 4, false));
         CK(ctx, grow(&ctx->win_val, &ctx->win_val_cap, SL * kAdjWinBlocks * 4, false));
         CK(ctx, grow(&ctx->win_pid, &ctx->win_pid_cap, SL * kAdjWinBlocks * 4, false));
@@ -775,6 +779,7 @@ srp_status eval_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const
             g.win_pid = ctx->win_pid + s0 * kAdjWinBlocks * 4;
             g.n_verts = h.n_verts;
             g.partials = ctx->adj_partials + s0 * pl.nba * pl.wa;
+            g.partials2 = ctx->adj_partials2 + s0 * (size_t)((pl.nba + kAdjSumRun - 1) / kAdjSumRun) * pl.wa;
             g.g_sun = adj->g_sun;
             g.g_dist = adj->g_dist;
             g.g_eval = adj->g_eval;
@@ -835,6 +840,7 @@ srp_status adj_enqueue(srp_ctx *ctx, Mesh *m, const srp_eval_params *prm, const 
         g.win_pid = ctx->win_pid;
         g.n_verts = h.n_verts;
         g.partials = ctx->adj_partials;
+        g.partials2 = ctx->adj_partials2;
         g.g_sun = ab.g_sun;
         g.g_dist = ab.g_dist;
         g.g_eval = ab.g_eval;
@@ -1018,6 +1024,7 @@ void srp_destroy(srp_ctx *ctx)
     dfree(ctx->io);
     dfree(ctx->hits);
     dfree(ctx->adj_partials);
+    dfree(ctx->adj_partials2);
     dfree(ctx->win_ids);
     dfree(ctx->win_val);
     dfree(ctx->win_pid);

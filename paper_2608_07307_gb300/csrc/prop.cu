@@ -482,11 +482,14 @@ __global__ void k_adj_prop_out(int n, PropDev P, int stage, const StageRec *rec,
         double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2], rn = sqrt(r2);
         double mu = P.central == 1 ? kMuSun : kMuEarth;
         double ra = y[0] * ab[0] + y[1] * ab[1] + y[2] * ab[2];
-        for (int k = 0; k < 3; k++) rb[k] += -mu * (ab[k] / (r2 * rn) - 3.0 * y[k] * ra / (r2 * r2 * rn));
+        // one reciprocal instead of a division per term (GB300's FP64 divisions are long chains)
+        const double ir3 = 1.0 / (r2 * rn), ir5 = ir3 / r2;
+        for (int k = 0; k < 3; k++) rb[k] += -mu * (ab[k] * ir3 - 3.0 * y[k] * ra * ir5);
     }
     if (P.central == 0 && P.j2) {
         double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-        double z2 = y[2] * y[2] / r2;
+        const double ir2 = 1.0 / r2;
+        double z2 = y[2] * y[2] * ir2;
         double f = -1.5 * kJ2 * kMuEarth * kREarth * kREarth / (r2 * r2 * sqrt(r2));
         double g[3] = {y[0] * (1.0 - 5.0 * z2), y[1] * (1.0 - 5.0 * z2), y[2] * (3.0 - 5.0 * z2)};
         double fb = ab[0] * g[0] + ab[1] * g[1] + ab[2] * g[2];
@@ -494,25 +497,28 @@ __global__ void k_adj_prop_out(int n, PropDev P, int stage, const StageRec *rec,
         rb[1] += f * ab[1] * (1.0 - 5.0 * z2);
         rb[2] += f * ab[2] * (3.0 - 5.0 * z2);
         double z2b = -5.0 * f * (ab[0] * y[0] + ab[1] * y[1] + ab[2] * y[2]);
-        rb[2] += z2b * 2.0 * y[2] / r2;
-        double r2b = -z2b * y[2] * y[2] / (r2 * r2) + fb * (-2.5) * f / r2;
+        rb[2] += z2b * 2.0 * y[2] * ir2;
+        double r2b = -z2b * y[2] * y[2] * (ir2 * ir2) + fb * (-2.5) * f * ir2;
         for (int k = 0; k < 3; k++) rb[k] += 2.0 * r2b * y[k];
     }
     if (P.central == 0 && P.sun3) {
         double d[3] = {r.rsun[0] - y[0], r.rsun[1] - y[1], r.rsun[2] - y[2]};
         double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dn = sqrt(d2);
         double da = d[0] * ab[0] + d[1] * ab[1] + d[2] * ab[2];
-        for (int k = 0; k < 3; k++) rb[k] += -kMuSun * (ab[k] / (d2 * dn) - 3.0 * d[k] * da / (d2 * d2 * dn));
+        const double id3 = 1.0 / (d2 * dn), id5 = id3 / d2;
+        for (int k = 0; k < 3; k++) rb[k] += -kMuSun * (ab[k] * id3 - 3.0 * d[k] * da * id5);
     }
     if (r.lit) {
         // a_SRP = R F / m, s_body = R^T s_hat, s_hat = w / |w|, w = r_sun - r, dist = |w| / AU
         const double *R = r.R, *gs = g_sun + 3 * i;
         double Rb[9];
+        const double im = 1.0 / P.mass;
         for (int a = 0; a < 3; a++)
-            for (int b = 0; b < 3; b++) Rb[3 * a + b] = ab[a] * r.F[b] / P.mass;
+            for (int b = 0; b < 3; b++) Rb[3 * a + b] = ab[a] * r.F[b] * im;
         double w[3] = {r.rsun[0] - y[0], r.rsun[1] - y[1], r.rsun[2] - y[2]};
         double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-        double sh[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+        const double iwn = 1.0 / wn;
+        double sh[3] = {w[0] * iwn, w[1] * iwn, w[2] * iwn};
         double shb[3];
         for (int a = 0; a < 3; a++) {
             shb[a] = R[3 * a] * gs[0] + R[3 * a + 1] * gs[1] + R[3 * a + 2] * gs[2];
@@ -520,7 +526,7 @@ __global__ void k_adj_prop_out(int n, PropDev P, int stage, const StageRec *rec,
         }
         double sd = shb[0] * sh[0] + shb[1] * sh[1] + shb[2] * sh[2];
         for (int k = 0; k < 3; k++) {
-            double wb = (shb[k] - sd * sh[k]) / wn + g_dist[i] * sh[k] / kAU;
+            double wb = (shb[k] - sd * sh[k]) * iwn + g_dist[i] * sh[k] * (1.0 / kAU);
             rb[k] -= wb;
         }
         // attitude: R = Q(q) or R = L(y) Q(q)
@@ -553,10 +559,11 @@ __global__ void k_adj_prop_out(int n, PropDev P, int stage, const StageRec *rec,
             const double *v = y + 3;
             double hv[3] = {y[1] * v[2] - y[2] * v[1], y[2] * v[0] - y[0] * v[2], y[0] * v[1] - y[1] * v[0]};
             double hn = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
-            double hh[3] = {hv[0] / hn, hv[1] / hn, hv[2] / hn};
+            const double ihn = 1.0 / hn;
+            double hh[3] = {hv[0] * ihn, hv[1] * ihn, hv[2] * ihn};
             double yd = ybb[0] * hh[0] + ybb[1] * hh[1] + ybb[2] * hh[2];
             double hb[3];
-            for (int k = 0; k < 3; k++) hb[k] = -(ybb[k] - yd * hh[k]) / hn;
+            for (int k = 0; k < 3; k++) hb[k] = -(ybb[k] - yd * hh[k]) * ihn;
             rb[0] += v[1] * hb[2] - v[2] * hb[1];
             rb[1] += v[2] * hb[0] - v[0] * hb[2];
             rb[2] += v[0] * hb[1] - v[1] * hb[0];
@@ -564,9 +571,10 @@ __global__ void k_adj_prop_out(int n, PropDev P, int stage, const StageRec *rec,
             vb[1] += hb[2] * y[0] - hb[0] * y[2];
             vb[2] += hb[0] * y[1] - hb[1] * y[0];
             double rn = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
-            double rh[3] = {y[0] / rn, y[1] / rn, y[2] / rn};
+            const double irn = 1.0 / rn;
+            double rh[3] = {y[0] * irn, y[1] * irn, y[2] * irn};
             double zd = zbb[0] * rh[0] + zbb[1] * rh[1] + zbb[2] * rh[2];
-            for (int k = 0; k < 3; k++) rb[k] += -(zbb[k] - zd * rh[k]) / rn;
+            for (int k = 0; k < 3; k++) rb[k] += -(zbb[k] - zd * rh[k]) * irn;
         }
         // Q of the normalised quaternion, differentiated
         double g[4];

@@ -437,12 +437,14 @@ struct AdjArgs {
     int *win_pid;                // [S][kAdjWinBlocks][4] and their vertices
     int n_verts;                 // most vertices of the slots' meshes
     double *partials;            // [S][nb][width]
+    double *partials2;           // [S][ceil(nb / kAdjSumRun)][width] runs of kAdjSumRun partials summed, when nb > 2 kAdjSumRun
     double *g_sun;               // [n][3] out
     double *g_dist;              // [n] out, or null
     double *g_eval;              // [n][2 n_mats + n_parts] out: per-evaluation coefficient and angle terms
 };
 constexpr int kAdjFixed = 14;    // dbar(3) ubar(3) vbar(3) umin umax vmin vmax, sum of the local loss
 constexpr int kAdjWinBlocks = 32;  // most blocks a slot's window search uses
+constexpr int kAdjSumRun = 32;     // ray-block partials one block of the first summing level adds
 int adj_blocks(int S, size_t rays);
 cudaError_t launch_adjoint(const AdjArgs &a, int S, cudaStream_t st);
 cudaError_t launch_adj_sum(const double *g_eval, int n, int n_mats, int n_parts, double *g_mat, double *g_angle,
