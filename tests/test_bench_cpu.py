@@ -46,3 +46,21 @@ def test_parity_record_reads_the_stored_oracle_forces():
     assert abs(rec["force_rel_err_max"] - 2e-5) < 1e-12
     # sizes the file holds no oracle values for
     assert bench.parity_record(_FakeCtx(_rows()), 0, SimpleNamespace(facet=0.025, N=512, bounces=1)) is None
+
+
+def test_relative_errors_and_golden_rows():
+    """The per-direction error the bench reports: force relative to the oracle
+    force's norm, torque relative to the larger of the oracle's torque and force
+    norms (a torque near zero is judged against the force's scale); and the
+    stored rows it compares with."""
+    sys.path.insert(0, ROOT)
+    import bench
+    Fo = np.array([[3.0, 4.0, 0.0], [0.0, 0.0, 2.0]])
+    To = np.array([[0.0, 0.0, 10.0], [0.0, 0.0, 0.0]])
+    F = Fo + np.array([[0.0, 0.0, 5e-5], [1e-4, 0.0, 0.0]])
+    T = To + np.array([[0.0, 1e-3, 0.0], [0.0, 2e-4, 0.0]])
+    rf, rt = bench._rel_errors(F, T, Fo, To)
+    assert np.allclose(rf, [1e-5, 5e-5]) and np.allclose(rt, [1e-4, 1e-4])
+    rows = bench._golden_rows("boxwing_forces.txt")
+    assert len(rows) == 256 and all(len(r) == 7 for r in rows)
+    assert bench._golden_rows("no_such_file.txt") == []
